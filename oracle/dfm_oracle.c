@@ -1,0 +1,660 @@
+/*
+ * FP64 CPU oracle for discrete flow mapping (DFM) on tetrahedral meshes.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the
+ * benchmark's CPU-baseline leg may call this code; the product path never
+ * does.  It shares no code with the CUDA library.
+ *
+ * What it computes (Bajars, Chappell, Sondergaard, Tanner, "Transport of
+ * phase space densities through tetrahedral meshes using discrete flow
+ * mapping"):
+ *
+ *   B_IJ = lambda * N_{n'm'} / sqrt(|T_l| |T_l'|)
+ *          * Int_{hemisphere} Z_{n'}^{m'}(p') Z_n^m(p) S_{l->l'}(d) cos(theta) dw
+ *
+ * (Sec. 3.2, Eqs. Bapprox and B4DInt with rho = sin(theta), so that
+ * rho drho dphi = cos(theta) dw), where S_{l->l'}(d) is the damped area of the
+ * set of source points on face l whose ray in direction d leaves the tet
+ * through face l' (Sec. 3.3), N_{n'm'} = (2n'+2)/(eps_{m'} pi) is the inverse
+ * Zernike norm (Sec. 3.1) and lambda the reflection/transmission weight.
+ *
+ * Routes chosen to be independent of the GPU path:
+ *   - Zernike radial polynomials by the factorial closed form and angles by
+ *     atan2/cos/sin (the GPU uses the recursion of Sec. 3.1);
+ *   - S_{l->l'}(d) by projecting face l' onto the plane of face l along d,
+ *     clipping against face l (Sutherland-Hodgman) and integrating exp(-mu L)
+ *     over the clipped polygon with a collapsed Gauss rule (the GPU uses the
+ *     closed form of Sec. 3.3 on the triangle OBC);
+ *   - the direction integral over the seven sub-regions of Sec. 3.4, each
+ *     mapped from [-1,1]^2 by the bilinear map of Eq. (Parametr) and projected
+ *     onto the hemisphere, with tensor Gauss-Legendre nodes supplied by the
+ *     caller (numpy) and the order doubled until successive estimates agree.
+ *
+ * Conventions (the paper leaves the face frame open, Sec. 3.3): tet t has
+ * vertices (v0,v1,v2,v3); face f is opposite v_f with vertices
+ * (v_{f+1}, v_{f+2}, v_{f+3}) mod 4; row 4t+f.  Frame origin = first face
+ * vertex, e1 = unit(second - first), n = inward unit normal (towards v_f),
+ * e2 = n x e1.  Momentum p = (d.e1, d.e2) for inward unit direction d.
+ * Zernike index idx = (n(n+2)+m)/2, m = -n, -n+2, ..., n.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef struct { double x, y, z; } vec3;
+
+static vec3 v3(double x, double y, double z) { vec3 r = {x, y, z}; return r; }
+static vec3 vadd(vec3 a, vec3 b) { return v3(a.x + b.x, a.y + b.y, a.z + b.z); }
+static vec3 vsub(vec3 a, vec3 b) { return v3(a.x - b.x, a.y - b.y, a.z - b.z); }
+static vec3 vscale(vec3 a, double s) { return v3(a.x * s, a.y * s, a.z * s); }
+static double vdot(vec3 a, vec3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+static vec3 vcross(vec3 a, vec3 b) {
+  return v3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+static double vnorm(vec3 a) { return sqrt(vdot(a, a)); }
+static vec3 vunit(vec3 a) { return vscale(a, 1.0 / vnorm(a)); }
+
+static vec3 vert(const double* V, int64_t i) { return v3(V[3 * i], V[3 * i + 1], V[3 * i + 2]); }
+
+/* ------------------------------------------------------------------------ */
+/* Face geometry                                                             */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  vec3 p[3];      /* face vertices in frame order */
+  vec3 apex;      /* tet vertex opposite the face */
+  vec3 e1, e2, n; /* tangent axes and inward unit normal */
+  double area;
+} face_t;
+
+static void face_of(const double* V, const int32_t* T, int64_t t, int f, face_t* F) {
+  const int32_t* tv = T + 4 * t;
+  for (int k = 0; k < 3; ++k) F->p[k] = vert(V, tv[(f + 1 + k) % 4]);
+  F->apex = vert(V, tv[f]);
+  vec3 a = vsub(F->p[1], F->p[0]), b = vsub(F->p[2], F->p[0]);
+  vec3 c = vcross(a, b);
+  F->area = 0.5 * vnorm(c);
+  if (vdot(c, vsub(F->apex, F->p[0])) < 0) c = vscale(c, -1.0);
+  F->n = vunit(c);
+  F->e1 = vunit(a);
+  F->e2 = vcross(F->n, F->e1);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Zernike polynomials (Sec. 3.1): factorial closed form + atan2 angles      */
+/* ------------------------------------------------------------------------ */
+
+static double factorial(int k) {
+  double r = 1.0;
+  for (int i = 2; i <= k; ++i) r *= i;
+  return r;
+}
+
+/* R_n^m(rho) = sum_k (-1)^k (n-k)! / (k! ((n+m)/2-k)! ((n-m)/2-k)!) rho^(n-2k) */
+static double zern_radial(int n, int m, double rho) {
+  if (m < 0) m = -m;
+  if (m > n || ((n - m) & 1)) return 0.0;
+  double s = 0.0;
+  for (int k = 0; k <= (n - m) / 2; ++k) {
+    double c = factorial(n - k) / (factorial(k) * factorial((n + m) / 2 - k) * factorial((n - m) / 2 - k));
+    if (k & 1) c = -c;
+    s += c * pow(rho, n - 2 * k);
+  }
+  return s;
+}
+
+static int nbasis(int Np) { return (Np + 1) * (Np + 2) / 2; }
+
+static void zern_all(int Np, double px, double py, double* Z) {
+  double rho = sqrt(px * px + py * py);
+  double phi = rho > 0.0 ? atan2(py, px) : 0.0;
+  for (int n = 0; n <= Np; ++n)
+    for (int m = -n; m <= n; m += 2) {
+      int idx = (n * (n + 2) + m) / 2;
+      double R = zern_radial(n, m, rho);
+      Z[idx] = m >= 0 ? R * cos(m * phi) : R * sin(-m * phi);
+    }
+}
+
+/* inverse norm N_{nm} = (2n+2)/(eps_m pi), eps_0 = 2 */
+static double zern_invnorm(int n, int m) { return (2.0 * n + 2.0) / ((m == 0 ? 2.0 : 1.0) * M_PI); }
+
+void orc_zernike(int Np, int64_t npts, const double* px, const double* py, double* out) {
+  int nb = nbasis(Np);
+  for (int64_t i = 0; i < npts; ++i) zern_all(Np, px[i], py[i], out + i * nb);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Spatial integral S_{l->l'}(d) by projection and clipping (Sec. 3.3)       */
+/* ------------------------------------------------------------------------ */
+
+typedef struct { double x, y, L; } pt2;
+
+/* Clip a convex polygon (in face-plane coordinates, carrying the affine value L)
+ * against the half-plane a*x + b*y + c >= 0. */
+static int clip_half(const pt2* in, int nin, pt2* out, double a, double b, double c) {
+  int nout = 0;
+  for (int i = 0; i < nin; ++i) {
+    pt2 P = in[i], Q = in[(i + 1) % nin];
+    double fp = a * P.x + b * P.y + c, fq = a * Q.x + b * Q.y + c;
+    if (fp >= 0) out[nout++] = P;
+    if ((fp >= 0) != (fq >= 0)) {
+      double s = fp / (fp - fq);
+      pt2 R = {P.x + s * (Q.x - P.x), P.y + s * (Q.y - P.y), P.L + s * (Q.L - P.L)};
+      out[nout++] = R;
+    }
+  }
+  return nout;
+}
+
+/* Integral of exp(-mu L) (and of -L exp(-mu L)) over a triangle whose vertex
+ * values of the affine function L are given; collapsed (Duffy) tensor Gauss. */
+static void tri_exp_integral(pt2 A, pt2 B, pt2 C, double mu, int nq, const double* gx, const double* gw,
+                             double* val, double* dval) {
+  double area = 0.5 * fabs((B.x - A.x) * (C.y - A.y) - (C.x - A.x) * (B.y - A.y));
+  double s = 0.0, ds = 0.0;
+  for (int i = 0; i < nq; ++i) {
+    double u = 0.5 * (1.0 + gx[i]);
+    for (int j = 0; j < nq; ++j) {
+      double v = (1.0 - u) * 0.5 * (1.0 + gx[j]);
+      double w = gw[i] * gw[j] * 0.25 * (1.0 - u); /* du dv on the unit simplex */
+      double L = A.L + u * (B.L - A.L) + v * (C.L - A.L);
+      double e = exp(-mu * L);
+      s += w * e;
+      ds += w * (-L * e);
+    }
+  }
+  *val += 2.0 * area * s;
+  *dval += 2.0 * area * ds;
+}
+
+/* S(d) = Int_{s in src, ray s + t d exits through dst} exp(-mu L(s)) ds.
+ * dst: the three vertices of the destination face, dst_n its outward unit
+ * normal (pointing out of the tet).  Returns also dS/dmu and the clipped area. */
+static double spatial_clip(const face_t* src, const vec3* dst, vec3 dst_n, vec3 d, double mu, int nq,
+                           const double* gx, const double* gw, double* dS, double* area_out) {
+  double dn = vdot(d, src->n);
+  double ddst = vdot(d, dst_n);
+  pt2 poly[16], tmp[16];
+  int np = 3;
+  for (int k = 0; k < 3; ++k) {
+    /* project dst vertex X onto the source plane along d: X' = X - t d */
+    double t = vdot(vsub(dst[k], src->p[0]), src->n) / dn;
+    vec3 Xp = vsub(dst[k], vscale(d, t));
+    vec3 r = vsub(Xp, src->p[0]);
+    poly[k].x = vdot(r, src->e1);
+    poly[k].y = vdot(r, src->e2);
+    poly[k].L = t; /* distance from X' to X along d */
+  }
+  (void)ddst;
+  /* source triangle in plane coordinates, counter-clockwise */
+  double sx[3], sy[3];
+  for (int k = 0; k < 3; ++k) {
+    vec3 r = vsub(src->p[k], src->p[0]);
+    sx[k] = vdot(r, src->e1);
+    sy[k] = vdot(r, src->e2);
+  }
+  double orient = (sx[1] - sx[0]) * (sy[2] - sy[0]) - (sx[2] - sx[0]) * (sy[1] - sy[0]);
+  double sgn = orient > 0 ? 1.0 : -1.0;
+  /* make the projected destination polygon counter-clockwise too (not needed
+   * for clipping correctness, only for the fan) */
+  for (int k = 0; k < 3 && np > 0; ++k) {
+    int k1 = (k + 1) % 3;
+    double ex = sx[k1] - sx[k], ey = sy[k1] - sy[k];
+    /* inside: sgn * cross(edge, p - start) >= 0 */
+    double a = -sgn * ey, b = sgn * ex, c = -(a * sx[k] + b * sy[k]);
+    np = clip_half(poly, np, tmp, a, b, c);
+    memcpy(poly, tmp, sizeof(pt2) * np);
+  }
+  double S = 0.0, dSv = 0.0, area = 0.0;
+  for (int k = 1; k + 1 < np; ++k) {
+    tri_exp_integral(poly[0], poly[k], poly[k + 1], mu, nq, gx, gw, &S, &dSv);
+    area += 0.5 * fabs((poly[k].x - poly[0].x) * (poly[k + 1].y - poly[0].y) -
+                       (poly[k + 1].x - poly[0].x) * (poly[k].y - poly[0].y));
+  }
+  if (dS) *dS = dSv;
+  if (area_out) *area_out = area;
+  return S;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Direction sub-regions (Sec. 3.3-3.4)                                      */
+/* ------------------------------------------------------------------------ */
+
+/* For source face l and destination face l' of the same tet: A = the source
+ * vertex not on l' (tet vertex l'), B and C the two shared vertices (in face
+ * order), D the apex (tet vertex l).  The point P where the ray through D
+ * meets the source plane falls in one of seven regions cut out by the lines
+ * AB, BC, CA; as directions these are spherical polygons with generators
+ *   0 interior      {D-A, D-B, D-C}
+ *   1 wedge at A    {D-A, B-A, C-A}
+ *   2 strip on AB   {D-A, D-B, C-B, C-A}
+ *   3 strip on AC   {D-A, D-C, B-C, B-A}
+ *   4 wedge at B    {D-B, C-B, A-B}
+ *   5 wedge at C    {D-C, A-C, B-C}
+ *   6 strip on BC   {D-B, D-C, A-C, A-B}
+ * Regions 4-6 give an empty integration triangle for l' (Sec. 3.3). */
+static int region_generators(const face_t* src, vec3 A, vec3 B, vec3 C, int region, vec3* g) {
+  vec3 D = src->apex;
+  switch (region) {
+    case 0: g[0] = vsub(D, A); g[1] = vsub(D, B); g[2] = vsub(D, C); return 3;
+    case 1: g[0] = vsub(D, A); g[1] = vsub(B, A); g[2] = vsub(C, A); return 3;
+    case 2: g[0] = vsub(D, A); g[1] = vsub(D, B); g[2] = vsub(C, B); g[3] = vsub(C, A); return 4;
+    case 3: g[0] = vsub(D, A); g[1] = vsub(D, C); g[2] = vsub(B, C); g[3] = vsub(B, A); return 4;
+    case 4: g[0] = vsub(D, B); g[1] = vsub(C, B); g[2] = vsub(A, B); return 3;
+    case 5: g[0] = vsub(D, C); g[1] = vsub(A, C); g[2] = vsub(B, C); return 3;
+    default: g[0] = vsub(D, B); g[1] = vsub(D, C); g[2] = vsub(A, C); g[3] = vsub(A, B); return 4;
+  }
+}
+
+/* Bilinear map of Eq. (Parametr) through unit generators v1..v4 (v4 = v1 for a
+ * triangle).  Returns the unit direction and the Jacobian of Sec. 3.4, which
+ * includes the factor cos(theta) = sin(2 theta)/(2 sin theta). */
+static vec3 bilinear_dir(const vec3* v, double xi, double eta, vec3 n, double* jac) {
+  vec3 a = vscale(vadd(vadd(v[0], v[1]), vadd(v[2], v[3])), 0.25);
+  vec3 b = vscale(vsub(vadd(v[1], v[2]), vadd(v[0], v[3])), 0.25);
+  vec3 c = vscale(vsub(vadd(v[2], v[3]), vadd(v[0], v[1])), 0.25);
+  vec3 dd = vscale(vsub(vadd(v[2], v[0]), vadd(v[3], v[1])), 0.25);
+  vec3 f = vadd(vadd(a, vscale(b, xi)), vadd(vscale(c, eta), vscale(dd, xi * eta)));
+  vec3 fx = vadd(b, vscale(dd, eta));
+  vec3 fe = vadd(c, vscale(dd, xi));
+  double r = vnorm(f);
+  double det = vdot(f, vcross(fx, fe));
+  *jac = fabs(vdot(f, n) * det) / (r * r * r * r);
+  return vscale(f, 1.0 / r);
+}
+
+static void region_unit_gens(const face_t* src, vec3 A, vec3 B, vec3 C, int region, vec3* v) {
+  vec3 g[4];
+  int ng = region_generators(src, A, B, C, region, g);
+  for (int k = 0; k < ng; ++k) v[k] = vunit(g[k]);
+  if (ng == 3) v[3] = v[0];
+}
+
+/* projected solid angle Int cos(theta) dw of one region by the quadrature */
+double orc_region_cos_measure(const double* V, const int32_t* T, int64_t t, int f, int fp, int region, int q,
+                              const double* gx, const double* gw) {
+  face_t src;
+  face_of(V, T, t, f, &src);
+  const int32_t* tv = T + 4 * t;
+  vec3 A = vert(V, tv[fp]);
+  vec3 BC[2];
+  int nb = 0;
+  for (int k = 0; k < 4; ++k)
+    if (k != f && k != fp) BC[nb++] = vert(V, tv[k]);
+  vec3 v[4];
+  region_unit_gens(&src, A, BC[0], BC[1], region, v);
+  double s = 0.0;
+  for (int i = 0; i < q; ++i)
+    for (int j = 0; j < q; ++j) {
+      double jac;
+      bilinear_dir(v, gx[i], gx[j], src.n, &jac);
+      s += gw[i] * gw[j] * jac;
+    }
+  return s;
+}
+
+/* ------------------------------------------------------------------------ */
+/* One operator block                                                        */
+/* ------------------------------------------------------------------------ */
+
+/* Block for source face (t,f) -> destination face fp of tet t, received by row
+ * recv_row (the neighbour's row across fp, or 4t+fp on the boundary), with
+ * weight lam and damping mu of tet t.  out: nb x nb row-major, row = test
+ * index (n',m') on the receiving face, column = trial index (n,m) on the
+ * source face.  dout (optional): d(block)/d(mu).  regions_mask selects which
+ * of the seven direction regions are integrated (0x0F = the four non-empty
+ * ones; 0x7F = all seven, for checks). */
+static void block_fixed(const double* V, const int32_t* T, int64_t t, int f, int fp, int64_t recv_row,
+                        double mu, double lam, int Np, int q, const double* gx, const double* gw, int nq_tri,
+                        const double* tx, const double* tw, int regions_mask, double* out, double* dout) {
+  int nb = nbasis(Np);
+  face_t src, dstf, recv;
+  face_of(V, T, t, f, &src);
+  face_of(V, T, t, fp, &dstf);
+  face_of(V, T, recv_row / 4, (int)(recv_row % 4), &recv);
+  const int32_t* tv = T + 4 * t;
+  vec3 A = vert(V, tv[fp]);
+  vec3 BC[2];
+  int k2 = 0;
+  for (int k = 0; k < 4; ++k)
+    if (k != f && k != fp) BC[k2++] = vert(V, tv[k]);
+  vec3 dst_n_out = vscale(dstf.n, -1.0);
+  double* Zp = (double*)malloc(sizeof(double) * nb);
+  double* Zq = (double*)malloc(sizeof(double) * nb);
+  memset(out, 0, sizeof(double) * nb * nb);
+  if (dout) memset(dout, 0, sizeof(double) * nb * nb);
+  for (int region = 0; region < 7; ++region) {
+    if (!(regions_mask & (1 << region))) continue;
+    vec3 v[4];
+    region_unit_gens(&src, A, BC[0], BC[1], region, v);
+    for (int i = 0; i < q; ++i)
+      for (int j = 0; j < q; ++j) {
+        double jac;
+        vec3 d = bilinear_dir(v, gx[i], gx[j], src.n, &jac);
+        double w = gw[i] * gw[j] * jac;
+        double dS;
+        double S = spatial_clip(&src, dstf.p, dst_n_out, d, mu, nq_tri, tx, tw, &dS, NULL);
+        if (S == 0.0 && dS == 0.0) continue;
+        zern_all(Np, vdot(d, src.e1), vdot(d, src.e2), Zp);
+        zern_all(Np, vdot(d, recv.e1), vdot(d, recv.e2), Zq);
+        for (int a = 0; a < nb; ++a) {
+          double wa = w * Zq[a];
+          for (int b = 0; b < nb; ++b) {
+            out[a * nb + b] += wa * S * Zp[b];
+            if (dout) dout[a * nb + b] += wa * dS * Zp[b];
+          }
+        }
+      }
+  }
+  double sc = lam / sqrt(src.area * dstf.area);
+  for (int n = 0; n <= Np; ++n)
+    for (int m = -n; m <= n; m += 2) {
+      int a = (n * (n + 2) + m) / 2;
+      double s = sc * zern_invnorm(n, m);
+      for (int b = 0; b < nb; ++b) {
+        out[a * nb + b] *= s;
+        if (dout) dout[a * nb + b] *= s;
+      }
+    }
+  free(Zp);
+  free(Zq);
+}
+
+/* Gauss-Legendre table: levels k = 0..nlev-1 with orders qs[k], nodes/weights
+ * at offset offs[k] in gx/gw. */
+typedef struct {
+  int nlev;
+  const int* qs;
+  const int* offs;
+  const double* gx;
+  const double* gw;
+} gl_table;
+
+/* Blocks for a list of face pairs.  Fixed order: level = lev0 only (rtol <= 0).
+ * Adaptive: start at level lev0, double (next level) until the block max-norm
+ * change is <= rtol * block max-norm; q_used returns the accepted order (or
+ * -order if the top level was reached without meeting rtol). */
+int orc_blocks(const double* V, const int32_t* T, int64_t npairs, const int64_t* tet, const int32_t* f,
+               const int32_t* fp, const int64_t* recv_row, const double* mu, const double* lam, int Np,
+               int nlev, const int* qs, const int* offs, const double* gx, const double* gw, int lev0,
+               double rtol, int tri_lev, int regions_mask, int nthreads, double* out, double* dout,
+               int32_t* q_used) {
+  int nb = nbasis(Np);
+  gl_table G = {nlev, qs, offs, gx, gw};
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+  (void)nthreads;
+#endif
+#pragma omp parallel
+  {
+    double* prev = (double*)malloc(sizeof(double) * nb * nb);
+    double* prevd = (double*)malloc(sizeof(double) * nb * nb);
+#pragma omp for schedule(dynamic, 4)
+    for (int64_t i = 0; i < npairs; ++i) {
+      double* o = out + i * nb * nb;
+      double* od = dout ? dout + i * nb * nb : NULL;
+      const double* tx = G.gx + G.offs[tri_lev];
+      const double* tw = G.gw + G.offs[tri_lev];
+      int nt = G.qs[tri_lev];
+      int lev = lev0;
+      block_fixed(V, T, tet[i], f[i], fp[i], recv_row[i], mu[i], lam[i], Np, G.qs[lev], G.gx + G.offs[lev],
+                  G.gw + G.offs[lev], nt, tx, tw, regions_mask, o, od);
+      int accepted = rtol > 0 ? -G.qs[lev] : G.qs[lev];
+      while (rtol > 0 && lev + 1 < G.nlev) {
+        memcpy(prev, o, sizeof(double) * nb * nb);
+        if (od) memcpy(prevd, od, sizeof(double) * nb * nb);
+        ++lev;
+        block_fixed(V, T, tet[i], f[i], fp[i], recv_row[i], mu[i], lam[i], Np, G.qs[lev], G.gx + G.offs[lev],
+                    G.gw + G.offs[lev], nt, tx, tw, regions_mask, o, od);
+        double dmax = 0.0, bmax = 0.0, ddmax = 0.0, dbmax = 0.0;
+        for (int k = 0; k < nb * nb; ++k) {
+          dmax = fmax(dmax, fabs(o[k] - prev[k]));
+          bmax = fmax(bmax, fabs(o[k]));
+          if (od) {
+            ddmax = fmax(ddmax, fabs(od[k] - prevd[k]));
+            dbmax = fmax(dbmax, fabs(od[k]));
+          }
+        }
+        if (dmax <= rtol * bmax && (!od || ddmax <= rtol * dbmax)) {
+          accepted = G.qs[lev];
+          break;
+        }
+        accepted = -G.qs[lev];
+      }
+      if (q_used) q_used[i] = accepted;
+    }
+    free(prev);
+    free(prevd);
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Monte Carlo ray tracing of one block (brute-force pin)                   */
+/* ------------------------------------------------------------------------ */
+
+static uint64_t splitmix64(uint64_t* s) {
+  uint64_t z = (*s += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+static double urand(uint64_t* s) { return (splitmix64(s) >> 11) * (1.0 / 9007199254740992.0); }
+
+/* Estimate of the block (t,f)->(t,fp) received by recv_row, and its standard
+ * error, from nsamp samples: s uniform on face f, p uniform on the unit disc
+ * (a cosine-weighted inward direction), the ray traced to the face it leaves
+ * through; B = lam N_{n'm'} pi sqrt(A_l/A_l') E[Z(p') Z(p) exp(-mu L) 1{exit=l'}]. */
+int orc_mc_block(const double* V, const int32_t* T, int64_t t, int f, int fp, int64_t recv_row, double mu,
+                 double lam, int Np, int64_t nsamp, uint64_t seed, int nthreads, double* mean, double* stderr_) {
+  int nb = nbasis(Np);
+  face_t src, recv, faces[4];
+  face_of(V, T, t, f, &src);
+  face_of(V, T, recv_row / 4, (int)(recv_row % 4), &recv);
+  for (int k = 0; k < 4; ++k) face_of(V, T, t, k, &faces[k]);
+  double* S1 = (double*)calloc(nb * nb, sizeof(double));
+  double* S2 = (double*)calloc(nb * nb, sizeof(double));
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+  (void)nthreads;
+#endif
+#pragma omp parallel
+  {
+    double* s1 = (double*)calloc(nb * nb, sizeof(double));
+    double* s2 = (double*)calloc(nb * nb, sizeof(double));
+    double* Zp = (double*)malloc(sizeof(double) * nb);
+    double* Zq = (double*)malloc(sizeof(double) * nb);
+#pragma omp for schedule(static)
+    for (int64_t chunk = 0; chunk < 1024; ++chunk) {
+      /* independent stream per chunk: start at a hashed point of the 2^64 cycle */
+      uint64_t h = seed ^ ((uint64_t)chunk * 0xD1B54A32D192ED03ull);
+      uint64_t st = splitmix64(&h);
+      st ^= splitmix64(&h) << 1;
+      int64_t lo = nsamp * chunk / 1024, hi = nsamp * (chunk + 1) / 1024;
+      for (int64_t i = lo; i < hi; ++i) {
+        /* uniform point on the source triangle */
+        double r1 = urand(&st), r2 = urand(&st);
+        if (r1 + r2 > 1.0) { r1 = 1.0 - r1; r2 = 1.0 - r2; }
+        vec3 s = vadd(src.p[0], vadd(vscale(vsub(src.p[1], src.p[0]), r1), vscale(vsub(src.p[2], src.p[0]), r2)));
+        /* uniform point on the unit disc by rejection */
+        double px, py;
+        do {
+          px = 2.0 * urand(&st) - 1.0;
+          py = 2.0 * urand(&st) - 1.0;
+        } while (px * px + py * py >= 1.0);
+        double pz = sqrt(1.0 - px * px - py * py);
+        vec3 d = vadd(vadd(vscale(src.e1, px), vscale(src.e2, py)), vscale(src.n, pz));
+        /* exit face: smallest positive distance to the other three face planes */
+        int ex = -1;
+        double L = 1e300;
+        for (int k = 0; k < 4; ++k) {
+          if (k == f) continue;
+          double dn = -vdot(d, faces[k].n); /* outward normal component */
+          if (dn <= 0) continue;
+          double tk = vdot(vsub(s, faces[k].p[0]), faces[k].n) / dn;
+          if (tk < L) { L = tk; ex = k; }
+        }
+        if (ex != fp) continue;
+        double e = exp(-mu * L);
+        zern_all(Np, px, py, Zp);
+        zern_all(Np, vdot(d, recv.e1), vdot(d, recv.e2), Zq);
+        for (int a = 0; a < nb; ++a)
+          for (int b = 0; b < nb; ++b) {
+            double x = Zq[a] * Zp[b] * e;
+            s1[a * nb + b] += x;
+            s2[a * nb + b] += x * x;
+          }
+      }
+    }
+#pragma omp critical
+    for (int k = 0; k < nb * nb; ++k) {
+      S1[k] += s1[k];
+      S2[k] += s2[k];
+    }
+    free(s1); free(s2); free(Zp); free(Zq);
+  }
+  double Adst = faces[fp].area;
+  for (int n = 0; n <= Np; ++n)
+    for (int m = -n; m <= n; m += 2) {
+      int a = (n * (n + 2) + m) / 2;
+      double sc = lam * zern_invnorm(n, m) * M_PI * sqrt(src.area / Adst);
+      for (int b = 0; b < nb; ++b) {
+        double m1 = S1[a * nb + b] / (double)nsamp;
+        double var = S2[a * nb + b] / (double)nsamp - m1 * m1;
+        mean[a * nb + b] = sc * m1;
+        stderr_[a * nb + b] = fabs(sc) * sqrt(fmax(var, 0.0) / (double)nsamp);
+      }
+    }
+  free(S1);
+  free(S2);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Per-direction spatial quantities (for checks)                            */
+/* ------------------------------------------------------------------------ */
+
+/* For direction d (global, need not be unit) from source face (t,f): the clipped
+ * area and damped integral for each destination fp != f, plus the brute-force
+ * check quantity Int_{face} exp(-mu L_exit) over a grid of nsub^2 sub-triangles
+ * is left to callers.  out_S[3], out_area[3] ordered by fp ascending. */
+void orc_spatial(const double* V, const int32_t* T, int64_t t, int f, const double* dir, double mu, int nq,
+                 const double* gx, const double* gw, double* out_S, double* out_dS, double* out_area) {
+  face_t src, dstf;
+  face_of(V, T, t, f, &src);
+  vec3 d = vunit(v3(dir[0], dir[1], dir[2]));
+  int k = 0;
+  for (int fp = 0; fp < 4; ++fp) {
+    if (fp == f) continue;
+    face_of(V, T, t, fp, &dstf);
+    out_S[k] = spatial_clip(&src, dstf.p, vscale(dstf.n, -1.0), d, mu, nq, gx, gw, &out_dS[k], &out_area[k]);
+    ++k;
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Interior density functional (Sec. 4.1, Eq. IntDens)                      */
+/* ------------------------------------------------------------------------ */
+
+/* g-vector of the interior density at point r inside tet t:
+ *   rho_T(r) = sum_{l, nm} rho_(t,l,nm) g_(l,nm),
+ *   g_(l,nm) = (1/sqrt|T_l|) Int_{T_l} Z_nm(p(s->r)) cos(vartheta) exp(-mu|r-s|)/|r-s|^2 ds
+ * (c = 1), with p(s->r) the tangential part of unit(r - s) in face l's frame.
+ * out: [4][nb]; dout: d/dmu of the same.  Collapsed Gauss of order nq per face. */
+void orc_interior_g(const double* V, const int32_t* T, int64_t t, const double* r, double mu, int Np, int nq,
+                    const double* gx, const double* gw, double* out, double* dout) {
+  int nb = nbasis(Np);
+  double* Z = (double*)malloc(sizeof(double) * nb);
+  vec3 R = v3(r[0], r[1], r[2]);
+  for (int l = 0; l < 4; ++l) {
+    face_t F;
+    face_of(V, T, t, l, &F);
+    double* o = out + l * nb;
+    double* od = dout + l * nb;
+    for (int k = 0; k < nb; ++k) o[k] = od[k] = 0.0;
+    vec3 e1 = vsub(F.p[1], F.p[0]), e2 = vsub(F.p[2], F.p[0]);
+    for (int i = 0; i < nq; ++i) {
+      double u = 0.5 * (1.0 + gx[i]);
+      for (int j = 0; j < nq; ++j) {
+        double v = (1.0 - u) * 0.5 * (1.0 + gx[j]);
+        double w = gw[i] * gw[j] * 0.25 * (1.0 - u) * 2.0 * F.area;
+        vec3 s = vadd(F.p[0], vadd(vscale(e1, u), vscale(e2, v)));
+        vec3 rs = vsub(R, s);
+        double dist = vnorm(rs);
+        vec3 dd = vscale(rs, 1.0 / dist);
+        double cosv = vdot(dd, F.n);
+        double ker = cosv * exp(-mu * dist) / (dist * dist);
+        zern_all(Np, vdot(dd, F.e1), vdot(dd, F.e2), Z);
+        for (int k = 0; k < nb; ++k) {
+          o[k] += w * ker * Z[k];
+          od[k] += w * (-dist) * ker * Z[k];
+        }
+      }
+    }
+    double sc = 1.0 / sqrt(F.area);
+    for (int k = 0; k < nb; ++k) {
+      o[k] *= sc;
+      od[k] *= sc;
+    }
+  }
+  free(Z);
+}
+
+/* ------------------------------------------------------------------------ */
+/* FP64 operator application in the oracle's own layout                      */
+/* ------------------------------------------------------------------------ */
+
+/* Oracle layout: column J = 4t+f owns 3 blocks (destination faces fp != f in
+ * ascending order), blocks[J][k][nb][nb], received by dest[J][k].
+ * y = x0 + alpha * B x  (trans = 0) or  y = x0 + alpha * B^T x  (trans = 1).
+ * x, y, x0: [nrows][nb] for a single right-hand side. */
+void orc_apply(int64_t nrows, int nb, const double* blocks, const int64_t* dest, const double* x,
+               const double* x0, double alpha, int trans, int nthreads, double* y) {
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+  (void)nthreads;
+#endif
+  if (!trans) {
+    /* products of every block with its column's coefficients (parallel), then
+     * a serial scatter-add into the receiving rows */
+    double* prod = (double*)malloc(sizeof(double) * nrows * 3 * nb);
+#pragma omp parallel for schedule(static)
+    for (int64_t J = 0; J < nrows; ++J)
+      for (int k = 0; k < 3; ++k) {
+        const double* blk = blocks + ((J * 3 + k) * (int64_t)nb) * nb;
+        for (int a = 0; a < nb; ++a) {
+          double s = 0.0;
+          for (int b = 0; b < nb; ++b) s += blk[a * nb + b] * x[J * nb + b];
+          prod[(J * 3 + k) * nb + a] = s;
+        }
+      }
+    for (int64_t i = 0; i < nrows * nb; ++i) y[i] = x0 ? x0[i] : 0.0;
+    for (int64_t J = 0; J < nrows; ++J)
+      for (int k = 0; k < 3; ++k) {
+        int64_t R = dest[3 * J + k];
+        for (int a = 0; a < nb; ++a) y[R * nb + a] += alpha * prod[(J * 3 + k) * nb + a];
+      }
+    free(prod);
+  } else {
+#pragma omp parallel for schedule(static)
+    for (int64_t J = 0; J < nrows; ++J) {
+      for (int b = 0; b < nb; ++b) {
+        double s = 0.0;
+        for (int k = 0; k < 3; ++k) {
+          int64_t R = dest[3 * J + k];
+          const double* blk = blocks + ((J * 3 + k) * (int64_t)nb) * nb;
+          for (int a = 0; a < nb; ++a) s += blk[a * nb + b] * x[R * nb + a];
+        }
+        y[J * nb + b] = (x0 ? x0[J * nb + b] : 0.0) + alpha * s;
+      }
+    }
+  }
+}

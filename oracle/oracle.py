@@ -1,0 +1,475 @@
+"""Python side of the FP64 CPU oracle for discrete flow mapping.
+
+TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's
+CPU-baseline leg are the only callers.  The product (the CUDA library and its
+binding) never imports this module, and this module imports nothing from the
+product except the seeded input generators, which hold no method arithmetic.
+
+The quadrature-heavy parts live in dfm_oracle.c (loaded through ctypes); this
+file does the orchestration in plain numpy: mesh topology by a dictionary of
+sorted vertex triples, the Galerkin source vector, operator application,
+direct and Krylov solves, the interior density functional and the adjoint
+gradient.  Each function names the part of the paper it follows.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "dfm_oracle.c")
+_LIBDIR = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_LIBDIR, "liboracle.so")
+
+
+def build(force: bool = False) -> str:
+    """Compile dfm_oracle.c into oracle/_build/liboracle.so (gcc, OpenMP)."""
+    os.makedirs(_LIBDIR, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-std=gnu11", "-O2", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+_dp = ctypes.POINTER(ctypes.c_double)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = ctypes.CDLL(build())
+        L.orc_blocks.restype = ctypes.c_int
+        L.orc_mc_block.restype = ctypes.c_int
+        L.orc_region_cos_measure.restype = ctypes.c_double
+        _lib = L
+    return _lib
+
+
+def _p(a, typ=_dp):
+    return a.ctypes.data_as(typ)
+
+
+def nbasis(Np: int) -> int:
+    """Number of momentum basis functions for order Np (Sec. 3.1, Eq. FBApprox)."""
+    return (Np + 1) * (Np + 2) // 2
+
+
+def zernike_index(n: int, m: int) -> int:
+    return (n * (n + 2) + m) // 2
+
+
+def zernike_nm(Np: int):
+    """(n, m) of each basis index, in index order."""
+    out = []
+    for n in range(Np + 1):
+        for m in range(-n, n + 1, 2):
+            out.append((n, m))
+    return out
+
+
+def zernike(Np: int, px, py) -> np.ndarray:
+    """Zernike polynomials Z_n^m at points p of the unit disc (Sec. 3.1), [npts, nb]."""
+    px = np.ascontiguousarray(np.atleast_1d(px), dtype=np.float64)
+    py = np.ascontiguousarray(np.atleast_1d(py), dtype=np.float64)
+    out = np.empty((px.size, nbasis(Np)), dtype=np.float64)
+    lib().orc_zernike(ctypes.c_int(Np), ctypes.c_int64(px.size), _p(px), _p(py), _p(out))
+    return out
+
+
+def zernike_invnorm(Np: int) -> np.ndarray:
+    """N_{nm} = (2n+2)/(eps_m pi), eps_0 = 2 (Sec. 3.1-3.2)."""
+    return np.array([(2 * n + 2) / ((2.0 if m == 0 else 1.0) * np.pi) for n, m in zernike_nm(Np)])
+
+
+# Gauss-Legendre orders used by the oracle; the direction integral doubles
+# through these, the spatial (triangle) integral uses TRI_ORDER.
+GL_ORDERS = (4, 8, 16, 32, 64)
+TRI_ORDER = 12
+
+
+class _GL:
+    def __init__(self, orders):
+        xs, ws, offs = [], [], []
+        off = 0
+        for q in orders:
+            x, w = np.polynomial.legendre.leggauss(q)
+            xs.append(x)
+            ws.append(w)
+            offs.append(off)
+            off += q
+        self.qs = np.array(orders, dtype=np.int32)
+        self.offs = np.array(offs, dtype=np.int32)
+        self.x = np.concatenate(xs)
+        self.w = np.concatenate(ws)
+
+
+_gl_cache = {}
+
+
+def gl_table(orders=GL_ORDERS + (TRI_ORDER,)):
+    key = tuple(orders)
+    if key not in _gl_cache:
+        _gl_cache[key] = _GL(key)
+    return _gl_cache[key]
+
+
+# ---------------------------------------------------------------------------
+# Mesh topology and face geometry
+# ---------------------------------------------------------------------------
+
+@dataclass
+class Topology:
+    """recv[4t + f] = the row that receives flux leaving tet t through face f:
+    the neighbour's row across f, or 4t + f itself on the boundary.
+    boundary[row] = True for boundary rows.  src_tet[R], src_face[R]: the tet
+    whose flux row R receives and that tet's exit face (the inverse map)."""
+
+    recv: np.ndarray
+    boundary: np.ndarray
+    src_tet: np.ndarray
+    src_face: np.ndarray
+
+
+def topology(tets: np.ndarray) -> Topology:
+    """Face adjacency of a conforming tet mesh (Sec. 2) by a dictionary of sorted
+    vertex triples.  Face f of tet t is the face opposite its local vertex f."""
+    nt = tets.shape[0]
+    seen = {}
+    recv = np.arange(4 * nt, dtype=np.int64)
+    for t in range(nt):
+        tv = tets[t]
+        for f in range(4):
+            key = tuple(sorted(int(tv[k]) for k in range(4) if k != f))
+            row = 4 * t + f
+            if key in seen:
+                other = seen.pop(key)
+                recv[row] = other
+                recv[other] = row
+            else:
+                seen[key] = row
+    boundary = recv == np.arange(4 * nt)
+    # row R receives from the tet on the other side (itself on the boundary)
+    src_tet = recv // 4
+    src_face = recv % 4
+    return Topology(recv=recv, boundary=boundary, src_tet=src_tet, src_face=src_face)
+
+
+def face_areas(verts: np.ndarray, tets: np.ndarray) -> np.ndarray:
+    """|T_{t,f}| for every row 4t + f."""
+    out = np.empty(4 * tets.shape[0])
+    for f in range(4):
+        idx = [(f + 1 + k) % 4 for k in range(3)]
+        a, b, c = (verts[tets[:, i]] for i in idx)
+        out[f::4] = 0.5 * np.linalg.norm(np.cross(b - a, c - a), axis=1)
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Operator blocks (Sec. 3.2-3.4)
+# ---------------------------------------------------------------------------
+
+@dataclass
+class Operator:
+    """Discretised transfer operator in the oracle's own column layout:
+    blocks[J, k] (nb x nb, rows = test index on the receiving face, columns =
+    trial index on the source face) for source column J = 4t + f and its k-th
+    destination face fp != f (ascending), received by dest[J, k].
+    dblocks: d(blocks)/d(mu_t) when requested.  q_used: accepted order."""
+
+    Np: int
+    blocks: np.ndarray
+    dest: np.ndarray
+    dblocks: np.ndarray | None = None
+    q_used: np.ndarray | None = None
+
+    @property
+    def nb(self):
+        return nbasis(self.Np)
+
+    @property
+    def nrows(self):
+        return self.blocks.shape[0]
+
+
+def pair_list(nt: int):
+    """All (t, f, fp) face pairs with fp != f, in column-major order."""
+    t = np.repeat(np.arange(nt, dtype=np.int64), 12)
+    f = np.tile(np.repeat(np.arange(4, dtype=np.int32), 3), nt)
+    fp_tab = np.array([[1, 2, 3], [0, 2, 3], [0, 1, 3], [0, 1, 2]], dtype=np.int32)
+    fp = np.tile(fp_tab.reshape(-1), nt)
+    return t, f, fp
+
+
+def blocks_for_pairs(verts, tets, topo: Topology, mu_tet, refl_row, Np, t, f, fp, q=None, rtol=1e-13,
+                     lev0=1, with_derivative=False, regions_mask=0x0F, nthreads=0):
+    """Blocks for the listed face pairs (t, f) -> fp.
+
+    Fixed order when q is given (one of GL_ORDERS); otherwise the order doubles
+    from GL_ORDERS[lev0] until the block max-norm changes by <= rtol relative.
+    lambda = refl_row[recv] on boundary rows, 1 on interior faces (uniform media,
+    transmission probability 1, Sec. 3.3).  The damping is mu of tet t.
+    """
+    G = gl_table()
+    verts = np.ascontiguousarray(verts, dtype=np.float64)
+    tets = np.ascontiguousarray(tets, dtype=np.int32)
+    t = np.ascontiguousarray(t, dtype=np.int64)
+    f = np.ascontiguousarray(f, dtype=np.int32)
+    fp = np.ascontiguousarray(fp, dtype=np.int32)
+    n = t.size
+    recv = np.ascontiguousarray(topo.recv[4 * t + fp], dtype=np.int64)
+    mu = np.ascontiguousarray(np.asarray(mu_tet, dtype=np.float64)[t])
+    refl_row = np.broadcast_to(np.asarray(refl_row, dtype=np.float64), (4 * tets.shape[0],))
+    lam = np.where(topo.boundary[recv], refl_row[recv], 1.0).astype(np.float64)
+    lam = np.ascontiguousarray(lam)
+    nb = nbasis(Np)
+    out = np.empty((n, nb, nb))
+    dout = np.empty((n, nb, nb)) if with_derivative else None
+    qu = np.empty(n, dtype=np.int32)
+    if q is not None:
+        lev0 = list(G.qs).index(q)
+        rtol = 0.0
+    tri_lev = list(G.qs).index(TRI_ORDER)
+    nlev = len(GL_ORDERS)
+    lib().orc_blocks(_p(verts), _p(tets, _i32p), ctypes.c_int64(n), _p(t, _i64p), _p(f, _i32p), _p(fp, _i32p),
+                     _p(recv, _i64p), _p(mu), _p(lam), ctypes.c_int(Np), ctypes.c_int(nlev), _p(G.qs, _i32p),
+                     _p(G.offs, _i32p), _p(G.x), _p(G.w), ctypes.c_int(lev0), ctypes.c_double(rtol),
+                     ctypes.c_int(tri_lev), ctypes.c_int(regions_mask), ctypes.c_int(nthreads), _p(out),
+                     _p(dout) if dout is not None else None, _p(qu, _i32p))
+    return out, dout, qu, recv
+
+
+def assemble(verts, tets, mu_tet, refl, Np, q=None, rtol=1e-13, with_derivative=False, topo=None,
+             nthreads=0) -> Operator:
+    """The whole operator B (all 12 face pairs of every tet), Sec. 3.2."""
+    topo = topo or topology(tets)
+    nt = tets.shape[0]
+    t, f, fp = pair_list(nt)
+    out, dout, qu, recv = blocks_for_pairs(verts, tets, topo, mu_tet, refl, Np, t, f, fp, q=q, rtol=rtol,
+                                           with_derivative=with_derivative, nthreads=nthreads)
+    nb = nbasis(Np)
+    return Operator(Np=Np, blocks=out.reshape(4 * nt, 3, nb, nb), dest=recv.reshape(4 * nt, 3),
+                    dblocks=None if dout is None else dout.reshape(4 * nt, 3, nb, nb), q_used=qu)
+
+
+def region_cos_measure(verts, tets, t, f, fp, region, q=32):
+    """Int cos(theta) dw over one of the seven direction regions by quadrature."""
+    x, w = np.polynomial.legendre.leggauss(q)
+    return lib().orc_region_cos_measure(_p(np.ascontiguousarray(verts, dtype=np.float64)),
+                                        _p(np.ascontiguousarray(tets, dtype=np.int32), _i32p), ctypes.c_int64(t),
+                                        ctypes.c_int(f), ctypes.c_int(fp), ctypes.c_int(region), ctypes.c_int(q),
+                                        _p(x), _p(w))
+
+
+def spatial(verts, tets, t, f, direction, mu, nq=TRI_ORDER):
+    """S_{f->fp}(d), dS/dmu and the clipped area for the three fp != f (ascending)."""
+    x, w = np.polynomial.legendre.leggauss(nq)
+    S = np.empty(3)
+    dS = np.empty(3)
+    A = np.empty(3)
+    d = np.ascontiguousarray(direction, dtype=np.float64)
+    lib().orc_spatial(_p(np.ascontiguousarray(verts, dtype=np.float64)),
+                      _p(np.ascontiguousarray(tets, dtype=np.int32), _i32p), ctypes.c_int64(t), ctypes.c_int(f),
+                      _p(d), ctypes.c_double(mu), ctypes.c_int(nq), _p(x), _p(w), _p(S), _p(dS), _p(A))
+    return S, dS, A
+
+
+def mc_block(verts, tets, t, f, fp, recv_row, mu, lam, Np, nsamp=10 ** 7, seed=1, nthreads=0):
+    """Brute-force Monte Carlo ray tracing of one block: (mean, standard error)."""
+    nb = nbasis(Np)
+    mean = np.empty((nb, nb))
+    se = np.empty((nb, nb))
+    lib().orc_mc_block(_p(np.ascontiguousarray(verts, dtype=np.float64)),
+                       _p(np.ascontiguousarray(tets, dtype=np.int32), _i32p), ctypes.c_int64(t), ctypes.c_int(f),
+                       ctypes.c_int(fp), ctypes.c_int64(recv_row), ctypes.c_double(mu), ctypes.c_double(lam),
+                       ctypes.c_int(Np), ctypes.c_int64(nsamp), ctypes.c_uint64(seed), ctypes.c_int(nthreads),
+                       _p(mean), _p(se))
+    return mean, se
+
+
+# ---------------------------------------------------------------------------
+# Operator application and solves (Sec. 2, Eqs. NSum and GovIE)
+# ---------------------------------------------------------------------------
+
+def apply(op: Operator, x: np.ndarray, trans: bool = False, x0=None, alpha=1.0, nthreads=0) -> np.ndarray:
+    """y = x0 + alpha * B x (or B^T x), x of shape [nrows, nb] (one right-hand side)."""
+    nb = op.nb
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(op.nrows, nb)
+    y = np.empty_like(x)
+    blocks = np.ascontiguousarray(op.blocks)
+    dest = np.ascontiguousarray(op.dest, dtype=np.int64)
+    x0p = None if x0 is None else _p(np.ascontiguousarray(x0, dtype=np.float64).reshape(op.nrows, nb))
+    lib().orc_apply(ctypes.c_int64(op.nrows), ctypes.c_int(nb), _p(blocks), _p(dest, _i64p), _p(x), x0p,
+                    ctypes.c_double(alpha), ctypes.c_int(1 if trans else 0), ctypes.c_int(nthreads), _p(y))
+    return y
+
+
+def dense(op: Operator) -> np.ndarray:
+    """B as a dense [nrows*nb, nrows*nb] matrix (small meshes only)."""
+    nb = op.nb
+    n = op.nrows * nb
+    M = np.zeros((n, n))
+    for J in range(op.nrows):
+        for k in range(3):
+            R = int(op.dest[J, k])
+            M[R * nb:(R + 1) * nb, J * nb:(J + 1) * nb] += op.blocks[J, k]
+    return M
+
+
+def source_vector(verts, tets, rows, Np, weights=None) -> np.ndarray:
+    """Galerkin coefficients of a unit isotropic density on boundary face rows:
+    rho0 = 1 on Q_row projects onto b_l Z_0^0 with coefficient sqrt(|T_l|) * 1
+    (b_l = 1/sqrt|T_l|, the Zernike (0,0) inverse norm 1/pi times the disc area pi),
+    and to zero on every other basis function (Sec. 3.1-3.2).  [nrows, nb]."""
+    nb = nbasis(Np)
+    area = face_areas(verts, tets)
+    x = np.zeros((4 * tets.shape[0], nb))
+    w = np.ones(len(rows)) if weights is None else weights
+    for r, wt in zip(np.atleast_1d(rows), np.atleast_1d(w)):
+        x[int(r), 0] += wt * np.sqrt(area[int(r)])
+    return x
+
+
+def solve_dense(op: Operator, rho0: np.ndarray) -> np.ndarray:
+    """rho = (I - B)^{-1} rho0 by LU (Eq. GovIE); small meshes."""
+    M = np.eye(op.nrows * op.nb) - dense(op)
+    return np.linalg.solve(M, rho0.reshape(-1)).reshape(op.nrows, op.nb)
+
+
+def neumann(op: Operator, rho0: np.ndarray, tol=1e-10, maxit=100000):
+    """Neumann series rho = sum_n B^n rho0 (Eq. NSum), iterated as x <- rho0 + B x
+    until ||x_{k+1} - x_k|| <= tol ||x_{k+1}||."""
+    x = rho0.copy()
+    for it in range(1, maxit + 1):
+        xn = apply(op, x, x0=rho0)
+        if np.linalg.norm(xn - x) <= tol * np.linalg.norm(xn):
+            return xn, it
+        x = xn
+    return x, -maxit
+
+
+def gmres(matvec, b: np.ndarray, tol=1e-12, restart=200, maxit=20000, x0=None):
+    """Restarted GMRES (modified Gram-Schmidt Arnoldi, Givens rotations) on a
+    flat vector; stops on the true residual ||b - A x|| <= tol ||b||."""
+    b = b.reshape(-1)
+    x = np.zeros_like(b) if x0 is None else x0.reshape(-1).copy()
+    bn = np.linalg.norm(b)
+    if bn == 0:
+        return x, 0
+    total = 0
+    while total < maxit:
+        r = b - matvec(x)
+        beta = np.linalg.norm(r)
+        if beta <= tol * bn:
+            return x, total
+        m = restart
+        V = np.zeros((m + 1, b.size))
+        H = np.zeros((m + 1, m))
+        cs = np.zeros(m)
+        sn = np.zeros(m)
+        g = np.zeros(m + 1)
+        g[0] = beta
+        V[0] = r / beta
+        k_done = 0
+        for k in range(m):
+            w = matvec(V[k])
+            for i in range(k + 1):
+                H[i, k] = np.dot(V[i], w)
+                w = w - H[i, k] * V[i]
+            H[k + 1, k] = np.linalg.norm(w)
+            if H[k + 1, k] > 0:
+                V[k + 1] = w / H[k + 1, k]
+            for i in range(k):
+                a, c = H[i, k], H[i + 1, k]
+                H[i, k] = cs[i] * a + sn[i] * c
+                H[i + 1, k] = -sn[i] * a + cs[i] * c
+            den = np.hypot(H[k, k], H[k + 1, k])
+            cs[k] = H[k, k] / den
+            sn[k] = H[k + 1, k] / den
+            H[k, k] = den
+            H[k + 1, k] = 0.0
+            g[k + 1] = -sn[k] * g[k]
+            g[k] = cs[k] * g[k]
+            total += 1
+            k_done = k + 1
+            if abs(g[k + 1]) <= 0.5 * tol * bn or total >= maxit:
+                break
+        y = np.linalg.solve(np.triu(H[:k_done, :k_done]), g[:k_done])
+        x = x + V[:k_done].T @ y
+    r = b - matvec(x)
+    return x, (total if np.linalg.norm(r) <= tol * bn else -total)
+
+
+def solve_gmres(op: Operator, rho0: np.ndarray, tol=1e-12, restart=200, maxit=20000, trans=False, nthreads=0):
+    """(I - B) x = rho0 (or (I - B)^T x = rho0) by restarted GMRES, FP64."""
+    nb = op.nb
+
+    def mv(v):
+        return apply(op, v.reshape(op.nrows, nb), trans=trans, x0=v.reshape(op.nrows, nb), alpha=-1.0,
+                     nthreads=nthreads).reshape(-1)
+
+    x, it = gmres(mv, rho0.reshape(-1), tol=tol, restart=restart, maxit=maxit)
+    return x.reshape(op.nrows, nb), it
+
+
+def residual(op: Operator, x: np.ndarray, rho0: np.ndarray) -> float:
+    """||rho0 - (I - B) x|| / ||rho0|| in FP64."""
+    r = rho0 - apply(op, x, x0=x, alpha=-1.0)
+    return float(np.linalg.norm(r) / np.linalg.norm(rho0))
+
+
+# ---------------------------------------------------------------------------
+# Interior density and the adjoint gradient (Sec. 4.1, Eq. IntDens)
+# ---------------------------------------------------------------------------
+
+def centroids(verts, tets):
+    return verts[tets].mean(axis=1)
+
+
+def interior_g(verts, tets, t, r, mu, Np, nq=24):
+    """g[4, nb] and dg/dmu with rho_T(r) = sum_{l,nm} rho_(t,l,nm) g[l,nm]."""
+    nb = nbasis(Np)
+    x, w = np.polynomial.legendre.leggauss(nq)
+    g = np.empty((4, nb))
+    dg = np.empty((4, nb))
+    rr = np.ascontiguousarray(r, dtype=np.float64)
+    lib().orc_interior_g(_p(np.ascontiguousarray(verts, dtype=np.float64)),
+                         _p(np.ascontiguousarray(tets, dtype=np.int32), _i32p), ctypes.c_int64(int(t)), _p(rr),
+                         ctypes.c_double(mu), ctypes.c_int(Np), ctypes.c_int(nq), _p(x), _p(w), _p(g), _p(dg))
+    return g, dg
+
+
+def receiver_functional(verts, tets, mu_tet, Np, receiver, nq=24):
+    """J(rho) = mean over receiver tets e of rho_T(centroid_e) = gvec . rho.
+    Returns gvec [nrows, nb] and dgvec/dmu_e stacked per receiver tet."""
+    nb = nbasis(Np)
+    gvec = np.zeros((4 * tets.shape[0], nb))
+    dg = {}
+    cen = centroids(verts, tets)
+    for e in np.atleast_1d(receiver):
+        g, d = interior_g(verts, tets, int(e), cen[int(e)], float(mu_tet[int(e)]), Np, nq=nq)
+        gvec[4 * e:4 * e + 4] += g / len(receiver)
+        dg[int(e)] = d / len(receiver)
+    return gvec, dg
+
+
+def gradient(op: Operator, rho: np.ndarray, lam: np.ndarray, dg: dict, nt: int) -> np.ndarray:
+    """dJ/dmu_e = (dg/dmu_e) . rho + sum_{blocks of tet e} lam_R^T (dB/dmu_e) rho_J,
+    with (I - B)^T lam = g (the adjoint equation).  op must carry dblocks."""
+    nb = op.nb
+    grad = np.zeros(nt)
+    db = op.dblocks.reshape(nt, 4, 3, nb, nb)
+    dest = op.dest.reshape(nt, 4, 3)
+    rho_t = rho.reshape(nt, 4, nb)
+    lam_r = lam[dest]  # [nt, 4, 3, nb]
+    grad += np.einsum("tfka,tfkab,tfb->t", lam_r, db, rho_t)
+    for e, d in dg.items():
+        grad[e] += float(np.sum(d * rho[4 * e:4 * e + 4]))
+    return grad

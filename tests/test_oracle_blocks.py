@@ -1,0 +1,111 @@
+"""Pins for whole operator blocks of the oracle (Sec. 3.2, Eqs. Bapprox/B4DInt).
+
+- regular tetrahedron at mu = 0: every face sees each other face with view
+  factor 1/3 (symmetry plus closure), so B_(00),(00) = 1/3 for all 12 pairs;
+- reciprocity: reversing a ray swaps source and receiving face and negates
+  both tangential momenta, so on one tet with lambda = 1,
+  B_{(l',n'm'),(l,nm)} / N_{n'm'} = (-1)^(n+n') B_{(l,nm),(l',n'm')} / N_{nm};
+- brute-force Monte Carlo ray tracing of individual blocks (5 sigma);
+- conservation (Sec. 2): with mu = 0 and fully reflecting walls the phase-space
+  mass pi sum_J sqrt|T_J| rho_(J,00) is preserved, i.e. w^T B = w^T with
+  w_I = sqrt|T_I| on the (0,0) slots and 0 elsewhere;
+- the adaptive order doubling reaches its tolerance.
+"""
+import numpy as np
+import pytest
+
+from paper_1608_04607_gb300.inputs import kuhn_cube_mesh
+
+REG_V = np.array([[1, 1, 1], [1, -1, -1], [-1, 1, -1], [-1, -1, 1]], dtype=np.float64)
+ONE_TET = np.array([[0, 1, 2, 3]], dtype=np.int32)
+
+
+def test_regular_tet_view_factor(oracle_mod):
+    op = oracle_mod.assemble(REG_V, ONE_TET, np.array([0.0]), 1.0, 2, q=32)
+    np.testing.assert_allclose(op.blocks[:, :, 0, 0], 1.0 / 3.0, atol=1e-12)
+
+
+def _jittered_tet():
+    m = kuhn_cube_mesh(2, jitter=0.2, seed=11)
+    return m.verts, m.tets[[9]].copy()
+
+
+@pytest.mark.parametrize("mu", [0.0, 0.8])
+def test_reciprocity_single_tet(oracle_mod, mu):
+    V, T = _jittered_tet()
+    Np = 3
+    op = oracle_mod.assemble(V, T, np.array([mu]), 1.0, Np, q=32)
+    N = oracle_mod.zernike_invnorm(Np)
+    sign = np.array([(-1) ** n for n, m in oracle_mod.zernike_nm(Np)])
+    fps = {f: [k for k in range(4) if k != f] for f in range(4)}
+    blk = lambda f, fp: op.blocks[f, fps[f].index(fp)]
+    for f in range(4):
+        for fp in range(4):
+            if fp == f:
+                continue
+            lhs = blk(f, fp) / N[:, None]
+            rhs = (blk(fp, f) / N[:, None]).T * np.outer(sign, sign)
+            np.testing.assert_allclose(lhs, rhs, atol=1e-11)
+    # view factor closure at mu = 0: sum_l' sqrt(A_l'/A_l) B_00,00 = 1
+    if mu == 0.0:
+        A = oracle_mod.face_areas(V, T)
+        for f in range(4):
+            s = sum(np.sqrt(A[fp] / A[f]) * blk(f, fp)[0, 0] for fp in fps[f])
+            assert s == pytest.approx(1.0, abs=1e-11)
+
+
+@pytest.mark.parametrize("pair", [(0, 1), (2, 3), (3, 0)])
+def test_monte_carlo_ray_tracing(oracle_mod, pair):
+    V, T = _jittered_tet()
+    f, fp = pair
+    Np, mu, lam = 3, 0.7, 0.9
+    topo = oracle_mod.topology(T)
+    out, _, q, recv = oracle_mod.blocks_for_pairs(V, T, topo, np.array([mu]), lam, Np, np.array([0]), np.array([f]),
+                                                  np.array([fp]))
+    assert q[0] > 0
+    mean, se = oracle_mod.mc_block(V, T, 0, f, fp, int(recv[0]), mu, lam, Np, nsamp=4 * 10 ** 6, seed=7 + f)
+    z = np.abs(out[0] - mean) / np.maximum(se, 1e-12)
+    assert z.max() < 5.0, (z.max(), np.unravel_index(z.argmax(), z.shape))
+
+
+def test_monte_carlo_interior_neighbour_frame(oracle_mod):
+    """A block received by the neighbour across an interior face uses the
+    neighbour's face frame; MC checks that too."""
+    m = kuhn_cube_mesh(2, jitter=0.2, seed=11)
+    topo = oracle_mod.topology(m.tets)
+    rows = np.nonzero(~topo.boundary)[0]
+    r = int(rows[5])
+    t, fp = divmod(r, 4)
+    f = (fp + 1) % 4
+    Np, mu = 2, 0.3
+    out, _, _, recv = oracle_mod.blocks_for_pairs(m.verts, m.tets, topo, np.full(m.n_tets, mu), 0.5, Np,
+                                                  np.array([t]), np.array([f]), np.array([fp]))
+    assert int(recv[0]) != r and not topo.boundary[recv[0]]
+    mean, se = oracle_mod.mc_block(m.verts, m.tets, t, f, fp, int(recv[0]), mu, 1.0, Np, nsamp=4 * 10 ** 6, seed=3)
+    z = np.abs(out[0] - mean) / np.maximum(se, 1e-12)
+    assert z.max() < 5.0
+
+
+def test_conservation_weighted_column_sums(oracle_mod):
+    m = kuhn_cube_mesh(2, jitter=0.2, seed=11)
+    Np = 3
+    op = oracle_mod.assemble(m.verts, m.tets, np.zeros(m.n_tets), 1.0, Np, q=32)
+    A = oracle_mod.face_areas(m.verts, m.tets)
+    w = np.zeros((op.nrows, op.nb))
+    w[:, 0] = np.sqrt(A)
+    wB = oracle_mod.apply(op, w, trans=True)  # (B^T w)
+    np.testing.assert_allclose(wB, w, atol=1e-11)
+    # with damping the mass strictly decreases
+    op2 = oracle_mod.assemble(m.verts, m.tets, np.full(m.n_tets, 0.5), 0.9, Np, q=32)
+    wB2 = oracle_mod.apply(op2, w, trans=True)
+    assert np.all(wB2[:, 0] < w[:, 0])
+
+
+def test_adaptive_order_reaches_tolerance(oracle_mod):
+    m = kuhn_cube_mesh(2, jitter=0.2, seed=11)
+    topo = oracle_mod.topology(m.tets)
+    t, f, fp = oracle_mod.pair_list(m.n_tets)
+    sel = np.arange(0, 12 * m.n_tets, 17)
+    out, _, q, _ = oracle_mod.blocks_for_pairs(m.verts, m.tets, topo, np.full(m.n_tets, 0.05), 0.95, 4, t[sel],
+                                               f[sel], fp[sel], rtol=1e-12)
+    assert np.all(q > 0)
