@@ -1,0 +1,215 @@
+/*
+ * dfm.h -- C ABI of the GB300 discrete-flow-mapping library (libdfm.so).
+ *
+ * Discrete flow mapping (DFM) transports a phase-space boundary density
+ * through a conforming tetrahedral mesh.  The library implements the
+ * data-parallel hot path of the method of Bajars, Chappell, Sondergaard and
+ * Tanner ("Transport of phase space densities through tetrahedral meshes
+ * using discrete flow mapping"):
+ *
+ *   1. assembly of the Galerkin matrix B of the weighted boundary transfer
+ *      operator (Sec. 3.2, Eqs. Bapprox and B4DInt): for every tetrahedron and
+ *      every ordered pair (l, l') of its faces an N_b x N_b block, with the
+ *      spatial integral done in closed form (Sec. 3.3) and the direction
+ *      integral by quadrature over the seven direction sub-regions (Sec. 3.4);
+ *   2. the stationary solve (I - B) rho = rho0 (Sec. 2, Eqs. NSum/GovIE);
+ *   3. the interior density functional (Sec. 4.1, Eq. IntDens) and the adjoint
+ *      gradient of a receiver functional with respect to per-tet damping.
+ *
+ * Conventions shared by every entry point:
+ *   - tet t has vertices (v0, v1, v2, v3); face f is the face opposite v_f,
+ *     with vertices (v_{f+1}, v_{f+2}, v_{f+3}) (indices mod 4); it is row
+ *     r = 4 t + f of every coefficient vector;
+ *   - the face frame (the paper leaves it open, Sec. 3.3): origin at the
+ *     first face vertex, e1 along the first edge, n the inward unit normal
+ *     (towards v_f), e2 = n x e1; the tangential momentum of an inward unit
+ *     direction d is p = (d.e1, d.e2);
+ *   - momentum basis: Zernike polynomials Z_n^m, n = 0..Np, m = -n, -n+2, .., n
+ *     (Sec. 3.1), index (n (n+2) + m) / 2, N_b = (Np+1)(Np+2)/2;
+ *   - a coefficient vector is rho[row][N_b] (row-major, FP64 unless stated);
+ *     R right-hand sides are stored one after the other: rho[R][rows][N_b];
+ *   - uniform media (c = rho_f = 1): a ray leaving through an interior face is
+ *     transmitted with probability 1 into the neighbour (Sec. 3.3 with equal
+ *     impedances); at a boundary face it is specularly reflected with weight
+ *     r (the face's reflection coefficient; r = 0 is an open boundary).
+ *
+ * Memory: mesh arrays passed to dfm_mesh_create are HOST pointers and are
+ * copied.  Every other array argument is a DEVICE pointer owned by the caller
+ * unless stated.  Handles (dfm_mesh, dfm_op) are owned by the library and
+ * freed by their destroy call.  Work runs on the CUDA stream given
+ * (a cudaStream_t passed as void*, NULL = legacy default stream); calls
+ * return after enqueueing except where a result must come back to the host
+ * (stated per call).
+ *
+ * Errors: every int-returning call returns DFM_OK (0) or a negative DFM_ERR_*
+ * code and never throws; dfm_last_error() returns a message for the calling
+ * thread's last failure.
+ */
+#ifndef DFM_H
+#define DFM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DFM_OK 0
+#define DFM_ERR_ARG (-1)           /* invalid argument (NULL, size, range) */
+#define DFM_ERR_MESH (-2)          /* degenerate tet, non-manifold face, bad index */
+#define DFM_ERR_CUDA (-3)          /* a CUDA runtime call failed */
+#define DFM_ERR_OOM (-4)           /* device allocation failed */
+#define DFM_ERR_NOT_CONVERGED (-5) /* iteration cap reached; info still filled */
+#define DFM_ERR_NONFINITE (-6)     /* NaN/Inf met in a residual or input */
+#define DFM_ERR_UNSUPPORTED (-7)   /* option combination not built */
+
+/* storage/arithmetic precision of operator blocks */
+#define DFM_F64 0
+#define DFM_F32 1
+#define DFM_BF16 2
+
+/* stationary solvers */
+#define DFM_SOLVE_NEUMANN 0   /* x <- rho0 + B x (Eq. NSum), FP64 */
+#define DFM_SOLVE_GMRES 1     /* restarted GMRES on (I - B) x = rho0 in the operator's precision */
+#define DFM_SOLVE_GMRES_IR 2  /* FP64-residual iterative refinement around FP32 GMRES */
+
+typedef struct dfm_mesh dfm_mesh;
+typedef struct dfm_op dfm_op;
+
+typedef struct {
+  int64_t n_verts;
+  int64_t n_tets;
+  int64_t n_rows;           /* 4 n_tets */
+  int64_t n_boundary_rows;  /* faces on the mesh boundary */
+  double min_abs_volume;    /* smallest |tet volume| */
+  double total_volume;
+} dfm_mesh_info_t;
+
+/* Build a mesh (Sec. 2: conforming tet mesh, per-face neighbours).
+ *   verts [n_verts][3] FP64, tets [n_tets][4] int32 (any orientation): HOST.
+ *   refl  [4 n_tets] FP64 per-row reflection coefficient in [0, 1] (only
+ *         boundary rows are read) or NULL to use refl_default everywhere.
+ * Runs the face-matching (open-addressing hash on sorted vertex triples) and
+ * face-geometry kernels, then waits on the stream for the mesh check.
+ * Errors: DFM_ERR_ARG (sizes, NULL, refl outside [0,1]), DFM_ERR_MESH
+ * (vertex index out of range, zero-volume tet, a face shared by > 2 tets). */
+int dfm_mesh_create(const double* verts, int64_t n_verts, const int32_t* tets, int64_t n_tets, const double* refl,
+                    double refl_default, void* stream, dfm_mesh** out);
+void dfm_mesh_destroy(dfm_mesh* mesh);
+int dfm_mesh_info(const dfm_mesh* mesh, dfm_mesh_info_t* info);
+
+/* Copy the face matching to the host: recv[4 n_tets] int32, recv[4t+f] = the
+ * row that receives flux leaving tet t through face f (the neighbour's row, or
+ * 4t+f itself on the boundary).  Blocks until copied. */
+int dfm_mesh_recv(const dfm_mesh* mesh, int32_t* recv_host);
+
+/* Gauss-Legendre nodes and weights on [-1, 1] (the per-patch direction rule,
+ * Sec. 3.4), computed on the device in FP64 by Newton iteration on the
+ * Legendre three-term recurrence.  x, w: device FP64 [q], 1 <= q <= 64. */
+int dfm_gauss_legendre(int q, double* x, double* w, void* stream);
+
+typedef struct {
+  int Np;               /* momentum order 0..8 (N_b = (Np+1)(Np+2)/2) */
+  const double* mu;     /* device FP64 [n_tets] damping per tet, or NULL */
+  double mu_uniform;    /* damping when mu == NULL (>= 0) */
+  int quad_order;       /* Gauss-Legendre order per direction patch; 0 = Np + 6 */
+  double max_patch_deg; /* split direction patches until every edge <= this angle; 0 = 60 */
+  int precision;        /* DFM_F64 or DFM_F32 (FP32 arithmetic, FP64 geometry set-up) */
+} dfm_params;
+
+typedef struct {
+  int Np, nb;
+  int precision;
+  int64_t n_rows;
+  int64_t row_stride;   /* elements between consecutive rows of vals */
+  const void* vals;     /* device: vals[row][3][nb][nb] (+ padding to row_stride) */
+  int64_t bytes;        /* bytes of vals */
+} dfm_op_info_t;
+
+/* Assemble B (Sec. 3.2-3.4).  Block layout: row R holds the three blocks
+ * that R receives, all from one tet t (t = recv[R]/4, exit face l' =
+ * recv[R]%4): slot k is source face l = the k-th face of t other than l'
+ * (ascending).  Each block is nb x nb row-major: row = test index (n',m') on
+ * the receiving face, column = trial index (n,m) on the source face:
+ *   B = lambda N_{n'm'} / sqrt(|T_l||T_l'|) sum_nodes w J S(d) Z_{n'm'}(p') Z_nm(p),
+ *   S(d) = 2 A_nabla(d) phi2(mu L_O(d)), phi2(x) = (x - 1 + e^-x)/x^2 (Sec. 3.3).
+ * Asynchronous on the stream.  Errors: DFM_ERR_ARG, DFM_ERR_OOM. */
+int dfm_assemble(const dfm_mesh* mesh, const dfm_params* params, void* stream, dfm_op** out);
+/* Re-assemble into an existing operator of the same mesh, Np and precision
+ * (no allocation); used for repeated assembly with new damping. */
+int dfm_assemble_into(const dfm_mesh* mesh, const dfm_params* params, dfm_op* op, void* stream);
+void dfm_op_destroy(dfm_op* op);
+int dfm_op_info(const dfm_op* op, dfm_op_info_t* info);
+/* Copy the block storage (dfm_op_info_t.bytes bytes, layout above) to dst, a
+ * device or host pointer; asynchronous on the stream. */
+int dfm_op_copy_vals(const dfm_op* op, void* dst, int64_t bytes, void* stream);
+
+/* y = x0 + alpha * B x (trans = 0) or y = x0 + alpha * B^T x (trans = 1) for
+ * R right-hand sides; x, y, x0 device [R][rows][nb] of type xtype
+ * (DFM_F64 or DFM_F32); x0 may be NULL (treated as 0) or alias x; y must not
+ * alias x.  Asynchronous. */
+int dfm_apply(const dfm_op* op, const void* x, const void* x0, void* y, int R, double alpha, int trans, int xtype,
+              void* stream);
+
+/* Galerkin coefficients of unit isotropic sources (Sec. 3.1-3.2): for source
+ * s, rho0[s][row_s][(0,0)] = sqrt(|T_row_s|) and zero elsewhere.
+ * rows_host: HOST int64 [n_src] boundary (or any) rows; rho0: device FP64
+ * [n_src][rows][nb] (fully overwritten).  Asynchronous. */
+int dfm_source(const dfm_mesh* mesh, int Np, const int64_t* rows_host, int n_src, double* rho0, void* stream);
+
+typedef struct {
+  int method;        /* DFM_SOLVE_* */
+  double tol;        /* stop when ||rho0 - (I - B) x|| <= tol ||rho0|| (FP64 residual; Neumann: relative increment) */
+  int max_iter;      /* cap on operator applications (0 = 20000) */
+  int restart;       /* GMRES restart length (0 = 64) */
+  int use_x0;        /* 1: rho holds the initial guess on entry */
+  double inner_tol;  /* GMRES_IR: inner FP32 relative tolerance (0 = 1e-4) */
+} dfm_solve_opts;
+
+typedef struct {
+  int iters;         /* operator applications used */
+  int outer;         /* refinement steps (GMRES_IR) or restarts */
+  double resid;      /* final relative residual (FP64) of the worst right-hand side */
+} dfm_solve_info;
+
+/* Stationary density rho = (I - B)^{-1} rho0 (Eq. GovIE) for R right-hand
+ * sides, rho0 and rho device FP64 [R][rows][nb].  Synchronises with the
+ * stream once per iteration to read convergence scalars.  Returns
+ * DFM_ERR_NOT_CONVERGED (info filled, rho = last iterate) at the cap and
+ * DFM_ERR_NONFINITE if a residual is not finite. */
+int dfm_solve(const dfm_op* op, const double* rho0, int R, double* rho, const dfm_solve_opts* opts, void* stream,
+              dfm_solve_info* info);
+
+/* Kernel accounting, for benchmarks and profiling.
+ *   dfm_launch_count: number of CUDA kernels this library has launched in the
+ *     process so far (all kernels, all streams).
+ *   dfm_stats_enable(1): from now on record a CUDA event pair around every
+ *     launch of the kernels below, on the stream each runs on;
+ *   dfm_stats_reset: forget the recorded pairs (the event pool is reused);
+ *   dfm_kernel_stats: launches and summed device milliseconds of one kernel
+ *     since the last reset (waits for the recorded events). */
+#define DFM_KERNEL_ASSEMBLE 0 /* operator assembly (one warp per face pair) */
+#define DFM_KERNEL_SPMV 1     /* y = x0 + alpha B x */
+#define DFM_KERNEL_SPMV_T 2   /* y = x0 + alpha B^T x */
+#define DFM_KERNEL_DOT 3      /* Krylov multi-dot */
+#define DFM_KERNEL_AXPY 4     /* Krylov multi-axpy */
+long long dfm_launch_count(void);
+int dfm_stats_enable(int on);
+int dfm_stats_reset(void);
+int dfm_kernel_stats(int kernel, int64_t* launches, double* total_ms);
+
+/* Quadrature nodes evaluated by the last assembly into op (all face pairs);
+ * waits for that assembly.  The benchmark turns it into counted FLOPs. */
+int dfm_op_nodes(const dfm_op* op, int64_t* nodes);
+
+/* Thread-local message for the last failing call ("" if none). */
+const char* dfm_last_error(void);
+
+/* Library version string. */
+const char* dfm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DFM_H */

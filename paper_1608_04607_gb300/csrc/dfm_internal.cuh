@@ -1,0 +1,87 @@
+// Internal declarations shared by the CUDA translation units of libdfm.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "dfm.h"
+
+namespace dfm {
+
+// Sets the thread-local error message and returns code.
+int set_error(int code, const std::string& msg);
+int cuda_error(cudaError_t e, const char* where);
+
+#define DFM_CUDA_CHECK(expr)                                  \
+  do {                                                        \
+    cudaError_t e_ = (expr);                                  \
+    if (e_ != cudaSuccess) return ::dfm::cuda_error(e_, #expr); \
+  } while (0)
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+inline int nbasis(int Np) { return (Np + 1) * (Np + 2) / 2; }
+
+// Per-row face geometry (FP64), row = 4 t + f.
+struct FaceGeom {
+  double o[3];   // frame origin (first face vertex)
+  double e1[3];  // tangent axis along the first edge
+  double e2[3];  // n x e1
+  double n[3];   // inward unit normal
+  double area;
+  double pad[3];
+};
+
+}  // namespace dfm
+
+struct dfm_mesh {
+  int64_t nv = 0, nt = 0, nrows = 0, nboundary = 0;
+  double min_abs_volume = 0, total_volume = 0;
+  double* verts = nullptr;        // device [nv][3]
+  int32_t* tets = nullptr;        // device [nt][4]
+  int32_t* recv = nullptr;        // device [4 nt]
+  double* refl = nullptr;         // device [4 nt] reflection coefficient per row
+  dfm::FaceGeom* geom = nullptr;  // device [4 nt]
+};
+
+struct dfm_op {
+  const dfm_mesh* mesh = nullptr;
+  int Np = 0, nb = 0, precision = DFM_F32;
+  int64_t nrows = 0, row_stride = 0;
+  void* vals = nullptr;  // device
+  int64_t bytes = 0;
+  // assembly scratch (per-pair constants, Gauss table), grown on demand
+  void* work = nullptr;
+  int64_t work_bytes = 0;
+  // solver workspace (Krylov basis and vectors), grown on demand
+  void* swork = nullptr;
+  int64_t swork_bytes = 0;
+};
+
+namespace dfm {
+// launch accounting (stats.cu): every kernel launch site calls count_launch();
+// timed sites wrap the launch in a KernelTimer (event pair when enabled).
+void count_launch();
+class KernelTimer {
+ public:
+  KernelTimer(int kernel, cudaStream_t st);
+  ~KernelTimer();
+ private:
+  int kernel_;
+  cudaStream_t st_;
+  int e0_;
+};
+#define DFM_LAUNCHED() ::dfm::count_launch()
+
+// row stride (elements) of the block storage: 3 nb^2 rounded up to 8 elements
+inline int64_t op_row_stride(int nb) { return ((3 * (int64_t)nb * nb + 7) / 8) * 8; }
+inline int elem_size(int precision) { return precision == DFM_F64 ? 8 : (precision == DFM_F32 ? 4 : 2); }
+
+// implemented in spmv.cu
+int apply_impl(const dfm_op* op, const void* x, const void* x0, void* y, int R, double alpha, int trans, int xtype,
+               cudaStream_t st);
+// implemented in quad.cu
+int gauss_legendre_device(int q, double* x, double* w, cudaStream_t st);
+}  // namespace dfm

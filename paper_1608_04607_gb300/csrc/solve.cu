@@ -1,0 +1,534 @@
+// Stationary solve (I - B) rho = rho0 (Sec. 2, Eqs. NSum and GovIE).
+//
+//  - Neumann: the series rho = sum_n B^n rho0 summed as x <- rho0 + B x, FP64,
+//    stopped on the relative increment.
+//  - GMRES: restarted GMRES(m) in the operator's precision; Arnoldi by
+//    classical Gram-Schmidt with one conditional re-orthogonalisation pass,
+//    Givens rotations on the host.
+//  - GMRES_IR: iterative refinement; the residual r = rho0 - (I - B) x is
+//    formed in FP64 (FP32 blocks widened exactly, FP64 accumulation) and each
+//    correction solves (I - B) d = r / |r| by FP32 GMRES to a loose tolerance.
+//    Since the FP64 residual, not the FP32 inner solve, decides convergence,
+//    the final accuracy is that of the FP64 residual.
+//
+// Vector kernels use fixed grids and a deterministic two-stage reduction.
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "dfm_internal.cuh"
+
+namespace dfm {
+namespace {
+
+constexpr int kRedBlocks = 512;  // partial-sum blocks of the reductions
+constexpr int kRedThreads = 256;
+constexpr int kDotChunk = 8;     // dot products per pass over the vector
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  T s = T(0);
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : T(0);
+    s = warp_sum(s);
+  }
+  return s;  // valid in thread 0
+}
+
+// partial[b][j] = sum over block b's slice of V[j][i] * w[i], j < k (V rows of length n, stride ld)
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads)
+multi_dot_kernel(const T* __restrict__ V, int64_t ld, int k, const T* __restrict__ w, int64_t n, T* __restrict__ partial) {
+  __shared__ T sh[32];
+  for (int j0 = 0; j0 < k; j0 += kDotChunk) {
+    T acc[kDotChunk];
+#pragma unroll
+    for (int c = 0; c < kDotChunk; ++c) acc[c] = T(0);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+      const T wi = w[i];
+#pragma unroll
+      for (int c = 0; c < kDotChunk; ++c)
+        if (j0 + c < k) acc[c] = fma(V[(int64_t)(j0 + c) * ld + i], wi, acc[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < kDotChunk; ++c) {
+      if (j0 + c >= k) break;
+      const T s = block_sum(acc[c], sh);
+      if (threadIdx.x == 0) partial[(int64_t)blockIdx.x * k + j0 + c] = s;
+    }
+  }
+}
+
+// out[j] = sum_b partial[b][j]
+template <typename T>
+__global__ void reduce_partials_kernel(const T* __restrict__ partial, int nblk, int k, T* __restrict__ out) {
+  __shared__ T sh[32];
+  for (int j = blockIdx.x; j < k; j += gridDim.x) {
+    T s = T(0);
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += partial[(int64_t)b * k + j];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) out[j] = s;
+  }
+}
+
+// w[i] += sum_j coef_sign * h[j] * V[j][i]; partial[b] = sum of squares of the new w over block b
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads)
+multi_axpy_kernel(const T* __restrict__ V, int64_t ld, int k, const T* __restrict__ h, T coef_sign, T* w, int64_t n,
+                  T* __restrict__ partial) {
+  __shared__ T sh[32];
+  __shared__ T hs[128];
+  for (int j = threadIdx.x; j < k && j < 128; j += blockDim.x) hs[j] = coef_sign * h[j];
+  __syncthreads();
+  T sq = T(0);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    T v = w[i];
+    for (int j = 0; j < k; ++j) v = fma(hs[j], V[(int64_t)j * ld + i], v);
+    w[i] = v;
+    sq = fma(v, v, sq);
+  }
+  if (partial) {
+    const T s = block_sum(sq, sh);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+  }
+}
+
+template <typename T>
+__global__ void scale_kernel(T* __restrict__ y, const T* __restrict__ x, T s, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = s * x[i];
+}
+
+// y = a * x + b * z
+template <typename T>
+__global__ void axpby_kernel(T* __restrict__ y, T a, const T* __restrict__ x, T b, const T* __restrict__ z, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = a * x[i] + b * z[i];
+}
+
+// y = a - b (all FP64)
+__global__ void sub_kernel(double* __restrict__ y, const double* __restrict__ a, const double* __restrict__ b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = a[i] - b[i];
+}
+
+// partial[b] = (sum (a-b)^2, sum a^2)
+__global__ void __launch_bounds__(kRedThreads)
+diff_norm_kernel(const double* __restrict__ a, const double* __restrict__ b, int64_t n, double* __restrict__ partial) {
+  __shared__ double sh[32];
+  double d2 = 0.0, a2 = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double d = a[i] - b[i];
+    d2 = fma(d, d, d2);
+    a2 = fma(a[i], a[i], a2);
+  }
+  const double s1 = block_sum(d2, sh);
+  if (threadIdx.x == 0) partial[2 * blockIdx.x] = s1;
+  const double s2 = block_sum(a2, sh);
+  if (threadIdx.x == 0) partial[2 * blockIdx.x + 1] = s2;
+}
+
+// rf = (float)(r * s)
+__global__ void to_f32_kernel(float* __restrict__ y, const double* __restrict__ x, double s, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = (float)(x[i] * s);
+}
+
+// x += s * (double)d
+__global__ void add_f32_kernel(double* __restrict__ x, const float* __restrict__ d, double s, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = fma(s, (double)d[i], x[i]);
+}
+
+__global__ void source_kernel(const FaceGeom* __restrict__ geom, const int64_t* __restrict__ rows, int n_src,
+                              int64_t nrows, int nb, double* __restrict__ rho0) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n_src) return;
+  const int64_t r = rows[s];
+  rho0[((int64_t)s * nrows + r) * nb] = sqrt(geom[r].area);
+}
+
+// ---------------------------------------------------------------------------
+// Host-side helpers
+// ---------------------------------------------------------------------------
+
+struct Ctx {
+  const dfm_op* op;
+  cudaStream_t st;
+  int nsm;
+  int64_t n;  // rows * nb
+};
+
+inline unsigned grid_for(int64_t n, int nsm) {
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)nsm * 8));
+}
+
+template <typename T>
+int dots(const Ctx& c, const T* V, int64_t ld, int k, const T* w, T* partial, T* out_dev, T* out_host) {
+  {
+    ::dfm::KernelTimer timer_(DFM_KERNEL_DOT, c.st);
+    multi_dot_kernel<T><<<kRedBlocks, kRedThreads, 0, c.st>>>(V, ld, k, w, c.n, partial);
+  }
+  DFM_LAUNCHED();
+  DFM_CUDA_CHECK(cudaGetLastError());
+  reduce_partials_kernel<T><<<std::min(k, 64), kRedThreads, 0, c.st>>>(partial, kRedBlocks, k, out_dev);
+  DFM_LAUNCHED();
+  DFM_CUDA_CHECK(cudaGetLastError());
+  DFM_CUDA_CHECK(cudaMemcpyAsync(out_host, out_dev, sizeof(T) * k, cudaMemcpyDeviceToHost, c.st));
+  DFM_CUDA_CHECK(cudaStreamSynchronize(c.st));
+  return DFM_OK;
+}
+
+// w += sign * V h; returns |w|^2 in *sq_host (synchronises)
+template <typename T>
+int axpy_norm(const Ctx& c, const T* V, int64_t ld, int k, const T* h_dev, T sign, T* w, T* partial, T* red_dev,
+              double* sq_host) {
+  {
+    ::dfm::KernelTimer timer_(DFM_KERNEL_AXPY, c.st);
+    multi_axpy_kernel<T><<<kRedBlocks, kRedThreads, 0, c.st>>>(V, ld, k, h_dev, sign, w, c.n, partial);
+  }
+  DFM_LAUNCHED();
+  DFM_CUDA_CHECK(cudaGetLastError());
+  reduce_partials_kernel<T><<<1, kRedThreads, 0, c.st>>>(partial, kRedBlocks, 1, red_dev);
+  DFM_LAUNCHED();
+  DFM_CUDA_CHECK(cudaGetLastError());
+  T s;
+  DFM_CUDA_CHECK(cudaMemcpyAsync(&s, red_dev, sizeof(T), cudaMemcpyDeviceToHost, c.st));
+  DFM_CUDA_CHECK(cudaStreamSynchronize(c.st));
+  *sq_host = (double)s;
+  return DFM_OK;
+}
+
+template <typename T>
+int norm2(const Ctx& c, const T* v, T* partial, T* red_dev, double* out) {
+  T s;
+  int rc = dots<T>(c, v, 0, 1, v, partial, red_dev, &s);
+  *out = sqrt((double)s);
+  return rc;
+}
+
+// workspace carving
+struct Work {
+  char* base;
+  int64_t off = 0;
+  template <typename T>
+  T* take(int64_t count) {
+    off = (off + 255) & ~int64_t(255);
+    T* p = reinterpret_cast<T*>(base + off);
+    off += count * (int64_t)sizeof(T);
+    return p;
+  }
+};
+
+int ensure_work(const dfm_op* cop, int64_t bytes) {
+  dfm_op* op = const_cast<dfm_op*>(cop);
+  if (op->swork_bytes >= bytes) return DFM_OK;
+  cudaFree(op->swork);
+  op->swork = nullptr;
+  op->swork_bytes = 0;
+  DFM_CUDA_CHECK(cudaMalloc(&op->swork, bytes));
+  op->swork_bytes = bytes;
+  return DFM_OK;
+}
+
+// GMRES(m) on (I - B) x = b in precision T (operator applied as TV with TX = T).
+// x holds the initial guess.  tol is relative to |b|.  Counts operator
+// applications in *iters (incremented); stops at max_iter.  *est returns the
+// final true relative residual in precision T.
+template <typename T>
+int gmres(const Ctx& c, const T* b, T* x, double tol, int m, int max_iter, int* iters, double* est, T* V, T* tmp,
+          T* h_dev, T* partial, T* red_dev) {
+  const int64_t n = c.n;
+  const int xtype = sizeof(T) == 8 ? DFM_F64 : DFM_F32;
+  std::vector<T> hh(m + 2);
+  std::vector<double> H((m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+  double bnorm;
+  int rc = norm2<T>(c, b, partial, red_dev, &bnorm);
+  if (rc) return rc;
+  if (!(bnorm == bnorm) || isinf(bnorm)) return set_error(DFM_ERR_NONFINITE, "dfm_solve: non-finite right-hand side");
+  if (bnorm == 0.0) {
+    DFM_CUDA_CHECK(cudaMemsetAsync(x, 0, sizeof(T) * n, c.st));
+    *est = 0.0;
+    return DFM_OK;
+  }
+  while (true) {
+    // r = b - (I - B) x = (b - x) + B x   -> V[0]
+    axpby_kernel<T><<<grid_for(n, c.nsm), 256, 0, c.st>>>(tmp, T(1), b, T(-1), x, n);
+    DFM_LAUNCHED();
+    DFM_CUDA_CHECK(cudaGetLastError());
+    rc = apply_impl(c.op, x, tmp, V, 1, 1.0, 0, xtype, c.st);
+    if (rc) return rc;
+    ++*iters;
+    double beta;
+    rc = norm2<T>(c, V, partial, red_dev, &beta);
+    if (rc) return rc;
+    if (!(beta == beta) || isinf(beta)) return set_error(DFM_ERR_NONFINITE, "dfm_solve: non-finite residual");
+    *est = beta / bnorm;
+    if (beta <= tol * bnorm) return DFM_OK;
+    if (*iters >= max_iter) return DFM_ERR_NOT_CONVERGED;
+    scale_kernel<T><<<grid_for(n, c.nsm), 256, 0, c.st>>>(V, V, T(1.0 / beta), n);
+    DFM_LAUNCHED();
+    DFM_CUDA_CHECK(cudaGetLastError());
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int kdone = 0;
+    for (int j = 0; j < m; ++j) {
+      T* vj = V + (int64_t)j * n;
+      T* w = V + (int64_t)(j + 1) * n;
+      // w = v_j - B v_j
+      rc = apply_impl(c.op, vj, vj, w, 1, -1.0, 0, xtype, c.st);
+      if (rc) return rc;
+      ++*iters;
+      // classical Gram-Schmidt: h = V^T w (plus |w|^2 as the last entry)
+      rc = dots<T>(c, V, n, j + 2, w, partial, h_dev, hh.data());
+      if (rc) return rc;
+      const double wnorm_before = sqrt(std::max(0.0, (double)hh[j + 1]));
+      double sq;
+      rc = axpy_norm<T>(c, V, n, j + 1, h_dev, T(-1), w, partial, red_dev, &sq);
+      if (rc) return rc;
+      for (int i = 0; i <= j; ++i) H[i * m + j] = (double)hh[i];
+      if (sqrt(sq) < 0.5 * wnorm_before) {  // re-orthogonalise once
+        rc = dots<T>(c, V, n, j + 1, w, partial, h_dev, hh.data());
+        if (rc) return rc;
+        rc = axpy_norm<T>(c, V, n, j + 1, h_dev, T(-1), w, partial, red_dev, &sq);
+        if (rc) return rc;
+        for (int i = 0; i <= j; ++i) H[i * m + j] += (double)hh[i];
+      }
+      double hn = sqrt(sq);
+      if (!(hn == hn)) return set_error(DFM_ERR_NONFINITE, "dfm_solve: non-finite Krylov vector");
+      H[(j + 1) * m + j] = hn;
+      if (hn > 0) {
+        scale_kernel<T><<<grid_for(n, c.nsm), 256, 0, c.st>>>(w, w, T(1.0 / hn), n);
+        DFM_LAUNCHED();
+        DFM_CUDA_CHECK(cudaGetLastError());
+      }
+      for (int i = 0; i < j; ++i) {
+        const double a = H[i * m + j], bb = H[(i + 1) * m + j];
+        H[i * m + j] = cs[i] * a + sn[i] * bb;
+        H[(i + 1) * m + j] = -sn[i] * a + cs[i] * bb;
+      }
+      const double den = hypot(H[j * m + j], H[(j + 1) * m + j]);
+      cs[j] = den > 0 ? H[j * m + j] / den : 1.0;
+      sn[j] = den > 0 ? H[(j + 1) * m + j] / den : 0.0;
+      H[j * m + j] = den;
+      H[(j + 1) * m + j] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      kdone = j + 1;
+      if (fabs(g[j + 1]) <= 0.5 * tol * bnorm || *iters >= max_iter || hn == 0.0) break;
+    }
+    // y = H^{-1} g (upper triangular), x += V y
+    for (int i = kdone - 1; i >= 0; --i) {
+      double s = g[i];
+      for (int k = i + 1; k < kdone; ++k) s -= H[i * m + k] * y[k];
+      y[i] = H[i * m + i] != 0.0 ? s / H[i * m + i] : 0.0;
+    }
+    for (int i = 0; i < kdone; ++i) hh[i] = (T)y[i];
+    DFM_CUDA_CHECK(cudaMemcpyAsync(h_dev, hh.data(), sizeof(T) * kdone, cudaMemcpyHostToDevice, c.st));
+    {
+      ::dfm::KernelTimer timer_(DFM_KERNEL_AXPY, c.st);
+      multi_axpy_kernel<T><<<kRedBlocks, kRedThreads, 0, c.st>>>(V, n, kdone, h_dev, T(1), x, n, nullptr);
+    }
+    DFM_LAUNCHED();
+    DFM_CUDA_CHECK(cudaGetLastError());
+  }
+}
+
+// FP64 relative residual |rho0 - (I - B) x| / |rho0| with FP64 vectors
+int residual64(const Ctx& c, const double* rho0, const double* x, double* r, double* partial, double* red_dev,
+               double* out, double* rnorm_abs) {
+  sub_kernel<<<grid_for(c.n, c.nsm), 256, 0, c.st>>>(r, rho0, x, c.n);
+  DFM_LAUNCHED();
+  DFM_CUDA_CHECK(cudaGetLastError());
+  // r = (rho0 - x) + B x, written to a second half of r
+  double* r2 = r + c.n;
+  int rc = apply_impl(c.op, x, r, r2, 1, 1.0, 0, DFM_F64, c.st);
+  if (rc) return rc;
+  double rn, bn;
+  rc = norm2<double>(c, r2, partial, red_dev, &rn);
+  if (rc) return rc;
+  rc = norm2<double>(c, rho0, partial, red_dev, &bn);
+  if (rc) return rc;
+  *rnorm_abs = rn;
+  *out = bn > 0 ? rn / bn : rn;
+  return DFM_OK;
+}
+
+}  // namespace
+}  // namespace dfm
+
+using namespace dfm;
+
+extern "C" int dfm_source(const dfm_mesh* mesh, int Np, const int64_t* rows_host, int n_src, double* rho0,
+                          void* stream) {
+  if (!mesh || !rows_host || !rho0 || n_src < 1 || Np < 0 || Np > 8)
+    return set_error(DFM_ERR_ARG, "dfm_source: bad argument");
+  for (int s = 0; s < n_src; ++s)
+    if (rows_host[s] < 0 || rows_host[s] >= mesh->nrows) return set_error(DFM_ERR_ARG, "dfm_source: row out of range");
+  cudaStream_t st = as_stream(stream);
+  const int nb = nbasis(Np);
+  int64_t* rows_d = nullptr;
+  DFM_CUDA_CHECK(cudaMallocAsync(&rows_d, sizeof(int64_t) * n_src, st));
+  DFM_CUDA_CHECK(cudaMemcpyAsync(rows_d, rows_host, sizeof(int64_t) * n_src, cudaMemcpyHostToDevice, st));
+  DFM_CUDA_CHECK(cudaMemsetAsync(rho0, 0, sizeof(double) * n_src * mesh->nrows * nb, st));
+  source_kernel<<<(n_src + 127) / 128, 128, 0, st>>>(mesh->geom, rows_d, n_src, mesh->nrows, nb, rho0);
+  DFM_LAUNCHED();
+  DFM_CUDA_CHECK(cudaGetLastError());
+  DFM_CUDA_CHECK(cudaFreeAsync(rows_d, st));
+  return DFM_OK;
+}
+
+extern "C" int dfm_solve(const dfm_op* op, const double* rho0, int R, double* rho, const dfm_solve_opts* opts,
+                         void* stream, dfm_solve_info* info) {
+  if (!op || !rho0 || !rho || !opts || R < 1) return set_error(DFM_ERR_ARG, "dfm_solve: bad argument");
+  if (rho == rho0) return set_error(DFM_ERR_ARG, "dfm_solve: rho must not alias rho0");
+  if (!(opts->tol > 0)) return set_error(DFM_ERR_ARG, "dfm_solve: tol must be > 0");
+  const int method = opts->method;
+  const int max_iter = opts->max_iter > 0 ? opts->max_iter : 20000;
+  const int m = opts->restart > 0 ? std::min(opts->restart, 120) : 64;
+  const double inner_tol = opts->inner_tol > 0 ? opts->inner_tol : 1e-4;
+  Ctx c;
+  c.op = op;
+  c.st = as_stream(stream);
+  c.n = op->nrows * op->nb;
+  int dev = 0;
+  DFM_CUDA_CHECK(cudaGetDevice(&dev));
+  DFM_CUDA_CHECK(cudaDeviceGetAttribute(&c.nsm, cudaDevAttrMultiProcessorCount, dev));
+  const int64_t n = c.n;
+  if (method == DFM_SOLVE_NEUMANN && op->precision != DFM_F64 && op->precision != DFM_F32)
+    return set_error(DFM_ERR_UNSUPPORTED, "dfm_solve: Neumann needs an FP64 or FP32 operator");
+  if (method == DFM_SOLVE_GMRES_IR && op->precision != DFM_F32)
+    return set_error(DFM_ERR_UNSUPPORTED, "dfm_solve: GMRES_IR needs an FP32 operator");
+  if (method < 0 || method > 2) return set_error(DFM_ERR_ARG, "dfm_solve: unknown method");
+  // workspace: FP64 vectors (x scratch, residual x2), Krylov basis in the inner precision
+  const bool inner64 = (method == DFM_SOLVE_GMRES && op->precision == DFM_F64);
+  const int64_t es = inner64 ? 8 : 4;
+  int64_t bytes = 0;
+  bytes += 4 * n * 8 + 4096;                            // r (2n), tmp64 (n), xold (n)
+  const int64_t inner_bytes = (int64_t)(m + 5) * n * es + 8 * 256;  // V (m+1), tmp, b, x inner (+ alignment)
+  bytes += inner_bytes + 4096;
+  bytes += (kRedBlocks * 130 + 256) * 8 + 4096;         // partials, h, red
+  int rc = ensure_work(op, bytes + 8 * 256);
+  if (rc) return rc;
+  Work W{reinterpret_cast<char*>(op->swork)};
+  double* r64 = W.take<double>(2 * n);
+  double* tmp64 = W.take<double>(n);
+  double* xold = W.take<double>(n);
+  double* part64 = W.take<double>(kRedBlocks * 130);
+  double* h64 = W.take<double>(130);
+  double* red64 = W.take<double>(8);
+  char* inner_base = W.take<char>(inner_bytes);
+  dfm_solve_info acc_info{0, 0, 0.0};
+  int status = DFM_OK;
+  for (int s = 0; s < R && status != DFM_ERR_NONFINITE; ++s) {
+    const double* b = rho0 + (int64_t)s * n;
+    double* x = rho + (int64_t)s * n;
+    int iters = 0, outer = 0;
+    double resid = 0.0, rabs = 0.0;
+    if (!opts->use_x0) DFM_CUDA_CHECK(cudaMemsetAsync(x, 0, sizeof(double) * n, c.st));
+    int rs = DFM_OK;
+    if (method == DFM_SOLVE_NEUMANN) {
+      // x <- rho0 + B x until |x_new - x| <= tol |x_new|
+      std::vector<double> ph(2 * kRedBlocks);
+      while (true) {
+        DFM_CUDA_CHECK(cudaMemcpyAsync(xold, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, c.st));
+        rs = apply_impl(op, xold, b, x, 1, 1.0, 0, DFM_F64, c.st);
+        if (rs) return rs;
+        ++iters;
+        diff_norm_kernel<<<kRedBlocks, kRedThreads, 0, c.st>>>(x, xold, n, part64);
+        DFM_LAUNCHED();
+        DFM_CUDA_CHECK(cudaGetLastError());
+        DFM_CUDA_CHECK(cudaMemcpyAsync(ph.data(), part64, sizeof(double) * 2 * kRedBlocks, cudaMemcpyDeviceToHost, c.st));
+        DFM_CUDA_CHECK(cudaStreamSynchronize(c.st));
+        double d2 = 0, a2 = 0;
+        for (int i = 0; i < kRedBlocks; ++i) {
+          d2 += ph[2 * i];
+          a2 += ph[2 * i + 1];
+        }
+        if (!(d2 == d2) || isinf(d2)) {
+          rs = set_error(DFM_ERR_NONFINITE, "dfm_solve: non-finite Neumann iterate");
+          break;
+        }
+        if (sqrt(d2) <= opts->tol * sqrt(a2)) break;
+        if (iters >= max_iter) {
+          rs = set_error(DFM_ERR_NOT_CONVERGED, "dfm_solve: Neumann series reached max_iter");
+          break;
+        }
+      }
+      if (rs != DFM_ERR_NONFINITE) {
+        int r2 = residual64(c, b, x, r64, part64, red64, &resid, &rabs);
+        if (r2) return r2;
+      }
+    } else if (method == DFM_SOLVE_GMRES && inner64) {
+      Work Wi{inner_base};
+      double* V = Wi.take<double>((int64_t)(m + 1) * n);
+      double* tmp = Wi.take<double>(n);
+      double est = 0;
+      rs = gmres<double>(c, b, x, opts->tol, m, max_iter, &iters, &est, V, tmp, h64, part64, red64);
+      if (rs == DFM_ERR_NOT_CONVERGED) set_error(rs, "dfm_solve: GMRES reached max_iter");
+      if (rs == DFM_OK || rs == DFM_ERR_NOT_CONVERGED) {
+        int r2 = residual64(c, b, x, r64, part64, red64, &resid, &rabs);
+        if (r2) return r2;
+      }
+    } else {
+      // FP32 Krylov: plain GMRES (tol on the FP32 residual) or refinement around it
+      Work Wi{inner_base};
+      float* V = Wi.take<float>((int64_t)(m + 1) * n);
+      float* tmp = Wi.take<float>(n);
+      float* bf = Wi.take<float>(n);
+      float* xf = Wi.take<float>(n);
+      float* part32 = reinterpret_cast<float*>(part64);
+      float* h32 = reinterpret_cast<float*>(h64);
+      float* red32 = reinterpret_cast<float*>(red64);
+      while (true) {
+        int r2 = residual64(c, b, x, r64, part64, red64, &resid, &rabs);
+        if (r2) return r2;
+        if (!(resid == resid) || isinf(resid)) {
+          rs = set_error(DFM_ERR_NONFINITE, "dfm_solve: non-finite residual");
+          break;
+        }
+        if (resid <= opts->tol) break;
+        if (iters >= max_iter) {
+          rs = set_error(DFM_ERR_NOT_CONVERGED, "dfm_solve: refinement reached max_iter");
+          break;
+        }
+        // correction: (I - B) d = r / |r| in FP32
+        to_f32_kernel<<<grid_for(n, c.nsm), 256, 0, c.st>>>(bf, r64 + n, 1.0 / rabs, n);
+        DFM_LAUNCHED();
+        DFM_CUDA_CHECK(cudaGetLastError());
+        DFM_CUDA_CHECK(cudaMemsetAsync(xf, 0, sizeof(float) * n, c.st));
+        double est = 0;
+        const double itol = method == DFM_SOLVE_GMRES_IR ? inner_tol : std::max(opts->tol, 1e-6);
+        int gi = gmres<float>(c, bf, xf, itol, m, max_iter, &iters, &est, V, tmp, h32, part32, red32);
+        if (gi != DFM_OK && gi != DFM_ERR_NOT_CONVERGED) return gi;
+        add_f32_kernel<<<grid_for(n, c.nsm), 256, 0, c.st>>>(x, xf, rabs, n);
+        DFM_LAUNCHED();
+        DFM_CUDA_CHECK(cudaGetLastError());
+        ++outer;
+        if (outer > 200) {
+          rs = set_error(DFM_ERR_NOT_CONVERGED, "dfm_solve: refinement stalled");
+          break;
+        }
+      }
+    }
+    acc_info.iters += iters;
+    acc_info.outer += outer;
+    acc_info.resid = std::max(acc_info.resid, resid);
+    if (rs != DFM_OK && status == DFM_OK) status = rs;
+  }
+  if (info) *info = acc_info;
+  return status;
+}

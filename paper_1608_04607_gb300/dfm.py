@@ -1,0 +1,323 @@
+"""Python binding of libdfm (include/dfm.h): argument marshalling only.
+
+Every step of the method runs in the CUDA library; this module converts numpy
+arrays and torch CUDA tensors to the C ABI's plain pointers and sizes, owns
+the library handles and raises DFMError on a non-zero status.  There is no
+CPU fallback: if libdfm.so cannot be loaded, importing the library raises.
+PyTorch provides device memory and the current CUDA stream only.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libdfm.so")
+
+DFM_OK = 0
+DFM_ERR_ARG = -1
+DFM_ERR_MESH = -2
+DFM_ERR_CUDA = -3
+DFM_ERR_OOM = -4
+DFM_ERR_NOT_CONVERGED = -5
+DFM_ERR_NONFINITE = -6
+DFM_ERR_UNSUPPORTED = -7
+
+F64, F32, BF16 = 0, 1, 2
+NEUMANN, GMRES, GMRES_IR = 0, 1, 2
+
+
+class DFMError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"dfm error {code}: {msg}")
+        self.code = code
+
+
+class MeshInfo(ctypes.Structure):
+    _fields_ = [("n_verts", ctypes.c_int64), ("n_tets", ctypes.c_int64), ("n_rows", ctypes.c_int64),
+                ("n_boundary_rows", ctypes.c_int64), ("min_abs_volume", ctypes.c_double),
+                ("total_volume", ctypes.c_double)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("Np", ctypes.c_int), ("mu", ctypes.c_void_p), ("mu_uniform", ctypes.c_double),
+                ("quad_order", ctypes.c_int), ("max_patch_deg", ctypes.c_double), ("precision", ctypes.c_int)]
+
+
+class OpInfo(ctypes.Structure):
+    _fields_ = [("Np", ctypes.c_int), ("nb", ctypes.c_int), ("precision", ctypes.c_int), ("n_rows", ctypes.c_int64),
+                ("row_stride", ctypes.c_int64), ("vals", ctypes.c_void_p), ("bytes", ctypes.c_int64)]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("method", ctypes.c_int), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
+                ("restart", ctypes.c_int), ("use_x0", ctypes.c_int), ("inner_tol", ctypes.c_double)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("outer", ctypes.c_int), ("resid", ctypes.c_double)]
+
+
+_lib = None
+
+# every entry point of include/dfm.h with its ctypes signature
+_vp, _i, _i64, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+SIGNATURES = {
+    "dfm_mesh_create": (_i, [_vp, _i64, _vp, _i64, _vp, _d, _vp, ctypes.POINTER(_vp)]),
+    "dfm_mesh_destroy": (None, [_vp]),
+    "dfm_mesh_info": (_i, [_vp, ctypes.POINTER(MeshInfo)]),
+    "dfm_mesh_recv": (_i, [_vp, _vp]),
+    "dfm_gauss_legendre": (_i, [_i, _vp, _vp, _vp]),
+    "dfm_assemble": (_i, [_vp, ctypes.POINTER(Params), _vp, ctypes.POINTER(_vp)]),
+    "dfm_assemble_into": (_i, [_vp, ctypes.POINTER(Params), _vp, _vp]),
+    "dfm_op_destroy": (None, [_vp]),
+    "dfm_op_info": (_i, [_vp, ctypes.POINTER(OpInfo)]),
+    "dfm_op_copy_vals": (_i, [_vp, _vp, _i64, _vp]),
+    "dfm_apply": (_i, [_vp, _vp, _vp, _vp, _i, _d, _i, _i, _vp]),
+    "dfm_source": (_i, [_vp, _i, _vp, _i, _vp, _vp]),
+    "dfm_solve": (_i, [_vp, _vp, _i, _vp, ctypes.POINTER(SolveOpts), _vp, ctypes.POINTER(SolveInfo)]),
+    "dfm_launch_count": (ctypes.c_longlong, []),
+    "dfm_stats_enable": (_i, [_i]),
+    "dfm_stats_reset": (_i, []),
+    "dfm_kernel_stats": (_i, [_i, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]),
+    "dfm_op_nodes": (_i, [_vp, ctypes.POINTER(ctypes.c_int64)]),
+    "dfm_last_error": (ctypes.c_char_p, []),
+    "dfm_version": (ctypes.c_char_p, []),
+}
+
+
+def load(path: str = LIB_PATH):
+    """Load libdfm.so (building it with nvcc first if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        from . import build as _build
+
+        _build.build()
+    L = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(rc, what=""):
+    if rc != DFM_OK:
+        msg = _lib.dfm_last_error().decode()
+        raise DFMError(rc, f"{what}: {msg}" if what else msg)
+
+
+def _stream():
+    import torch
+
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    """Device pointer of a contiguous torch CUDA tensor (or None)."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def nbasis(Np: int) -> int:
+    return (Np + 1) * (Np + 2) // 2
+
+
+class Mesh:
+    """A tetrahedral mesh on the device (dfm_mesh_create)."""
+
+    def __init__(self, verts, tets, refl=0.95):
+        L = load()
+        v = np.ascontiguousarray(verts, dtype=np.float64)
+        t = np.ascontiguousarray(tets, dtype=np.int32)
+        if np.ndim(refl) == 0:
+            rp, rd = None, float(refl)
+        else:
+            r = np.ascontiguousarray(refl, dtype=np.float64)
+            rp, rd = r.ctypes.data_as(ctypes.c_void_p), 0.0
+        h = ctypes.c_void_p()
+        _check(L.dfm_mesh_create(v.ctypes.data_as(ctypes.c_void_p), v.shape[0], t.ctypes.data_as(ctypes.c_void_p),
+                                 t.shape[0], rp, rd, _stream(), ctypes.byref(h)), "dfm_mesh_create")
+        self._h = h
+        self.n_tets = int(t.shape[0])
+        self.n_rows = 4 * self.n_tets
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> MeshInfo:
+        mi = MeshInfo()
+        _check(_lib.dfm_mesh_info(self._h, ctypes.byref(mi)), "dfm_mesh_info")
+        return mi
+
+    def recv(self) -> np.ndarray:
+        out = np.empty(self.n_rows, dtype=np.int32)
+        _check(_lib.dfm_mesh_recv(self._h, out.ctypes.data_as(ctypes.c_void_p)), "dfm_mesh_recv")
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.dfm_mesh_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Operator:
+    """The assembled operator B (dfm_assemble)."""
+
+    def __init__(self, mesh: Mesh, Np: int, mu=0.0, precision=F32, quad_order=0, max_patch_deg=0.0):
+        import torch
+
+        self.mesh = mesh
+        self._keep = []
+        p = self._params(Np, mu, precision, quad_order, max_patch_deg)
+        h = ctypes.c_void_p()
+        _check(_lib.dfm_assemble(mesh.handle, ctypes.byref(p), _stream(), ctypes.byref(h)), "dfm_assemble")
+        self._h = h
+        oi = OpInfo()
+        _check(_lib.dfm_op_info(h, ctypes.byref(oi)), "dfm_op_info")
+        self.Np, self.nb, self.precision = oi.Np, oi.nb, oi.precision
+        self.n_rows, self.row_stride, self.bytes = oi.n_rows, oi.row_stride, oi.bytes
+        self._torch = torch
+
+    def _params(self, Np, mu, precision, quad_order, max_patch_deg):
+        import torch
+
+        p = Params()
+        p.Np = Np
+        if isinstance(mu, torch.Tensor):
+            mu_t = mu.to(device="cuda", dtype=torch.float64).contiguous()
+            self._keep = [mu_t]
+            p.mu = mu_t.data_ptr()
+            p.mu_uniform = 0.0
+        else:
+            p.mu = None
+            p.mu_uniform = float(mu)
+        p.quad_order = quad_order
+        p.max_patch_deg = max_patch_deg
+        p.precision = precision
+        return p
+
+    def reassemble(self, mu, quad_order=0, max_patch_deg=0.0):
+        p = self._params(self.Np, mu, self.precision, quad_order, max_patch_deg)
+        _check(_lib.dfm_assemble_into(self.mesh.handle, ctypes.byref(p), self._h, _stream()), "dfm_assemble_into")
+
+    @property
+    def handle(self):
+        return self._h
+
+    def blocks(self):
+        """Copy of the block storage as a torch CUDA tensor [rows, 3, nb, nb]."""
+        torch = self._torch
+        dt = {F64: torch.float64, F32: torch.float32}[self.precision]
+        buf = torch.empty(self.n_rows * self.row_stride, dtype=dt, device="cuda")
+        _check(_lib.dfm_op_copy_vals(self._h, _ptr(buf), self.bytes, _stream()), "dfm_op_copy_vals")
+        nb = self.nb
+        return buf.view(self.n_rows, self.row_stride)[:, :3 * nb * nb].reshape(self.n_rows, 3, nb, nb)
+
+    def apply(self, x, x0=None, alpha=1.0, trans=False, out=None):
+        """y = x0 + alpha B x (or B^T x); x of shape [R, rows, nb] or [rows, nb]."""
+        torch = self._torch
+        xtype = {torch.float64: F64, torch.float32: F32}[x.dtype]
+        R = 1 if x.dim() == 2 else x.shape[0]
+        y = torch.empty_like(x) if out is None else out
+        _check(_lib.dfm_apply(self._h, _ptr(x), _ptr(x0), _ptr(y), R, float(alpha), int(bool(trans)), xtype,
+                              _stream()), "dfm_apply")
+        return y
+
+    def solve(self, rho0, method=GMRES_IR, tol=1e-8, max_iter=0, restart=0, x0=None, inner_tol=0.0,
+              raise_on_nonconvergence=True):
+        """rho = (I - B)^{-1} rho0 (FP64, [R, rows, nb] or [rows, nb]); returns (rho, SolveInfo)."""
+        torch = self._torch
+        R = 1 if rho0.dim() == 2 else rho0.shape[0]
+        rho = torch.empty_like(rho0) if x0 is None else x0.clone()
+        o = SolveOpts(method=method, tol=tol, max_iter=max_iter, restart=restart, use_x0=int(x0 is not None),
+                      inner_tol=inner_tol)
+        info = SolveInfo()
+        rc = _lib.dfm_solve(self._h, _ptr(rho0), R, _ptr(rho), ctypes.byref(o), _stream(), ctypes.byref(info))
+        if rc == DFM_ERR_NOT_CONVERGED and not raise_on_nonconvergence:
+            return rho, info
+        _check(rc, "dfm_solve")
+        return rho, info
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.dfm_op_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def source(mesh: Mesh, Np: int, rows):
+    """Unit isotropic sources on the given rows: FP64 [n_src, rows, nb] (dfm_source)."""
+    import torch
+
+    rows = np.ascontiguousarray(np.atleast_1d(rows), dtype=np.int64)
+    out = torch.empty((rows.size, mesh.n_rows, nbasis(Np)), dtype=torch.float64, device="cuda")
+    _check(_lib.dfm_source(mesh.handle, Np, rows.ctypes.data_as(ctypes.c_void_p), rows.size, _ptr(out), _stream()),
+           "dfm_source")
+    return out
+
+
+def gauss_legendre(q: int):
+    """Gauss-Legendre nodes/weights computed on the device (dfm_gauss_legendre)."""
+    import torch
+
+    x = torch.empty(q, dtype=torch.float64, device="cuda")
+    w = torch.empty(q, dtype=torch.float64, device="cuda")
+    load()
+    _check(_lib.dfm_gauss_legendre(q, _ptr(x), _ptr(w), _stream()), "dfm_gauss_legendre")
+    return x, w
+
+
+KERNEL_ASSEMBLE, KERNEL_SPMV, KERNEL_SPMV_T, KERNEL_DOT, KERNEL_AXPY = 0, 1, 2, 3, 4
+
+
+def launch_count() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(load().dfm_launch_count())
+
+
+def stats_enable(on: bool = True):
+    _check(load().dfm_stats_enable(int(bool(on))), "dfm_stats_enable")
+
+
+def stats_reset():
+    _check(load().dfm_stats_reset(), "dfm_stats_reset")
+
+
+def kernel_stats(kernel: int):
+    """(launches, total device ms) of one kernel since the last reset."""
+    n = ctypes.c_int64()
+    ms = ctypes.c_double()
+    _check(load().dfm_kernel_stats(kernel, ctypes.byref(n), ctypes.byref(ms)), "dfm_kernel_stats")
+    return int(n.value), float(ms.value)
+
+
+def op_nodes(op: "Operator") -> int:
+    n = ctypes.c_int64()
+    _check(load().dfm_op_nodes(op.handle, ctypes.byref(n)), "dfm_op_nodes")
+    return int(n.value)
+
+
+def version() -> str:
+    return load().dfm_version().decode()

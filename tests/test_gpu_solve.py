@@ -1,0 +1,135 @@
+"""GPU parity of the block-sparse operator application, sources and the
+stationary solvers against the FP64 oracle, through the C ABI.
+
+The solve is checked two ways (a solution error bound needs both):
+ - against an FP64 solve of the SAME assembled operator (the GPU blocks
+   widened to FP64 and solved by the oracle's dense LU), which isolates the
+   solver: relative error <= 1e-6 after refinement (1e-9 for the FP64 path);
+ - end to end against the oracle's own operator, where the quadrature error
+   of the blocks (~3e-7) is amplified by the conditioning of I - B.
+"""
+import numpy as np
+import pytest
+
+from gpu_helpers import need_gpu, to_oracle_layout
+from paper_1608_04607_gb300.inputs import kuhn_cube_mesh, workload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def D():
+    need_gpu()
+    from paper_1608_04607_gb300 import dfm
+
+    dfm.load()
+    return dfm
+
+
+def _gpu_op_as_oracle(oracle_mod, op, mesh, nt, Np):
+    blocks = to_oracle_layout(op.blocks().cpu().numpy(), mesh.recv(), nt)
+    t, f, fp = oracle_mod.pair_list(nt)
+    dest = mesh.recv()[4 * t + fp].reshape(4 * nt, 3).astype(np.int64)
+    return oracle_mod.Operator(Np=Np, blocks=np.ascontiguousarray(blocks), dest=dest)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("xdt", ["f64", "f32"])
+def test_apply_forward_and_transpose(D, oracle_mod, prec, xdt):
+    import torch
+
+    m = kuhn_cube_mesh(3, jitter=0.2, seed=8)
+    Np = 4
+    mesh = D.Mesh(m.verts, m.tets, refl=0.9)
+    op = D.Operator(mesh, Np, mu=0.2, precision=prec)
+    ref_op = _gpu_op_as_oracle(oracle_mod, op, mesh, m.n_tets, Np)
+    rng = np.random.default_rng(1)
+    R = 3
+    x = rng.standard_normal((R, 4 * m.n_tets, op.nb))
+    x0 = rng.standard_normal((R, 4 * m.n_tets, op.nb))
+    dt = torch.float64 if xdt == "f64" else torch.float32
+    xt = torch.tensor(x, dtype=dt, device="cuda")
+    x0t = torch.tensor(x0, dtype=dt, device="cuda")
+    tol = 1e-12 if (xdt == "f64") else 2e-6
+    for trans in (False, True):
+        y = op.apply(xt, x0=x0t, alpha=-0.7, trans=trans).cpu().numpy()
+        for r in range(R):
+            xr = xt[r].double().cpu().numpy()
+            x0r = x0t[r].double().cpu().numpy()
+            yr = oracle_mod.apply(ref_op, xr, trans=trans, x0=x0r, alpha=-0.7)
+            assert np.abs(y[r] - yr).max() <= tol * np.abs(yr).max()
+        # x0 = NULL
+        y2 = op.apply(xt, alpha=1.0, trans=trans).cpu().numpy()
+        yr = oracle_mod.apply(ref_op, xt[0].double().cpu().numpy(), trans=trans)
+        assert np.abs(y2[0] - yr).max() <= tol * np.abs(yr).max()
+
+
+def test_source_vector(D, oracle_mod):
+    m = kuhn_cube_mesh(3, jitter=0.2, seed=8)
+    mesh = D.Mesh(m.verts, m.tets)
+    rows = np.array([5, 77, 300, 5])
+    got = D.source(mesh, 3, rows).cpu().numpy()
+    for s, r in enumerate(rows):
+        ref = oracle_mod.source_vector(m.verts, m.tets, [r], 3)
+        np.testing.assert_allclose(got[s], ref, rtol=1e-15, atol=0)
+
+
+def test_single_cube_neumann(D, oracle_mod):
+    """The small single-cube workload: FP64 operator, Neumann series to 1e-10."""
+    import torch
+
+    w = workload("kuhn1_np2")
+    m = w["mesh"]
+    mesh = D.Mesh(m.verts, m.tets, refl=w["refl"])
+    op = D.Operator(mesh, w["Np"], mu=0.1, precision=D.F64)
+    rho0 = D.source(mesh, w["Np"], w["sources"])
+    rho, info = op.solve(rho0, method=D.NEUMANN, tol=1e-10)
+    assert info.iters > 10
+    got = rho[0].cpu().numpy()
+    same = _gpu_op_as_oracle(oracle_mod, op, mesh, m.n_tets, w["Np"])
+    ref_same = oracle_mod.solve_dense(same, rho0[0].cpu().numpy())
+    # stopping on the increment |x_k+1 - x_k| <= tol |x_k+1| leaves an error of at
+    # most about tol * r / (1 - r), r the spectral radius of B
+    r = np.max(np.abs(np.linalg.eigvals(oracle_mod.dense(same))))
+    bound = 1e-10 * r / (1 - r)
+    assert np.linalg.norm(got - ref_same) <= 1.5 * bound * np.linalg.norm(ref_same)
+    own = oracle_mod.assemble(m.verts, m.tets, w["mu"], w["refl"], w["Np"])
+    ref_own = oracle_mod.solve_dense(own, oracle_mod.source_vector(m.verts, m.tets, w["sources"], w["Np"]))
+    assert np.linalg.norm(got - ref_own) <= 1e-5 * np.linalg.norm(ref_own)
+    # GMRES on the FP64 operator agrees
+    rho2, info2 = op.solve(rho0, method=D.GMRES, tol=1e-12)
+    assert np.linalg.norm(rho2[0].cpu().numpy() - ref_same) <= 1e-10 * np.linalg.norm(ref_same)
+
+
+@pytest.mark.parametrize("method", ["ir", "gmres64"])
+def test_gmres_jittered(D, oracle_mod, method):
+    m = kuhn_cube_mesh(3, jitter=0.2, seed=8)
+    Np = 3
+    mesh = D.Mesh(m.verts, m.tets, refl=0.95)
+    prec = D.F32 if method == "ir" else D.F64
+    op = D.Operator(mesh, Np, mu=0.05, precision=prec)
+    rows = [int(np.nonzero(mesh.recv() == np.arange(mesh.n_rows))[0][3])]
+    rho0 = D.source(mesh, Np, rows)
+    meth = D.GMRES_IR if method == "ir" else D.GMRES
+    rho, info = op.solve(rho0, method=meth, tol=1e-10, restart=40)
+    assert info.resid <= 1e-10
+    same = _gpu_op_as_oracle(oracle_mod, op, mesh, m.n_tets, Np)
+    b = rho0[0].cpu().numpy()
+    ref = oracle_mod.solve_dense(same, b)
+    got = rho[0].cpu().numpy()
+    assert np.linalg.norm(got - ref) <= 1e-8 * np.linalg.norm(ref)
+    # the library's FP64 residual agrees with the oracle's
+    assert oracle_mod.residual(same, got, b) <= 1.5e-10
+
+
+def test_solver_reports_nonconvergence(D):
+    m = kuhn_cube_mesh(2, jitter=0.2, seed=8)
+    mesh = D.Mesh(m.verts, m.tets, refl=0.95)
+    op = D.Operator(mesh, 2, mu=0.05, precision=D.F64)
+    rho0 = D.source(mesh, 2, [0])
+    with pytest.raises(D.DFMError) as e:
+        op.solve(rho0, method=D.NEUMANN, tol=1e-14, max_iter=5)
+    assert e.value.code == D.DFM_ERR_NOT_CONVERGED
+    rho, info = op.solve(rho0, method=D.GMRES_IR if op.precision == D.F32 else D.GMRES, tol=1e-14, max_iter=3,
+                         raise_on_nonconvergence=False)
+    assert info.iters <= 4
