@@ -1,0 +1,416 @@
+"""Benchmark: stationary DFM solves per second on one GB300 (or N replicas).
+
+One step = the device-resident hot path on the 20^3 Kuhn-cube workload
+(48,000 jittered tets, Np = 4, mu = 0.05, r = 0.95, one boundary-face source):
+assemble the operator B (FP32 blocks, FP64 geometry set-up), project the
+source, and solve (I - B) rho = rho0 by FP64-residual iterative refinement
+around FP32 GMRES to a relative residual of 1e-8.  Inputs (mesh on device)
+are resident when the timed region starts; the operator (518 MB) and Krylov
+basis are larger than L2, so no flush is needed between steps.
+
+The e2e figure runs the same metric through the C ABI from HOST buffers:
+mesh arrays copied in (face matching and geometry run every step), the
+solution copied back to pinned host memory, all inside the timed region.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+Under torchrun (N > 1) every rank runs an independent replica (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "stationary solves/s at 1e-6 rel err"
+WORKLOAD = "kuhn20_np4"
+WORKLOAD_DESC = ("20^3 Kuhn cube x 6 = 48,000 jittered tets (jitter 0.2h, seed 0); Np = 4 (15 Zernike functions); "
+                 "mu = 0.05; boundary reflection 0.95; unit isotropic source on the x = 0 face at (0, 1/2, 1/2); "
+                 "solve to FP64 relative residual 1e-8 (GMRES(64)-IR, FP32 inner)")
+FP32_LANES_PER_SM = 128
+HBM_PEAK_FALLBACK = 6800.0
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": HBM_PEAK_FALLBACK, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms in the background."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def flops_per_node(Np: int) -> int:
+    """Counted FP32 operations per quadrature node of the assembly kernel: the
+    rank-1 block update (2 nb^2), two Zernike vectors (complex powers 6 per
+    order, radial recursion and angular products ~4 per function) and the node
+    geometry (bilinear map, Jacobian, closed-form S, phi2: 130)."""
+    nb = (Np + 1) * (Np + 2) // 2
+    return 2 * nb * nb + 2 * (6 * Np + 4 * nb) + 130
+
+
+def spmv_bytes(n_rows, nb, vec_bytes, with_x0=True):
+    """Algorithmic bytes of one y = x0 + alpha B x: blocks (FP32) and row map
+    read once, x read once, x0 read once, y written once."""
+    return n_rows * (3 * nb * nb * 4 + 4 + nb * vec_bytes * (3 if with_x0 else 2))
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1608_04607_gb300 import dfm
+    from paper_1608_04607_gb300.inputs import workload
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl")
+    w = workload(args.workload)
+    m = w["mesh"]
+    Np = w["Np"]
+    tol = args.tol if args.tol else w["tol"]
+    mu = float(w["mu"][0])
+    rows = np.asarray(w["sources"], dtype=np.int64)
+    dfm.load()
+
+    mesh = dfm.Mesh(m.verts, m.tets, refl=w["refl"])
+    op = dfm.Operator(mesh, Np, mu=mu, precision=dfm.F32)
+    method = dfm.GMRES_IR
+
+    def step():
+        op.reassemble(mu)
+        rho0 = dfm.source(mesh, Np, rows)
+        rho, info = op.solve(rho0, method=method, tol=tol, restart=args.restart)
+        return rho, info
+
+    for _ in range(args.warmup):
+        rho, info = step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: device-resident steps --------------------------------
+    sampler = ClockSampler(local)
+    dfm.stats_reset()
+    dfm.stats_enable(True)
+    l0 = dfm.launch_count()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    infos = []
+    for _ in range(args.steps):
+        rho, info = step()
+        infos.append((info.iters, info.outer, info.resid))
+    e1.record()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    launches = dfm.launch_count() - l0
+    dfm.stats_enable(False)
+    elapsed_ms = e0.elapsed_time(e1)
+    kstats = {k: dfm.kernel_stats(k) for k in (dfm.KERNEL_ASSEMBLE, dfm.KERNEL_SPMV, dfm.KERNEL_SPMV64,
+                                                dfm.KERNEL_DOT, dfm.KERNEL_AXPY)}
+    nodes = dfm.op_nodes(op)
+    if ws > 1:
+        t = torch.tensor([elapsed_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+
+    # ---- e2e: C ABI from host buffers, copies inside the timed region --------
+    e2e = None
+    if not args.no_e2e:
+        host_rho = torch.empty((1, mesh.n_rows, op.nb), dtype=torch.float64, pin_memory=True)
+        verts = np.ascontiguousarray(m.verts)
+        tets = np.ascontiguousarray(m.tets)
+
+        def e2e_step():
+            mh = dfm.Mesh(verts, tets, refl=w["refl"])
+            o = dfm.Operator(mh, Np, mu=mu, precision=dfm.F32)
+            r0 = dfm.source(mh, Np, rows)
+            x, inf = o.solve(r0, method=method, tol=tol, restart=args.restart)
+            host_rho.copy_(x, non_blocking=True)
+            torch.cuda.synchronize()
+            o.close()
+            mh.close()
+            return inf
+
+        e2e_step()
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(max(1, args.steps)):
+            e2e_step()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if ws > 1:
+            t = torch.tensor([dt], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        h2d = verts.nbytes + tets.nbytes + 4 * m.n_tets * 8 + rows.nbytes
+        d2h = host_rho.numel() * 8
+        e2e = {"value": ws * max(1, args.steps) / dt, "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return
+
+    peaks, peak_src = _peaks()
+    nsm = torch.cuda.get_device_properties(local).multi_processor_count
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak_tflops = nsm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    hbm_peak = float(peaks.get("hbm_gbs", HBM_PEAK_FALLBACK))
+    nb = op.nb
+
+    kern = {}
+    n_asm, ms_asm = kstats[dfm.KERNEL_ASSEMBLE]
+    if n_asm:
+        fl = nodes * flops_per_node(Np)  # per launch (the last assembly; every launch is identical)
+        ach = fl / (ms_asm / n_asm * 1e-3) / 1e12
+        kern["assemble"] = {"bound": "alu", "launches": n_asm, "ms_per_launch": ms_asm / n_asm,
+                            "achieved": ach, "peak": fp32_peak_tflops, "unit": "TFLOP/s", "frac": ach / fp32_peak_tflops,
+                            "nodes_per_launch": nodes, "flops_per_node": flops_per_node(Np),
+                            "blocks_per_s": 12 * m.n_tets / (ms_asm / n_asm * 1e-3)}
+    n_sp, ms_sp = kstats[dfm.KERNEL_SPMV]
+    if n_sp:
+        by = spmv_bytes(mesh.n_rows, nb, 4)
+        ach = by / (ms_sp / n_sp * 1e-3) / 1e9
+        kern["spmv_f32"] = {"bound": "hbm", "launches": n_sp, "ms_per_launch": ms_sp / n_sp, "achieved": ach,
+                            "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak, "bytes_per_launch": by}
+    n_sp64, ms_sp64 = kstats[dfm.KERNEL_SPMV64]
+    if n_sp64:
+        by = spmv_bytes(mesh.n_rows, nb, 8)
+        ach = by / (ms_sp64 / n_sp64 * 1e-3) / 1e9
+        kern["spmv_f64vec"] = {"bound": "hbm", "launches": n_sp64, "ms_per_launch": ms_sp64 / n_sp64,
+                               "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+                               "bytes_per_launch": by}
+    for name, kid in (("dot", dfm.KERNEL_DOT), ("axpy", dfm.KERNEL_AXPY)):
+        n, ms = kstats[kid]
+        if n:
+            kern[name] = {"launches": n, "ms_total": ms}
+    total = {"assemble": ms_asm, "spmv_f32": ms_sp, "spmv_f64vec": ms_sp64,
+             "dot": kstats[dfm.KERNEL_DOT][1], "axpy": kstats[dfm.KERNEL_AXPY][1]}
+    dominant = max((k for k in ("assemble", "spmv_f32") if k in kern), key=lambda k: total[k])
+    d = kern[dominant]
+    roofline = {"bound": d["bound"], "achieved": round(d["achieved"], 3), "peak": round(d["peak"], 3),
+                "unit": d["unit"], "frac": round(d["frac"], 4), "traffic": None, "kernel": dominant,
+                "peak_source": peak_src if d["bound"] == "hbm" else
+                f"{nsm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz"}
+
+    iters = [i[0] for i in infos]
+    res = {
+        "metric": METRIC,
+        "value": ws * args.steps / (elapsed_ms * 1e-3),
+        "unit": "solves/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": elapsed_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 blocks/Krylov, f64 residual",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "desc": WORKLOAD_DESC if args.workload == WORKLOAD else args.workload,
+                   "n_tets": int(m.n_tets), "n_rows": int(mesh.n_rows), "nb": nb, "tol": tol,
+                   "restart": args.restart, "l2": "inputs larger than L2 (operator %.0f MB)" % (op.bytes / 1e6),
+                   "parallelism": f"replicas x{ws}"},
+        "roofline": roofline,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "assembly_blocks_per_s": kern.get("assemble", {}).get("blocks_per_s"),
+        "solve": {"operator_applications": iters[-1], "refinements": infos[-1][1], "resid": infos[-1][2]},
+        "kernels": {k: {kk: (round(vv, 5) if isinstance(vv, float) else vv) for kk, vv in v.items()}
+                    for k, v in kern.items()},
+        "kernel_ms_per_step": {k: round(v / args.steps, 4) for k, v in total.items()},
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        res["cpu_baseline"] = cpu_baseline(args.workload, op_apps=iters[-1], seconds=args.cpu_seconds)
+    print(json.dumps(res))
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (reported baseline and the reference arm)
+# ---------------------------------------------------------------------------
+
+def _oracle_sample(wname, seconds, op_apps=None):
+    """Time the FP64 oracle, as it stands, on a bounded sample of the workload:
+    (a) adaptive (1e-13) assembly of randomly drawn face pairs until about
+    `seconds`/2 of wall time, giving seconds per block; (b) restarted GMRES
+    iterations of the oracle at full size on an operator with the workload's
+    sparsity, giving seconds per operator application (block values do not
+    change the work).  Extrapolated solve time = (a) x 12 N + (b) x op_apps."""
+    import oracle
+    from paper_1608_04607_gb300.inputs import workload
+
+    w = workload(wname)
+    m = w["mesh"]
+    Np = w["Np"]
+    nb = (Np + 1) * (Np + 2) // 2
+    threads = os.cpu_count() or 1
+    topo = oracle.topology(m.tets)
+    t, f, fp = oracle.pair_list(m.n_tets)
+    rng = np.random.default_rng(0)
+    mu = w["mu"] if "mu" in w else np.full(m.n_tets, 0.05)
+    # (a) assembly sample, grown until the time budget is used
+    n_pairs = 0
+    t_asm = 0.0
+    batch = max(threads, 8)
+    while t_asm < 0.5 * seconds:
+        sel = rng.integers(0, t.size, size=batch)
+        t0 = time.perf_counter()
+        oracle.blocks_for_pairs(m.verts, m.tets, topo, mu, w["refl"], Np, t[sel], f[sel], fp[sel], rtol=1e-13)
+        t_asm += time.perf_counter() - t0
+        n_pairs += batch
+        batch *= 2
+    per_block = t_asm / n_pairs
+    # (b) oracle GMRES iterations at full size
+    blocks = rng.standard_normal((4 * m.n_tets, 3, nb, nb)) * (0.3 / nb)
+    dest = topo.recv[4 * np.repeat(np.arange(m.n_tets), 12) + fp].reshape(4 * m.n_tets, 3)
+    op = oracle.Operator(Np=Np, blocks=blocks, dest=dest)
+    rho0 = oracle.source_vector(m.verts, m.tets, w["sources"][:1], Np)
+    k = 16
+    t0 = time.perf_counter()
+    oracle.solve_gmres(op, rho0, tol=1e-300, restart=64, maxit=k)
+    per_app = (time.perf_counter() - t0) / k
+    if op_apps is None:
+        op_apps = 0
+    est = per_block * 12 * m.n_tets + per_app * op_apps
+    sample = (f"oracle assembly of {n_pairs} random face pairs (adaptive to 1e-13) and {k} oracle GMRES(64) "
+              f"iterations at full size; extrapolated to 12 x {m.n_tets} blocks + {op_apps} operator applications")
+    return est, sample, threads, per_block, per_app
+
+
+def cpu_baseline(wname, op_apps, seconds=20.0):
+    est, sample, threads, per_block, per_app = _oracle_sample(wname, seconds, op_apps)
+    return {"value": 1.0 / est, "unit": "solves/s", "cores": threads, "kind": "oracle", "sample": sample,
+            "s_per_block": per_block, "s_per_application": per_app}
+
+
+def run_reference(args):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return
+    # operator applications the oracle's GMRES-IR-equivalent solve needs: the
+    # oracle's own restarted GMRES iteration count on this workload, measured
+    # once on its sparsity pattern is not available without a full oracle
+    # assembly, so the reference arm uses the count of the same solver class
+    # recorded with the workload (FP64 GMRES(64) to 1e-8).
+    apps = args.ref_apps
+    vals = []
+    last = None
+    for i in range(args.warmup + args.steps):
+        est, sample, threads, _, _ = _oracle_sample(args.workload, args.cpu_seconds / 2, apps)
+        if i >= args.warmup:
+            vals.append(est)
+        last = (sample, threads)
+    v = 1.0 / statistics.mean(vals)
+    res = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(vals) * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": args.workload, "desc": WORKLOAD_DESC if args.workload == WORKLOAD else args.workload},
+           "cpu_baseline": {"value": v, "unit": "solves/s", "cores": last[1], "kind": "oracle", "sample": last[0]},
+           "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(res))
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--tol", type=float, default=0.0)
+    ap.add_argument("--restart", type=int, default=64)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--ref-apps", type=int, default=600)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -193,6 +193,7 @@ int dfm_solve(const dfm_op* op, const double* rho0, int R, double* rho, const df
 #define DFM_KERNEL_SPMV_T 2   /* y = x0 + alpha B^T x */
 #define DFM_KERNEL_DOT 3      /* Krylov multi-dot */
 #define DFM_KERNEL_AXPY 4     /* Krylov multi-axpy */
+#define DFM_KERNEL_SPMV64 5   /* y = x0 + alpha B x with FP64 vectors (residuals) */
 long long dfm_launch_count(void);
 int dfm_stats_enable(int on);
 int dfm_stats_reset(void);

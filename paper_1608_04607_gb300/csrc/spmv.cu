@@ -127,7 +127,7 @@ int launch(const dfm_op* op, const TX* x, const TX* x0, TX* y, int R, double alp
     const int64_t ntiles = (op->nrows + rpt - 1) / rpt;
     const int64_t grid = std::min<int64_t>(ntiles, (int64_t)nsm * per_sm);
     {
-      ::dfm::KernelTimer timer_(DFM_KERNEL_SPMV, st);
+      ::dfm::KernelTimer timer_(sizeof(TX) == 8 ? DFM_KERNEL_SPMV64 : DFM_KERNEL_SPMV, st);
       spmv_kernel<TV, TX, TA><<<(unsigned)grid, kThreads, smem, st>>>(vals, op->row_stride, recv, op->nrows, op->nb,
                                                                       rpt, x, x0, y, R, (TA)alpha);
     }

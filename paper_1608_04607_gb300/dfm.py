@@ -289,7 +289,7 @@ def gauss_legendre(q: int):
     return x, w
 
 
-KERNEL_ASSEMBLE, KERNEL_SPMV, KERNEL_SPMV_T, KERNEL_DOT, KERNEL_AXPY = 0, 1, 2, 3, 4
+KERNEL_ASSEMBLE, KERNEL_SPMV, KERNEL_SPMV_T, KERNEL_DOT, KERNEL_AXPY, KERNEL_SPMV64 = 0, 1, 2, 3, 4, 5
 
 
 def launch_count() -> int:
