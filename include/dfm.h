@@ -164,6 +164,7 @@ typedef struct {
   int restart;       /* GMRES restart length (0 = 64) */
   int use_x0;        /* 1: rho holds the initial guess on entry */
   double inner_tol;  /* GMRES_IR: inner FP32 relative tolerance (0 = 1e-4) */
+  int transpose;     /* 1: solve (I - B)^T x = rho0 instead (the adjoint equation) */
 } dfm_solve_opts;
 
 typedef struct {
@@ -180,6 +181,37 @@ typedef struct {
 int dfm_solve(const dfm_op* op, const double* rho0, int R, double* rho, const dfm_solve_opts* opts, void* stream,
               dfm_solve_info* info);
 
+/* Interior density functional (Sec. 4.1, Eq. IntDens, c = 1): for each listed
+ * tet e, the coefficients g_e of
+ *   rho_T(r_e) = sum_{l, nm} rho_(e,l,nm) g_e[l][nm],
+ *   g_e[l][nm] = |T_l|^{-1/2} Int_{T_l} Z_nm(p(s->r_e)) cos(vartheta) exp(-mu_e |r_e - s|) / |r_e - s|^2 ds,
+ * at r_e = the tet's centroid, p(s->r) the tangential part of unit(r - s) in
+ * face l's frame, and dg_e = d g_e / d mu_e.  Each face integral uses a
+ * collapsed tensor Gauss-Legendre rule of order nq (0 = 16) in FP64.
+ *   tets_host: HOST int64 [n] tet ids; weights_host: HOST FP64 [n] or NULL (1).
+ *   gvec, dgvec: device FP64 [rows][nb]; on return gvec[4e+l] += w_e g_e[l] and
+ *   dgvec[4e+l] += w_e dg_e[l] for the listed tets (other rows untouched), so
+ *   J(rho) = gvec . rho and dJ/dmu_e (explicit part) = dgvec[4e..4e+3] . rho[4e..4e+3].
+ *   mu: device FP64 [n_tets] or NULL for mu_uniform.  Asynchronous. */
+int dfm_interior_density(const dfm_mesh* mesh, int Np, const double* mu, double mu_uniform, const int64_t* tets_host,
+                         const double* weights_host, int n, int nq, double* gvec, double* dgvec, void* stream);
+
+/* Adjoint gradient of J = sum_r gvec . rho_r with respect to the per-tet damping
+ * (the operator's dependence on mu through exp(-mu L), Sec. 2 and Sec. 3.3):
+ *   (I - B)^T lambda = gvec  (solved with opts, transpose forced on),
+ *   dJ_dmu[r][t] = sum over the 12 face pairs of tet t of lambda_R^T (dB/dmu_t) rho_r,J
+ *                  + dgvec[4t..4t+3] . rho_r[4t..4t+3]   (if dgvec != NULL),
+ * with dB/dmu from the same quadrature as the assembly and
+ * d/dmu [2 A phi2(mu L_O)] = 2 A L_O phi2'(mu L_O); dB/dmu is never stored.
+ *   params: the damping the operator was assembled with (mu, Np, quadrature).
+ *   rho: device FP64 [R][rows][nb]; gvec, dgvec: device FP64 [rows][nb] (one
+ *   functional shared by all R right-hand sides, so one adjoint solve serves all);
+ *   lambda_out: device FP64 [rows][nb]; dJ_dmu: device FP64 [R][n_tets] (overwritten).
+ * Synchronises like dfm_solve.  Errors as dfm_solve. */
+int dfm_adjoint(const dfm_op* op, const dfm_params* params, const double* rho, int R, const double* gvec,
+                const double* dgvec, double* lambda_out, double* dJ_dmu, const dfm_solve_opts* opts, void* stream,
+                dfm_solve_info* info);
+
 /* Kernel accounting, for benchmarks and profiling.
  *   dfm_launch_count: number of CUDA kernels this library has launched in the
  *     process so far (all kernels, all streams).
@@ -194,6 +226,7 @@ int dfm_solve(const dfm_op* op, const double* rho0, int R, double* rho, const df
 #define DFM_KERNEL_DOT 3      /* Krylov multi-dot */
 #define DFM_KERNEL_AXPY 4     /* Krylov multi-axpy */
 #define DFM_KERNEL_SPMV64 5   /* y = x0 + alpha B x with FP64 vectors (residuals) */
+#define DFM_KERNEL_CONTRACT 6 /* fused lambda^T (dB/dmu) rho per tet */
 long long dfm_launch_count(void);
 int dfm_stats_enable(int on);
 int dfm_stats_reset(void);

@@ -169,7 +169,8 @@ struct Ctx {
   const dfm_op* op;
   cudaStream_t st;
   int nsm;
-  int64_t n;  // rows * nb
+  int64_t n;      // rows * nb
+  int trans = 0;  // 1: the operator is applied transposed (adjoint solves)
 };
 
 inline unsigned grid_for(int64_t n, int nsm) {
@@ -269,7 +270,7 @@ int gmres(const Ctx& c, const T* b, T* x, double tol, int m, int max_iter, int* 
     axpby_kernel<T><<<grid_for(n, c.nsm), 256, 0, c.st>>>(tmp, T(1), b, T(-1), x, n);
     DFM_LAUNCHED();
     DFM_CUDA_CHECK(cudaGetLastError());
-    rc = apply_impl(c.op, x, tmp, V, 1, 1.0, 0, xtype, c.st);
+    rc = apply_impl(c.op, x, tmp, V, 1, 1.0, c.trans, xtype, c.st);
     if (rc) return rc;
     ++*iters;
     double beta;
@@ -289,7 +290,7 @@ int gmres(const Ctx& c, const T* b, T* x, double tol, int m, int max_iter, int* 
       T* vj = V + (int64_t)j * n;
       T* w = V + (int64_t)(j + 1) * n;
       // w = v_j - B v_j
-      rc = apply_impl(c.op, vj, vj, w, 1, -1.0, 0, xtype, c.st);
+      rc = apply_impl(c.op, vj, vj, w, 1, -1.0, c.trans, xtype, c.st);
       if (rc) return rc;
       ++*iters;
       // classical Gram-Schmidt: h = V^T w (plus |w|^2 as the last entry)
@@ -355,7 +356,7 @@ int residual64(const Ctx& c, const double* rho0, const double* x, double* r, dou
   DFM_CUDA_CHECK(cudaGetLastError());
   // r = (rho0 - x) + B x, written to a second half of r
   double* r2 = r + c.n;
-  int rc = apply_impl(c.op, x, r, r2, 1, 1.0, 0, DFM_F64, c.st);
+  int rc = apply_impl(c.op, x, r, r2, 1, 1.0, c.trans, DFM_F64, c.st);
   if (rc) return rc;
   double rn, bn;
   rc = norm2<double>(c, r2, partial, red_dev, &rn);
@@ -404,6 +405,7 @@ extern "C" int dfm_solve(const dfm_op* op, const double* rho0, int R, double* rh
   c.op = op;
   c.st = as_stream(stream);
   c.n = op->nrows * op->nb;
+  c.trans = opts->transpose ? 1 : 0;
   int dev = 0;
   DFM_CUDA_CHECK(cudaGetDevice(&dev));
   DFM_CUDA_CHECK(cudaDeviceGetAttribute(&c.nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -445,7 +447,7 @@ extern "C" int dfm_solve(const dfm_op* op, const double* rho0, int R, double* rh
       std::vector<double> ph(2 * kRedBlocks);
       while (true) {
         DFM_CUDA_CHECK(cudaMemcpyAsync(xold, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, c.st));
-        rs = apply_impl(op, xold, b, x, 1, 1.0, 0, DFM_F64, c.st);
+        rs = apply_impl(op, xold, b, x, 1, 1.0, c.trans, DFM_F64, c.st);
         if (rs) return rs;
         ++iters;
         diff_norm_kernel<<<kRedBlocks, kRedThreads, 0, c.st>>>(x, xold, n, part64);
