@@ -25,6 +25,7 @@ namespace {
 constexpr int kRedBlocks = 512;  // partial-sum blocks of the reductions
 constexpr int kRedThreads = 256;
 constexpr int kDotChunk = 8;     // dot products per pass over the vector
+constexpr int kMaxKrylov = 256;  // largest GMRES restart length
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
@@ -90,13 +91,22 @@ __global__ void __launch_bounds__(kRedThreads)
 multi_axpy_kernel(const T* __restrict__ V, int64_t ld, int k, const T* __restrict__ h, T coef_sign, T* w, int64_t n,
                   T* __restrict__ partial) {
   __shared__ T sh[32];
-  __shared__ T hs[128];
-  for (int j = threadIdx.x; j < k && j < 128; j += blockDim.x) hs[j] = coef_sign * h[j];
+  __shared__ T hs[kMaxKrylov + 8];
+  for (int j = threadIdx.x; j < k && j < kMaxKrylov + 8; j += blockDim.x) hs[j] = coef_sign * h[j];
   __syncthreads();
   T sq = T(0);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    T v = w[i];
-    for (int j = 0; j < k; ++j) v = fma(hs[j], V[(int64_t)j * ld + i], v);
+    // four independent chains keep several loads in flight per thread
+    T v0 = w[i], v1 = T(0), v2 = T(0), v3 = T(0);
+    int j = 0;
+    for (; j + 4 <= k; j += 4) {
+      v0 = fma(hs[j], V[(int64_t)j * ld + i], v0);
+      v1 = fma(hs[j + 1], V[(int64_t)(j + 1) * ld + i], v1);
+      v2 = fma(hs[j + 2], V[(int64_t)(j + 2) * ld + i], v2);
+      v3 = fma(hs[j + 3], V[(int64_t)(j + 3) * ld + i], v3);
+    }
+    for (; j < k; ++j) v0 = fma(hs[j], V[(int64_t)j * ld + i], v0);
+    const T v = (v0 + v1) + (v2 + v3);
     w[i] = v;
     sq = fma(v, v, sq);
   }
@@ -245,15 +255,21 @@ int ensure_work(const dfm_op* cop, int64_t bytes) {
   return DFM_OK;
 }
 
-// GMRES(m) on (I - B) x = b in precision T (operator applied as TV with TX = T).
-// x holds the initial guess.  tol is relative to |b|.  Counts operator
-// applications in *iters (incremented); stops at max_iter.  *est returns the
-// final true relative residual in precision T.
+// GMRES(m) on (I - B) x = b in precision T (operator applied as TV with TX = T),
+// right-preconditioned by the Neumann polynomial p(B) = sum_{k<d} B^k:
+//   (I - B) p(B) = I - B^d,  so the Arnoldi process runs on I - B^d and the
+//   update is x += p(B) (V y), p(B) z evaluated by Horner (s <- z + B s).
+// The polynomial shrinks the Krylov dimension about d-fold for a modest
+// increase in operator applications, which keeps the quadratic Gram-Schmidt
+// cost small.  x holds the initial guess; tol is relative to |b|; operator
+// applications are added to *iters, capped by max_iter.  *est returns the
+// last relative residual estimate.  t1, t2: scratch vectors of length n.
 template <typename T>
-int gmres(const Ctx& c, const T* b, T* x, double tol, int m, int max_iter, int* iters, double* est, T* V, T* tmp,
-          T* h_dev, T* partial, T* red_dev) {
+int gmres(const Ctx& c, const T* b, T* x, double tol, int m, int d, int max_iter, int* iters, double* est, T* V,
+          T* tmp, T* t1, T* t2, T* h_dev, T* partial, T* red_dev) {
   const int64_t n = c.n;
   const int xtype = sizeof(T) == 8 ? DFM_F64 : DFM_F32;
+  if (d < 1) d = 1;
   std::vector<T> hh(m + 2);
   std::vector<double> H((m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
   double bnorm;
@@ -265,6 +281,18 @@ int gmres(const Ctx& c, const T* b, T* x, double tol, int m, int max_iter, int* 
     *est = 0.0;
     return DFM_OK;
   }
+  // w = v - B^d v  (d operator applications, ping-pong through t1/t2)
+  auto apply_poly_op = [&](const T* v, T* w) -> int {
+    const T* src = v;
+    for (int k = 1; k < d; ++k) {
+      T* dst = (k & 1) ? t1 : t2;
+      int r = apply_impl(c.op, src, nullptr, dst, 1, 1.0, c.trans, xtype, c.st);
+      if (r) return r;
+      src = dst;
+    }
+    *iters += d;
+    return apply_impl(c.op, src, v, w, 1, -1.0, c.trans, xtype, c.st);
+  };
   while (true) {
     // r = b - (I - B) x = (b - x) + B x   -> V[0]
     axpby_kernel<T><<<grid_for(n, c.nsm), 256, 0, c.st>>>(tmp, T(1), b, T(-1), x, n);
@@ -289,10 +317,8 @@ int gmres(const Ctx& c, const T* b, T* x, double tol, int m, int max_iter, int* 
     for (int j = 0; j < m; ++j) {
       T* vj = V + (int64_t)j * n;
       T* w = V + (int64_t)(j + 1) * n;
-      // w = v_j - B v_j
-      rc = apply_impl(c.op, vj, vj, w, 1, -1.0, c.trans, xtype, c.st);
+      rc = apply_poly_op(vj, w);
       if (rc) return rc;
-      ++*iters;
       // classical Gram-Schmidt: h = V^T w (plus |w|^2 as the last entry)
       rc = dots<T>(c, V, n, j + 2, w, partial, h_dev, hh.data());
       if (rc) return rc;
@@ -329,9 +355,10 @@ int gmres(const Ctx& c, const T* b, T* x, double tol, int m, int max_iter, int* 
       g[j + 1] = -sn[j] * g[j];
       g[j] = cs[j] * g[j];
       kdone = j + 1;
-      if (fabs(g[j + 1]) <= 0.5 * tol * bnorm || *iters >= max_iter || hn == 0.0) break;
+      *est = fabs(g[j + 1]) / bnorm;
+      if (fabs(g[j + 1]) <= 0.5 * tol * bnorm || *iters + d >= max_iter || hn == 0.0) break;
     }
-    // y = H^{-1} g (upper triangular), x += V y
+    // y = H^{-1} g (upper triangular); z = V y; x += p(B) z
     for (int i = kdone - 1; i >= 0; --i) {
       double s = g[i];
       for (int k = i + 1; k < kdone; ++k) s -= H[i * m + k] * y[k];
@@ -339,10 +366,22 @@ int gmres(const Ctx& c, const T* b, T* x, double tol, int m, int max_iter, int* 
     }
     for (int i = 0; i < kdone; ++i) hh[i] = (T)y[i];
     DFM_CUDA_CHECK(cudaMemcpyAsync(h_dev, hh.data(), sizeof(T) * kdone, cudaMemcpyHostToDevice, c.st));
+    DFM_CUDA_CHECK(cudaMemsetAsync(tmp, 0, sizeof(T) * n, c.st));
     {
       ::dfm::KernelTimer timer_(DFM_KERNEL_AXPY, c.st);
-      multi_axpy_kernel<T><<<kRedBlocks, kRedThreads, 0, c.st>>>(V, n, kdone, h_dev, T(1), x, n, nullptr);
+      multi_axpy_kernel<T><<<kRedBlocks, kRedThreads, 0, c.st>>>(V, n, kdone, h_dev, T(1), tmp, n, nullptr);
     }
+    DFM_LAUNCHED();
+    DFM_CUDA_CHECK(cudaGetLastError());
+    const T* s_src = tmp;
+    for (int k = 1; k < d; ++k) {  // Horner: s <- z + B s
+      T* dst = (k & 1) ? t1 : t2;
+      rc = apply_impl(c.op, s_src, tmp, dst, 1, 1.0, c.trans, xtype, c.st);
+      if (rc) return rc;
+      s_src = dst;
+    }
+    *iters += d - 1;
+    axpby_kernel<T><<<grid_for(n, c.nsm), 256, 0, c.st>>>(x, T(1), x, T(1), s_src, n);
     DFM_LAUNCHED();
     DFM_CUDA_CHECK(cudaGetLastError());
   }
@@ -399,8 +438,9 @@ extern "C" int dfm_solve(const dfm_op* op, const double* rho0, int R, double* rh
   if (!(opts->tol > 0)) return set_error(DFM_ERR_ARG, "dfm_solve: tol must be > 0");
   const int method = opts->method;
   const int max_iter = opts->max_iter > 0 ? opts->max_iter : 20000;
-  const int m = opts->restart > 0 ? std::min(opts->restart, 120) : 64;
-  const double inner_tol = opts->inner_tol > 0 ? opts->inner_tol : 1e-4;
+  const int m = opts->restart > 0 ? std::min(opts->restart, kMaxKrylov) : 128;
+  const double inner_tol = opts->inner_tol > 0 ? opts->inner_tol : 1e-6;
+  const int poly = opts->poly_degree > 0 ? std::min(opts->poly_degree, 64) : 16;
   Ctx c;
   c.op = op;
   c.st = as_stream(stream);
@@ -420,17 +460,17 @@ extern "C" int dfm_solve(const dfm_op* op, const double* rho0, int R, double* rh
   const int64_t es = inner64 ? 8 : 4;
   int64_t bytes = 0;
   bytes += 4 * n * 8 + 4096;                            // r (2n), tmp64 (n), xold (n)
-  const int64_t inner_bytes = (int64_t)(m + 5) * n * es + 8 * 256;  // V (m+1), tmp, b, x inner (+ alignment)
+  const int64_t inner_bytes = (int64_t)(m + 7) * n * es + 8 * 256;  // V (m+1), tmp, t1, t2, b, x (+ alignment)
   bytes += inner_bytes + 4096;
-  bytes += (kRedBlocks * 130 + 256) * 8 + 4096;         // partials, h, red
+  bytes += ((int64_t)kRedBlocks * (kMaxKrylov + 8) + 2 * (kMaxKrylov + 8) + 256) * 8 + 4096;  // partials, h, red
   int rc = ensure_work(op, bytes + 8 * 256);
   if (rc) return rc;
   Work W{reinterpret_cast<char*>(op->swork)};
   double* r64 = W.take<double>(2 * n);
   double* tmp64 = W.take<double>(n);
   double* xold = W.take<double>(n);
-  double* part64 = W.take<double>(kRedBlocks * 130);
-  double* h64 = W.take<double>(130);
+  double* part64 = W.take<double>((int64_t)kRedBlocks * (kMaxKrylov + 8));
+  double* h64 = W.take<double>(2 * (kMaxKrylov + 8));
   double* red64 = W.take<double>(8);
   char* inner_base = W.take<char>(inner_bytes);
   dfm_solve_info acc_info{0, 0, 0.0};
@@ -478,8 +518,11 @@ extern "C" int dfm_solve(const dfm_op* op, const double* rho0, int R, double* rh
       Work Wi{inner_base};
       double* V = Wi.take<double>((int64_t)(m + 1) * n);
       double* tmp = Wi.take<double>(n);
+      double* t1 = Wi.take<double>(n);
+      double* t2 = Wi.take<double>(n);
       double est = 0;
-      rs = gmres<double>(c, b, x, opts->tol, m, max_iter, &iters, &est, V, tmp, h64, part64, red64);
+      rs = gmres<double>(c, b, x, opts->tol, m, opts->poly_degree > 0 ? poly : 1, max_iter, &iters, &est, V, tmp,
+                         t1, t2, h64, part64, red64);
       if (rs == DFM_ERR_NOT_CONVERGED) set_error(rs, "dfm_solve: GMRES reached max_iter");
       if (rs == DFM_OK || rs == DFM_ERR_NOT_CONVERGED) {
         int r2 = residual64(c, b, x, r64, part64, red64, &resid, &rabs);
@@ -490,6 +533,8 @@ extern "C" int dfm_solve(const dfm_op* op, const double* rho0, int R, double* rh
       Work Wi{inner_base};
       float* V = Wi.take<float>((int64_t)(m + 1) * n);
       float* tmp = Wi.take<float>(n);
+      float* t1 = Wi.take<float>(n);
+      float* t2 = Wi.take<float>(n);
       float* bf = Wi.take<float>(n);
       float* xf = Wi.take<float>(n);
       float* part32 = reinterpret_cast<float*>(part64);
@@ -513,8 +558,12 @@ extern "C" int dfm_solve(const dfm_op* op, const double* rho0, int R, double* rh
         DFM_CUDA_CHECK(cudaGetLastError());
         DFM_CUDA_CHECK(cudaMemsetAsync(xf, 0, sizeof(float) * n, c.st));
         double est = 0;
-        const double itol = method == DFM_SOLVE_GMRES_IR ? inner_tol : std::max(opts->tol, 1e-6);
-        int gi = gmres<float>(c, bf, xf, itol, m, max_iter, &iters, &est, V, tmp, h32, part32, red32);
+        // inner tolerance: what this refinement step still has to gain, floored
+        // at what FP32 Krylov vectors can deliver
+        const double need = opts->tol / std::max(resid, 1e-300);
+        const double itol = method == DFM_SOLVE_GMRES_IR ? std::max(inner_tol, 0.3 * need)
+                                                         : std::max(opts->tol, 1e-6);
+        int gi = gmres<float>(c, bf, xf, itol, m, poly, max_iter, &iters, &est, V, tmp, t1, t2, h32, part32, red32);
         if (gi != DFM_OK && gi != DFM_ERR_NOT_CONVERGED) return gi;
         add_f32_kernel<<<grid_for(n, c.nsm), 256, 0, c.st>>>(x, xf, rabs, n);
         DFM_LAUNCHED();

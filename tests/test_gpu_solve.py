@@ -133,3 +133,25 @@ def test_solver_reports_nonconvergence(D):
     rho, info = op.solve(rho0, method=D.GMRES_IR if op.precision == D.F32 else D.GMRES, tol=1e-14, max_iter=3,
                          raise_on_nonconvergence=False)
     assert info.iters <= 4
+
+
+@pytest.mark.parametrize("poly", [1, 4, 16])
+def test_polynomial_preconditioning_and_transpose(D, oracle_mod, poly):
+    """GMRES-IR with the Neumann-polynomial right preconditioner of degree d,
+    forward and transposed (adjoint) systems, against LU on the same operator."""
+    m = kuhn_cube_mesh(3, jitter=0.2, seed=9)
+    Np = 2
+    mesh = D.Mesh(m.verts, m.tets, refl=0.95)
+    op = D.Operator(mesh, Np, mu=0.05, precision=D.F32)
+    same = _gpu_op_as_oracle(oracle_mod, op, mesh, m.n_tets, Np)
+    M = np.eye(same.nrows * same.nb) - oracle_mod.dense(same)
+    rng = np.random.default_rng(poly)
+    import torch
+
+    b = torch.tensor(rng.standard_normal((1, mesh.n_rows, op.nb)), device="cuda")
+    for trans in (False, True):
+        x, info = op.solve(b, method=D.GMRES_IR, tol=1e-10, poly_degree=poly, transpose=trans)
+        ref = np.linalg.solve(M.T if trans else M, b[0].cpu().numpy().ravel())
+        got = x[0].cpu().numpy().ravel()
+        assert np.linalg.norm(got - ref) <= 1e-8 * np.linalg.norm(ref)
+        assert info.resid <= 1e-10
