@@ -248,7 +248,7 @@ def run_gpu(args):
                             "blocks_per_s": 12 * m.n_tets / (ms_asm / n_asm * 1e-3)}
     n_sp, ms_sp = kstats[dfm.KERNEL_SPMV]
     if n_sp:
-        by = spmv_bytes(mesh.n_rows, nb, 4)
+        by = spmv_bytes(mesh.n_rows, nb, 4, with_x0=False)  # most launches are polynomial hops without x0
         ach = by / (ms_sp / n_sp * 1e-3) / 1e9
         kern["spmv_f32"] = {"bound": "hbm", "launches": n_sp, "ms_per_launch": ms_sp / n_sp, "achieved": ach,
                             "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak, "bytes_per_launch": by}
