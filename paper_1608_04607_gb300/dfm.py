@@ -80,6 +80,9 @@ SIGNATURES = {
     "dfm_apply": (_i, [_vp, _vp, _vp, _vp, _i, _d, _i, _i, _vp]),
     "dfm_source": (_i, [_vp, _i, _vp, _i, _vp, _vp]),
     "dfm_solve": (_i, [_vp, _vp, _i, _vp, ctypes.POINTER(SolveOpts), _vp, ctypes.POINTER(SolveInfo)]),
+    "dfm_interior_density": (_i, [_vp, _i, _vp, _d, _vp, _vp, _i, _i, _vp, _vp, _vp]),
+    "dfm_adjoint": (_i, [_vp, ctypes.POINTER(Params), _vp, _i, _vp, _vp, _vp, _vp, ctypes.POINTER(SolveOpts), _vp,
+                         ctypes.POINTER(SolveInfo)]),
     "dfm_launch_count": (ctypes.c_longlong, []),
     "dfm_stats_enable": (_i, [_i]),
     "dfm_stats_reset": (_i, []),
@@ -187,6 +190,7 @@ class Operator:
         self.mesh = mesh
         self._keep = []
         p = self._params(Np, mu, precision, quad_order, max_patch_deg)
+        self._p = p
         h = ctypes.c_void_p()
         _check(_lib.dfm_assemble(mesh.handle, ctypes.byref(p), _stream(), ctypes.byref(h)), "dfm_assemble")
         self._h = h
@@ -216,6 +220,7 @@ class Operator:
 
     def reassemble(self, mu, quad_order=0, max_patch_deg=0.0):
         p = self._params(self.Np, mu, self.precision, quad_order, max_patch_deg)
+        self._p = p
         _check(_lib.dfm_assemble_into(self.mesh.handle, ctypes.byref(p), self._h, _stream()), "dfm_assemble_into")
 
     @property
@@ -256,6 +261,21 @@ class Operator:
         _check(rc, "dfm_solve")
         return rho, info
 
+    def adjoint(self, rho, gvec, dgvec=None, method=GMRES_IR, tol=1e-8, max_iter=0, restart=0, inner_tol=0.0,
+                poly_degree=0):
+        """lambda = (I - B)^{-T} gvec and dJ/dmu for J = sum_r gvec . rho_r (dfm_adjoint).
+        rho: FP64 [R, rows, nb]; gvec/dgvec: FP64 [rows, nb].  Returns (lambda, dJ_dmu [R, n_tets], info)."""
+        torch = self._torch
+        R = 1 if rho.dim() == 2 else rho.shape[0]
+        lam = torch.empty((self.n_rows, self.nb), dtype=torch.float64, device="cuda")
+        dj = torch.empty((R, self.mesh.n_tets), dtype=torch.float64, device="cuda")
+        o = SolveOpts(method=method, tol=tol, max_iter=max_iter, restart=restart, use_x0=0, inner_tol=inner_tol,
+                      transpose=1, poly_degree=poly_degree)
+        info = SolveInfo()
+        _check(_lib.dfm_adjoint(self._h, ctypes.byref(self._p), _ptr(rho), R, _ptr(gvec), _ptr(dgvec), _ptr(lam),
+                                _ptr(dj), ctypes.byref(o), _stream(), ctypes.byref(info)), "dfm_adjoint")
+        return lam, dj, info
+
     def close(self):
         if getattr(self, "_h", None):
             _lib.dfm_op_destroy(self._h)
@@ -279,6 +299,73 @@ def source(mesh: Mesh, Np: int, rows):
     return out
 
 
+def interior_density(mesh: Mesh, Np: int, tets, weights=None, mu=0.0, nq=0, gvec=None, dgvec=None):
+    """Interior density coefficients at tet centroids (dfm_interior_density):
+    adds w_e g_e into gvec and w_e dg_e/dmu_e into dgvec (FP64 [rows, nb], created
+    zeroed when not given).  J(rho) = (gvec * rho).sum()."""
+    import torch
+
+    nb = nbasis(Np)
+    tets = np.ascontiguousarray(np.atleast_1d(tets), dtype=np.int64)
+    if gvec is None:
+        gvec = torch.zeros((mesh.n_rows, nb), dtype=torch.float64, device="cuda")
+    if dgvec is None:
+        dgvec = torch.zeros((mesh.n_rows, nb), dtype=torch.float64, device="cuda")
+    wp = None
+    if weights is not None:
+        w = np.ascontiguousarray(np.broadcast_to(np.asarray(weights, dtype=np.float64), tets.shape))
+        wp = w.ctypes.data_as(ctypes.c_void_p)
+    keep = None
+    if isinstance(mu, torch.Tensor):
+        keep = mu.to(device="cuda", dtype=torch.float64).contiguous()
+        mup, muu = _ptr(keep), 0.0
+    else:
+        mup, muu = None, float(mu)
+    _check(load().dfm_interior_density(mesh.handle, Np, mup, muu, tets.ctypes.data_as(ctypes.c_void_p), wp,
+                                       tets.size, nq, _ptr(gvec), _ptr(dgvec), _stream()), "dfm_interior_density")
+    return gvec, dgvec
+
+
+class DFMSolve:
+    """rho = (I - B(mu))^{-1} rho0 as a torch.autograd.Function of the per-tet
+    damping mu: forward = dfm_assemble + dfm_solve, backward = dfm_adjoint
+    (grad_mu = lambda^T dB/dmu rho, grad_rho0 = lambda).  The functional's own
+    explicit mu-dependence is added by ReceiverFunctional."""
+
+    @staticmethod
+    def apply(mesh, Np, mu, rho0, tol=1e-8, **solve_kw):
+        import torch
+
+        class _Fn(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, mu_t, rho0_t):
+                op = Operator(mesh, Np, mu=mu_t.detach(), precision=F32)
+                rho, _ = op.solve(rho0_t.detach().contiguous(), tol=tol, **solve_kw)
+                ctx.op = op
+                ctx.save_for_backward(rho)
+                return rho
+
+            @staticmethod
+            def backward(ctx, grad_rho):
+                (rho,) = ctx.saved_tensors
+                op = ctx.op
+                g = grad_rho.contiguous()
+                R = 1 if rho.dim() == 2 else rho.shape[0]
+                gsum = g if g.dim() == 2 else g
+                if gsum.dim() == 3 and gsum.shape[0] > 1:
+                    # one adjoint solve per distinct functional
+                    grads, lams = [], []
+                    for r in range(gsum.shape[0]):
+                        lam, dj, _ = op.adjoint(rho[r:r + 1], gsum[r], tol=tol)
+                        grads.append(dj[0])
+                        lams.append(lam)
+                    return torch.stack(grads).sum(0), torch.stack(lams)
+                lam, dj, _ = op.adjoint(rho, gsum.reshape(op.n_rows, op.nb), tol=tol)
+                return dj.sum(0), lam.reshape(rho0.shape)
+
+        return _Fn.apply(mu, rho0)
+
+
 def gauss_legendre(q: int):
     """Gauss-Legendre nodes/weights computed on the device (dfm_gauss_legendre)."""
     import torch
@@ -290,7 +377,7 @@ def gauss_legendre(q: int):
     return x, w
 
 
-KERNEL_ASSEMBLE, KERNEL_SPMV, KERNEL_SPMV_T, KERNEL_DOT, KERNEL_AXPY, KERNEL_SPMV64 = 0, 1, 2, 3, 4, 5
+KERNEL_ASSEMBLE, KERNEL_SPMV, KERNEL_SPMV_T, KERNEL_DOT, KERNEL_AXPY, KERNEL_SPMV64, KERNEL_CONTRACT = range(7)
 
 
 def launch_count() -> int:
