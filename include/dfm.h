@@ -103,6 +103,28 @@ int dfm_mesh_info(const dfm_mesh* mesh, dfm_mesh_info_t* info);
  * 4t+f itself on the boundary).  Blocks until copied. */
 int dfm_mesh_recv(const dfm_mesh* mesh, int32_t* recv_host);
 
+/* Face matching (the recv map of dfm_mesh_recv) WITHOUT ANY DEVICE ALLOCATION.
+ * The paper has no counterpart: this is a library service for callers that
+ * cannot call cudaMalloc -- applications that hand all device memory to their
+ * own pool or arena up front (an untracked allocation would fail or fragment
+ * it) and code that must not enter the CUDA allocator where it runs.
+ *   tets:  device int32 [n_tets][4] (caller-owned input);
+ *   recv:  device int32 [4 n_tets] (caller-owned output), same meaning as
+ *          dfm_mesh_recv;
+ *   n_boundary: host int64, receives the number of boundary rows (or NULL).
+ * The hash table lives in a fixed file-scope __device__ array of 2^20 slots
+ * (16 MiB), present on every GPU that loads the library until the process
+ * exits; meshes above 131,072 tets (or 2^21 - 1 vertices) are rejected with
+ * DFM_ERR_ARG.  The first call on a device looks up the array's device
+ * address there (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  Every call shares the array and re-initialises it, so calls
+ * whose work overlaps on the GPU (other streams or host threads on the same
+ * device) race and must be serialised by the caller.  Waits on the stream to
+ * read back the error flags and the boundary count.  Errors: DFM_ERR_ARG,
+ * DFM_ERR_MESH (as dfm_mesh_create), DFM_ERR_CUDA. */
+int dfm_face_match_static(const int32_t* tets, int64_t n_verts, int64_t n_tets, int32_t* recv, int64_t* n_boundary,
+                          void* stream);
+
 /* Gauss-Legendre nodes and weights on [-1, 1] (the per-patch direction rule,
  * Sec. 3.4), computed on the device in FP64 by Newton iteration on the
  * Legendre three-term recurrence.  x, w: device FP64 [q], 1 <= q <= 64. */

@@ -71,6 +71,7 @@ SIGNATURES = {
     "dfm_mesh_destroy": (None, [_vp]),
     "dfm_mesh_info": (_i, [_vp, ctypes.POINTER(MeshInfo)]),
     "dfm_mesh_recv": (_i, [_vp, _vp]),
+    "dfm_face_match_static": (_i, [_vp, _i64, _i64, _vp, ctypes.POINTER(ctypes.c_int64), _vp]),
     "dfm_gauss_legendre": (_i, [_i, _vp, _vp, _vp]),
     "dfm_assemble": (_i, [_vp, ctypes.POINTER(Params), _vp, ctypes.POINTER(_vp)]),
     "dfm_assemble_into": (_i, [_vp, ctypes.POINTER(Params), _vp, _vp]),
