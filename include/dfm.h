@@ -211,7 +211,7 @@ int dfm_solve(const dfm_op* op, const double* rho0, int R, double* rho, const df
  *   g_e[l][nm] = |T_l|^{-1/2} Int_{T_l} Z_nm(p(s->r_e)) cos(vartheta) exp(-mu_e |r_e - s|) / |r_e - s|^2 ds,
  * at r_e = the tet's centroid, p(s->r) the tangential part of unit(r - s) in
  * face l's frame, and dg_e = d g_e / d mu_e.  Each face integral uses a
- * collapsed tensor Gauss-Legendre rule of order nq (0 = 16) in FP64.
+ * collapsed tensor Gauss-Legendre rule of order nq (0 = 32) in FP64.
  *   tets_host: HOST int64 [n] tet ids; weights_host: HOST FP64 [n] or NULL (1).
  *   gvec, dgvec: device FP64 [rows][nb]; on return gvec[4e+l] += w_e g_e[l] and
  *   dgvec[4e+l] += w_e dg_e[l] for the listed tets (other rows untouched), so

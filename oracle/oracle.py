@@ -433,7 +433,7 @@ def centroids(verts, tets):
     return verts[tets].mean(axis=1)
 
 
-def interior_g(verts, tets, t, r, mu, Np, nq=24):
+def interior_g(verts, tets, t, r, mu, Np, nq=48):
     """g[4, nb] and dg/dmu with rho_T(r) = sum_{l,nm} rho_(t,l,nm) g[l,nm]."""
     nb = nbasis(Np)
     x, w = np.polynomial.legendre.leggauss(nq)
@@ -446,7 +446,7 @@ def interior_g(verts, tets, t, r, mu, Np, nq=24):
     return g, dg
 
 
-def receiver_functional(verts, tets, mu_tet, Np, receiver, nq=24):
+def receiver_functional(verts, tets, mu_tet, Np, receiver, nq=48):
     """J(rho) = mean over receiver tets e of rho_T(centroid_e) = gvec . rho.
     Returns gvec [nrows, nb] and dgvec/dmu_e stacked per receiver tet."""
     nb = nbasis(Np)

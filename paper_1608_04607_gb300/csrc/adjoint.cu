@@ -211,7 +211,7 @@ extern "C" int dfm_interior_density(const dfm_mesh* mesh, int Np, const double* 
                                     double* dgvec, void* stream) {
   if (!mesh || !tets_host || !gvec || n < 1 || Np < 0 || Np > 8)
     return set_error(DFM_ERR_ARG, "dfm_interior_density: bad argument");
-  if (nq == 0) nq = 16;
+  if (nq == 0) nq = 32;
   if (nq < 2 || nq > 64) return set_error(DFM_ERR_ARG, "dfm_interior_density: nq must be in 2..64");
   if (!mu && !(mu_uniform >= 0)) return set_error(DFM_ERR_ARG, "dfm_interior_density: mu_uniform must be >= 0");
   for (int i = 0; i < n; ++i)

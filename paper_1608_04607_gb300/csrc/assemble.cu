@@ -275,6 +275,12 @@ extern "C" int dfm_assemble(const dfm_mesh* mesh, const dfm_params* p, void* str
     delete op;
     return cuda_error(e, "dfm_assemble: cudaMalloc(vals)");
   }
+  e = cudaMalloc(&op->dev_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(op->dev_err, 0, sizeof(int), as_stream(stream));
+  if (e != cudaSuccess) {
+    dfm_op_destroy(op);
+    return cuda_error(e, "dfm_assemble: error flag");
+  }
   // padding between rows stays zero
   e = cudaMemsetAsync(op->vals, 0, op->bytes, as_stream(stream));
   if (e != cudaSuccess) {
@@ -295,6 +301,7 @@ extern "C" void dfm_op_destroy(dfm_op* op) {
   cudaFree(op->vals);
   cudaFree(op->work);
   cudaFree(op->swork);
+  cudaFree(op->dev_err);
   delete op;
 }
 

@@ -52,6 +52,7 @@ struct dfm_op {
   int64_t nrows = 0, row_stride = 0;
   void* vals = nullptr;  // device
   int64_t bytes = 0;
+  int* dev_err = nullptr;  // device flag set by kernels whose bounded waits time out
   // assembly scratch (per-pair constants, Gauss table), grown on demand
   void* work = nullptr;
   int64_t work_bytes = 0;

@@ -581,5 +581,14 @@ extern "C" int dfm_solve(const dfm_op* op, const double* rho0, int R, double* rh
     if (rs != DFM_OK && status == DFM_OK) status = rs;
   }
   if (info) *info = acc_info;
+  if (op->dev_err) {  // a pipelined operator application gave up waiting
+    int e = 0;
+    DFM_CUDA_CHECK(cudaMemcpyAsync(&e, op->dev_err, sizeof(int), cudaMemcpyDeviceToHost, c.st));
+    DFM_CUDA_CHECK(cudaStreamSynchronize(c.st));
+    if (e) {
+      DFM_CUDA_CHECK(cudaMemsetAsync(op->dev_err, 0, sizeof(int), c.st));
+      return set_error(DFM_ERR_CUDA, "dfm_solve: an operator application timed out waiting for its data");
+    }
+  }
   return status;
 }

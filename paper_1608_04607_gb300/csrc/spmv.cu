@@ -3,11 +3,11 @@
 // so every block row and every block column holds exactly three blocks).
 //
 // Forward: row R receives three blocks, all from tet t = recv[R]/4, whose
-// source faces are the three faces of t other than l' = recv[R]%4.  A thread
-// block stages a tile of consecutive rows of the operator (contiguous in
-// memory, 16-byte aligned rows) and the coefficients of each row's source tet
-// in shared memory with vector loads, then one thread per (row, test index)
-// forms its dot products; the staged tile is reused for every right-hand side.
+// source faces are the three faces of t other than l' = recv[R]%4.  Tiles of
+// consecutive rows (contiguous in memory, 32-byte aligned rows) stream into
+// shared memory through a TMA bulk-copy pipeline; one thread per (row, test
+// index) forms its dot products against the source tet's coefficients (read
+// through the read-only cache); a staged tile serves every right-hand side.
 //
 // Transpose: column J = 4t + l owns the blocks (t, l) -> l' received by rows
 // recv[4t + l'] in slot l - (l > l'); one thread per (column, trial index)
@@ -20,58 +20,6 @@ namespace dfm {
 namespace {
 
 constexpr int kThreads = 128;
-
-template <typename TV, typename TX, typename TA>
-__global__ void __launch_bounds__(kThreads)
-spmv_kernel(const TV* __restrict__ vals, int64_t row_stride, const int32_t* __restrict__ recv, int64_t nrows, int nb,
-            int rows_per_tile, const TX* __restrict__ x, const TX* x0, TX* y, int R,
-            TA alpha) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  TV* s_vals = reinterpret_cast<TV*>(smem_raw);
-  TA* s_x = reinterpret_cast<TA*>(smem_raw + sizeof(TV) * rows_per_tile * row_stride);
-  const int64_t ntiles = (nrows + rows_per_tile - 1) / rows_per_tile;
-  const int nb2 = nb * nb;
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t R0 = tile * rows_per_tile;
-    const int64_t left = nrows - R0;
-    const int nr = left < rows_per_tile ? (int)left : rows_per_tile;
-    // stage the tile's operator rows (contiguous, 16-byte vectors)
-    const int4* src = reinterpret_cast<const int4*>(vals + R0 * row_stride);
-    int4* dst = reinterpret_cast<int4*>(s_vals);
-    const int64_t nvec = (int64_t)nr * row_stride * sizeof(TV) / 16;
-    for (int64_t i = threadIdx.x; i < nvec; i += blockDim.x) dst[i] = __ldg(src + i);
-    for (int rhs = 0; rhs < R; ++rhs) {
-      const TX* xr = x + (int64_t)rhs * nrows * nb;
-      // stage the four rows of each tile row's source tet
-      for (int i = threadIdx.x; i < nr * 4 * nb; i += blockDim.x) {
-        const int r = i / (4 * nb);
-        const int j = i - r * 4 * nb;
-        const int64_t t = recv[R0 + r] >> 2;
-        s_x[i] = (TA)xr[4 * t * nb + j];
-      }
-      __syncthreads();
-      for (int i = threadIdx.x; i < nr * nb; i += blockDim.x) {
-        const int r = i / nb;
-        const int a = i - r * nb;
-        const int lp = recv[R0 + r] & 3;
-        const TV* blk = s_vals + (int64_t)r * row_stride + a * nb;
-        const TA* xs = s_x + r * 4 * nb;
-        TA acc = TA(0);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          const int l = k + (k >= lp ? 1 : 0);
-          const TV* bk = blk + k * nb2;
-          const TA* xl = xs + l * nb;
-          for (int b = 0; b < nb; ++b) acc = fma((TA)bk[b], xl[b], acc);
-        }
-        const int64_t o = ((int64_t)rhs * nrows + R0 + r) * nb + a;
-        const TA base = x0 ? (TA)x0[o] : TA(0);
-        y[o] = (TX)(base + alpha * acc);
-      }
-      __syncthreads();
-    }
-  }
-}
 
 template <typename TV, typename TX, typename TA>
 __global__ void __launch_bounds__(kThreads)
@@ -102,6 +50,130 @@ spmv_t_kernel(const TV* __restrict__ vals, int64_t row_stride, const int32_t* __
   }
 }
 
+// ---------------------------------------------------------------------------
+// Forward application with a TMA bulk-copy pipeline.
+//
+// Each block walks its tiles (consecutive rows, one contiguous range of the
+// operator) with kStages shared-memory buffers: one thread issues a 1-D
+// cp.async.bulk copy per tile, completion is tracked by a per-stage mbarrier
+// (expect_tx), and the block computes tile i while tiles i+1..i+kStages-1 are
+// in flight.  Every wait is bounded; on a time-out the block records an error,
+// waits (bounded) for its own copies and leaves.
+// ---------------------------------------------------------------------------
+constexpr int kStages = 4;
+constexpr long long kWaitPolls = 1ll << 24;
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+  for (long long i = 0; i < kWaitPolls; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+template <int NB, typename TV, typename TX, typename TA>
+__global__ void __launch_bounds__(kThreads)
+spmv_tma_kernel(const TV* __restrict__ vals, int64_t row_stride, const int32_t* __restrict__ recv, int64_t nrows,
+                int rows_per_tile, int stages, const TX* __restrict__ x, const TX* x0, TX* y, int R, TA alpha,
+                int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
+  TV* buf = reinterpret_cast<TV*>(smem_raw + 128);
+  constexpr int NB2 = NB * NB;
+  const int64_t tile_elems = (int64_t)rows_per_tile * row_stride;
+  const int64_t ntiles = (nrows + rows_per_tile - 1) / rows_per_tile;
+  const int64_t mine = ntiles > (int64_t)blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < stages; ++s) mbar_init(&bars[s], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  auto issue = [&](int64_t i) {
+    const int64_t tile = blockIdx.x + i * (int64_t)gridDim.x;
+    const int s = (int)(i % stages);
+    const int64_t R0 = tile * rows_per_tile;
+    const int64_t left = nrows - R0;
+    const int nr = left < rows_per_tile ? (int)left : rows_per_tile;
+    const unsigned bytes = (unsigned)(nr * row_stride * (int64_t)sizeof(TV));
+    mbar_arrive_expect_tx(&bars[s], bytes);
+    bulk_copy_g2s(buf + s * tile_elems, vals + R0 * row_stride, bytes, &bars[s]);
+  };
+  if (threadIdx.x == 0)
+    for (int64_t i = 0; i < mine && i < stages; ++i) issue(i);
+  int64_t i = 0;
+  for (; i < mine; ++i) {
+    const int s = (int)(i % stages);
+    const bool ok = mbar_wait_bounded(&bars[s], (unsigned)((i / stages) & 1));
+    if (!__syncthreads_and(ok)) break;
+    const TV* tv = buf + s * tile_elems;
+    const int64_t R0 = (blockIdx.x + i * (int64_t)gridDim.x) * rows_per_tile;
+    const int64_t left = nrows - R0;
+    const int nr = left < rows_per_tile ? (int)left : rows_per_tile;
+    for (int e = threadIdx.x; e < nr * NB; e += blockDim.x) {
+      const int r = e / NB;
+      const int a = e - r * NB;
+      const int32_t src = recv[R0 + r];
+      const int lp = src & 3;
+      const int64_t t = src >> 2;
+      const TV* blk = tv + (int64_t)r * row_stride + a * NB;
+      for (int rhs = 0; rhs < R; ++rhs) {
+        const TX* xs = x + ((int64_t)rhs * nrows + 4 * t) * NB;
+        TA acc = TA(0);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const int l = k + (k >= lp ? 1 : 0);
+          const TV* bk = blk + k * NB2;
+          const TX* xl = xs + l * NB;
+#pragma unroll
+          for (int b = 0; b < NB; ++b) acc = fma((TA)bk[b], (TA)__ldg(xl + b), acc);
+        }
+        const int64_t o = ((int64_t)rhs * nrows + R0 + r) * NB + a;
+        const TA base = x0 ? (TA)x0[o] : TA(0);
+        y[o] = (TX)(base + alpha * acc);
+      }
+    }
+    __syncthreads();  // every thread is done with stage s
+    if (threadIdx.x == 0 && i + stages < mine) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(i + stages);
+    }
+  }
+  if (i < mine) {
+    // a wait timed out: record it and wait (bounded) for this block's copies in flight
+    if (threadIdx.x == 0) {
+      atomicOr(err, 1);
+      for (int64_t j = i; j < mine && j < i + stages; ++j)
+        mbar_wait_bounded(&bars[j % stages], (unsigned)((j / stages) & 1));
+    }
+    __syncthreads();
+  }
+}
+
 int rows_per_tile_for(int nb) {
   int r = kThreads / nb;
   if (r < 1) r = 1;
@@ -116,22 +188,42 @@ int launch(const dfm_op* op, const TX* x, const TX* x0, TX* y, int R, double alp
   DFM_CUDA_CHECK(cudaGetDevice(&dev));
   DFM_CUDA_CHECK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   if (!trans) {
-    const int rpt = rows_per_tile_for(op->nb);
-    const size_t smem = sizeof(TV) * rpt * op->row_stride + sizeof(TA) * rpt * 4 * op->nb;
-    if (smem > 200 * 1024) return set_error(DFM_ERR_UNSUPPORTED, "dfm_apply: tile does not fit shared memory");
-    DFM_CUDA_CHECK(cudaFuncSetAttribute(spmv_kernel<TV, TX, TA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)smem));
-    int per_sm = 0;
-    DFM_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, spmv_kernel<TV, TX, TA>, kThreads, smem));
-    if (per_sm < 1) per_sm = 1;
-    const int64_t ntiles = (op->nrows + rpt - 1) / rpt;
-    const int64_t grid = std::min<int64_t>(ntiles, (int64_t)nsm * per_sm);
-    {
-      ::dfm::KernelTimer timer_(sizeof(TX) == 8 ? DFM_KERNEL_SPMV64 : DFM_KERNEL_SPMV, st);
-      spmv_kernel<TV, TX, TA><<<(unsigned)grid, kThreads, smem, st>>>(vals, op->row_stride, recv, op->nrows, op->nb,
-                                                                      rpt, x, x0, y, R, (TA)alpha);
+    int rpt = rows_per_tile_for(op->nb);
+    const int64_t row_bytes = op->row_stride * (int64_t)sizeof(TV);
+    const int64_t budget = 200 * 1024 - 128;
+    while (rpt > 1 && rpt * row_bytes * 2 > budget) --rpt;  // keep at least two stages
+    int stages = (int)std::min<int64_t>(kStages, budget / (rpt * row_bytes));
+    if (stages < 1) return set_error(DFM_ERR_UNSUPPORTED, "dfm_apply: an operator row does not fit shared memory");
+    const size_t smem = 128 + (size_t)stages * rpt * row_bytes;
+    int rc = DFM_OK;
+    auto go = [&](auto kernel) -> int {
+      DFM_CUDA_CHECK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      int per_sm = 0;
+      DFM_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem));
+      if (per_sm < 1) per_sm = 1;
+      const int64_t ntiles = (op->nrows + rpt - 1) / rpt;
+      const int64_t grid = std::min<int64_t>(ntiles, (int64_t)nsm * per_sm);
+      {
+        ::dfm::KernelTimer timer_(sizeof(TX) == 8 ? DFM_KERNEL_SPMV64 : DFM_KERNEL_SPMV, st);
+        kernel<<<(unsigned)grid, kThreads, smem, st>>>(vals, op->row_stride, recv, op->nrows, rpt, stages, x, x0, y, R,
+                                                       (TA)alpha, op->dev_err);
+      }
+      DFM_LAUNCHED();
+      return DFM_OK;
+    };
+    switch (op->nb) {
+      case 1: rc = go(spmv_tma_kernel<1, TV, TX, TA>); break;
+      case 3: rc = go(spmv_tma_kernel<3, TV, TX, TA>); break;
+      case 6: rc = go(spmv_tma_kernel<6, TV, TX, TA>); break;
+      case 10: rc = go(spmv_tma_kernel<10, TV, TX, TA>); break;
+      case 15: rc = go(spmv_tma_kernel<15, TV, TX, TA>); break;
+      case 21: rc = go(spmv_tma_kernel<21, TV, TX, TA>); break;
+      case 28: rc = go(spmv_tma_kernel<28, TV, TX, TA>); break;
+      case 36: rc = go(spmv_tma_kernel<36, TV, TX, TA>); break;
+      case 45: rc = go(spmv_tma_kernel<45, TV, TX, TA>); break;
+      default: return set_error(DFM_ERR_UNSUPPORTED, "dfm_apply: unsupported basis size");
     }
-    DFM_LAUNCHED();
+    if (rc) return rc;
   } else {
     const int64_t total = op->nrows * op->nb * (int64_t)R;
     const int64_t grid = std::min<int64_t>((total + kThreads - 1) / kThreads, (int64_t)nsm * 16);

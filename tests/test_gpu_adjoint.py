@@ -41,11 +41,13 @@ def test_interior_density_matches_oracle(D, oracle_mod, problem):
     w = 1.0 / len(p["receiver"])
     g, dg = D.interior_density(p["mesh"], p["Np"], p["receiver"], weights=w, mu=p["mu_t"])
     gref, dgref = oracle_mod.receiver_functional(m.verts, m.tets, p["mu"], p["Np"], p["receiver"])
-    np.testing.assert_allclose(g.cpu().numpy(), gref, rtol=0, atol=1e-10 * np.abs(gref).max())
+    # both sides integrate a smooth but sharply peaked kernel (the centroid of a
+    # sliver tet is close to a face): order 32 on the GPU, 48 in the oracle
+    np.testing.assert_allclose(g.cpu().numpy(), gref, rtol=0, atol=5e-8 * np.abs(gref).max())
     dgr = np.zeros_like(gref)
     for e, d in dgref.items():
         dgr[4 * e:4 * e + 4] = d
-    np.testing.assert_allclose(dg.cpu().numpy(), dgr, rtol=0, atol=1e-10 * np.abs(dgr).max())
+    np.testing.assert_allclose(dg.cpu().numpy(), dgr, rtol=0, atol=5e-8 * np.abs(dgr).max())
 
 
 def test_adjoint_gradient_matches_oracle(D, oracle_mod, problem):
