@@ -392,6 +392,41 @@ def run_reference(args):
     print(json.dumps(res))
 
 
+def run_apply(args):
+    """Operator-application micro-benchmark: K timed y = x0 - B x launches
+    (FP32 vectors) on the workload's assembled operator, for the SpMV roofline
+    and for profiling the kernel in isolation."""
+    import torch
+
+    from paper_1608_04607_gb300 import dfm
+    from paper_1608_04607_gb300.inputs import workload
+
+    torch.cuda.set_device(0)
+    w = workload(args.workload)
+    m = w["mesh"]
+    mesh = dfm.Mesh(m.verts, m.tets, refl=w["refl"])
+    op = dfm.Operator(mesh, w["Np"], mu=float(w["mu"][0]), precision=dfm.F32)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.randn((1, mesh.n_rows, op.nb), device="cuda", dtype=torch.float32, generator=g)
+    y = torch.empty_like(x)
+    for _ in range(args.warmup):
+        op.apply(x, x0=x, alpha=-1.0, out=y)
+    torch.cuda.synchronize()
+    dfm.stats_reset()
+    dfm.stats_enable(True)
+    for _ in range(args.steps):
+        op.apply(x, x0=x, alpha=-1.0, out=y)
+    torch.cuda.synchronize()
+    n, ms = dfm.kernel_stats(dfm.KERNEL_SPMV)
+    dfm.stats_enable(False)
+    peaks, src = _peaks()
+    by = spmv_bytes(mesh.n_rows, op.nb, 4, with_x0=True)
+    ach = by / (ms / n * 1e-3) / 1e9
+    print(json.dumps({"mode": "apply", "workload": args.workload, "launches": n, "ms_per_launch": ms / n,
+                      "bytes_per_launch": by, "achieved_gbs": ach, "peak_gbs": peaks.get("hbm_gbs"),
+                      "frac": ach / float(peaks.get("hbm_gbs", HBM_PEAK_FALLBACK)), "peak_source": src}))
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -406,9 +441,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--ref-apps", type=int, default=600)
+    ap.add_argument("--mode", choices=["solve", "apply"], default="solve")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.mode == "apply":
+        run_apply(args)
     else:
         run_gpu(args)
 
