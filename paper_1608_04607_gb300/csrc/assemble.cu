@@ -37,15 +37,63 @@
 #include "dfm_internal.cuh"
 #include "node.cuh"
 
+#include <cstddef>
+#include <type_traits>
+
 namespace dfm {
 namespace {
+
+// Store one staged row: scale * v[0..NB) followed by zeros up to NBP, as
+// 16-byte vectors for FP32 (rows are 16-byte aligned, see Tile::LD).
+template <int NBP, int NB, typename T>
+__device__ __forceinline__ void stage_row(T* row, const T* v, T scale) {
+  if constexpr (std::is_same<T, float>::value) {
+#pragma unroll
+    for (int u = 0; u < NBP / 4; ++u) {
+      float4 q;
+      q.x = (4 * u + 0 < NB) ? scale * v[4 * u + 0 < NB ? 4 * u + 0 : 0] : 0.f;
+      q.y = (4 * u + 1 < NB) ? scale * v[4 * u + 1 < NB ? 4 * u + 1 : 0] : 0.f;
+      q.z = (4 * u + 2 < NB) ? scale * v[4 * u + 2 < NB ? 4 * u + 2 : 0] : 0.f;
+      q.w = (4 * u + 3 < NB) ? scale * v[4 * u + 3 < NB ? 4 * u + 3 : 0] : 0.f;
+      *reinterpret_cast<float4*>(row + 4 * u) = q;
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < NBP; ++c) row[c] = c < NB ? scale * v[c < NB ? c : 0] : T(0);
+  }
+}
+
+// Load N consecutive staged values with the widest aligned vector loads.
+template <int N, typename T>
+__device__ __forceinline__ void load_run(const T* p, T* out) {
+  if constexpr (std::is_same<T, float>::value && N % 4 == 0) {
+#pragma unroll
+    for (int u = 0; u < N / 4; ++u) {
+      const float4 q = *reinterpret_cast<const float4*>(p + 4 * u);
+      out[4 * u] = q.x;
+      out[4 * u + 1] = q.y;
+      out[4 * u + 2] = q.z;
+      out[4 * u + 3] = q.w;
+    }
+  } else if constexpr (std::is_same<T, float>::value && N % 2 == 0) {
+#pragma unroll
+    for (int u = 0; u < N / 2; ++u) {
+      const float2 q = *reinterpret_cast<const float2*>(p + 2 * u);
+      out[2 * u] = q.x;
+      out[2 * u + 1] = q.y;
+    }
+  } else {
+#pragma unroll
+    for (int u = 0; u < N; ++u) out[u] = p[u];
+  }
+}
 
 // Shared memory of one warp: patch state plus the staged node vectors.
 template <int NP, typename T>
 struct WarpSmem {
   PatchSmem P;
-  T zq[32 * Tile<NP>::LD];  // w * Z(p') per node
-  T zp[32 * Tile<NP>::LD];  // Z(p) per node
+  alignas(16) T zq[32 * Tile<NP>::LD];  // w * Z(p') per node (16-byte aligned rows)
+  alignas(16) T zp[32 * Tile<NP>::LD];  // Z(p) per node
 };
 
 template <int NP, typename T>
@@ -68,11 +116,6 @@ assemble_kernel(const PairConst* __restrict__ pairs, int64_t npairs, const doubl
     s_w[threadIdx.x] = (T)gl_w[threadIdx.x];
   }
   if (threadIdx.x < NB) s_ninv[threadIdx.x] = zernike_invnorm(threadIdx.x);
-  // zero the staging buffers once (padding columns stay zero)
-  for (int i = lane; i < 32 * LD; i += 32) {
-    S.zq[i] = T(0);
-    S.zp[i] = T(0);
-  }
   __syncthreads();
   const int qq = q * q;
   const int a0 = (lane >> 2) * TR;
@@ -121,19 +164,15 @@ assemble_kernel(const PairConst* __restrict__ pairs, int64_t npairs, const doubl
 #pragma unroll
           for (int c = 0; c < NB; ++c) Zp[c] = Zq[c] = T(0);
         }
-#pragma unroll
-        for (int c = 0; c < NB; ++c) {
-          S.zq[lane * LD + c] = wnode * Zq[c];
-          S.zp[lane * LD + c] = Zp[c];
-        }
+        stage_row<TL::NBP, NB>(&S.zq[lane * LD], Zq, wnode);
+        stage_row<TL::NBP, NB>(&S.zp[lane * LD], Zp, T(1));
         __syncwarp();
         const int kmax = min(32, nodes - base);
+#pragma unroll 2
         for (int kk = 0; kk < kmax; ++kk) {
           T av[TR], bv[TC];
-#pragma unroll
-          for (int r = 0; r < TR; ++r) av[r] = S.zq[kk * LD + a0 + r];
-#pragma unroll
-          for (int c = 0; c < TC; ++c) bv[c] = S.zp[kk * LD + b0 + c];
+          load_run<TR>(&S.zq[kk * LD + a0], av);
+          load_run<TC>(&S.zp[kk * LD + b0], bv);
 #pragma unroll
           for (int r = 0; r < TR; ++r)
 #pragma unroll
@@ -159,6 +198,11 @@ assemble_kernel(const PairConst* __restrict__ pairs, int64_t npairs, const doubl
     __syncwarp();
   }
 }
+
+using WarpSmem4f = WarpSmem<4, float>;
+using WarpSmem8f = WarpSmem<8, float>;
+static_assert(offsetof(WarpSmem4f, zq) % 16 == 0 && sizeof(WarpSmem4f) % 16 == 0, "16-byte aligned staging rows");
+static_assert(offsetof(WarpSmem8f, zq) % 16 == 0 && sizeof(WarpSmem8f) % 16 == 0, "16-byte aligned staging rows");
 
 template <int NP, typename T>
 constexpr size_t assemble_smem_bytes() {

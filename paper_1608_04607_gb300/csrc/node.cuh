@@ -172,7 +172,10 @@ struct Tile {
   static constexpr int NBP = ((NB + 7) / 8) * 8;  // padded block side
   static constexpr int TR = NBP / 8;              // rows per lane (8 row groups)
   static constexpr int TC = NBP / 4;              // columns per lane (4 column groups)
-  static constexpr int LD = NBP + 1;              // staging row stride (odd: conflict-free stores)
+  // staging row stride: NBP + 4 keeps rows 16-byte aligned and shifts each
+  // row by 16 bytes modulo 128, so eight lanes storing 16-byte vectors of
+  // eight consecutive rows hit eight distinct bank groups
+  static constexpr int LD = NBP + 4;
 };
 
 constexpr int kWarps = 4;        // warps (face pairs) per block

@@ -12,6 +12,8 @@
 // Transpose: column J = 4t + l owns the blocks (t, l) -> l' received by rows
 // recv[4t + l'] in slot l - (l > l'); one thread per (column, trial index)
 // walks the three blocks with coalesced reads along the trial index.
+#include <stdint.h>
+
 #include <algorithm>
 
 #include "dfm_internal.cuh"
@@ -61,6 +63,7 @@ spmv_t_kernel(const TV* __restrict__ vals, int64_t row_stride, const int32_t* __
 // waits (bounded) for its own copies and leaves.
 // ---------------------------------------------------------------------------
 constexpr int kStages = 4;
+constexpr int kMaxStagedRhs = 4;  // right-hand sides staged per operator pass
 constexpr long long kWaitPolls = 1ll << 24;
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -101,11 +104,18 @@ __global__ void __launch_bounds__(kThreads)
 spmv_tma_kernel(const TV* __restrict__ vals, int64_t row_stride, const int32_t* __restrict__ recv, int64_t nrows,
                 int rows_per_tile, int stages, const TX* __restrict__ x, const TX* x0, TX* y, int R, TA alpha,
                 int* __restrict__ err) {
+  // shared memory: [mbarriers | recv per stage | stage buffers]; a stage holds
+  // the tile's operator rows followed by, per right-hand side and tile row, the
+  // 4 x NB coefficients of the row's source tet (one contiguous 16-byte-aligned
+  // block of x, fetched by its own bulk copy)
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
-  TV* buf = reinterpret_cast<TV*>(smem_raw + 128);
+  int32_t* s_recv = reinterpret_cast<int32_t*>(smem_raw + 64);
   constexpr int NB2 = NB * NB;
-  const int64_t tile_elems = (int64_t)rows_per_tile * row_stride;
+  const int64_t vals_bytes = (int64_t)rows_per_tile * row_stride * (int64_t)sizeof(TV);
+  const int64_t xblk = 4 * NB * (int64_t)sizeof(TX);
+  const int64_t stage_bytes = vals_bytes + (int64_t)R * rows_per_tile * xblk;
+  unsigned char* stage0 = smem_raw + 64 + ((stages * rows_per_tile * 4 + 127) / 128) * 128 + 64;
   const int64_t ntiles = (nrows + rows_per_tile - 1) / rows_per_tile;
   const int64_t mine = ntiles > (int64_t)blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   if (threadIdx.x == 0) {
@@ -119,9 +129,16 @@ spmv_tma_kernel(const TV* __restrict__ vals, int64_t row_stride, const int32_t* 
     const int64_t R0 = tile * rows_per_tile;
     const int64_t left = nrows - R0;
     const int nr = left < rows_per_tile ? (int)left : rows_per_tile;
-    const unsigned bytes = (unsigned)(nr * row_stride * (int64_t)sizeof(TV));
-    mbar_arrive_expect_tx(&bars[s], bytes);
-    bulk_copy_g2s(buf + s * tile_elems, vals + R0 * row_stride, bytes, &bars[s]);
+    unsigned char* st = stage0 + s * stage_bytes;
+    int32_t* rs = s_recv + s * rows_per_tile;
+    for (int r = 0; r < nr; ++r) rs[r] = recv[R0 + r];
+    const unsigned vb = (unsigned)(nr * row_stride * (int64_t)sizeof(TV));
+    mbar_arrive_expect_tx(&bars[s], vb + (unsigned)(R * nr * xblk));
+    bulk_copy_g2s(st, vals + R0 * row_stride, vb, &bars[s]);
+    for (int rhs = 0; rhs < R; ++rhs)
+      for (int r = 0; r < nr; ++r)
+        bulk_copy_g2s(st + vals_bytes + ((int64_t)rhs * rows_per_tile + r) * xblk,
+                      x + ((int64_t)rhs * nrows + 4 * (int64_t)(rs[r] >> 2)) * NB, (unsigned)xblk, &bars[s]);
   };
   if (threadIdx.x == 0)
     for (int64_t i = 0; i < mine && i < stages; ++i) issue(i);
@@ -130,19 +147,20 @@ spmv_tma_kernel(const TV* __restrict__ vals, int64_t row_stride, const int32_t* 
     const int s = (int)(i % stages);
     const bool ok = mbar_wait_bounded(&bars[s], (unsigned)((i / stages) & 1));
     if (!__syncthreads_and(ok)) break;
-    const TV* tv = buf + s * tile_elems;
+    const unsigned char* st = stage0 + s * stage_bytes;
+    const TV* tv = reinterpret_cast<const TV*>(st);
+    const TX* tx = reinterpret_cast<const TX*>(st + vals_bytes);
+    const int32_t* rs = s_recv + s * rows_per_tile;
     const int64_t R0 = (blockIdx.x + i * (int64_t)gridDim.x) * rows_per_tile;
     const int64_t left = nrows - R0;
     const int nr = left < rows_per_tile ? (int)left : rows_per_tile;
     for (int e = threadIdx.x; e < nr * NB; e += blockDim.x) {
       const int r = e / NB;
       const int a = e - r * NB;
-      const int32_t src = recv[R0 + r];
-      const int lp = src & 3;
-      const int64_t t = src >> 2;
+      const int lp = rs[r] & 3;
       const TV* blk = tv + (int64_t)r * row_stride + a * NB;
       for (int rhs = 0; rhs < R; ++rhs) {
-        const TX* xs = x + ((int64_t)rhs * nrows + 4 * t) * NB;
+        const TX* xs = tx + ((int64_t)rhs * rows_per_tile + r) * 4 * NB;
         TA acc = TA(0);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -150,7 +168,7 @@ spmv_tma_kernel(const TV* __restrict__ vals, int64_t row_stride, const int32_t* 
           const TV* bk = blk + k * NB2;
           const TX* xl = xs + l * NB;
 #pragma unroll
-          for (int b = 0; b < NB; ++b) acc = fma((TA)bk[b], (TA)__ldg(xl + b), acc);
+          for (int b = 0; b < NB; ++b) acc = fma((TA)bk[b], (TA)xl[b], acc);
         }
         const int64_t o = ((int64_t)rhs * nrows + R0 + r) * NB + a;
         const TA base = x0 ? (TA)x0[o] : TA(0);
@@ -188,13 +206,24 @@ int launch(const dfm_op* op, const TX* x, const TX* x0, TX* y, int R, double alp
   DFM_CUDA_CHECK(cudaGetDevice(&dev));
   DFM_CUDA_CHECK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   if (!trans) {
+    if ((reinterpret_cast<uintptr_t>(x) & 15) || (reinterpret_cast<uintptr_t>(op->vals) & 15))
+      return set_error(DFM_ERR_ARG, "dfm_apply: x must be 16-byte aligned");
+    if (R > kMaxStagedRhs) {  // several passes, each staging up to kMaxStagedRhs right-hand sides
+      const int64_t stride = op->nrows * (int64_t)op->nb;
+      for (int r0 = 0; r0 < R; r0 += kMaxStagedRhs) {
+        const int rc = launch<TV, TX, TA>(op, x + r0 * stride, x0 ? x0 + r0 * stride : nullptr, y + r0 * stride,
+                                          std::min(kMaxStagedRhs, R - r0), alpha, 0, st);
+        if (rc) return rc;
+      }
+      return DFM_OK;
+    }
     int rpt = rows_per_tile_for(op->nb);
-    const int64_t row_bytes = op->row_stride * (int64_t)sizeof(TV);
-    const int64_t budget = 200 * 1024 - 128;
+    const int64_t row_bytes = op->row_stride * (int64_t)sizeof(TV) + (int64_t)R * 4 * op->nb * (int64_t)sizeof(TX);
+    const int64_t budget = 200 * 1024 - 1024;
     while (rpt > 1 && rpt * row_bytes * 2 > budget) --rpt;  // keep at least two stages
     int stages = (int)std::min<int64_t>(kStages, budget / (rpt * row_bytes));
     if (stages < 1) return set_error(DFM_ERR_UNSUPPORTED, "dfm_apply: an operator row does not fit shared memory");
-    const size_t smem = 128 + (size_t)stages * rpt * row_bytes;
+    const size_t smem = 64 + ((stages * rpt * 4 + 127) / 128) * 128 + 64 + (size_t)stages * rpt * row_bytes;
     int rc = DFM_OK;
     auto go = [&](auto kernel) -> int {
       DFM_CUDA_CHECK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

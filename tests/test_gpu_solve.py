@@ -155,3 +155,18 @@ def test_polynomial_preconditioning_and_transpose(D, oracle_mod, poly):
         got = x[0].cpu().numpy().ravel()
         assert np.linalg.norm(got - ref) <= 1e-8 * np.linalg.norm(ref)
         assert info.resid <= 1e-10
+
+
+def test_apply_rejects_misaligned_vectors(D):
+    """The operator application streams x through 16-byte bulk copies; a
+    misaligned x is refused on the host before any launch."""
+    import torch
+
+    m = kuhn_cube_mesh(2, jitter=0.2, seed=8)
+    mesh = D.Mesh(m.verts, m.tets)
+    op = D.Operator(mesh, 2, mu=0.1)
+    buf = torch.zeros(mesh.n_rows * op.nb + 1, dtype=torch.float32, device="cuda")
+    x = buf[1:].view(mesh.n_rows, op.nb)
+    with pytest.raises(D.DFMError) as e:
+        op.apply(x)
+    assert e.value.code == D.DFM_ERR_ARG
