@@ -300,11 +300,39 @@ def run_gpu(args):
                     for k, v in kern.items()},
         "kernel_ms_per_step": {k: round(v / args.steps, 4) for k, v in total.items()},
     }
+    if not args.no_comparator:
+        res["fp64_gpu_path"] = fp64_comparator(dfm, mesh, Np, mu, rows, tol)
     if ws == 1 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(args.workload, op_apps=iters[-1], seconds=args.cpu_seconds)
     print(json.dumps(res))
     if ws > 1:
         dist.destroy_process_group()
+
+
+def fp64_comparator(dfm, mesh, Np, mu, rows, tol):
+    """The plain FP64 GPU path on the same workload: FP64 assembly and FP64
+    GMRES (same polynomial preconditioner, restart) to the same residual.
+    One warm-up and one timed solve."""
+    import torch
+
+    def once():
+        op = dfm.Operator(mesh, Np, mu=mu, precision=dfm.F64)
+        rho0 = dfm.source(mesh, Np, rows)
+        rho, info = op.solve(rho0, method=dfm.GMRES, tol=tol, poly_degree=16)
+        op.close()
+        return info
+
+    once()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    info = once()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    return {"value": 1e3 / ms, "unit": "solves/s", "ms_per_solve": ms, "operator_applications": info.iters,
+            "resid": info.resid, "desc": "FP64 blocks, FP64 GMRES(128) with sum_{k<16} B^k, same tolerance"}
 
 
 # ---------------------------------------------------------------------------
@@ -439,6 +467,7 @@ def main():
     ap.add_argument("--poly", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-comparator", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--ref-apps", type=int, default=600)
     ap.add_argument("--mode", choices=["solve", "apply"], default="solve")

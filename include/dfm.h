@@ -189,6 +189,9 @@ typedef struct {
   int transpose;     /* 1: solve (I - B)^T x = rho0 instead (the adjoint equation) */
   int poly_degree;   /* right preconditioner p(B) = sum_{k<d} B^k, so GMRES runs on I - B^d:
                         GMRES_IR inner solves: 0 = 16; GMRES on an FP64 operator: 0 = none */
+  int batch;         /* GMRES_IR with R > 1: right-hand sides iterated in lockstep, sharing
+                        every operator pass (0 = up to 16, capped so the group's FP32 Krylov
+                        basis stays within 24 GiB) */
 } dfm_solve_opts;
 
 typedef struct {

@@ -163,6 +163,109 @@ __global__ void add_f32_kernel(double* __restrict__ x, const float* __restrict__
     x[i] = fma(s, (double)d[i], x[i]);
 }
 
+
+// ---------------------------------------------------------------------------
+// Batched kernels: R right-hand sides in lockstep (blockIdx.y = right-hand
+// side).  Vector r of Krylov step j lives at V + j * ldj + r * ldr.
+// ---------------------------------------------------------------------------
+constexpr int kBRedBlocks = 128;  // partial-sum blocks per right-hand side
+
+// partial[(r * gridDim.x + b) * k + j] = slice of V[j]_r . w_r
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads)
+bdot_kernel(const T* __restrict__ V, int64_t ldj, int64_t ldr, int k, const T* __restrict__ w, int64_t wldr, int64_t n,
+            T* __restrict__ partial) {
+  __shared__ T sh[32];
+  const int r = blockIdx.y;
+  const T* wr = w + r * wldr;
+  for (int j0 = 0; j0 < k; j0 += kDotChunk) {
+    T acc[kDotChunk];
+#pragma unroll
+    for (int c = 0; c < kDotChunk; ++c) acc[c] = T(0);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+      const T wi = wr[i];
+#pragma unroll
+      for (int c = 0; c < kDotChunk; ++c)
+        if (j0 + c < k) acc[c] = fma(V[(int64_t)(j0 + c) * ldj + r * ldr + i], wi, acc[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < kDotChunk; ++c) {
+      if (j0 + c >= k) break;
+      const T sum = block_sum(acc[c], sh);
+      if (threadIdx.x == 0) partial[((int64_t)r * gridDim.x + blockIdx.x) * k + j0 + c] = sum;
+    }
+  }
+}
+
+// out[r * ldo + j] = sum_b partial[(r * nblk + b) * k + j]; grid (k, R)
+template <typename T>
+__global__ void breduce_kernel(const T* __restrict__ partial, int nblk, int k, int64_t ldo, T* __restrict__ out) {
+  __shared__ T sh[32];
+  const int j = blockIdx.x, r = blockIdx.y;
+  T sum = T(0);
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) sum += partial[((int64_t)r * nblk + b) * k + j];
+  sum = block_sum(sum, sh);
+  if (threadIdx.x == 0) out[r * ldo + j] = sum;
+}
+
+// w_r += sign * sum_j h[r * hld + j] V[j]_r;  partial[r * gridDim.x + b] = slice of |w_r|^2
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads)
+baxpy_kernel(const T* __restrict__ V, int64_t ldj, int64_t ldr, int k, const T* __restrict__ h, int hld, T sign, T* w,
+             int64_t wldr, int64_t n, T* __restrict__ partial) {
+  __shared__ T sh[32];
+  __shared__ T hs[kMaxKrylov + 8];
+  const int r = blockIdx.y;
+  for (int j = threadIdx.x; j < k && j < kMaxKrylov + 8; j += blockDim.x) hs[j] = sign * h[(int64_t)r * hld + j];
+  __syncthreads();
+  T* wr = w + r * wldr;
+  const T* Vr = V + r * ldr;
+  T sq = T(0);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    T v0 = wr[i], v1 = T(0), v2 = T(0), v3 = T(0);
+    int j = 0;
+    for (; j + 4 <= k; j += 4) {
+      v0 = fma(hs[j], Vr[(int64_t)j * ldj + i], v0);
+      v1 = fma(hs[j + 1], Vr[(int64_t)(j + 1) * ldj + i], v1);
+      v2 = fma(hs[j + 2], Vr[(int64_t)(j + 2) * ldj + i], v2);
+      v3 = fma(hs[j + 3], Vr[(int64_t)(j + 3) * ldj + i], v3);
+    }
+    for (; j < k; ++j) v0 = fma(hs[j], Vr[(int64_t)j * ldj + i], v0);
+    const T v = (v0 + v1) + (v2 + v3);
+    wr[i] = v;
+    sq = fma(v, v, sq);
+  }
+  if (partial) {
+    const T sum = block_sum(sq, sh);
+    if (threadIdx.x == 0) partial[(int64_t)r * gridDim.x + blockIdx.x] = sum;
+  }
+}
+
+// w_r *= s[r]
+template <typename T>
+__global__ void bscale_kernel(T* w, int64_t wldr, const T* __restrict__ s, int64_t n) {
+  const int r = blockIdx.y;
+  const T f = s[r];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    w[r * wldr + i] *= f;
+}
+
+// y_r = (float)(x_r * s[r])  (FP64 residual -> FP32 right-hand side)
+__global__ void bto_f32_kernel(float* __restrict__ y, const double* __restrict__ x, const double* __restrict__ s,
+                               int64_t n) {
+  const int r = blockIdx.y;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[r * n + i] = (float)(x[r * n + i] * s[r]);
+}
+
+// x_r += s[r] * (double)d_r
+__global__ void badd_f32_kernel(double* __restrict__ x, const float* __restrict__ d, const double* __restrict__ s,
+                                int64_t n) {
+  const int r = blockIdx.y;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[r * n + i] = fma(s[r], (double)d[r * n + i], x[r * n + i]);
+}
+
 __global__ void source_kernel(const FaceGeom* __restrict__ geom, const int64_t* __restrict__ rows, int n_src,
                               int64_t nrows, int nb, double* __restrict__ rho0) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -407,6 +510,246 @@ int residual64(const Ctx& c, const double* rho0, const double* x, double* r, dou
   return DFM_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// Batched host helpers
+// ---------------------------------------------------------------------------
+
+// host[r * k + j] = V[j]_r . w_r  (synchronises)
+template <typename T>
+int bdots(const Ctx& c, int R, const T* V, int64_t ldj, int64_t ldr, int k, const T* w, int64_t wldr, T* partial,
+          T* out_dev, T* out_host) {
+  {
+    ::dfm::KernelTimer timer_(DFM_KERNEL_DOT, c.st);
+    bdot_kernel<T><<<dim3(kBRedBlocks, R), kRedThreads, 0, c.st>>>(V, ldj, ldr, k, w, wldr, c.n, partial);
+  }
+  DFM_LAUNCHED();
+  DFM_CUDA_CHECK(cudaGetLastError());
+  breduce_kernel<T><<<dim3(k, R), 128, 0, c.st>>>(partial, kBRedBlocks, k, k, out_dev);
+  DFM_LAUNCHED();
+  DFM_CUDA_CHECK(cudaGetLastError());
+  DFM_CUDA_CHECK(cudaMemcpyAsync(out_host, out_dev, sizeof(T) * k * R, cudaMemcpyDeviceToHost, c.st));
+  DFM_CUDA_CHECK(cudaStreamSynchronize(c.st));
+  return DFM_OK;
+}
+
+// w_r += sign * V h_r (h_dev [R][hld]); sq_host[r] = |w_r|^2  (synchronises when sq_host)
+template <typename T>
+int baxpy(const Ctx& c, int R, const T* V, int64_t ldj, int64_t ldr, int k, const T* h_dev, int hld, T sign, T* w,
+          int64_t wldr, T* partial, T* red_dev, std::vector<double>* sq_host) {
+  {
+    ::dfm::KernelTimer timer_(DFM_KERNEL_AXPY, c.st);
+    baxpy_kernel<T><<<dim3(kBRedBlocks, R), kRedThreads, 0, c.st>>>(V, ldj, ldr, k, h_dev, hld, sign, w, wldr, c.n,
+                                                                     sq_host ? partial : nullptr);
+  }
+  DFM_LAUNCHED();
+  DFM_CUDA_CHECK(cudaGetLastError());
+  if (!sq_host) return DFM_OK;
+  breduce_kernel<T><<<dim3(1, R), 128, 0, c.st>>>(partial, kBRedBlocks, 1, 1, red_dev);
+  DFM_LAUNCHED();
+  DFM_CUDA_CHECK(cudaGetLastError());
+  std::vector<T> tmp(R);
+  DFM_CUDA_CHECK(cudaMemcpyAsync(tmp.data(), red_dev, sizeof(T) * R, cudaMemcpyDeviceToHost, c.st));
+  DFM_CUDA_CHECK(cudaStreamSynchronize(c.st));
+  sq_host->resize(R);
+  for (int r = 0; r < R; ++r) (*sq_host)[r] = (double)tmp[r];
+  return DFM_OK;
+}
+
+template <typename T>
+int bscale(const Ctx& c, int R, T* w, int64_t wldr, const std::vector<double>& f, T* s_dev) {
+  std::vector<T> fh(R);
+  for (int r = 0; r < R; ++r) fh[r] = (T)f[r];
+  DFM_CUDA_CHECK(cudaMemcpyAsync(s_dev, fh.data(), sizeof(T) * R, cudaMemcpyHostToDevice, c.st));
+  bscale_kernel<T><<<dim3(grid_for(c.n, c.nsm), R), 256, 0, c.st>>>(w, wldr, s_dev, c.n);
+  DFM_LAUNCHED();
+  DFM_CUDA_CHECK(cudaGetLastError());
+  return DFM_OK;
+}
+
+// GMRES(m) for R right-hand sides in lockstep, right-preconditioned by
+// p(B) = sum_{k<d} B^k (see gmres()); every operator application is one
+// launch over all R vectors, so the operator is read once per hop for all of
+// them.  Each right-hand side keeps its own Hessenberg matrix and stops
+// contributing once its residual estimate meets tol (relative to |b_r|).
+// b, x: [R][n]; V: [(m+1)][R][n]; tmp, t1, t2: [R][n].
+template <typename T>
+int gmres_batched(const Ctx& c, int R, const T* b, T* x, double tol, int m, int d, int max_iter, int* iters,
+                  std::vector<double>* est, T* V, T* tmp, T* t1, T* t2, T* h_dev, T* partial, T* red_dev) {
+  const int64_t n = c.n;
+  const int64_t Rn = (int64_t)R * n;
+  const int xtype = sizeof(T) == 8 ? DFM_F64 : DFM_F32;
+  const int hld = m + 2;
+  std::vector<T> hh((size_t)R * hld);
+  std::vector<std::vector<double>> H(R, std::vector<double>((m + 1) * m)), cs(R, std::vector<double>(m)),
+      sn(R, std::vector<double>(m)), g(R, std::vector<double>(m + 1));
+  std::vector<double> bnorm(R), beta(R), sq, f(R);
+  std::vector<int> kdone(R), active(R);
+  est->assign(R, 0.0);
+  int rc = bdots<T>(c, R, b, 0, n, 1, b, n, partial, h_dev, hh.data());
+  if (rc) return rc;
+  for (int r = 0; r < R; ++r) {
+    bnorm[r] = sqrt(std::max(0.0, (double)hh[r]));
+    if (!(bnorm[r] == bnorm[r]) || isinf(bnorm[r]))
+      return set_error(DFM_ERR_NONFINITE, "dfm_solve: non-finite right-hand side");
+  }
+  auto poly_op = [&](const T* v, T* w) -> int {
+    const T* src = v;
+    for (int k = 1; k < d; ++k) {
+      T* dst = (k & 1) ? t1 : t2;
+      int r2 = apply_impl(c.op, src, nullptr, dst, R, 1.0, c.trans, xtype, c.st);
+      if (r2) return r2;
+      src = dst;
+    }
+    *iters += d;
+    return apply_impl(c.op, src, v, w, R, -1.0, c.trans, xtype, c.st);
+  };
+  while (true) {
+    axpby_kernel<T><<<grid_for(Rn, c.nsm), 256, 0, c.st>>>(tmp, T(1), b, T(-1), x, Rn);
+    DFM_LAUNCHED();
+    DFM_CUDA_CHECK(cudaGetLastError());
+    rc = apply_impl(c.op, x, tmp, V, R, 1.0, c.trans, xtype, c.st);
+    if (rc) return rc;
+    ++*iters;
+    rc = bdots<T>(c, R, V, 0, n, 1, V, n, partial, h_dev, hh.data());
+    if (rc) return rc;
+    int nact = 0;
+    for (int r = 0; r < R; ++r) {
+      beta[r] = sqrt(std::max(0.0, (double)hh[r]));
+      if (!(beta[r] == beta[r]) || isinf(beta[r])) return set_error(DFM_ERR_NONFINITE, "dfm_solve: non-finite residual");
+      (*est)[r] = bnorm[r] > 0 ? beta[r] / bnorm[r] : 0.0;
+      active[r] = beta[r] > tol * bnorm[r] && bnorm[r] > 0;
+      nact += active[r];
+      f[r] = active[r] ? 1.0 / beta[r] : 0.0;
+      g[r].assign(m + 1, 0.0);
+      g[r][0] = active[r] ? beta[r] : 0.0;
+      kdone[r] = 0;
+    }
+    if (nact == 0) return DFM_OK;
+    if (*iters >= max_iter) return DFM_ERR_NOT_CONVERGED;
+    rc = bscale<T>(c, R, V, n, f, red_dev);
+    if (rc) return rc;
+    for (int j = 0; j < m; ++j) {
+      T* vj = V + (int64_t)j * Rn;
+      T* w = V + (int64_t)(j + 1) * Rn;
+      rc = poly_op(vj, w);
+      if (rc) return rc;
+      rc = bdots<T>(c, R, V, Rn, n, j + 2, w, n, partial, h_dev, hh.data());
+      if (rc) return rc;
+      std::vector<double> before(R);
+      for (int r = 0; r < R; ++r) before[r] = sqrt(std::max(0.0, (double)hh[(size_t)r * (j + 2) + j + 1]));
+      // pack h_r[0..j] with stride hld for the update
+      std::vector<T> hp((size_t)R * hld, T(0));
+      for (int r = 0; r < R; ++r)
+        for (int i = 0; i <= j; ++i) {
+          hp[(size_t)r * hld + i] = hh[(size_t)r * (j + 2) + i];
+          H[r][i * m + j] = (double)hh[(size_t)r * (j + 2) + i];
+        }
+      DFM_CUDA_CHECK(cudaMemcpyAsync(h_dev, hp.data(), sizeof(T) * R * hld, cudaMemcpyHostToDevice, c.st));
+      rc = baxpy<T>(c, R, V, Rn, n, j + 1, h_dev, hld, T(-1), w, n, partial, red_dev, &sq);
+      if (rc) return rc;
+      bool reorth = false;
+      for (int r = 0; r < R; ++r) reorth |= (active[r] && sqrt(sq[r]) < 0.5 * before[r]);
+      if (reorth) {
+        rc = bdots<T>(c, R, V, Rn, n, j + 1, w, n, partial, h_dev, hh.data());
+        if (rc) return rc;
+        std::fill(hp.begin(), hp.end(), T(0));
+        for (int r = 0; r < R; ++r)
+          for (int i = 0; i <= j; ++i) {
+            hp[(size_t)r * hld + i] = hh[(size_t)r * (j + 1) + i];
+            H[r][i * m + j] += (double)hh[(size_t)r * (j + 1) + i];
+          }
+        DFM_CUDA_CHECK(cudaMemcpyAsync(h_dev, hp.data(), sizeof(T) * R * hld, cudaMemcpyHostToDevice, c.st));
+        rc = baxpy<T>(c, R, V, Rn, n, j + 1, h_dev, hld, T(-1), w, n, partial, red_dev, &sq);
+        if (rc) return rc;
+      }
+      int still = 0;
+      for (int r = 0; r < R; ++r) {
+        const double hn = sqrt(std::max(0.0, sq[r]));
+        if (!(hn == hn)) return set_error(DFM_ERR_NONFINITE, "dfm_solve: non-finite Krylov vector");
+        f[r] = (active[r] && hn > 0) ? 1.0 / hn : 0.0;
+        if (!active[r]) continue;
+        std::vector<double>& Hr = H[r];
+        Hr[(j + 1) * m + j] = hn;
+        for (int i = 0; i < j; ++i) {
+          const double a = Hr[i * m + j], bb = Hr[(i + 1) * m + j];
+          Hr[i * m + j] = cs[r][i] * a + sn[r][i] * bb;
+          Hr[(i + 1) * m + j] = -sn[r][i] * a + cs[r][i] * bb;
+        }
+        const double den = hypot(Hr[j * m + j], Hr[(j + 1) * m + j]);
+        cs[r][j] = den > 0 ? Hr[j * m + j] / den : 1.0;
+        sn[r][j] = den > 0 ? Hr[(j + 1) * m + j] / den : 0.0;
+        Hr[j * m + j] = den;
+        Hr[(j + 1) * m + j] = 0.0;
+        g[r][j + 1] = -sn[r][j] * g[r][j];
+        g[r][j] = cs[r][j] * g[r][j];
+        kdone[r] = j + 1;
+        (*est)[r] = fabs(g[r][j + 1]) / bnorm[r];
+        if (fabs(g[r][j + 1]) <= 0.5 * tol * bnorm[r] || hn == 0.0) active[r] = 0;
+        still += active[r];
+      }
+      rc = bscale<T>(c, R, w, n, f, red_dev);
+      if (rc) return rc;
+      if (still == 0 || *iters + d >= max_iter) break;
+    }
+    // per right-hand side: y_r = H_r^{-1} g_r; x_r += p(B) V y_r
+    int kmax = 0;
+    std::vector<T> yp((size_t)R * hld, T(0));
+    for (int r = 0; r < R; ++r) {
+      const int kd = kdone[r];
+      kmax = std::max(kmax, kd);
+      std::vector<double> y(kd);
+      for (int i = kd - 1; i >= 0; --i) {
+        double acc = g[r][i];
+        for (int k2 = i + 1; k2 < kd; ++k2) acc -= H[r][i * m + k2] * y[k2];
+        y[i] = H[r][i * m + i] != 0.0 ? acc / H[r][i * m + i] : 0.0;
+      }
+      for (int i = 0; i < kd; ++i) yp[(size_t)r * hld + i] = (T)y[i];
+    }
+    if (kmax == 0) continue;
+    DFM_CUDA_CHECK(cudaMemcpyAsync(h_dev, yp.data(), sizeof(T) * R * hld, cudaMemcpyHostToDevice, c.st));
+    DFM_CUDA_CHECK(cudaMemsetAsync(tmp, 0, sizeof(T) * Rn, c.st));
+    rc = baxpy<T>(c, R, V, Rn, n, kmax, h_dev, hld, T(1), tmp, n, partial, red_dev, nullptr);
+    if (rc) return rc;
+    const T* s_src = tmp;
+    for (int k = 1; k < d; ++k) {  // Horner: s <- z + B s
+      T* dst = (k & 1) ? t1 : t2;
+      rc = apply_impl(c.op, s_src, tmp, dst, R, 1.0, c.trans, xtype, c.st);
+      if (rc) return rc;
+      s_src = dst;
+    }
+    *iters += d - 1;
+    axpby_kernel<T><<<grid_for(Rn, c.nsm), 256, 0, c.st>>>(x, T(1), x, T(1), s_src, Rn);
+    DFM_LAUNCHED();
+    DFM_CUDA_CHECK(cudaGetLastError());
+  }
+}
+
+// FP64 residuals r_r = rho0_r - (I - B) x_r for R right-hand sides:
+// rel[r] = |r_r| / |rho0_r|, abs[r] = |r_r|; the residuals are left in r + R n.
+int bresidual64(const Ctx& c, int R, const double* rho0, const double* x, double* r, double* partial, double* red_dev,
+                std::vector<double>* rel, std::vector<double>* absn) {
+  const int64_t Rn = (int64_t)R * c.n;
+  sub_kernel<<<grid_for(Rn, c.nsm), 256, 0, c.st>>>(r, rho0, x, Rn);
+  DFM_LAUNCHED();
+  DFM_CUDA_CHECK(cudaGetLastError());
+  double* r2 = r + Rn;
+  int rc = apply_impl(c.op, x, r, r2, R, 1.0, c.trans, DFM_F64, c.st);
+  if (rc) return rc;
+  std::vector<double> rn(R), bn(R);
+  rc = bdots<double>(c, R, r2, 0, c.n, 1, r2, c.n, partial, red_dev, rn.data());
+  if (rc) return rc;
+  rc = bdots<double>(c, R, rho0, 0, c.n, 1, rho0, c.n, partial, red_dev, bn.data());
+  if (rc) return rc;
+  rel->resize(R);
+  absn->resize(R);
+  for (int i = 0; i < R; ++i) {
+    (*absn)[i] = sqrt(std::max(0.0, rn[i]));
+    const double b = sqrt(std::max(0.0, bn[i]));
+    (*rel)[i] = b > 0 ? (*absn)[i] / b : (*absn)[i];
+  }
+  return DFM_OK;
+}
 }  // namespace
 }  // namespace dfm
 
@@ -455,24 +798,105 @@ extern "C" int dfm_solve(const dfm_op* op, const double* rho0, int R, double* rh
   if (method == DFM_SOLVE_GMRES_IR && op->precision != DFM_F32)
     return set_error(DFM_ERR_UNSUPPORTED, "dfm_solve: GMRES_IR needs an FP32 operator");
   if (method < 0 || method > 2) return set_error(DFM_ERR_ARG, "dfm_solve: unknown method");
+  // right-hand sides solved in lockstep (GMRES_IR with R > 1): group size
+  // capped so that the FP32 Krylov basis of a group stays within 24 GiB
+  const bool batched = (method == DFM_SOLVE_GMRES_IR && R > 1);
+  int Rg = 1;
+  if (batched) {
+    const int64_t per_rhs = (int64_t)(m + 6) * n * 4;
+    const int64_t cap = opts->batch > 0 ? opts->batch : 16;
+    Rg = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)R, cap, (int64_t(24) << 30) / per_rhs}));
+  }
   // workspace: FP64 vectors (x scratch, residual x2), Krylov basis in the inner precision
   const bool inner64 = (method == DFM_SOLVE_GMRES && op->precision == DFM_F64);
   const int64_t es = inner64 ? 8 : 4;
+  const int64_t hcap = (int64_t)Rg * (kMaxKrylov + 8);
   int64_t bytes = 0;
-  bytes += 4 * n * 8 + 4096;                            // r (2n), tmp64 (n), xold (n)
-  const int64_t inner_bytes = (int64_t)(m + 7) * n * es + 8 * 256;  // V (m+1), tmp, t1, t2, b, x (+ alignment)
+  bytes += (2 * (int64_t)Rg + 2) * n * 8 + 4096;          // r (2 Rg n), tmp64 (n), xold (n)
+  const int64_t inner_bytes = (int64_t)(m + 7) * Rg * n * es + 8 * 256;  // V (m+1), tmp, t1, t2, b, x
   bytes += inner_bytes + 4096;
-  bytes += ((int64_t)kRedBlocks * (kMaxKrylov + 8) + 2 * (kMaxKrylov + 8) + 256) * 8 + 4096;  // partials, h, red
+  const int64_t part_elems = std::max<int64_t>((int64_t)kRedBlocks * (kMaxKrylov + 8), (int64_t)kBRedBlocks * hcap);
+  bytes += (part_elems + 2 * hcap + 2 * Rg + 256) * 8 + 4096;  // partials, h, red
   int rc = ensure_work(op, bytes + 8 * 256);
   if (rc) return rc;
   Work W{reinterpret_cast<char*>(op->swork)};
-  double* r64 = W.take<double>(2 * n);
+  double* r64 = W.take<double>(2 * (int64_t)Rg * n);
   double* tmp64 = W.take<double>(n);
   double* xold = W.take<double>(n);
-  double* part64 = W.take<double>((int64_t)kRedBlocks * (kMaxKrylov + 8));
-  double* h64 = W.take<double>(2 * (kMaxKrylov + 8));
-  double* red64 = W.take<double>(8);
+  double* part64 = W.take<double>(part_elems);
+  double* h64 = W.take<double>(2 * hcap);
+  double* red64 = W.take<double>(std::max(8, 2 * Rg));
   char* inner_base = W.take<char>(inner_bytes);
+  if (batched) {
+    Work Wi{inner_base};
+    float* V = Wi.take<float>((int64_t)(m + 1) * Rg * n);
+    float* tmp = Wi.take<float>((int64_t)Rg * n);
+    float* t1 = Wi.take<float>((int64_t)Rg * n);
+    float* t2 = Wi.take<float>((int64_t)Rg * n);
+    float* bf = Wi.take<float>((int64_t)Rg * n);
+    float* xf = Wi.take<float>((int64_t)Rg * n);
+    float* part32 = reinterpret_cast<float*>(part64);
+    float* h32 = reinterpret_cast<float*>(h64);
+    float* red32 = reinterpret_cast<float*>(red64);
+    dfm_solve_info ai{0, 0, 0.0};
+    int status = DFM_OK;
+    for (int g0 = 0; g0 < R; g0 += Rg) {
+      const int Rc = std::min(Rg, R - g0);
+      const double* b = rho0 + (int64_t)g0 * n;
+      double* x = rho + (int64_t)g0 * n;
+      if (!opts->use_x0) DFM_CUDA_CHECK(cudaMemsetAsync(x, 0, sizeof(double) * Rc * n, c.st));
+      int iters = 0, outer = 0;
+      std::vector<double> rel, absn, est;
+      int gs = DFM_OK;
+      while (true) {
+        rc = bresidual64(c, Rc, b, x, r64, part64, red64, &rel, &absn);
+        if (rc) return rc;
+        double worst = 0.0;
+        bool bad = false;
+        for (int r = 0; r < Rc; ++r) {
+          bad |= !(rel[r] == rel[r]) || isinf(rel[r]);
+          worst = std::max(worst, rel[r]);
+        }
+        if (bad) {
+          gs = set_error(DFM_ERR_NONFINITE, "dfm_solve: non-finite residual");
+          break;
+        }
+        if (worst <= opts->tol) break;
+        if (iters >= max_iter || outer > 200) {
+          gs = set_error(DFM_ERR_NOT_CONVERGED, "dfm_solve: batched refinement reached max_iter");
+          break;
+        }
+        std::vector<double> sdown(Rc), sup(Rc);
+        for (int r = 0; r < Rc; ++r) {
+          const bool act = rel[r] > opts->tol && absn[r] > 0;
+          sdown[r] = act ? 1.0 / absn[r] : 0.0;
+          sup[r] = act ? absn[r] : 0.0;
+        }
+        DFM_CUDA_CHECK(cudaMemcpyAsync(red64, sdown.data(), sizeof(double) * Rc, cudaMemcpyHostToDevice, c.st));
+        bto_f32_kernel<<<dim3(grid_for(n, c.nsm), Rc), 256, 0, c.st>>>(bf, r64 + (int64_t)Rc * n, red64, n);
+        DFM_LAUNCHED();
+        DFM_CUDA_CHECK(cudaGetLastError());
+        DFM_CUDA_CHECK(cudaMemsetAsync(xf, 0, sizeof(float) * Rc * n, c.st));
+        const double itol = std::max(inner_tol, 0.3 * opts->tol / std::max(worst, 1e-300));
+        int gi = gmres_batched<float>(c, Rc, bf, xf, itol, m, poly, max_iter, &iters, &est, V, tmp, t1, t2, h32,
+                                      part32, red32);
+        if (gi != DFM_OK && gi != DFM_ERR_NOT_CONVERGED) return gi;
+        DFM_CUDA_CHECK(cudaMemcpyAsync(red64, sup.data(), sizeof(double) * Rc, cudaMemcpyHostToDevice, c.st));
+        badd_f32_kernel<<<dim3(grid_for(n, c.nsm), Rc), 256, 0, c.st>>>(x, xf, red64, n);
+        DFM_LAUNCHED();
+        DFM_CUDA_CHECK(cudaGetLastError());
+        ++outer;
+      }
+      double worst = 0.0;
+      for (double v : rel) worst = std::max(worst, v);
+      ai.iters += iters;
+      ai.outer += outer;
+      ai.resid = std::max(ai.resid, worst);
+      if (gs != DFM_OK && status == DFM_OK) status = gs;
+    }
+    if (info) *info = ai;
+    return status;
+  }
   dfm_solve_info acc_info{0, 0, 0.0};
   int status = DFM_OK;
   for (int s = 0; s < R && status != DFM_ERR_NONFINITE; ++s) {

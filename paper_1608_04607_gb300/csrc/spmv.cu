@@ -64,7 +64,8 @@ spmv_t_kernel(const TV* __restrict__ vals, int64_t row_stride, const int32_t* __
 // ---------------------------------------------------------------------------
 constexpr int kStages = 4;
 constexpr int kMaxStagedRhs = 4;  // right-hand sides staged per operator pass
-constexpr long long kWaitPolls = 1ll << 24;
+constexpr int kConsumerWarps = 4;  // computing warps per block (plus one producer warp)
+constexpr long long kWaitPolls = 1ll << 22;
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -99,54 +100,88 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
   return false;
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// Warp-specialised pipeline.  Warp 0 is the producer: for each of the block's
+// tiles it waits until the stage is free (`empty` barrier, one arrival per
+// consumer warp), reads the tile's row map (one coalesced load by the lanes),
+// and issues the bulk copies (operator rows; per row and right-hand side the
+// source tet's 4 x NB coefficients), all completing on the stage's `full`
+// barrier.  Warps 1..kConsumerWarps compute.  All waits are bounded; the
+// producer drains its outstanding copies (bounded) before the block exits.
 template <int NB, typename TV, typename TX, typename TA>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(32 * (kConsumerWarps + 1))
 spmv_tma_kernel(const TV* __restrict__ vals, int64_t row_stride, const int32_t* __restrict__ recv, int64_t nrows,
                 int rows_per_tile, int stages, const TX* __restrict__ x, const TX* x0, TX* y, int R, TA alpha,
                 int* __restrict__ err) {
-  // shared memory: [mbarriers | recv per stage | stage buffers]; a stage holds
-  // the tile's operator rows followed by, per right-hand side and tile row, the
-  // 4 x NB coefficients of the row's source tet (one contiguous 16-byte-aligned
-  // block of x, fetched by its own bulk copy)
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
-  int32_t* s_recv = reinterpret_cast<int32_t*>(smem_raw + 64);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw);
+  uint64_t* empty = full + kStages;
+  int32_t* s_recv = reinterpret_cast<int32_t*>(smem_raw + 128);
   constexpr int NB2 = NB * NB;
   const int64_t vals_bytes = (int64_t)rows_per_tile * row_stride * (int64_t)sizeof(TV);
   const int64_t xblk = 4 * NB * (int64_t)sizeof(TX);
   const int64_t stage_bytes = vals_bytes + (int64_t)R * rows_per_tile * xblk;
-  unsigned char* stage0 = smem_raw + 64 + ((stages * rows_per_tile * 4 + 127) / 128) * 128 + 64;
+  unsigned char* stage0 = smem_raw + 128 + ((stages * rows_per_tile * 4 + 127) / 128) * 128;
   const int64_t ntiles = (nrows + rows_per_tile - 1) / rows_per_tile;
   const int64_t mine = ntiles > (int64_t)blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < stages; ++s) mbar_init(&bars[s], 1);
+    for (int s = 0; s < stages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kConsumerWarps);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  auto issue = [&](int64_t i) {
-    const int64_t tile = blockIdx.x + i * (int64_t)gridDim.x;
+  if (warp == 0) {
+    // ---------------- producer ----------------
+    int64_t issued = 0;
+    bool ok = true;
+    for (int64_t i = 0; i < mine && ok; ++i) {
+      const int s = (int)(i % stages);
+      if (i >= stages) ok = mbar_wait_bounded(&empty[s], (unsigned)(((i / stages) - 1) & 1));
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) break;
+      const int64_t R0 = (blockIdx.x + i * (int64_t)gridDim.x) * rows_per_tile;
+      const int64_t left = nrows - R0;
+      const int nr = left < rows_per_tile ? (int)left : rows_per_tile;
+      unsigned char* st = stage0 + s * stage_bytes;
+      int32_t* rs = s_recv + s * rows_per_tile;
+      for (int r = lane; r < nr; r += 32) rs[r] = recv[R0 + r];
+      __syncwarp();  // the row map is written before lane 0's arrive publishes the stage
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      if (lane == 0) {
+        const unsigned vb = (unsigned)(nr * row_stride * (int64_t)sizeof(TV));
+        mbar_arrive_expect_tx(&full[s], vb + (unsigned)(R * nr * xblk));
+        bulk_copy_g2s(st, vals + R0 * row_stride, vb, &full[s]);
+      }
+      for (int r = lane; r < nr; r += 32)
+        for (int rhs = 0; rhs < R; ++rhs)
+          bulk_copy_g2s(st + vals_bytes + ((int64_t)rhs * rows_per_tile + r) * xblk,
+                        x + ((int64_t)rhs * nrows + 4 * (int64_t)(rs[r] >> 2)) * NB, (unsigned)xblk, &full[s]);
+      issued = i + 1;
+    }
+    if (!ok && lane == 0) atomicOr(err, 1);
+    // drain: every issued stage must have landed before the block's shared memory goes away
+    if (lane == 0)
+      for (int64_t j = (issued > stages ? issued - stages : 0); j < issued; ++j)
+        mbar_wait_bounded(&full[j % stages], (unsigned)((j / stages) & 1));
+    return;
+  }
+  // ---------------- consumers ----------------
+  const int ctid = threadIdx.x - 32;
+  const int nthreads = 32 * kConsumerWarps;
+  for (int64_t i = 0; i < mine; ++i) {
     const int s = (int)(i % stages);
-    const int64_t R0 = tile * rows_per_tile;
-    const int64_t left = nrows - R0;
-    const int nr = left < rows_per_tile ? (int)left : rows_per_tile;
-    unsigned char* st = stage0 + s * stage_bytes;
-    int32_t* rs = s_recv + s * rows_per_tile;
-    for (int r = 0; r < nr; ++r) rs[r] = recv[R0 + r];
-    const unsigned vb = (unsigned)(nr * row_stride * (int64_t)sizeof(TV));
-    mbar_arrive_expect_tx(&bars[s], vb + (unsigned)(R * nr * xblk));
-    bulk_copy_g2s(st, vals + R0 * row_stride, vb, &bars[s]);
-    for (int rhs = 0; rhs < R; ++rhs)
-      for (int r = 0; r < nr; ++r)
-        bulk_copy_g2s(st + vals_bytes + ((int64_t)rhs * rows_per_tile + r) * xblk,
-                      x + ((int64_t)rhs * nrows + 4 * (int64_t)(rs[r] >> 2)) * NB, (unsigned)xblk, &bars[s]);
-  };
-  if (threadIdx.x == 0)
-    for (int64_t i = 0; i < mine && i < stages; ++i) issue(i);
-  int64_t i = 0;
-  for (; i < mine; ++i) {
-    const int s = (int)(i % stages);
-    const bool ok = mbar_wait_bounded(&bars[s], (unsigned)((i / stages) & 1));
-    if (!__syncthreads_and(ok)) break;
+    const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&full[s], (unsigned)((i / stages) & 1)));
+    if (!ok) {
+      if (lane == 0) atomicOr(err, 1);
+      break;
+    }
     const unsigned char* st = stage0 + s * stage_bytes;
     const TV* tv = reinterpret_cast<const TV*>(st);
     const TX* tx = reinterpret_cast<const TX*>(st + vals_bytes);
@@ -154,41 +189,31 @@ spmv_tma_kernel(const TV* __restrict__ vals, int64_t row_stride, const int32_t* 
     const int64_t R0 = (blockIdx.x + i * (int64_t)gridDim.x) * rows_per_tile;
     const int64_t left = nrows - R0;
     const int nr = left < rows_per_tile ? (int)left : rows_per_tile;
-    for (int e = threadIdx.x; e < nr * NB; e += blockDim.x) {
+    for (int e = ctid; e < nr * NB; e += nthreads) {
       const int r = e / NB;
       const int a = e - r * NB;
       const int lp = rs[r] & 3;
       const TV* blk = tv + (int64_t)r * row_stride + a * NB;
       for (int rhs = 0; rhs < R; ++rhs) {
         const TX* xs = tx + ((int64_t)rhs * rows_per_tile + r) * 4 * NB;
-        TA acc = TA(0);
+        TA acc[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
           const int l = k + (k >= lp ? 1 : 0);
           const TV* bk = blk + k * NB2;
           const TX* xl = xs + l * NB;
+          TA a0 = TA(0);
 #pragma unroll
-          for (int b = 0; b < NB; ++b) acc = fma((TA)bk[b], (TA)xl[b], acc);
+          for (int b = 0; b < NB; ++b) a0 = fma((TA)bk[b], (TA)xl[b], a0);
+          acc[k] = a0;
         }
         const int64_t o = ((int64_t)rhs * nrows + R0 + r) * NB + a;
         const TA base = x0 ? (TA)x0[o] : TA(0);
-        y[o] = (TX)(base + alpha * acc);
+        y[o] = (TX)(base + alpha * ((acc[0] + acc[1]) + acc[2]));
       }
     }
-    __syncthreads();  // every thread is done with stage s
-    if (threadIdx.x == 0 && i + stages < mine) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue(i + stages);
-    }
-  }
-  if (i < mine) {
-    // a wait timed out: record it and wait (bounded) for this block's copies in flight
-    if (threadIdx.x == 0) {
-      atomicOr(err, 1);
-      for (int64_t j = i; j < mine && j < i + stages; ++j)
-        mbar_wait_bounded(&bars[j % stages], (unsigned)((j / stages) & 1));
-    }
-    __syncthreads();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
   }
 }
 
@@ -223,19 +248,19 @@ int launch(const dfm_op* op, const TX* x, const TX* x0, TX* y, int R, double alp
     while (rpt > 1 && rpt * row_bytes * 2 > budget) --rpt;  // keep at least two stages
     int stages = (int)std::min<int64_t>(kStages, budget / (rpt * row_bytes));
     if (stages < 1) return set_error(DFM_ERR_UNSUPPORTED, "dfm_apply: an operator row does not fit shared memory");
-    const size_t smem = 64 + ((stages * rpt * 4 + 127) / 128) * 128 + 64 + (size_t)stages * rpt * row_bytes;
+    const size_t smem = 128 + ((stages * rpt * 4 + 127) / 128) * 128 + (size_t)stages * rpt * row_bytes;
     int rc = DFM_OK;
     auto go = [&](auto kernel) -> int {
       DFM_CUDA_CHECK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       int per_sm = 0;
-      DFM_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem));
+      DFM_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 32 * (kConsumerWarps + 1), smem));
       if (per_sm < 1) per_sm = 1;
       const int64_t ntiles = (op->nrows + rpt - 1) / rpt;
       const int64_t grid = std::min<int64_t>(ntiles, (int64_t)nsm * per_sm);
       {
         ::dfm::KernelTimer timer_(sizeof(TX) == 8 ? DFM_KERNEL_SPMV64 : DFM_KERNEL_SPMV, st);
-        kernel<<<(unsigned)grid, kThreads, smem, st>>>(vals, op->row_stride, recv, op->nrows, rpt, stages, x, x0, y, R,
-                                                       (TA)alpha, op->dev_err);
+        kernel<<<(unsigned)grid, 32 * (kConsumerWarps + 1), smem, st>>>(vals, op->row_stride, recv, op->nrows, rpt,
+                                                                         stages, x, x0, y, R, (TA)alpha, op->dev_err);
       }
       DFM_LAUNCHED();
       return DFM_OK;

@@ -55,7 +55,7 @@ class OpInfo(ctypes.Structure):
 class SolveOpts(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("restart", ctypes.c_int), ("use_x0", ctypes.c_int), ("inner_tol", ctypes.c_double),
-                ("transpose", ctypes.c_int), ("poly_degree", ctypes.c_int)]
+                ("transpose", ctypes.c_int), ("poly_degree", ctypes.c_int), ("batch", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -248,13 +248,13 @@ class Operator:
         return y
 
     def solve(self, rho0, method=GMRES_IR, tol=1e-8, max_iter=0, restart=0, x0=None, inner_tol=0.0,
-              raise_on_nonconvergence=True, transpose=False, poly_degree=0):
+              raise_on_nonconvergence=True, transpose=False, poly_degree=0, batch=0):
         """rho = (I - B)^{-1} rho0 (FP64, [R, rows, nb] or [rows, nb]); returns (rho, SolveInfo)."""
         torch = self._torch
         R = 1 if rho0.dim() == 2 else rho0.shape[0]
         rho = torch.empty_like(rho0) if x0 is None else x0.clone()
         o = SolveOpts(method=method, tol=tol, max_iter=max_iter, restart=restart, use_x0=int(x0 is not None),
-                      inner_tol=inner_tol, transpose=int(bool(transpose)), poly_degree=poly_degree)
+                      inner_tol=inner_tol, transpose=int(bool(transpose)), poly_degree=poly_degree, batch=batch)
         info = SolveInfo()
         rc = _lib.dfm_solve(self._h, _ptr(rho0), R, _ptr(rho), ctypes.byref(o), _stream(), ctypes.byref(info))
         if rc == DFM_ERR_NOT_CONVERGED and not raise_on_nonconvergence:
@@ -271,7 +271,7 @@ class Operator:
         lam = torch.empty((self.n_rows, self.nb), dtype=torch.float64, device="cuda")
         dj = torch.empty((R, self.mesh.n_tets), dtype=torch.float64, device="cuda")
         o = SolveOpts(method=method, tol=tol, max_iter=max_iter, restart=restart, use_x0=0, inner_tol=inner_tol,
-                      transpose=1, poly_degree=poly_degree)
+                      transpose=1, poly_degree=poly_degree, batch=0)
         info = SolveInfo()
         _check(_lib.dfm_adjoint(self._h, ctypes.byref(self._p), _ptr(rho), R, _ptr(gvec), _ptr(dgvec), _ptr(lam),
                                 _ptr(dj), ctypes.byref(o), _stream(), ctypes.byref(info)), "dfm_adjoint")
