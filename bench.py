@@ -455,6 +455,74 @@ def run_apply(args):
                       "frac": ach / float(peaks.get("hbm_gbs", HBM_PEAK_FALLBACK)), "peak_source": src}))
 
 
+def run_adjoint(args):
+    """Adjoint workload: gradient of the mean receiver-region interior density
+    with respect to per-tet damping (log-normal field) on the 40^3 Kuhn cube
+    (384,000 tets, Np = 3).  Times forward assembly + solve, the receiver
+    functional and the adjoint (transposed solve + fused dB/dmu contraction);
+    optionally checks the gradient against central differences of the GPU
+    forward solve on the sampled elements (step 1e-4)."""
+    import torch
+
+    from paper_1608_04607_gb300 import dfm
+    from paper_1608_04607_gb300.inputs import workload
+
+    torch.cuda.set_device(0)
+    wname = args.workload if args.workload != WORKLOAD else "kuhn40_np3_adjoint"
+    w = workload(wname)
+    m = w["mesh"]
+    Np = w["Np"]
+    mu = torch.tensor(w["mu"], device="cuda")
+    rows = np.asarray(w["sources"], dtype=np.int64)
+    receiver = w["receiver"]
+    tol = args.tol if args.tol else w["tol"]
+    mesh = dfm.Mesh(m.verts, m.tets, refl=w["refl"])
+
+    def forward(mu_vec, op=None):
+        if op is None:
+            op = dfm.Operator(mesh, Np, mu=mu_vec, precision=dfm.F32)
+        else:
+            op.reassemble(mu_vec)
+        rho0 = dfm.source(mesh, Np, rows)
+        rho, info = op.solve(rho0, method=dfm.GMRES_IR, tol=tol)
+        g, dg = dfm.interior_density(mesh, Np, receiver, weights=1.0 / len(receiver), mu=mu_vec)
+        return op, rho, g, dg, info
+
+    op, rho, g, dg, info = forward(mu)
+    lam, dj, ainfo = op.adjoint(rho, g, dg, tol=tol)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev[0].record()
+    op, rho, g, dg, info = forward(mu, op)
+    ev[1].record()
+    lam, dj, ainfo = op.adjoint(rho, g, dg, tol=tol)
+    ev[2].record()
+    torch.cuda.synchronize()
+    J = float((g * rho[0]).sum())
+    res = {"mode": "adjoint", "workload": wname, "n_tets": int(m.n_tets), "nb": op.nb, "J": J,
+           "forward_ms": ev[0].elapsed_time(ev[1]), "adjoint_ms": ev[1].elapsed_time(ev[2]),
+           "forward_applications": info.iters, "adjoint_applications": ainfo.iters,
+           "grad_abs_max": float(dj.abs().max())}
+    if args.fd:
+        grad = dj[0].cpu().numpy()
+        els = w["fd"][:args.fd]
+        rel = []
+        h = 1e-4
+        for e in els:
+            vals = []
+            for sgn in (1, -1):
+                mp = mu.clone()
+                mp[int(e)] += sgn * h
+                _, r2, g2, _, _ = forward(mp, op)
+                vals.append(float((g2 * r2[0]).sum()))
+            fd = (vals[0] - vals[1]) / (2 * h)
+            rel.append(abs(grad[int(e)] - fd) / max(abs(fd), 1e-6 * res["grad_abs_max"]))
+        res["fd_elements"] = len(els)
+        res["fd_max_rel_err"] = float(max(rel))
+        res["fd_median_rel_err"] = float(np.median(rel))
+    print(json.dumps(res))
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -470,12 +538,15 @@ def main():
     ap.add_argument("--no-comparator", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--ref-apps", type=int, default=600)
-    ap.add_argument("--mode", choices=["solve", "apply"], default="solve")
+    ap.add_argument("--mode", choices=["solve", "apply", "adjoint"], default="solve")
+    ap.add_argument("--fd", type=int, default=0, help="adjoint mode: elements checked by central differences")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
     elif args.mode == "apply":
         run_apply(args)
+    elif args.mode == "adjoint":
+        run_adjoint(args)
     else:
         run_gpu(args)
 
