@@ -478,13 +478,16 @@ def run_adjoint(args):
     tol = args.tol if args.tol else w["tol"]
     mesh = dfm.Mesh(m.verts, m.tets, refl=w["refl"])
 
-    def forward(mu_vec, op=None):
+    def forward(mu_vec, op=None, fp64=False):
         if op is None:
-            op = dfm.Operator(mesh, Np, mu=mu_vec, precision=dfm.F32)
+            op = dfm.Operator(mesh, Np, mu=mu_vec, precision=dfm.F64 if fp64 else dfm.F32)
         else:
             op.reassemble(mu_vec)
         rho0 = dfm.source(mesh, Np, rows)
-        rho, info = op.solve(rho0, method=dfm.GMRES_IR, tol=tol)
+        if fp64:
+            rho, info = op.solve(rho0, method=dfm.GMRES, tol=1e-12, poly_degree=16)
+        else:
+            rho, info = op.solve(rho0, method=dfm.GMRES_IR, tol=tol)
         g, dg = dfm.interior_density(mesh, Np, receiver, weights=1.0 / len(receiver), mu=mu_vec)
         return op, rho, g, dg, info
 
@@ -504,19 +507,24 @@ def run_adjoint(args):
            "forward_applications": info.iters, "adjoint_applications": ainfo.iters,
            "grad_abs_max": float(dj.abs().max())}
     if args.fd:
+        # central differences of the FP64 forward path (FP64 blocks, FP64 GMRES to 1e-12)
         grad = dj[0].cpu().numpy()
         els = w["fd"][:args.fd]
         rel = []
+        ok = []
         h = 1e-4
+        op64 = None
         for e in els:
             vals = []
             for sgn in (1, -1):
                 mp = mu.clone()
                 mp[int(e)] += sgn * h
-                _, r2, g2, _, _ = forward(mp, op)
+                op64, r2, g2, _, _ = forward(mp, op64, fp64=True)
                 vals.append(float((g2 * r2[0]).sum()))
             fd = (vals[0] - vals[1]) / (2 * h)
-            rel.append(abs(grad[int(e)] - fd) / max(abs(fd), 1e-6 * res["grad_abs_max"]))
+            rel.append(abs(grad[int(e)] - fd) / max(abs(fd), 1e-300))
+            ok.append(abs(grad[int(e)] - fd) <= 1e-3 * abs(fd) + 1e-6 * res["grad_abs_max"])
+        res["fd_pass"] = int(sum(ok))
         res["fd_elements"] = len(els)
         res["fd_max_rel_err"] = float(max(rel))
         res["fd_median_rel_err"] = float(np.median(rel))
