@@ -115,7 +115,7 @@ template <int NB, typename TV, typename TX, typename TA>
 __global__ void __launch_bounds__(32 * (kConsumerWarps + 1))
 spmv_tma_kernel(const TV* __restrict__ vals, int64_t row_stride, const int32_t* __restrict__ recv, int64_t nrows,
                 int rows_per_tile, int stages, const TX* __restrict__ x, const TX* x0, TX* y, int R, TA alpha,
-                int* __restrict__ err) {
+                int stage_x0, int* __restrict__ err) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw);
   uint64_t* empty = full + kStages;
@@ -123,7 +123,8 @@ spmv_tma_kernel(const TV* __restrict__ vals, int64_t row_stride, const int32_t* 
   constexpr int NB2 = NB * NB;
   const int64_t vals_bytes = (int64_t)rows_per_tile * row_stride * (int64_t)sizeof(TV);
   const int64_t xblk = 4 * NB * (int64_t)sizeof(TX);
-  const int64_t stage_bytes = vals_bytes + (int64_t)R * rows_per_tile * xblk;
+  const int64_t x0_bytes = stage_x0 ? (int64_t)R * rows_per_tile * NB * (int64_t)sizeof(TX) : 0;
+  const int64_t stage_bytes = vals_bytes + (int64_t)R * rows_per_tile * xblk + ((x0_bytes + 15) / 16) * 16;
   unsigned char* stage0 = smem_raw + 128 + ((stages * rows_per_tile * 4 + 127) / 128) * 128;
   const int64_t ntiles = (nrows + rows_per_tile - 1) / rows_per_tile;
   const int64_t mine = ntiles > (int64_t)blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
@@ -139,30 +140,56 @@ spmv_tma_kernel(const TV* __restrict__ vals, int64_t row_stride, const int32_t* 
   __syncthreads();
   if (warp == 0) {
     // ---------------- producer ----------------
+    // lane r handles tile row r (rows_per_tile <= 32); the row map of the next
+    // tile is loaded one iteration ahead so its latency overlaps this tile's issue
     int64_t issued = 0;
     bool ok = true;
+    auto tile_rows = [&](int64_t i, int64_t* R0, int* nr) {
+      *R0 = (blockIdx.x + i * (int64_t)gridDim.x) * rows_per_tile;
+      const int64_t left = nrows - *R0;
+      *nr = left < rows_per_tile ? (int)left : rows_per_tile;
+    };
+    int32_t next_src = 0;
+    if (mine > 0) {
+      int64_t R0;
+      int nr;
+      tile_rows(0, &R0, &nr);
+      if (lane < nr) next_src = recv[R0 + lane];
+    }
     for (int64_t i = 0; i < mine && ok; ++i) {
       const int s = (int)(i % stages);
+      int64_t R0;
+      int nr;
+      tile_rows(i, &R0, &nr);
+      const int32_t src = next_src;
+      if (i + 1 < mine) {
+        int64_t R1;
+        int n1;
+        tile_rows(i + 1, &R1, &n1);
+        if (lane < n1) next_src = recv[R1 + lane];
+      }
       if (i >= stages) ok = mbar_wait_bounded(&empty[s], (unsigned)(((i / stages) - 1) & 1));
       ok = __all_sync(0xffffffffu, ok);
       if (!ok) break;
-      const int64_t R0 = (blockIdx.x + i * (int64_t)gridDim.x) * rows_per_tile;
-      const int64_t left = nrows - R0;
-      const int nr = left < rows_per_tile ? (int)left : rows_per_tile;
       unsigned char* st = stage0 + s * stage_bytes;
       int32_t* rs = s_recv + s * rows_per_tile;
-      for (int r = lane; r < nr; r += 32) rs[r] = recv[R0 + r];
+      if (lane < nr) rs[lane] = src;
       __syncwarp();  // the row map is written before lane 0's arrive publishes the stage
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      const unsigned x0b = stage_x0 ? (unsigned)((int64_t)R * nr * NB * (int64_t)sizeof(TX)) : 0u;
       if (lane == 0) {
         const unsigned vb = (unsigned)(nr * row_stride * (int64_t)sizeof(TV));
-        mbar_arrive_expect_tx(&full[s], vb + (unsigned)(R * nr * xblk));
+        mbar_arrive_expect_tx(&full[s], vb + (unsigned)(R * nr * xblk) + x0b);
         bulk_copy_g2s(st, vals + R0 * row_stride, vb, &full[s]);
+        for (int rhs = 0; rhs < R && stage_x0; ++rhs)
+          bulk_copy_g2s(st + vals_bytes + (int64_t)R * rows_per_tile * xblk +
+                            (int64_t)rhs * rows_per_tile * NB * (int64_t)sizeof(TX),
+                        x0 + ((int64_t)rhs * nrows + R0) * NB, (unsigned)(nr * NB * sizeof(TX)), &full[s]);
       }
-      for (int r = lane; r < nr; r += 32)
+      if (lane < nr)
         for (int rhs = 0; rhs < R; ++rhs)
-          bulk_copy_g2s(st + vals_bytes + ((int64_t)rhs * rows_per_tile + r) * xblk,
-                        x + ((int64_t)rhs * nrows + 4 * (int64_t)(rs[r] >> 2)) * NB, (unsigned)xblk, &full[s]);
+          bulk_copy_g2s(st + vals_bytes + ((int64_t)rhs * rows_per_tile + lane) * xblk,
+                        x + ((int64_t)rhs * nrows + 4 * (int64_t)(src >> 2)) * NB, (unsigned)xblk, &full[s]);
       issued = i + 1;
     }
     if (!ok && lane == 0) atomicOr(err, 1);
@@ -185,6 +212,7 @@ spmv_tma_kernel(const TV* __restrict__ vals, int64_t row_stride, const int32_t* 
     const unsigned char* st = stage0 + s * stage_bytes;
     const TV* tv = reinterpret_cast<const TV*>(st);
     const TX* tx = reinterpret_cast<const TX*>(st + vals_bytes);
+    const TX* tx0 = reinterpret_cast<const TX*>(st + vals_bytes + (int64_t)R * rows_per_tile * xblk);
     const int32_t* rs = s_recv + s * rows_per_tile;
     const int64_t R0 = (blockIdx.x + i * (int64_t)gridDim.x) * rows_per_tile;
     const int64_t left = nrows - R0;
@@ -208,7 +236,7 @@ spmv_tma_kernel(const TV* __restrict__ vals, int64_t row_stride, const int32_t* 
           acc[k] = a0;
         }
         const int64_t o = ((int64_t)rhs * nrows + R0 + r) * NB + a;
-        const TA base = x0 ? (TA)x0[o] : TA(0);
+        const TA base = stage_x0 ? (TA)tx0[((int64_t)rhs * rows_per_tile + r) * NB + a] : (x0 ? (TA)x0[o] : TA(0));
         y[o] = (TX)(base + alpha * ((acc[0] + acc[1]) + acc[2]));
       }
     }
@@ -242,13 +270,22 @@ int launch(const dfm_op* op, const TX* x, const TX* x0, TX* y, int R, double alp
       }
       return DFM_OK;
     }
-    int rpt = rows_per_tile_for(op->nb);
-    const int64_t row_bytes = op->row_stride * (int64_t)sizeof(TV) + (int64_t)R * 4 * op->nb * (int64_t)sizeof(TX);
+    int rpt = std::min(32, rows_per_tile_for(op->nb));
+    // x0 rides in the pipeline when every tile's slice is a whole number of 16-byte units
+    const int stage_x0 = (x0 && !(reinterpret_cast<uintptr_t>(x0) & 15) &&
+                          ((int64_t)op->nb * (int64_t)sizeof(TX)) % 16 == 0)
+                             ? 1
+                             : (x0 && !(reinterpret_cast<uintptr_t>(x0) & 15) &&
+                                (op->nrows % rpt) == 0 && ((int64_t)rpt * op->nb * (int64_t)sizeof(TX)) % 16 == 0)
+                                   ? 1
+                                   : 0;
+    const int64_t row_bytes = op->row_stride * (int64_t)sizeof(TV) + (int64_t)R * 4 * op->nb * (int64_t)sizeof(TX) +
+                              (stage_x0 ? (int64_t)R * op->nb * (int64_t)sizeof(TX) : 0);
     const int64_t budget = 200 * 1024 - 1024;
     while (rpt > 1 && rpt * row_bytes * 2 > budget) --rpt;  // keep at least two stages
     int stages = (int)std::min<int64_t>(kStages, budget / (rpt * row_bytes));
     if (stages < 1) return set_error(DFM_ERR_UNSUPPORTED, "dfm_apply: an operator row does not fit shared memory");
-    const size_t smem = 128 + ((stages * rpt * 4 + 127) / 128) * 128 + (size_t)stages * rpt * row_bytes;
+    const size_t smem = 128 + ((stages * rpt * 4 + 127) / 128) * 128 + (size_t)stages * (rpt * row_bytes + 16);
     int rc = DFM_OK;
     auto go = [&](auto kernel) -> int {
       DFM_CUDA_CHECK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -260,7 +297,8 @@ int launch(const dfm_op* op, const TX* x, const TX* x0, TX* y, int R, double alp
       {
         ::dfm::KernelTimer timer_(sizeof(TX) == 8 ? DFM_KERNEL_SPMV64 : DFM_KERNEL_SPMV, st);
         kernel<<<(unsigned)grid, 32 * (kConsumerWarps + 1), smem, st>>>(vals, op->row_stride, recv, op->nrows, rpt,
-                                                                         stages, x, x0, y, R, (TA)alpha, op->dev_err);
+                                                                         stages, x, x0, y, R, (TA)alpha, stage_x0,
+                                                                         op->dev_err);
       }
       DFM_LAUNCHED();
       return DFM_OK;
