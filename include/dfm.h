@@ -137,6 +137,11 @@ typedef struct {
   int quad_order;       /* Gauss-Legendre order per direction patch; 0 = Np + 6 */
   double max_patch_deg; /* split direction patches until every edge <= this angle; 0 = 60 */
   int precision;        /* DFM_F64 or DFM_F32 (FP32 arithmetic, FP64 geometry set-up) */
+  int moment;           /* 0: B itself.  k = 1..3: the k-th damping derivative d^k B / d mu^k at the
+                           given damping (every tet's mu moved together), i.e. the spatial factor
+                           2|OBC| phi2(mu L_O) replaced by 2|OBC| L_O^k phi2^(k)(mu L_O).  Then
+                           B(mu_c + e) = sum_k e^k/k! B^(k): Taylor moments that let right-hand
+                           sides with different uniform damping share one set of operators. */
 } dfm_params;
 
 typedef struct {
@@ -173,6 +178,15 @@ int dfm_op_copy_vals(const dfm_op* op, void* dst, int64_t bytes, void* stream);
 int dfm_apply(const dfm_op* op, const void* x, const void* x0, void* y, int R, double alpha, int trans, int xtype,
               void* stream);
 
+/* Several operators applied together, with per-right-hand-side weights:
+ *   y_r = x0_r + alpha * sum_k coef_host[r * K + k] B_k x_r,  r < R, k < K <= 4.
+ * ops: K FP32 operators of the same mesh and Np (e.g. the damping moments
+ * B^(k) of dfm_params.moment, with coef = (mu_r - mu_c)^k / k!); x, x0, y as
+ * for dfm_apply (forward only).  Every operator tile is streamed once per pass
+ * over up to 16 right-hand sides.  Asynchronous. */
+int dfm_apply_combo(const dfm_op* const* ops, int K, const double* coef_host, const void* x, const void* x0, void* y,
+                    int R, double alpha, int xtype, void* stream);
+
 /* Galerkin coefficients of unit isotropic sources (Sec. 3.1-3.2): for source
  * s, rho0[s][row_s][(0,0)] = sqrt(|T_row_s|) and zero elsewhere.
  * rows_host: HOST int64 [n_src] boundary (or any) rows; rho0: device FP64
@@ -207,6 +221,14 @@ typedef struct {
  * DFM_ERR_NONFINITE if a residual is not finite. */
 int dfm_solve(const dfm_op* op, const double* rho0, int R, double* rho, const dfm_solve_opts* opts, void* stream,
               dfm_solve_info* info);
+
+/* dfm_solve for right-hand sides with their own operators
+ * B_r = sum_k coef_host[r * K + k] B_k (see dfm_apply_combo): the stationary
+ * densities rho_r = (I - B_r)^{-1} rho0_r, batched as in dfm_solve (every
+ * operator pass serves a group of right-hand sides).  opts->method must be
+ * DFM_SOLVE_GMRES_IR, no transpose.  Errors as dfm_solve. */
+int dfm_solve_combo(const dfm_op* const* ops, int K, const double* coef_host, const double* rho0, int R, double* rho,
+                    const dfm_solve_opts* opts, void* stream, dfm_solve_info* info);
 
 /* Interior density functional (Sec. 4.1, Eq. IntDens, c = 1): for each listed
  * tet e, the coefficients g_e of

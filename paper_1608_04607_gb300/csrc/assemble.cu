@@ -96,11 +96,13 @@ struct WarpSmem {
   alignas(16) T zp[32 * Tile<NP>::LD];  // Z(p) per node
 };
 
-template <int NP, typename T>
+// QC > 0 fixes the per-patch Gauss order at compile time (the default
+// N_p + 6), which turns the node-index divisions into multiplies.
+template <int NP, typename T, int QC>
 __global__ void __launch_bounds__(kWarps * 32)
 assemble_kernel(const PairConst* __restrict__ pairs, int64_t npairs, const double* __restrict__ gl_x,
-                const double* __restrict__ gl_w, int q, float cos_max, T* __restrict__ vals, int64_t row_stride,
-                unsigned long long* __restrict__ node_count) {
+                const double* __restrict__ gl_w, int q_rt, float cos_max, T* __restrict__ vals, int64_t row_stride,
+                unsigned long long* __restrict__ node_count, int moment) {
   using TL = Tile<NP>;
   constexpr int NB = TL::NB, TR = TL::TR, TC = TL::TC, LD = TL::LD;
   extern __shared__ __align__(16) unsigned char dyn_smem[];
@@ -111,6 +113,7 @@ assemble_kernel(const PairConst* __restrict__ pairs, int64_t npairs, const doubl
   const int lane = threadIdx.x & 31;
   const int wid = threadIdx.x >> 5;
   WarpSmem<NP, T>& S = smem[wid];
+  const int q = QC > 0 ? QC : q_rt;
   if (threadIdx.x < q) {
     s_x[threadIdx.x] = (T)gl_x[threadIdx.x];
     s_w[threadIdx.x] = (T)gl_w[threadIdx.x];
@@ -154,7 +157,17 @@ assemble_kernel(const PairConst* __restrict__ pairs, int64_t npairs, const doubl
           const int i = rem / q;
           const int j = rem - i * q;
           const NodeGeom<T> g = node_geom<T>(S.P.patch[pi], s_x[i], s_x[j], pc);
-          if (g.valid) wnode = s_w[i] * s_w[j] * g.jac * T(2) * g.Anab * phi2<T>(mu * g.LO);
+          if (g.valid) {
+            // S = 2 |OBC| phi2(mu L_O) (Sec. 3.3); moment k: d^k S / d mu^k = 2 |OBC| L_O^k phi2^(k)(mu L_O)
+            T sk;
+            if (moment == 0) {
+              sk = phi2<T>(mu * g.LO);
+            } else {
+              sk = phi2_deriv<T>(moment, mu * g.LO);
+              for (int e = 0; e < moment; ++e) sk *= g.LO;
+            }
+            wnode = s_w[i] * s_w[j] * g.jac * T(2) * g.Anab * sk;
+          }
           const T d0 = g.d0, d1 = g.d1, d2 = g.d2;
           zernike<NP, T>(d0, d1, Zp);
           const T qx = d0 * (T)pc.R1[0] + d1 * (T)pc.R1[1] + d2 * (T)pc.R1[2];
@@ -209,37 +222,48 @@ constexpr size_t assemble_smem_bytes() {
   return sizeof(WarpSmem<NP, T>) * kWarps + 2 * kMaxQ * sizeof(T) + 64 * sizeof(float);
 }
 
-template <int NP, typename T>
-int launch_assemble(const PairConst* pairs, int64_t npairs, const double* glx, const double* glw, int q,
-                    float cos_max, T* vals, int64_t row_stride, unsigned long long* nodes, cudaStream_t st) {
+template <int NP, typename T, int QC>
+int launch_assemble_q(const PairConst* pairs, int64_t npairs, const double* glx, const double* glw, int q,
+                      float cos_max, T* vals, int64_t row_stride, unsigned long long* nodes, int moment,
+                      cudaStream_t st) {
   constexpr size_t smem = assemble_smem_bytes<NP, T>();
   static_assert(smem <= 220 * 1024, "assembly shared memory");
-  DFM_CUDA_CHECK(cudaFuncSetAttribute(assemble_kernel<NP, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  DFM_CUDA_CHECK(
+      cudaFuncSetAttribute(assemble_kernel<NP, T, QC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int64_t blocks = (npairs + kWarps - 1) / kWarps;
   if (blocks > 0x7fffffff) return set_error(DFM_ERR_ARG, "dfm_assemble: too many face pairs");
   {
     ::dfm::KernelTimer timer_(DFM_KERNEL_ASSEMBLE, st);
-    assemble_kernel<NP, T><<<(unsigned)blocks, kWarps * 32, smem, st>>>(pairs, npairs, glx, glw, q, cos_max, vals,
-                                                                        row_stride, nodes);
+    assemble_kernel<NP, T, QC><<<(unsigned)blocks, kWarps * 32, smem, st>>>(pairs, npairs, glx, glw, q, cos_max,
+                                                                            vals, row_stride, nodes, moment);
   }
   DFM_LAUNCHED();
   DFM_CUDA_CHECK(cudaGetLastError());
   return DFM_OK;
 }
 
+template <int NP, typename T>
+int launch_assemble(const PairConst* pairs, int64_t npairs, const double* glx, const double* glw, int q,
+                    float cos_max, T* vals, int64_t row_stride, unsigned long long* nodes, int moment, cudaStream_t st) {
+  if (std::is_same<T, float>::value && q == NP + 6)
+    return launch_assemble_q<NP, T, NP + 6>(pairs, npairs, glx, glw, q, cos_max, vals, row_stride, nodes, moment,
+                                            st);
+  return launch_assemble_q<NP, T, 0>(pairs, npairs, glx, glw, q, cos_max, vals, row_stride, nodes, moment, st);
+}
+
 template <typename T>
 int dispatch_np(int Np, const PairConst* pairs, int64_t npairs, const double* glx, const double* glw, int q,
-                float cos_max, T* vals, int64_t row_stride, unsigned long long* nodes, cudaStream_t st) {
+                float cos_max, T* vals, int64_t row_stride, unsigned long long* nodes, int moment, cudaStream_t st) {
   switch (Np) {
-    case 0: return launch_assemble<0, T>(pairs, npairs, glx, glw, q, cos_max, vals, row_stride, nodes, st);
-    case 1: return launch_assemble<1, T>(pairs, npairs, glx, glw, q, cos_max, vals, row_stride, nodes, st);
-    case 2: return launch_assemble<2, T>(pairs, npairs, glx, glw, q, cos_max, vals, row_stride, nodes, st);
-    case 3: return launch_assemble<3, T>(pairs, npairs, glx, glw, q, cos_max, vals, row_stride, nodes, st);
-    case 4: return launch_assemble<4, T>(pairs, npairs, glx, glw, q, cos_max, vals, row_stride, nodes, st);
-    case 5: return launch_assemble<5, T>(pairs, npairs, glx, glw, q, cos_max, vals, row_stride, nodes, st);
-    case 6: return launch_assemble<6, T>(pairs, npairs, glx, glw, q, cos_max, vals, row_stride, nodes, st);
-    case 7: return launch_assemble<7, T>(pairs, npairs, glx, glw, q, cos_max, vals, row_stride, nodes, st);
-    case 8: return launch_assemble<8, T>(pairs, npairs, glx, glw, q, cos_max, vals, row_stride, nodes, st);
+    case 0: return launch_assemble<0, T>(pairs, npairs, glx, glw, q, cos_max, vals, row_stride, nodes, moment, st);
+    case 1: return launch_assemble<1, T>(pairs, npairs, glx, glw, q, cos_max, vals, row_stride, nodes, moment, st);
+    case 2: return launch_assemble<2, T>(pairs, npairs, glx, glw, q, cos_max, vals, row_stride, nodes, moment, st);
+    case 3: return launch_assemble<3, T>(pairs, npairs, glx, glw, q, cos_max, vals, row_stride, nodes, moment, st);
+    case 4: return launch_assemble<4, T>(pairs, npairs, glx, glw, q, cos_max, vals, row_stride, nodes, moment, st);
+    case 5: return launch_assemble<5, T>(pairs, npairs, glx, glw, q, cos_max, vals, row_stride, nodes, moment, st);
+    case 6: return launch_assemble<6, T>(pairs, npairs, glx, glw, q, cos_max, vals, row_stride, nodes, moment, st);
+    case 7: return launch_assemble<7, T>(pairs, npairs, glx, glw, q, cos_max, vals, row_stride, nodes, moment, st);
+    case 8: return launch_assemble<8, T>(pairs, npairs, glx, glw, q, cos_max, vals, row_stride, nodes, moment, st);
     default: return set_error(DFM_ERR_ARG, "dfm_assemble: Np must be in 0..8");
   }
 }
@@ -254,6 +278,7 @@ int check_params(const dfm_mesh* mesh, const dfm_params* p) {
   if (q < 1 || q > kMaxQ) return set_error(DFM_ERR_ARG, "dfm_assemble: quad_order must be in 1..32");
   const double deg = p->max_patch_deg > 0 ? p->max_patch_deg : 60.0;
   if (!(deg >= 10.0 && deg <= 180.0)) return set_error(DFM_ERR_ARG, "dfm_assemble: max_patch_deg must be in [10, 180]");
+  if (p->moment < 0 || p->moment > 3) return set_error(DFM_ERR_ARG, "dfm_assemble: moment must be in 0..3");
   return DFM_OK;
 }
 
@@ -296,9 +321,9 @@ extern "C" int dfm_assemble_into(const dfm_mesh* mesh, const dfm_params* p, dfm_
   DFM_CUDA_CHECK(cudaGetLastError());
   if (op->precision == DFM_F32)
     return dispatch_np<float>(p->Np, pairs, npairs, glx, glw, q, cos_max, (float*)op->vals, op->row_stride, nodes,
-                              st);
+                              p->moment, st);
   return dispatch_np<double>(p->Np, pairs, npairs, glx, glw, q, cos_max, (double*)op->vals, op->row_stride, nodes,
-                             st);
+                             p->moment, st);
 }
 
 extern "C" int dfm_assemble(const dfm_mesh* mesh, const dfm_params* p, void* stream, dfm_op** out) {

@@ -83,6 +83,8 @@ inline int elem_size(int precision) { return precision == DFM_F64 ? 8 : (precisi
 // implemented in spmv.cu
 int apply_impl(const dfm_op* op, const void* x, const void* x0, void* y, int R, double alpha, int trans, int xtype,
                cudaStream_t st);
+int apply_combo_impl(const dfm_op* const* ops, int K, const double* coef, const void* x, const void* x0, void* y,
+                     int R, double alpha, int xtype, cudaStream_t st);
 // implemented in quad.cu
 int gauss_legendre_device(int q, double* x, double* w, cudaStream_t st);
 }  // namespace dfm

@@ -324,6 +324,42 @@ __device__ __forceinline__ T phi2_prime(T x) {
   return (T(2) - x - (x + T(2)) * exp_t<T>(-x)) / (x * x * x);
 }
 
+// k-th derivative of phi2 (k <= 3): phi2^(k)(x) = (-1)^k Int_0^1 (1-u) u^k e^{-x u} du.
+// Below x = 1 the Taylor series sum_m (-1)^(m+k) (m+k)!/(m! (m+k+2)!) x^m
+// (20 terms); above, a 16-point Gauss rule on the integral (the integrand is
+// smooth), so no cancellation occurs at any x >= 0.
+template <typename T>
+__device__ __forceinline__ T phi2_deriv(int k, T x) {
+  if (k == 0 && x < T(0.5)) return phi2<T>(x);
+  if (x < T(1)) {
+    T fk = T(1);  // k!
+    for (int i = 2; i <= k; ++i) fk *= T(i);
+    T term = ((k & 1) ? T(-1) : T(1)) * fk / (fk * T(k + 1) * T(k + 2));  // (-1)^k k!/(k+2)!
+    T sum = term;
+#pragma unroll 4
+    for (int m = 0; m < 19; ++m) {
+      term *= -x * T(m + k + 1) / (T(m + 1) * T(m + k + 3));
+      sum += term;
+    }
+    return sum;
+  }
+  const T gx[8] = {T(0.0950125098376374), T(0.2816035507792589), T(0.4580167776572274), T(0.6178762444026438),
+                   T(0.7554044083550030), T(0.8656312023878318), T(0.9445750230732326), T(0.9894009349916499)};
+  const T gw[8] = {T(0.1894506104550685), T(0.1826034150449236), T(0.1691565193950025), T(0.1495959888165767),
+                   T(0.1246289712555339), T(0.0951585116824928), T(0.0622535239386479), T(0.0271524594117541)};
+  T sum = T(0);
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int sgn = -1; sgn <= 1; sgn += 2) {
+      const T u = T(0.5) * (T(1) + T(sgn) * gx[i]);
+      T uk = T(1);
+      for (int j = 0; j < k; ++j) uk *= u;
+      sum += T(0.5) * gw[i] * (T(1) - u) * uk * exp_t<T>(-x * u);
+    }
+  return (k & 1) ? -sum : sum;
+}
+
 // Geometry of one quadrature node of a patch: direction d (unit, source
 // frame), Jacobian of Sec. 3.4 (includes cos theta), and the closed-form
 // quantities |OBC| and L_O of Sec. 3.3 (valid = s_A > 0).

@@ -284,7 +284,18 @@ struct Ctx {
   int nsm;
   int64_t n;      // rows * nb
   int trans = 0;  // 1: the operator is applied transposed (adjoint solves)
+  // per-right-hand-side operators sum_k coef[r][k] B_k (K > 1), coef already
+  // offset to the first right-hand side of the current group
+  const dfm_op* const* combo = nullptr;
+  int K = 1;
+  const double* coef = nullptr;
 };
+
+// y = x0 + alpha * A x for the R right-hand sides of the current group
+inline int ctx_apply(const Ctx& c, const void* x, const void* x0, void* y, int R, double alpha, int xtype) {
+  if (c.combo) return apply_combo_impl(c.combo, c.K, c.coef, x, x0, y, R, alpha, xtype, c.st);
+  return apply_impl(c.op, x, x0, y, R, alpha, c.trans, xtype, c.st);
+}
 
 inline unsigned grid_for(int64_t n, int nsm) {
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)nsm * 8));
@@ -389,19 +400,19 @@ int gmres(const Ctx& c, const T* b, T* x, double tol, int m, int d, int max_iter
     const T* src = v;
     for (int k = 1; k < d; ++k) {
       T* dst = (k & 1) ? t1 : t2;
-      int r = apply_impl(c.op, src, nullptr, dst, 1, 1.0, c.trans, xtype, c.st);
+      int r = ctx_apply(c, src, nullptr, dst, 1, 1.0, xtype);
       if (r) return r;
       src = dst;
     }
     *iters += d;
-    return apply_impl(c.op, src, v, w, 1, -1.0, c.trans, xtype, c.st);
+    return ctx_apply(c, src, v, w, 1, -1.0, xtype);
   };
   while (true) {
     // r = b - (I - B) x = (b - x) + B x   -> V[0]
     axpby_kernel<T><<<grid_for(n, c.nsm), 256, 0, c.st>>>(tmp, T(1), b, T(-1), x, n);
     DFM_LAUNCHED();
     DFM_CUDA_CHECK(cudaGetLastError());
-    rc = apply_impl(c.op, x, tmp, V, 1, 1.0, c.trans, xtype, c.st);
+    rc = ctx_apply(c, x, tmp, V, 1, 1.0, xtype);
     if (rc) return rc;
     ++*iters;
     double beta;
@@ -479,7 +490,7 @@ int gmres(const Ctx& c, const T* b, T* x, double tol, int m, int d, int max_iter
     const T* s_src = tmp;
     for (int k = 1; k < d; ++k) {  // Horner: s <- z + B s
       T* dst = (k & 1) ? t1 : t2;
-      rc = apply_impl(c.op, s_src, tmp, dst, 1, 1.0, c.trans, xtype, c.st);
+      rc = ctx_apply(c, s_src, tmp, dst, 1, 1.0, xtype);
       if (rc) return rc;
       s_src = dst;
     }
@@ -498,7 +509,7 @@ int residual64(const Ctx& c, const double* rho0, const double* x, double* r, dou
   DFM_CUDA_CHECK(cudaGetLastError());
   // r = (rho0 - x) + B x, written to a second half of r
   double* r2 = r + c.n;
-  int rc = apply_impl(c.op, x, r, r2, 1, 1.0, c.trans, DFM_F64, c.st);
+  int rc = ctx_apply(c, x, r, r2, 1, 1.0, DFM_F64);
   if (rc) return rc;
   double rn, bn;
   rc = norm2<double>(c, r2, partial, red_dev, &rn);
@@ -597,18 +608,18 @@ int gmres_batched(const Ctx& c, int R, const T* b, T* x, double tol, int m, int 
     const T* src = v;
     for (int k = 1; k < d; ++k) {
       T* dst = (k & 1) ? t1 : t2;
-      int r2 = apply_impl(c.op, src, nullptr, dst, R, 1.0, c.trans, xtype, c.st);
+      int r2 = ctx_apply(c, src, nullptr, dst, R, 1.0, xtype);
       if (r2) return r2;
       src = dst;
     }
     *iters += d;
-    return apply_impl(c.op, src, v, w, R, -1.0, c.trans, xtype, c.st);
+    return ctx_apply(c, src, v, w, R, -1.0, xtype);
   };
   while (true) {
     axpby_kernel<T><<<grid_for(Rn, c.nsm), 256, 0, c.st>>>(tmp, T(1), b, T(-1), x, Rn);
     DFM_LAUNCHED();
     DFM_CUDA_CHECK(cudaGetLastError());
-    rc = apply_impl(c.op, x, tmp, V, R, 1.0, c.trans, xtype, c.st);
+    rc = ctx_apply(c, x, tmp, V, R, 1.0, xtype);
     if (rc) return rc;
     ++*iters;
     rc = bdots<T>(c, R, V, 0, n, 1, V, n, partial, h_dev, hh.data());
@@ -714,7 +725,7 @@ int gmres_batched(const Ctx& c, int R, const T* b, T* x, double tol, int m, int 
     const T* s_src = tmp;
     for (int k = 1; k < d; ++k) {  // Horner: s <- z + B s
       T* dst = (k & 1) ? t1 : t2;
-      rc = apply_impl(c.op, s_src, tmp, dst, R, 1.0, c.trans, xtype, c.st);
+      rc = ctx_apply(c, s_src, tmp, dst, R, 1.0, xtype);
       if (rc) return rc;
       s_src = dst;
     }
@@ -734,7 +745,7 @@ int bresidual64(const Ctx& c, int R, const double* rho0, const double* x, double
   DFM_LAUNCHED();
   DFM_CUDA_CHECK(cudaGetLastError());
   double* r2 = r + Rn;
-  int rc = apply_impl(c.op, x, r, r2, R, 1.0, c.trans, DFM_F64, c.st);
+  int rc = ctx_apply(c, x, r, r2, R, 1.0, DFM_F64);
   if (rc) return rc;
   std::vector<double> rn(R), bn(R);
   rc = bdots<double>(c, R, r2, 0, c.n, 1, r2, c.n, partial, red_dev, rn.data());
@@ -774,8 +785,10 @@ extern "C" int dfm_source(const dfm_mesh* mesh, int Np, const int64_t* rows_host
   return DFM_OK;
 }
 
-extern "C" int dfm_solve(const dfm_op* op, const double* rho0, int R, double* rho, const dfm_solve_opts* opts,
-                         void* stream, dfm_solve_info* info) {
+namespace dfm {
+namespace {
+int solve_impl(const dfm_op* op, const dfm_op* const* combo, int K, const double* coef, const double* rho0, int R,
+               double* rho, const dfm_solve_opts* opts, void* stream, dfm_solve_info* info) {
   if (!op || !rho0 || !rho || !opts || R < 1) return set_error(DFM_ERR_ARG, "dfm_solve: bad argument");
   if (rho == rho0) return set_error(DFM_ERR_ARG, "dfm_solve: rho must not alias rho0");
   if (!(opts->tol > 0)) return set_error(DFM_ERR_ARG, "dfm_solve: tol must be > 0");
@@ -789,6 +802,11 @@ extern "C" int dfm_solve(const dfm_op* op, const double* rho0, int R, double* rh
   c.st = as_stream(stream);
   c.n = op->nrows * op->nb;
   c.trans = opts->transpose ? 1 : 0;
+  c.combo = combo;
+  c.K = K;
+  c.coef = coef;
+  if (combo && (c.trans || opts->method != DFM_SOLVE_GMRES_IR))
+    return set_error(DFM_ERR_UNSUPPORTED, "dfm_solve_combo: only GMRES_IR without transpose");
   int dev = 0;
   DFM_CUDA_CHECK(cudaGetDevice(&dev));
   DFM_CUDA_CHECK(cudaDeviceGetAttribute(&c.nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -842,6 +860,7 @@ extern "C" int dfm_solve(const dfm_op* op, const double* rho0, int R, double* rh
     int status = DFM_OK;
     for (int g0 = 0; g0 < R; g0 += Rg) {
       const int Rc = std::min(Rg, R - g0);
+      if (combo) c.coef = coef + (int64_t)g0 * K;
       const double* b = rho0 + (int64_t)g0 * n;
       double* x = rho + (int64_t)g0 * n;
       if (!opts->use_x0) DFM_CUDA_CHECK(cudaMemsetAsync(x, 0, sizeof(double) * Rc * n, c.st));
@@ -900,6 +919,7 @@ extern "C" int dfm_solve(const dfm_op* op, const double* rho0, int R, double* rh
   dfm_solve_info acc_info{0, 0, 0.0};
   int status = DFM_OK;
   for (int s = 0; s < R && status != DFM_ERR_NONFINITE; ++s) {
+    if (combo) c.coef = coef + (int64_t)s * K;
     const double* b = rho0 + (int64_t)s * n;
     double* x = rho + (int64_t)s * n;
     int iters = 0, outer = 0;
@@ -911,7 +931,7 @@ extern "C" int dfm_solve(const dfm_op* op, const double* rho0, int R, double* rh
       std::vector<double> ph(2 * kRedBlocks);
       while (true) {
         DFM_CUDA_CHECK(cudaMemcpyAsync(xold, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, c.st));
-        rs = apply_impl(op, xold, b, x, 1, 1.0, c.trans, DFM_F64, c.st);
+        rs = ctx_apply(c, xold, b, x, 1, 1.0, DFM_F64);
         if (rs) return rs;
         ++iters;
         diff_norm_kernel<<<kRedBlocks, kRedThreads, 0, c.st>>>(x, xold, n, part64);
@@ -1015,4 +1035,20 @@ extern "C" int dfm_solve(const dfm_op* op, const double* rho0, int R, double* rh
     }
   }
   return status;
+}
+}  // namespace
+}  // namespace dfm
+
+extern "C" int dfm_solve(const dfm_op* op, const double* rho0, int R, double* rho, const dfm_solve_opts* opts,
+                         void* stream, dfm_solve_info* info) {
+  return dfm::solve_impl(op, nullptr, 1, nullptr, rho0, R, rho, opts, stream, info);
+}
+
+extern "C" int dfm_solve_combo(const dfm_op* const* ops, int K, const double* coef_host, const double* rho0, int R,
+                               double* rho, const dfm_solve_opts* opts, void* stream, dfm_solve_info* info) {
+  if (!ops || K < 1 || K > 4 || !coef_host) return dfm::set_error(DFM_ERR_ARG, "dfm_solve_combo: bad argument");
+  for (int k = 0; k < K; ++k)
+    if (!ops[k] || ops[k]->mesh != ops[0]->mesh || ops[k]->Np != ops[0]->Np || ops[k]->precision != DFM_F32)
+      return dfm::set_error(DFM_ERR_ARG, "dfm_solve_combo: operators must be FP32 and share mesh and Np");
+  return dfm::solve_impl(ops[0], ops, K, coef_host, rho0, R, rho, opts, stream, info);
 }

@@ -63,7 +63,7 @@ spmv_t_kernel(const TV* __restrict__ vals, int64_t row_stride, const int32_t* __
 // waits (bounded) for its own copies and leaves.
 // ---------------------------------------------------------------------------
 constexpr int kStages = 4;
-constexpr int kMaxStagedRhs = 4;  // right-hand sides staged per operator pass
+constexpr int kMaxStagedRhs = 16;  // right-hand sides staged per operator pass
 constexpr int kConsumerWarps = 4;  // computing warps per block (plus one producer warp)
 constexpr long long kWaitPolls = 1ll << 22;
 
@@ -100,6 +100,15 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
   return false;
 }
 
+// Operators applied together: y_r = x0_r + alpha * sum_k coef[r][k] B_k x_r,
+// for the right-hand sides of one launch (k < K <= kMaxCombo, r < kMaxStagedRhs).
+constexpr int kMaxCombo = 4;
+struct Combo {
+  const void* vals[kMaxCombo];
+  int K;
+  double coef[kMaxStagedRhs][kMaxCombo];
+};
+
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
@@ -113,7 +122,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // producer drains its outstanding copies (bounded) before the block exits.
 template <int NB, typename TV, typename TX, typename TA>
 __global__ void __launch_bounds__(32 * (kConsumerWarps + 1))
-spmv_tma_kernel(const TV* __restrict__ vals, int64_t row_stride, const int32_t* __restrict__ recv, int64_t nrows,
+spmv_tma_kernel(const Combo cb, int64_t row_stride, const int32_t* __restrict__ recv, int64_t nrows,
                 int rows_per_tile, int stages, const TX* __restrict__ x, const TX* x0, TX* y, int R, TA alpha,
                 int stage_x0, int* __restrict__ err) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -121,7 +130,9 @@ spmv_tma_kernel(const TV* __restrict__ vals, int64_t row_stride, const int32_t* 
   uint64_t* empty = full + kStages;
   int32_t* s_recv = reinterpret_cast<int32_t*>(smem_raw + 128);
   constexpr int NB2 = NB * NB;
-  const int64_t vals_bytes = (int64_t)rows_per_tile * row_stride * (int64_t)sizeof(TV);
+  const int K = cb.K;
+  const int64_t op_tile_bytes = (int64_t)rows_per_tile * row_stride * (int64_t)sizeof(TV);
+  const int64_t vals_bytes = K * op_tile_bytes;
   const int64_t xblk = 4 * NB * (int64_t)sizeof(TX);
   const int64_t x0_bytes = stage_x0 ? (int64_t)R * rows_per_tile * NB * (int64_t)sizeof(TX) : 0;
   const int64_t stage_bytes = vals_bytes + (int64_t)R * rows_per_tile * xblk + ((x0_bytes + 15) / 16) * 16;
@@ -179,8 +190,10 @@ spmv_tma_kernel(const TV* __restrict__ vals, int64_t row_stride, const int32_t* 
       const unsigned x0b = stage_x0 ? (unsigned)((int64_t)R * nr * NB * (int64_t)sizeof(TX)) : 0u;
       if (lane == 0) {
         const unsigned vb = (unsigned)(nr * row_stride * (int64_t)sizeof(TV));
-        mbar_arrive_expect_tx(&full[s], vb + (unsigned)(R * nr * xblk) + x0b);
-        bulk_copy_g2s(st, vals + R0 * row_stride, vb, &full[s]);
+        mbar_arrive_expect_tx(&full[s], K * vb + (unsigned)(R * nr * xblk) + x0b);
+        for (int k = 0; k < K; ++k)
+          bulk_copy_g2s(st + k * op_tile_bytes, reinterpret_cast<const TV*>(cb.vals[k]) + R0 * row_stride, vb,
+                        &full[s]);
         for (int rhs = 0; rhs < R && stage_x0; ++rhs)
           bulk_copy_g2s(st + vals_bytes + (int64_t)R * rows_per_tile * xblk +
                             (int64_t)rhs * rows_per_tile * NB * (int64_t)sizeof(TX),
@@ -221,23 +234,28 @@ spmv_tma_kernel(const TV* __restrict__ vals, int64_t row_stride, const int32_t* 
       const int r = e / NB;
       const int a = e - r * NB;
       const int lp = rs[r] & 3;
-      const TV* blk = tv + (int64_t)r * row_stride + a * NB;
       for (int rhs = 0; rhs < R; ++rhs) {
         const TX* xs = tx + ((int64_t)rhs * rows_per_tile + r) * 4 * NB;
-        TA acc[3];
+        TA total = TA(0);
+        for (int kk = 0; kk < K; ++kk) {
+          const TV* blk = tv + kk * (op_tile_bytes / (int64_t)sizeof(TV)) + (int64_t)r * row_stride + a * NB;
+          TA acc[3];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          const int l = k + (k >= lp ? 1 : 0);
-          const TV* bk = blk + k * NB2;
-          const TX* xl = xs + l * NB;
-          TA a0 = TA(0);
+          for (int k = 0; k < 3; ++k) {
+            const int l = k + (k >= lp ? 1 : 0);
+            const TV* bk = blk + k * NB2;
+            const TX* xl = xs + l * NB;
+            TA a0 = TA(0);
 #pragma unroll
-          for (int b = 0; b < NB; ++b) a0 = fma((TA)bk[b], (TA)xl[b], a0);
-          acc[k] = a0;
+            for (int b = 0; b < NB; ++b) a0 = fma((TA)bk[b], (TA)xl[b], a0);
+            acc[k] = a0;
+          }
+          const TA sum = (acc[0] + acc[1]) + acc[2];
+          total = (K == 1) ? sum : fma((TA)cb.coef[rhs][kk], sum, total);
         }
         const int64_t o = ((int64_t)rhs * nrows + R0 + r) * NB + a;
         const TA base = stage_x0 ? (TA)tx0[((int64_t)rhs * rows_per_tile + r) * NB + a] : (x0 ? (TA)x0[o] : TA(0));
-        y[o] = (TX)(base + alpha * ((acc[0] + acc[1]) + acc[2]));
+        y[o] = (TX)(base + alpha * total);
       }
     }
     __syncwarp();
@@ -252,7 +270,8 @@ int rows_per_tile_for(int nb) {
 }
 
 template <typename TV, typename TX, typename TA>
-int launch(const dfm_op* op, const TX* x, const TX* x0, TX* y, int R, double alpha, int trans, cudaStream_t st) {
+int launch(const dfm_op* op, const TX* x, const TX* x0, TX* y, int R, double alpha, int trans, cudaStream_t st,
+           const dfm_op* const* combo_ops = nullptr, int K = 1, const double* coef = nullptr) {
   const TV* vals = reinterpret_cast<const TV*>(op->vals);
   const int32_t* recv = op->mesh->recv;
   int dev = 0, nsm = 0;
@@ -265,7 +284,8 @@ int launch(const dfm_op* op, const TX* x, const TX* x0, TX* y, int R, double alp
       const int64_t stride = op->nrows * (int64_t)op->nb;
       for (int r0 = 0; r0 < R; r0 += kMaxStagedRhs) {
         const int rc = launch<TV, TX, TA>(op, x + r0 * stride, x0 ? x0 + r0 * stride : nullptr, y + r0 * stride,
-                                          std::min(kMaxStagedRhs, R - r0), alpha, 0, st);
+                                          std::min(kMaxStagedRhs, R - r0), alpha, 0, st, combo_ops, K,
+                                          coef ? coef + (int64_t)r0 * K : nullptr);
         if (rc) return rc;
       }
       return DFM_OK;
@@ -279,8 +299,14 @@ int launch(const dfm_op* op, const TX* x, const TX* x0, TX* y, int R, double alp
                                 (op->nrows % rpt) == 0 && ((int64_t)rpt * op->nb * (int64_t)sizeof(TX)) % 16 == 0)
                                    ? 1
                                    : 0;
-    const int64_t row_bytes = op->row_stride * (int64_t)sizeof(TV) + (int64_t)R * 4 * op->nb * (int64_t)sizeof(TX) +
+    const int64_t row_bytes = K * op->row_stride * (int64_t)sizeof(TV) +
+                              (int64_t)R * 4 * op->nb * (int64_t)sizeof(TX) +
                               (stage_x0 ? (int64_t)R * op->nb * (int64_t)sizeof(TX) : 0);
+    Combo cb{};
+    cb.K = K;
+    for (int k = 0; k < K; ++k) cb.vals[k] = combo_ops ? combo_ops[k]->vals : op->vals;
+    for (int r = 0; r < R; ++r)
+      for (int k = 0; k < K; ++k) cb.coef[r][k] = coef ? coef[(int64_t)r * K + k] : 1.0;
     const int64_t budget = 200 * 1024 - 1024;
     while (rpt > 1 && rpt * row_bytes * 2 > budget) --rpt;  // keep at least two stages
     int stages = (int)std::min<int64_t>(kStages, budget / (rpt * row_bytes));
@@ -296,7 +322,7 @@ int launch(const dfm_op* op, const TX* x, const TX* x0, TX* y, int R, double alp
       const int64_t grid = std::min<int64_t>(ntiles, (int64_t)nsm * per_sm);
       {
         ::dfm::KernelTimer timer_(sizeof(TX) == 8 ? DFM_KERNEL_SPMV64 : DFM_KERNEL_SPMV, st);
-        kernel<<<(unsigned)grid, 32 * (kConsumerWarps + 1), smem, st>>>(vals, op->row_stride, recv, op->nrows, rpt,
+        kernel<<<(unsigned)grid, 32 * (kConsumerWarps + 1), smem, st>>>(cb, op->row_stride, recv, op->nrows, rpt,
                                                                          stages, x, x0, y, R, (TA)alpha, stage_x0,
                                                                          op->dev_err);
       }
@@ -350,7 +376,30 @@ int apply_impl(const dfm_op* op, const void* x, const void* x0, void* y, int R, 
   return set_error(DFM_ERR_UNSUPPORTED, "dfm_apply: unsupported operator/vector precision");
 }
 
+int apply_combo_impl(const dfm_op* const* ops, int K, const double* coef, const void* x, const void* x0, void* y,
+                     int R, double alpha, int xtype, cudaStream_t st) {
+  if (!ops || K < 1 || K > kMaxCombo || !coef || !x || !y || R < 1)
+    return set_error(DFM_ERR_ARG, "dfm_apply_combo: bad argument (1 <= K <= 4)");
+  if (x == y) return set_error(DFM_ERR_ARG, "dfm_apply_combo: y must not alias x");
+  for (int k = 0; k < K; ++k) {
+    if (!ops[k] || ops[k]->mesh != ops[0]->mesh || ops[k]->Np != ops[0]->Np || ops[k]->precision != DFM_F32)
+      return set_error(DFM_ERR_ARG, "dfm_apply_combo: operators must be FP32 and share mesh and Np");
+  }
+  if (xtype == DFM_F64)
+    return launch<float, double, double>(ops[0], (const double*)x, (const double*)x0, (double*)y, R, alpha, 0, st, ops,
+                                         K, coef);
+  if (xtype == DFM_F32)
+    return launch<float, float, float>(ops[0], (const float*)x, (const float*)x0, (float*)y, R, alpha, 0, st, ops, K,
+                                       coef);
+  return set_error(DFM_ERR_UNSUPPORTED, "dfm_apply_combo: unsupported vector precision");
+}
+
 }  // namespace dfm
+
+extern "C" int dfm_apply_combo(const dfm_op* const* ops, int K, const double* coef_host, const void* x, const void* x0,
+                               void* y, int R, double alpha, int xtype, void* stream) {
+  return dfm::apply_combo_impl(ops, K, coef_host, x, x0, y, R, alpha, xtype, dfm::as_stream(stream));
+}
 
 extern "C" int dfm_apply(const dfm_op* op, const void* x, const void* x0, void* y, int R, double alpha, int trans,
                          int xtype, void* stream) {

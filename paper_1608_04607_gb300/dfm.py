@@ -44,7 +44,8 @@ class MeshInfo(ctypes.Structure):
 
 class Params(ctypes.Structure):
     _fields_ = [("Np", ctypes.c_int), ("mu", ctypes.c_void_p), ("mu_uniform", ctypes.c_double),
-                ("quad_order", ctypes.c_int), ("max_patch_deg", ctypes.c_double), ("precision", ctypes.c_int)]
+                ("quad_order", ctypes.c_int), ("max_patch_deg", ctypes.c_double), ("precision", ctypes.c_int),
+                ("moment", ctypes.c_int)]
 
 
 class OpInfo(ctypes.Structure):
@@ -80,6 +81,8 @@ SIGNATURES = {
     "dfm_op_copy_vals": (_i, [_vp, _vp, _i64, _vp]),
     "dfm_apply": (_i, [_vp, _vp, _vp, _vp, _i, _d, _i, _i, _vp]),
     "dfm_source": (_i, [_vp, _i, _vp, _i, _vp, _vp]),
+    "dfm_apply_combo": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _i, _d, _i, _vp]),
+    "dfm_solve_combo": (_i, [_vp, _i, _vp, _vp, _i, _vp, ctypes.POINTER(SolveOpts), _vp, ctypes.POINTER(SolveInfo)]),
     "dfm_solve": (_i, [_vp, _vp, _i, _vp, ctypes.POINTER(SolveOpts), _vp, ctypes.POINTER(SolveInfo)]),
     "dfm_interior_density": (_i, [_vp, _i, _vp, _d, _vp, _vp, _i, _i, _vp, _vp, _vp]),
     "dfm_adjoint": (_i, [_vp, ctypes.POINTER(Params), _vp, _i, _vp, _vp, _vp, _vp, ctypes.POINTER(SolveOpts), _vp,
@@ -185,11 +188,12 @@ class Mesh:
 class Operator:
     """The assembled operator B (dfm_assemble)."""
 
-    def __init__(self, mesh: Mesh, Np: int, mu=0.0, precision=F32, quad_order=0, max_patch_deg=0.0):
+    def __init__(self, mesh: Mesh, Np: int, mu=0.0, precision=F32, quad_order=0, max_patch_deg=0.0, moment=0):
         import torch
 
         self.mesh = mesh
         self._keep = []
+        self.moment = moment
         p = self._params(Np, mu, precision, quad_order, max_patch_deg)
         self._p = p
         h = ctypes.c_void_p()
@@ -217,6 +221,7 @@ class Operator:
         p.quad_order = quad_order
         p.max_patch_deg = max_patch_deg
         p.precision = precision
+        p.moment = getattr(self, "moment", 0)
         return p
 
     def reassemble(self, mu, quad_order=0, max_patch_deg=0.0):
@@ -297,6 +302,52 @@ def source(mesh: Mesh, Np: int, rows):
     out = torch.empty((rows.size, mesh.n_rows, nbasis(Np)), dtype=torch.float64, device="cuda")
     _check(_lib.dfm_source(mesh.handle, Np, rows.ctypes.data_as(ctypes.c_void_p), rows.size, _ptr(out), _stream()),
            "dfm_source")
+    return out
+
+
+def _op_array(ops):
+    arr = (ctypes.c_void_p * len(ops))(*[o.handle.value for o in ops])
+    return arr
+
+
+def apply_combo(ops, coef, x, x0=None, alpha=1.0, out=None):
+    """y_r = x0_r + alpha sum_k coef[r, k] B_k x_r (dfm_apply_combo); x FP32/FP64 [R, rows, nb]."""
+    import torch
+
+    coef = np.ascontiguousarray(coef, dtype=np.float64)
+    R = 1 if x.dim() == 2 else x.shape[0]
+    assert coef.shape == (R, len(ops))
+    xtype = {torch.float64: F64, torch.float32: F32}[x.dtype]
+    y = torch.empty_like(x) if out is None else out
+    _check(load().dfm_apply_combo(_op_array(ops), len(ops), coef.ctypes.data_as(ctypes.c_void_p), _ptr(x), _ptr(x0),
+                                  _ptr(y), R, float(alpha), xtype, _stream()), "dfm_apply_combo")
+    return y
+
+
+def solve_combo(ops, coef, rho0, tol=1e-8, max_iter=0, restart=0, inner_tol=0.0, poly_degree=0, batch=0):
+    """rho_r = (I - sum_k coef[r, k] B_k)^{-1} rho0_r (dfm_solve_combo); returns (rho, SolveInfo)."""
+    import torch
+
+    coef = np.ascontiguousarray(coef, dtype=np.float64)
+    R = 1 if rho0.dim() == 2 else rho0.shape[0]
+    rho = torch.empty_like(rho0)
+    o = SolveOpts(method=GMRES_IR, tol=tol, max_iter=max_iter, restart=restart, use_x0=0, inner_tol=inner_tol,
+                  transpose=0, poly_degree=poly_degree, batch=batch)
+    info = SolveInfo()
+    _check(load().dfm_solve_combo(_op_array(ops), len(ops), coef.ctypes.data_as(ctypes.c_void_p), _ptr(rho0), R,
+                                  _ptr(rho), ctypes.byref(o), _stream(), ctypes.byref(info)), "dfm_solve_combo")
+    return rho, info
+
+
+def moment_coefficients(mu_rhs, mu_c, K):
+    """Taylor weights (mu_r - mu_c)^k / k! of the damping moments B^(k)."""
+    mu_rhs = np.atleast_1d(np.asarray(mu_rhs, dtype=np.float64))
+    out = np.empty((mu_rhs.size, K))
+    fact = 1.0
+    for k in range(K):
+        if k > 0:
+            fact *= k
+        out[:, k] = (mu_rhs - mu_c) ** k / fact
     return out
 
 
