@@ -39,6 +39,11 @@ WORKLOAD_DESC = ("20^3 Kuhn cube x 6 = 48,000 jittered tets (jitter 0.2h, seed 0
                  "mu = 0.05; boundary reflection 0.95; unit isotropic source on the x = 0 face at (0, 1/2, 1/2); "
                  "solve to FP64 relative residual 1e-8 (FP64-residual refinement around FP32 GMRES(128) right-preconditioned by sum_{k<16} B^k)")
 FP32_LANES_PER_SM = 128
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# operator-application kernel measured by ncu on this workload (y = x0 - B x
+# launch of the apply mode; see profiles/spmv_tma_kuhn20_np4.md).  Keyed by the
+# kernel instantiation and workload; reset to None whenever the kernel changes.
+MEASURED_TRAFFIC = {("spmv_tma_kernel<15, float, float, float>", "kuhn20_np4"): 547.2e6}
 HBM_PEAK_FALLBACK = 6800.0
 
 
@@ -267,8 +272,11 @@ def run_gpu(args):
              "dot": kstats[dfm.KERNEL_DOT][1], "axpy": kstats[dfm.KERNEL_AXPY][1]}
     dominant = max((k for k in ("assemble", "spmv_f32") if k in kern), key=lambda k: total[k])
     d = kern[dominant]
+    traffic = None
+    if dominant == "spmv_f32":
+        traffic = MEASURED_TRAFFIC.get((f"spmv_tma_kernel<{nb}, float, float, float>", args.workload))
     roofline = {"bound": d["bound"], "achieved": round(d["achieved"], 3), "peak": round(d["peak"], 3),
-                "unit": d["unit"], "frac": round(d["frac"], 4), "traffic": None, "kernel": dominant,
+                "unit": d["unit"], "frac": round(d["frac"], 4), "traffic": traffic, "kernel": dominant,
                 "peak_source": peak_src if d["bound"] == "hbm" else
                 f"{nsm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz"}
 
@@ -485,20 +493,23 @@ def run_adjoint(args):
             op.reassemble(mu_vec)
         rho0 = dfm.source(mesh, Np, rows)
         if fp64:
-            rho, info = op.solve(rho0, method=dfm.GMRES, tol=1e-12, poly_degree=16)
+            rho, info = op.solve(rho0, method=dfm.GMRES, tol=1e-12, poly_degree=args.poly or 32,
+                                 restart=args.restart or 256)
         else:
-            rho, info = op.solve(rho0, method=dfm.GMRES_IR, tol=tol)
+            rho, info = op.solve(rho0, method=dfm.GMRES_IR, tol=tol, poly_degree=args.poly or 32,
+                                 restart=args.restart or 256)
         g, dg = dfm.interior_density(mesh, Np, receiver, weights=1.0 / len(receiver), mu=mu_vec)
         return op, rho, g, dg, info
 
+    akw = dict(tol=tol, poly_degree=args.poly or 32, restart=args.restart or 256)
     op, rho, g, dg, info = forward(mu)
-    lam, dj, ainfo = op.adjoint(rho, g, dg, tol=tol)
+    lam, dj, ainfo = op.adjoint(rho, g, dg, **akw)
     torch.cuda.synchronize()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     ev[0].record()
     op, rho, g, dg, info = forward(mu, op)
     ev[1].record()
-    lam, dj, ainfo = op.adjoint(rho, g, dg, tol=tol)
+    lam, dj, ainfo = op.adjoint(rho, g, dg, **akw)
     ev[2].record()
     torch.cuda.synchronize()
     J = float((g * rho[0]).sum())

@@ -395,6 +395,7 @@ int gmres(const Ctx& c, const T* b, T* x, double tol, int m, int d, int max_iter
     *est = 0.0;
     return DFM_OK;
   }
+  double prev_beta = -1.0;
   // w = v - B^d v  (d operator applications, ping-pong through t1/t2)
   auto apply_poly_op = [&](const T* v, T* w) -> int {
     const T* src = v;
@@ -422,6 +423,10 @@ int gmres(const Ctx& c, const T* b, T* x, double tol, int m, int d, int max_iter
     *est = beta / bnorm;
     if (beta <= tol * bnorm) return DFM_OK;
     if (*iters >= max_iter) return DFM_ERR_NOT_CONVERGED;
+    // a restart cycle that gained less than 10% means the working precision is
+    // exhausted: stop and let the caller's FP64 refinement take over
+    if (prev_beta > 0 && beta > 0.9 * prev_beta) return DFM_ERR_NOT_CONVERGED;
+    prev_beta = beta;
     scale_kernel<T><<<grid_for(n, c.nsm), 256, 0, c.st>>>(V, V, T(1.0 / beta), n);
     DFM_LAUNCHED();
     DFM_CUDA_CHECK(cudaGetLastError());
@@ -604,6 +609,7 @@ int gmres_batched(const Ctx& c, int R, const T* b, T* x, double tol, int m, int 
     if (!(bnorm[r] == bnorm[r]) || isinf(bnorm[r]))
       return set_error(DFM_ERR_NONFINITE, "dfm_solve: non-finite right-hand side");
   }
+  double prev_worst = -1.0;
   auto poly_op = [&](const T* v, T* w) -> int {
     const T* src = v;
     for (int k = 1; k < d; ++k) {
@@ -638,6 +644,13 @@ int gmres_batched(const Ctx& c, int R, const T* b, T* x, double tol, int m, int 
     }
     if (nact == 0) return DFM_OK;
     if (*iters >= max_iter) return DFM_ERR_NOT_CONVERGED;
+    {
+      double worst = 0.0;
+      for (int r = 0; r < R; ++r)
+        if (active[r]) worst = std::max(worst, (*est)[r]);
+      if (prev_worst > 0 && worst > 0.9 * prev_worst) return DFM_ERR_NOT_CONVERGED;  // precision exhausted
+      prev_worst = worst;
+    }
     rc = bscale<T>(c, R, V, n, f, red_dev);
     if (rc) return rc;
     for (int j = 0; j < m; ++j) {
@@ -795,7 +808,7 @@ int solve_impl(const dfm_op* op, const dfm_op* const* combo, int K, const double
   const int method = opts->method;
   const int max_iter = opts->max_iter > 0 ? opts->max_iter : 20000;
   const int m = opts->restart > 0 ? std::min(opts->restart, kMaxKrylov) : 128;
-  const double inner_tol = opts->inner_tol > 0 ? opts->inner_tol : 1e-6;
+  const double inner_tol = opts->inner_tol > 0 ? opts->inner_tol : 1e-5;
   const int poly = opts->poly_degree > 0 ? std::min(opts->poly_degree, 64) : 16;
   Ctx c;
   c.op = op;
