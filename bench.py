@@ -43,6 +43,7 @@ FP32_LANES_PER_SM = 128
 # operator-application kernel measured by ncu on this workload (y = x0 - B x
 # launch of the apply mode; see profiles/spmv_tma_kuhn20_np4.md).  Keyed by the
 # kernel instantiation and workload; reset to None whenever the kernel changes.
+PRECOND = {"f32": 0, "f16": 3, "bf16": 2}
 MEASURED_TRAFFIC = {("spmv_tma_kernel<15, float, float, float>", "kuhn20_np4"): 547.2e6}
 HBM_PEAK_FALLBACK = 6800.0
 
@@ -155,7 +156,8 @@ def run_gpu(args):
     def step():
         op.reassemble(mu)
         rho0 = dfm.source(mesh, Np, rows)
-        rho, info = op.solve(rho0, method=method, tol=tol, restart=args.restart, poly_degree=args.poly)
+        rho, info = op.solve(rho0, method=method, tol=tol, restart=args.restart, poly_degree=args.poly,
+                             precond_precision=PRECOND[args.precond])
         return rho, info
 
     for _ in range(args.warmup):
@@ -205,7 +207,8 @@ def run_gpu(args):
             mh = dfm.Mesh(verts, tets, refl=w["refl"])
             o = dfm.Operator(mh, Np, mu=mu, precision=dfm.F32)
             r0 = dfm.source(mh, Np, rows)
-            x, inf = o.solve(r0, method=method, tol=tol, restart=args.restart, poly_degree=args.poly)
+            x, inf = o.solve(r0, method=method, tol=tol, restart=args.restart, poly_degree=args.poly,
+                             precond_precision=PRECOND[args.precond])
             host_rho.copy_(x, non_blocking=True)
             torch.cuda.synchronize()
             o.close()
@@ -296,7 +299,7 @@ def run_gpu(args):
         "data": "synthetic",
         "config": {"workload": args.workload, "desc": WORKLOAD_DESC if args.workload == WORKLOAD else args.workload,
                    "n_tets": int(m.n_tets), "n_rows": int(mesh.n_rows), "nb": nb, "tol": tol,
-                   "restart": args.restart or 128, "poly_degree": args.poly or 16, "l2": "inputs larger than L2 (operator %.0f MB)" % (op.bytes / 1e6),
+                   "restart": args.restart or 128, "poly_degree": args.poly or 16, "precond": args.precond, "l2": "inputs larger than L2 (operator %.0f MB)" % (op.bytes / 1e6),
                    "parallelism": f"replicas x{ws}"},
         "roofline": roofline,
         "e2e": e2e,
@@ -609,6 +612,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparator", action="store_true")
+    ap.add_argument("--precond", choices=["f32", "f16", "bf16"], default="f32",
+                    help="precision of the blocks used by the polynomial preconditioner's hops")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--ref-apps", type=int, default=600)
     ap.add_argument("--mode", choices=["solve", "apply", "adjoint", "batched"], default="solve")

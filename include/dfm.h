@@ -67,6 +67,7 @@ extern "C" {
 #define DFM_F64 0
 #define DFM_F32 1
 #define DFM_BF16 2
+#define DFM_F16 3
 
 /* stationary solvers */
 #define DFM_SOLVE_NEUMANN 0   /* x <- rho0 + B x (Eq. NSum), FP64 */
@@ -204,6 +205,11 @@ typedef struct {
   int transpose;     /* 1: solve (I - B)^T x = rho0 instead (the adjoint equation) */
   int poly_degree;   /* right preconditioner p(B) = sum_{k<d} B^k, so GMRES runs on I - B^d:
                         GMRES_IR inner solves: 0 = 16; GMRES on an FP64 operator: 0 = none */
+  int precond_precision; /* GMRES_IR: 0 = the polynomial preconditioner uses the operator itself;
+                        DFM_F16 or DFM_BF16 = its hops use a 16-bit copy of the blocks (made once
+                        per assembly, half the bytes per hop) and the inner solver is flexible
+                        GMRES, which tolerates the inexact preconditioner; the Krylov operator
+                        I - B and the FP64 residual keep the FP32 blocks */
   int batch;         /* GMRES_IR with R > 1: right-hand sides iterated in lockstep, sharing
                         every operator pass (0 = up to 16, capped so the group's FP32 Krylov
                         basis stays within 24 GiB) */

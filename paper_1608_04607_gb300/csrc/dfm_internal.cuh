@@ -53,6 +53,10 @@ struct dfm_op {
   void* vals = nullptr;  // device
   int64_t bytes = 0;
   int* dev_err = nullptr;  // device flag set by kernels whose bounded waits time out
+  // 16-bit copy of the blocks for inexact preconditioner hops (same layout)
+  void* lp_vals = nullptr;
+  int lp_precision = 0;
+  bool lp_valid = false;
   // assembly scratch (per-pair constants, Gauss table), grown on demand
   void* work = nullptr;
   int64_t work_bytes = 0;
@@ -85,6 +89,9 @@ int apply_impl(const dfm_op* op, const void* x, const void* x0, void* y, int R, 
                cudaStream_t st);
 int apply_combo_impl(const dfm_op* const* ops, int K, const double* coef, const void* x, const void* x0, void* y,
                      int R, double alpha, int xtype, cudaStream_t st);
+// 16-bit copy of op's blocks (made on first use after each assembly); returns a
+// view operator that applies it (same mesh, layout and error flag)
+int lowp_view(const dfm_op* op, int precision, cudaStream_t st, dfm_op* view);
 // implemented in quad.cu
 int gauss_legendre_device(int q, double* x, double* w, cudaStream_t st);
 }  // namespace dfm

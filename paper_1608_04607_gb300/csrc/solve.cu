@@ -380,7 +380,7 @@ int ensure_work(const dfm_op* cop, int64_t bytes) {
 // last relative residual estimate.  t1, t2: scratch vectors of length n.
 template <typename T>
 int gmres(const Ctx& c, const T* b, T* x, double tol, int m, int d, int max_iter, int* iters, double* est, T* V,
-          T* tmp, T* t1, T* t2, T* h_dev, T* partial, T* red_dev) {
+          T* tmp, T* t1, T* t2, T* h_dev, T* partial, T* red_dev, const dfm_op* lp = nullptr, T* Z = nullptr) {
   const int64_t n = c.n;
   const int xtype = sizeof(T) == 8 ? DFM_F64 : DFM_F32;
   if (d < 1) d = 1;
@@ -436,8 +436,22 @@ int gmres(const Ctx& c, const T* b, T* x, double tol, int m, int d, int max_iter
     for (int j = 0; j < m; ++j) {
       T* vj = V + (int64_t)j * n;
       T* w = V + (int64_t)(j + 1) * n;
-      rc = apply_poly_op(vj, w);
-      if (rc) return rc;
+      if (lp) {
+        // flexible step: z_j = p~(B) v_j by Horner on the 16-bit copy, w = z_j - B z_j
+        T* zj = Z + (int64_t)j * n;
+        const T* src = vj;
+        if (d == 1) DFM_CUDA_CHECK(cudaMemcpyAsync(zj, vj, sizeof(T) * n, cudaMemcpyDeviceToDevice, c.st));
+        for (int k = 1; k < d; ++k) {
+          T* dst = (k == d - 1) ? zj : ((k & 1) ? t1 : t2);
+          rc = apply_impl(lp, src, vj, dst, 1, 1.0, 0, xtype, c.st);
+          if (rc) return rc;
+          src = dst;
+        }
+        *iters += d;
+        rc = ctx_apply(c, zj, zj, w, 1, -1.0, xtype);
+      } else {
+        rc = apply_poly_op(vj, w);
+      }
       // classical Gram-Schmidt: h = V^T w (plus |w|^2 as the last entry)
       rc = dots<T>(c, V, n, j + 2, w, partial, h_dev, hh.data());
       if (rc) return rc;
@@ -485,6 +499,15 @@ int gmres(const Ctx& c, const T* b, T* x, double tol, int m, int d, int max_iter
     }
     for (int i = 0; i < kdone; ++i) hh[i] = (T)y[i];
     DFM_CUDA_CHECK(cudaMemcpyAsync(h_dev, hh.data(), sizeof(T) * kdone, cudaMemcpyHostToDevice, c.st));
+    if (lp) {  // flexible update: x += Z y
+      {
+        ::dfm::KernelTimer timer_(DFM_KERNEL_AXPY, c.st);
+        multi_axpy_kernel<T><<<kRedBlocks, kRedThreads, 0, c.st>>>(Z, n, kdone, h_dev, T(1), x, n, nullptr);
+      }
+      DFM_LAUNCHED();
+      DFM_CUDA_CHECK(cudaGetLastError());
+      continue;
+    }
     DFM_CUDA_CHECK(cudaMemsetAsync(tmp, 0, sizeof(T) * n, c.st));
     {
       ::dfm::KernelTimer timer_(DFM_KERNEL_AXPY, c.st);
@@ -591,7 +614,8 @@ int bscale(const Ctx& c, int R, T* w, int64_t wldr, const std::vector<double>& f
 // b, x: [R][n]; V: [(m+1)][R][n]; tmp, t1, t2: [R][n].
 template <typename T>
 int gmres_batched(const Ctx& c, int R, const T* b, T* x, double tol, int m, int d, int max_iter, int* iters,
-                  std::vector<double>* est, T* V, T* tmp, T* t1, T* t2, T* h_dev, T* partial, T* red_dev) {
+                  std::vector<double>* est, T* V, T* tmp, T* t1, T* t2, T* h_dev, T* partial, T* red_dev,
+                  const dfm_op* lp = nullptr, T* Z = nullptr) {
   const int64_t n = c.n;
   const int64_t Rn = (int64_t)R * n;
   const int xtype = sizeof(T) == 8 ? DFM_F64 : DFM_F32;
@@ -656,7 +680,22 @@ int gmres_batched(const Ctx& c, int R, const T* b, T* x, double tol, int m, int 
     for (int j = 0; j < m; ++j) {
       T* vj = V + (int64_t)j * Rn;
       T* w = V + (int64_t)(j + 1) * Rn;
-      rc = poly_op(vj, w);
+      if (lp) {
+        // flexible step: z_j = p~(B) v_j on the 16-bit copy, w = z_j - B z_j
+        T* zj = Z + (int64_t)j * Rn;
+        const T* src = vj;
+        if (d == 1) DFM_CUDA_CHECK(cudaMemcpyAsync(zj, vj, sizeof(T) * Rn, cudaMemcpyDeviceToDevice, c.st));
+        for (int k = 1; k < d; ++k) {
+          T* dst = (k == d - 1) ? zj : ((k & 1) ? t1 : t2);
+          rc = apply_impl(lp, src, vj, dst, R, 1.0, 0, xtype, c.st);
+          if (rc) return rc;
+          src = dst;
+        }
+        *iters += d;
+        rc = ctx_apply(c, zj, zj, w, R, -1.0, xtype);
+      } else {
+        rc = poly_op(vj, w);
+      }
       if (rc) return rc;
       rc = bdots<T>(c, R, V, Rn, n, j + 2, w, n, partial, h_dev, hh.data());
       if (rc) return rc;
@@ -732,6 +771,11 @@ int gmres_batched(const Ctx& c, int R, const T* b, T* x, double tol, int m, int 
     }
     if (kmax == 0) continue;
     DFM_CUDA_CHECK(cudaMemcpyAsync(h_dev, yp.data(), sizeof(T) * R * hld, cudaMemcpyHostToDevice, c.st));
+    if (lp) {  // flexible update: x_r += Z_r y_r
+      rc = baxpy<T>(c, R, Z, Rn, n, kmax, h_dev, hld, T(1), x, n, partial, red_dev, nullptr);
+      if (rc) return rc;
+      continue;
+    }
     DFM_CUDA_CHECK(cudaMemsetAsync(tmp, 0, sizeof(T) * Rn, c.st));
     rc = baxpy<T>(c, R, V, Rn, n, kmax, h_dev, hld, T(1), tmp, n, partial, red_dev, nullptr);
     if (rc) return rc;
@@ -810,6 +854,9 @@ int solve_impl(const dfm_op* op, const dfm_op* const* combo, int K, const double
   const int m = opts->restart > 0 ? std::min(opts->restart, kMaxKrylov) : 128;
   const double inner_tol = opts->inner_tol > 0 ? opts->inner_tol : 1e-5;
   const int poly = opts->poly_degree > 0 ? std::min(opts->poly_degree, 64) : 16;
+  const bool use_lp = opts->precond_precision != 0 && method == DFM_SOLVE_GMRES_IR && !combo && !opts->transpose;
+  if (opts->precond_precision != 0 && opts->precond_precision != DFM_F16 && opts->precond_precision != DFM_BF16)
+    return set_error(DFM_ERR_ARG, "dfm_solve: precond_precision must be 0, DFM_F16 or DFM_BF16");
   Ctx c;
   c.op = op;
   c.st = as_stream(stream);
@@ -834,7 +881,7 @@ int solve_impl(const dfm_op* op, const dfm_op* const* combo, int K, const double
   const bool batched = (method == DFM_SOLVE_GMRES_IR && R > 1);
   int Rg = 1;
   if (batched) {
-    const int64_t per_rhs = (int64_t)(m + 6) * n * 4;
+    const int64_t per_rhs = (int64_t)(m + 6 + (use_lp ? m : 0)) * n * 4;
     const int64_t cap = opts->batch > 0 ? opts->batch : 16;
     Rg = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)R, cap, (int64_t(24) << 30) / per_rhs}));
   }
@@ -844,7 +891,8 @@ int solve_impl(const dfm_op* op, const dfm_op* const* combo, int K, const double
   const int64_t hcap = (int64_t)Rg * (kMaxKrylov + 8);
   int64_t bytes = 0;
   bytes += (2 * (int64_t)Rg + 2) * n * 8 + 4096;          // r (2 Rg n), tmp64 (n), xold (n)
-  const int64_t inner_bytes = (int64_t)(m + 7) * Rg * n * es + 8 * 256;  // V (m+1), tmp, t1, t2, b, x
+  const int64_t inner_bytes =
+      (int64_t)(m + 7 + (use_lp ? m : 0)) * Rg * n * es + 9 * 256;  // V (m+1), tmp, t1, t2, b, x [, Z (m)]
   bytes += inner_bytes + 4096;
   const int64_t part_elems = std::max<int64_t>((int64_t)kRedBlocks * (kMaxKrylov + 8), (int64_t)kBRedBlocks * hcap);
   bytes += (part_elems + 2 * hcap + 2 * Rg + 256) * 8 + 4096;  // partials, h, red
@@ -858,6 +906,13 @@ int solve_impl(const dfm_op* op, const dfm_op* const* combo, int K, const double
   double* h64 = W.take<double>(2 * hcap);
   double* red64 = W.take<double>(std::max(8, 2 * Rg));
   char* inner_base = W.take<char>(inner_bytes);
+  dfm_op lpv;
+  const dfm_op* lp = nullptr;
+  if (use_lp) {
+    rc = lowp_view(op, opts->precond_precision, c.st, &lpv);
+    if (rc) return rc;
+    lp = &lpv;
+  }
   if (batched) {
     Work Wi{inner_base};
     float* V = Wi.take<float>((int64_t)(m + 1) * Rg * n);
@@ -866,6 +921,7 @@ int solve_impl(const dfm_op* op, const dfm_op* const* combo, int K, const double
     float* t2 = Wi.take<float>((int64_t)Rg * n);
     float* bf = Wi.take<float>((int64_t)Rg * n);
     float* xf = Wi.take<float>((int64_t)Rg * n);
+    float* Zb = use_lp ? Wi.take<float>((int64_t)m * Rg * n) : nullptr;
     float* part32 = reinterpret_cast<float*>(part64);
     float* h32 = reinterpret_cast<float*>(h64);
     float* red32 = reinterpret_cast<float*>(red64);
@@ -911,7 +967,7 @@ int solve_impl(const dfm_op* op, const dfm_op* const* combo, int K, const double
         DFM_CUDA_CHECK(cudaMemsetAsync(xf, 0, sizeof(float) * Rc * n, c.st));
         const double itol = std::max(inner_tol, 0.3 * opts->tol / std::max(worst, 1e-300));
         int gi = gmres_batched<float>(c, Rc, bf, xf, itol, m, poly, max_iter, &iters, &est, V, tmp, t1, t2, h32,
-                                      part32, red32);
+                                      part32, red32, lp, Zb);
         if (gi != DFM_OK && gi != DFM_ERR_NOT_CONVERGED) return gi;
         DFM_CUDA_CHECK(cudaMemcpyAsync(red64, sup.data(), sizeof(double) * Rc, cudaMemcpyHostToDevice, c.st));
         badd_f32_kernel<<<dim3(grid_for(n, c.nsm), Rc), 256, 0, c.st>>>(x, xf, red64, n);
@@ -994,6 +1050,7 @@ int solve_impl(const dfm_op* op, const dfm_op* const* combo, int K, const double
       float* t2 = Wi.take<float>(n);
       float* bf = Wi.take<float>(n);
       float* xf = Wi.take<float>(n);
+      float* Zs = use_lp ? Wi.take<float>((int64_t)m * n) : nullptr;
       float* part32 = reinterpret_cast<float*>(part64);
       float* h32 = reinterpret_cast<float*>(h64);
       float* red32 = reinterpret_cast<float*>(red64);
@@ -1020,7 +1077,8 @@ int solve_impl(const dfm_op* op, const dfm_op* const* combo, int K, const double
         const double need = opts->tol / std::max(resid, 1e-300);
         const double itol = method == DFM_SOLVE_GMRES_IR ? std::max(inner_tol, 0.3 * need)
                                                          : std::max(opts->tol, 1e-6);
-        int gi = gmres<float>(c, bf, xf, itol, m, poly, max_iter, &iters, &est, V, tmp, t1, t2, h32, part32, red32);
+        int gi = gmres<float>(c, bf, xf, itol, m, poly, max_iter, &iters, &est, V, tmp, t1, t2, h32, part32, red32,
+                              method == DFM_SOLVE_GMRES_IR ? lp : nullptr, Zs);
         if (gi != DFM_OK && gi != DFM_ERR_NOT_CONVERGED) return gi;
         add_f32_kernel<<<grid_for(n, c.nsm), 256, 0, c.st>>>(x, xf, rabs, n);
         DFM_LAUNCHED();

@@ -15,6 +15,10 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <type_traits>
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "dfm_internal.cuh"
 
@@ -372,8 +376,55 @@ int apply_impl(const dfm_op* op, const void* x, const void* x0, void* y, int R, 
       return launch<float, float, float>(op, (const float*)x, (const float*)x0, (float*)y, R, alpha, trans, st);
     if (op->precision == DFM_F64)
       return launch<double, float, double>(op, (const float*)x, (const float*)x0, (float*)y, R, alpha, trans, st);
+    if (op->precision == DFM_F16 && !trans)
+      return launch<__half, float, float>(op, (const float*)x, (const float*)x0, (float*)y, R, alpha, trans, st);
+    if (op->precision == DFM_BF16 && !trans)
+      return launch<__nv_bfloat16, float, float>(op, (const float*)x, (const float*)x0, (float*)y, R, alpha, trans,
+                                                 st);
   }
   return set_error(DFM_ERR_UNSUPPORTED, "dfm_apply: unsupported operator/vector precision");
+}
+
+namespace {
+template <typename T16>
+__global__ void to_16bit_kernel(const float* __restrict__ src, T16* __restrict__ dst, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if constexpr (std::is_same<T16, __half>::value)
+      dst[i] = __float2half_rn(src[i]);
+    else
+      dst[i] = __float2bfloat16_rn(src[i]);
+  }
+}
+}  // namespace
+
+int lowp_view(const dfm_op* cop, int precision, cudaStream_t st, dfm_op* view) {
+  dfm_op* op = const_cast<dfm_op*>(cop);
+  if (op->precision != DFM_F32 || (precision != DFM_F16 && precision != DFM_BF16))
+    return set_error(DFM_ERR_UNSUPPORTED, "preconditioner copy: needs an FP32 operator and DFM_F16 or DFM_BF16");
+  if (!op->lp_vals) {
+    DFM_CUDA_CHECK(cudaMalloc(&op->lp_vals, op->nrows * op->row_stride * 2));
+  }
+  if (!op->lp_valid || op->lp_precision != precision) {
+    const int64_t n = op->nrows * op->row_stride;
+    if (precision == DFM_F16)
+      to_16bit_kernel<__half><<<1024, 256, 0, st>>>((const float*)op->vals, (__half*)op->lp_vals, n);
+    else
+      to_16bit_kernel<__nv_bfloat16><<<1024, 256, 0, st>>>((const float*)op->vals, (__nv_bfloat16*)op->lp_vals, n);
+    DFM_LAUNCHED();
+    DFM_CUDA_CHECK(cudaGetLastError());
+    op->lp_precision = precision;
+    op->lp_valid = true;
+  }
+  view->mesh = op->mesh;
+  view->Np = op->Np;
+  view->nb = op->nb;
+  view->precision = precision;
+  view->nrows = op->nrows;
+  view->row_stride = op->row_stride;
+  view->vals = op->lp_vals;
+  view->bytes = op->nrows * op->row_stride * 2;
+  view->dev_err = op->dev_err;
+  return DFM_OK;
 }
 
 int apply_combo_impl(const dfm_op* const* ops, int K, const double* coef, const void* x, const void* x0, void* y,

@@ -26,7 +26,7 @@ DFM_ERR_NOT_CONVERGED = -5
 DFM_ERR_NONFINITE = -6
 DFM_ERR_UNSUPPORTED = -7
 
-F64, F32, BF16 = 0, 1, 2
+F64, F32, BF16, F16 = 0, 1, 2, 3
 NEUMANN, GMRES, GMRES_IR = 0, 1, 2
 
 
@@ -56,7 +56,8 @@ class OpInfo(ctypes.Structure):
 class SolveOpts(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("restart", ctypes.c_int), ("use_x0", ctypes.c_int), ("inner_tol", ctypes.c_double),
-                ("transpose", ctypes.c_int), ("poly_degree", ctypes.c_int), ("batch", ctypes.c_int)]
+                ("transpose", ctypes.c_int), ("poly_degree", ctypes.c_int), ("precond_precision", ctypes.c_int),
+                ("batch", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -253,13 +254,14 @@ class Operator:
         return y
 
     def solve(self, rho0, method=GMRES_IR, tol=1e-8, max_iter=0, restart=0, x0=None, inner_tol=0.0,
-              raise_on_nonconvergence=True, transpose=False, poly_degree=0, batch=0):
+              raise_on_nonconvergence=True, transpose=False, poly_degree=0, batch=0, precond_precision=0):
         """rho = (I - B)^{-1} rho0 (FP64, [R, rows, nb] or [rows, nb]); returns (rho, SolveInfo)."""
         torch = self._torch
         R = 1 if rho0.dim() == 2 else rho0.shape[0]
         rho = torch.empty_like(rho0) if x0 is None else x0.clone()
         o = SolveOpts(method=method, tol=tol, max_iter=max_iter, restart=restart, use_x0=int(x0 is not None),
-                      inner_tol=inner_tol, transpose=int(bool(transpose)), poly_degree=poly_degree, batch=batch)
+                      inner_tol=inner_tol, transpose=int(bool(transpose)), poly_degree=poly_degree,
+                      precond_precision=precond_precision, batch=batch)
         info = SolveInfo()
         rc = _lib.dfm_solve(self._h, _ptr(rho0), R, _ptr(rho), ctypes.byref(o), _stream(), ctypes.byref(info))
         if rc == DFM_ERR_NOT_CONVERGED and not raise_on_nonconvergence:

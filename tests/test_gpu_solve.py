@@ -194,3 +194,34 @@ def test_batched_refinement_matches_lu(D, oracle_mod, R, batch):
         ref = np.linalg.solve(M, b[r].ravel())
         got = x[r].cpu().numpy().ravel()
         assert np.linalg.norm(got - ref) <= 1e-8 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("prec", ["f16", "bf16"])
+@pytest.mark.parametrize("R", [1, 3])
+def test_flexible_gmres_with_16bit_preconditioner(D, oracle_mod, prec, R):
+    """The polynomial preconditioner's hops run on a 16-bit copy of the blocks
+    (flexible GMRES); the solution still meets the FP64 residual tolerance and
+    equals LU on the FP32 operator."""
+    import torch
+
+    m = kuhn_cube_mesh(3, jitter=0.2, seed=13)
+    Np = 2
+    mesh = D.Mesh(m.verts, m.tets, refl=0.95)
+    op = D.Operator(mesh, Np, mu=0.05, precision=D.F32)
+    same = _gpu_op_as_oracle(oracle_mod, op, mesh, m.n_tets, Np)
+    M = np.eye(same.nrows * same.nb) - oracle_mod.dense(same)
+    rng = np.random.default_rng(R)
+    b = rng.standard_normal((R, mesh.n_rows, op.nb))
+    pp = D.F16 if prec == "f16" else D.BF16
+    x, info = op.solve(torch.tensor(b, device="cuda"), method=D.GMRES_IR, tol=1e-10, precond_precision=pp)
+    assert info.resid <= 1e-10
+    for r in range(R):
+        ref = np.linalg.solve(M, b[r].ravel())
+        assert np.linalg.norm(x[r].cpu().numpy().ravel() - ref) <= 1e-8 * np.linalg.norm(ref)
+    # re-assembly refreshes the 16-bit copy
+    op.reassemble(0.2)
+    x2, info2 = op.solve(torch.tensor(b, device="cuda"), method=D.GMRES_IR, tol=1e-10, precond_precision=pp)
+    same2 = _gpu_op_as_oracle(oracle_mod, op, mesh, m.n_tets, Np)
+    M2 = np.eye(same2.nrows * same2.nb) - oracle_mod.dense(same2)
+    ref2 = np.linalg.solve(M2, b[0].ravel())
+    assert np.linalg.norm(x2[0].cpu().numpy().ravel() - ref2) <= 1e-8 * np.linalg.norm(ref2)
