@@ -200,7 +200,7 @@ typedef struct {
   int max_iter;      /* cap on operator applications (0 = 20000) */
   int restart;       /* GMRES restart length, <= 256 (0 = 128) */
   int use_x0;        /* 1: rho holds the initial guess on entry */
-  double inner_tol;  /* GMRES_IR: floor of the inner FP32 relative tolerance (0 = 1e-5); an inner
+  double inner_tol;  /* GMRES_IR: floor of the inner FP32 relative tolerance (0 = 1e-6); an inner
                         solve also stops when a restart cycle gains less than 10% */
   int transpose;     /* 1: solve (I - B)^T x = rho0 instead (the adjoint equation) */
   int poly_degree;   /* right preconditioner p(B) = sum_{k<d} B^k, so GMRES runs on I - B^d:

@@ -852,7 +852,7 @@ int solve_impl(const dfm_op* op, const dfm_op* const* combo, int K, const double
   const int method = opts->method;
   const int max_iter = opts->max_iter > 0 ? opts->max_iter : 20000;
   const int m = opts->restart > 0 ? std::min(opts->restart, kMaxKrylov) : 128;
-  const double inner_tol = opts->inner_tol > 0 ? opts->inner_tol : 1e-5;
+  const double inner_tol = opts->inner_tol > 0 ? opts->inner_tol : 1e-6;
   const int poly = opts->poly_degree > 0 ? std::min(opts->poly_degree, 64) : 16;
   const bool use_lp = opts->precond_precision != 0 && method == DFM_SOLVE_GMRES_IR && !combo && !opts->transpose;
   if (opts->precond_precision != 0 && opts->precond_precision != DFM_F16 && opts->precond_precision != DFM_BF16)
@@ -890,7 +890,8 @@ int solve_impl(const dfm_op* op, const dfm_op* const* combo, int K, const double
   const int64_t es = inner64 ? 8 : 4;
   const int64_t hcap = (int64_t)Rg * (kMaxKrylov + 8);
   int64_t bytes = 0;
-  bytes += (2 * (int64_t)Rg + 2) * n * 8 + 4096;          // r (2 Rg n), tmp64 (n), xold (n)
+  const bool gather = combo && K > 1 && batched && R > Rg;
+  bytes += (2 * (int64_t)Rg + 2 + (gather ? 2 * (int64_t)Rg : 0)) * n * 8 + 8192;  // r, tmp64, xold [, gather b/x]
   const int64_t inner_bytes =
       (int64_t)(m + 7 + (use_lp ? m : 0)) * Rg * n * es + 9 * 256;  // V (m+1), tmp, t1, t2, b, x [, Z (m)]
   bytes += inner_bytes + 4096;
@@ -902,6 +903,8 @@ int solve_impl(const dfm_op* op, const dfm_op* const* combo, int K, const double
   double* r64 = W.take<double>(2 * (int64_t)Rg * n);
   double* tmp64 = W.take<double>(n);
   double* xold = W.take<double>(n);
+  double* gather_b = gather ? W.take<double>((int64_t)Rg * n) : nullptr;
+  double* gather_x = gather ? W.take<double>((int64_t)Rg * n) : nullptr;
   double* part64 = W.take<double>(part_elems);
   double* h64 = W.take<double>(2 * hcap);
   double* red64 = W.take<double>(std::max(8, 2 * Rg));
@@ -927,11 +930,37 @@ int solve_impl(const dfm_op* op, const dfm_op* const* combo, int K, const double
     float* red32 = reinterpret_cast<float*>(red64);
     dfm_solve_info ai{0, 0, 0.0};
     int status = DFM_OK;
+    // right-hand sides with their own damping converge at different rates and a
+    // lockstep group runs at its slowest member's pace: order them by the first
+    // damping moment weight (mu_r - mu_c) so that each group holds similar ones
+    std::vector<int> order(R);
+    for (int r = 0; r < R; ++r) order[r] = r;
+    const bool reorder = combo && K > 1 && R > Rg;
+    if (reorder)
+      std::stable_sort(order.begin(), order.end(),
+                       [&](int a, int b2) { return coef[(int64_t)a * K + 1] < coef[(int64_t)b2 * K + 1]; });
+    std::vector<double> grp_coef;
     for (int g0 = 0; g0 < R; g0 += Rg) {
       const int Rc = std::min(Rg, R - g0);
-      if (combo) c.coef = coef + (int64_t)g0 * K;
       const double* b = rho0 + (int64_t)g0 * n;
       double* x = rho + (int64_t)g0 * n;
+      if (reorder) {  // gather the group into contiguous buffers
+        b = gather_b;
+        x = gather_x;
+        grp_coef.resize((size_t)Rc * K);
+        for (int r = 0; r < Rc; ++r) {
+          const int src = order[g0 + r];
+          DFM_CUDA_CHECK(cudaMemcpyAsync(gather_b + (int64_t)r * n, rho0 + (int64_t)src * n, sizeof(double) * n,
+                                         cudaMemcpyDeviceToDevice, c.st));
+          if (opts->use_x0)
+            DFM_CUDA_CHECK(cudaMemcpyAsync(gather_x + (int64_t)r * n, rho + (int64_t)src * n, sizeof(double) * n,
+                                           cudaMemcpyDeviceToDevice, c.st));
+          for (int k = 0; k < K; ++k) grp_coef[(size_t)r * K + k] = coef[(int64_t)src * K + k];
+        }
+        c.coef = grp_coef.data();
+      } else if (combo) {
+        c.coef = coef + (int64_t)g0 * K;
+      }
       if (!opts->use_x0) DFM_CUDA_CHECK(cudaMemsetAsync(x, 0, sizeof(double) * Rc * n, c.st));
       int iters = 0, outer = 0;
       std::vector<double> rel, absn, est;
@@ -975,6 +1004,10 @@ int solve_impl(const dfm_op* op, const dfm_op* const* combo, int K, const double
         DFM_CUDA_CHECK(cudaGetLastError());
         ++outer;
       }
+      if (reorder)  // scatter the group's solutions back
+        for (int r = 0; r < Rc; ++r)
+          DFM_CUDA_CHECK(cudaMemcpyAsync(rho + (int64_t)order[g0 + r] * n, gather_x + (int64_t)r * n,
+                                         sizeof(double) * n, cudaMemcpyDeviceToDevice, c.st));
       double worst = 0.0;
       for (double v : rel) worst = std::max(worst, v);
       ai.iters += iters;

@@ -267,6 +267,136 @@ spmv_tma_kernel(const Combo cb, int64_t row_stride, const int32_t* __restrict__ 
   }
 }
 
+
+// Transposed application y = x0 + alpha B^T x with the same pipeline.  A tile
+// is a run of consecutive source tets; the blocks leaving tet t are the rows
+// recv[4t + l'] (l' = 0..3, one full row each, all three slots come from t), so
+// every operator row is copied exactly once over the whole grid.  Producer lane
+// r of a tile copies row r by TMA and stages x of that row (NB values, loaded
+// one tile ahead into registers).  Consumers form, for column J = 4t + l,
+//   (B^T x)_J[b] = sum_{l' != l} sum_a B_{recv[4t+l'], slot(l,l')}[a][b] x_{recv[4t+l']}[a],
+// slot(l, l') = l - (l > l').  One right-hand side per launch.
+template <int NB, typename TV, typename TX, typename TA>
+__global__ void __launch_bounds__(32 * (kConsumerWarps + 1))
+spmv_t_tma_kernel(const TV* __restrict__ vals, int64_t row_stride, const int32_t* __restrict__ recv, int64_t nt,
+                  int tets_per_tile, int stages, const TX* __restrict__ x, const TX* x0, TX* y, TA alpha,
+                  int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw);
+  uint64_t* empty = full + kStages;
+  const int rpt = 4 * tets_per_tile;  // rows per tile (<= 32)
+  constexpr int NB2 = NB * NB;
+  const int64_t row_bytes = row_stride * (int64_t)sizeof(TV);
+  const int64_t xs_bytes = ((int64_t)rpt * NB * sizeof(TA) + 15) / 16 * 16;
+  const int64_t stage_bytes = rpt * row_bytes + xs_bytes;
+  unsigned char* stage0 = smem_raw + 128;
+  const int64_t ntiles = (nt + tets_per_tile - 1) / tets_per_tile;
+  const int64_t mine = ntiles > (int64_t)blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < stages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kConsumerWarps);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  auto tile_tets = [&](int64_t i, int64_t* T0, int* ntt) {
+    *T0 = (blockIdx.x + i * (int64_t)gridDim.x) * tets_per_tile;
+    const int64_t left = nt - *T0;
+    *ntt = left < tets_per_tile ? (int)left : tets_per_tile;
+  };
+  if (warp == 0) {
+    // ---------------- producer ----------------
+    int64_t issued = 0;
+    bool ok = true;
+    int32_t next_row = 0;
+    TA next_x[NB];
+    auto fetch = [&](int64_t i, int32_t* row, TA* xv) {
+      int64_t T0;
+      int ntt;
+      tile_tets(i, &T0, &ntt);
+      if (lane < 4 * ntt) {
+        *row = recv[4 * T0 + lane];
+        const TX* xr = x + (int64_t)(*row) * NB;
+#pragma unroll
+        for (int a = 0; a < NB; ++a) xv[a] = (TA)__ldg(xr + a);
+      }
+    };
+    if (mine > 0) fetch(0, &next_row, next_x);
+    for (int64_t i = 0; i < mine && ok; ++i) {
+      const int s = (int)(i % stages);
+      int64_t T0;
+      int ntt;
+      tile_tets(i, &T0, &ntt);
+      const int32_t row = next_row;
+      TA xv[NB];
+#pragma unroll
+      for (int a = 0; a < NB; ++a) xv[a] = next_x[a];
+      if (i + 1 < mine) fetch(i + 1, &next_row, next_x);
+      if (i >= stages) ok = mbar_wait_bounded(&empty[s], (unsigned)(((i / stages) - 1) & 1));
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) break;
+      unsigned char* st = stage0 + s * stage_bytes;
+      TA* xs = reinterpret_cast<TA*>(st + rpt * row_bytes);
+      const int nr = 4 * ntt;
+      if (lane < nr) {
+#pragma unroll
+        for (int a = 0; a < NB; ++a) xs[lane * NB + a] = xv[a];
+      }
+      __syncwarp();  // staged x is written before lane 0's arrive publishes the stage
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      if (lane == 0) mbar_arrive_expect_tx(&full[s], (unsigned)(nr * row_bytes));
+      if (lane < nr) bulk_copy_g2s(st + lane * row_bytes, vals + (int64_t)row * row_stride, (unsigned)row_bytes, &full[s]);
+      issued = i + 1;
+    }
+    if (!ok && lane == 0) atomicOr(err, 1);
+    if (lane == 0)
+      for (int64_t j = (issued > stages ? issued - stages : 0); j < issued; ++j)
+        mbar_wait_bounded(&full[j % stages], (unsigned)((j / stages) & 1));
+    return;
+  }
+  // ---------------- consumers ----------------
+  const int ctid = threadIdx.x - 32;
+  const int nthreads = 32 * kConsumerWarps;
+  for (int64_t i = 0; i < mine; ++i) {
+    const int s = (int)(i % stages);
+    const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&full[s], (unsigned)((i / stages) & 1)));
+    if (!ok) {
+      if (lane == 0) atomicOr(err, 1);
+      break;
+    }
+    const unsigned char* st = stage0 + s * stage_bytes;
+    const TV* tv = reinterpret_cast<const TV*>(st);
+    const TA* xs = reinterpret_cast<const TA*>(st + rpt * row_bytes);
+    int64_t T0;
+    int ntt;
+    tile_tets(i, &T0, &ntt);
+    for (int e = ctid; e < ntt * 4 * NB; e += nthreads) {
+      const int lt = e / (4 * NB);
+      const int rem = e - lt * 4 * NB;
+      const int l = rem / NB;
+      const int b = rem - l * NB;
+      TA acc = TA(0);
+#pragma unroll
+      for (int lp = 0; lp < 4; ++lp) {
+        if (lp == l) continue;
+        const int slot = l - (l > lp ? 1 : 0);
+        const TV* blk = tv + (int64_t)(lt * 4 + lp) * row_stride + slot * NB2 + b;
+        const TA* xr = xs + (lt * 4 + lp) * NB;
+#pragma unroll
+        for (int a = 0; a < NB; ++a) acc = fma((TA)blk[a * NB], xr[a], acc);
+      }
+      const int64_t o = (4 * (T0 + lt) + l) * NB + b;
+      const TA base = x0 ? (TA)x0[o] : TA(0);
+      y[o] = (TX)(base + alpha * acc);
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
+  }
+}
+
 int rows_per_tile_for(int nb) {
   int r = kThreads / nb;
   if (r < 1) r = 1;
@@ -343,6 +473,51 @@ int launch(const dfm_op* op, const TX* x, const TX* x0, TX* y, int R, double alp
       case 28: rc = go(spmv_tma_kernel<28, TV, TX, TA>); break;
       case 36: rc = go(spmv_tma_kernel<36, TV, TX, TA>); break;
       case 45: rc = go(spmv_tma_kernel<45, TV, TX, TA>); break;
+      default: return set_error(DFM_ERR_UNSUPPORTED, "dfm_apply: unsupported basis size");
+    }
+    if (rc) return rc;
+  } else if (combo_ops == nullptr && !(reinterpret_cast<uintptr_t>(op->vals) & 15)) {
+    // pipelined transposed application, one right-hand side per launch
+    const int64_t nt = op->nrows / 4;
+    const int64_t row_bytes = op->row_stride * (int64_t)sizeof(TV);
+    int tpt = 2;  // tets per tile (8 rows)
+    const int64_t xs_bytes = ((int64_t)4 * tpt * op->nb * (int64_t)sizeof(TA) + 15) / 16 * 16;
+    const int64_t budget = 200 * 1024 - 512;
+    const int64_t stage_bytes = 4 * tpt * row_bytes + xs_bytes;
+    const int stages = (int)std::min<int64_t>(kStages, budget / stage_bytes);
+    if (stages < 2) return set_error(DFM_ERR_UNSUPPORTED, "dfm_apply: operator rows too large for the transposed pipeline");
+    const size_t smem = 128 + (size_t)stages * stage_bytes;
+    const int64_t stride = op->nrows * (int64_t)op->nb;
+    auto go = [&](auto kernel) -> int {
+      DFM_CUDA_CHECK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      int per_sm = 0;
+      DFM_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 32 * (kConsumerWarps + 1), smem));
+      if (per_sm < 1) per_sm = 1;
+      const int64_t ntiles = (nt + tpt - 1) / tpt;
+      const int64_t grid = std::min<int64_t>(ntiles, (int64_t)nsm * per_sm);
+      for (int r = 0; r < R; ++r) {
+        {
+          ::dfm::KernelTimer timer_(DFM_KERNEL_SPMV_T, st);
+          kernel<<<(unsigned)grid, 32 * (kConsumerWarps + 1), smem, st>>>(
+              vals, op->row_stride, recv, nt, tpt, stages, x + r * stride, x0 ? x0 + r * stride : nullptr,
+              y + r * stride, (TA)alpha, op->dev_err);
+        }
+        DFM_LAUNCHED();
+        DFM_CUDA_CHECK(cudaGetLastError());
+      }
+      return DFM_OK;
+    };
+    int rc = DFM_OK;
+    switch (op->nb) {
+      case 1: rc = go(spmv_t_tma_kernel<1, TV, TX, TA>); break;
+      case 3: rc = go(spmv_t_tma_kernel<3, TV, TX, TA>); break;
+      case 6: rc = go(spmv_t_tma_kernel<6, TV, TX, TA>); break;
+      case 10: rc = go(spmv_t_tma_kernel<10, TV, TX, TA>); break;
+      case 15: rc = go(spmv_t_tma_kernel<15, TV, TX, TA>); break;
+      case 21: rc = go(spmv_t_tma_kernel<21, TV, TX, TA>); break;
+      case 28: rc = go(spmv_t_tma_kernel<28, TV, TX, TA>); break;
+      case 36: rc = go(spmv_t_tma_kernel<36, TV, TX, TA>); break;
+      case 45: rc = go(spmv_t_tma_kernel<45, TV, TX, TA>); break;
       default: return set_error(DFM_ERR_UNSUPPORTED, "dfm_apply: unsupported basis size");
     }
     if (rc) return rc;
