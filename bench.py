@@ -37,7 +37,7 @@ METRIC = "stationary solves/s at 1e-6 rel err"
 WORKLOAD = "kuhn20_np4"
 WORKLOAD_DESC = ("20^3 Kuhn cube x 6 = 48,000 jittered tets (jitter 0.2h, seed 0); Np = 4 (15 Zernike functions); "
                  "mu = 0.05; boundary reflection 0.95; unit isotropic source on the x = 0 face at (0, 1/2, 1/2); "
-                 "solve to FP64 relative residual 1e-8 (FP64-residual refinement around FP32 GMRES(128) right-preconditioned by sum_{k<16} B^k)")
+                 "solve to FP64 relative residual 1e-8 (FP64-residual refinement around flexible FP32 GMRES(128) right-preconditioned by sum_{k<16} B^k evaluated on an FP16 copy of the blocks)")
 FP32_LANES_PER_SM = 128
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # operator-application kernel measured by ncu on this workload (y = x0 - B x
@@ -189,7 +189,7 @@ def run_gpu(args):
     dfm.stats_enable(False)
     elapsed_ms = e0.elapsed_time(e1)
     kstats = {k: dfm.kernel_stats(k) for k in (dfm.KERNEL_ASSEMBLE, dfm.KERNEL_SPMV, dfm.KERNEL_SPMV64,
-                                                dfm.KERNEL_DOT, dfm.KERNEL_AXPY)}
+                                                dfm.KERNEL_DOT, dfm.KERNEL_AXPY, dfm.KERNEL_SPMV16)}
     nodes = dfm.op_nodes(op)
     if ws > 1:
         t = torch.tensor([elapsed_ms], device="cuda", dtype=torch.float64)
@@ -256,9 +256,18 @@ def run_gpu(args):
                             "blocks_per_s": 12 * m.n_tets / (ms_asm / n_asm * 1e-3)}
     n_sp, ms_sp = kstats[dfm.KERNEL_SPMV]
     if n_sp:
-        by = spmv_bytes(mesh.n_rows, nb, 4, with_x0=False)  # most launches are polynomial hops without x0
+        # with the 16-bit preconditioner the FP32 launches are the Krylov operator w = z - B z (x0 = z);
+        # without it most are polynomial hops without x0
+        by = spmv_bytes(mesh.n_rows, nb, 4, with_x0=bool(n_sp16))
         ach = by / (ms_sp / n_sp * 1e-3) / 1e9
         kern["spmv_f32"] = {"bound": "hbm", "launches": n_sp, "ms_per_launch": ms_sp / n_sp, "achieved": ach,
+                            "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak, "bytes_per_launch": by}
+    n_sp16, ms_sp16 = kstats[dfm.KERNEL_SPMV16]
+    if n_sp16:
+        # 16-bit blocks; FP32 x, x0 (Horner's z) and y
+        by = mesh.n_rows * (3 * nb * nb * 2 + 4 + nb * 4 * 3)
+        ach = by / (ms_sp16 / n_sp16 * 1e-3) / 1e9
+        kern["spmv_f16"] = {"bound": "hbm", "launches": n_sp16, "ms_per_launch": ms_sp16 / n_sp16, "achieved": ach,
                             "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak, "bytes_per_launch": by}
     n_sp64, ms_sp64 = kstats[dfm.KERNEL_SPMV64]
     if n_sp64:
@@ -271,13 +280,15 @@ def run_gpu(args):
         n, ms = kstats[kid]
         if n:
             kern[name] = {"launches": n, "ms_total": ms}
-    total = {"assemble": ms_asm, "spmv_f32": ms_sp, "spmv_f64vec": ms_sp64,
+    total = {"assemble": ms_asm, "spmv_f32": ms_sp, "spmv_f16": ms_sp16, "spmv_f64vec": ms_sp64,
              "dot": kstats[dfm.KERNEL_DOT][1], "axpy": kstats[dfm.KERNEL_AXPY][1]}
-    dominant = max((k for k in ("assemble", "spmv_f32") if k in kern), key=lambda k: total[k])
+    dominant = max((k for k in ("assemble", "spmv_f32", "spmv_f16") if k in kern), key=lambda k: total[k])
     d = kern[dominant]
     traffic = None
     if dominant == "spmv_f32":
         traffic = MEASURED_TRAFFIC.get((f"spmv_tma_kernel<{nb}, float, float, float>", args.workload))
+    elif dominant == "spmv_f16":
+        traffic = MEASURED_TRAFFIC.get((f"spmv_tma_kernel<{nb}, __half, float, float>", args.workload))
     roofline = {"bound": d["bound"], "achieved": round(d["achieved"], 3), "peak": round(d["peak"], 3),
                 "unit": d["unit"], "frac": round(d["frac"], 4), "traffic": traffic, "kernel": dominant,
                 "peak_source": peak_src if d["bound"] == "hbm" else
@@ -295,7 +306,9 @@ def run_gpu(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32 blocks/Krylov, f64 residual",
+        "dtype": ("f32 blocks, f16 preconditioner copy, f32 Krylov, f64 residual" if args.precond == "f16" else
+                  "f32 blocks, bf16 preconditioner copy, f32 Krylov, f64 residual" if args.precond == "bf16" else
+                  "f32 blocks/Krylov, f64 residual"),
         "data": "synthetic",
         "config": {"workload": args.workload, "desc": WORKLOAD_DESC if args.workload == WORKLOAD else args.workload,
                    "n_tets": int(m.n_tets), "n_rows": int(mesh.n_rows), "nb": nb, "tol": tol,
@@ -612,7 +625,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparator", action="store_true")
-    ap.add_argument("--precond", choices=["f32", "f16", "bf16"], default="f32",
+    ap.add_argument("--precond", choices=["f32", "f16", "bf16"], default="f16",
                     help="precision of the blocks used by the polynomial preconditioner's hops")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--ref-apps", type=int, default=600)

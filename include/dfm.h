@@ -283,6 +283,7 @@ int dfm_adjoint(const dfm_op* op, const dfm_params* params, const double* rho, i
 #define DFM_KERNEL_AXPY 4     /* Krylov multi-axpy */
 #define DFM_KERNEL_SPMV64 5   /* y = x0 + alpha B x with FP64 vectors (residuals) */
 #define DFM_KERNEL_CONTRACT 6 /* fused lambda^T (dB/dmu) rho per tet */
+#define DFM_KERNEL_SPMV16 7   /* y = x0 + alpha B x on the 16-bit preconditioner copy */
 long long dfm_launch_count(void);
 int dfm_stats_enable(int on);
 int dfm_stats_reset(void);

@@ -455,7 +455,8 @@ int launch(const dfm_op* op, const TX* x, const TX* x0, TX* y, int R, double alp
       const int64_t ntiles = (op->nrows + rpt - 1) / rpt;
       const int64_t grid = std::min<int64_t>(ntiles, (int64_t)nsm * per_sm);
       {
-        ::dfm::KernelTimer timer_(sizeof(TX) == 8 ? DFM_KERNEL_SPMV64 : DFM_KERNEL_SPMV, st);
+        ::dfm::KernelTimer timer_(sizeof(TX) == 8 ? DFM_KERNEL_SPMV64 : (sizeof(TV) == 2 ? DFM_KERNEL_SPMV16 : DFM_KERNEL_SPMV),
+                                 st);
         kernel<<<(unsigned)grid, 32 * (kConsumerWarps + 1), smem, st>>>(cb, op->row_stride, recv, op->nrows, rpt,
                                                                          stages, x, x0, y, R, (TA)alpha, stage_x0,
                                                                          op->dev_err);

@@ -431,7 +431,7 @@ def gauss_legendre(q: int):
     return x, w
 
 
-KERNEL_ASSEMBLE, KERNEL_SPMV, KERNEL_SPMV_T, KERNEL_DOT, KERNEL_AXPY, KERNEL_SPMV64, KERNEL_CONTRACT = range(7)
+KERNEL_ASSEMBLE, KERNEL_SPMV, KERNEL_SPMV_T, KERNEL_DOT, KERNEL_AXPY, KERNEL_SPMV64, KERNEL_CONTRACT, KERNEL_SPMV16 = range(8)
 
 
 def launch_count() -> int:
