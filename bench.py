@@ -37,7 +37,19 @@ METRIC = "stationary solves/s at 1e-6 rel err"
 WORKLOAD = "kuhn20_np4"
 WORKLOAD_DESC = ("20^3 Kuhn cube x 6 = 48,000 jittered tets (jitter 0.2h, seed 0); Np = 4 (15 Zernike functions); "
                  "mu = 0.05; boundary reflection 0.95; unit isotropic source on the x = 0 face at (0, 1/2, 1/2); "
-                 "solve to FP64 relative residual 1e-8 (FP64-residual refinement around flexible FP32 GMRES(128) right-preconditioned by sum_{k<16} B^k evaluated on an FP16 copy of the blocks)")
+                 "solve to FP64 relative residual 1e-8")
+SOLVER_DESC = {
+    "f32": "FP64-residual refinement around FP32 GMRES(128) right-preconditioned by sum_{k<16} B^k",
+    "f16": ("FP64-residual refinement around flexible FP32 GMRES(128) right-preconditioned by sum_{k<16} B^k "
+            "evaluated on an FP16 copy of the blocks"),
+    "bf16": ("FP64-residual refinement around flexible FP32 GMRES(128) right-preconditioned by sum_{k<16} B^k "
+             "evaluated on a BF16 copy of the blocks"),
+}
+# Operator applications of the FP64 solve on the 20^3 workload: FP64 GMRES(128)
+# right-preconditioned by sum_{k<16} B^k reaches the 1e-8 residual after 1,809
+# applications (the count the FP64 comparator path records).  The oracle arm
+# charges its measured per-application cost this many times.
+REF_APPLICATIONS = {"kuhn20_np4": 1809}
 FP32_LANES_PER_SM = 128
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # operator-application kernel measured by ncu on this workload (y = x0 - B x
@@ -111,6 +123,19 @@ def _dist():
     return ws, rank, local
 
 
+def max_over_ranks(value, ws, device):
+    """The largest of every rank's `value` (a time): replicas run independently
+    and the job takes as long as its slowest rank."""
+    if ws <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
@@ -124,10 +149,66 @@ def flops_per_node(Np: int) -> int:
     return 2 * nb * nb + 2 * (6 * Np + 4 * nb) + 130
 
 
-def spmv_bytes(n_rows, nb, vec_bytes, with_x0=True):
-    """Algorithmic bytes of one y = x0 + alpha B x: blocks (FP32) and row map
-    read once, x read once, x0 read once, y written once."""
-    return n_rows * (3 * nb * nb * 4 + 4 + nb * vec_bytes * (3 if with_x0 else 2))
+def spmv_bytes(n_rows, nb, vec_bytes, with_x0=True, block_bytes=4):
+    """Algorithmic bytes of one y = x0 + alpha B x: blocks and row map read
+    once, x read once, x0 read once, y written once."""
+    return n_rows * (3 * nb * nb * block_bytes + 4 + nb * vec_bytes * (3 if with_x0 else 2))
+
+
+def summarize_kernels(kstats, n_rows, n_tets, Np, nodes, nsm, peaks, peak_src, workload, precond):
+    """Per-kernel rooflines of a timed region and the dominant kernel's.
+    kstats: name -> (launches, total ms) for assemble, spmv_f32, spmv_16bit
+    (the preconditioner's hops on the 16-bit copy, precond "f16" or "bf16"),
+    spmv_f64vec, dot, axpy.  Returns (per-kernel dict, total ms per kernel,
+    roofline of the kernel with the largest total among assemble/spmv)."""
+    nb = (Np + 1) * (Np + 2) // 2
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak_tflops = nsm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    hbm_peak = float(peaks.get("hbm_gbs", HBM_PEAK_FALLBACK))
+    kern = {}
+
+    def hbm(name, n, ms, by):
+        ach = by / (ms / n * 1e-3) / 1e9
+        kern[name] = {"bound": "hbm", "launches": n, "ms_per_launch": ms / n, "achieved": ach, "peak": hbm_peak,
+                      "unit": "GB/s", "frac": ach / hbm_peak, "bytes_per_launch": by}
+
+    n_asm, ms_asm = kstats["assemble"]
+    if n_asm:
+        fl = nodes * flops_per_node(Np)  # per launch (every launch of the step is identical)
+        ach = fl / (ms_asm / n_asm * 1e-3) / 1e12
+        kern["assemble"] = {"bound": "alu", "launches": n_asm, "ms_per_launch": ms_asm / n_asm,
+                            "achieved": ach, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
+                            "frac": ach / fp32_peak_tflops, "nodes_per_launch": nodes,
+                            "flops_per_node": flops_per_node(Np),
+                            "blocks_per_s": 12 * n_tets / (ms_asm / n_asm * 1e-3)}
+    n, ms = kstats["spmv_f32"]
+    if n:
+        # with a 16-bit preconditioner copy the FP32 launches are the Krylov
+        # operator w = z - B z (x0 = z); without it most are polynomial hops
+        # without x0
+        hbm("spmv_f32", n, ms, spmv_bytes(n_rows, nb, 4, with_x0=precond != "f32"))
+    n, ms = kstats["spmv_16bit"]
+    if n:
+        hbm("spmv_16bit", n, ms, spmv_bytes(n_rows, nb, 4, with_x0=True, block_bytes=2))
+    n, ms = kstats["spmv_f64vec"]
+    if n:
+        hbm("spmv_f64vec", n, ms, spmv_bytes(n_rows, nb, 8))
+    for name in ("dot", "axpy"):
+        n, ms = kstats[name]
+        if n:
+            kern[name] = {"launches": n, "ms_total": ms}
+    total = {k: v[1] for k, v in kstats.items()}
+    dominant = max((k for k in ("assemble", "spmv_f32", "spmv_16bit") if k in kern), key=lambda k: total[k])
+    d = kern[dominant]
+    inst = {"spmv_f32": f"spmv_tma_kernel<{nb}, float, float, float>",
+            "spmv_16bit": f"spmv_tma_kernel<{nb}, {'__half' if precond == 'f16' else '__nv_bfloat16'}, float, float>"
+            }.get(dominant)
+    traffic = MEASURED_TRAFFIC.get((inst, workload)) if inst else None
+    roofline = {"bound": d["bound"], "achieved": round(d["achieved"], 3), "peak": round(d["peak"], 3),
+                "unit": d["unit"], "frac": round(d["frac"], 4), "traffic": traffic, "kernel": dominant,
+                "peak_source": peak_src if d["bound"] == "hbm" else
+                f"{nsm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz"}
+    return kern, total, roofline
 
 
 def run_gpu(args):
@@ -191,10 +272,7 @@ def run_gpu(args):
     kstats = {k: dfm.kernel_stats(k) for k in (dfm.KERNEL_ASSEMBLE, dfm.KERNEL_SPMV, dfm.KERNEL_SPMV64,
                                                 dfm.KERNEL_DOT, dfm.KERNEL_AXPY, dfm.KERNEL_SPMV16)}
     nodes = dfm.op_nodes(op)
-    if ws > 1:
-        t = torch.tensor([elapsed_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = max_over_ranks(elapsed_ms, ws, "cuda")
 
     # ---- e2e: C ABI from host buffers, copies inside the timed region --------
     e2e = None
@@ -224,10 +302,7 @@ def run_gpu(args):
             e2e_step()
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        if ws > 1:
-            t = torch.tensor([dt], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = max_over_ranks(dt, ws, "cuda")
         h2d = verts.nbytes + tets.nbytes + 4 * m.n_tets * 8 + rows.nbytes
         d2h = host_rho.numel() * 8
         e2e = {"value": ws * max(1, args.steps) / dt, "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
@@ -240,59 +315,13 @@ def run_gpu(args):
 
     peaks, peak_src = _peaks()
     nsm = torch.cuda.get_device_properties(local).multi_processor_count
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak_tflops = nsm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    hbm_peak = float(peaks.get("hbm_gbs", HBM_PEAK_FALLBACK))
     nb = op.nb
-
-    kern = {}
-    n_asm, ms_asm = kstats[dfm.KERNEL_ASSEMBLE]
-    if n_asm:
-        fl = nodes * flops_per_node(Np)  # per launch (the last assembly; every launch is identical)
-        ach = fl / (ms_asm / n_asm * 1e-3) / 1e12
-        kern["assemble"] = {"bound": "alu", "launches": n_asm, "ms_per_launch": ms_asm / n_asm,
-                            "achieved": ach, "peak": fp32_peak_tflops, "unit": "TFLOP/s", "frac": ach / fp32_peak_tflops,
-                            "nodes_per_launch": nodes, "flops_per_node": flops_per_node(Np),
-                            "blocks_per_s": 12 * m.n_tets / (ms_asm / n_asm * 1e-3)}
-    n_sp, ms_sp = kstats[dfm.KERNEL_SPMV]
-    if n_sp:
-        # with the 16-bit preconditioner the FP32 launches are the Krylov operator w = z - B z (x0 = z);
-        # without it most are polynomial hops without x0
-        by = spmv_bytes(mesh.n_rows, nb, 4, with_x0=bool(n_sp16))
-        ach = by / (ms_sp / n_sp * 1e-3) / 1e9
-        kern["spmv_f32"] = {"bound": "hbm", "launches": n_sp, "ms_per_launch": ms_sp / n_sp, "achieved": ach,
-                            "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak, "bytes_per_launch": by}
-    n_sp16, ms_sp16 = kstats[dfm.KERNEL_SPMV16]
-    if n_sp16:
-        # 16-bit blocks; FP32 x, x0 (Horner's z) and y
-        by = mesh.n_rows * (3 * nb * nb * 2 + 4 + nb * 4 * 3)
-        ach = by / (ms_sp16 / n_sp16 * 1e-3) / 1e9
-        kern["spmv_f16"] = {"bound": "hbm", "launches": n_sp16, "ms_per_launch": ms_sp16 / n_sp16, "achieved": ach,
-                            "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak, "bytes_per_launch": by}
-    n_sp64, ms_sp64 = kstats[dfm.KERNEL_SPMV64]
-    if n_sp64:
-        by = spmv_bytes(mesh.n_rows, nb, 8)
-        ach = by / (ms_sp64 / n_sp64 * 1e-3) / 1e9
-        kern["spmv_f64vec"] = {"bound": "hbm", "launches": n_sp64, "ms_per_launch": ms_sp64 / n_sp64,
-                               "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
-                               "bytes_per_launch": by}
-    for name, kid in (("dot", dfm.KERNEL_DOT), ("axpy", dfm.KERNEL_AXPY)):
-        n, ms = kstats[kid]
-        if n:
-            kern[name] = {"launches": n, "ms_total": ms}
-    total = {"assemble": ms_asm, "spmv_f32": ms_sp, "spmv_f16": ms_sp16, "spmv_f64vec": ms_sp64,
-             "dot": kstats[dfm.KERNEL_DOT][1], "axpy": kstats[dfm.KERNEL_AXPY][1]}
-    dominant = max((k for k in ("assemble", "spmv_f32", "spmv_f16") if k in kern), key=lambda k: total[k])
-    d = kern[dominant]
-    traffic = None
-    if dominant == "spmv_f32":
-        traffic = MEASURED_TRAFFIC.get((f"spmv_tma_kernel<{nb}, float, float, float>", args.workload))
-    elif dominant == "spmv_f16":
-        traffic = MEASURED_TRAFFIC.get((f"spmv_tma_kernel<{nb}, __half, float, float>", args.workload))
-    roofline = {"bound": d["bound"], "achieved": round(d["achieved"], 3), "peak": round(d["peak"], 3),
-                "unit": d["unit"], "frac": round(d["frac"], 4), "traffic": traffic, "kernel": dominant,
-                "peak_source": peak_src if d["bound"] == "hbm" else
-                f"{nsm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz"}
+    kern, total, roofline = summarize_kernels(
+        {"assemble": kstats[dfm.KERNEL_ASSEMBLE], "spmv_f32": kstats[dfm.KERNEL_SPMV],
+         "spmv_16bit": kstats[dfm.KERNEL_SPMV16], "spmv_f64vec": kstats[dfm.KERNEL_SPMV64],
+         "dot": kstats[dfm.KERNEL_DOT], "axpy": kstats[dfm.KERNEL_AXPY]},
+        n_rows=mesh.n_rows, n_tets=int(m.n_tets), Np=Np, nodes=nodes, nsm=nsm, peaks=peaks, peak_src=peak_src,
+        workload=args.workload, precond=args.precond)
 
     iters = [i[0] for i in infos]
     res = {
@@ -310,7 +339,9 @@ def run_gpu(args):
                   "f32 blocks, bf16 preconditioner copy, f32 Krylov, f64 residual" if args.precond == "bf16" else
                   "f32 blocks/Krylov, f64 residual"),
         "data": "synthetic",
-        "config": {"workload": args.workload, "desc": WORKLOAD_DESC if args.workload == WORKLOAD else args.workload,
+        "config": {"workload": args.workload,
+                   "desc": (WORKLOAD_DESC if args.workload == WORKLOAD else args.workload) + "; "
+                   + SOLVER_DESC[args.precond],
                    "n_tets": int(m.n_tets), "n_rows": int(mesh.n_rows), "nb": nb, "tol": tol,
                    "restart": args.restart or 128, "poly_degree": args.poly or 16, "precond": args.precond, "l2": "inputs larger than L2 (operator %.0f MB)" % (op.bytes / 1e6),
                    "parallelism": f"replicas x{ws}"},
@@ -421,12 +452,11 @@ def run_reference(args):
     ws, rank, local = _dist()
     if rank != 0:
         return
-    # operator applications the oracle's GMRES-IR-equivalent solve needs: the
-    # oracle's own restarted GMRES iteration count on this workload, measured
-    # once on its sparsity pattern is not available without a full oracle
-    # assembly, so the reference arm uses the count of the same solver class
-    # recorded with the workload (FP64 GMRES(64) to 1e-8).
-    apps = args.ref_apps
+    # a full oracle solve takes about half an hour of CPU time, so each step
+    # times the oracle on a bounded sample (assembly of random face pairs and
+    # full-size GMRES iterations) and extrapolates to the whole solve with the
+    # FP64 path's application count
+    apps = args.ref_apps or REF_APPLICATIONS.get(args.workload, 2000)
     vals = []
     last = None
     for i in range(args.warmup + args.steps):
@@ -438,7 +468,9 @@ def run_reference(args):
     res = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": ws,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(vals) * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": args.workload, "desc": WORKLOAD_DESC if args.workload == WORKLOAD else args.workload},
+           "config": {"workload": args.workload,
+                      "desc": (WORKLOAD_DESC if args.workload == WORKLOAD else args.workload)
+                      + "; FP64 CPU oracle (adaptive assembly to 1e-13, restarted GMRES), timed on a bounded sample"},
            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": last[1], "kind": "oracle", "sample": last[0]},
            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(res))
@@ -628,7 +660,8 @@ def main():
     ap.add_argument("--precond", choices=["f32", "f16", "bf16"], default="f16",
                     help="precision of the blocks used by the polynomial preconditioner's hops")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
-    ap.add_argument("--ref-apps", type=int, default=600)
+    ap.add_argument("--ref-apps", type=int, default=0,
+                    help="reference arm: operator applications charged per solve (0 = the FP64 path's count)")
     ap.add_argument("--mode", choices=["solve", "apply", "adjoint", "batched"], default="solve")
     ap.add_argument("--rhs", type=int, default=0, help="batched mode: number of right-hand sides (0 = all)")
     ap.add_argument("--batch", type=int, default=0, help="batched mode: right-hand sides per lockstep group")
