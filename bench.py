@@ -40,9 +40,9 @@ WORKLOAD_DESC = ("20^3 Kuhn cube x 6 = 48,000 jittered tets (jitter 0.2h, seed 0
                  "solve to FP64 relative residual 1e-8")
 SOLVER_DESC = {
     "f32": "FP64-residual refinement around FP32 GMRES(128) right-preconditioned by sum_{k<16} B^k",
-    "f16": ("FP64-residual refinement around flexible FP32 GMRES(128) right-preconditioned by sum_{k<16} B^k "
+    "f16": ("FP64-residual refinement around flexible FP32 GMRES(128) right-preconditioned by sum_{k<32} B^k "
             "evaluated on an FP16 copy of the blocks"),
-    "bf16": ("FP64-residual refinement around flexible FP32 GMRES(128) right-preconditioned by sum_{k<16} B^k "
+    "bf16": ("FP64-residual refinement around flexible FP32 GMRES(128) right-preconditioned by sum_{k<32} B^k "
              "evaluated on a BF16 copy of the blocks"),
 }
 # Operator applications of the FP64 solve on the 20^3 workload: FP64 GMRES(128)
@@ -52,11 +52,11 @@ SOLVER_DESC = {
 REF_APPLICATIONS = {"kuhn20_np4": 1809}
 FP32_LANES_PER_SM = 128
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# operator-application kernel measured by ncu on this workload (y = x0 - B x
-# launch of the apply mode; see profiles/spmv_tma_kuhn20_np4.md).  Keyed by the
-# kernel instantiation and workload; reset to None whenever the kernel changes.
+# step's dominant kernel measured by ncu on this workload (mean of two
+# launches; profiles/hop_kuhn20_np4.md).  Keyed by the kernel instantiation and
+# workload; an entry is dropped whenever its kernel changes.
 PRECOND = {"f32": 0, "f16": 3, "bf16": 2}
-MEASURED_TRAFFIC = {("spmv_tma_kernel<15, float, float, float>", "kuhn20_np4"): 547.2e6}
+MEASURED_TRAFFIC = {("hop_kernel<15, __half>", "kuhn20_np4"): 303.9e6}
 HBM_PEAK_FALLBACK = 6800.0
 
 
@@ -200,9 +200,8 @@ def summarize_kernels(kstats, n_rows, n_tets, Np, nodes, nsm, peaks, peak_src, w
     total = {k: v[1] for k, v in kstats.items()}
     dominant = max((k for k in ("assemble", "spmv_f32", "spmv_16bit") if k in kern), key=lambda k: total[k])
     d = kern[dominant]
-    inst = {"spmv_f32": f"spmv_tma_kernel<{nb}, float, float, float>",
-            "spmv_16bit": f"spmv_tma_kernel<{nb}, {'__half' if precond == 'f16' else '__nv_bfloat16'}, float, float>"
-            }.get(dominant)
+    inst = {"spmv_f32": f"spmv_tma_kernel<{nb}, 1, float, float, float>",
+            "spmv_16bit": f"hop_kernel<{nb}, {'__half' if precond == 'f16' else '__nv_bfloat16'}>"}.get(dominant)
     traffic = MEASURED_TRAFFIC.get((inst, workload)) if inst else None
     roofline = {"bound": d["bound"], "achieved": round(d["achieved"], 3), "peak": round(d["peak"], 3),
                 "unit": d["unit"], "frac": round(d["frac"], 4), "traffic": traffic, "kernel": dominant,
@@ -343,7 +342,7 @@ def run_gpu(args):
                    "desc": (WORKLOAD_DESC if args.workload == WORKLOAD else args.workload) + "; "
                    + SOLVER_DESC[args.precond],
                    "n_tets": int(m.n_tets), "n_rows": int(mesh.n_rows), "nb": nb, "tol": tol,
-                   "restart": args.restart or 128, "poly_degree": args.poly or 16, "precond": args.precond, "l2": "inputs larger than L2 (operator %.0f MB)" % (op.bytes / 1e6),
+                   "restart": args.restart or 128, "poly_degree": args.poly or (16 if args.precond == "f32" else 32), "precond": args.precond, "l2": "inputs larger than L2 (operator %.0f MB)" % (op.bytes / 1e6),
                    "parallelism": f"replicas x{ws}"},
         "roofline": roofline,
         "e2e": e2e,

@@ -204,7 +204,8 @@ typedef struct {
                         solve also stops when a restart cycle gains less than 10% */
   int transpose;     /* 1: solve (I - B)^T x = rho0 instead (the adjoint equation) */
   int poly_degree;   /* right preconditioner p(B) = sum_{k<d} B^k, so GMRES runs on I - B^d:
-                        GMRES_IR inner solves: 0 = 16; GMRES on an FP64 operator: 0 = none */
+                        GMRES_IR inner solves: 0 = 16 (32 with a 16-bit precond_precision);
+                        GMRES on an FP64 operator: 0 = none */
   int precond_precision; /* GMRES_IR: 0 = the polynomial preconditioner uses the operator itself;
                         DFM_F16 or DFM_BF16 = its hops use a 16-bit copy of the blocks (made once
                         per assembly, half the bytes per hop) and the inner solver is flexible
@@ -236,6 +237,19 @@ int dfm_solve(const dfm_op* op, const double* rho0, int R, double* rho, const df
  * DFM_SOLVE_GMRES_IR, no transpose.  Errors as dfm_solve. */
 int dfm_solve_combo(const dfm_op* const* ops, int K, const double* coef_host, const double* rho0, int R, double* rho,
                     const dfm_solve_opts* opts, void* stream, dfm_solve_info* info);
+
+/* The inexact polynomial preconditioner of the flexible inner solve
+ * (dfm_solve_opts.precond_precision), on its own.  The paper gives no
+ * solver; this is a building block for callers' own Krylov methods:
+ *   z_r = sum_{k<degree} B~^k x_r,  r < R,
+ * B~ = the FP16 (precision DFM_F16) or BF16 (DFM_BF16) rounding, to nearest,
+ * of op's FP32 blocks (made on first use and again after each assembly),
+ * evaluated by Horner's rule z <- x + B~ z with FP32 vectors and FP32
+ * accumulation.  op: FP32 operator; x, z: device FP32 [R][rows][nb], 16-byte
+ * aligned, z must not alias x; 1 <= degree <= 64.  Uses a scratch of
+ * 3 R rows NBP floats (NBP = nb rounded up to 8) taken with cudaMallocAsync
+ * on the stream and released in stream order.  Asynchronous. */
+int dfm_precond_apply(const dfm_op* op, int precision, int degree, const float* x, float* z, int R, void* stream);
 
 /* Interior density functional (Sec. 4.1, Eq. IntDens, c = 1): for each listed
  * tet e, the coefficients g_e of

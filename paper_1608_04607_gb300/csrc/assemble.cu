@@ -368,6 +368,8 @@ extern "C" int dfm_assemble(const dfm_mesh* mesh, const dfm_params* p, void* str
 
 extern "C" void dfm_op_destroy(dfm_op* op) {
   if (!op) return;
+  forget_sweep(op->vals);
+  forget_sweep(op->lp_vals);
   cudaFree(op->vals);
   cudaFree(op->work);
   cudaFree(op->swork);

@@ -91,7 +91,21 @@ int apply_combo_impl(const dfm_op* const* ops, int K, const double* coef, const 
                      int R, double alpha, int xtype, cudaStream_t st);
 // 16-bit copy of op's blocks (made on first use after each assembly); returns a
 // view operator that applies it (same mesh, layout and error flag)
-int lowp_view(const dfm_op* op, int precision, cudaStream_t st, dfm_op* view);
+// Consecutive applications of one operator alternate the direction in which
+// they sweep its rows (0 or 1 for this launch; state kept per values buffer);
+// forget_sweep drops the state of a buffer that is being freed.
+int next_sweep_direction(const void* vals);
+void forget_sweep(const void* vals);
+// Polynomial-preconditioner hops on a 16-bit copy of the blocks (hop.cu).
+// Padded width of a face's coefficients in hop vectors and in the copy.
+inline int hop_nbp(int nb) { return (nb + 7) / 8 * 8; }
+// (re)builds op->lp_vals (precision DFM_F16 or DFM_BF16) from the FP32 blocks
+int prepare_lowp(const dfm_op* op, int precision, cudaStream_t st);
+// vp[row][0..nbp) = v[row][0..nb), zero padded; rows = R * nrows
+int hop_pack(const float* v, float* vp, int64_t rows, int nb, cudaStream_t st);
+// y = x0 + B~ x for R right-hand sides, x and x0 padded; y padded (out_padded)
+// or in the unpadded [R][rows][nb] layout
+int hop_apply(const dfm_op* op, const float* xp, const float* x0p, float* y, int R, int out_padded, cudaStream_t st);
 // implemented in quad.cu
 int gauss_legendre_device(int q, double* x, double* w, cudaStream_t st);
 }  // namespace dfm

@@ -15,6 +15,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "dfm_internal.cuh"
@@ -378,9 +379,39 @@ int ensure_work(const dfm_op* cop, int64_t bytes) {
 // cost small.  x holds the initial guess; tol is relative to |b|; operator
 // applications are added to *iters, capped by max_iter.  *est returns the
 // last relative residual estimate.  t1, t2: scratch vectors of length n.
+// Flexible variant: the preconditioner's hops run on the operator's 16-bit
+// copy (hop_apply) through zero-padded FP32 vectors vp (the packed v_j), ha,
+// hb ([R][rows][NBP] each); the result z_j = p~(B) v_j lands in Z.
+struct Hop {
+  const dfm_op* op = nullptr;
+  float* vp = nullptr;
+  float* ha = nullptr;
+  float* hb = nullptr;
+};
+
+// z = sum_{k<d} B~^k v for R vectors v ([R][n]) by Horner, z <- v + B~ z.
+inline int hop_horner(const Ctx& c, const Hop& hp, int R, int d, const float* v, float* z) {
+  const int64_t rows = (int64_t)R * c.op->nrows;
+  if (d == 1) {
+    DFM_CUDA_CHECK(cudaMemcpyAsync(z, v, sizeof(float) * rows * c.op->nb, cudaMemcpyDeviceToDevice, c.st));
+    return DFM_OK;
+  }
+  int rc = hop_pack(v, hp.vp, rows, c.op->nb, c.st);
+  if (rc) return rc;
+  const float* src = hp.vp;
+  for (int k = 1; k < d; ++k) {
+    const bool last = (k == d - 1);
+    float* dst = last ? z : ((k & 1) ? hp.ha : hp.hb);
+    rc = hop_apply(hp.op, src, hp.vp, dst, R, last ? 0 : 1, c.st);
+    if (rc) return rc;
+    src = dst;
+  }
+  return DFM_OK;
+}
+
 template <typename T>
 int gmres(const Ctx& c, const T* b, T* x, double tol, int m, int d, int max_iter, int* iters, double* est, T* V,
-          T* tmp, T* t1, T* t2, T* h_dev, T* partial, T* red_dev, const dfm_op* lp = nullptr, T* Z = nullptr) {
+          T* tmp, T* t1, T* t2, T* h_dev, T* partial, T* red_dev, const Hop* lp = nullptr, T* Z = nullptr) {
   const int64_t n = c.n;
   const int xtype = sizeof(T) == 8 ? DFM_F64 : DFM_F32;
   if (d < 1) d = 1;
@@ -439,14 +470,12 @@ int gmres(const Ctx& c, const T* b, T* x, double tol, int m, int d, int max_iter
       if (lp) {
         // flexible step: z_j = p~(B) v_j by Horner on the 16-bit copy, w = z_j - B z_j
         T* zj = Z + (int64_t)j * n;
-        const T* src = vj;
-        if (d == 1) DFM_CUDA_CHECK(cudaMemcpyAsync(zj, vj, sizeof(T) * n, cudaMemcpyDeviceToDevice, c.st));
-        for (int k = 1; k < d; ++k) {
-          T* dst = (k == d - 1) ? zj : ((k & 1) ? t1 : t2);
-          rc = apply_impl(lp, src, vj, dst, 1, 1.0, 0, xtype, c.st);
-          if (rc) return rc;
-          src = dst;
+        if constexpr (std::is_same<T, float>::value) {
+          rc = hop_horner(c, *lp, 1, d, vj, zj);
+        } else {
+          rc = set_error(DFM_ERR_UNSUPPORTED, "dfm_solve: 16-bit preconditioner hops need FP32 Krylov vectors");
         }
+        if (rc) return rc;
         *iters += d;
         rc = ctx_apply(c, zj, zj, w, 1, -1.0, xtype);
       } else {
@@ -615,7 +644,7 @@ int bscale(const Ctx& c, int R, T* w, int64_t wldr, const std::vector<double>& f
 template <typename T>
 int gmres_batched(const Ctx& c, int R, const T* b, T* x, double tol, int m, int d, int max_iter, int* iters,
                   std::vector<double>* est, T* V, T* tmp, T* t1, T* t2, T* h_dev, T* partial, T* red_dev,
-                  const dfm_op* lp = nullptr, T* Z = nullptr) {
+                  const Hop* lp = nullptr, T* Z = nullptr) {
   const int64_t n = c.n;
   const int64_t Rn = (int64_t)R * n;
   const int xtype = sizeof(T) == 8 ? DFM_F64 : DFM_F32;
@@ -683,14 +712,12 @@ int gmres_batched(const Ctx& c, int R, const T* b, T* x, double tol, int m, int 
       if (lp) {
         // flexible step: z_j = p~(B) v_j on the 16-bit copy, w = z_j - B z_j
         T* zj = Z + (int64_t)j * Rn;
-        const T* src = vj;
-        if (d == 1) DFM_CUDA_CHECK(cudaMemcpyAsync(zj, vj, sizeof(T) * Rn, cudaMemcpyDeviceToDevice, c.st));
-        for (int k = 1; k < d; ++k) {
-          T* dst = (k == d - 1) ? zj : ((k & 1) ? t1 : t2);
-          rc = apply_impl(lp, src, vj, dst, R, 1.0, 0, xtype, c.st);
-          if (rc) return rc;
-          src = dst;
+        if constexpr (std::is_same<T, float>::value) {
+          rc = hop_horner(c, *lp, R, d, vj, zj);
+        } else {
+          rc = set_error(DFM_ERR_UNSUPPORTED, "dfm_solve: 16-bit preconditioner hops need FP32 Krylov vectors");
         }
+        if (rc) return rc;
         *iters += d;
         rc = ctx_apply(c, zj, zj, w, R, -1.0, xtype);
       } else {
@@ -853,7 +880,9 @@ int solve_impl(const dfm_op* op, const dfm_op* const* combo, int K, const double
   const int max_iter = opts->max_iter > 0 ? opts->max_iter : 20000;
   const int m = opts->restart > 0 ? std::min(opts->restart, kMaxKrylov) : 128;
   const double inner_tol = opts->inner_tol > 0 ? opts->inner_tol : 1e-6;
-  const int poly = opts->poly_degree > 0 ? std::min(opts->poly_degree, 64) : 16;
+  // default degree: 32 when the hops run on the 16-bit copy (half the bytes
+  // per hop moves the balance between hops and Gram-Schmidt work), else 16
+  const int poly = opts->poly_degree > 0 ? std::min(opts->poly_degree, 64) : (opts->precond_precision ? 32 : 16);
   const bool use_lp = opts->precond_precision != 0 && method == DFM_SOLVE_GMRES_IR && !combo && !opts->transpose;
   if (opts->precond_precision != 0 && opts->precond_precision != DFM_F16 && opts->precond_precision != DFM_BF16)
     return set_error(DFM_ERR_ARG, "dfm_solve: precond_precision must be 0, DFM_F16 or DFM_BF16");
@@ -881,7 +910,8 @@ int solve_impl(const dfm_op* op, const dfm_op* const* combo, int K, const double
   const bool batched = (method == DFM_SOLVE_GMRES_IR && R > 1);
   int Rg = 1;
   if (batched) {
-    const int64_t per_rhs = (int64_t)(m + 6 + (use_lp ? m : 0)) * n * 4;
+    const int64_t per_rhs =
+        (int64_t)(m + 6 + (use_lp ? m : 0)) * n * 4 + (use_lp ? 3 * op->nrows * hop_nbp(op->nb) * 4 : 0);
     const int64_t cap = opts->batch > 0 ? opts->batch : 16;
     Rg = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)R, cap, (int64_t(24) << 30) / per_rhs}));
   }
@@ -892,8 +922,9 @@ int solve_impl(const dfm_op* op, const dfm_op* const* combo, int K, const double
   int64_t bytes = 0;
   const bool gather = combo && K > 1 && batched && R > Rg;
   bytes += (2 * (int64_t)Rg + 2 + (gather ? 2 * (int64_t)Rg : 0)) * n * 8 + 8192;  // r, tmp64, xold [, gather b/x]
-  const int64_t inner_bytes =
-      (int64_t)(m + 7 + (use_lp ? m : 0)) * Rg * n * es + 9 * 256;  // V (m+1), tmp, t1, t2, b, x [, Z (m)]
+  const int64_t hop_elems = use_lp ? (int64_t)Rg * op->nrows * hop_nbp(op->nb) : 0;  // one padded hop vector
+  const int64_t inner_bytes = (int64_t)(m + 7 + (use_lp ? m : 0)) * Rg * n * es + 3 * hop_elems * 4 +
+                              12 * 256;  // V (m+1), tmp, t1, t2, b, x [, Z (m), vp, ha, hb]
   bytes += inner_bytes + 4096;
   const int64_t part_elems = std::max<int64_t>((int64_t)kRedBlocks * (kMaxKrylov + 8), (int64_t)kBRedBlocks * hcap);
   bytes += (part_elems + 2 * hcap + 2 * Rg + 256) * 8 + 4096;  // partials, h, red
@@ -909,12 +940,13 @@ int solve_impl(const dfm_op* op, const dfm_op* const* combo, int K, const double
   double* h64 = W.take<double>(2 * hcap);
   double* red64 = W.take<double>(std::max(8, 2 * Rg));
   char* inner_base = W.take<char>(inner_bytes);
-  dfm_op lpv;
-  const dfm_op* lp = nullptr;
+  Hop hop;
+  const Hop* lp = nullptr;
   if (use_lp) {
-    rc = lowp_view(op, opts->precond_precision, c.st, &lpv);
+    rc = prepare_lowp(op, opts->precond_precision, c.st);
     if (rc) return rc;
-    lp = &lpv;
+    hop.op = op;
+    lp = &hop;
   }
   if (batched) {
     Work Wi{inner_base};
@@ -925,6 +957,11 @@ int solve_impl(const dfm_op* op, const dfm_op* const* combo, int K, const double
     float* bf = Wi.take<float>((int64_t)Rg * n);
     float* xf = Wi.take<float>((int64_t)Rg * n);
     float* Zb = use_lp ? Wi.take<float>((int64_t)m * Rg * n) : nullptr;
+    if (use_lp) {
+      hop.vp = Wi.take<float>(hop_elems);
+      hop.ha = Wi.take<float>(hop_elems);
+      hop.hb = Wi.take<float>(hop_elems);
+    }
     float* part32 = reinterpret_cast<float*>(part64);
     float* h32 = reinterpret_cast<float*>(h64);
     float* red32 = reinterpret_cast<float*>(red64);
@@ -1084,6 +1121,11 @@ int solve_impl(const dfm_op* op, const dfm_op* const* combo, int K, const double
       float* bf = Wi.take<float>(n);
       float* xf = Wi.take<float>(n);
       float* Zs = use_lp ? Wi.take<float>((int64_t)m * n) : nullptr;
+      if (use_lp) {
+        hop.vp = Wi.take<float>(hop_elems);
+        hop.ha = Wi.take<float>(hop_elems);
+        hop.hb = Wi.take<float>(hop_elems);
+      }
       float* part32 = reinterpret_cast<float*>(part64);
       float* h32 = reinterpret_cast<float*>(h64);
       float* red32 = reinterpret_cast<float*>(red64);

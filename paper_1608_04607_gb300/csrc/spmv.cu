@@ -17,13 +17,16 @@
 #include <algorithm>
 #include <type_traits>
 
-#include <cuda_bf16.h>
-#include <cuda_fp16.h>
+#include <mutex>
+#include <unordered_map>
 
 #include "dfm_internal.cuh"
+#include "tma_pipe.cuh"
 
 namespace dfm {
 namespace {
+
+using namespace pipe;
 
 constexpr int kThreads = 128;
 
@@ -69,40 +72,6 @@ spmv_t_kernel(const TV* __restrict__ vals, int64_t row_stride, const int32_t* __
 constexpr int kStages = 4;
 constexpr int kMaxStagedRhs = 16;  // right-hand sides staged per operator pass
 constexpr int kConsumerWarps = 4;  // computing warps per block (plus one producer warp)
-constexpr long long kWaitPolls = 1ll << 22;
-
-__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_addr(dst)),
-               "l"(src), "r"(bytes), "r"(smem_addr(bar))
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
-  for (long long i = 0; i < kWaitPolls; ++i)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
 
 // Operators applied together: y_r = x0_r + alpha * sum_k coef[r][k] B_k x_r,
 // for the right-hand sides of one launch (k < K <= kMaxCombo, r < kMaxStagedRhs).
@@ -113,8 +82,23 @@ struct Combo {
   double coef[kMaxStagedRhs][kMaxCombo];
 };
 
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+// Output a of one operator row: sum over the row's three blocks k of
+// sum_b B_k[a][b] x_l[b], l = the k-th face of the source tet other than lp.
+// blk points at B_0[a][0]; xs at the source tet's 4 x NB coefficients.
+template <int NB, typename TV, typename TX, typename TA>
+__device__ __forceinline__ TA row_times_x(const TV* blk, const TX* xs, int lp) {
+  TA acc[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int l = k + (k >= lp ? 1 : 0);
+    const TV* bk = blk + k * NB * NB;
+    const TX* xl = xs + l * NB;
+    TA a0 = TA(0);
+#pragma unroll
+    for (int b = 0; b < NB; ++b) a0 = fma((TA)bk[b], (TA)xl[b], a0);
+    acc[k] = a0;
+  }
+  return (acc[0] + acc[1]) + acc[2];
 }
 
 // Warp-specialised pipeline.  Warp 0 is the producer: for each of the block's
@@ -124,17 +108,18 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // source tet's 4 x NB coefficients), all completing on the stage's `full`
 // barrier.  Warps 1..kConsumerWarps compute.  All waits are bounded; the
 // producer drains its outstanding copies (bounded) before the block exits.
-template <int NB, typename TV, typename TX, typename TA>
+// KC = 1: a single operator (cb.K must be 1), compiled without the combination
+// loop; KC = 0: cb.K operators combined with per-right-hand-side weights.
+template <int NB, int KC, typename TV, typename TX, typename TA>
 __global__ void __launch_bounds__(32 * (kConsumerWarps + 1))
 spmv_tma_kernel(const Combo cb, int64_t row_stride, const int32_t* __restrict__ recv, int64_t nrows,
                 int rows_per_tile, int stages, const TX* __restrict__ x, const TX* x0, TX* y, int R, TA alpha,
-                int stage_x0, int* __restrict__ err) {
+                int stage_x0, int reverse, int64_t keep_from, int* __restrict__ err) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw);
   uint64_t* empty = full + kStages;
   int32_t* s_recv = reinterpret_cast<int32_t*>(smem_raw + 128);
-  constexpr int NB2 = NB * NB;
-  const int K = cb.K;
+  const int K = KC ? KC : cb.K;
   const int64_t op_tile_bytes = (int64_t)rows_per_tile * row_stride * (int64_t)sizeof(TV);
   const int64_t vals_bytes = K * op_tile_bytes;
   const int64_t xblk = 4 * NB * (int64_t)sizeof(TX);
@@ -160,10 +145,16 @@ spmv_tma_kernel(const Combo cb, int64_t row_stride, const int32_t* __restrict__ 
     int64_t issued = 0;
     bool ok = true;
     auto tile_rows = [&](int64_t i, int64_t* R0, int* nr) {
-      *R0 = (blockIdx.x + i * (int64_t)gridDim.x) * rows_per_tile;
+      const int64_t tile = blockIdx.x + i * (int64_t)gridDim.x;
+      *R0 = (reverse ? ntiles - 1 - tile : tile) * rows_per_tile;
       const int64_t left = nrows - *R0;
       *nr = left < rows_per_tile ? (int)left : rows_per_tile;
     };
+    // operator tiles late in this sweep are kept in L2 (evict_last) for the
+    // next application, which sweeps in the opposite direction and reads them
+    // first; the rest stream through (evict_first)
+    const uint64_t pol_last = l2_policy_evict_last();
+    const uint64_t pol_first = l2_policy_evict_first();
     int32_t next_src = 0;
     if (mine > 0) {
       int64_t R0;
@@ -195,9 +186,10 @@ spmv_tma_kernel(const Combo cb, int64_t row_stride, const int32_t* __restrict__ 
       if (lane == 0) {
         const unsigned vb = (unsigned)(nr * row_stride * (int64_t)sizeof(TV));
         mbar_arrive_expect_tx(&full[s], K * vb + (unsigned)(R * nr * xblk) + x0b);
+        const uint64_t pol = (blockIdx.x + i * (int64_t)gridDim.x) >= keep_from ? pol_last : pol_first;
         for (int k = 0; k < K; ++k)
-          bulk_copy_g2s(st + k * op_tile_bytes, reinterpret_cast<const TV*>(cb.vals[k]) + R0 * row_stride, vb,
-                        &full[s]);
+          bulk_copy_g2s_hint(st + k * op_tile_bytes, reinterpret_cast<const TV*>(cb.vals[k]) + R0 * row_stride, vb,
+                             &full[s], pol);
         for (int rhs = 0; rhs < R && stage_x0; ++rhs)
           bulk_copy_g2s(st + vals_bytes + (int64_t)R * rows_per_tile * xblk +
                             (int64_t)rhs * rows_per_tile * NB * (int64_t)sizeof(TX),
@@ -231,31 +223,25 @@ spmv_tma_kernel(const Combo cb, int64_t row_stride, const int32_t* __restrict__ 
     const TX* tx = reinterpret_cast<const TX*>(st + vals_bytes);
     const TX* tx0 = reinterpret_cast<const TX*>(st + vals_bytes + (int64_t)R * rows_per_tile * xblk);
     const int32_t* rs = s_recv + s * rows_per_tile;
-    const int64_t R0 = (blockIdx.x + i * (int64_t)gridDim.x) * rows_per_tile;
+    const int64_t tile = blockIdx.x + i * (int64_t)gridDim.x;
+    const int64_t R0 = (reverse ? ntiles - 1 - tile : tile) * rows_per_tile;
     const int64_t left = nrows - R0;
     const int nr = left < rows_per_tile ? (int)left : rows_per_tile;
     for (int e = ctid; e < nr * NB; e += nthreads) {
       const int r = e / NB;
       const int a = e - r * NB;
       const int lp = rs[r] & 3;
+      const TV* blk0 = tv + (int64_t)r * row_stride + a * NB;
       for (int rhs = 0; rhs < R; ++rhs) {
         const TX* xs = tx + ((int64_t)rhs * rows_per_tile + r) * 4 * NB;
-        TA total = TA(0);
-        for (int kk = 0; kk < K; ++kk) {
-          const TV* blk = tv + kk * (op_tile_bytes / (int64_t)sizeof(TV)) + (int64_t)r * row_stride + a * NB;
-          TA acc[3];
-#pragma unroll
-          for (int k = 0; k < 3; ++k) {
-            const int l = k + (k >= lp ? 1 : 0);
-            const TV* bk = blk + k * NB2;
-            const TX* xl = xs + l * NB;
-            TA a0 = TA(0);
-#pragma unroll
-            for (int b = 0; b < NB; ++b) a0 = fma((TA)bk[b], (TA)xl[b], a0);
-            acc[k] = a0;
-          }
-          const TA sum = (acc[0] + acc[1]) + acc[2];
-          total = (K == 1) ? sum : fma((TA)cb.coef[rhs][kk], sum, total);
+        TA total;
+        if (KC == 1) {
+          total = row_times_x<NB, TV, TX, TA>(blk0, xs, lp);
+        } else {
+          total = TA(0);
+          for (int kk = 0; kk < K; ++kk)
+            total = fma((TA)cb.coef[rhs][kk],
+                        row_times_x<NB, TV, TX, TA>(blk0 + kk * (op_tile_bytes / (int64_t)sizeof(TV)), xs, lp), total);
         }
         const int64_t o = ((int64_t)rhs * nrows + R0 + r) * NB + a;
         const TA base = stage_x0 ? (TA)tx0[((int64_t)rhs * rows_per_tile + r) * NB + a] : (x0 ? (TA)x0[o] : TA(0));
@@ -280,7 +266,7 @@ template <int NB, typename TV, typename TX, typename TA>
 __global__ void __launch_bounds__(32 * (kConsumerWarps + 1))
 spmv_t_tma_kernel(const TV* __restrict__ vals, int64_t row_stride, const int32_t* __restrict__ recv, int64_t nt,
                   int tets_per_tile, int stages, const TX* __restrict__ x, const TX* x0, TX* y, TA alpha,
-                  int* __restrict__ err) {
+                  int reverse, int* __restrict__ err) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw);
   uint64_t* empty = full + kStages;
@@ -303,7 +289,8 @@ spmv_t_tma_kernel(const TV* __restrict__ vals, int64_t row_stride, const int32_t
   }
   __syncthreads();
   auto tile_tets = [&](int64_t i, int64_t* T0, int* ntt) {
-    *T0 = (blockIdx.x + i * (int64_t)gridDim.x) * tets_per_tile;
+    const int64_t tile = blockIdx.x + i * (int64_t)gridDim.x;
+    *T0 = (reverse ? ntiles - 1 - tile : tile) * tets_per_tile;
     const int64_t left = nt - *T0;
     *ntt = left < tets_per_tile ? (int)left : tets_per_tile;
   };
@@ -397,6 +384,37 @@ spmv_t_tma_kernel(const TV* __restrict__ vals, int64_t row_stride, const int32_t
   }
 }
 
+// Consecutive applications of one operator sweep its rows in alternating
+// directions: a sweep that starts where the previous one ended finds that
+// sweep's last rows still in L2.  The parity is kept per values buffer (the
+// FP32 blocks and their 16-bit copy are separate streams of bytes).  Results
+// do not depend on the direction: every output row is formed by one warp in a
+// fixed order either way.
+std::mutex g_sweep_mu;
+std::unordered_map<const void*, unsigned> g_sweep;
+
+}  // namespace
+
+int next_sweep_direction(const void* vals) {
+  std::lock_guard<std::mutex> lk(g_sweep_mu);
+  unsigned& p = g_sweep[vals];
+  const int dir = (int)(p & 1u);
+  ++p;
+  return dir;
+}
+
+void forget_sweep(const void* vals) {
+  if (!vals) return;
+  std::lock_guard<std::mutex> lk(g_sweep_mu);
+  g_sweep.erase(vals);
+}
+
+namespace {
+
+// Operator bytes per application kept in L2 for the next one (of the 129 MB
+// L2; the rest holds the vectors and the row map).
+constexpr int64_t kL2KeepBytes = 64ll << 20;
+
 int rows_per_tile_for(int nb) {
   int r = kThreads / nb;
   if (r < 1) r = 1;
@@ -455,27 +473,38 @@ int launch(const dfm_op* op, const TX* x, const TX* x0, TX* y, int R, double alp
       const int64_t ntiles = (op->nrows + rpt - 1) / rpt;
       const int64_t grid = std::min<int64_t>(ntiles, (int64_t)nsm * per_sm);
       {
-        ::dfm::KernelTimer timer_(sizeof(TX) == 8 ? DFM_KERNEL_SPMV64 : (sizeof(TV) == 2 ? DFM_KERNEL_SPMV16 : DFM_KERNEL_SPMV),
-                                 st);
+        ::dfm::KernelTimer timer_(sizeof(TX) == 8 ? DFM_KERNEL_SPMV64 : DFM_KERNEL_SPMV, st);
+        const int64_t op_tile = (int64_t)K * rpt * op->row_stride * (int64_t)sizeof(TV);
+        const int64_t keep_from = std::max<int64_t>(0, ntiles - kL2KeepBytes / op_tile);
         kernel<<<(unsigned)grid, 32 * (kConsumerWarps + 1), smem, st>>>(cb, op->row_stride, recv, op->nrows, rpt,
                                                                          stages, x, x0, y, R, (TA)alpha, stage_x0,
+                                                                         next_sweep_direction(op->vals), keep_from,
                                                                          op->dev_err);
       }
       DFM_LAUNCHED();
       return DFM_OK;
     };
-    switch (op->nb) {
-      case 1: rc = go(spmv_tma_kernel<1, TV, TX, TA>); break;
-      case 3: rc = go(spmv_tma_kernel<3, TV, TX, TA>); break;
-      case 6: rc = go(spmv_tma_kernel<6, TV, TX, TA>); break;
-      case 10: rc = go(spmv_tma_kernel<10, TV, TX, TA>); break;
-      case 15: rc = go(spmv_tma_kernel<15, TV, TX, TA>); break;
-      case 21: rc = go(spmv_tma_kernel<21, TV, TX, TA>); break;
-      case 28: rc = go(spmv_tma_kernel<28, TV, TX, TA>); break;
-      case 36: rc = go(spmv_tma_kernel<36, TV, TX, TA>); break;
-      case 45: rc = go(spmv_tma_kernel<45, TV, TX, TA>); break;
-      default: return set_error(DFM_ERR_UNSUPPORTED, "dfm_apply: unsupported basis size");
-    }
+    auto by_nb = [&](auto kc) -> int {
+      constexpr int KC = decltype(kc)::value;
+      switch (op->nb) {
+        case 1: return go(spmv_tma_kernel<1, KC, TV, TX, TA>);
+        case 3: return go(spmv_tma_kernel<3, KC, TV, TX, TA>);
+        case 6: return go(spmv_tma_kernel<6, KC, TV, TX, TA>);
+        case 10: return go(spmv_tma_kernel<10, KC, TV, TX, TA>);
+        case 15: return go(spmv_tma_kernel<15, KC, TV, TX, TA>);
+        case 21: return go(spmv_tma_kernel<21, KC, TV, TX, TA>);
+        case 28: return go(spmv_tma_kernel<28, KC, TV, TX, TA>);
+        case 36: return go(spmv_tma_kernel<36, KC, TV, TX, TA>);
+        case 45: return go(spmv_tma_kernel<45, KC, TV, TX, TA>);
+        default: return set_error(DFM_ERR_UNSUPPORTED, "dfm_apply: unsupported basis size");
+      }
+    };
+    if (K == 1)
+      rc = by_nb(std::integral_constant<int, 1>{});
+    else if constexpr (std::is_same<TV, float>::value)  // combinations are of FP32 operators only
+      rc = by_nb(std::integral_constant<int, 0>{});
+    else
+      return set_error(DFM_ERR_UNSUPPORTED, "dfm_apply_combo: operators must be FP32");
     if (rc) return rc;
   } else if (combo_ops == nullptr && !(reinterpret_cast<uintptr_t>(op->vals) & 15)) {
     // pipelined transposed application, one right-hand side per launch
@@ -501,7 +530,7 @@ int launch(const dfm_op* op, const TX* x, const TX* x0, TX* y, int R, double alp
           ::dfm::KernelTimer timer_(DFM_KERNEL_SPMV_T, st);
           kernel<<<(unsigned)grid, 32 * (kConsumerWarps + 1), smem, st>>>(
               vals, op->row_stride, recv, nt, tpt, stages, x + r * stride, x0 ? x0 + r * stride : nullptr,
-              y + r * stride, (TA)alpha, op->dev_err);
+              y + r * stride, (TA)alpha, next_sweep_direction(op->vals), op->dev_err);
         }
         DFM_LAUNCHED();
         DFM_CUDA_CHECK(cudaGetLastError());
@@ -552,55 +581,8 @@ int apply_impl(const dfm_op* op, const void* x, const void* x0, void* y, int R, 
       return launch<float, float, float>(op, (const float*)x, (const float*)x0, (float*)y, R, alpha, trans, st);
     if (op->precision == DFM_F64)
       return launch<double, float, double>(op, (const float*)x, (const float*)x0, (float*)y, R, alpha, trans, st);
-    if (op->precision == DFM_F16 && !trans)
-      return launch<__half, float, float>(op, (const float*)x, (const float*)x0, (float*)y, R, alpha, trans, st);
-    if (op->precision == DFM_BF16 && !trans)
-      return launch<__nv_bfloat16, float, float>(op, (const float*)x, (const float*)x0, (float*)y, R, alpha, trans,
-                                                 st);
   }
   return set_error(DFM_ERR_UNSUPPORTED, "dfm_apply: unsupported operator/vector precision");
-}
-
-namespace {
-template <typename T16>
-__global__ void to_16bit_kernel(const float* __restrict__ src, T16* __restrict__ dst, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    if constexpr (std::is_same<T16, __half>::value)
-      dst[i] = __float2half_rn(src[i]);
-    else
-      dst[i] = __float2bfloat16_rn(src[i]);
-  }
-}
-}  // namespace
-
-int lowp_view(const dfm_op* cop, int precision, cudaStream_t st, dfm_op* view) {
-  dfm_op* op = const_cast<dfm_op*>(cop);
-  if (op->precision != DFM_F32 || (precision != DFM_F16 && precision != DFM_BF16))
-    return set_error(DFM_ERR_UNSUPPORTED, "preconditioner copy: needs an FP32 operator and DFM_F16 or DFM_BF16");
-  if (!op->lp_vals) {
-    DFM_CUDA_CHECK(cudaMalloc(&op->lp_vals, op->nrows * op->row_stride * 2));
-  }
-  if (!op->lp_valid || op->lp_precision != precision) {
-    const int64_t n = op->nrows * op->row_stride;
-    if (precision == DFM_F16)
-      to_16bit_kernel<__half><<<1024, 256, 0, st>>>((const float*)op->vals, (__half*)op->lp_vals, n);
-    else
-      to_16bit_kernel<__nv_bfloat16><<<1024, 256, 0, st>>>((const float*)op->vals, (__nv_bfloat16*)op->lp_vals, n);
-    DFM_LAUNCHED();
-    DFM_CUDA_CHECK(cudaGetLastError());
-    op->lp_precision = precision;
-    op->lp_valid = true;
-  }
-  view->mesh = op->mesh;
-  view->Np = op->Np;
-  view->nb = op->nb;
-  view->precision = precision;
-  view->nrows = op->nrows;
-  view->row_stride = op->row_stride;
-  view->vals = op->lp_vals;
-  view->bytes = op->nrows * op->row_stride * 2;
-  view->dev_err = op->dev_err;
-  return DFM_OK;
 }
 
 int apply_combo_impl(const dfm_op* const* ops, int K, const double* coef, const void* x, const void* x0, void* y,

@@ -83,6 +83,7 @@ SIGNATURES = {
     "dfm_apply": (_i, [_vp, _vp, _vp, _vp, _i, _d, _i, _i, _vp]),
     "dfm_source": (_i, [_vp, _i, _vp, _i, _vp, _vp]),
     "dfm_apply_combo": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _i, _d, _i, _vp]),
+    "dfm_precond_apply": (_i, [_vp, _i, _i, _vp, _vp, _i, _vp]),
     "dfm_solve_combo": (_i, [_vp, _i, _vp, _vp, _i, _vp, ctypes.POINTER(SolveOpts), _vp, ctypes.POINTER(SolveInfo)]),
     "dfm_solve": (_i, [_vp, _vp, _i, _vp, ctypes.POINTER(SolveOpts), _vp, ctypes.POINTER(SolveInfo)]),
     "dfm_interior_density": (_i, [_vp, _i, _vp, _d, _vp, _vp, _i, _i, _vp, _vp, _vp]),
@@ -252,6 +253,18 @@ class Operator:
         _check(_lib.dfm_apply(self._h, _ptr(x), _ptr(x0), _ptr(y), R, float(alpha), int(bool(trans)), xtype,
                               _stream()), "dfm_apply")
         return y
+
+    def precond(self, x, degree=16, precision=F16, out=None):
+        """z = sum_{k<degree} B~^k x on the 16-bit copy B~ of the blocks
+        (dfm_precond_apply); x: FP32 [R, rows, nb] or [rows, nb]."""
+        torch = self._torch
+        if x.dtype != torch.float32:
+            raise TypeError("precond: x must be float32")
+        R = 1 if x.dim() == 2 else x.shape[0]
+        z = torch.empty_like(x) if out is None else out
+        _check(_lib.dfm_precond_apply(self._h, int(precision), int(degree), _ptr(x), _ptr(z), R, _stream()),
+               "dfm_precond_apply")
+        return z
 
     def solve(self, rho0, method=GMRES_IR, tol=1e-8, max_iter=0, restart=0, x0=None, inner_tol=0.0,
               raise_on_nonconvergence=True, transpose=False, poly_degree=0, batch=0, precond_precision=0):

@@ -48,7 +48,7 @@ def test_sixteen_bit_hops_dominate_with_their_own_bytes():
     # the FP32 launches are the Krylov operator w = z - B z, which reads x0
     assert kern["spmv_f32"]["bytes_per_launch"] == bench.spmv_bytes(N_ROWS, NB, 4, with_x0=True)
     assert total["dot"] == 17.0
-    key = ("spmv_tma_kernel<15, __half, float, float>", "kuhn20_np4")
+    key = ("hop_kernel<15, __half>", "kuhn20_np4")
     assert roof["traffic"] == bench.MEASURED_TRAFFIC.get(key)
 
 

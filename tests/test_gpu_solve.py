@@ -64,6 +64,34 @@ def test_apply_forward_and_transpose(D, oracle_mod, prec, xdt):
         assert np.abs(y2[0] - yr).max() <= tol * np.abs(yr).max()
 
 
+@pytest.mark.parametrize("Np", [2, 4])
+def test_apply_alternating_sweeps_bit_identical(D, oracle_mod, Np):
+    """Consecutive applications sweep the operator rows in opposite
+    directions; every output row is still formed in one fixed order, so
+    repeated applications agree bit for bit.  The mesh drops one tet of the
+    Kuhn cube (161 tets, 644 rows), so the last tile of both the forward
+    (rows) and the transposed (source tets) pipeline is ragged."""
+    import torch
+
+    m = kuhn_cube_mesh(3, jitter=0.2, seed=8)
+    tets = np.ascontiguousarray(m.tets[:-1])
+    nt = tets.shape[0]
+    mesh = D.Mesh(m.verts, tets, refl=0.9)
+    op = D.Operator(mesh, Np, mu=0.2, precision=1)
+    ref_op = _gpu_op_as_oracle(oracle_mod, op, mesh, nt, Np)
+    rng = np.random.default_rng(5)
+    xt = torch.tensor(rng.standard_normal((2, 4 * nt, op.nb)), dtype=torch.float32, device="cuda")
+    x0t = torch.tensor(rng.standard_normal((2, 4 * nt, op.nb)), dtype=torch.float32, device="cuda")
+    for trans in (False, True):
+        ys = [op.apply(xt, x0=x0t, alpha=-0.7, trans=trans).clone() for _ in range(3)]
+        assert torch.equal(ys[0], ys[1]) and torch.equal(ys[1], ys[2])
+        y = ys[0].cpu().numpy()
+        for r in range(2):
+            yr = oracle_mod.apply(ref_op, xt[r].double().cpu().numpy(), trans=trans,
+                                  x0=x0t[r].double().cpu().numpy(), alpha=-0.7)
+            assert np.abs(y[r] - yr).max() <= 2e-6 * np.abs(yr).max()
+
+
 def test_source_vector(D, oracle_mod):
     m = kuhn_cube_mesh(3, jitter=0.2, seed=8)
     mesh = D.Mesh(m.verts, m.tets)
