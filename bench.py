@@ -44,6 +44,8 @@ SOLVER_DESC = {
             "evaluated on an FP16 copy of the blocks"),
     "bf16": ("FP64-residual refinement around flexible FP32 GMRES(128) right-preconditioned by sum_{k<32} B^k "
              "evaluated on a BF16 copy of the blocks"),
+    "fp8": ("FP64-residual refinement around flexible FP32 GMRES(128) right-preconditioned by sum_{k<32} B^k "
+            "evaluated on an e4m3 copy of the blocks (one FP32 scale per row)"),
 }
 # Operator applications of the FP64 solve on the 20^3 workload: FP64 GMRES(128)
 # right-preconditioned by sum_{k<16} B^k reaches the 1e-8 residual after 1,809
@@ -55,8 +57,8 @@ FP32_LANES_PER_SM = 128
 # step's dominant kernel measured by ncu on this workload (mean of two
 # launches; profiles/hop_kuhn20_np4.md).  Keyed by the kernel instantiation and
 # workload; an entry is dropped whenever its kernel changes.
-PRECOND = {"f32": 0, "f16": 3, "bf16": 2}
-MEASURED_TRAFFIC = {("hop_kernel<15, __half>", "kuhn20_np4"): 303.9e6}
+PRECOND = {"f32": 0, "f16": 3, "bf16": 2, "fp8": 4}
+MEASURED_TRAFFIC = {}
 HBM_PEAK_FALLBACK = 6800.0
 
 
@@ -157,8 +159,9 @@ def spmv_bytes(n_rows, nb, vec_bytes, with_x0=True, block_bytes=4):
 
 def summarize_kernels(kstats, n_rows, n_tets, Np, nodes, nsm, peaks, peak_src, workload, precond):
     """Per-kernel rooflines of a timed region and the dominant kernel's.
-    kstats: name -> (launches, total ms) for assemble, spmv_f32, spmv_16bit
-    (the preconditioner's hops on the 16-bit copy, precond "f16" or "bf16"),
+    kstats: name -> (launches, total ms) for assemble, spmv_f32, hop (the
+    preconditioner's hops on the low-precision copy, precond "f16", "bf16" or
+    "fp8"),
     spmv_f64vec, dot, axpy.  Returns (per-kernel dict, total ms per kernel,
     roofline of the kernel with the largest total among assemble/spmv)."""
     nb = (Np + 1) * (Np + 2) // 2
@@ -187,9 +190,14 @@ def summarize_kernels(kstats, n_rows, n_tets, Np, nodes, nsm, peaks, peak_src, w
         # operator w = z - B z (x0 = z); without it most are polynomial hops
         # without x0
         hbm("spmv_f32", n, ms, spmv_bytes(n_rows, nb, 4, with_x0=precond != "f32"))
-    n, ms = kstats["spmv_16bit"]
+    n, ms = kstats["hop"]
     if n:
-        hbm("spmv_16bit", n, ms, spmv_bytes(n_rows, nb, 4, with_x0=True, block_bytes=2))
+        # unpadded copy values (+ the FP32 scale of an e4m3 row), row map, and
+        # x, x0, y in the hop vectors' precision (FP16 with the FP16 and e4m3
+        # copies, FP32 with the BF16 copy)
+        eb = 1 if precond == "fp8" else 2
+        vb = 4 if precond == "bf16" else 2
+        hbm("hop", n, ms, spmv_bytes(n_rows, nb, vb, with_x0=True, block_bytes=eb) + (4 * n_rows if eb == 1 else 0))
     n, ms = kstats["spmv_f64vec"]
     if n:
         hbm("spmv_f64vec", n, ms, spmv_bytes(n_rows, nb, 8))
@@ -198,10 +206,11 @@ def summarize_kernels(kstats, n_rows, n_tets, Np, nodes, nsm, peaks, peak_src, w
         if n:
             kern[name] = {"launches": n, "ms_total": ms}
     total = {k: v[1] for k, v in kstats.items()}
-    dominant = max((k for k in ("assemble", "spmv_f32", "spmv_16bit") if k in kern), key=lambda k: total[k])
+    dominant = max((k for k in ("assemble", "spmv_f32", "hop") if k in kern), key=lambda k: total[k])
     d = kern[dominant]
     inst = {"spmv_f32": f"spmv_tma_kernel<{nb}, 1, float, float, float>",
-            "spmv_16bit": f"hop_kernel<{nb}, {'__half' if precond == 'f16' else '__nv_bfloat16'}>"}.get(dominant)
+            "hop": f"hop_kernel<{nb}, {dict(f16='__half', bf16='__nv_bfloat16', fp8='__nv_fp8_e4m3').get(precond)}>"
+            }.get(dominant)
     traffic = MEASURED_TRAFFIC.get((inst, workload)) if inst else None
     roofline = {"bound": d["bound"], "achieved": round(d["achieved"], 3), "peak": round(d["peak"], 3),
                 "unit": d["unit"], "frac": round(d["frac"], 4), "traffic": traffic, "kernel": dominant,
@@ -317,7 +326,7 @@ def run_gpu(args):
     nb = op.nb
     kern, total, roofline = summarize_kernels(
         {"assemble": kstats[dfm.KERNEL_ASSEMBLE], "spmv_f32": kstats[dfm.KERNEL_SPMV],
-         "spmv_16bit": kstats[dfm.KERNEL_SPMV16], "spmv_f64vec": kstats[dfm.KERNEL_SPMV64],
+         "hop": kstats[dfm.KERNEL_SPMV16], "spmv_f64vec": kstats[dfm.KERNEL_SPMV64],
          "dot": kstats[dfm.KERNEL_DOT], "axpy": kstats[dfm.KERNEL_AXPY]},
         n_rows=mesh.n_rows, n_tets=int(m.n_tets), Np=Np, nodes=nodes, nsm=nsm, peaks=peaks, peak_src=peak_src,
         workload=args.workload, precond=args.precond)
@@ -334,9 +343,8 @@ def run_gpu(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": ("f32 blocks, f16 preconditioner copy, f32 Krylov, f64 residual" if args.precond == "f16" else
-                  "f32 blocks, bf16 preconditioner copy, f32 Krylov, f64 residual" if args.precond == "bf16" else
-                  "f32 blocks/Krylov, f64 residual"),
+        "dtype": ("f32 blocks/Krylov, f64 residual" if args.precond == "f32" else
+                  f"f32 blocks, {args.precond} preconditioner copy, f32 Krylov, f64 residual"),
         "data": "synthetic",
         "config": {"workload": args.workload,
                    "desc": (WORKLOAD_DESC if args.workload == WORKLOAD else args.workload) + "; "
@@ -656,7 +664,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparator", action="store_true")
-    ap.add_argument("--precond", choices=["f32", "f16", "bf16"], default="f16",
+    ap.add_argument("--precond", choices=["f32", "f16", "bf16", "fp8"], default="f16",
                     help="precision of the blocks used by the polynomial preconditioner's hops")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--ref-apps", type=int, default=0,

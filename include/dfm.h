@@ -68,6 +68,7 @@ extern "C" {
 #define DFM_F32 1
 #define DFM_BF16 2
 #define DFM_F16 3
+#define DFM_FP8E4M3 4 /* preconditioner copy only: e4m3 values with one FP32 scale per operator row */
 
 /* stationary solvers */
 #define DFM_SOLVE_NEUMANN 0   /* x <- rho0 + B x (Eq. NSum), FP64 */
@@ -208,7 +209,8 @@ typedef struct {
                         GMRES on an FP64 operator: 0 = none */
   int precond_precision; /* GMRES_IR: 0 = the polynomial preconditioner uses the operator itself;
                         DFM_F16 or DFM_BF16 = its hops use a 16-bit copy of the blocks (made once
-                        per assembly, half the bytes per hop) and the inner solver is flexible
+                        per assembly, half the bytes per hop); DFM_FP8E4M3 = an 8-bit e4m3 copy
+                        with one FP32 scale per row (a quarter of the bytes); the inner solver is flexible
                         GMRES, which tolerates the inexact preconditioner; the Krylov operator
                         I - B and the FP64 residual keep the FP32 blocks */
   int batch;         /* GMRES_IR with R > 1: right-hand sides iterated in lockstep, sharing
@@ -243,7 +245,9 @@ int dfm_solve_combo(const dfm_op* const* ops, int K, const double* coef_host, co
  * solver; this is a building block for callers' own Krylov methods:
  *   z_r = sum_{k<degree} B~^k x_r,  r < R,
  * B~ = the FP16 (precision DFM_F16) or BF16 (DFM_BF16) rounding, to nearest,
- * of op's FP32 blocks (made on first use and again after each assembly),
+ * of op's FP32 blocks, or (DFM_FP8E4M3) s_R q with q the e4m3 rounding (to
+ * nearest even, saturating) of B/s_R and s_R = (max |entry| of row R) / 448
+ * in FP32 (made on first use and again after each assembly),
  * evaluated by Horner's rule z <- x + B~ z with FP32 vectors and FP32
  * accumulation.  op: FP32 operator; x, z: device FP32 [R][rows][nb], 16-byte
  * aligned, z must not alias x; 1 <= degree <= 64.  Uses a scratch of

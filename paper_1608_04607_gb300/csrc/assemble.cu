@@ -34,6 +34,8 @@
 // block with every lane owning a TR x TC register tile.
 #include <math.h>
 
+#include <cuda_bf16.h>
+
 #include "dfm_internal.cuh"
 #include "node.cuh"
 
@@ -98,10 +100,11 @@ struct WarpSmem {
 
 // QC > 0 fixes the per-patch Gauss order at compile time (the default
 // N_p + 6), which turns the node-index divisions into multiplies.
-template <int NP, typename T, int QC>
+// TO: storage type of the blocks (T, or BF16 rounded from FP32 sums).
+template <int NP, typename T, int QC, typename TO>
 __global__ void __launch_bounds__(kWarps * 32)
 assemble_kernel(const PairConst* __restrict__ pairs, int64_t npairs, const double* __restrict__ gl_x,
-                const double* __restrict__ gl_w, int q_rt, float cos_max, T* __restrict__ vals, int64_t row_stride,
+                const double* __restrict__ gl_w, int q_rt, float cos_max, TO* __restrict__ vals, int64_t row_stride,
                 unsigned long long* __restrict__ node_count, int moment) {
   using TL = Tile<NP>;
   constexpr int NB = TL::NB, TR = TL::TR, TC = TL::TC, LD = TL::LD;
@@ -196,7 +199,7 @@ assemble_kernel(const PairConst* __restrict__ pairs, int64_t npairs, const doubl
     }
     if (lane == 0) atomicAdd(node_count, pair_nodes);
     // epilogue: scale row a by lambda N_a / sqrt(|T_l||T_l'|) and store
-    T* out = vals + (int64_t)pc.out_row * row_stride + (int64_t)pc.slot * NB * NB;
+    TO* out = vals + (int64_t)pc.out_row * row_stride + (int64_t)pc.slot * NB * NB;
 #pragma unroll
     for (int r = 0; r < TR; ++r) {
       const int a = a0 + r;
@@ -205,7 +208,12 @@ assemble_kernel(const PairConst* __restrict__ pairs, int64_t npairs, const doubl
 #pragma unroll
       for (int c = 0; c < TC; ++c) {
         const int b = b0 + c;
-        if (b < NB) out[a * NB + b] = acc[r][c] * s;
+        if (b < NB) {
+          if constexpr (std::is_same<TO, __nv_bfloat16>::value)
+            out[a * NB + b] = __float2bfloat16_rn(acc[r][c] * s);
+          else
+            out[a * NB + b] = acc[r][c] * s;
+        }
       }
     }
     __syncwarp();
@@ -222,48 +230,49 @@ constexpr size_t assemble_smem_bytes() {
   return sizeof(WarpSmem<NP, T>) * kWarps + 2 * kMaxQ * sizeof(T) + 64 * sizeof(float);
 }
 
-template <int NP, typename T, int QC>
+template <int NP, typename T, int QC, typename TO>
 int launch_assemble_q(const PairConst* pairs, int64_t npairs, const double* glx, const double* glw, int q,
-                      float cos_max, T* vals, int64_t row_stride, unsigned long long* nodes, int moment,
+                      float cos_max, TO* vals, int64_t row_stride, unsigned long long* nodes, int moment,
                       cudaStream_t st) {
   constexpr size_t smem = assemble_smem_bytes<NP, T>();
   static_assert(smem <= 220 * 1024, "assembly shared memory");
   DFM_CUDA_CHECK(
-      cudaFuncSetAttribute(assemble_kernel<NP, T, QC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      cudaFuncSetAttribute(assemble_kernel<NP, T, QC, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int64_t blocks = (npairs + kWarps - 1) / kWarps;
   if (blocks > 0x7fffffff) return set_error(DFM_ERR_ARG, "dfm_assemble: too many face pairs");
   {
     ::dfm::KernelTimer timer_(DFM_KERNEL_ASSEMBLE, st);
-    assemble_kernel<NP, T, QC><<<(unsigned)blocks, kWarps * 32, smem, st>>>(pairs, npairs, glx, glw, q, cos_max,
-                                                                            vals, row_stride, nodes, moment);
+    assemble_kernel<NP, T, QC, TO><<<(unsigned)blocks, kWarps * 32, smem, st>>>(pairs, npairs, glx, glw, q, cos_max,
+                                                                                vals, row_stride, nodes, moment);
   }
   DFM_LAUNCHED();
   DFM_CUDA_CHECK(cudaGetLastError());
   return DFM_OK;
 }
 
-template <int NP, typename T>
+template <int NP, typename T, typename TO>
 int launch_assemble(const PairConst* pairs, int64_t npairs, const double* glx, const double* glw, int q,
-                    float cos_max, T* vals, int64_t row_stride, unsigned long long* nodes, int moment, cudaStream_t st) {
+                    float cos_max, TO* vals, int64_t row_stride, unsigned long long* nodes, int moment,
+                    cudaStream_t st) {
   if (std::is_same<T, float>::value && q == NP + 6)
-    return launch_assemble_q<NP, T, NP + 6>(pairs, npairs, glx, glw, q, cos_max, vals, row_stride, nodes, moment,
-                                            st);
-  return launch_assemble_q<NP, T, 0>(pairs, npairs, glx, glw, q, cos_max, vals, row_stride, nodes, moment, st);
+    return launch_assemble_q<NP, T, NP + 6, TO>(pairs, npairs, glx, glw, q, cos_max, vals, row_stride, nodes, moment,
+                                                st);
+  return launch_assemble_q<NP, T, 0, TO>(pairs, npairs, glx, glw, q, cos_max, vals, row_stride, nodes, moment, st);
 }
 
-template <typename T>
+template <typename T, typename TO = T>
 int dispatch_np(int Np, const PairConst* pairs, int64_t npairs, const double* glx, const double* glw, int q,
-                float cos_max, T* vals, int64_t row_stride, unsigned long long* nodes, int moment, cudaStream_t st) {
+                float cos_max, TO* vals, int64_t row_stride, unsigned long long* nodes, int moment, cudaStream_t st) {
   switch (Np) {
-    case 0: return launch_assemble<0, T>(pairs, npairs, glx, glw, q, cos_max, vals, row_stride, nodes, moment, st);
-    case 1: return launch_assemble<1, T>(pairs, npairs, glx, glw, q, cos_max, vals, row_stride, nodes, moment, st);
-    case 2: return launch_assemble<2, T>(pairs, npairs, glx, glw, q, cos_max, vals, row_stride, nodes, moment, st);
-    case 3: return launch_assemble<3, T>(pairs, npairs, glx, glw, q, cos_max, vals, row_stride, nodes, moment, st);
-    case 4: return launch_assemble<4, T>(pairs, npairs, glx, glw, q, cos_max, vals, row_stride, nodes, moment, st);
-    case 5: return launch_assemble<5, T>(pairs, npairs, glx, glw, q, cos_max, vals, row_stride, nodes, moment, st);
-    case 6: return launch_assemble<6, T>(pairs, npairs, glx, glw, q, cos_max, vals, row_stride, nodes, moment, st);
-    case 7: return launch_assemble<7, T>(pairs, npairs, glx, glw, q, cos_max, vals, row_stride, nodes, moment, st);
-    case 8: return launch_assemble<8, T>(pairs, npairs, glx, glw, q, cos_max, vals, row_stride, nodes, moment, st);
+    case 0: return launch_assemble<0, T, TO>(pairs, npairs, glx, glw, q, cos_max, vals, row_stride, nodes, moment, st);
+    case 1: return launch_assemble<1, T, TO>(pairs, npairs, glx, glw, q, cos_max, vals, row_stride, nodes, moment, st);
+    case 2: return launch_assemble<2, T, TO>(pairs, npairs, glx, glw, q, cos_max, vals, row_stride, nodes, moment, st);
+    case 3: return launch_assemble<3, T, TO>(pairs, npairs, glx, glw, q, cos_max, vals, row_stride, nodes, moment, st);
+    case 4: return launch_assemble<4, T, TO>(pairs, npairs, glx, glw, q, cos_max, vals, row_stride, nodes, moment, st);
+    case 5: return launch_assemble<5, T, TO>(pairs, npairs, glx, glw, q, cos_max, vals, row_stride, nodes, moment, st);
+    case 6: return launch_assemble<6, T, TO>(pairs, npairs, glx, glw, q, cos_max, vals, row_stride, nodes, moment, st);
+    case 7: return launch_assemble<7, T, TO>(pairs, npairs, glx, glw, q, cos_max, vals, row_stride, nodes, moment, st);
+    case 8: return launch_assemble<8, T, TO>(pairs, npairs, glx, glw, q, cos_max, vals, row_stride, nodes, moment, st);
     default: return set_error(DFM_ERR_ARG, "dfm_assemble: Np must be in 0..8");
   }
 }
@@ -271,8 +280,8 @@ int dispatch_np(int Np, const PairConst* pairs, int64_t npairs, const double* gl
 int check_params(const dfm_mesh* mesh, const dfm_params* p) {
   if (!mesh || !p) return set_error(DFM_ERR_ARG, "dfm_assemble: NULL mesh or params");
   if (p->Np < 0 || p->Np > 8) return set_error(DFM_ERR_ARG, "dfm_assemble: Np must be in 0..8");
-  if (p->precision != DFM_F32 && p->precision != DFM_F64)
-    return set_error(DFM_ERR_UNSUPPORTED, "dfm_assemble: precision must be DFM_F32 or DFM_F64");
+  if (p->precision != DFM_F32 && p->precision != DFM_F64 && p->precision != DFM_BF16)
+    return set_error(DFM_ERR_UNSUPPORTED, "dfm_assemble: precision must be DFM_F32, DFM_F64 or DFM_BF16");
   if (!p->mu && !(p->mu_uniform >= 0.0)) return set_error(DFM_ERR_ARG, "dfm_assemble: mu_uniform must be >= 0");
   const int q = p->quad_order ? p->quad_order : p->Np + 6;
   if (q < 1 || q > kMaxQ) return set_error(DFM_ERR_ARG, "dfm_assemble: quad_order must be in 1..32");
@@ -323,6 +332,9 @@ extern "C" int dfm_assemble_into(const dfm_mesh* mesh, const dfm_params* p, dfm_
   if (op->precision == DFM_F32)
     return dispatch_np<float>(p->Np, pairs, npairs, glx, glw, q, cos_max, (float*)op->vals, op->row_stride, nodes,
                               p->moment, st);
+  if (op->precision == DFM_BF16)
+    return dispatch_np<float, __nv_bfloat16>(p->Np, pairs, npairs, glx, glw, q, cos_max, (__nv_bfloat16*)op->vals,
+                                             op->row_stride, nodes, p->moment, st);
   return dispatch_np<double>(p->Np, pairs, npairs, glx, glw, q, cos_max, (double*)op->vals, op->row_stride, nodes,
                              p->moment, st);
 }

@@ -55,6 +55,7 @@ struct dfm_op {
   int* dev_err = nullptr;  // device flag set by kernels whose bounded waits time out
   // 16-bit copy of the blocks for inexact preconditioner hops (same layout)
   void* lp_vals = nullptr;
+  int64_t lp_bytes = 0;
   int lp_precision = 0;
   bool lp_valid = false;
   // assembly scratch (per-pair constants, Gauss table), grown on demand
@@ -99,13 +100,14 @@ void forget_sweep(const void* vals);
 // Polynomial-preconditioner hops on a 16-bit copy of the blocks (hop.cu).
 // Padded width of a face's coefficients in hop vectors and in the copy.
 inline int hop_nbp(int nb) { return (nb + 7) / 8 * 8; }
-// (re)builds op->lp_vals (precision DFM_F16 or DFM_BF16) from the FP32 blocks
+// (re)builds op->lp_vals (precision DFM_F16, DFM_BF16 or DFM_FP8E4M3) from the FP32 blocks
 int prepare_lowp(const dfm_op* op, int precision, cudaStream_t st);
-// vp[row][0..nbp) = v[row][0..nb), zero padded; rows = R * nrows
-int hop_pack(const float* v, float* vp, int64_t rows, int nb, cudaStream_t st);
-// y = x0 + B~ x for R right-hand sides, x and x0 padded; y padded (out_padded)
-// or in the unpadded [R][rows][nb] layout
-int hop_apply(const dfm_op* op, const float* xp, const float* x0p, float* y, int R, int out_padded, cudaStream_t st);
+// z = sum_{k<d} B~^k v for R vectors ([R][rows][nb] FP32) by Horner on the
+// low-precision copy; vp, ha, hb: 16-byte-aligned scratch of R rows NBP floats
+// each.  FP16/e4m3 copies run on FP16 vectors holding v * vscale (a power of
+// two that keeps |v| vscale <= 2^-8).
+int hop_horner(const dfm_op* op, int R, int d, const float* v, float* z, void* vp, void* ha, void* hb, float vscale,
+               cudaStream_t st);
 // implemented in quad.cu
 int gauss_legendre_device(int q, double* x, double* w, cudaStream_t st);
 }  // namespace dfm

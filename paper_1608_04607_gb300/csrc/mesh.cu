@@ -215,7 +215,6 @@ extern "C" int dfm_mesh_create(const double* verts, int64_t n_verts, const int32
   double* vol_d = nullptr;
   uint64_t tsize = 1;
   while (tsize < (uint64_t)(2 * nrows)) tsize <<= 1;
-  int rc = DFM_OK;
   auto fail = [&](int code) {
     cudaFree(keys); cudaFree(rowA); cudaFree(rowB); cudaFree(err_d); cudaFree(nb_d); cudaFree(vol_d);
     dfm_mesh_destroy(m);
@@ -280,7 +279,6 @@ extern "C" int dfm_mesh_create(const double* verts, int64_t n_verts, const int32
   m->total_volume = vsum;
   cudaFree(keys); cudaFree(rowA); cudaFree(rowB); cudaFree(err_d); cudaFree(nb_d); cudaFree(vol_d);
   *out = m;
-  (void)rc;
   return DFM_OK;
 #undef TRY
 }

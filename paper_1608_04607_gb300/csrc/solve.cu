@@ -389,24 +389,11 @@ struct Hop {
   float* hb = nullptr;
 };
 
-// z = sum_{k<d} B~^k v for R vectors v ([R][n]) by Horner, z <- v + B~ z.
-inline int hop_horner(const Ctx& c, const Hop& hp, int R, int d, const float* v, float* z) {
-  const int64_t rows = (int64_t)R * c.op->nrows;
-  if (d == 1) {
-    DFM_CUDA_CHECK(cudaMemcpyAsync(z, v, sizeof(float) * rows * c.op->nb, cudaMemcpyDeviceToDevice, c.st));
-    return DFM_OK;
-  }
-  int rc = hop_pack(v, hp.vp, rows, c.op->nb, c.st);
-  if (rc) return rc;
-  const float* src = hp.vp;
-  for (int k = 1; k < d; ++k) {
-    const bool last = (k == d - 1);
-    float* dst = last ? z : ((k & 1) ? hp.ha : hp.hb);
-    rc = hop_apply(hp.op, src, hp.vp, dst, R, last ? 0 : 1, c.st);
-    if (rc) return rc;
-    src = dst;
-  }
-  return DFM_OK;
+// z = sum_{k<d} B~^k v for R unit-norm vectors v ([R][n]) by Horner on the
+// low-precision copy; unit norm keeps |v| <= 1, so the FP16 hop vectors hold
+// v 2^-8.
+inline int precond_hops(const Ctx& c, const Hop& hp, int R, int d, const float* v, float* z) {
+  return ::dfm::hop_horner(hp.op, R, d, v, z, hp.vp, hp.ha, hp.hb, 1.0f / 256.0f, c.st);
 }
 
 template <typename T>
@@ -471,7 +458,7 @@ int gmres(const Ctx& c, const T* b, T* x, double tol, int m, int d, int max_iter
         // flexible step: z_j = p~(B) v_j by Horner on the 16-bit copy, w = z_j - B z_j
         T* zj = Z + (int64_t)j * n;
         if constexpr (std::is_same<T, float>::value) {
-          rc = hop_horner(c, *lp, 1, d, vj, zj);
+          rc = precond_hops(c, *lp, 1, d, vj, zj);
         } else {
           rc = set_error(DFM_ERR_UNSUPPORTED, "dfm_solve: 16-bit preconditioner hops need FP32 Krylov vectors");
         }
@@ -713,7 +700,7 @@ int gmres_batched(const Ctx& c, int R, const T* b, T* x, double tol, int m, int 
         // flexible step: z_j = p~(B) v_j on the 16-bit copy, w = z_j - B z_j
         T* zj = Z + (int64_t)j * Rn;
         if constexpr (std::is_same<T, float>::value) {
-          rc = hop_horner(c, *lp, R, d, vj, zj);
+          rc = precond_hops(c, *lp, R, d, vj, zj);
         } else {
           rc = set_error(DFM_ERR_UNSUPPORTED, "dfm_solve: 16-bit preconditioner hops need FP32 Krylov vectors");
         }
@@ -884,8 +871,9 @@ int solve_impl(const dfm_op* op, const dfm_op* const* combo, int K, const double
   // per hop moves the balance between hops and Gram-Schmidt work), else 16
   const int poly = opts->poly_degree > 0 ? std::min(opts->poly_degree, 64) : (opts->precond_precision ? 32 : 16);
   const bool use_lp = opts->precond_precision != 0 && method == DFM_SOLVE_GMRES_IR && !combo && !opts->transpose;
-  if (opts->precond_precision != 0 && opts->precond_precision != DFM_F16 && opts->precond_precision != DFM_BF16)
-    return set_error(DFM_ERR_ARG, "dfm_solve: precond_precision must be 0, DFM_F16 or DFM_BF16");
+  if (opts->precond_precision != 0 && opts->precond_precision != DFM_F16 && opts->precond_precision != DFM_BF16 &&
+      opts->precond_precision != DFM_FP8E4M3)
+    return set_error(DFM_ERR_ARG, "dfm_solve: precond_precision must be 0, DFM_F16, DFM_BF16 or DFM_FP8E4M3");
   Ctx c;
   c.op = op;
   c.st = as_stream(stream);
@@ -902,18 +890,23 @@ int solve_impl(const dfm_op* op, const dfm_op* const* combo, int K, const double
   const int64_t n = c.n;
   if (method == DFM_SOLVE_NEUMANN && op->precision != DFM_F64 && op->precision != DFM_F32)
     return set_error(DFM_ERR_UNSUPPORTED, "dfm_solve: Neumann needs an FP64 or FP32 operator");
-  if (method == DFM_SOLVE_GMRES_IR && op->precision != DFM_F32)
-    return set_error(DFM_ERR_UNSUPPORTED, "dfm_solve: GMRES_IR needs an FP32 operator");
+  if (method == DFM_SOLVE_GMRES_IR && op->precision != DFM_F32 && op->precision != DFM_BF16)
+    return set_error(DFM_ERR_UNSUPPORTED, "dfm_solve: GMRES_IR needs an FP32 or BF16 operator");
   if (method < 0 || method > 2) return set_error(DFM_ERR_ARG, "dfm_solve: unknown method");
   // right-hand sides solved in lockstep (GMRES_IR with R > 1): group size
-  // capped so that the FP32 Krylov basis of a group stays within 24 GiB
+  // capped so that a group's FP32 Krylov vectors take at most half of the
+  // device memory that is free (plus what this operator's solver workspace
+  // already holds), and at least 24 GiB
   const bool batched = (method == DFM_SOLVE_GMRES_IR && R > 1);
   int Rg = 1;
   if (batched) {
     const int64_t per_rhs =
         (int64_t)(m + 6 + (use_lp ? m : 0)) * n * 4 + (use_lp ? 3 * op->nrows * hop_nbp(op->nb) * 4 : 0);
     const int64_t cap = opts->batch > 0 ? opts->batch : 16;
-    Rg = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)R, cap, (int64_t(24) << 30) / per_rhs}));
+    size_t free_b = 0, total_b = 0;
+    DFM_CUDA_CHECK(cudaMemGetInfo(&free_b, &total_b));
+    const int64_t budget = std::max<int64_t>(int64_t(24) << 30, ((int64_t)free_b + op->swork_bytes) / 2);
+    Rg = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)R, cap, budget / per_rhs}));
   }
   // workspace: FP64 vectors (x scratch, residual x2), Krylov basis in the inner precision
   const bool inner64 = (method == DFM_SOLVE_GMRES && op->precision == DFM_F64);

@@ -17,6 +17,8 @@
 #include <algorithm>
 #include <type_traits>
 
+#include <cuda_bf16.h>
+
 #include <mutex>
 #include <unordered_map>
 
@@ -576,11 +578,17 @@ int apply_impl(const dfm_op* op, const void* x, const void* x0, void* y, int R, 
       return launch<double, double, double>(op, (const double*)x, (const double*)x0, (double*)y, R, alpha, trans, st);
     if (op->precision == DFM_F32)
       return launch<float, double, double>(op, (const double*)x, (const double*)x0, (double*)y, R, alpha, trans, st);
+    if (op->precision == DFM_BF16)
+      return launch<__nv_bfloat16, double, double>(op, (const double*)x, (const double*)x0, (double*)y, R, alpha,
+                                                   trans, st);
   } else if (xtype == DFM_F32) {
     if (op->precision == DFM_F32)
       return launch<float, float, float>(op, (const float*)x, (const float*)x0, (float*)y, R, alpha, trans, st);
     if (op->precision == DFM_F64)
       return launch<double, float, double>(op, (const float*)x, (const float*)x0, (float*)y, R, alpha, trans, st);
+    if (op->precision == DFM_BF16)
+      return launch<__nv_bfloat16, float, float>(op, (const float*)x, (const float*)x0, (float*)y, R, alpha, trans,
+                                                 st);
   }
   return set_error(DFM_ERR_UNSUPPORTED, "dfm_apply: unsupported operator/vector precision");
 }

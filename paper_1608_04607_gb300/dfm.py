@@ -26,7 +26,7 @@ DFM_ERR_NOT_CONVERGED = -5
 DFM_ERR_NONFINITE = -6
 DFM_ERR_UNSUPPORTED = -7
 
-F64, F32, BF16, F16 = 0, 1, 2, 3
+F64, F32, BF16, F16, FP8E4M3 = 0, 1, 2, 3, 4
 NEUMANN, GMRES, GMRES_IR = 0, 1, 2
 
 
@@ -238,7 +238,7 @@ class Operator:
     def blocks(self):
         """Copy of the block storage as a torch CUDA tensor [rows, 3, nb, nb]."""
         torch = self._torch
-        dt = {F64: torch.float64, F32: torch.float32}[self.precision]
+        dt = {F64: torch.float64, F32: torch.float32, BF16: torch.bfloat16}[self.precision]
         buf = torch.empty(self.n_rows * self.row_stride, dtype=dt, device="cuda")
         _check(_lib.dfm_op_copy_vals(self._h, _ptr(buf), self.bytes, _stream()), "dfm_op_copy_vals")
         nb = self.nb
@@ -255,8 +255,9 @@ class Operator:
         return y
 
     def precond(self, x, degree=16, precision=F16, out=None):
-        """z = sum_{k<degree} B~^k x on the 16-bit copy B~ of the blocks
-        (dfm_precond_apply); x: FP32 [R, rows, nb] or [rows, nb]."""
+        """z = sum_{k<degree} B~^k x on the low-precision copy B~ of the blocks
+        (dfm_precond_apply; precision F16, BF16 or FP8E4M3); x: FP32
+        [R, rows, nb] or [rows, nb]."""
         torch = self._torch
         if x.dtype != torch.float32:
             raise TypeError("precond: x must be float32")

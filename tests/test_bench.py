@@ -17,7 +17,7 @@ N_ROWS, NB, NP = 192_000, 15, 4
 
 
 def _stats(**kw):
-    base = {"assemble": (0, 0.0), "spmv_f32": (0, 0.0), "spmv_16bit": (0, 0.0), "spmv_f64vec": (0, 0.0),
+    base = {"assemble": (0, 0.0), "spmv_f32": (0, 0.0), "hop": (0, 0.0), "spmv_f64vec": (0, 0.0),
             "dot": (0, 0.0), "axpy": (0, 0.0)}
     base.update(kw)
     return base
@@ -37,11 +37,11 @@ def test_spmv_bytes_counts_each_operand_once():
 
 
 def test_sixteen_bit_hops_dominate_with_their_own_bytes():
-    st = _stats(assemble=(1, 22.0), spmv_f32=(120, 12.0), spmv_16bit=(1880, 110.0), dot=(250, 17.0))
+    st = _stats(assemble=(1, 22.0), spmv_f32=(120, 12.0), hop=(1880, 110.0), dot=(250, 17.0))
     kern, total, roof = _summ(st, "f16")
-    assert roof["kernel"] == "spmv_16bit" and roof["bound"] == "hbm" and roof["unit"] == "GB/s"
-    by = N_ROWS * (3 * NB * NB * 2 + 4 + NB * 4 * 3)
-    assert kern["spmv_16bit"]["bytes_per_launch"] == by
+    assert roof["kernel"] == "hop" and roof["bound"] == "hbm" and roof["unit"] == "GB/s"
+    by = N_ROWS * (3 * NB * NB * 2 + 4 + NB * 2 * 3)  # FP16 copy, FP16 hop vectors
+    assert kern["hop"]["bytes_per_launch"] == by
     ach = by / (110.0 / 1880 * 1e-3) / 1e9
     assert roof["achieved"] == pytest.approx(ach, rel=1e-6)
     assert roof["peak"] == 6000.0 and roof["frac"] == pytest.approx(ach / 6000.0, abs=1e-4)
@@ -50,6 +50,15 @@ def test_sixteen_bit_hops_dominate_with_their_own_bytes():
     assert total["dot"] == 17.0
     key = ("hop_kernel<15, __half>", "kuhn20_np4")
     assert roof["traffic"] == bench.MEASURED_TRAFFIC.get(key)
+
+
+def test_fp8_hops_count_one_byte_per_value_and_the_row_scale():
+    st = _stats(assemble=(1, 22.0), spmv_f32=(60, 6.0), hop=(1900, 60.0))
+    kern, _, roof = _summ(st, "fp8")
+    assert roof["kernel"] == "hop"
+    assert kern["hop"]["bytes_per_launch"] == N_ROWS * (3 * NB * NB * 1 + 4 + NB * 2 * 3 + 4)
+    kern, _, _ = _summ(st, "bf16")  # BF16 copy: FP32 hop vectors
+    assert kern["hop"]["bytes_per_launch"] == N_ROWS * (3 * NB * NB * 2 + 4 + NB * 4 * 3)
 
 
 def test_fp32_preconditioner_hops_read_no_x0():

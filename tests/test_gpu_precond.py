@@ -1,14 +1,14 @@
-"""GPU parity of the 16-bit polynomial preconditioner (dfm_precond_apply,
-the hops of the flexible inner solve) with the oracle.
+"""GPU parity of the low-precision polynomial preconditioner
+(dfm_precond_apply, the hops of the flexible inner solve) with the oracle.
 
 The preconditioner is z = sum_{k<d} B~^k x, B~ the FP16 or BF16 rounding (to
-nearest, ties to even) of the FP32 blocks.  The oracle evaluates the same sum
-in FP64 from the GPU's FP32 blocks rounded the same way on the host, so the
-only difference left is FP32 arithmetic in the kernels: relative error
-<= 2e-5 of max |z| for up to 5 hops.  The mesh drops one tet of the Kuhn cube
-(161 tets), so the last tile of rows is ragged for every basis size; N_p = 2,
-4, 5 give 6, 15, 21 functions (padded widths 8, 16, 24: 16, 8 and 5 rows per
-tile)."""
+nearest, ties to even) of the FP32 blocks, or s_R times their e4m3 rounding
+relative to a per-row scale s_R = max |row entry| / 448.  The oracle
+evaluates the same sum in FP64 from the GPU's FP32 blocks rounded the same way
+on the host, so the only difference left is the kernels' arithmetic (see
+TOL).  The mesh drops one tet of the Kuhn cube (161 tets), so the last tile
+of rows is ragged for every basis size; N_p = 2, 4, 5 give 6, 15, 21
+functions (padded widths 8, 16, 24: 16, 8 and 5 rows per tile)."""
 import numpy as np
 import pytest
 
@@ -27,6 +27,16 @@ def D():
     return dfm
 
 
+# The BF16 copy runs on FP32 vectors with FP32 accumulation: only FP32
+# rounding separates it from the oracle (<= 2e-5 of max |z| over 4 hops).  The
+# FP16 and e4m3 copies run on FP16 vectors (x scaled by a power of two) and
+# sum each block's products in packed FP16 before adding the three blocks in
+# FP32: per hop the vector is rounded to FP16 (relative 2^-11) and each lane
+# adds 2 NBP/8 <= 6 products with one rounding each, so 5 hops stay within
+# 3e-3 of max |z|, while a wrong block, slot or scale gives errors of order 1.
+TOL = {"bf16": 2e-5, "f16": 3e-3, "e4m3": 3e-3}
+
+
 def _round_f16(a32):
     return np.asarray(a32, dtype=np.float32).astype(np.float16).astype(np.float64)
 
@@ -37,6 +47,30 @@ def _round_bf16(a32):
     return u.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
+def _e4m3(v):
+    """Round float32 values to e4m3 (to nearest, ties to even; saturate at
+    448): 3 fraction bits, normal exponents down to 2^-6, subnormal spacing
+    2^-9."""
+    v = np.asarray(v, dtype=np.float64)
+    a = np.abs(v)
+    _, ex = np.frexp(a)  # a = f 2^ex, f in [0.5, 1)
+    e = np.maximum(ex - 1, -6)
+    spacing = np.ldexp(1.0, e - 3)
+    q = np.round(a / spacing) * spacing
+    return np.sign(v) * np.minimum(q, 448.0)
+
+
+def _round_e4m3_rows(b32, recv, nt):
+    """The e4m3 copy in the operator's row layout b32[row, slot, a, b]:
+    s_R = max |entry of row R| / 448 (FP32), q = e4m3(v / s_R) with v / s_R
+    rounded to FP32, value = s_R q."""
+    b32 = np.asarray(b32, dtype=np.float32)
+    mx = np.abs(b32).reshape(b32.shape[0], -1).max(axis=1).astype(np.float32)
+    s = np.where(mx > 0, mx / np.float32(448.0), np.float32(1.0)).astype(np.float32)
+    ratio = (b32 / s[:, None, None, None]).astype(np.float32)
+    return _e4m3(ratio) * s.astype(np.float64)[:, None, None, None]
+
+
 @pytest.fixture(scope="module")
 def mesh161():
     m = kuhn_cube_mesh(3, jitter=0.2, seed=8)
@@ -44,7 +78,7 @@ def mesh161():
 
 
 @pytest.mark.parametrize("Np", [2, 4, 5])
-@pytest.mark.parametrize("prec", ["f16", "bf16"])
+@pytest.mark.parametrize("prec", ["f16", "bf16", "e4m3"])
 def test_precond_matches_oracle_on_rounded_blocks(D, oracle_mod, mesh161, Np, prec):
     import torch
 
@@ -53,7 +87,10 @@ def test_precond_matches_oracle_on_rounded_blocks(D, oracle_mod, mesh161, Np, pr
     mesh = D.Mesh(verts, tets, refl=0.9)
     op = D.Operator(mesh, Np, mu=0.2, precision=D.F32)
     b32 = op.blocks().cpu().numpy()
-    rounded = _round_f16(b32) if prec == "f16" else _round_bf16(b32)
+    if prec == "e4m3":
+        rounded = _round_e4m3_rows(b32, mesh.recv(), nt)
+    else:
+        rounded = _round_f16(b32) if prec == "f16" else _round_bf16(b32)
     blocks = to_oracle_layout(rounded, mesh.recv(), nt)
     t, f, fp = oracle_mod.pair_list(nt)
     dest = mesh.recv()[4 * t + fp].reshape(4 * nt, 3).astype(np.int64)
@@ -63,13 +100,14 @@ def test_precond_matches_oracle_on_rounded_blocks(D, oracle_mod, mesh161, Np, pr
     x = rng.standard_normal((R, 4 * nt, op.nb)).astype(np.float32)
     xt = torch.tensor(x, device="cuda")
     for d in (1, 2, 5):
-        z = op.precond(xt, degree=d, precision=D.F16 if prec == "f16" else D.BF16).cpu().numpy()
+        z = op.precond(xt, degree=d, precision={"f16": D.F16, "bf16": D.BF16, "e4m3": D.FP8E4M3}[prec])
+        z = z.cpu().numpy()
         for r in range(R):
             xr = x[r].astype(np.float64)
             zr = xr.copy()
             for _ in range(d - 1):
                 zr = xr + oracle_mod.apply(ref_op, zr)
-            assert np.abs(z[r] - zr).max() <= 2e-5 * np.abs(zr).max(), (d, r)
+            assert np.abs(z[r] - zr).max() <= TOL[prec] * np.abs(zr).max(), (d, r)
 
 
 def test_precond_tracks_reassembly_and_rejects_bad_arguments(D, mesh161):
@@ -93,3 +131,21 @@ def test_precond_tracks_reassembly_and_rejects_bad_arguments(D, mesh161):
         op.precond(x, degree=65)
     with pytest.raises(RuntimeError):
         op.precond(x, degree=2, out=x)
+
+
+@pytest.mark.parametrize("prec", ["f16", "e4m3"])
+def test_precond_fp16_vectors_follow_the_input_scale(D, mesh161, prec):
+    """The FP16 hop vectors hold x times a power of two chosen from max |x|,
+    so the result scales with x across the FP16 range and beyond it."""
+    import torch
+
+    verts, tets = mesh161
+    mesh = D.Mesh(verts, tets, refl=0.9)
+    op = D.Operator(mesh, 4, mu=0.2, precision=D.F32)
+    p = D.F16 if prec == "f16" else D.FP8E4M3
+    x = torch.randn((4 * tets.shape[0], op.nb), device="cuda", dtype=torch.float32)
+    z = op.precond(x, degree=6, precision=p)
+    for s in (2.0 ** 40, 2.0 ** -40):
+        zs = op.precond(x * s, degree=6, precision=p)
+        assert torch.isfinite(zs).all()
+        assert float((zs / s - z).abs().max()) <= 1e-6 * float(z.abs().max())
