@@ -432,6 +432,11 @@ def _oracle_sample(wname, seconds, op_apps=None):
         n_pairs += batch
         batch *= 2
     per_block = t_asm / n_pairs
+    # the same assembly on one thread (a fixed sample of 32 pairs)
+    sel = rng.integers(0, t.size, size=32)
+    t0 = time.perf_counter()
+    oracle.blocks_for_pairs(m.verts, m.tets, topo, mu, w["refl"], Np, t[sel], f[sel], fp[sel], rtol=1e-13, nthreads=1)
+    per_block_1t = (time.perf_counter() - t0) / 32
     # (b) oracle GMRES iterations at full size
     blocks = rng.standard_normal((4 * m.n_tets, 3, nb, nb)) * (0.3 / nb)
     dest = topo.recv[4 * np.repeat(np.arange(m.n_tets), 12) + fp].reshape(4 * m.n_tets, 3)
@@ -446,13 +451,28 @@ def _oracle_sample(wname, seconds, op_apps=None):
     est = per_block * 12 * m.n_tets + per_app * op_apps
     sample = (f"oracle assembly of {n_pairs} random face pairs (adaptive to 1e-13) and {k} oracle GMRES(64) "
               f"iterations at full size; extrapolated to 12 x {m.n_tets} blocks + {op_apps} operator applications")
-    return est, sample, threads, per_block, per_app
+    return est, sample, threads, per_block, per_app, per_block_1t
+
+
+def _cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k = line.split(":")[0].strip().lower()
+                if k in ("model name", "cpu part", "hardware"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+
+    return platform.processor() or platform.machine()
 
 
 def cpu_baseline(wname, op_apps, seconds=20.0):
-    est, sample, threads, per_block, per_app = _oracle_sample(wname, seconds, op_apps)
+    est, sample, threads, per_block, per_app, per_block_1t = _oracle_sample(wname, seconds, op_apps)
     return {"value": 1.0 / est, "unit": "solves/s", "cores": threads, "kind": "oracle", "sample": sample,
-            "s_per_block": per_block, "s_per_application": per_app}
+            "s_per_block": per_block, "s_per_block_1thread": per_block_1t, "s_per_application": per_app,
+            "cpu_model": _cpu_model()}
 
 
 def run_reference(args):
@@ -467,7 +487,7 @@ def run_reference(args):
     vals = []
     last = None
     for i in range(args.warmup + args.steps):
-        est, sample, threads, _, _ = _oracle_sample(args.workload, args.cpu_seconds / 2, apps)
+        est, sample, threads, _, _, _ = _oracle_sample(args.workload, args.cpu_seconds / 2, apps)
         if i >= args.warmup:
             vals.append(est)
         last = (sample, threads)
@@ -525,7 +545,9 @@ def run_batched(args):
     K = 3 damping moments B^(k) = d^k B / d mu^k at mu_c = 0.105 once and
     solves all right-hand sides with B(mu_r) = sum_k (mu_r - mu_c)^k / k! B^(k)
     (truncation below 1e-7 for these tets), in lockstep groups that share
-    every operator pass, to an FP64 relative residual of 1e-6."""
+    every operator pass, to an FP64 relative residual of 1e-6.  With
+    --precond f16/bf16/fp8 the polynomial preconditioner's hops run on a
+    low-precision copy of B(mu_c) alone (flexible inner solve)."""
     import torch
 
     from paper_1608_04607_gb300 import dfm
@@ -550,7 +572,7 @@ def run_batched(args):
             o.reassemble(mu_c)
         rho0 = dfm.source(mesh, Np, rows)
         return dfm.solve_combo(ops, coef, rho0, tol=tol, batch=args.batch, poly_degree=args.poly,
-                               restart=args.restart)
+                               restart=args.restart, precond_precision=PRECOND[args.precond])
 
     rho, info = step()
     torch.cuda.synchronize()
@@ -566,10 +588,107 @@ def run_batched(args):
     ms = e0.elapsed_time(e1)
     n_sp, ms_sp = dfm.kernel_stats(dfm.KERNEL_SPMV)
     n_as, ms_as = dfm.kernel_stats(dfm.KERNEL_ASSEMBLE)
+    n_hop, ms_hop = dfm.kernel_stats(dfm.KERNEL_SPMV16)
     print(json.dumps({"mode": "batched", "workload": wname, "n_tets": int(m.n_tets), "rhs": R, "K": K,
-                      "value": R / (ms * 1e-3), "unit": "solves/s", "ms_per_step": ms,
+                      "value": R / (ms * 1e-3), "unit": "solves/s", "ms_per_step": ms, "precond": args.precond,
                       "operator_passes": info.iters, "resid_worst": info.resid,
-                      "assembly_ms": ms_as, "spmv_launches": n_sp, "spmv_ms": ms_sp}))
+                      "assembly_ms": ms_as, "combo_launches": n_sp, "combo_ms": ms_sp,
+                      "hop_launches": n_hop, "hop_ms": ms_hop,
+                      "dot_ms": dfm.kernel_stats(dfm.KERNEL_DOT)[1], "axpy_ms": dfm.kernel_stats(dfm.KERNEL_AXPY)[1]}))
+
+
+def run_many(args):
+    """Many-source workload with a 45-function basis: the 32^3 Kuhn cube
+    (196,608 tets, Np = 8, mu = 0.05, r = 0.95) with 64 random boundary-face
+    sources.  One step assembles the operator in BF16 (9.6 GB), solves all 64
+    right-hand sides to an FP64 relative residual of 1e-6 (FP64-residual
+    refinement around flexible FP32 GMRES in lockstep groups, preconditioned by
+    sum_{k<d} B~^k on an e4m3 copy of the blocks), and runs the adjoint of
+    J = sum_r mean receiver density (cells [14,18)^3): one transposed solve and
+    the dB/dmu contraction for all 64 solutions."""
+    import torch
+
+    from paper_1608_04607_gb300 import dfm
+    from paper_1608_04607_gb300.inputs import workload
+
+    torch.cuda.set_device(0)
+    wname = args.workload if args.workload != WORKLOAD else "kuhn32_np8_rhs64"
+    w = workload(wname)
+    m = w["mesh"]
+    Np = w["Np"]
+    rows = np.asarray(w["sources"], dtype=np.int64)[: (args.rhs or len(w["sources"]))]
+    R = len(rows)
+    tol = args.tol if args.tol else w["tol"]
+    mu = float(w["mu"][0])
+    receiver = w["receiver"]
+    restart = args.restart or 64
+    batch = args.batch or 8
+    precond = PRECOND[args.precond]
+    mesh = dfm.Mesh(m.verts, m.tets, refl=w["refl"])
+    op = dfm.Operator(mesh, Np, mu=mu, precision=dfm.BF16)
+    g, dg = dfm.interior_density(mesh, Np, receiver, weights=1.0 / len(receiver), mu=mu)
+
+    def solve(rho0):
+        return op.solve(rho0, tol=tol, restart=restart, poly_degree=args.poly, batch=batch, precond_precision=precond)
+
+    rho, info = solve(dfm.source(mesh, Np, rows))  # warm-up (allocations)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    dfm.stats_reset()
+    dfm.stats_enable(True)
+    ev[0].record()
+    op.reassemble(mu)
+    ev[1].record()
+    rho, info = solve(dfm.source(mesh, Np, rows))
+    ev[2].record()
+    lam, dj, ainfo = op.adjoint(rho, g, dg, tol=tol, restart=restart, poly_degree=args.poly)
+    ev[3].record()
+    torch.cuda.synchronize()
+    dfm.stats_enable(False)
+    asm_ms, solve_ms, adj_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3])
+    peaks, peak_src = _peaks()
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    ks = {name: dfm.kernel_stats(k) for name, k in (("assemble", dfm.KERNEL_ASSEMBLE), ("spmv", dfm.KERNEL_SPMV),
+                                                    ("hop", dfm.KERNEL_SPMV16), ("spmv_t", dfm.KERNEL_SPMV_T),
+                                                    ("spmv_f64vec", dfm.KERNEL_SPMV64), ("contract", dfm.KERNEL_CONTRACT),
+                                                    ("dot", dfm.KERNEL_DOT), ("axpy", dfm.KERNEL_AXPY))}
+    nb = op.nb
+    hbm_peak = float(peaks.get("hbm_gbs", HBM_PEAK_FALLBACK))
+    Rl = min(batch, R)
+    kern = {}
+    n, ms = ks["assemble"]
+    if n:
+        fl = dfm.op_nodes(op) * flops_per_node(Np)
+        fp32_peak = nsm * FP32_LANES_PER_SM * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+        ach = fl / (ms / n * 1e-3) / 1e12
+        kern["assemble"] = {"bound": "alu", "ms_per_launch": ms / n, "achieved": ach, "peak": fp32_peak,
+                            "unit": "TFLOP/s", "frac": ach / fp32_peak, "blocks_per_s": 12 * m.n_tets / (ms / n * 1e-3)}
+
+    def hbm(name, by):
+        n, ms = ks[name]
+        if n:
+            ach = by / (ms / n * 1e-3) / 1e9
+            kern[name] = {"bound": "hbm", "launches": n, "ms_per_launch": ms / n, "bytes_per_launch": by,
+                          "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak}
+
+    # BF16 blocks read once per launch; up to `batch` right-hand sides of FP32 x, x0, y
+    hbm("spmv", mesh.n_rows * (3 * nb * nb * 2 + 4) + 3 * nb * 4 * mesh.n_rows * Rl)
+    # e4m3 copy (+ row scale) once per launch; FP16 x, x0, y per right-hand side
+    hbm("hop", mesh.n_rows * (3 * nb * nb + 8) + 3 * nb * 2 * mesh.n_rows * Rl)
+    # transposed BF16 application, one right-hand side (the adjoint)
+    hbm("spmv_t", mesh.n_rows * (3 * nb * nb * 2 + 4) + 3 * nb * 4 * mesh.n_rows)
+    for k2 in ("spmv_f64vec", "contract", "dot", "axpy"):
+        n, ms = ks[k2]
+        if n:
+            kern[k2] = {"launches": n, "ms_total": ms}
+    print(json.dumps({"mode": "many", "workload": wname, "n_tets": int(m.n_tets), "nb": nb, "rhs": R,
+                      "metric": METRIC, "value": R / (solve_ms * 1e-3), "unit": "solves/s",
+                      "assembly_ms": asm_ms, "solve_ms": solve_ms, "adjoint_ms": adj_ms,
+                      "operator_passes": info.iters, "resid_worst": info.resid, "adjoint_passes": ainfo.iters,
+                      "adjoint_resid": ainfo.resid, "restart": restart, "batch": batch, "precond": args.precond,
+                      "poly_degree": args.poly or 32, "operator_bytes": op.bytes, "J": float((g * rho).sum()),
+                      "grad_abs_max": float(dj.abs().max()), "kernels": kern,
+                      "kernel_ms": {k: round(v[1], 2) for k, v in ks.items()}, "peak_source": peak_src}))
 
 
 def run_adjoint(args):
@@ -664,12 +783,12 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparator", action="store_true")
-    ap.add_argument("--precond", choices=["f32", "f16", "bf16", "fp8"], default="f16",
+    ap.add_argument("--precond", choices=["f32", "f16", "bf16", "fp8"], default="fp8",
                     help="precision of the blocks used by the polynomial preconditioner's hops")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--ref-apps", type=int, default=0,
                     help="reference arm: operator applications charged per solve (0 = the FP64 path's count)")
-    ap.add_argument("--mode", choices=["solve", "apply", "adjoint", "batched"], default="solve")
+    ap.add_argument("--mode", choices=["solve", "apply", "adjoint", "batched", "many"], default="solve")
     ap.add_argument("--rhs", type=int, default=0, help="batched mode: number of right-hand sides (0 = all)")
     ap.add_argument("--batch", type=int, default=0, help="batched mode: right-hand sides per lockstep group")
     ap.add_argument("--fd", type=int, default=0, help="adjoint mode: elements checked by central differences")
@@ -682,6 +801,8 @@ def main():
         run_adjoint(args)
     elif args.mode == "batched":
         run_batched(args)
+    elif args.mode == "many":
+        run_many(args)
     else:
         run_gpu(args)
 

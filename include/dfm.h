@@ -236,7 +236,10 @@ int dfm_solve(const dfm_op* op, const double* rho0, int R, double* rho, const df
  * B_r = sum_k coef_host[r * K + k] B_k (see dfm_apply_combo): the stationary
  * densities rho_r = (I - B_r)^{-1} rho0_r, batched as in dfm_solve (every
  * operator pass serves a group of right-hand sides).  opts->method must be
- * DFM_SOLVE_GMRES_IR, no transpose.  Errors as dfm_solve. */
+ * DFM_SOLVE_GMRES_IR, no transpose.  With opts->precond_precision set, the
+ * preconditioner's hops use a low-precision copy of B_0 alone (the same
+ * p(B~_0) for every right-hand side; the Krylov operator is each I - B_r).
+ * Errors as dfm_solve. */
 int dfm_solve_combo(const dfm_op* const* ops, int K, const double* coef_host, const double* rho0, int R, double* rho,
                     const dfm_solve_opts* opts, void* stream, dfm_solve_info* info);
 

@@ -1,0 +1,16 @@
+// Instantiation of the preconditioner hop kernel for the FP16 copy.
+#include "hop_kernel.cuh"
+
+namespace dfm {
+
+int hop_launch_f16(const dfm_op* op, const __half* xp, const __half* x0p, void* y, int R, float out_scale, bool outp,
+                   cudaStream_t st) {
+  using namespace hopk;
+  if (R == 1)
+    return outp ? launch_hop<__half, __half, true, 1>(op, xp, x0p, y, R, out_scale, st)
+                : launch_hop<__half, __half, false, 1>(op, xp, x0p, y, R, out_scale, st);
+  return outp ? launch_hop<__half, __half, true, kHopMaxRhs>(op, xp, x0p, y, R, out_scale, st)
+              : launch_hop<__half, __half, false, kHopMaxRhs>(op, xp, x0p, y, R, out_scale, st);
+}
+
+}  // namespace dfm

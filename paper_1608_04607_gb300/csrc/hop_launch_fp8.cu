@@ -1,0 +1,16 @@
+// Instantiation of the preconditioner hop kernel for the e4m3 copy.
+#include "hop_kernel.cuh"
+
+namespace dfm {
+
+int hop_launch_fp8(const dfm_op* op, const __half* xp, const __half* x0p, void* y, int R, float out_scale, bool outp,
+                   cudaStream_t st) {
+  using namespace hopk;
+  if (R == 1)
+    return outp ? launch_hop<__nv_fp8_e4m3, __half, true, 1>(op, xp, x0p, y, R, out_scale, st)
+                : launch_hop<__nv_fp8_e4m3, __half, false, 1>(op, xp, x0p, y, R, out_scale, st);
+  return outp ? launch_hop<__nv_fp8_e4m3, __half, true, kHopMaxRhs>(op, xp, x0p, y, R, out_scale, st)
+              : launch_hop<__nv_fp8_e4m3, __half, false, kHopMaxRhs>(op, xp, x0p, y, R, out_scale, st);
+}
+
+}  // namespace dfm

@@ -870,7 +870,9 @@ int solve_impl(const dfm_op* op, const dfm_op* const* combo, int K, const double
   // default degree: 32 when the hops run on the 16-bit copy (half the bytes
   // per hop moves the balance between hops and Gram-Schmidt work), else 16
   const int poly = opts->poly_degree > 0 ? std::min(opts->poly_degree, 64) : (opts->precond_precision ? 32 : 16);
-  const bool use_lp = opts->precond_precision != 0 && method == DFM_SOLVE_GMRES_IR && !combo && !opts->transpose;
+  // with combined operators the preconditioner's copy is made from ops[0]
+  // (B_0, e.g. B(mu_c)): one p(B~_0) serves every right-hand side's B_r
+  const bool use_lp = opts->precond_precision != 0 && method == DFM_SOLVE_GMRES_IR && !opts->transpose;
   if (opts->precond_precision != 0 && opts->precond_precision != DFM_F16 && opts->precond_precision != DFM_BF16 &&
       opts->precond_precision != DFM_FP8E4M3)
     return set_error(DFM_ERR_ARG, "dfm_solve: precond_precision must be 0, DFM_F16, DFM_BF16 or DFM_FP8E4M3");

@@ -1,8 +1,9 @@
 // Device helpers for the bulk-copy (TMA) pipelines of the operator
 // applications: mbarrier set-up, arrival and bounded waits, 1-D
 // cp.async.bulk global -> shared copies (optionally with an L2 eviction
-// hint).  Every wait polls at most kWaitPolls times; callers turn a time-out
-// into an error flag instead of spinning forever.
+// hint).  Every wait polls at most kWaitPolls times (each poll suspends for
+// at most about kSuspendNs, so a wait gives up after a few seconds); callers
+// turn a time-out into an error flag instead of spinning forever.
 #pragma once
 
 #include <stdint.h>
@@ -60,18 +61,35 @@ __device__ __forceinline__ uint64_t l2_policy_evict_first() {
   return p;
 }
 
+// 16-byte asynchronous global -> shared copy through L2 only (cp.async.cg);
+// both addresses 16-byte aligned
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+
+// one arrival on bar once every cp.async this thread issued so far has landed
+// (noinc: the arrival is part of the barrier's expected count)
+__device__ __forceinline__ void cp_async_arrive_noinc(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
 // makes the generic-proxy writes of this thread (e.g. a staged row map)
 // visible to later async-proxy operations on shared memory
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// The waiting thread may be suspended until the phase completes, for at most
+// about kSuspendNs per call (fewer polling instructions competing for issue
+// slots with the producer: 1-2% per application).
+constexpr unsigned kSuspendNs = 1000;
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
   unsigned ok;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
+      : "r"(smem_addr(bar)), "r"(parity), "r"(kSuspendNs)
       : "memory");
   return ok != 0;
 }

@@ -340,7 +340,8 @@ def apply_combo(ops, coef, x, x0=None, alpha=1.0, out=None):
     return y
 
 
-def solve_combo(ops, coef, rho0, tol=1e-8, max_iter=0, restart=0, inner_tol=0.0, poly_degree=0, batch=0):
+def solve_combo(ops, coef, rho0, tol=1e-8, max_iter=0, restart=0, inner_tol=0.0, poly_degree=0, batch=0,
+                precond_precision=0):
     """rho_r = (I - sum_k coef[r, k] B_k)^{-1} rho0_r (dfm_solve_combo); returns (rho, SolveInfo)."""
     import torch
 
@@ -348,7 +349,7 @@ def solve_combo(ops, coef, rho0, tol=1e-8, max_iter=0, restart=0, inner_tol=0.0,
     R = 1 if rho0.dim() == 2 else rho0.shape[0]
     rho = torch.empty_like(rho0)
     o = SolveOpts(method=GMRES_IR, tol=tol, max_iter=max_iter, restart=restart, use_x0=0, inner_tol=inner_tol,
-                  transpose=0, poly_degree=poly_degree, batch=batch)
+                  transpose=0, poly_degree=poly_degree, batch=batch, precond_precision=precond_precision)
     info = SolveInfo()
     _check(load().dfm_solve_combo(_op_array(ops), len(ops), coef.ctypes.data_as(ctypes.c_void_p), _ptr(rho0), R,
                                   _ptr(rho), ctypes.byref(o), _stream(), ctypes.byref(info)), "dfm_solve_combo")

@@ -77,3 +77,27 @@ def test_apply_combo_and_solve_combo(setup, oracle_mod):
         ref = oracle_mod.solve_dense(Br, rho0[r].cpu().numpy())
         got = rho[r].cpu().numpy()
         assert np.linalg.norm(got - ref) <= 1e-8 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("precond", ["f16", "fp8"])
+def test_solve_combo_with_low_precision_preconditioner(setup, oracle_mod, precond):
+    """The flexible solve preconditions every right-hand side with p(B~_0),
+    the polynomial on a low-precision copy of the first operator (B(mu_c));
+    the solutions still match LU with each right-hand side's own operator."""
+    dfm, m, mesh, Np, mu_c, K, ops = setup
+    rng = np.random.default_rng(4)
+    mu_rhs = rng.uniform(0.01, 0.2, 5)
+    coef = dfm.moment_coefficients(mu_rhs, mu_c, K)
+    R = len(mu_rhs)
+    recv = mesh.recv()
+    t, f, fp = oracle_mod.pair_list(m.n_tets)
+    dest = recv[4 * t + fp].reshape(-1, 3).astype(np.int64)
+    blocks = [to_oracle_layout(o.blocks().cpu().numpy(), recv, m.n_tets) for o in ops]
+    rho0 = dfm.source(mesh, Np, np.nonzero(recv == np.arange(mesh.n_rows))[0][rng.integers(0, 48, R)])
+    pp = dfm.F16 if precond == "f16" else dfm.FP8E4M3
+    rho, info = dfm.solve_combo(ops, coef, rho0, tol=1e-10, batch=4, precond_precision=pp)
+    assert info.resid <= 1e-10
+    for r in range(R):
+        Br = oracle_mod.Operator(Np=Np, blocks=sum(coef[r, k] * blocks[k] for k in range(K)), dest=dest)
+        ref = oracle_mod.solve_dense(Br, rho0[r].cpu().numpy())
+        assert np.linalg.norm(rho[r].cpu().numpy() - ref) <= 1e-8 * np.linalg.norm(ref)
