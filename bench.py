@@ -538,6 +538,47 @@ def run_apply(args):
                       "frac": ach / float(peaks.get("hbm_gbs", HBM_PEAK_FALLBACK)), "peak_source": src}))
 
 
+def run_hop(args):
+    """Preconditioner-hop micro-benchmark: z = sum_{k<9} B~^k x (8 hops per
+    call) on the workload's low-precision copy (--precond) for --rhs
+    right-hand sides (default 1), timed per hop launch with CUDA events."""
+    import torch
+
+    from paper_1608_04607_gb300 import dfm
+    from paper_1608_04607_gb300.inputs import workload
+
+    torch.cuda.set_device(0)
+    w = workload(args.workload)
+    m = w["mesh"]
+    R = args.rhs or 1
+    mesh = dfm.Mesh(m.verts, m.tets, refl=w["refl"])
+    prec = dfm.BF16 if w["Np"] >= 8 else dfm.F32
+    op = dfm.Operator(mesh, w["Np"], mu=float(np.asarray(w["mu"]).reshape(-1)[0]), precision=prec)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.randn((R, mesh.n_rows, op.nb), device="cuda", dtype=torch.float32, generator=g)
+    x /= x.norm(dim=(1, 2), keepdim=True)
+    pp = PRECOND[args.precond]
+    for _ in range(args.warmup):
+        op.precond(x, degree=9, precision=pp)
+    torch.cuda.synchronize()
+    dfm.stats_reset()
+    dfm.stats_enable(True)
+    for _ in range(args.steps):
+        op.precond(x, degree=9, precision=pp)
+    torch.cuda.synchronize()
+    n, ms = dfm.kernel_stats(dfm.KERNEL_SPMV16)
+    dfm.stats_enable(False)
+    nb = op.nb
+    eb = 1 if args.precond == "fp8" else 2
+    vb = 4 if args.precond == "bf16" else 2
+    by = mesh.n_rows * (3 * nb * nb * eb + 4 + (4 if eb == 1 else 0)) + 3 * nb * vb * mesh.n_rows * R
+    peaks, src = _peaks()
+    ach = by / (ms / n * 1e-3) / 1e9
+    print(json.dumps({"mode": "hop", "workload": args.workload, "precond": args.precond, "rhs": R, "launches": n,
+                      "ms_per_launch": ms / n, "bytes_per_launch": by, "achieved_gbs": ach,
+                      "frac": ach / float(peaks.get("hbm_gbs", HBM_PEAK_FALLBACK)), "peak_source": src}))
+
+
 def run_batched(args):
     """Batched workload: 128 right-hand sides (random boundary-face sources) on
     the 30^3 Kuhn cube (162,000 tets, Np = 4), each with its own uniform damping
@@ -788,7 +829,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--ref-apps", type=int, default=0,
                     help="reference arm: operator applications charged per solve (0 = the FP64 path's count)")
-    ap.add_argument("--mode", choices=["solve", "apply", "adjoint", "batched", "many"], default="solve")
+    ap.add_argument("--mode", choices=["solve", "apply", "hop", "adjoint", "batched", "many"], default="solve")
     ap.add_argument("--rhs", type=int, default=0, help="batched mode: number of right-hand sides (0 = all)")
     ap.add_argument("--batch", type=int, default=0, help="batched mode: right-hand sides per lockstep group")
     ap.add_argument("--fd", type=int, default=0, help="adjoint mode: elements checked by central differences")
@@ -797,6 +838,8 @@ def main():
         run_reference(args)
     elif args.mode == "apply":
         run_apply(args)
+    elif args.mode == "hop":
+        run_hop(args)
     elif args.mode == "adjoint":
         run_adjoint(args)
     elif args.mode == "batched":
