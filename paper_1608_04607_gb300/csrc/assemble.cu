@@ -189,10 +189,25 @@ assemble_kernel(const PairConst* __restrict__ pairs, int64_t npairs, const doubl
           T av[TR], bv[TC];
           load_run<TR>(&S.zq[kk * LD + a0], av);
           load_run<TC>(&S.zp[kk * LD + b0], bv);
+          if constexpr (std::is_same<T, float>::value) {
+            // packed FP32 FMAs (two independent roundings, the same results
+            // as scalar FMAs) halve the instructions of the rank-1 update
 #pragma unroll
-          for (int r = 0; r < TR; ++r)
+            for (int r = 0; r < TR; ++r) {
+              const float2 a2 = make_float2(av[r], av[r]);
 #pragma unroll
-            for (int c = 0; c < TC; ++c) acc[r][c] = fma(av[r], bv[c], acc[r][c]);
+              for (int c = 0; c < TC; c += 2) {
+                const float2 p2 = __ffma2_rn(a2, make_float2(bv[c], bv[c + 1]), make_float2(acc[r][c], acc[r][c + 1]));
+                acc[r][c] = p2.x;
+                acc[r][c + 1] = p2.y;
+              }
+            }
+          } else {
+#pragma unroll
+            for (int r = 0; r < TR; ++r)
+#pragma unroll
+              for (int c = 0; c < TC; ++c) acc[r][c] = fma(av[r], bv[c], acc[r][c]);
+          }
         }
         __syncwarp();
       }

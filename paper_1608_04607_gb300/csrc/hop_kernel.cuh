@@ -26,6 +26,8 @@ constexpr int kHopStages = 4;
 constexpr int kHopConsumerWarps = 8;
 constexpr int kHopMaxRhs = 16;  // right-hand sides staged per pass
 constexpr int64_t kHopSmemBudget = 200 * 1024 - 1024;  // dynamic shared memory per block for the stages
+constexpr int64_t kHopTwoBlockBytes = 110 * 1024;       // stage bytes that still fit two blocks per SM
+constexpr int kHopRhsInner = 4;  // right-hand sides sharing each decoded chunk (multi-RHS launches)
 // operator bytes per hop kept in L2 for the next one (which sweeps the other way)
 constexpr int64_t kHopL2KeepBytes = 64ll << 20;
 
@@ -135,9 +137,9 @@ __host__ __device__ constexpr int64_t copy_row_bytes(int nb, int nbp) {
 // padded of type V (OUTP), or FP32 unpadded (NB per face row) times out_scale.
 // With V = __half each block's 8-value chunks are multiplied and summed in
 // packed FP16 (one rounding per fused multiply-add; 2 x NBP/8 products per
-// lane) and the three block sums are added in FP32.  RC: 1 for a single
-// right-hand side, else kHopMaxRhs; with FP16 vectors each decoded chunk of
-// B~ then serves every right-hand side of the launch (R <= RC).
+// lane) and the three block sums are added in FP32.  With FP16 vectors the
+// right-hand sides are taken RC at a time, each decoded chunk of B~ serving
+// all RC of them.
 template <int NB, typename E, typename V, bool OUTP, int RC>
 __global__ void __launch_bounds__(32 * (kHopConsumerWarps + 1))
 hop_kernel(const unsigned char* __restrict__ vals, const int32_t* __restrict__ recv, int64_t nrows,
@@ -252,6 +254,7 @@ hop_kernel(const unsigned char* __restrict__ vals, const int32_t* __restrict__ r
       const unsigned char* xbase = st + (int64_t)RPT * ROW_BYTES;
       const V* x0base = reinterpret_cast<const V*>(xbase + (int64_t)R * RPT * XBLK);
       if constexpr (VH) {
+       for (int q0 = 0; q0 < R; q0 += RC) {
         float sum[RC];
 #pragma unroll
         for (int q = 0; q < RC; ++q) sum[q] = 0.f;
@@ -269,9 +272,9 @@ hop_kernel(const unsigned char* __restrict__ vals, const int32_t* __restrict__ r
               decode8h<E>(bk + (c * NB + a) * 8 * EB, bh);
 #pragma unroll
               for (int q = 0; q < RC; ++q) {
-                if (RC == 1 || q < R) {
+                if (q0 + q < R) {
                   const __half* xl =
-                      reinterpret_cast<const __half*>(xbase + ((int64_t)q * RPT + r) * XBLK) + l * NBP + c * 8;
+                      reinterpret_cast<const __half*>(xbase + ((int64_t)(q0 + q) * RPT + r) * XBLK) + l * NBP + c * 8;
                   const uint4 xv = *reinterpret_cast<const uint4*>(xl);
                   __half2 xh[4];
                   memcpy(xh, &xv, 16);
@@ -291,15 +294,17 @@ hop_kernel(const unsigned char* __restrict__ vals, const int32_t* __restrict__ r
         }
 #pragma unroll
         for (int q = 0; q < RC; ++q) {
-          if (RC == 1 || q < R) {
-            const float out = a < NB ? (float)x0base[((int64_t)q * RPT + r) * NBP + a] + alpha * (scale * sum[q]) : 0.f;
-            const int64_t row = (int64_t)q * nrows + R0 + r;
+          if (q0 + q < R) {
+            const int qq = q0 + q;
+            const float out = a < NB ? (float)x0base[((int64_t)qq * RPT + r) * NBP + a] + alpha * (scale * sum[q]) : 0.f;
+            const int64_t row = (int64_t)qq * nrows + R0 + r;
             if constexpr (OUTP)
               reinterpret_cast<V*>(yv)[row * NBP + a] = (V)out;  // pads (a >= NB) written as 0
             else if (a < NB)
               reinterpret_cast<float*>(yv)[row * NB + a] = out * out_scale;
           }
         }
+       }
       } else {
         for (int rhs = 0; rhs < R; ++rhs) {
           const float* xs = reinterpret_cast<const float*>(xbase + ((int64_t)rhs * RPT + r) * XBLK);
@@ -349,7 +354,11 @@ int launch_hop(const dfm_op* op, const V* xp, const V* x0p, void* y, int R, floa
   const int64_t row_bytes = copy_row_bytes<E>(nb, nbp);
   const int64_t vb = (int64_t)sizeof(V);
   const int64_t stage_bytes = rpt * row_bytes + (int64_t)R * rpt * (4 * nbp * vb + nbp * vb);
-  const int stages = (int)std::min<int64_t>(kHopStages, kHopSmemBudget / stage_bytes);
+  // up to kHopStages stages, but no more than leave room for two blocks per
+  // SM when the tiles are large (45 functions, several right-hand sides)
+  int stages = (int)std::min<int64_t>(kHopStages, kHopSmemBudget / stage_bytes);
+  if (stages > 2 && stages * stage_bytes > kHopTwoBlockBytes)
+    stages = (int)std::max<int64_t>(2, kHopTwoBlockBytes / stage_bytes);
   if (stages < 2) return set_error(DFM_ERR_UNSUPPORTED, "preconditioner hop: a tile does not fit shared memory");
   const size_t smem = 128 + ((kHopStages * rpt * 4 + 127) / 128) * 128 + (size_t)stages * stage_bytes;
   int dev = 0, nsm = 0;
