@@ -445,17 +445,22 @@ int launch(const dfm_op* op, const TX* x, const TX* x0, TX* y, int R, double alp
       return DFM_OK;
     }
     int rpt = std::min(32, rows_per_tile_for(op->nb));
-    // x0 rides in the pipeline when every tile's slice is a whole number of 16-byte units
-    const int stage_x0 = (x0 && !(reinterpret_cast<uintptr_t>(x0) & 15) &&
-                          ((int64_t)op->nb * (int64_t)sizeof(TX)) % 16 == 0)
-                             ? 1
-                             : (x0 && !(reinterpret_cast<uintptr_t>(x0) & 15) &&
-                                (op->nrows % rpt) == 0 && ((int64_t)rpt * op->nb * (int64_t)sizeof(TX)) % 16 == 0)
-                                   ? 1
-                                   : 0;
-    const int64_t row_bytes = K * op->row_stride * (int64_t)sizeof(TV) +
-                              (int64_t)R * 4 * op->nb * (int64_t)sizeof(TX) +
-                              (stage_x0 ? (int64_t)R * op->nb * (int64_t)sizeof(TX) : 0);
+    // x0 rides in the pipeline when every tile's slice (rows R0 .. R0+rp of
+    // every right-hand side) starts on a 16-byte boundary, in global and in
+    // shared memory, for tiles of rp rows
+    const int64_t x0_row = op->nb * (int64_t)sizeof(TX);
+    auto x0_aligned = [&](int rp) -> int {
+      return (x0 && !(reinterpret_cast<uintptr_t>(x0) & 15) &&
+              (x0_row % 16 == 0 || ((op->nrows % rp) == 0 && (rp * x0_row) % 16 == 0)))
+                 ? 1
+                 : 0;
+    };
+    int stage_x0 = x0_aligned(rpt);
+    auto bytes_per_row = [&]() -> int64_t {
+      return K * op->row_stride * (int64_t)sizeof(TV) + (int64_t)R * 4 * op->nb * (int64_t)sizeof(TX) +
+             (stage_x0 ? (int64_t)R * x0_row : 0);
+    };
+    int64_t row_bytes = bytes_per_row();
     Combo cb{};
     cb.K = K;
     for (int k = 0; k < K; ++k) cb.vals[k] = combo_ops ? combo_ops[k]->vals : op->vals;
@@ -463,6 +468,10 @@ int launch(const dfm_op* op, const TX* x, const TX* x0, TX* y, int R, double alp
       for (int k = 0; k < K; ++k) cb.coef[r][k] = coef ? coef[(int64_t)r * K + k] : 1.0;
     const int64_t budget = 200 * 1024 - 1024;
     while (rpt > 1 && rpt * row_bytes * 2 > budget) --rpt;  // keep at least two stages
+    if (stage_x0 && !x0_aligned(rpt)) {  // the smaller tiles break the slice alignment: read x0 directly
+      stage_x0 = 0;
+      row_bytes = bytes_per_row();
+    }
     int stages = (int)std::min<int64_t>(kStages, budget / (rpt * row_bytes));
     if (stages < 1) return set_error(DFM_ERR_UNSUPPORTED, "dfm_apply: an operator row does not fit shared memory");
     const size_t smem = 128 + ((stages * rpt * 4 + 127) / 128) * 128 + (size_t)stages * (rpt * row_bytes + 16);

@@ -92,6 +92,30 @@ def test_apply_alternating_sweeps_bit_identical(D, oracle_mod, Np):
             assert np.abs(y[r] - yr).max() <= 2e-6 * np.abs(yr).max()
 
 
+@pytest.mark.parametrize("R", [8, 16])
+@pytest.mark.parametrize("xdt", ["f64", "f32"])
+def test_apply_many_rhs_with_x0(D, oracle_mod, R, xdt):
+    """Many right-hand sides with x0: the staged rows no longer fit eight per
+    tile (FP64 vectors), so tiles shrink to 7 or 5 rows and the x0 slices of
+    such tiles are read directly instead of by 16-byte bulk copies."""
+    import torch
+
+    m = kuhn_cube_mesh(3, jitter=0.2, seed=8)
+    Np = 4
+    mesh = D.Mesh(m.verts, m.tets, refl=0.9)
+    op = D.Operator(mesh, Np, mu=0.2, precision=1)
+    ref_op = _gpu_op_as_oracle(oracle_mod, op, mesh, m.n_tets, Np)
+    rng = np.random.default_rng(R)
+    dt = torch.float64 if xdt == "f64" else torch.float32
+    xt = torch.tensor(rng.standard_normal((R, 4 * m.n_tets, op.nb)), dtype=dt, device="cuda")
+    x0t = torch.tensor(rng.standard_normal((R, 4 * m.n_tets, op.nb)), dtype=dt, device="cuda")
+    y = op.apply(xt, x0=x0t, alpha=-0.7).cpu().numpy()
+    tol = 1e-12 if xdt == "f64" else 2e-6
+    for r in range(R):
+        yr = oracle_mod.apply(ref_op, xt[r].double().cpu().numpy(), x0=x0t[r].double().cpu().numpy(), alpha=-0.7)
+        assert np.abs(y[r] - yr).max() <= tol * np.abs(yr).max()
+
+
 def test_source_vector(D, oracle_mod):
     m = kuhn_cube_mesh(3, jitter=0.2, seed=8)
     mesh = D.Mesh(m.verts, m.tets)
