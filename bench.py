@@ -55,10 +55,10 @@ REF_APPLICATIONS = {"kuhn20_np4": 1809}
 FP32_LANES_PER_SM = 128
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # step's dominant kernel measured by ncu on this workload (mean of two
-# launches; profiles/hop_kuhn20_np4.md).  Keyed by the kernel instantiation and
+# launches; profiles/hop_e4m3_kuhn20_np4.md).  Keyed by the kernel instantiation and
 # workload; an entry is dropped whenever its kernel changes.
 PRECOND = {"f32": 0, "f16": 3, "bf16": 2, "fp8": 4}
-MEASURED_TRAFFIC = {}
+MEASURED_TRAFFIC = {("hop_kernel<15, __nv_fp8_e4m3>", "kuhn20_np4"): 159.2e6}
 HBM_PEAK_FALLBACK = 6800.0
 
 
