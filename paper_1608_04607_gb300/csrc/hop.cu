@@ -188,7 +188,8 @@ int hop_apply_t(const dfm_op* op, const V* xp, const V* x0p, void* y, int R, boo
   const int rpt = (32 * kHopConsumerWarps) / nbp;
   const int64_t row_bytes = op->lp_precision == DFM_FP8E4M3 ? copy_row_bytes<__nv_fp8_e4m3>(op->nb, nbp)
                                                             : copy_row_bytes<__half>(op->nb, nbp);
-  const int64_t per_rhs = (int64_t)rpt * 5 * nbp * (int64_t)sizeof(V);
+  const int64_t per_rhs =
+      (int64_t)rpt * (5 * nbp * (int64_t)sizeof(V) + (std::is_same<V, __half>::value && R > 1 ? 16 : 0));
   const int64_t fit = (kHopSmemBudget / 2 - rpt * row_bytes) / per_rhs;
   if (fit < 1) return set_error(DFM_ERR_UNSUPPORTED, "preconditioner hop: a tile does not fit shared memory");
   const int rchunk = (int)std::min<int64_t>(kHopMaxRhs, fit);

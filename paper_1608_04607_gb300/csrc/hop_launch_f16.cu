@@ -9,6 +9,9 @@ int hop_launch_f16(const dfm_op* op, const __half* xp, const __half* x0p, void* 
   if (R == 1)
     return outp ? launch_hop<__half, __half, true, 1>(op, xp, x0p, y, R, out_scale, st)
                 : launch_hop<__half, __half, false, 1>(op, xp, x0p, y, R, out_scale, st);
+  if (hop_uses_mma(op->nb, R))  // several right-hand sides on tensor cores
+    return outp ? launch_hop<__half, __half, true, 1, true>(op, xp, x0p, y, R, out_scale, st)
+                : launch_hop<__half, __half, false, 1, true>(op, xp, x0p, y, R, out_scale, st);
   return outp ? launch_hop<__half, __half, true, kHopRhsInner>(op, xp, x0p, y, R, out_scale, st)
               : launch_hop<__half, __half, false, kHopRhsInner>(op, xp, x0p, y, R, out_scale, st);
 }

@@ -8,7 +8,10 @@ evaluates the same sum in FP64 from the GPU's FP32 blocks rounded the same way
 on the host, so the only difference left is the kernels' arithmetic (see
 TOL).  The mesh drops one tet of the Kuhn cube (161 tets), so the last tile
 of rows is ragged for every basis size; N_p = 2, 4, 5 give 6, 15, 21
-functions (padded widths 8, 16, 24: 16, 8 and 5 rows per tile)."""
+functions, N_p = 3 and 8 give 10 and 45 (padded widths 8, 16, 24, 16, 48).
+With several right-hand sides and a padded width that is a multiple of 16
+(N_p = 3, 4, 8 with the FP16 and e4m3 copies) the hops run on tensor cores;
+R = 9 fills one 8-right-hand-side tile and part of a second."""
 import numpy as np
 import pytest
 
@@ -77,9 +80,9 @@ def mesh161():
     return m.verts, np.ascontiguousarray(m.tets[:-1])
 
 
-@pytest.mark.parametrize("Np", [2, 4, 5])
+@pytest.mark.parametrize("Np,R", [(2, 3), (3, 3), (4, 3), (4, 9), (5, 3), (8, 5)])
 @pytest.mark.parametrize("prec", ["f16", "bf16", "e4m3"])
-def test_precond_matches_oracle_on_rounded_blocks(D, oracle_mod, mesh161, Np, prec):
+def test_precond_matches_oracle_on_rounded_blocks(D, oracle_mod, mesh161, Np, R, prec):
     import torch
 
     verts, tets = mesh161
@@ -96,7 +99,6 @@ def test_precond_matches_oracle_on_rounded_blocks(D, oracle_mod, mesh161, Np, pr
     dest = mesh.recv()[4 * t + fp].reshape(4 * nt, 3).astype(np.int64)
     ref_op = oracle_mod.Operator(Np=Np, blocks=np.ascontiguousarray(blocks), dest=dest)
     rng = np.random.default_rng(Np)
-    R = 3
     x = rng.standard_normal((R, 4 * nt, op.nb)).astype(np.float32)
     xt = torch.tensor(x, device="cuda")
     for d in (1, 2, 5):
