@@ -60,6 +60,10 @@ FP32_LANES_PER_SM = 128
 PRECOND = {"f32": 0, "f16": 3, "bf16": 2, "fp8": 4}
 MEASURED_TRAFFIC = {("hop_kernel<15, __nv_fp8_e4m3>", "kuhn20_np4"): 159.2e6}
 HBM_PEAK_FALLBACK = 6800.0
+# the timed region records CUDA events around every STATS_EVERY-th launch of
+# each kernel (per-kernel durations); an event pair per launch would add ~9%
+# to the step
+STATS_EVERY = 16
 
 
 def _peaks():
@@ -256,7 +260,7 @@ def run_gpu(args):
     # ---- timed region: device-resident steps --------------------------------
     sampler = ClockSampler(local)
     dfm.stats_reset()
-    dfm.stats_enable(True)
+    dfm.stats_enable(STATS_EVERY)
     l0 = dfm.launch_count()
     if ws > 1:
         dist.barrier()

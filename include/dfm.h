@@ -292,11 +292,17 @@ int dfm_adjoint(const dfm_op* op, const dfm_params* params, const double* rho, i
 /* Kernel accounting, for benchmarks and profiling.
  *   dfm_launch_count: number of CUDA kernels this library has launched in the
  *     process so far (all kernels, all streams).
- *   dfm_stats_enable(1): from now on record a CUDA event pair around every
- *     launch of the kernels below, on the stream each runs on;
- *   dfm_stats_reset: forget the recorded pairs (the event pool is reused);
- *   dfm_kernel_stats: launches and summed device milliseconds of one kernel
- *     since the last reset (waits for the recorded events). */
+ *   dfm_stats_enable(n): from now on record a CUDA event pair, on the stream
+ *     the kernel runs on, around every launch (n = 1) or every n-th launch
+ *     (n > 1, per kernel) of the kernels below; 0 stops.  Event records cost
+ *     GPU time between kernels, so sampling keeps the measured region close
+ *     to an uninstrumented run;
+ *   dfm_stats_reset: forget the recorded pairs and counts (events are reused);
+ *   dfm_kernel_stats: launches of one kernel since the last reset (all of
+ *     them while enabled) and their device milliseconds: the sum over the
+ *     timed launches scaled by launches / timed launches (waits for the
+ *     recorded events). */
+#define DFM_KERNEL_COUNT 8
 #define DFM_KERNEL_ASSEMBLE 0 /* operator assembly (one warp per face pair) */
 #define DFM_KERNEL_SPMV 1     /* y = x0 + alpha B x */
 #define DFM_KERNEL_SPMV_T 2   /* y = x0 + alpha B^T x */
@@ -304,7 +310,7 @@ int dfm_adjoint(const dfm_op* op, const dfm_params* params, const double* rho, i
 #define DFM_KERNEL_AXPY 4     /* Krylov multi-axpy */
 #define DFM_KERNEL_SPMV64 5   /* y = x0 + alpha B x with FP64 vectors (residuals) */
 #define DFM_KERNEL_CONTRACT 6 /* fused lambda^T (dB/dmu) rho per tet */
-#define DFM_KERNEL_SPMV16 7   /* y = x0 + alpha B x on the 16-bit preconditioner copy */
+#define DFM_KERNEL_SPMV16 7   /* preconditioner hop on the low-precision copy */
 long long dfm_launch_count(void);
 int dfm_stats_enable(int on);
 int dfm_stats_reset(void);

@@ -1,9 +1,10 @@
 // Launch counting and optional per-kernel CUDA-event timing.
 //
 // The benchmark reports the device time of the dominant kernels measured on
-// the stream they run on; when timing is enabled every timed launch site
-// records an event pair around its kernel.  Events come from a pool that is
-// reused after dfm_stats_reset, so steady-state timing allocates nothing.
+// the stream they run on; when timing is enabled a timed launch site records
+// an event pair around its kernel, at every launch or every n-th launch of
+// that kernel.  Events come from a pool that is reused after dfm_stats_reset,
+// so steady-state timing allocates nothing.
 #include <atomic>
 #include <mutex>
 #include <vector>
@@ -13,8 +14,9 @@
 namespace dfm {
 namespace {
 std::atomic<long long> g_launches{0};
-std::atomic<int> g_timing{0};
+std::atomic<int> g_timing{0};  // 0: off, n >= 1: every n-th launch of a kernel
 std::mutex g_mu;
+long long g_count[DFM_KERNEL_COUNT] = {};  // launches per kernel while timing was on
 struct Rec {
   int kernel;
   int e0, e1;
@@ -36,8 +38,10 @@ int take_event() {
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 KernelTimer::KernelTimer(int kernel, cudaStream_t st) : kernel_(kernel), st_(st), e0_(-1) {
-  if (!g_timing.load(std::memory_order_relaxed)) return;
+  const int every = g_timing.load(std::memory_order_relaxed);
+  if (!every || kernel < 0 || kernel >= DFM_KERNEL_COUNT) return;
   std::lock_guard<std::mutex> lk(g_mu);
+  if (g_count[kernel]++ % every != 0) return;
   e0_ = take_event();
   if (e0_ >= 0) cudaEventRecord(g_pool[e0_], st_);
 }
@@ -58,7 +62,8 @@ using namespace dfm;
 extern "C" long long dfm_launch_count(void) { return g_launches.load(); }
 
 extern "C" int dfm_stats_enable(int on) {
-  g_timing.store(on ? 1 : 0);
+  if (on < 0) return set_error(DFM_ERR_ARG, "dfm_stats_enable: negative sampling interval");
+  g_timing.store(on);
   return DFM_OK;
 }
 
@@ -66,6 +71,7 @@ extern "C" int dfm_stats_reset(void) {
   std::lock_guard<std::mutex> lk(g_mu);
   g_recs.clear();
   g_next = 0;
+  for (long long& c : g_count) c = 0;
   return DFM_OK;
 }
 
@@ -84,7 +90,8 @@ extern "C" int dfm_kernel_stats(int kernel, int64_t* launches, double* total_ms)
     ms += t;
     ++n;
   }
-  *launches = n;
-  *total_ms = ms;
+  const int64_t all = (kernel >= 0 && kernel < DFM_KERNEL_COUNT) ? g_count[kernel] : n;
+  *launches = all;
+  *total_ms = n ? ms * (double)all / (double)n : 0.0;
   return DFM_OK;
 }

@@ -454,8 +454,10 @@ def launch_count() -> int:
     return int(load().dfm_launch_count())
 
 
-def stats_enable(on: bool = True):
-    _check(load().dfm_stats_enable(int(bool(on))), "dfm_stats_enable")
+def stats_enable(on=True):
+    """True or 1: time every launch of the timed kernels; n > 1: every n-th
+    launch of each kernel; False or 0: stop (dfm_stats_enable)."""
+    _check(load().dfm_stats_enable(int(on)), "dfm_stats_enable")
 
 
 def stats_reset():

@@ -277,3 +277,23 @@ def test_flexible_gmres_with_16bit_preconditioner(D, oracle_mod, prec, R):
     M2 = np.eye(same2.nrows * same2.nb) - oracle_mod.dense(same2)
     ref2 = np.linalg.solve(M2, b[0].ravel())
     assert np.linalg.norm(x2[0].cpu().numpy().ravel() - ref2) <= 1e-8 * np.linalg.norm(ref2)
+
+
+def test_sampled_kernel_timing_counts_every_launch(D):
+    """dfm_stats_enable(n) times every n-th launch of a kernel but reports all
+    launches and scales the summed time to them."""
+    import torch
+
+    m = kuhn_cube_mesh(3, jitter=0.2, seed=8)
+    mesh = D.Mesh(m.verts, m.tets, refl=0.9)
+    op = D.Operator(mesh, 4, mu=0.2, precision=1)
+    x = torch.randn((mesh.n_rows, op.nb), device="cuda", dtype=torch.float32)
+    for every in (1, 4):
+        D.stats_reset()
+        D.stats_enable(every)
+        for _ in range(10):
+            op.apply(x, x0=x, alpha=-1.0)
+        D.stats_enable(False)
+        n, ms = D.kernel_stats(D.KERNEL_SPMV)
+        assert n == 10 and ms > 0
+    D.stats_reset()
