@@ -742,7 +742,9 @@ def run_adjoint(args):
     (384,000 tets, Np = 3).  Times forward assembly + solve, the receiver
     functional and the adjoint (transposed solve + fused dB/dmu contraction);
     optionally checks the gradient against central differences of the GPU
-    forward solve on the sampled elements (step 1e-4)."""
+    forward solve on the sampled elements (step 1e-4).  The forward solve's
+    preconditioner hops use the --precond copy; the transposed (adjoint) solve
+    applies the FP32 operator."""
     import torch
 
     from paper_1608_04607_gb300 import dfm
@@ -770,7 +772,7 @@ def run_adjoint(args):
                                  restart=args.restart or 256)
         else:
             rho, info = op.solve(rho0, method=dfm.GMRES_IR, tol=tol, poly_degree=args.poly or 32,
-                                 restart=args.restart or 256)
+                                 restart=args.restart or 256, precond_precision=PRECOND[args.precond])
         g, dg = dfm.interior_density(mesh, Np, receiver, weights=1.0 / len(receiver), mu=mu_vec)
         return op, rho, g, dg, info
 

@@ -185,7 +185,8 @@ int hop_apply_t(const dfm_op* op, const V* xp, const V* x0p, void* y, int R, boo
   // right-hand sides per launch: at most kHopMaxRhs, and few enough that two
   // stages fit in shared memory (large bases with many right-hand sides)
   const int nbp = hop_nbp(op->nb);
-  const int rpt = (32 * kHopConsumerWarps) / nbp;
+  const int rpt = op->lp_precision == DFM_FP8E4M3 ? hop_tile_rows<__nv_fp8_e4m3>(op->nb)
+                                                  : hop_tile_rows<__half>(op->nb);
   const int64_t row_bytes = op->lp_precision == DFM_FP8E4M3 ? copy_row_bytes<__nv_fp8_e4m3>(op->nb, nbp)
                                                             : copy_row_bytes<__half>(op->nb, nbp);
   const int64_t per_rhs =

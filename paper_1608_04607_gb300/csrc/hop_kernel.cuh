@@ -22,12 +22,13 @@ namespace hopk {
 
 using namespace pipe;
 
-constexpr int kHopStages = 3;  // 3 stages leave room for 5 blocks per SM at N_b = 15 (9% faster than 4)
+constexpr int kHopStages = 2;  // with 32-row tiles: 29.5 us per e4m3 hop (3 stages: 30.8, 4: 30.9)
 constexpr int kHopConsumerWarps = 8;
 constexpr int kHopMaxRhs = 16;  // right-hand sides staged per pass
 constexpr int64_t kHopSmemBudget = 200 * 1024 - 1024;  // dynamic shared memory per block for the stages
 constexpr int64_t kHopTwoBlockBytes = 110 * 1024;       // stage bytes that still fit two blocks per SM
 constexpr int kHopRhsInner = 4;  // right-hand sides sharing each decoded chunk (multi-RHS launches)
+constexpr int64_t kHopTileBytes = 48 * 1024;  // copy bytes of a tile for two consumer passes
 // operator bytes per hop kept in L2 for the next one (which sweeps the other way)
 constexpr int64_t kHopL2KeepBytes = 64ll << 20;
 
@@ -132,6 +133,19 @@ __host__ __device__ constexpr int64_t copy_row_bytes(int nb, int nbp) {
   return copy_body_bytes<E>(nb, nbp) + (Codec<E>::kScaled ? 16 : 0);
 }
 
+// Rows per tile: two consumer passes of (32 x consumer warps) / NBP rows (at
+// most 32, one per producer lane) when the tile's copy rows stay within
+// kHopTileBytes, else one pass.  Larger tiles amortise the per-tile barrier
+// round trip and copy issue over more bytes (e4m3 hop at N_b = 15: 33.1 ->
+// 30.8 us).
+template <typename E>
+__host__ __device__ constexpr int hop_tile_rows(int nb) {
+  const int nbp = (nb + 7) / 8 * 8;
+  const int step = (32 * kHopConsumerWarps) / nbp;
+  const int two = step * 2 < 32 ? step * 2 : 32;
+  return two * copy_row_bytes<E>(nb, nbp) <= kHopTileBytes ? two : step;
+}
+
 // y = x0 + alpha B~ x for R right-hand sides; x, x0 of type V (float, or
 // __half holding a scaled copy of the vector) padded to NBP per face row; y
 // padded of type V (OUTP), or FP32 unpadded (NB per face row) times out_scale.
@@ -183,7 +197,8 @@ hop_kernel(const unsigned char* __restrict__ vals, const int32_t* __restrict__ r
            float out_scale, int stages, int reverse, int64_t keep_from, int* __restrict__ err) {
   constexpr int NBP = (NB + 7) / 8 * 8;
   constexpr int NC = NBP / 8;
-  constexpr int RPT = (32 * kHopConsumerWarps) / NBP;  // rows per tile
+  constexpr int RSTEP = (32 * kHopConsumerWarps) / NBP;  // rows of one consumer pass
+  constexpr int RPT = hop_tile_rows<E>(NB);              // rows per tile (one or two passes)
   constexpr int EB = Codec<E>::kEB;
   constexpr unsigned ROW_BYTES = (unsigned)copy_row_bytes<E>(NB, NBP);
   constexpr unsigned BODY_BYTES = (unsigned)copy_body_bytes<E>(NB, NBP);
@@ -340,8 +355,8 @@ hop_kernel(const unsigned char* __restrict__ vals, const int32_t* __restrict__ r
   }
   // ---------------- consumers: thread (r, a), a < NBP ----------------
   const int ctid = threadIdx.x - 32;
-  const int r = ctid / NBP;
-  const int a = ctid - r * NBP;
+  const int r0c = ctid / NBP;
+  const int a = ctid - r0c * NBP;
   for (int64_t i = 0; i < mine; ++i) {
     const int s = (int)(i % stages);
     const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&full[s], (unsigned)((i / stages) & 1)));
@@ -352,7 +367,7 @@ hop_kernel(const unsigned char* __restrict__ vals, const int32_t* __restrict__ r
     const unsigned char* st = stage0 + s * stage_bytes;
     const int64_t R0 = tile_first_row(i);
     const int nr = (int)std::min<int64_t>(RPT, nrows - R0);
-    if (r < nr) {
+    for (int r = r0c; r0c < RSTEP && r < nr; r += RSTEP) {
       const int lp = s_recv[s * RPT + r] & 3;
       const unsigned char* brow = st + r * ROW_BYTES;
       float scale = 1.f;
@@ -456,7 +471,7 @@ template <typename E, typename V, bool OUTP, int RC, bool MMA = false>
 int launch_hop(const dfm_op* op, const V* xp, const V* x0p, void* y, int R, float out_scale, cudaStream_t st) {
   const int nb = op->nb;
   const int nbp = hop_nbp(nb);
-  const int rpt = (32 * kHopConsumerWarps) / nbp;
+  const int rpt = hop_tile_rows<E>(nb);
   const int64_t row_bytes = copy_row_bytes<E>(nb, nbp);
   const int64_t vb = (int64_t)sizeof(V);
   const int64_t stage_bytes = rpt * row_bytes + (int64_t)R * rpt * (4 * nbp * vb + (MMA ? 16 : 0) + nbp * vb);
