@@ -7,6 +7,7 @@
 #include <string>
 
 #include "dfm.h"
+#include "launch_geometry.h"
 
 namespace dfm {
 
@@ -82,7 +83,7 @@ class KernelTimer {
 #define DFM_LAUNCHED() ::dfm::count_launch()
 
 // row stride (elements) of the block storage: 3 nb^2 rounded up to 8 elements
-inline int64_t op_row_stride(int nb) { return ((3 * (int64_t)nb * nb + 7) / 8) * 8; }
+inline int64_t op_row_stride(int nb) { return geom::op_row_stride(nb); }
 inline int elem_size(int precision) { return precision == DFM_F64 ? 8 : (precision == DFM_F32 ? 4 : 2); }
 
 // implemented in spmv.cu
@@ -99,7 +100,7 @@ int next_sweep_direction(const void* vals);
 void forget_sweep(const void* vals);
 // Polynomial-preconditioner hops on a 16-bit copy of the blocks (hop.cu).
 // Padded width of a face's coefficients in hop vectors and in the copy.
-inline int hop_nbp(int nb) { return (nb + 7) / 8 * 8; }
+inline int hop_nbp(int nb) { return geom::hop_nbp(nb); }
 // (re)builds op->lp_vals (precision DFM_F16, DFM_BF16 or DFM_FP8E4M3) from the FP32 blocks
 int prepare_lowp(const dfm_op* op, int precision, cudaStream_t st);
 // z = sum_{k<d} B~^k v for R vectors ([R][rows][nb] FP32) by Horner on the

@@ -184,16 +184,10 @@ int hop_apply_t(const dfm_op* op, const V* xp, const V* x0p, void* y, int R, boo
   const int64_t ybytes = out_padded ? (int64_t)sizeof(V) : 4;
   // right-hand sides per launch: at most kHopMaxRhs, and few enough that two
   // stages fit in shared memory (large bases with many right-hand sides)
-  const int nbp = hop_nbp(op->nb);
-  const int rpt = op->lp_precision == DFM_FP8E4M3 ? hop_tile_rows<__nv_fp8_e4m3>(op->nb)
-                                                  : hop_tile_rows<__half>(op->nb);
-  const int64_t row_bytes = op->lp_precision == DFM_FP8E4M3 ? copy_row_bytes<__nv_fp8_e4m3>(op->nb, nbp)
-                                                            : copy_row_bytes<__half>(op->nb, nbp);
-  const int64_t per_rhs =
-      (int64_t)rpt * (5 * nbp * (int64_t)sizeof(V) + (std::is_same<V, __half>::value && R > 1 ? 16 : 0));
-  const int64_t fit = (kHopSmemBudget / 2 - rpt * row_bytes) / per_rhs;
-  if (fit < 1) return set_error(DFM_ERR_UNSUPPORTED, "preconditioner hop: a tile does not fit shared memory");
-  const int rchunk = (int)std::min<int64_t>(kHopMaxRhs, fit);
+  const bool fp8 = op->lp_precision == DFM_FP8E4M3;
+  const int rchunk = geom::hop_rhs_chunk(op->nb, fp8 ? 1 : 2, fp8, (int)sizeof(V),
+                                         std::is_same<V, __half>::value && R > 1);
+  if (rchunk < 1) return set_error(DFM_ERR_UNSUPPORTED, "preconditioner hop: a tile does not fit shared memory");
   for (int r0 = 0; r0 < R; r0 += rchunk) {
     const int Rp = std::min(rchunk, R - r0);
     const V* x = xp + r0 * stride_p;

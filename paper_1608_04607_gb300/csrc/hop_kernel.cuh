@@ -23,12 +23,10 @@ namespace hopk {
 using namespace pipe;
 
 constexpr int kHopStages = 2;  // with 32-row tiles: 29.5 us per e4m3 hop (3 stages: 30.8, 4: 30.9)
-constexpr int kHopConsumerWarps = 8;
-constexpr int kHopMaxRhs = 16;  // right-hand sides staged per pass
-constexpr int64_t kHopSmemBudget = 200 * 1024 - 1024;  // dynamic shared memory per block for the stages
-constexpr int64_t kHopTwoBlockBytes = 110 * 1024;       // stage bytes that still fit two blocks per SM
+// tile and stage geometry: launch_geometry.h (shared with the host-side check)
+using geom::kHopConsumerWarps;
+using geom::kHopMaxRhs;
 constexpr int kHopRhsInner = 4;  // right-hand sides sharing each decoded chunk (multi-RHS launches)
-constexpr int64_t kHopTileBytes = 48 * 1024;  // copy bytes of a tile for two consumer passes
 // operator bytes per hop kept in L2 for the next one (which sweeps the other way)
 constexpr int64_t kHopL2KeepBytes = 64ll << 20;
 
@@ -126,24 +124,17 @@ struct Codec<__nv_fp8_e4m3> {
 // for scaled formats, a 16-byte field whose first 4 bytes hold s_R
 template <typename E>
 __host__ __device__ constexpr int64_t copy_body_bytes(int nb, int nbp) {
-  return (3 * (int64_t)nb * nbp * Codec<E>::kEB + 15) / 16 * 16;
+  return geom::hop_body_bytes(nb, Codec<E>::kEB);
 }
 template <typename E>
 __host__ __device__ constexpr int64_t copy_row_bytes(int nb, int nbp) {
   return copy_body_bytes<E>(nb, nbp) + (Codec<E>::kScaled ? 16 : 0);
 }
 
-// Rows per tile: two consumer passes of (32 x consumer warps) / NBP rows (at
-// most 32, one per producer lane) when the tile's copy rows stay within
-// kHopTileBytes, else one pass.  Larger tiles amortise the per-tile barrier
-// round trip and copy issue over more bytes (e4m3 hop at N_b = 15: 33.1 ->
-// 30.8 us).
+// rows per tile (one or two consumer passes), see geom::hop_tile_rows
 template <typename E>
 __host__ __device__ constexpr int hop_tile_rows(int nb) {
-  const int nbp = (nb + 7) / 8 * 8;
-  const int step = (32 * kHopConsumerWarps) / nbp;
-  const int two = step * 2 < 32 ? step * 2 : 32;
-  return two * copy_row_bytes<E>(nb, nbp) <= kHopTileBytes ? two : step;
+  return geom::hop_tile_rows(nb, Codec<E>::kEB, Codec<E>::kScaled);
 }
 
 // y = x0 + alpha B~ x for R right-hand sides; x, x0 of type V (float, or
@@ -473,13 +464,8 @@ int launch_hop(const dfm_op* op, const V* xp, const V* x0p, void* y, int R, floa
   const int nbp = hop_nbp(nb);
   const int rpt = hop_tile_rows<E>(nb);
   const int64_t row_bytes = copy_row_bytes<E>(nb, nbp);
-  const int64_t vb = (int64_t)sizeof(V);
-  const int64_t stage_bytes = rpt * row_bytes + (int64_t)R * rpt * (4 * nbp * vb + (MMA ? 16 : 0) + nbp * vb);
-  // up to kHopStages stages, but no more than leave room for two blocks per
-  // SM when the tiles are large (45 functions, several right-hand sides)
-  int stages = (int)std::min<int64_t>(kHopStages, kHopSmemBudget / stage_bytes);
-  if (stages > 2 && stages * stage_bytes > kHopTwoBlockBytes)
-    stages = (int)std::max<int64_t>(2, kHopTwoBlockBytes / stage_bytes);
+  const int64_t stage_bytes = geom::hop_stage_bytes(nb, Codec<E>::kEB, Codec<E>::kScaled, (int)sizeof(V), R, MMA);
+  const int stages = geom::hop_stages(stage_bytes, kHopStages);
   if (stages < 2) return set_error(DFM_ERR_UNSUPPORTED, "preconditioner hop: a tile does not fit shared memory");
   const size_t smem = 128 + ((kHopStages * rpt * 4 + 127) / 128) * 128 + (size_t)stages * stage_bytes;
   int dev = 0, nsm = 0;

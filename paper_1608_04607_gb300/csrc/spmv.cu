@@ -417,12 +417,6 @@ namespace {
 // L2; the rest holds the vectors and the row map).
 constexpr int64_t kL2KeepBytes = 64ll << 20;
 
-int rows_per_tile_for(int nb) {
-  int r = kThreads / nb;
-  if (r < 1) r = 1;
-  return r;
-}
-
 template <typename TV, typename TX, typename TA>
 int launch(const dfm_op* op, const TX* x, const TX* x0, TX* y, int R, double alpha, int trans, cudaStream_t st,
            const dfm_op* const* combo_ops = nullptr, int K = 1, const double* coef = nullptr) {
@@ -444,35 +438,15 @@ int launch(const dfm_op* op, const TX* x, const TX* x0, TX* y, int R, double alp
       }
       return DFM_OK;
     }
-    int rpt = std::min(32, rows_per_tile_for(op->nb));
-    // x0 rides in the pipeline when every tile's slice (rows R0 .. R0+rp of
-    // every right-hand side) starts on a 16-byte boundary, in global and in
-    // shared memory, for tiles of rp rows
-    const int64_t x0_row = op->nb * (int64_t)sizeof(TX);
-    auto x0_aligned = [&](int rp) -> int {
-      return (x0 && !(reinterpret_cast<uintptr_t>(x0) & 15) &&
-              (x0_row % 16 == 0 || ((op->nrows % rp) == 0 && (rp * x0_row) % 16 == 0)))
-                 ? 1
-                 : 0;
-    };
-    int stage_x0 = x0_aligned(rpt);
-    auto bytes_per_row = [&]() -> int64_t {
-      return K * op->row_stride * (int64_t)sizeof(TV) + (int64_t)R * 4 * op->nb * (int64_t)sizeof(TX) +
-             (stage_x0 ? (int64_t)R * x0_row : 0);
-    };
-    int64_t row_bytes = bytes_per_row();
+    const geom::Fwd g = geom::fwd_geometry(op->nb, (int)sizeof(TV), (int)sizeof(TX), K, R, op->nrows,
+                                           x0 && !(reinterpret_cast<uintptr_t>(x0) & 15), kStages);
+    const int rpt = g.rpt, stage_x0 = g.stage_x0, stages = g.stages;
+    const int64_t row_bytes = g.row_bytes;
     Combo cb{};
     cb.K = K;
     for (int k = 0; k < K; ++k) cb.vals[k] = combo_ops ? combo_ops[k]->vals : op->vals;
     for (int r = 0; r < R; ++r)
       for (int k = 0; k < K; ++k) cb.coef[r][k] = coef ? coef[(int64_t)r * K + k] : 1.0;
-    const int64_t budget = 200 * 1024 - 1024;
-    while (rpt > 1 && rpt * row_bytes * 2 > budget) --rpt;  // keep at least two stages
-    if (stage_x0 && !x0_aligned(rpt)) {  // the smaller tiles break the slice alignment: read x0 directly
-      stage_x0 = 0;
-      row_bytes = bytes_per_row();
-    }
-    int stages = (int)std::min<int64_t>(kStages, budget / (rpt * row_bytes));
     if (stages < 1) return set_error(DFM_ERR_UNSUPPORTED, "dfm_apply: an operator row does not fit shared memory");
     const size_t smem = 128 + ((stages * rpt * 4 + 127) / 128) * 128 + (size_t)stages * (rpt * row_bytes + 16);
     int rc = DFM_OK;

@@ -1,0 +1,97 @@
+// Host-side check of the launch geometry of the pipelined operator
+// applications (launch_geometry.h): for every basis size, precision, number of
+// combined operators (up to 4, FP32 only) and right-hand sides and a set of
+// row counts, every bulk
+// copy starts and ends on a 16-byte boundary, shared memory stays within a
+// block's 227 KB, a tile has at most 32 rows and at least the required stages.
+// Built and run by tests/test_launch_geometry.py; prints "ok" or the first
+// violation and exits non-zero.
+#include <cstdio>
+#include <initializer_list>
+
+#include "launch_geometry.h"
+
+using namespace dfm::geom;
+
+static int fail(const char* what, int nb, int a, int b, int c, long long d) {
+  std::printf("violation: %s (nb=%d, %d, %d, %d, %lld)\n", what, nb, a, b, c, d);
+  return 1;
+}
+
+int main() {
+  const int nbs[] = {1, 3, 6, 10, 15, 21, 28, 36, 45};
+  const long long rows[] = {4, 24, 28, 644, 648, 4 * 6001, 192000, 648000, 786432};
+  const long long kSmem = 227 * 1024;
+  long long checked = 0;
+  // forward application: block bytes tv, vector bytes tx, K operators, R right-hand sides
+  for (int nb : nbs)
+    for (int tv : {2, 4, 8})
+      for (int tx : {4, 8})
+        for (int K = 1; K <= (tv == 4 ? 4 : 1); ++K)  // combined operators are FP32
+          for (int R = 1; R <= 16; ++R)
+            for (long long nrows : rows)
+              for (int x0a = 0; x0a < 2; ++x0a) {
+                const Fwd g = fwd_geometry(nb, tv, tx, K, R, nrows, x0a != 0, 4);
+                if (g.rpt < 1 || g.rpt > 32) return fail("rows per tile", nb, tv, tx, R, g.rpt);
+                if (g.stages < 1) return fail("no stage fits", nb, tv, tx, R, g.row_bytes);
+                const long long stride = op_row_stride(nb) * tv;
+                if (stride % 16) return fail("row stride", nb, tv, tx, R, stride);
+                const long long xblk = 4LL * nb * tx;
+                if (xblk % 16) return fail("x block", nb, tv, tx, R, xblk);
+                const long long x0row = (long long)nb * tx;
+                const long long x0b = g.stage_x0 ? (long long)R * g.rpt * x0row : 0;
+                const long long stage = K * g.rpt * stride + (long long)R * g.rpt * xblk + (x0b + 15) / 16 * 16;
+                const long long smem = 128 + ((long long)g.stages * g.rpt * 4 + 127) / 128 * 128 +
+                                       (long long)g.stages * (g.rpt * g.row_bytes + 16);
+                if (smem > kSmem) return fail("shared memory", nb, tv, tx, R, smem);
+                if (stage % 16 || stage > g.rpt * g.row_bytes + 16) return fail("stage size", nb, tv, tx, R, stage);
+                if (g.stage_x0) {
+                  if (!x0a) return fail("x0 staged without an aligned pointer", nb, tv, tx, R, 0);
+                  const long long ntiles = (nrows + g.rpt - 1) / g.rpt;
+                  for (long long ti = 0; ti < ntiles; ti = (ti == 4096 && ntiles > 4097) ? ntiles - 1 : ti + 1) {
+                    const long long R0 = ti * g.rpt;  // the first 4097 tiles and the last (ragged) one
+                    const long long nr = nrows - R0 < g.rpt ? nrows - R0 : g.rpt;
+                    for (int rhs = 0; rhs < R; ++rhs) {
+                      ++checked;
+                      if (((rhs * nrows + R0) * x0row) % 16) return fail("x0 source", nb, tv, tx, R, R0);
+                      if ((nr * x0row) % 16) return fail("x0 size", nb, tv, tx, R, R0);
+                      const long long dst = K * g.rpt * stride + (long long)R * g.rpt * xblk + rhs * g.rpt * x0row;
+                      if (dst % 16) return fail("x0 destination", nb, tv, tx, R, R0);
+                    }
+                  }
+                }
+              }
+  // preconditioner hops: copy bytes per value eb (FP16/BF16: 2, e4m3: 1 with a
+  // row scale), vector bytes vb (FP16: 2, FP32: 4), tensor-core layout mma
+  struct Fmt {
+    int eb;
+    bool scaled;
+    int vb;
+  };
+  const Fmt fmts[] = {{2, false, 2}, {2, false, 4}, {1, true, 2}};
+  for (int nb : nbs)
+    for (const Fmt& f : fmts)
+      for (int mma = 0; mma < 2; ++mma) {
+        if (mma && (f.vb != 2 || hop_nbp(nb) % 16)) continue;
+        const int rpt = hop_tile_rows(nb, f.eb, f.scaled);
+        const int step = (32 * kHopConsumerWarps) / hop_nbp(nb);
+        if (rpt < 1 || rpt > 32 || (rpt != step && rpt != 2 * step)) return fail("hop rows per tile", nb, f.eb, f.vb, mma, rpt);
+        const long long row = hop_row_bytes(nb, f.eb, f.scaled);
+        if (row % 16) return fail("hop copy row", nb, f.eb, f.vb, mma, row);
+        const long long xblk = 4LL * hop_nbp(nb) * f.vb + (mma ? 16 : 0), x0row = (long long)hop_nbp(nb) * f.vb;
+        if (xblk % 16 || x0row % 16) return fail("hop vector rows", nb, f.eb, f.vb, mma, xblk);
+        const int chunk = hop_rhs_chunk(nb, f.eb, f.scaled, f.vb, mma != 0);
+        if (chunk < 1) return fail("hop right-hand-side chunk", nb, f.eb, f.vb, mma, chunk);
+        for (int R = 1; R <= chunk; ++R) {
+          ++checked;
+          const long long stage = hop_stage_bytes(nb, f.eb, f.scaled, f.vb, R, mma != 0);
+          if (stage != rpt * row + (long long)R * rpt * (xblk + x0row)) return fail("hop stage bytes", nb, f.eb, f.vb, R, stage);
+          const int stages = hop_stages(stage, 2);
+          if (stages < 2) return fail("hop stages", nb, f.eb, f.vb, R, stage);
+          const long long smem = 128 + (2LL * rpt * 4 + 127) / 128 * 128 + (long long)stages * stage;
+          if (smem > kSmem) return fail("hop shared memory", nb, f.eb, f.vb, R, smem);
+        }
+      }
+  std::printf("ok %lld\n", checked);
+  return 0;
+}
