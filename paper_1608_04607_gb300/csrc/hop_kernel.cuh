@@ -132,9 +132,9 @@ __host__ __device__ constexpr int64_t copy_row_bytes(int nb, int nbp) {
 }
 
 // rows per tile (one or two consumer passes), see geom::hop_tile_rows
-template <typename E>
+template <typename E, bool MMA>
 __host__ __device__ constexpr int hop_tile_rows(int nb) {
-  return geom::hop_tile_rows(nb, Codec<E>::kEB, Codec<E>::kScaled);
+  return geom::hop_tile_rows(nb, Codec<E>::kEB, Codec<E>::kScaled, MMA);
 }
 
 // y = x0 + alpha B~ x for R right-hand sides; x, x0 of type V (float, or
@@ -189,7 +189,7 @@ hop_kernel(const unsigned char* __restrict__ vals, const int32_t* __restrict__ r
   constexpr int NBP = (NB + 7) / 8 * 8;
   constexpr int NC = NBP / 8;
   constexpr int RSTEP = (32 * kHopConsumerWarps) / NBP;  // rows of one consumer pass
-  constexpr int RPT = hop_tile_rows<E>(NB);              // rows per tile (one or two passes)
+  constexpr int RPT = hop_tile_rows<E, MMA>(NB);              // rows per tile (one or two passes)
   constexpr int EB = Codec<E>::kEB;
   constexpr unsigned ROW_BYTES = (unsigned)copy_row_bytes<E>(NB, NBP);
   constexpr unsigned BODY_BYTES = (unsigned)copy_body_bytes<E>(NB, NBP);
@@ -462,7 +462,7 @@ template <typename E, typename V, bool OUTP, int RC, bool MMA = false>
 int launch_hop(const dfm_op* op, const V* xp, const V* x0p, void* y, int R, float out_scale, cudaStream_t st) {
   const int nb = op->nb;
   const int nbp = hop_nbp(nb);
-  const int rpt = hop_tile_rows<E>(nb);
+  const int rpt = hop_tile_rows<E, MMA>(nb);
   const int64_t row_bytes = copy_row_bytes<E>(nb, nbp);
   const int64_t stage_bytes = geom::hop_stage_bytes(nb, Codec<E>::kEB, Codec<E>::kScaled, (int)sizeof(V), R, MMA);
   const int stages = geom::hop_stages(stage_bytes, kHopStages);

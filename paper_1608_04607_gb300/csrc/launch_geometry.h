@@ -72,18 +72,19 @@ constexpr int64_t hop_row_bytes(int nb, int eb, bool scaled) { return hop_body_b
 
 // rows per tile: two consumer passes of (32 x consumer warps) / NBP rows (at
 // most 32, one per producer lane) when the tile's copy rows stay within
-// kHopTileBytes, else one pass
-constexpr int hop_tile_rows(int nb, int eb, bool scaled) {
+// kHopTileBytes, else one pass; the tensor-core consumer (several right-hand
+// sides, whose staged coefficients already fill the tile) always takes one
+constexpr int hop_tile_rows(int nb, int eb, bool scaled, bool mma) {
   const int step = (32 * kHopConsumerWarps) / hop_nbp(nb);
   const int two = step * 2 < 32 ? step * 2 : 32;
-  return two * hop_row_bytes(nb, eb, scaled) <= kHopTileBytes ? two : step;
+  return (!mma && two * hop_row_bytes(nb, eb, scaled) <= kHopTileBytes) ? two : step;
 }
 
 // staged bytes per tile row for R right-hand sides: the copy row, each right-hand
 // side's source-tet coefficients (4 NBP vector entries, plus a 16-byte gap
 // for the tensor-core consumer) and its x0 row (NBP entries)
 constexpr int64_t hop_stage_bytes(int nb, int eb, bool scaled, int vb, int R, bool mma) {
-  return hop_tile_rows(nb, eb, scaled) *
+  return hop_tile_rows(nb, eb, scaled, mma) *
          (hop_row_bytes(nb, eb, scaled) + (int64_t)R * (4 * hop_nbp(nb) * vb + (mma ? 16 : 0) + hop_nbp(nb) * vb));
 }
 

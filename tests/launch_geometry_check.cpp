@@ -73,7 +73,7 @@ int main() {
     for (const Fmt& f : fmts)
       for (int mma = 0; mma < 2; ++mma) {
         if (mma && (f.vb != 2 || hop_nbp(nb) % 16)) continue;
-        const int rpt = hop_tile_rows(nb, f.eb, f.scaled);
+        const int rpt = hop_tile_rows(nb, f.eb, f.scaled, mma != 0);
         const int step = (32 * kHopConsumerWarps) / hop_nbp(nb);
         if (rpt < 1 || rpt > 32 || (rpt != step && rpt != 2 * step)) return fail("hop rows per tile", nb, f.eb, f.vb, mma, rpt);
         const long long row = hop_row_bytes(nb, f.eb, f.scaled);
