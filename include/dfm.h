@@ -210,7 +210,8 @@ typedef struct {
   int precond_precision; /* GMRES_IR: 0 = the polynomial preconditioner uses the operator itself;
                         DFM_F16 or DFM_BF16 = its hops use a 16-bit copy of the blocks (made once
                         per assembly, half the bytes per hop); DFM_FP8E4M3 = an 8-bit e4m3 copy
-                        with one FP32 scale per row (a quarter of the bytes); the inner solver is flexible
+                        with one FP32 scale per row (a quarter of the bytes); a transposed solve
+                        uses the same kinds of copy of B^T; the inner solver is flexible
                         GMRES, which tolerates the inexact preconditioner; the Krylov operator
                         I - B and the FP64 residual keep the FP32 blocks */
   int batch;         /* GMRES_IR with R > 1: right-hand sides iterated in lockstep, sharing
@@ -246,7 +247,7 @@ int dfm_solve_combo(const dfm_op* const* ops, int K, const double* coef_host, co
 /* The inexact polynomial preconditioner of the flexible inner solve
  * (dfm_solve_opts.precond_precision), on its own.  The paper gives no
  * solver; this is a building block for callers' own Krylov methods:
- *   z_r = sum_{k<degree} B~^k x_r,  r < R,
+ *   z_r = sum_{k<degree} B~^k x_r  (transpose != 0: sum_{k<degree} (B~^T)^k x_r),  r < R,
  * B~ = the FP16 (precision DFM_F16) or BF16 (DFM_BF16) rounding, to nearest,
  * of op's FP32 blocks, or (DFM_FP8E4M3) s_R q with q the e4m3 rounding (to
  * nearest even, saturating) of B/s_R and s_R = (max |entry| of row R) / 448
@@ -256,7 +257,8 @@ int dfm_solve_combo(const dfm_op* const* ops, int K, const double* coef_host, co
  * aligned, z must not alias x; 1 <= degree <= 64.  Uses a scratch of
  * 3 R rows NBP floats (NBP = nb rounded up to 8) taken with cudaMallocAsync
  * on the stream and released in stream order.  Asynchronous. */
-int dfm_precond_apply(const dfm_op* op, int precision, int degree, const float* x, float* z, int R, void* stream);
+int dfm_precond_apply(const dfm_op* op, int precision, int degree, int transpose, const float* x, float* z, int R,
+                      void* stream);
 
 /* Interior density functional (Sec. 4.1, Eq. IntDens, c = 1): for each listed
  * tet e, the coefficients g_e of

@@ -317,7 +317,8 @@ extern "C" int dfm_assemble_into(const dfm_mesh* mesh, const dfm_params* p, dfm_
   if (!op || op->mesh != mesh || op->Np != p->Np || op->precision != p->precision)
     return set_error(DFM_ERR_ARG, "dfm_assemble_into: operator does not match mesh/Np/precision");
   cudaStream_t st = as_stream(stream);
-  op->lp_valid = false;  // the 16-bit preconditioner copy follows the blocks
+  op->lp_valid = false;  // the low-precision preconditioner copies follow the blocks
+  op->lpT_valid = false;
   const int q = p->quad_order ? p->quad_order : p->Np + 6;
   const double deg = p->max_patch_deg > 0 ? p->max_patch_deg : 60.0;
   const float cos_max = (float)cos(deg * M_PI / 180.0);
@@ -397,11 +398,13 @@ extern "C" void dfm_op_destroy(dfm_op* op) {
   if (!op) return;
   forget_sweep(op->vals);
   forget_sweep(op->lp_vals);
+  forget_sweep(op->lpT_vals);
   cudaFree(op->vals);
   cudaFree(op->work);
   cudaFree(op->swork);
   cudaFree(op->dev_err);
   cudaFree(op->lp_vals);
+  cudaFree(op->lpT_vals);
   delete op;
 }
 

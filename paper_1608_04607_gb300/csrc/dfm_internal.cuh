@@ -59,6 +59,12 @@ struct dfm_op {
   int64_t lp_bytes = 0;
   int lp_precision = 0;
   bool lp_valid = false;
+  // the same for B^T (transposed solves): row J = 4t + l holds the blocks that
+  // column J sends, transposed, in the order of the receiving faces l' != l
+  void* lpT_vals = nullptr;
+  int64_t lpT_bytes = 0;
+  int lpT_precision = 0;
+  bool lpT_valid = false;
   // assembly scratch (per-pair constants, Gauss table), grown on demand
   void* work = nullptr;
   int64_t work_bytes = 0;
@@ -101,14 +107,25 @@ void forget_sweep(const void* vals);
 // Polynomial-preconditioner hops on a 16-bit copy of the blocks (hop.cu).
 // Padded width of a face's coefficients in hop vectors and in the copy.
 inline int hop_nbp(int nb) { return geom::hop_nbp(nb); }
-// (re)builds op->lp_vals (precision DFM_F16, DFM_BF16 or DFM_FP8E4M3) from the FP32 blocks
-int prepare_lowp(const dfm_op* op, int precision, cudaStream_t st);
+// (re)builds op->lp_vals (trans: op->lpT_vals) in precision DFM_F16, DFM_BF16
+// or DFM_FP8E4M3 from the FP32 or BF16 blocks
+int prepare_lowp(const dfm_op* op, int precision, cudaStream_t st, int trans = 0);
+// the forward (trans = 0) or transposed copy of op
+struct LowpView {
+  const void* vals;
+  int precision;
+  bool valid;
+};
+inline LowpView lowp_of(const dfm_op* op, int trans) {
+  return trans ? LowpView{op->lpT_vals, op->lpT_precision, op->lpT_valid}
+               : LowpView{op->lp_vals, op->lp_precision, op->lp_valid};
+}
 // z = sum_{k<d} B~^k v for R vectors ([R][rows][nb] FP32) by Horner on the
-// low-precision copy; vp, ha, hb: 16-byte-aligned scratch of R rows NBP floats
+// low-precision copy (trans: B~^T on the transposed copy); vp, ha, hb: 16-byte-aligned scratch of R rows NBP floats
 // each.  FP16/e4m3 copies run on FP16 vectors holding v * vscale (a power of
 // two that keeps |v| vscale <= 2^-8).
 int hop_horner(const dfm_op* op, int R, int d, const float* v, float* z, void* vp, void* ha, void* hb, float vscale,
-               cudaStream_t st);
+               cudaStream_t st, int trans = 0);
 // implemented in quad.cu
 int gauss_legendre_device(int q, double* x, double* w, cudaStream_t st);
 }  // namespace dfm

@@ -54,15 +54,38 @@ using namespace hopk;
 
 // FP16/BF16 copy: element i of the copy <- its block entry (0 in pads); the
 // blocks are FP32, or BF16 for a BF16 operator
+// Entry e of row J of the copy.  Forward (recvT == NULL): row J's own blocks.
+// Transposed: row J = 4t + l holds, for k = 0..2 and l' = the k-th face of t
+// other than l, the block that face l of t sends to row R = recvT[4t + l'],
+// transposed: entry (a, b) = B_{R, s}[b][a], s = l - (l > l') the slot of
+// face l among the faces of t other than l'.
+template <typename S>
+__device__ __forceinline__ float copy_entry_at(const S* src, int64_t row_stride, const int32_t* recvT, int64_t J,
+                                               int64_t e, int nb, int nbp) {
+  if (!recvT) return copy_entry(src + J * row_stride, e, nb, nbp);
+  const int k = (int)(e / ((int64_t)nb * nbp));
+  int64_t rem = e - (int64_t)k * nb * nbp;
+  const int c = (int)(rem / (nb * 8));
+  rem -= (int64_t)c * nb * 8;
+  const int a = (int)(rem / 8);
+  const int b = c * 8 + (int)(rem - a * 8);
+  if (b >= nb) return 0.f;
+  const int l = (int)(J & 3);
+  const int lq = k + (k >= l ? 1 : 0);
+  const int64_t Rr = recvT[(J & ~int64_t(3)) + lq];
+  const int slot = l - (l > lq ? 1 : 0);
+  return (float)src[Rr * row_stride + (int64_t)slot * nb * nb + (int64_t)b * nb + a];
+}
+
 template <typename E, typename S>
 __global__ void to_hop16_kernel(const S* __restrict__ src, int64_t row_stride, E* __restrict__ dst, int64_t nrows,
-                                int nb, int nbp) {
+                                int nb, int nbp, const int32_t* __restrict__ recvT) {
   const int64_t row_elems = 3 * (int64_t)nb * nbp;
   const int64_t total = nrows * row_elems;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t row = i / row_elems;
     const int64_t e = i - row * row_elems;
-    const float v = copy_entry(src + row * row_stride, e, nb, nbp);
+    const float v = copy_entry_at(src, row_stride, recvT, row, e, nb, nbp);
     if constexpr (std::is_same<E, __half>::value)
       dst[i] = __float2half_rn(v);
     else
@@ -73,21 +96,26 @@ __global__ void to_hop16_kernel(const S* __restrict__ src, int64_t row_stride, E
 // e4m3 copy: one warp per operator row; s_R = max |entry| / 448, q = e4m3(v / s_R)
 template <typename S>
 __global__ void to_hop8_kernel(const S* __restrict__ src, int64_t row_stride, unsigned char* __restrict__ dst,
-                               int64_t nrows, int nb, int nbp, int64_t body_bytes, int64_t row_bytes) {
+                               int64_t nrows, int nb, int nbp, int64_t body_bytes, int64_t row_bytes,
+                               const int32_t* __restrict__ recvT) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t n_entries = 3 * (int64_t)nb * nb;
   const int64_t n_vals = 3 * (int64_t)nb * nbp;
   for (int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; row < nrows; row += warps) {
-    const S* sr = src + row * row_stride;
     float mx = 0.f;
-    for (int64_t e = lane; e < n_entries; e += 32) mx = fmaxf(mx, fabsf((float)sr[e]));
+    if (!recvT) {
+      const S* sr = src + row * row_stride;
+      for (int64_t e = lane; e < n_entries; e += 32) mx = fmaxf(mx, fabsf((float)sr[e]));
+    } else {
+      for (int64_t e = lane; e < n_vals; e += 32) mx = fmaxf(mx, fabsf(copy_entry_at(src, row_stride, recvT, row, e, nb, nbp)));
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     const float s = mx > 0.f ? mx / 448.f : 1.f;
     unsigned char* dr = dst + row * row_bytes;
     for (int64_t e = lane; e < body_bytes; e += 32) {
-      const float v = e < n_vals ? copy_entry(sr, e, nb, nbp) : 0.f;
+      const float v = e < n_vals ? copy_entry_at(src, row_stride, recvT, row, e, nb, nbp) : 0.f;
       dr[e] = (unsigned char)__nv_cvt_float_to_fp8(v / s, __NV_SATFINITE, __NV_E4M3);
     }
     if (lane < 4) reinterpret_cast<float*>(dr + body_bytes)[lane] = lane == 0 ? s : 0.f;
@@ -124,41 +152,46 @@ int grid_for_elems(int64_t n) {
 
 }  // namespace
 
-int prepare_lowp(const dfm_op* cop, int precision, cudaStream_t st) {
+int prepare_lowp(const dfm_op* cop, int precision, cudaStream_t st, int trans) {
   dfm_op* op = const_cast<dfm_op*>(cop);
   if ((op->precision != DFM_F32 && op->precision != DFM_BF16) ||
       (precision != DFM_F16 && precision != DFM_BF16 && precision != DFM_FP8E4M3))
     return set_error(DFM_ERR_UNSUPPORTED,
                      "preconditioner copy: needs an FP32 or BF16 operator and DFM_F16, DFM_BF16 or DFM_FP8E4M3");
+  void*& vals = trans ? op->lpT_vals : op->lp_vals;
+  int64_t& have = trans ? op->lpT_bytes : op->lp_bytes;
+  int& prec = trans ? op->lpT_precision : op->lp_precision;
+  bool& valid = trans ? op->lpT_valid : op->lp_valid;
+  const int32_t* recvT = trans ? op->mesh->recv : nullptr;
   const int nb = op->nb, nbp = hop_nbp(nb);
   const int64_t row_bytes = precision == DFM_FP8E4M3 ? copy_row_bytes<__nv_fp8_e4m3>(nb, nbp)
                                                      : copy_row_bytes<__half>(nb, nbp);
   const int64_t bytes = op->nrows * row_bytes;
-  if (op->lp_vals && op->lp_bytes < bytes) {
-    forget_sweep(op->lp_vals);
-    DFM_CUDA_CHECK(cudaFree(op->lp_vals));
-    op->lp_vals = nullptr;
-    op->lp_valid = false;
+  if (vals && have < bytes) {
+    forget_sweep(vals);
+    DFM_CUDA_CHECK(cudaFree(vals));
+    vals = nullptr;
+    valid = false;
   }
-  if (!op->lp_vals) {
-    DFM_CUDA_CHECK(cudaMalloc(&op->lp_vals, bytes));
-    op->lp_bytes = bytes;
+  if (!vals) {
+    DFM_CUDA_CHECK(cudaMalloc(&vals, bytes));
+    have = bytes;
   }
-  if (!op->lp_valid || op->lp_precision != precision) {
+  if (!valid || prec != precision) {
     auto convert = [&](auto src) {
       using S = std::remove_const_t<std::remove_pointer_t<decltype(src)>>;
       if (precision == DFM_FP8E4M3) {
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((op->nrows * 32 + 255) / 256, 4096));
-        to_hop8_kernel<S><<<grid, 256, 0, st>>>(src, op->row_stride, (unsigned char*)op->lp_vals, op->nrows, nb, nbp,
-                                                copy_body_bytes<__nv_fp8_e4m3>(nb, nbp), row_bytes);
+        to_hop8_kernel<S><<<grid, 256, 0, st>>>(src, op->row_stride, (unsigned char*)vals, op->nrows, nb, nbp,
+                                                copy_body_bytes<__nv_fp8_e4m3>(nb, nbp), row_bytes, recvT);
       } else {
         const int grid = grid_for_elems(op->nrows * 3 * (int64_t)nb * nbp);
         if (precision == DFM_F16)
-          to_hop16_kernel<__half, S><<<grid, 256, 0, st>>>(src, op->row_stride, (__half*)op->lp_vals, op->nrows, nb,
-                                                            nbp);
+          to_hop16_kernel<__half, S><<<grid, 256, 0, st>>>(src, op->row_stride, (__half*)vals, op->nrows, nb, nbp,
+                                                            recvT);
         else
-          to_hop16_kernel<__nv_bfloat16, S><<<grid, 256, 0, st>>>(src, op->row_stride, (__nv_bfloat16*)op->lp_vals,
-                                                                   op->nrows, nb, nbp);
+          to_hop16_kernel<__nv_bfloat16, S><<<grid, 256, 0, st>>>(src, op->row_stride, (__nv_bfloat16*)vals,
+                                                                   op->nrows, nb, nbp, recvT);
       }
     };
     if (op->precision == DFM_F32)
@@ -167,8 +200,8 @@ int prepare_lowp(const dfm_op* cop, int precision, cudaStream_t st) {
       convert((const __nv_bfloat16*)op->vals);
     DFM_LAUNCHED();
     DFM_CUDA_CHECK(cudaGetLastError());
-    op->lp_precision = precision;
-    op->lp_valid = true;
+    prec = precision;
+    valid = true;
   }
   return DFM_OK;
 }
@@ -178,13 +211,14 @@ namespace {
 // one hop over all R right-hand sides (kHopMaxRhs per launch)
 template <typename V>
 int hop_apply_t(const dfm_op* op, const V* xp, const V* x0p, void* y, int R, bool out_padded, float out_scale,
-                cudaStream_t st) {
+                int trans, cudaStream_t st) {
+  const LowpView cp = lowp_of(op, trans);
   const int64_t stride_p = op->nrows * (int64_t)hop_nbp(op->nb);
   const int64_t stride_y = out_padded ? stride_p : op->nrows * (int64_t)op->nb;
   const int64_t ybytes = out_padded ? (int64_t)sizeof(V) : 4;
   // right-hand sides per launch: at most kHopMaxRhs, and few enough that two
   // stages fit in shared memory (large bases with many right-hand sides)
-  const bool fp8 = op->lp_precision == DFM_FP8E4M3;
+  const bool fp8 = cp.precision == DFM_FP8E4M3;
   const int rchunk = geom::hop_rhs_chunk(op->nb, fp8 ? 1 : 2, fp8, (int)sizeof(V),
                                          std::is_same<V, __half>::value && R > 1);
   if (rchunk < 1) return set_error(DFM_ERR_UNSUPPORTED, "preconditioner hop: a tile does not fit shared memory");
@@ -195,12 +229,12 @@ int hop_apply_t(const dfm_op* op, const V* xp, const V* x0p, void* y, int R, boo
     void* yy = static_cast<char*>(y) + r0 * stride_y * ybytes;
     int rc;
     if constexpr (std::is_same<V, __half>::value) {
-      if (op->lp_precision == DFM_F16)
-        rc = hop_launch_f16(op, x, x0, yy, Rp, out_scale, out_padded, st);
+      if (cp.precision == DFM_F16)
+        rc = hop_launch_f16(op, x, x0, yy, Rp, out_scale, out_padded, trans, st);
       else
-        rc = hop_launch_fp8(op, x, x0, yy, Rp, out_scale, out_padded, st);
+        rc = hop_launch_fp8(op, x, x0, yy, Rp, out_scale, out_padded, trans, st);
     } else {
-      rc = hop_launch_bf16(op, x, x0, yy, Rp, out_scale, out_padded, st);
+      rc = hop_launch_bf16(op, x, x0, yy, Rp, out_scale, out_padded, trans, st);
     }
     if (rc) return rc;
   }
@@ -209,7 +243,7 @@ int hop_apply_t(const dfm_op* op, const V* xp, const V* x0p, void* y, int R, boo
 
 template <typename V>
 int horner_t(const dfm_op* op, int R, int d, const float* v, float* z, void* vp_, void* ha_, void* hb_, float vscale,
-             cudaStream_t st) {
+             int trans, cudaStream_t st) {
   V* vp = static_cast<V*>(vp_);
   V* h[2] = {static_cast<V*>(ha_), static_cast<V*>(hb_)};
   const int64_t rows = (int64_t)R * op->nrows;
@@ -221,7 +255,7 @@ int horner_t(const dfm_op* op, int R, int d, const float* v, float* z, void* vp_
   for (int k = 1; k < d; ++k) {
     const bool last = (k == d - 1);
     void* dst = last ? static_cast<void*>(z) : static_cast<void*>(h[k & 1]);
-    const int rc = hop_apply_t<V>(op, src, vp, dst, R, !last, 1.0f / vscale, st);
+    const int rc = hop_apply_t<V>(op, src, vp, dst, R, !last, 1.0f / vscale, trans, st);
     if (rc) return rc;
     src = h[k & 1];
   }
@@ -231,11 +265,11 @@ int horner_t(const dfm_op* op, int R, int d, const float* v, float* z, void* vp_
 }  // namespace
 
 int hop_horner(const dfm_op* op, int R, int d, const float* v, float* z, void* vp, void* ha, void* hb, float vscale,
-               cudaStream_t st) {
-  if (!op || !op->lp_valid || !v || !z || R < 1 || d < 1)
+               cudaStream_t st, int trans) {
+  if (!op || !lowp_of(op, trans).valid || !v || !z || R < 1 || d < 1)
     return set_error(DFM_ERR_ARG, "preconditioner: no low-precision copy, NULL vector or bad degree");
   if ((reinterpret_cast<uintptr_t>(vp) | reinterpret_cast<uintptr_t>(ha) | reinterpret_cast<uintptr_t>(hb) |
-       reinterpret_cast<uintptr_t>(op->lp_vals)) & 15)
+       reinterpret_cast<uintptr_t>(lowp_of(op, trans).vals)) & 15)
     return set_error(DFM_ERR_ARG, "preconditioner: hop vectors and copy must be 16-byte aligned");
   if (d == 1) {
     DFM_CUDA_CHECK(cudaMemcpyAsync(z, v, sizeof(float) * (int64_t)R * op->nrows * op->nb, cudaMemcpyDeviceToDevice, st));
@@ -243,14 +277,14 @@ int hop_horner(const dfm_op* op, int R, int d, const float* v, float* z, void* v
   }
   // FP16 and e4m3 copies run the hops on FP16 vectors (v scaled by vscale);
   // the BF16 copy on FP32 vectors
-  if (op->lp_precision == DFM_BF16) return horner_t<float>(op, R, d, v, z, vp, ha, hb, 1.0f, st);
-  return horner_t<__half>(op, R, d, v, z, vp, ha, hb, vscale, st);
+  if (lowp_of(op, trans).precision == DFM_BF16) return horner_t<float>(op, R, d, v, z, vp, ha, hb, 1.0f, trans, st);
+  return horner_t<__half>(op, R, d, v, z, vp, ha, hb, vscale, trans, st);
 }
 
 }  // namespace dfm
 
-extern "C" int dfm_precond_apply(const dfm_op* op, int precision, int degree, const float* x, float* z, int R,
-                                 void* stream) {
+extern "C" int dfm_precond_apply(const dfm_op* op, int precision, int degree, int transpose, const float* x, float* z,
+                                 int R, void* stream) {
   using namespace dfm;
   if (!op || !x || !z || R < 1) return set_error(DFM_ERR_ARG, "dfm_precond_apply: NULL operator/vector or R < 1");
   if (x == z) return set_error(DFM_ERR_ARG, "dfm_precond_apply: z must not alias x");
@@ -258,7 +292,7 @@ extern "C" int dfm_precond_apply(const dfm_op* op, int precision, int degree, co
   if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(z)) & 15)
     return set_error(DFM_ERR_ARG, "dfm_precond_apply: x and z must be 16-byte aligned");
   cudaStream_t st = as_stream(stream);
-  int rc = prepare_lowp(op, precision, st);
+  int rc = prepare_lowp(op, precision, st, transpose ? 1 : 0);
   if (rc) return rc;
   const int64_t rows = (int64_t)R * op->nrows;
   const int64_t elems = rows * hop_nbp(op->nb);
@@ -284,7 +318,8 @@ extern "C" int dfm_precond_apply(const dfm_op* op, int precision, int degree, co
     int ex = 0;
     if (amax > 0.f && std::isfinite(amax)) frexpf(amax, &ex);  // amax < 2^ex
     const float vscale = ldexpf(1.0f, -(ex + 8));
-    rc = hop_horner(op, R, degree, x, z, scratch, scratch + vec_bytes, scratch + 2 * vec_bytes, vscale, st);
+    rc = hop_horner(op, R, degree, x, z, scratch, scratch + vec_bytes, scratch + 2 * vec_bytes, vscale, st,
+                    transpose ? 1 : 0);
   }
   const cudaError_t ef = cudaFreeAsync(scratch, st);
   if (e != cudaSuccess) return cuda_error(e, "dfm_precond_apply");

@@ -185,7 +185,7 @@ template <int NB, typename E, typename V, bool OUTP, int RC, bool MMA>
 __global__ void __launch_bounds__(32 * (kHopConsumerWarps + 1))
 hop_kernel(const unsigned char* __restrict__ vals, const int32_t* __restrict__ recv, int64_t nrows,
            const V* __restrict__ xp, const V* __restrict__ x0p, void* __restrict__ yv, int R, float alpha,
-           float out_scale, int stages, int reverse, int64_t keep_from, int* __restrict__ err) {
+           float out_scale, int stages, int reverse, int trans, int64_t keep_from, int* __restrict__ err) {
   constexpr int NBP = (NB + 7) / 8 * 8;
   constexpr int NC = NBP / 8;
   constexpr int RSTEP = (32 * kHopConsumerWarps) / NBP;  // rows of one consumer pass
@@ -228,26 +228,37 @@ hop_kernel(const unsigned char* __restrict__ vals, const int32_t* __restrict__ r
     const uint64_t pol_first = l2_policy_evict_first();
     int64_t issued = 0;
     bool ok = true;
-    int32_t next_src = 0;
+    // per tile row: the rows whose coefficients it gathers.  Forward: the
+    // source tet of row R (recv[R] / 4), whose 4 faces are consecutive rows.
+    // Transposed: the receiving rows recv[4t + l'] of the row's own tet t,
+    // one gathered face row each (read as one 16-byte vector of recv).
+    auto row_sources = [&](int64_t row) -> int4 {
+      if (trans) return *reinterpret_cast<const int4*>(recv + (row & ~int64_t(3)));
+      const int32_t q = recv[row];
+      return make_int4(q, q, q, q);
+    };
+    int4 next_src = make_int4(0, 0, 0, 0);
     if (mine > 0) {
       const int64_t R0 = tile_first_row(0);
-      if (lane < RPT && R0 + lane < nrows) next_src = recv[R0 + lane];
+      if (lane < RPT && R0 + lane < nrows) next_src = row_sources(R0 + lane);
     }
     for (int64_t i = 0; i < mine && ok; ++i) {
       const int s = (int)(i % stages);
       const int64_t R0 = tile_first_row(i);
       const int nr = (int)std::min<int64_t>(RPT, nrows - R0);
-      const int32_t src = next_src;
+      const int4 src = next_src;
       if (i + 1 < mine) {
         const int64_t R1 = tile_first_row(i + 1);
-        if (lane < RPT && R1 + lane < nrows) next_src = recv[R1 + lane];
+        if (lane < RPT && R1 + lane < nrows) next_src = row_sources(R1 + lane);
       }
       if (i >= stages) ok = mbar_wait_bounded(&empty[s], (unsigned)(((i / stages) - 1) & 1));
       ok = __all_sync(0xffffffffu, ok);
       if (!ok) break;
       unsigned char* st = stage0 + s * stage_bytes;
       int32_t* rs = s_recv + s * RPT;
-      if (lane < nr) rs[lane] = src;
+      // the consumers skip face (entry & 3) of the gathered four: the source
+      // tet's exit face (forward) or the row's own face (transposed)
+      if (lane < nr) rs[lane] = trans ? (int32_t)(R0 + lane) : src.x;
       __syncwarp();  // the row map is written before lane 0's arrive publishes the stage
       fence_proxy_async_smem();
       if (lane == 0) {
@@ -262,10 +273,22 @@ hop_kernel(const unsigned char* __restrict__ vals, const int32_t* __restrict__ r
         for (int rhs = 0; rhs < R; ++rhs) {
           unsigned char* dst =
               st + (int64_t)RPT * ROW_BYTES + (MMA ? (int64_t)lane * R + rhs : (int64_t)rhs * RPT + lane) * XBLK;
-          const unsigned char* srcp =
-              reinterpret_cast<const unsigned char*>(xp + ((int64_t)rhs * nrows + 4 * (int64_t)(src >> 2)) * NBP);
+          if (!trans) {
+            const unsigned char* srcp =
+                reinterpret_cast<const unsigned char*>(xp + ((int64_t)rhs * nrows + 4 * (int64_t)(src.x >> 2)) * NBP);
 #pragma unroll
-          for (unsigned off = 0; off < XBLK_D; off += 16) cp_async16(dst + off, srcp + off);
+            for (unsigned off = 0; off < XBLK_D; off += 16) cp_async16(dst + off, srcp + off);
+          } else {
+            const int32_t fr[4] = {src.x, src.y, src.z, src.w};
+#pragma unroll
+            for (int f = 0; f < 4; ++f) {
+              const unsigned char* srcp =
+                  reinterpret_cast<const unsigned char*>(xp + ((int64_t)rhs * nrows + fr[f]) * NBP);
+#pragma unroll
+              for (unsigned off = 0; off < XBLK_D / 4; off += 16)
+                cp_async16(dst + f * (XBLK_D / 4) + off, srcp + off);
+            }
+          }
         }
       cp_async_arrive_noinc(&full[s]);
       issued = i + 1;
@@ -459,7 +482,9 @@ hop_kernel(const unsigned char* __restrict__ vals, const int32_t* __restrict__ r
 }
 
 template <typename E, typename V, bool OUTP, int RC, bool MMA = false>
-int launch_hop(const dfm_op* op, const V* xp, const V* x0p, void* y, int R, float out_scale, cudaStream_t st) {
+int launch_hop(const dfm_op* op, const V* xp, const V* x0p, void* y, int R, float out_scale, int trans,
+               cudaStream_t st) {
+  const void* copy = lowp_of(op, trans).vals;
   const int nb = op->nb;
   const int nbp = hop_nbp(nb);
   const int rpt = hop_tile_rows<E, MMA>(nb);
@@ -482,8 +507,8 @@ int launch_hop(const dfm_op* op, const V* xp, const V* x0p, void* y, int R, floa
     {
       ::dfm::KernelTimer timer_(DFM_KERNEL_SPMV16, st);
       kernel<<<(unsigned)grid, 32 * (kHopConsumerWarps + 1), smem, st>>>(
-          reinterpret_cast<const unsigned char*>(op->lp_vals), op->mesh->recv, op->nrows, xp, x0p, y, R, 1.0f,
-          out_scale, stages, next_sweep_direction(op->lp_vals), keep_from, op->dev_err);
+          reinterpret_cast<const unsigned char*>(copy), op->mesh->recv, op->nrows, xp, x0p, y, R, 1.0f,
+          out_scale, stages, next_sweep_direction(copy), trans, keep_from, op->dev_err);
     }
     DFM_LAUNCHED();
     DFM_CUDA_CHECK(cudaGetLastError());
@@ -520,10 +545,10 @@ inline bool hop_uses_mma(int nb, int R) { return R > 1 && (((nb + 7) / 8 * 8) % 
 // y = x0 + B~ x on the copy of op (one copy format per entry point); x, x0
 // padded vectors of type V; y padded (outp) or FP32 unpadded times out_scale.
 int hop_launch_f16(const dfm_op* op, const __half* xp, const __half* x0p, void* y, int R, float out_scale, bool outp,
-                   cudaStream_t st);
+                   int trans, cudaStream_t st);
 int hop_launch_fp8(const dfm_op* op, const __half* xp, const __half* x0p, void* y, int R, float out_scale, bool outp,
-                   cudaStream_t st);
+                   int trans, cudaStream_t st);
 int hop_launch_bf16(const dfm_op* op, const float* xp, const float* x0p, void* y, int R, float out_scale, bool outp,
-                    cudaStream_t st);
+                    int trans, cudaStream_t st);
 
 }  // namespace dfm

@@ -3,17 +3,17 @@
 
 namespace dfm {
 
-int hop_launch_fp8(const dfm_op* op, const __half* xp, const __half* x0p, void* y, int R, float out_scale, bool outp,
-                   cudaStream_t st) {
+int hop_launch_fp8(const dfm_op* op, const __half* xp, const __half* x0p, void* y, int R, float out_scale,
+                   bool outp, int trans, cudaStream_t st) {
   using namespace hopk;
   if (R == 1)
-    return outp ? launch_hop<__nv_fp8_e4m3, __half, true, 1>(op, xp, x0p, y, R, out_scale, st)
-                : launch_hop<__nv_fp8_e4m3, __half, false, 1>(op, xp, x0p, y, R, out_scale, st);
+    return outp ? launch_hop<__nv_fp8_e4m3, __half, true, 1>(op, xp, x0p, y, R, out_scale, trans, st)
+                : launch_hop<__nv_fp8_e4m3, __half, false, 1>(op, xp, x0p, y, R, out_scale, trans, st);
   if (hop_uses_mma(op->nb, R))  // several right-hand sides on tensor cores
-    return outp ? launch_hop<__nv_fp8_e4m3, __half, true, 1, true>(op, xp, x0p, y, R, out_scale, st)
-                : launch_hop<__nv_fp8_e4m3, __half, false, 1, true>(op, xp, x0p, y, R, out_scale, st);
-  return outp ? launch_hop<__nv_fp8_e4m3, __half, true, kHopRhsInner>(op, xp, x0p, y, R, out_scale, st)
-              : launch_hop<__nv_fp8_e4m3, __half, false, kHopRhsInner>(op, xp, x0p, y, R, out_scale, st);
+    return outp ? launch_hop<__nv_fp8_e4m3, __half, true, 1, true>(op, xp, x0p, y, R, out_scale, trans, st)
+                : launch_hop<__nv_fp8_e4m3, __half, false, 1, true>(op, xp, x0p, y, R, out_scale, trans, st);
+  return outp ? launch_hop<__nv_fp8_e4m3, __half, true, kHopRhsInner>(op, xp, x0p, y, R, out_scale, trans, st)
+              : launch_hop<__nv_fp8_e4m3, __half, false, kHopRhsInner>(op, xp, x0p, y, R, out_scale, trans, st);
 }
 
 }  // namespace dfm

@@ -393,7 +393,7 @@ struct Hop {
 // low-precision copy; unit norm keeps |v| <= 1, so the FP16 hop vectors hold
 // v 2^-8.
 inline int precond_hops(const Ctx& c, const Hop& hp, int R, int d, const float* v, float* z) {
-  return ::dfm::hop_horner(hp.op, R, d, v, z, hp.vp, hp.ha, hp.hb, 1.0f / 256.0f, c.st);
+  return ::dfm::hop_horner(hp.op, R, d, v, z, hp.vp, hp.ha, hp.hb, 1.0f / 256.0f, c.st, c.trans);
 }
 
 template <typename T>
@@ -872,7 +872,8 @@ int solve_impl(const dfm_op* op, const dfm_op* const* combo, int K, const double
   const int poly = opts->poly_degree > 0 ? std::min(opts->poly_degree, 64) : (opts->precond_precision ? 32 : 16);
   // with combined operators the preconditioner's copy is made from ops[0]
   // (B_0, e.g. B(mu_c)): one p(B~_0) serves every right-hand side's B_r
-  const bool use_lp = opts->precond_precision != 0 && method == DFM_SOLVE_GMRES_IR && !opts->transpose;
+  // a transposed solve preconditions with p(B~^T) on the transposed copy
+  const bool use_lp = opts->precond_precision != 0 && method == DFM_SOLVE_GMRES_IR;
   if (opts->precond_precision != 0 && opts->precond_precision != DFM_F16 && opts->precond_precision != DFM_BF16 &&
       opts->precond_precision != DFM_FP8E4M3)
     return set_error(DFM_ERR_ARG, "dfm_solve: precond_precision must be 0, DFM_F16, DFM_BF16 or DFM_FP8E4M3");
@@ -938,7 +939,7 @@ int solve_impl(const dfm_op* op, const dfm_op* const* combo, int K, const double
   Hop hop;
   const Hop* lp = nullptr;
   if (use_lp) {
-    rc = prepare_lowp(op, opts->precond_precision, c.st);
+    rc = prepare_lowp(op, opts->precond_precision, c.st, opts->transpose ? 1 : 0);
     if (rc) return rc;
     hop.op = op;
     lp = &hop;

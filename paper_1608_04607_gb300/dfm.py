@@ -83,7 +83,7 @@ SIGNATURES = {
     "dfm_apply": (_i, [_vp, _vp, _vp, _vp, _i, _d, _i, _i, _vp]),
     "dfm_source": (_i, [_vp, _i, _vp, _i, _vp, _vp]),
     "dfm_apply_combo": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _i, _d, _i, _vp]),
-    "dfm_precond_apply": (_i, [_vp, _i, _i, _vp, _vp, _i, _vp]),
+    "dfm_precond_apply": (_i, [_vp, _i, _i, _i, _vp, _vp, _i, _vp]),
     "dfm_solve_combo": (_i, [_vp, _i, _vp, _vp, _i, _vp, ctypes.POINTER(SolveOpts), _vp, ctypes.POINTER(SolveInfo)]),
     "dfm_solve": (_i, [_vp, _vp, _i, _vp, ctypes.POINTER(SolveOpts), _vp, ctypes.POINTER(SolveInfo)]),
     "dfm_interior_density": (_i, [_vp, _i, _vp, _d, _vp, _vp, _i, _i, _vp, _vp, _vp]),
@@ -254,7 +254,7 @@ class Operator:
                               _stream()), "dfm_apply")
         return y
 
-    def precond(self, x, degree=16, precision=F16, out=None):
+    def precond(self, x, degree=16, precision=F16, out=None, transpose=False):
         """z = sum_{k<degree} B~^k x on the low-precision copy B~ of the blocks
         (dfm_precond_apply; precision F16, BF16 or FP8E4M3); x: FP32
         [R, rows, nb] or [rows, nb]."""
@@ -263,8 +263,8 @@ class Operator:
             raise TypeError("precond: x must be float32")
         R = 1 if x.dim() == 2 else x.shape[0]
         z = torch.empty_like(x) if out is None else out
-        _check(_lib.dfm_precond_apply(self._h, int(precision), int(degree), _ptr(x), _ptr(z), R, _stream()),
-               "dfm_precond_apply")
+        _check(_lib.dfm_precond_apply(self._h, int(precision), int(degree), int(bool(transpose)), _ptr(x), _ptr(z), R,
+                                      _stream()), "dfm_precond_apply")
         return z
 
     def solve(self, rho0, method=GMRES_IR, tol=1e-8, max_iter=0, restart=0, x0=None, inner_tol=0.0,
@@ -284,7 +284,7 @@ class Operator:
         return rho, info
 
     def adjoint(self, rho, gvec, dgvec=None, method=GMRES_IR, tol=1e-8, max_iter=0, restart=0, inner_tol=0.0,
-                poly_degree=0):
+                poly_degree=0, precond_precision=0):
         """lambda = (I - B)^{-T} gvec and dJ/dmu for J = sum_r gvec . rho_r (dfm_adjoint).
         rho: FP64 [R, rows, nb]; gvec/dgvec: FP64 [rows, nb].  Returns (lambda, dJ_dmu [R, n_tets], info)."""
         torch = self._torch
@@ -292,7 +292,7 @@ class Operator:
         lam = torch.empty((self.n_rows, self.nb), dtype=torch.float64, device="cuda")
         dj = torch.empty((R, self.mesh.n_tets), dtype=torch.float64, device="cuda")
         o = SolveOpts(method=method, tol=tol, max_iter=max_iter, restart=restart, use_x0=0, inner_tol=inner_tol,
-                      transpose=1, poly_degree=poly_degree, batch=0)
+                      transpose=1, poly_degree=poly_degree, batch=0, precond_precision=precond_precision)
         info = SolveInfo()
         _check(_lib.dfm_adjoint(self._h, ctypes.byref(self._p), _ptr(rho), R, _ptr(gvec), _ptr(dgvec), _ptr(lam),
                                 _ptr(dj), ctypes.byref(o), _stream(), ctypes.byref(info)), "dfm_adjoint")

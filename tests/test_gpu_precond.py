@@ -151,3 +151,72 @@ def test_precond_fp16_vectors_follow_the_input_scale(D, mesh161, prec):
         zs = op.precond(x * s, degree=6, precision=p)
         assert torch.isfinite(zs).all()
         assert float((zs / s - z).abs().max()) <= 1e-6 * float(z.abs().max())
+
+
+def _round_e4m3_columns(blocks32):
+    """The transposed e4m3 copy: row J of B^T holds the three blocks column J
+    sends (the oracle's column layout blocks[J]), so its scale is the largest
+    entry of blocks[J]; values rounded as in _round_e4m3_rows."""
+    b32 = np.asarray(blocks32, dtype=np.float32)
+    mx = np.abs(b32).reshape(b32.shape[0], -1).max(axis=1).astype(np.float32)
+    s = np.where(mx > 0, mx / np.float32(448.0), np.float32(1.0)).astype(np.float32)
+    ratio = (b32 / s[:, None, None, None]).astype(np.float32)
+    return _e4m3(ratio) * s.astype(np.float64)[:, None, None, None]
+
+
+@pytest.mark.parametrize("Np,R", [(2, 1), (4, 1), (4, 3), (8, 5)])
+@pytest.mark.parametrize("prec", ["f16", "bf16", "e4m3"])
+def test_transposed_precond_matches_oracle(D, oracle_mod, mesh161, Np, R, prec):
+    """z = sum_{k<d} (B~^T)^k x on the transposed copy (the adjoint solve's
+    preconditioner) against the oracle's transposed application of the same
+    rounded blocks."""
+    import torch
+
+    verts, tets = mesh161
+    nt = tets.shape[0]
+    mesh = D.Mesh(verts, tets, refl=0.9)
+    op = D.Operator(mesh, Np, mu=0.2, precision=D.F32)
+    cols32 = to_oracle_layout(op.blocks().cpu().numpy(), mesh.recv(), nt).astype(np.float32)
+    if prec == "e4m3":
+        rounded = _round_e4m3_columns(cols32)
+    else:
+        rounded = _round_f16(cols32) if prec == "f16" else _round_bf16(cols32)
+    t, f, fp = oracle_mod.pair_list(nt)
+    dest = mesh.recv()[4 * t + fp].reshape(4 * nt, 3).astype(np.int64)
+    ref_op = oracle_mod.Operator(Np=Np, blocks=np.ascontiguousarray(rounded), dest=dest)
+    rng = np.random.default_rng(10 + Np)
+    x = rng.standard_normal((R, 4 * nt, op.nb)).astype(np.float32)
+    xt = torch.tensor(x, device="cuda")
+    for d in (2, 5):
+        z = op.precond(xt, degree=d, precision={"f16": D.F16, "bf16": D.BF16, "e4m3": D.FP8E4M3}[prec],
+                       transpose=True).cpu().numpy()
+        for r in range(R):
+            xr = x[r].astype(np.float64)
+            zr = xr.copy()
+            for _ in range(d - 1):
+                zr = xr + oracle_mod.apply(ref_op, zr, trans=True)
+            assert np.abs(z[r] - zr).max() <= TOL[prec] * np.abs(zr).max(), (d, r)
+
+
+@pytest.mark.parametrize("prec", ["f16", "e4m3"])
+def test_transposed_solve_with_low_precision_preconditioner(D, oracle_mod, mesh161, prec):
+    """(I - B)^T x = b with the flexible solve preconditioned on the transposed
+    copy matches LU of the same FP32 operator."""
+    import torch
+
+    verts, tets = mesh161
+    nt = tets.shape[0]
+    mesh = D.Mesh(verts, tets, refl=0.9)
+    op = D.Operator(mesh, 4, mu=0.2, precision=D.F32)
+    blocks = to_oracle_layout(op.blocks().cpu().numpy(), mesh.recv(), nt)
+    t, f, fp = oracle_mod.pair_list(nt)
+    dest = mesh.recv()[4 * t + fp].reshape(4 * nt, 3).astype(np.int64)
+    ref_op = oracle_mod.Operator(Np=4, blocks=np.ascontiguousarray(blocks), dest=dest)
+    M = np.eye(ref_op.nrows * ref_op.nb) - oracle_mod.dense(ref_op)
+    rng = np.random.default_rng(3)
+    b = torch.tensor(rng.standard_normal((2, 4 * nt, op.nb)), dtype=torch.float64, device="cuda")
+    x, info = op.solve(b, tol=1e-10, transpose=True, precond_precision=D.F16 if prec == "f16" else D.FP8E4M3)
+    assert info.resid <= 1e-10
+    for r in range(2):
+        want = np.linalg.solve(M.T, b[r].cpu().numpy().ravel())
+        assert np.linalg.norm(x[r].cpu().numpy().ravel() - want) <= 1e-8 * np.linalg.norm(want)
