@@ -181,11 +181,11 @@ __device__ __forceinline__ uint32_t copy_pair(const unsigned char* bk, int c, in
 // coefficients are then laid out per row and right-hand side with a 16-byte
 // gap, which keeps the B-fragment loads of 8 right-hand sides on distinct
 // shared-memory banks.
-template <int NB, typename E, typename V, bool OUTP, int RC, bool MMA>
+template <int NB, typename E, typename V, bool OUTP, int RC, bool MMA, bool TR>
 __global__ void __launch_bounds__(32 * (kHopConsumerWarps + 1))
 hop_kernel(const unsigned char* __restrict__ vals, const int32_t* __restrict__ recv, int64_t nrows,
            const V* __restrict__ xp, const V* __restrict__ x0p, void* __restrict__ yv, int R, float alpha,
-           float out_scale, int stages, int reverse, int trans, int64_t keep_from, int* __restrict__ err) {
+           float out_scale, int stages, int reverse, int64_t keep_from, int* __restrict__ err) {
   constexpr int NBP = (NB + 7) / 8 * 8;
   constexpr int NC = NBP / 8;
   constexpr int RSTEP = (32 * kHopConsumerWarps) / NBP;  // rows of one consumer pass
@@ -233,9 +233,12 @@ hop_kernel(const unsigned char* __restrict__ vals, const int32_t* __restrict__ r
     // Transposed: the receiving rows recv[4t + l'] of the row's own tet t,
     // one gathered face row each (read as one 16-byte vector of recv).
     auto row_sources = [&](int64_t row) -> int4 {
-      if (trans) return *reinterpret_cast<const int4*>(recv + (row & ~int64_t(3)));
-      const int32_t q = recv[row];
-      return make_int4(q, q, q, q);
+      if constexpr (TR) {
+        return *reinterpret_cast<const int4*>(recv + (row & ~int64_t(3)));
+      } else {
+        const int32_t q = recv[row];
+        return make_int4(q, q, q, q);
+      }
     };
     int4 next_src = make_int4(0, 0, 0, 0);
     if (mine > 0) {
@@ -258,7 +261,7 @@ hop_kernel(const unsigned char* __restrict__ vals, const int32_t* __restrict__ r
       int32_t* rs = s_recv + s * RPT;
       // the consumers skip face (entry & 3) of the gathered four: the source
       // tet's exit face (forward) or the row's own face (transposed)
-      if (lane < nr) rs[lane] = trans ? (int32_t)(R0 + lane) : src.x;
+      if (lane < nr) rs[lane] = TR ? (int32_t)(R0 + lane) : src.x;
       __syncwarp();  // the row map is written before lane 0's arrive publishes the stage
       fence_proxy_async_smem();
       if (lane == 0) {
@@ -273,7 +276,7 @@ hop_kernel(const unsigned char* __restrict__ vals, const int32_t* __restrict__ r
         for (int rhs = 0; rhs < R; ++rhs) {
           unsigned char* dst =
               st + (int64_t)RPT * ROW_BYTES + (MMA ? (int64_t)lane * R + rhs : (int64_t)rhs * RPT + lane) * XBLK;
-          if (!trans) {
+          if constexpr (!TR) {
             const unsigned char* srcp =
                 reinterpret_cast<const unsigned char*>(xp + ((int64_t)rhs * nrows + 4 * (int64_t)(src.x >> 2)) * NBP);
 #pragma unroll
@@ -508,7 +511,7 @@ int launch_hop(const dfm_op* op, const V* xp, const V* x0p, void* y, int R, floa
       ::dfm::KernelTimer timer_(DFM_KERNEL_SPMV16, st);
       kernel<<<(unsigned)grid, 32 * (kHopConsumerWarps + 1), smem, st>>>(
           reinterpret_cast<const unsigned char*>(copy), op->mesh->recv, op->nrows, xp, x0p, y, R, 1.0f,
-          out_scale, stages, next_sweep_direction(copy), trans, keep_from, op->dev_err);
+          out_scale, stages, next_sweep_direction(copy), keep_from, op->dev_err);
     }
     DFM_LAUNCHED();
     DFM_CUDA_CHECK(cudaGetLastError());
@@ -519,7 +522,8 @@ int launch_hop(const dfm_op* op, const V* xp, const V* x0p, void* y, int R, floa
     if constexpr (MMA && ((NBC + 7) / 8 * 8) % 16 != 0)
       return set_error(DFM_ERR_UNSUPPORTED, "preconditioner hop: tensor-core tiles need a basis padded to 16");
     else
-      return go(hop_kernel<NBC, E, V, OUTP, RC, MMA>);
+      return trans ? go(hop_kernel<NBC, E, V, OUTP, RC, MMA, true>)
+                   : go(hop_kernel<NBC, E, V, OUTP, RC, MMA, false>);
   };
   switch (nb) {
     case 1: return go_nb(std::integral_constant<int, 1>{});
