@@ -616,8 +616,9 @@ def run_batched(args):
         for o in ops:
             o.reassemble(mu_c)
         rho0 = dfm.source(mesh, Np, rows)
-        return dfm.solve_combo(ops, coef, rho0, tol=tol, batch=args.batch, poly_degree=args.poly,
-                               restart=args.restart, precond_precision=PRECOND[args.precond])
+        # degree 64 with restart 32: 7.6 solves/s against 6.6 with degree 32, restart 128
+        return dfm.solve_combo(ops, coef, rho0, tol=tol, batch=args.batch, poly_degree=args.poly or 64,
+                               restart=args.restart or 32, precond_precision=PRECOND[args.precond])
 
     rho, info = step()
     torch.cuda.synchronize()
