@@ -59,6 +59,7 @@ inline Fwd fwd_geometry(int nb, int tv, int tx, int K, int R, int64_t nrows, boo
 
 // ---- preconditioner hops on the low-precision copy (hop_kernel) ----
 constexpr int kHopConsumerWarps = 8;
+constexpr int kHopPasses = 2;  // consumer passes per tile when the copy rows are small
 constexpr int kHopMaxRhs = 16;               // right-hand sides staged per pass
 constexpr int64_t kHopTileBytes = 48 * 1024;  // copy bytes of a tile for two consumer passes
 constexpr int64_t kHopTwoBlockBytes = 110 * 1024;  // stage bytes that still fit two blocks per SM
@@ -76,8 +77,8 @@ constexpr int64_t hop_row_bytes(int nb, int eb, bool scaled) { return hop_body_b
 // sides, whose staged coefficients already fill the tile) always takes one
 constexpr int hop_tile_rows(int nb, int eb, bool scaled, bool mma) {
   const int step = (32 * kHopConsumerWarps) / hop_nbp(nb);
-  const int two = step * 2 < 32 ? step * 2 : 32;
-  return (!mma && two * hop_row_bytes(nb, eb, scaled) <= kHopTileBytes) ? two : step;
+  const int two = step * kHopPasses < 32 ? step * kHopPasses : 32;
+  return (!mma && two * hop_row_bytes(nb, eb, scaled) <= kHopTileBytes) ? two : (step < 32 ? step : 32);
 }
 
 // staged bytes per tile row for R right-hand sides: the copy row, each right-hand
