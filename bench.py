@@ -354,7 +354,7 @@ def run_gpu(args):
                    "desc": (WORKLOAD_DESC if args.workload == WORKLOAD else args.workload) + "; "
                    + SOLVER_DESC[args.precond],
                    "n_tets": int(m.n_tets), "n_rows": int(mesh.n_rows), "nb": nb, "tol": tol,
-                   "restart": args.restart or 128, "poly_degree": args.poly or (16 if args.precond == "f32" else 32), "precond": args.precond, "l2": "inputs larger than L2 (operator %.0f MB)" % (op.bytes / 1e6),
+                   "restart": args.restart or 128, "poly_degree": args.poly or (16 if args.precond == "f32" else 48), "precond": args.precond, "l2": "inputs larger than L2 (operator %.0f MB)" % (op.bytes / 1e6),
                    "parallelism": f"replicas x{ws}"},
         "roofline": roofline,
         "e2e": e2e,

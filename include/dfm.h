@@ -205,7 +205,7 @@ typedef struct {
                         solve also stops when a restart cycle gains less than 10% */
   int transpose;     /* 1: solve (I - B)^T x = rho0 instead (the adjoint equation) */
   int poly_degree;   /* right preconditioner p(B) = sum_{k<d} B^k, so GMRES runs on I - B^d:
-                        GMRES_IR inner solves: 0 = 16 (32 with a 16-bit precond_precision);
+                        GMRES_IR inner solves: 0 = 16 (48 with a low-precision precond_precision);
                         GMRES on an FP64 operator: 0 = none */
   int precond_precision; /* GMRES_IR: 0 = the polynomial preconditioner uses the operator itself;
                         DFM_F16 or DFM_BF16 = its hops use a 16-bit copy of the blocks (made once
