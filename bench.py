@@ -39,12 +39,12 @@ WORKLOAD_DESC = ("20^3 Kuhn cube x 6 = 48,000 jittered tets (jitter 0.2h, seed 0
                  "mu = 0.05; boundary reflection 0.95; unit isotropic source on the x = 0 face at (0, 1/2, 1/2); "
                  "solve to FP64 relative residual 1e-8")
 SOLVER_DESC = {
-    "f32": "FP64-residual refinement around FP32 GMRES(128) right-preconditioned by sum_{k<16} B^k",
-    "f16": ("FP64-residual refinement around flexible FP32 GMRES(128) right-preconditioned by sum_{k<32} B^k "
+    "f32": "FP64-residual refinement around FP32 GMRES({restart}) right-preconditioned by sum_{{k<{d}}} B^k",
+    "f16": ("FP64-residual refinement around flexible FP32 GMRES({restart}) right-preconditioned by sum_{{k<{d}}} B^k "
             "evaluated on an FP16 copy of the blocks"),
-    "bf16": ("FP64-residual refinement around flexible FP32 GMRES(128) right-preconditioned by sum_{k<32} B^k "
+    "bf16": ("FP64-residual refinement around flexible FP32 GMRES({restart}) right-preconditioned by sum_{{k<{d}}} B^k "
              "evaluated on a BF16 copy of the blocks"),
-    "fp8": ("FP64-residual refinement around flexible FP32 GMRES(128) right-preconditioned by sum_{k<32} B^k "
+    "fp8": ("FP64-residual refinement around flexible FP32 GMRES({restart}) right-preconditioned by sum_{{k<{d}}} B^k "
             "evaluated on an e4m3 copy of the blocks (one FP32 scale per row)"),
 }
 # Operator applications of the FP64 solve on the 20^3 workload: FP64 GMRES(128)
@@ -352,7 +352,8 @@ def run_gpu(args):
         "data": "synthetic",
         "config": {"workload": args.workload,
                    "desc": (WORKLOAD_DESC if args.workload == WORKLOAD else args.workload) + "; "
-                   + SOLVER_DESC[args.precond],
+                   + SOLVER_DESC[args.precond].format(
+                       restart=args.restart or 128, d=args.poly or (16 if args.precond == "f32" else 48)),
                    "n_tets": int(m.n_tets), "n_rows": int(mesh.n_rows), "nb": nb, "tol": tol,
                    "restart": args.restart or 128, "poly_degree": args.poly or (16 if args.precond == "f32" else 48), "precond": args.precond, "l2": "inputs larger than L2 (operator %.0f MB)" % (op.bytes / 1e6),
                    "parallelism": f"replicas x{ws}"},
