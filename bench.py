@@ -644,6 +644,67 @@ def run_batched(args):
                       "dot_ms": dfm.kernel_stats(dfm.KERNEL_DOT)[1], "axpy_ms": dfm.kernel_stats(dfm.KERNEL_AXPY)[1]}))
 
 
+def run_cuboid(args):
+    """Cuboid verification of Sec. 4.1 on the GPU: the Kuhn cuboid
+    (0, 2) x (-1/2, 1/2)^2 with n cells per unit length (n = 4: 768 tets, the
+    size of the paper's 972-tet mesh; n = 8: 6,144 tets), every wall
+    reflecting (r = 1), mu = eta omega / (2c) = 0.4 pi (eta = 0.004,
+    omega = 200 pi, c = 1) and a unit density entering the x = 0 side along
+    its normal (Eq. RhoNeumann).  Each step of a case re-assembles B in FP32,
+    solves to an FP64 relative residual of 1e-10 and reads rho_T at every
+    centroid (Eq. IntDens); the line gives each case's median step time and
+    the relative mean error (mean |rho_T - rho*| / mean rho*) against the
+    exact ray solution rho* of Eq. ExactSol."""
+    import torch
+
+    from paper_1608_04607_gb300 import dfm
+    from paper_1608_04607_gb300.inputs import cuboid_rows_x0, kuhn_cuboid_mesh
+
+    torch.cuda.set_device(0)
+    mu, length = 0.4 * np.pi, 2.0
+    cases = []
+    for n in (4, 8):
+        m = kuhn_cuboid_mesh(n, length=length)
+        mesh = dfm.Mesh(m.verts, m.tets, refl=1.0)
+        rows = cuboid_rows_x0(m)
+        x = m.verts[m.tets].mean(axis=1)[:, 0]
+        exact = (np.exp(-mu * x) + np.exp(-mu * (2 * length - x))) / (1 - np.exp(-2 * mu * length))
+        tets = np.arange(m.n_tets)
+        for Np in (4, 6, 8):
+            op = dfm.Operator(mesh, Np, mu=mu, precision=dfm.F32)
+
+            def step():
+                op.reassemble(mu)
+                rho0 = dfm.source_directed(mesh, Np, rows, combine=True)
+                rho, info = op.solve(rho0, tol=1e-10)
+                g, _ = dfm.interior_density(mesh, Np, tets, mu=mu)
+                return dfm.tet_density(mesh, Np, g, rho), info
+
+            for _ in range(max(args.warmup, 1)):
+                step()
+            times = []
+            for _ in range(max(args.steps, 1)):
+                ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+                torch.cuda.synchronize()
+                ev[0].record()
+                dens, info = step()
+                ev[1].record()
+                torch.cuda.synchronize()
+                times.append(ev[0].elapsed_time(ev[1]))
+            d = dens.cpu().numpy()
+            err = float(np.mean(np.abs(d - exact)) / np.mean(exact))
+            cases.append({"n_tets": m.n_tets, "Np": Np, "ms_per_step": statistics.median(times),
+                          "rel_mean_err": err, "operator_applications": info.iters, "resid": info.resid})
+            op.close()
+        mesh.close()
+    print(json.dumps({"metric": "cuboid relative mean error against the exact ray solution", "mode": "cuboid",
+                      "value": cases[2]["rel_mean_err"], "unit": "fraction", "higher_is_better": False,
+                      "steps": args.steps, "warmup": args.warmup, "data": "synthetic",
+                      "config": {"workload": "kuhn cuboid 2 x 1 x 1, n = 4 and 8 cells per unit length",
+                                 "mu": mu, "refl": 1.0, "source": "normal incidence on x = 0", "tol": 1e-10},
+                      "cases": cases}))
+
+
 def run_many(args):
     """Many-source workload with a 45-function basis: the 32^3 Kuhn cube
     (196,608 tets, Np = 8, mu = 0.05, r = 0.95) with 64 random boundary-face
@@ -841,7 +902,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--ref-apps", type=int, default=0,
                     help="reference arm: operator applications charged per solve (0 = the FP64 path's count)")
-    ap.add_argument("--mode", choices=["solve", "apply", "hop", "adjoint", "batched", "many"], default="solve")
+    ap.add_argument("--mode", choices=["solve", "apply", "hop", "adjoint", "batched", "many", "cuboid"], default="solve")
     ap.add_argument("--rhs", type=int, default=0, help="batched mode: number of right-hand sides (0 = all)")
     ap.add_argument("--batch", type=int, default=0, help="batched mode: right-hand sides per lockstep group")
     ap.add_argument("--fd", type=int, default=0, help="adjoint mode: elements checked by central differences")
@@ -858,6 +919,8 @@ def main():
         run_batched(args)
     elif args.mode == "many":
         run_many(args)
+    elif args.mode == "cuboid":
+        run_cuboid(args)
     else:
         run_gpu(args)
 

@@ -195,6 +195,28 @@ int dfm_apply_combo(const dfm_op* const* ops, int K, const double* coef_host, co
  * [n_src][rows][nb] (fully overwritten).  Asynchronous. */
 int dfm_source(const dfm_mesh* mesh, int Np, const int64_t* rows_host, int n_src, double* rho0, void* stream);
 
+/* Galerkin coefficients of unit boundary densities with one ray direction
+ * (Sec. 4.1, Eq. RhoNeumann, generalised from the normal to any inward d):
+ * the density delta(p - p_d) on face T_row, p_d = (d.e1, d.e2) the
+ * tangential momentum of the unit inward direction d, projects onto
+ *   rho0[row][(n,m)] = N_nm Z_n^m(p_d) sqrt(|T_row|),   N_nm = (2n+2)/(eps_m pi)
+ * (the inverse norm of Z_n^m on the unit disc, eps_0 = 2, eps_m = 1 else).
+ * For d = the inward normal (p_d = 0) only m = 0, n even survive:
+ * (n+1)/pi (-1)^(n/2) sqrt(|T_row|).
+ *   rows_host: HOST int64 [n_src] rows.  dirs_host: HOST FP64 [n_src][3]
+ *   directions (any length > 0; normalised here) or NULL for each row's
+ *   inward normal.  combine = 0: rho0 device FP64 [n_src][rows][nb], source s
+ *   alone in right-hand side s; combine = 1: rho0 device FP64 [rows][nb], all
+ *   sources in one right-hand side (rows must then be distinct).  rho0 is
+ *   fully overwritten.
+ * Asynchronous when dirs_host is NULL; with directions it waits on the stream
+ * and returns DFM_ERR_ARG if some d does not point strictly into its tet
+ * (d.n <= 0 after normalisation), leaving rho0 with that source's row zero.
+ * Errors: DFM_ERR_ARG (NULL, Np outside 0..8, row out of range, zero
+ * direction, repeated row with combine = 1). */
+int dfm_source_directed(const dfm_mesh* mesh, int Np, const int64_t* rows_host, const double* dirs_host, int n_src,
+                        int combine, double* rho0, void* stream);
+
 typedef struct {
   int method;        /* DFM_SOLVE_* */
   double tol;        /* stop when ||rho0 - (I - B) x|| <= tol ||rho0|| (FP64 residual; Neumann: relative increment) */
@@ -274,6 +296,17 @@ int dfm_precond_apply(const dfm_op* op, int precision, int degree, int transpose
  *   mu: device FP64 [n_tets] or NULL for mu_uniform.  Asynchronous. */
 int dfm_interior_density(const dfm_mesh* mesh, int Np, const double* mu, double mu_uniform, const int64_t* tets_host,
                          const double* weights_host, int n, int nq, double* gvec, double* dgvec, void* stream);
+
+/* Per-tet values of a tet-local functional:
+ *   out[r][e] = sum_{l < 4} sum_{nm} gvec[4e+l][nm] rho_r[4e+l][nm].
+ * With gvec from dfm_interior_density over every tet (weights 1), out[r][e]
+ * is the interior density rho_T(r_e) of right-hand side r at tet e's centroid
+ * (Sec. 4.1, Eq. IntDens).
+ *   gvec: device FP64 [rows][nb]; rho: device FP64 [R][rows][nb];
+ *   out: device FP64 [R][n_tets] (overwritten).  Asynchronous.
+ * Errors: DFM_ERR_ARG (NULL, R < 1, Np outside 0..8). */
+int dfm_tet_density(const dfm_mesh* mesh, int Np, const double* gvec, const double* rho, int R, double* out,
+                    void* stream);
 
 /* Adjoint gradient of J = sum_r gvec . rho_r with respect to the per-tet damping
  * (the operator's dependence on mu through exp(-mu L), Sec. 2 and Sec. 3.3):

@@ -337,6 +337,63 @@ def source_vector(verts, tets, rows, Np, weights=None) -> np.ndarray:
     return x
 
 
+def face_frames(verts, tets):
+    """Frame of every row 4t + f (the convention of dfm_oracle.c, Sec. 3.3 leaves
+    it open): origin at the first face vertex v_{f+1}, e1 = unit(v_{f+2} - v_{f+1}),
+    n = unit normal towards v_f, e2 = n x e1.  Returns (e1, e2, n) [rows, 3] each."""
+    nt = tets.shape[0]
+    e1 = np.empty((4 * nt, 3))
+    e2 = np.empty((4 * nt, 3))
+    nn = np.empty((4 * nt, 3))
+    for f in range(4):
+        p0, p1, p2 = (verts[tets[:, (f + 1 + k) % 4]] for k in range(3))
+        apex = verts[tets[:, f]]
+        a = p1 - p0
+        c = np.cross(a, p2 - p0)
+        c *= np.sign(np.einsum("ij,ij->i", c, apex - p0))[:, None]
+        n = c / np.linalg.norm(c, axis=1)[:, None]
+        u = a / np.linalg.norm(a, axis=1)[:, None]
+        e1[f::4], nn[f::4], e2[f::4] = u, n, np.cross(n, u)
+    return e1, e2, nn
+
+
+def source_directed(verts, tets, rows, Np, dirs=None, combine=False) -> np.ndarray:
+    """Galerkin coefficients of a unit density travelling in one direction d on
+    each listed face (Sec. 4.1, Eq. RhoNeumann for d = the inward normal).  The
+    density delta(p - p_d), p_d = (d.e1, d.e2), projected onto the basis of
+    Eq. FBApprox: coefficient (n, m) = (inverse norm N_nm) * <delta, Z_n^m> *
+    <1_T, 1/sqrt|T|> = N_nm Z_n^m(p_d) sqrt|T|.  dirs None = inward normals.
+    Returns [n_src, rows, nb], or [rows, nb] summed when combine is set."""
+    nb = nbasis(Np)
+    rows = np.atleast_1d(np.asarray(rows, dtype=np.int64))
+    area = face_areas(verts, tets)
+    e1, e2, nn = face_frames(verts, tets)
+    inv = zernike_invnorm(Np)
+    out = np.zeros((rows.size, 4 * tets.shape[0], nb))
+    for s, r in enumerate(rows):
+        if dirs is None:
+            p = (0.0, 0.0)
+        else:
+            d = np.asarray(dirs[s], dtype=np.float64)
+            d = d / np.linalg.norm(d)
+            if not d @ nn[r] > 0:
+                raise ValueError("direction does not enter the tet")
+            p = (d @ e1[r], d @ e2[r])
+        out[s, r] = inv * zernike(Np, p[0], p[1])[0] * np.sqrt(area[r])
+    return out.sum(axis=0) if combine else out
+
+
+def tet_density(verts, tets, mu_tet, Np, rho, nq=48) -> np.ndarray:
+    """rho_T at every tet centroid (Sec. 4.1, Eq. IntDens) for rho [rows, nb]:
+    the per-tet functional g_t of interior_g applied to the tet's four rows."""
+    cen = centroids(verts, tets)
+    out = np.empty(tets.shape[0])
+    for t in range(tets.shape[0]):
+        g, _ = interior_g(verts, tets, t, cen[t], float(mu_tet[t]), Np, nq=nq)
+        out[t] = np.sum(g * rho[4 * t:4 * t + 4])
+    return out
+
+
 def solve_dense(op: Operator, rho0: np.ndarray) -> np.ndarray:
     """rho = (I - B)^{-1} rho0 by LU (Eq. GovIE); small meshes."""
     M = np.eye(op.nrows * op.nb) - dense(op)

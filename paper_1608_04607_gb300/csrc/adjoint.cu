@@ -201,6 +201,23 @@ int launch_contract(int Np, const PairConst* pairs, int64_t npairs, const double
   return DFM_OK;
 }
 
+// out[r][e] = sum over tet e's four rows of gvec . rho_r: one warp per (r, e),
+// the lanes striding over the 4 nb contiguous coefficients of the tet
+__global__ void tet_density_kernel(const double* __restrict__ g, const double* __restrict__ rho, int64_t nt,
+                                   int nb, int64_t units, double* __restrict__ out) {
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= units) return;  // blockDim is a multiple of 32: whole warps leave together
+  const int64_t r = w / nt, e = w - r * nt;
+  const double* gp = g + 4 * e * nb;
+  const double* xp = rho + (r * 4 * nt + 4 * e) * nb;
+  double acc = 0.0;
+  for (int k = lane; k < 4 * nb; k += 32) acc = fma(gp[k], xp[k], acc);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) out[w] = acc;
+}
+
 }  // namespace
 }  // namespace dfm
 
@@ -242,6 +259,20 @@ extern "C" int dfm_interior_density(const dfm_mesh* mesh, int Np, const double* 
   DFM_LAUNCHED();
   DFM_CUDA_CHECK(cudaGetLastError());
   DFM_CUDA_CHECK(cudaFreeAsync(buf, st));
+  return DFM_OK;
+}
+
+extern "C" int dfm_tet_density(const dfm_mesh* mesh, int Np, const double* gvec, const double* rho, int R,
+                               double* out, void* stream) {
+  if (!mesh || !gvec || !rho || !out || R < 1 || Np < 0 || Np > 8)
+    return set_error(DFM_ERR_ARG, "dfm_tet_density: bad argument");
+  const int64_t units = (int64_t)R * mesh->nt;
+  const int64_t blocks = (units + 7) / 8;  // 8 warps per block
+  if (blocks > 0x7fffffff) return set_error(DFM_ERR_ARG, "dfm_tet_density: too many right-hand sides");
+  cudaStream_t st = as_stream(stream);
+  tet_density_kernel<<<(unsigned)blocks, 256, 0, st>>>(gvec, rho, mesh->nt, nbasis(Np), units, out);
+  DFM_LAUNCHED();
+  DFM_CUDA_CHECK(cudaGetLastError());
   return DFM_OK;
 }
 

@@ -1,6 +1,6 @@
 // Node arithmetic shared by the assembly and adjoint kernels (Sec. 3.1-3.4):
 // per-pair constants, direction patches, the closed-form spatial integral
-// and the Zernike recursion.  Included by assemble.cu and adjoint.cu; every
+// and the Zernike recursion.  Included by assemble.cu, adjoint.cu and source.cu; every
 // symbol is TU-local (anonymous namespace).
 #pragma once
 

@@ -82,11 +82,13 @@ SIGNATURES = {
     "dfm_op_copy_vals": (_i, [_vp, _vp, _i64, _vp]),
     "dfm_apply": (_i, [_vp, _vp, _vp, _vp, _i, _d, _i, _i, _vp]),
     "dfm_source": (_i, [_vp, _i, _vp, _i, _vp, _vp]),
+    "dfm_source_directed": (_i, [_vp, _i, _vp, _vp, _i, _i, _vp, _vp]),
     "dfm_apply_combo": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _i, _d, _i, _vp]),
     "dfm_precond_apply": (_i, [_vp, _i, _i, _i, _vp, _vp, _i, _vp]),
     "dfm_solve_combo": (_i, [_vp, _i, _vp, _vp, _i, _vp, ctypes.POINTER(SolveOpts), _vp, ctypes.POINTER(SolveInfo)]),
     "dfm_solve": (_i, [_vp, _vp, _i, _vp, ctypes.POINTER(SolveOpts), _vp, ctypes.POINTER(SolveInfo)]),
     "dfm_interior_density": (_i, [_vp, _i, _vp, _d, _vp, _vp, _i, _i, _vp, _vp, _vp]),
+    "dfm_tet_density": (_i, [_vp, _i, _vp, _vp, _i, _vp, _vp]),
     "dfm_adjoint": (_i, [_vp, ctypes.POINTER(Params), _vp, _i, _vp, _vp, _vp, _vp, ctypes.POINTER(SolveOpts), _vp,
                          ctypes.POINTER(SolveInfo)]),
     "dfm_launch_count": (ctypes.c_longlong, []),
@@ -321,6 +323,25 @@ def source(mesh: Mesh, Np: int, rows):
     return out
 
 
+def source_directed(mesh: Mesh, Np: int, rows, dirs=None, combine=False):
+    """Unit densities along one ray direction per row (dfm_source_directed):
+    dirs [n_src, 3] (None = each row's inward normal, Eq. RhoNeumann).  Returns
+    FP64 [n_src, rows, nb], or [rows, nb] with every source in one right-hand
+    side when combine is set."""
+    import torch
+
+    rows = np.ascontiguousarray(np.atleast_1d(rows), dtype=np.int64)
+    dp = None
+    if dirs is not None:
+        d = np.ascontiguousarray(np.asarray(dirs, dtype=np.float64).reshape(rows.size, 3))
+        dp = d.ctypes.data_as(ctypes.c_void_p)
+    shape = (mesh.n_rows, nbasis(Np)) if combine else (rows.size, mesh.n_rows, nbasis(Np))
+    out = torch.empty(shape, dtype=torch.float64, device="cuda")
+    _check(load().dfm_source_directed(mesh.handle, Np, rows.ctypes.data_as(ctypes.c_void_p), dp, rows.size,
+                                      int(bool(combine)), _ptr(out), _stream()), "dfm_source_directed")
+    return out
+
+
 def _op_array(ops):
     arr = (ctypes.c_void_p * len(ops))(*[o.handle.value for o in ops])
     return arr
@@ -393,6 +414,23 @@ def interior_density(mesh: Mesh, Np: int, tets, weights=None, mu=0.0, nq=0, gvec
     _check(load().dfm_interior_density(mesh.handle, Np, mup, muu, tets.ctypes.data_as(ctypes.c_void_p), wp,
                                        tets.size, nq, _ptr(gvec), _ptr(dgvec), _stream()), "dfm_interior_density")
     return gvec, dgvec
+
+
+def tet_density(mesh: Mesh, Np: int, gvec, rho):
+    """Per-tet sums of gvec . rho over each tet's four rows (dfm_tet_density):
+    rho FP64 [R, rows, nb] or [rows, nb]; returns FP64 [R, n_tets] or [n_tets].
+    With gvec from interior_density over all tets this is rho_T at every centroid."""
+    import torch
+
+    nb = nbasis(Np)
+    R = 1 if rho.dim() == 2 else rho.shape[0]
+    if (gvec.dtype != torch.float64 or rho.dtype != torch.float64 or tuple(gvec.shape) != (mesh.n_rows, nb)
+            or tuple(rho.shape[-2:]) != (mesh.n_rows, nb)):
+        raise ValueError("tet_density: gvec [rows, nb] and rho [R, rows, nb] must be FP64")
+    out = torch.empty((R, mesh.n_tets), dtype=torch.float64, device="cuda")
+    _check(load().dfm_tet_density(mesh.handle, Np, _ptr(gvec), _ptr(rho), R, _ptr(out), _stream()),
+           "dfm_tet_density")
+    return out[0] if rho.dim() == 2 else out
 
 
 class DFMSolve:

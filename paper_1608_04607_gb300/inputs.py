@@ -156,6 +156,79 @@ def source_row_minus_x(mesh: KuhnMesh, point_yz=None) -> int:
     raise ValueError("point not on the x = 0 side")
 
 
+@dataclass(frozen=True)
+class KuhnCuboid:
+    """A Kuhn-split box (0, length) x (-1/2, 1/2)^2 of cubic cells of side h = 1/n:
+    nx = round(length n) cells along x, n along y and z, six tets per cell.
+    verts: float64 [nv, 3], vertex (i, j, k) at index i + (nx+1)(j + (n+1)k);
+    tets: int32 [6 nx n^2, 4], positively oriented before jitter."""
+
+    verts: np.ndarray
+    tets: np.ndarray
+    nx: int
+    n: int
+    h: float
+    length: float
+
+    @property
+    def n_tets(self) -> int:
+        return int(self.tets.shape[0])
+
+    @property
+    def n_rows(self) -> int:
+        return 4 * self.n_tets
+
+
+def kuhn_cuboid_mesh(n: int, length: float = 2.0, jitter: float = 0.2, seed: int = 0) -> KuhnCuboid:
+    """The cuboid cavity of the paper's verification (Sec. 4.1), (0, length) x
+    (-1/2, 1/2)^2, as a Kuhn split of cubic cells with interior vertices
+    jittered by U[-jitter h, jitter h] per coordinate (PCG64 seed); boundary
+    vertices stay on the box so its six sides stay planar."""
+    nx = int(round(length * n))
+    if n < 1 or nx < 1:
+        raise ValueError("need at least one cell per axis")
+    h = 1.0 / n
+    dims = np.array([nx, n, n])
+    ii, jj, kk = np.meshgrid(np.arange(nx + 1), np.arange(n + 1), np.arange(n + 1), indexing="ij")
+    g = np.stack([ii.ravel(), jj.ravel(), kk.ravel()], axis=1)
+    g = g[np.lexsort((g[:, 0], g[:, 1], g[:, 2]))]  # index i + (nx+1)(j + (n+1)k)
+    verts = np.stack([g[:, 0] * h, g[:, 1] * h - 0.5, g[:, 2] * h - 0.5], axis=1)
+    ci = np.stack(np.meshgrid(np.arange(nx), np.arange(n), np.arange(n), indexing="ij"), axis=-1).reshape(-1, 3)
+    ci = ci[np.lexsort((ci[:, 0], ci[:, 1], ci[:, 2]))]
+
+    def vid(c):
+        return c[:, 0] + (nx + 1) * (c[:, 1] + (n + 1) * c[:, 2])
+
+    tets = np.empty((ci.shape[0], 6, 4), dtype=np.int64)
+    unit = np.eye(3, dtype=np.int64)
+    for p, perm in enumerate(_PERMS):
+        c1 = ci + unit[perm[0]]
+        c2 = c1 + unit[perm[1]]
+        tets[:, p, :] = np.stack([vid(ci), vid(c1), vid(c2), vid(ci + 1)], axis=1)
+    tets = tets.reshape(-1, 4)
+    a, b, c, d = (verts[tets[:, k]] for k in range(4))
+    neg = np.einsum("ij,ij->i", np.cross(b - a, c - a), d - a) < 0
+    tets[neg, 2], tets[neg, 3] = tets[neg, 3].copy(), tets[neg, 2].copy()
+    if jitter > 0:
+        rng = np.random.Generator(np.random.PCG64(seed))
+        delta = rng.uniform(-jitter * h, jitter * h, size=verts.shape)
+        interior = np.all((g > 0) & (g < dims[None, :]), axis=1)
+        verts = verts + delta * interior[:, None]
+    return KuhnCuboid(verts=np.ascontiguousarray(verts), tets=np.ascontiguousarray(tets.astype(np.int32)),
+                      nx=nx, n=n, h=h, length=float(length))
+
+
+def cuboid_rows_x0(mesh: KuhnCuboid) -> np.ndarray:
+    """Rows 4t + f whose face lies on the x = 0 side of the cuboid, ascending."""
+    i = mesh.tets.astype(np.int64) % (mesh.nx + 1)  # grid index along x of every tet vertex
+    out = []
+    for f in range(4):
+        others = [k for k in range(4) if k != f]
+        t = np.nonzero(np.all(i[:, others] == 0, axis=1))[0]
+        out.append(4 * t + f)
+    return np.sort(np.concatenate(out)).astype(np.int64)
+
+
 def random_boundary_rows(mesh: KuhnMesh, count: int, seed: int = 2) -> np.ndarray:
     """count boundary rows drawn uniformly with replacement (PCG64 seed)."""
     rows = boundary_faces(mesh)[:, 0]

@@ -31,3 +31,21 @@ def test_sources_and_fields_are_reproducible():
     assert abs(np.mean(z)) < 0.5 and 0.3 < np.std(z) < 1.5
     s = I.source_row_minus_x(I.kuhn_cube_mesh(4), (0.5, 0.5))
     assert s in set(I.boundary_faces(I.kuhn_cube_mesh(4))[:, 0])
+
+
+def test_kuhn_cuboid_mesh():
+    from paper_1608_04607_gb300 import inputs as I
+
+    m = I.kuhn_cuboid_mesh(3, length=2.0, jitter=0.2, seed=0)
+    assert (m.nx, m.n, m.n_tets) == (6, 3, 6 * 6 * 9)
+    v, t = m.verts, m.tets
+    a, b, c, d = (v[t[:, k]] for k in range(4))
+    vol = np.einsum("ij,ij->i", np.cross(b - a, c - a), d - a) / 6
+    assert vol.min() > 0 and abs(vol.sum() - 2.0) < 1e-12
+    assert np.allclose(v.min(0), [0, -0.5, -0.5]) and np.allclose(v.max(0), [2, 0.5, 0.5])
+    rows = I.cuboid_rows_x0(m)
+    assert rows.size == 2 * 3 * 3
+    for r in rows:
+        tt, f = divmod(int(r), 4)
+        assert np.all(v[[t[tt, k] for k in range(4) if k != f], 0] == 0.0)
+    assert np.array_equal(I.kuhn_cuboid_mesh(3).verts, m.verts)  # seeded
