@@ -140,6 +140,27 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _vec(t, rows, nb, dtypes, what):
+    """Check a coefficient tensor [R, rows, nb] or [rows, nb] of an allowed dtype
+    before its pointer crosses the ABI (the library cannot see sizes); returns R."""
+    import torch
+
+    if not isinstance(t, torch.Tensor) or t.dtype not in dtypes or t.dim() not in (2, 3) \
+            or tuple(t.shape[-2:]) != (rows, nb):
+        got = (tuple(t.shape), t.dtype) if isinstance(t, torch.Tensor) else type(t).__name__
+        raise DFMError(DFM_ERR_ARG, f"{what}: expected [R, {rows}, {nb}] or [{rows}, {nb}] of "
+                                    f"{'/'.join(str(d) for d in dtypes)}, got {got}")
+    return 1 if t.dim() == 2 else t.shape[0]
+
+
+def _like(t, ref, what):
+    """Check that an optional companion tensor has ref's dtype and shape."""
+    import torch
+
+    if t is not None and (not isinstance(t, torch.Tensor) or t.dtype != ref.dtype or t.shape != ref.shape):
+        raise DFMError(DFM_ERR_ARG, f"{what}: expected {tuple(ref.shape)} {ref.dtype}")
+
+
 def nbasis(Np: int) -> int:
     return (Np + 1) * (Np + 2) // 2
 
@@ -249,8 +270,10 @@ class Operator:
     def apply(self, x, x0=None, alpha=1.0, trans=False, out=None):
         """y = x0 + alpha B x (or B^T x); x of shape [R, rows, nb] or [rows, nb]."""
         torch = self._torch
+        R = _vec(x, self.n_rows, self.nb, (torch.float32, torch.float64), "apply: x")
+        _like(x0, x, "apply: x0")
+        _like(out, x, "apply: out")
         xtype = {torch.float64: F64, torch.float32: F32}[x.dtype]
-        R = 1 if x.dim() == 2 else x.shape[0]
         y = torch.empty_like(x) if out is None else out
         _check(_lib.dfm_apply(self._h, _ptr(x), _ptr(x0), _ptr(y), R, float(alpha), int(bool(trans)), xtype,
                               _stream()), "dfm_apply")
@@ -263,7 +286,8 @@ class Operator:
         torch = self._torch
         if x.dtype != torch.float32:
             raise TypeError("precond: x must be float32")
-        R = 1 if x.dim() == 2 else x.shape[0]
+        R = _vec(x, self.n_rows, self.nb, (torch.float32,), "precond: x")
+        _like(out, x, "precond: out")
         z = torch.empty_like(x) if out is None else out
         _check(_lib.dfm_precond_apply(self._h, int(precision), int(degree), int(bool(transpose)), _ptr(x), _ptr(z), R,
                                       _stream()), "dfm_precond_apply")
@@ -273,7 +297,8 @@ class Operator:
               raise_on_nonconvergence=True, transpose=False, poly_degree=0, batch=0, precond_precision=0):
         """rho = (I - B)^{-1} rho0 (FP64, [R, rows, nb] or [rows, nb]); returns (rho, SolveInfo)."""
         torch = self._torch
-        R = 1 if rho0.dim() == 2 else rho0.shape[0]
+        R = _vec(rho0, self.n_rows, self.nb, (torch.float64,), "solve: rho0")
+        _like(x0, rho0, "solve: x0")
         rho = torch.empty_like(rho0) if x0 is None else x0.clone()
         o = SolveOpts(method=method, tol=tol, max_iter=max_iter, restart=restart, use_x0=int(x0 is not None),
                       inner_tol=inner_tol, transpose=int(bool(transpose)), poly_degree=poly_degree,
@@ -290,7 +315,10 @@ class Operator:
         """lambda = (I - B)^{-T} gvec and dJ/dmu for J = sum_r gvec . rho_r (dfm_adjoint).
         rho: FP64 [R, rows, nb]; gvec/dgvec: FP64 [rows, nb].  Returns (lambda, dJ_dmu [R, n_tets], info)."""
         torch = self._torch
-        R = 1 if rho.dim() == 2 else rho.shape[0]
+        R = _vec(rho, self.n_rows, self.nb, (torch.float64,), "adjoint: rho")
+        if _vec(gvec, self.n_rows, self.nb, (torch.float64,), "adjoint: gvec") != 1 or gvec.dim() != 2:
+            raise DFMError(DFM_ERR_ARG, "adjoint: gvec must be [rows, nb]")
+        _like(dgvec, gvec, "adjoint: dgvec")
         lam = torch.empty((self.n_rows, self.nb), dtype=torch.float64, device="cuda")
         dj = torch.empty((R, self.mesh.n_tets), dtype=torch.float64, device="cuda")
         o = SolveOpts(method=method, tol=tol, max_iter=max_iter, restart=restart, use_x0=0, inner_tol=inner_tol,
@@ -352,8 +380,11 @@ def apply_combo(ops, coef, x, x0=None, alpha=1.0, out=None):
     import torch
 
     coef = np.ascontiguousarray(coef, dtype=np.float64)
-    R = 1 if x.dim() == 2 else x.shape[0]
-    assert coef.shape == (R, len(ops))
+    R = _vec(x, ops[0].n_rows, ops[0].nb, (torch.float32, torch.float64), "apply_combo: x")
+    _like(x0, x, "apply_combo: x0")
+    _like(out, x, "apply_combo: out")
+    if coef.shape != (R, len(ops)):
+        raise DFMError(DFM_ERR_ARG, f"apply_combo: coef must be [{R}, {len(ops)}]")
     xtype = {torch.float64: F64, torch.float32: F32}[x.dtype]
     y = torch.empty_like(x) if out is None else out
     _check(load().dfm_apply_combo(_op_array(ops), len(ops), coef.ctypes.data_as(ctypes.c_void_p), _ptr(x), _ptr(x0),
@@ -367,7 +398,9 @@ def solve_combo(ops, coef, rho0, tol=1e-8, max_iter=0, restart=0, inner_tol=0.0,
     import torch
 
     coef = np.ascontiguousarray(coef, dtype=np.float64)
-    R = 1 if rho0.dim() == 2 else rho0.shape[0]
+    R = _vec(rho0, ops[0].n_rows, ops[0].nb, (torch.float64,), "solve_combo: rho0")
+    if coef.shape != (R, len(ops)):
+        raise DFMError(DFM_ERR_ARG, f"solve_combo: coef must be [{R}, {len(ops)}]")
     rho = torch.empty_like(rho0)
     o = SolveOpts(method=GMRES_IR, tol=tol, max_iter=max_iter, restart=restart, use_x0=0, inner_tol=inner_tol,
                   transpose=0, poly_degree=poly_degree, batch=batch, precond_precision=precond_precision)
@@ -401,6 +434,9 @@ def interior_density(mesh: Mesh, Np: int, tets, weights=None, mu=0.0, nq=0, gvec
         gvec = torch.zeros((mesh.n_rows, nb), dtype=torch.float64, device="cuda")
     if dgvec is None:
         dgvec = torch.zeros((mesh.n_rows, nb), dtype=torch.float64, device="cuda")
+    for t, what in ((gvec, "interior_density: gvec"), (dgvec, "interior_density: dgvec")):
+        if _vec(t, mesh.n_rows, nb, (torch.float64,), what) != 1 or t.dim() != 2:
+            raise DFMError(DFM_ERR_ARG, f"{what} must be [rows, nb]")
     wp = None
     if weights is not None:
         w = np.ascontiguousarray(np.broadcast_to(np.asarray(weights, dtype=np.float64), tets.shape))
@@ -423,10 +459,9 @@ def tet_density(mesh: Mesh, Np: int, gvec, rho):
     import torch
 
     nb = nbasis(Np)
-    R = 1 if rho.dim() == 2 else rho.shape[0]
-    if (gvec.dtype != torch.float64 or rho.dtype != torch.float64 or tuple(gvec.shape) != (mesh.n_rows, nb)
-            or tuple(rho.shape[-2:]) != (mesh.n_rows, nb)):
-        raise ValueError("tet_density: gvec [rows, nb] and rho [R, rows, nb] must be FP64")
+    R = _vec(rho, mesh.n_rows, nb, (torch.float64,), "tet_density: rho")
+    if _vec(gvec, mesh.n_rows, nb, (torch.float64,), "tet_density: gvec") != 1 or gvec.dim() != 2:
+        raise DFMError(DFM_ERR_ARG, "tet_density: gvec must be [rows, nb]")
     out = torch.empty((R, mesh.n_tets), dtype=torch.float64, device="cuda")
     _check(load().dfm_tet_density(mesh.handle, Np, _ptr(gvec), _ptr(rho), R, _ptr(out), _stream()),
            "dfm_tet_density")
