@@ -584,6 +584,46 @@ def run_hop(args):
                       "frac": ach / float(peaks.get("hbm_gbs", HBM_PEAK_FALLBACK)), "peak_source": src}))
 
 
+def fp64_sample(dfm, mesh, Np, mus, rows, tol, per_rhs_assembly):
+    """The plain FP64 GPU path on a sample of a multi-source workload: FP64
+    blocks and FP64 GMRES(128) with sum_{k<16} B^k (the settings of the
+    single-source comparator), one solve per source, to the same residual.
+    With per_rhs_assembly every source has its own damping, so its FP64
+    operator is assembled inside the timed region, as the mixed-precision
+    step assembles its moments; otherwise one operator serves all sources and
+    only the solves are timed.  The first source is solved once untimed."""
+    import torch
+
+    shared = None if per_rhs_assembly else dfm.Operator(mesh, Np, mu=float(mus[0]), precision=dfm.F64)
+
+    def one(mu, row):
+        op = dfm.Operator(mesh, Np, mu=float(mu), precision=dfm.F64) if per_rhs_assembly else shared
+        rho, info = op.solve(dfm.source(mesh, Np, [int(row)]), method=dfm.GMRES, tol=tol, poly_degree=16,
+                             restart=128)
+        if per_rhs_assembly:
+            op.close()
+        return info
+
+    one(mus[0], rows[0])
+    times, apps = [], []
+    for mu, row in zip(mus, rows):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        torch.cuda.synchronize()
+        ev[0].record()
+        info = one(mu, row)
+        ev[1].record()
+        torch.cuda.synchronize()
+        times.append(ev[0].elapsed_time(ev[1]))
+        apps.append(int(info.iters))
+    if shared is not None:
+        shared.close()
+    ms = sum(times)
+    return {"value": len(times) / (ms * 1e-3), "unit": "solves/s", "ms_per_solve": ms / len(times),
+            "sample": f"the first {len(times)} sources", "operator_applications": apps,
+            "assembly_in_timed_region": bool(per_rhs_assembly),
+            "desc": "FP64 blocks, FP64 GMRES(128) with sum_{k<16} B^k, same tolerance"}
+
+
 def run_batched(args):
     """Batched workload: 128 right-hand sides (random boundary-face sources) on
     the 30^3 Kuhn cube (162,000 tets, Np = 4), each with its own uniform damping
@@ -636,12 +676,19 @@ def run_batched(args):
     n_sp, ms_sp = dfm.kernel_stats(dfm.KERNEL_SPMV)
     n_as, ms_as = dfm.kernel_stats(dfm.KERNEL_ASSEMBLE)
     n_hop, ms_hop = dfm.kernel_stats(dfm.KERNEL_SPMV16)
-    print(json.dumps({"mode": "batched", "workload": wname, "n_tets": int(m.n_tets), "rhs": R, "K": K,
-                      "value": R / (ms * 1e-3), "unit": "solves/s", "ms_per_step": ms, "precond": args.precond,
-                      "operator_passes": info.iters, "resid_worst": info.resid,
-                      "assembly_ms": ms_as, "combo_launches": n_sp, "combo_ms": ms_sp,
-                      "hop_launches": n_hop, "hop_ms": ms_hop,
-                      "dot_ms": dfm.kernel_stats(dfm.KERNEL_DOT)[1], "axpy_ms": dfm.kernel_stats(dfm.KERNEL_AXPY)[1]}))
+    res = {"mode": "batched", "workload": wname, "n_tets": int(m.n_tets), "rhs": R, "K": K,
+           "value": R / (ms * 1e-3), "unit": "solves/s", "ms_per_step": ms, "precond": args.precond,
+           "operator_passes": info.iters, "resid_worst": info.resid,
+           "assembly_ms": ms_as, "combo_launches": n_sp, "combo_ms": ms_sp,
+           "hop_launches": n_hop, "hop_ms": ms_hop,
+           "dot_ms": dfm.kernel_stats(dfm.KERNEL_DOT)[1], "axpy_ms": dfm.kernel_stats(dfm.KERNEL_AXPY)[1]}
+    if args.fp64_sample:
+        for o in ops:
+            o.close()
+        del rho
+        n = min(args.fp64_sample, R)
+        res["fp64_comparator"] = fp64_sample(dfm, mesh, Np, mu_rhs[:n], rows[:n], tol, per_rhs_assembly=True)
+    print(json.dumps(res))
 
 
 def run_cuboid(args):
@@ -792,14 +839,21 @@ def run_many(args):
         n, ms = ks[k2]
         if n:
             kern[k2] = {"launches": n, "ms_total": ms}
-    print(json.dumps({"mode": "many", "workload": wname, "n_tets": int(m.n_tets), "nb": nb, "rhs": R,
-                      "metric": METRIC, "value": R / (solve_ms * 1e-3), "unit": "solves/s",
-                      "assembly_ms": asm_ms, "solve_ms": solve_ms, "adjoint_ms": adj_ms,
-                      "operator_passes": info.iters, "resid_worst": info.resid, "adjoint_passes": ainfo.iters,
-                      "adjoint_resid": ainfo.resid, "restart": restart, "batch": batch, "precond": args.precond,
-                      "poly_degree": poly, "operator_bytes": op.bytes, "J": float((g * rho).sum()),
-                      "grad_abs_max": float(dj.abs().max()), "kernels": kern,
-                      "kernel_ms": {k: round(v[1], 2) for k, v in ks.items()}, "peak_source": peak_src}))
+    res = {"mode": "many", "workload": wname, "n_tets": int(m.n_tets), "nb": nb, "rhs": R,
+           "metric": METRIC, "value": R / (solve_ms * 1e-3), "unit": "solves/s",
+           "assembly_ms": asm_ms, "solve_ms": solve_ms, "adjoint_ms": adj_ms,
+           "operator_passes": info.iters, "resid_worst": info.resid, "adjoint_passes": ainfo.iters,
+           "adjoint_resid": ainfo.resid, "restart": restart, "batch": batch, "precond": args.precond,
+           "poly_degree": poly, "operator_bytes": op.bytes, "J": float((g * rho).sum()),
+           "grad_abs_max": float(dj.abs().max()), "kernels": kern,
+           "kernel_ms": {k: round(v[1], 2) for k, v in ks.items()}, "peak_source": peak_src}
+    if args.fp64_sample:
+        # the BF16 operator and the solutions make room for the 38 GB FP64 operator
+        op.close()
+        del rho, lam
+        n = min(args.fp64_sample, R)
+        res["fp64_comparator"] = fp64_sample(dfm, mesh, Np, [mu] * n, rows[:n], tol, per_rhs_assembly=False)
+    print(json.dumps(res))
 
 
 def run_adjoint(args):
@@ -905,6 +959,8 @@ def main():
     ap.add_argument("--mode", choices=["solve", "apply", "hop", "adjoint", "batched", "many", "cuboid"], default="solve")
     ap.add_argument("--rhs", type=int, default=0, help="batched mode: number of right-hand sides (0 = all)")
     ap.add_argument("--batch", type=int, default=0, help="batched mode: right-hand sides per lockstep group")
+    ap.add_argument("--fp64-sample", type=int, default=0,
+                    help="batched and many modes: time the plain FP64 GPU path on this many sources")
     ap.add_argument("--fd", type=int, default=0, help="adjoint mode: elements checked by central differences")
     args = ap.parse_args()
     if args.impl == "reference":
