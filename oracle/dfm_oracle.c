@@ -309,14 +309,45 @@ double orc_region_cos_measure(const double* V, const int32_t* T, int64_t t, int 
  * source face.  dout (optional): d(block)/d(mu).  regions_mask selects which
  * of the seven direction regions are integrated (0x0F = the four non-empty
  * ones; 0x7F = all seven, for checks). */
+/* Heterogeneous media at the exit face fp (Sec. 3.3): kind 0 = no interface
+ * (constant lambda: transmission with probability 1 in uniform media, or a
+ * boundary reflection with weight r); kind 1 = the part transmitted into the
+ * neighbour, weight lambda_t(d), received with the tangential direction
+ * scaled by c_ratio = c_i / c_j (Snell's law, sin(theta_t) = (c_i/c_j)
+ * sin(theta_r)); kind 2 = the part reflected back into tet t, weight
+ * 1 - lambda_t(d), received on face (t, fp) itself with the specularly
+ * reflected direction (same tangential components).  z_src = z_j, z_dst = z_i
+ * are the impedances rho_f c of the two tets. */
+typedef struct {
+  int kind;
+  double c_ratio, z_src, z_dst;
+} media_t;
+
+/* lambda_t = 4 z_i z_j cos(theta_r) cos(theta_t) / (z_i cos(theta_r) + z_j cos(theta_t))^2,
+ * zero beyond the critical angle (total internal reflection) */
+static double transmission(double cos_r, double c_ratio, double z_src, double z_dst) {
+  double s2 = c_ratio * c_ratio * (1.0 - cos_r * cos_r);
+  if (s2 >= 1.0) return 0.0;
+  double cos_t = sqrt(1.0 - s2);
+  double den = z_dst * cos_r + z_src * cos_t;
+  return 4.0 * z_dst * z_src * cos_r * cos_t / (den * den);
+}
+
+double orc_transmission(double cos_r, double c_ratio, double z_src, double z_dst) {
+  return transmission(cos_r, c_ratio, z_src, z_dst);
+}
+
 static void block_fixed(const double* V, const int32_t* T, int64_t t, int f, int fp, int64_t recv_row,
                         double mu, double lam, int Np, int q, const double* gx, const double* gw, int nq_tri,
-                        const double* tx, const double* tw, int regions_mask, double* out, double* dout) {
+                        const double* tx, const double* tw, int regions_mask, const media_t* md, double* out,
+                        double* dout) {
   int nb = nbasis(Np);
   face_t src, dstf, recv;
   face_of(V, T, t, f, &src);
   face_of(V, T, t, fp, &dstf);
   face_of(V, T, recv_row / 4, (int)(recv_row % 4), &recv);
+  const int kind = md ? md->kind : 0;
+  const double c_ratio = kind == 1 ? md->c_ratio : 1.0;
   const int32_t* tv = T + 4 * t;
   vec3 A = vert(V, tv[fp]);
   vec3 BC[2];
@@ -340,8 +371,14 @@ static void block_fixed(const double* V, const int32_t* T, int64_t t, int f, int
         double dS;
         double S = spatial_clip(&src, dstf.p, dst_n_out, d, mu, nq_tri, tx, tw, &dS, NULL);
         if (S == 0.0 && dS == 0.0) continue;
+        if (kind) {
+          double lt = transmission(-vdot(d, dstf.n), md->c_ratio, md->z_src, md->z_dst);
+          double wl = kind == 1 ? lt : 1.0 - lt;
+          if (wl == 0.0) continue;
+          w *= wl;
+        }
         zern_all(Np, vdot(d, src.e1), vdot(d, src.e2), Zp);
-        zern_all(Np, vdot(d, recv.e1), vdot(d, recv.e2), Zq);
+        zern_all(Np, c_ratio * vdot(d, recv.e1), c_ratio * vdot(d, recv.e2), Zq);
         for (int a = 0; a < nb; ++a) {
           double wa = w * Zq[a];
           for (int b = 0; b < nb; ++b) {
@@ -379,11 +416,12 @@ typedef struct {
  * Adaptive: start at level lev0, double (next level) until the block max-norm
  * change is <= rtol * block max-norm; q_used returns the accepted order (or
  * -order if the top level was reached without meeting rtol). */
-int orc_blocks(const double* V, const int32_t* T, int64_t npairs, const int64_t* tet, const int32_t* f,
-               const int32_t* fp, const int64_t* recv_row, const double* mu, const double* lam, int Np,
-               int nlev, const int* qs, const int* offs, const double* gx, const double* gw, int lev0,
-               double rtol, int tri_lev, int regions_mask, int nthreads, double* out, double* dout,
-               int32_t* q_used) {
+static int blocks_adaptive(const double* V, const int32_t* T, int64_t npairs, const int64_t* tet,
+                           const int32_t* f, const int32_t* fp, const int64_t* recv_row, const double* mu,
+                           const double* lam, const int32_t* kind, const double* c_ratio, const double* z_src,
+                           const double* z_dst, int Np, int nlev, const int* qs, const int* offs,
+                           const double* gx, const double* gw, int lev0, double rtol, int tri_lev,
+                           int regions_mask, int nthreads, double* out, double* dout, int32_t* q_used) {
   int nb = nbasis(Np);
   gl_table G = {nlev, qs, offs, gx, gw};
 #ifdef _OPENMP
@@ -403,15 +441,24 @@ int orc_blocks(const double* V, const int32_t* T, int64_t npairs, const int64_t*
       const double* tw = G.gw + G.offs[tri_lev];
       int nt = G.qs[tri_lev];
       int lev = lev0;
+      media_t mdi;
+      const media_t* md = NULL;
+      if (kind) {
+        mdi.kind = kind[i];
+        mdi.c_ratio = c_ratio[i];
+        mdi.z_src = z_src[i];
+        mdi.z_dst = z_dst[i];
+        md = &mdi;
+      }
       block_fixed(V, T, tet[i], f[i], fp[i], recv_row[i], mu[i], lam[i], Np, G.qs[lev], G.gx + G.offs[lev],
-                  G.gw + G.offs[lev], nt, tx, tw, regions_mask, o, od);
+                  G.gw + G.offs[lev], nt, tx, tw, regions_mask, md, o, od);
       int accepted = rtol > 0 ? -G.qs[lev] : G.qs[lev];
       while (rtol > 0 && lev + 1 < G.nlev) {
         memcpy(prev, o, sizeof(double) * nb * nb);
         if (od) memcpy(prevd, od, sizeof(double) * nb * nb);
         ++lev;
         block_fixed(V, T, tet[i], f[i], fp[i], recv_row[i], mu[i], lam[i], Np, G.qs[lev], G.gx + G.offs[lev],
-                    G.gw + G.offs[lev], nt, tx, tw, regions_mask, o, od);
+                    G.gw + G.offs[lev], nt, tx, tw, regions_mask, md, o, od);
         double dmax = 0.0, bmax = 0.0, ddmax = 0.0, dbmax = 0.0;
         for (int k = 0; k < nb * nb; ++k) {
           dmax = fmax(dmax, fabs(o[k] - prev[k]));
@@ -435,6 +482,26 @@ int orc_blocks(const double* V, const int32_t* T, int64_t npairs, const int64_t*
   return 0;
 }
 
+int orc_blocks(const double* V, const int32_t* T, int64_t npairs, const int64_t* tet, const int32_t* f,
+               const int32_t* fp, const int64_t* recv_row, const double* mu, const double* lam, int Np,
+               int nlev, const int* qs, const int* offs, const double* gx, const double* gw, int lev0,
+               double rtol, int tri_lev, int regions_mask, int nthreads, double* out, double* dout,
+               int32_t* q_used) {
+  return blocks_adaptive(V, T, npairs, tet, f, fp, recv_row, mu, lam, NULL, NULL, NULL, NULL, Np, nlev, qs, offs,
+                         gx, gw, lev0, rtol, tri_lev, regions_mask, nthreads, out, dout, q_used);
+}
+
+/* As orc_blocks, with per-pair media (kind, c_ratio, z_src, z_dst; see media_t). */
+int orc_blocks_media(const double* V, const int32_t* T, int64_t npairs, const int64_t* tet, const int32_t* f,
+                     const int32_t* fp, const int64_t* recv_row, const double* mu, const double* lam,
+                     const int32_t* kind, const double* c_ratio, const double* z_src, const double* z_dst, int Np,
+                     int nlev, const int* qs, const int* offs, const double* gx, const double* gw, int lev0,
+                     double rtol, int tri_lev, int regions_mask, int nthreads, double* out, double* dout,
+                     int32_t* q_used) {
+  return blocks_adaptive(V, T, npairs, tet, f, fp, recv_row, mu, lam, kind, c_ratio, z_src, z_dst, Np, nlev, qs,
+                         offs, gx, gw, lev0, rtol, tri_lev, regions_mask, nthreads, out, dout, q_used);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Monte Carlo ray tracing of one block (brute-force pin)                   */
 /* ------------------------------------------------------------------------ */
@@ -451,9 +518,12 @@ static double urand(uint64_t* s) { return (splitmix64(s) >> 11) * (1.0 / 9007199
  * error, from nsamp samples: s uniform on face f, p uniform on the unit disc
  * (a cosine-weighted inward direction), the ray traced to the face it leaves
  * through; B = lam N_{n'm'} pi sqrt(A_l/A_l') E[Z(p') Z(p) exp(-mu L) 1{exit=l'}]. */
-int orc_mc_block(const double* V, const int32_t* T, int64_t t, int f, int fp, int64_t recv_row, double mu,
-                 double lam, int Np, int64_t nsamp, uint64_t seed, int nthreads, double* mean, double* stderr_) {
+static int mc_block(const double* V, const int32_t* T, int64_t t, int f, int fp, int64_t recv_row, double mu,
+                    double lam, const media_t* md, int Np, int64_t nsamp, uint64_t seed, int nthreads, double* mean,
+                    double* stderr_) {
   int nb = nbasis(Np);
+  const int kind = md ? md->kind : 0;
+  const double c_ratio = kind == 1 ? md->c_ratio : 1.0;
   face_t src, recv, faces[4];
   face_of(V, T, t, f, &src);
   face_of(V, T, recv_row / 4, (int)(recv_row % 4), &recv);
@@ -503,8 +573,12 @@ int orc_mc_block(const double* V, const int32_t* T, int64_t t, int f, int fp, in
         }
         if (ex != fp) continue;
         double e = exp(-mu * L);
+        if (kind) {
+          double lt = transmission(-vdot(d, faces[fp].n), md->c_ratio, md->z_src, md->z_dst);
+          e *= kind == 1 ? lt : 1.0 - lt;
+        }
         zern_all(Np, px, py, Zp);
-        zern_all(Np, vdot(d, recv.e1), vdot(d, recv.e2), Zq);
+        zern_all(Np, c_ratio * vdot(d, recv.e1), c_ratio * vdot(d, recv.e2), Zq);
         for (int a = 0; a < nb; ++a)
           for (int b = 0; b < nb; ++b) {
             double x = Zq[a] * Zp[b] * e;
@@ -535,6 +609,20 @@ int orc_mc_block(const double* V, const int32_t* T, int64_t t, int f, int fp, in
   free(S1);
   free(S2);
   return 0;
+}
+
+int orc_mc_block(const double* V, const int32_t* T, int64_t t, int f, int fp, int64_t recv_row, double mu,
+                 double lam, int Np, int64_t nsamp, uint64_t seed, int nthreads, double* mean, double* stderr_) {
+  return mc_block(V, T, t, f, fp, recv_row, mu, lam, NULL, Np, nsamp, seed, nthreads, mean, stderr_);
+}
+
+/* As orc_mc_block, with the media of the exit face (see media_t): the traced
+ * ray is weighted by lambda_t(d) (kind 1) or 1 - lambda_t(d) (kind 2). */
+int orc_mc_block_media(const double* V, const int32_t* T, int64_t t, int f, int fp, int64_t recv_row, double mu,
+                       int kind, double c_ratio, double z_src, double z_dst, int Np, int64_t nsamp, uint64_t seed,
+                       int nthreads, double* mean, double* stderr_) {
+  media_t md = {kind, c_ratio, z_src, z_dst};
+  return mc_block(V, T, t, f, fp, recv_row, mu, 1.0, &md, Np, nsamp, seed, nthreads, mean, stderr_);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -49,6 +49,8 @@ def lib():
         L.orc_blocks.restype = ctypes.c_int
         L.orc_mc_block.restype = ctypes.c_int
         L.orc_region_cos_measure.restype = ctypes.c_double
+        L.orc_transmission.restype = ctypes.c_double
+        L.orc_transmission.argtypes = [ctypes.c_double] * 4
         _lib = L
     return _lib
 
@@ -189,6 +191,12 @@ class Operator:
     dest: np.ndarray
     dblocks: np.ndarray | None = None
     q_used: np.ndarray | None = None
+    # heterogeneous media (Sec. 3.3): rblocks[J, k] is the part of the flux of
+    # column J that an interface between unequal media reflects back into the
+    # column's own tet, received by rdest[J, k] = 4t + fp (zero blocks on the
+    # boundary, where blocks already hold the reflection)
+    rblocks: np.ndarray | None = None
+    rdest: np.ndarray | None = None
 
     @property
     def nb(self):
@@ -259,6 +267,90 @@ def assemble(verts, tets, mu_tet, refl, Np, q=None, rtol=1e-13, with_derivative=
                     dblocks=None if dout is None else dout.reshape(4 * nt, 3, nb, nb), q_used=qu)
 
 
+def transmission(cos_r, c_ratio, z_src, z_dst) -> float:
+    """Acoustic transmission probability across an interface (Sec. 3.3):
+    lambda_t = 4 z_i z_j cos(theta_r) cos(theta_t) / (z_i cos(theta_r) + z_j cos(theta_t))^2
+    with sin(theta_t) = (c_i / c_j) sin(theta_r) (Snell's law), zero beyond the
+    critical angle; j is the tet the ray leaves (z_src), i the one it enters."""
+    return float(lib().orc_transmission(cos_r, c_ratio, z_src, z_dst))
+
+
+def assemble_media(verts, tets, mu_tet, c_tet, rhof_tet, refl, Np, q=None, rtol=1e-13, topo=None,
+                   nthreads=0) -> Operator:
+    """B for heterogeneous media (Sec. 3.2 Eq. B4DInt with the transmission
+    law of Sec. 3.3): per-tet propagation speed c and fluid density rho_f
+    (impedance z = rho_f c).  A ray leaving tet j through an interior face
+    enters the neighbour i with probability lambda_t(theta_r), its tangential
+    direction scaled by c_i / c_j (the receiving Zernike argument is the
+    transmitted direction rescaled to the unit disc), and returns into tet j
+    by specular reflection with probability 1 - lambda_t (rblocks, received by
+    the exit face's own row).  Boundary faces reflect with weight r as in
+    assemble.  With equal media everywhere this is assemble's operator and the
+    rblocks vanish."""
+    G = gl_table()
+    topo = topo or topology(tets)
+    verts = np.ascontiguousarray(verts, dtype=np.float64)
+    tets = np.ascontiguousarray(tets, dtype=np.int32)
+    nt = tets.shape[0]
+    t, f, fp = pair_list(nt)
+    recv = np.ascontiguousarray(topo.recv[4 * t + fp], dtype=np.int64)
+    bnd = topo.boundary[recv]
+    c_tet = np.broadcast_to(np.asarray(c_tet, dtype=np.float64), (nt,))
+    z_tet = c_tet * np.broadcast_to(np.asarray(rhof_tet, dtype=np.float64), (nt,))
+    i = recv // 4
+    mu = np.ascontiguousarray(np.asarray(mu_tet, dtype=np.float64)[t])
+    refl_row = np.broadcast_to(np.asarray(refl, dtype=np.float64), (4 * nt,))
+    nb = nbasis(Np)
+    if q is not None:
+        lev0, rtol = list(G.qs).index(q), 0.0
+    else:
+        lev0 = 1
+    tri_lev = list(G.qs).index(TRI_ORDER)
+
+    def run(sel, rows, kind, lam):
+        n = int(np.count_nonzero(sel))
+        out = np.zeros((n, nb, nb))
+        qu = np.empty(n, dtype=np.int32)
+        if n == 0:
+            return out, qu
+        a = lambda v, dt=np.float64: np.ascontiguousarray(np.asarray(v)[sel], dtype=dt)  # noqa: E731
+        lib().orc_blocks_media(_p(verts), _p(tets, _i32p), ctypes.c_int64(n), _p(a(t, np.int64), _i64p),
+                               _p(a(f, np.int32), _i32p), _p(a(fp, np.int32), _i32p), _p(a(rows, np.int64), _i64p),
+                               _p(a(mu)), _p(a(lam)), _p(a(kind, np.int32), _i32p), _p(a(c_tet[i] / c_tet[t])),
+                               _p(a(z_tet[t])), _p(a(z_tet[i])), ctypes.c_int(Np), ctypes.c_int(len(GL_ORDERS)),
+                               _p(G.qs, _i32p), _p(G.offs, _i32p), _p(G.x), _p(G.w), ctypes.c_int(lev0),
+                               ctypes.c_double(rtol), ctypes.c_int(tri_lev), ctypes.c_int(0x0F),
+                               ctypes.c_int(nthreads), _p(out), None, _p(qu, _i32p))
+        return out, qu
+
+    everything = np.ones(t.size, dtype=bool)
+    lam = np.where(bnd, refl_row[recv], 1.0)
+    kind = np.where(bnd, 0, 1)
+    b1, q1 = run(everything, recv, kind, lam)
+    rb = np.zeros((t.size, nb, nb))
+    b2, _ = run(~bnd, 4 * t + fp, np.full(t.size, 2), np.ones(t.size))
+    rb[~bnd] = b2
+    return Operator(Np=Np, blocks=b1.reshape(4 * nt, 3, nb, nb), dest=recv.reshape(4 * nt, 3), q_used=q1,
+                    rblocks=rb.reshape(4 * nt, 3, nb, nb), rdest=(4 * t + fp).reshape(4 * nt, 3))
+
+
+def mc_block_media(verts, tets, t, f, fp, recv_row, mu, kind, c_ratio, z_src, z_dst, Np, nsamp=10 ** 7, seed=1,
+                   nthreads=0):
+    """Monte Carlo ray tracing of one block across an interface (kind 1: the
+    transmitted part, received by recv_row; kind 2: the reflected part, received
+    by row 4t + fp): (mean, standard error)."""
+    nb = nbasis(Np)
+    mean = np.empty((nb, nb))
+    se = np.empty((nb, nb))
+    lib().orc_mc_block_media(_p(np.ascontiguousarray(verts, dtype=np.float64)),
+                             _p(np.ascontiguousarray(tets, dtype=np.int32), _i32p), ctypes.c_int64(t),
+                             ctypes.c_int(f), ctypes.c_int(fp), ctypes.c_int64(recv_row), ctypes.c_double(mu),
+                             ctypes.c_int(kind), ctypes.c_double(c_ratio), ctypes.c_double(z_src),
+                             ctypes.c_double(z_dst), ctypes.c_int(Np), ctypes.c_int64(nsamp), ctypes.c_uint64(seed),
+                             ctypes.c_int(nthreads), _p(mean), _p(se))
+    return mean, se
+
+
 def region_cos_measure(verts, tets, t, f, fp, region, q=32):
     """Int cos(theta) dw over one of the seven direction regions by quadrature."""
     x, w = np.polynomial.legendre.leggauss(q)
@@ -308,6 +400,13 @@ def apply(op: Operator, x: np.ndarray, trans: bool = False, x0=None, alpha=1.0, 
     x0p = None if x0 is None else _p(np.ascontiguousarray(x0, dtype=np.float64).reshape(op.nrows, nb))
     lib().orc_apply(ctypes.c_int64(op.nrows), ctypes.c_int(nb), _p(blocks), _p(dest, _i64p), _p(x), x0p,
                     ctypes.c_double(alpha), ctypes.c_int(1 if trans else 0), ctypes.c_int(nthreads), _p(y))
+    if op.rblocks is not None:
+        rb = np.ascontiguousarray(op.rblocks)
+        rd = np.ascontiguousarray(op.rdest, dtype=np.int64)
+        y2 = np.empty_like(x)
+        lib().orc_apply(ctypes.c_int64(op.nrows), ctypes.c_int(nb), _p(rb), _p(rd, _i64p), _p(x), _p(y),
+                        ctypes.c_double(alpha), ctypes.c_int(1 if trans else 0), ctypes.c_int(nthreads), _p(y2))
+        y = y2
     return y
 
 
@@ -320,6 +419,9 @@ def dense(op: Operator) -> np.ndarray:
         for k in range(3):
             R = int(op.dest[J, k])
             M[R * nb:(R + 1) * nb, J * nb:(J + 1) * nb] += op.blocks[J, k]
+            if op.rblocks is not None:
+                R = int(op.rdest[J, k])
+                M[R * nb:(R + 1) * nb, J * nb:(J + 1) * nb] += op.rblocks[J, k]
     return M
 
 
