@@ -867,8 +867,9 @@ int solve_impl(const dfm_op* op, const dfm_op* const* combo, int K, const double
   const int max_iter = opts->max_iter > 0 ? opts->max_iter : 20000;
   const int m = opts->restart > 0 ? std::min(opts->restart, kMaxKrylov) : 128;
   const double inner_tol = opts->inner_tol > 0 ? opts->inner_tol : 1e-6;
-  // default degree: 32 when the hops run on the 16-bit copy (half the bytes
-  // per hop moves the balance between hops and Gram-Schmidt work), else 16
+  // default degree: 48 when the hops run on a low-precision copy (a half or a
+  // quarter of the bytes per hop moves the balance between hops and
+  // Gram-Schmidt work towards more hops per Krylov step), else 16
   const int poly = opts->poly_degree > 0 ? std::min(opts->poly_degree, 64) : (opts->precond_precision ? 48 : 16);
   // with combined operators the preconditioner's copy is made from ops[0]
   // (B_0, e.g. B(mu_c)): one p(B~_0) serves every right-hand side's B_r
