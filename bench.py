@@ -488,6 +488,9 @@ def run_reference(args):
     # times the oracle on a bounded sample (assembly of random face pairs and
     # full-size GMRES iterations) and extrapolates to the whole solve with the
     # FP64 path's application count
+    from paper_1608_04607_gb300.inputs import workload
+
+    wl = workload(args.workload)
     apps = args.ref_apps or REF_APPLICATIONS.get(args.workload, 2000)
     vals = []
     last = None
@@ -502,7 +505,9 @@ def run_reference(args):
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": args.workload,
                       "desc": (WORKLOAD_DESC if args.workload == WORKLOAD else args.workload)
-                      + "; FP64 CPU oracle (adaptive assembly to 1e-13, restarted GMRES), timed on a bounded sample"},
+                      + "; FP64 CPU oracle (adaptive assembly to 1e-13, restarted GMRES), timed on a bounded sample",
+                      "n_tets": int(wl["mesh"].n_tets), "n_rows": int(wl["mesh"].n_rows),
+                      "nb": (wl["Np"] + 1) * (wl["Np"] + 2) // 2, "tol": args.tol or wl["tol"]},
            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": last[1], "kind": "oracle", "sample": last[0]},
            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(res))
