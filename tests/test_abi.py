@@ -30,3 +30,30 @@ def test_library_exports_every_declared_symbol():
     # the binding covers the whole header
     assert set(declared_functions()) == set(dfm.SIGNATURES)
     assert lib.dfm_version
+
+
+def test_null_handles_are_rejected_on_the_host():
+    """Argument checks run before any CUDA call: NULL handles and empty counts
+    come back as DFM_ERR_ARG with a message, here without a GPU."""
+    from paper_1608_04607_gb300 import dfm
+
+    L = dfm.load()
+    ARG = dfm.DFM_ERR_ARG
+    one = (ctypes.c_int64 * 1)(0)
+    calls = {
+        "dfm_source": lambda: L.dfm_source(None, 2, one, 1, None, None),
+        "dfm_source_directed": lambda: L.dfm_source_directed(None, 2, one, None, 1, 0, None, None),
+        "dfm_tet_density": lambda: L.dfm_tet_density(None, 2, None, None, 1, None, None),
+        "dfm_interior_density": lambda: L.dfm_interior_density(None, 2, None, 0.0, one, None, 1, 0, None, None,
+                                                               None),
+        "dfm_apply": lambda: L.dfm_apply(None, None, None, None, 1, 1.0, 0, dfm.F32, None),
+        "dfm_precond_apply": lambda: L.dfm_precond_apply(None, dfm.F16, 4, 0, None, None, 1, None),
+        "dfm_solve": lambda: L.dfm_solve(None, None, 1, None, None, None, None),
+        "dfm_solve_combo": lambda: L.dfm_solve_combo(None, 0, None, None, 1, None, None, None, None),
+        "dfm_adjoint": lambda: L.dfm_adjoint(None, None, None, 1, None, None, None, None, None, None, None),
+        "dfm_op_info": lambda: L.dfm_op_info(None, None),
+        "dfm_mesh_info": lambda: L.dfm_mesh_info(None, None),
+    }
+    for name, call in calls.items():
+        assert call() == ARG, name
+        assert L.dfm_last_error().decode().startswith(name), (name, L.dfm_last_error())
