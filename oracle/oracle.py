@@ -485,6 +485,59 @@ def source_directed(verts, tets, rows, Np, dirs=None, combine=False) -> np.ndarr
     return out.sum(axis=0) if combine else out
 
 
+def point_source(verts, tets, r0, Np, mu_tet, refl, strength=1.0, nq=48, topo=None) -> np.ndarray:
+    """Galerkin coefficients of a point source at r0 (Sec. 4.2, Eq. SourceRho)
+    in uniform media.  Rays leave r0 in every direction, cross the tet that
+    holds them and enter the next tet through a face F that does not contain
+    r0; on F the density is strength * cos(theta) exp(-mu R) / R^2 times a
+    delta at the ray's inward direction u = unit(s - r0), R = |s - r0|, theta
+    the angle between u and the receiving face's inward normal (Eq. SourceRho
+    with strength = rho_f omega^2 / (16 pi^2 c); the paper writes the
+    direction from the source's side, r0 - s, in that tet's own frame).  It
+    is received by the row across F (the neighbour's face), or by F's own row
+    with weight r and the specularly reflected direction (same tangential
+    components) on the boundary.  Projection onto the basis of Eq. FBApprox:
+        a[row][(n,m)] = N_nm / sqrt|F| Int_F strength cos exp(-mu R)/R^2 Z_n^m(p(u)) ds
+    by collapsed tensor Gauss-Legendre of order nq.  r0 inside a tet uses its
+    four faces; r0 on a face, an edge or at a vertex uses, in every tet whose
+    closure holds it, the faces that do not contain it.  [nrows, nb]."""
+    topo = topo or topology(tets)
+    nt = tets.shape[0]
+    nb = nbasis(Np)
+    inv = zernike_invnorm(Np)
+    e1, e2, nn = face_frames(verts, tets)
+    area = face_areas(verts, tets)
+    refl_row = np.broadcast_to(np.asarray(refl, dtype=np.float64), (4 * nt,))
+    mu_tet = np.broadcast_to(np.asarray(mu_tet, dtype=np.float64), (nt,))
+    r0 = np.asarray(r0, dtype=np.float64)
+    gx, gw = np.polynomial.legendre.leggauss(nq)
+    u = 0.5 * (1 + gx)[:, None] * np.ones(nq)[None, :]
+    v = (1 - u) * 0.5 * (1 + gx)[None, :]
+    wq = (gw[:, None] * gw[None, :]) * 0.25 * (1 - u)  # x 2|F| below
+    out = np.zeros((4 * nt, nb))
+    for k in range(nt):
+        P = verts[tets[k]]
+        lam = np.linalg.solve(np.vstack([P.T, np.ones(4)]), np.append(r0, 1.0))  # barycentric coordinates
+        if lam.min() < -1e-12:
+            continue
+        for l in range(4):
+            if lam[l] <= 1e-12:  # r0 lies on face l (opposite vertex l)
+                continue
+            row = 4 * k + l
+            rec = int(topo.recv[row])
+            wgt = refl_row[row] if topo.boundary[row] else 1.0
+            p0, p1, p2 = (verts[tets[k, (l + 1 + i) % 4]] for i in range(3))
+            s = p0 + u[..., None] * (p1 - p0) + v[..., None] * (p2 - p0)
+            d = s - r0
+            R = np.linalg.norm(d, axis=-1)
+            uv = d / R[..., None]
+            cos = uv @ (-nn[row])  # the ray leaves tet k through F: outward normal of (k, l)
+            ker = (wq * 2 * area[row] * cos * np.exp(-mu_tet[k] * R) / R ** 2).reshape(-1)
+            Z = zernike(Np, (uv @ e1[rec]).reshape(-1), (uv @ e2[rec]).reshape(-1))
+            out[rec] += wgt * strength * inv * (ker @ Z) / np.sqrt(area[row])
+    return out
+
+
 def tet_density(verts, tets, mu_tet, Np, rho, nq=48) -> np.ndarray:
     """rho_T at every tet centroid (Sec. 4.1, Eq. IntDens) for rho [rows, nb]:
     the per-tet functional g_t of interior_g applied to the tet's four rows."""
