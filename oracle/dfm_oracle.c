@@ -38,6 +38,13 @@
  * Zernike index idx = (n(n+2)+m)/2, m = -n, -n+2, ..., n.
  */
 #include <math.h>
+
+/* Planted mistakes for the mutation test of the pins: the tests build this file
+ * a second time with -DORC_MUTATE=k and check that some pin fails; the oracle
+ * itself is built with the default 0, which compiles none of them. */
+#ifndef ORC_MUTATE
+#define ORC_MUTATE 0
+#endif
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -80,7 +87,7 @@ static void face_of(const double* V, const int32_t* T, int64_t t, int f, face_t*
   F->area = 0.5 * vnorm(c);
   if (vdot(c, vsub(F->apex, F->p[0])) < 0) c = vscale(c, -1.0);
   F->n = vunit(c);
-  F->e1 = vunit(a);
+  F->e1 = ORC_MUTATE == 6 ? a : vunit(a);
   F->e2 = vcross(F->n, F->e1);
 }
 
@@ -116,12 +123,14 @@ static void zern_all(int Np, double px, double py, double* Z) {
     for (int m = -n; m <= n; m += 2) {
       int idx = (n * (n + 2) + m) / 2;
       double R = zern_radial(n, m, rho);
-      Z[idx] = m >= 0 ? R * cos(m * phi) : R * sin(-m * phi);
+      Z[idx] = (m >= 0 || ORC_MUTATE == 1) ? R * cos(m * phi) : R * sin(-m * phi);
     }
 }
 
 /* inverse norm N_{nm} = (2n+2)/(eps_m pi), eps_0 = 2 */
-static double zern_invnorm(int n, int m) { return (2.0 * n + 2.0) / ((m == 0 ? 2.0 : 1.0) * M_PI); }
+static double zern_invnorm(int n, int m) {
+  return (2.0 * n + 2.0) / ((m == 0 && ORC_MUTATE != 2 ? 2.0 : 1.0) * M_PI);
+}
 
 void orc_zernike(int Np, int64_t npts, const double* px, const double* py, double* out) {
   int nb = nbasis(Np);
@@ -163,7 +172,7 @@ static void tri_exp_integral(pt2 A, pt2 B, pt2 C, double mu, int nq, const doubl
       double v = (1.0 - u) * 0.5 * (1.0 + gx[j]);
       double w = gw[i] * gw[j] * 0.25 * (1.0 - u); /* du dv on the unit simplex */
       double L = A.L + u * (B.L - A.L) + v * (C.L - A.L);
-      double e = exp(-mu * L);
+      double e = exp(-(ORC_MUTATE == 4 ? 0.5 : 1.0) * mu * L);
       s += w * e;
       ds += w * (-L * e);
     }
@@ -202,7 +211,7 @@ static double spatial_clip(const face_t* src, const vec3* dst, vec3 dst_n, vec3 
   double sgn = orient > 0 ? 1.0 : -1.0;
   /* make the projected destination polygon counter-clockwise too (not needed
    * for clipping correctness, only for the fan) */
-  for (int k = 0; k < 3 && np > 0; ++k) {
+  for (int k = 0; k < 3 && np > 0 && ORC_MUTATE != 7; ++k) {
     int k1 = (k + 1) % 3;
     double ex = sx[k1] - sx[k], ey = sy[k1] - sy[k];
     /* inside: sgn * cross(edge, p - start) >= 0 */
@@ -329,7 +338,7 @@ static double transmission(double cos_r, double c_ratio, double z_src, double z_
   double s2 = c_ratio * c_ratio * (1.0 - cos_r * cos_r);
   if (s2 >= 1.0) return 0.0;
   double cos_t = sqrt(1.0 - s2);
-  double den = z_dst * cos_r + z_src * cos_t;
+  double den = ORC_MUTATE == 9 ? z_src * cos_r + z_dst * cos_t : z_dst * cos_r + z_src * cos_t;
   return 4.0 * z_dst * z_src * cos_r * cos_t / (den * den);
 }
 
@@ -378,7 +387,11 @@ static void block_fixed(const double* V, const int32_t* T, int64_t t, int f, int
           w *= wl;
         }
         zern_all(Np, vdot(d, src.e1), vdot(d, src.e2), Zp);
-        zern_all(Np, c_ratio * vdot(d, recv.e1), c_ratio * vdot(d, recv.e2), Zq);
+        if (ORC_MUTATE == 3)
+          zern_all(Np, vdot(d, src.e1), vdot(d, src.e2), Zq);
+        else
+          zern_all(Np, (ORC_MUTATE == 10 && kind == 1 ? 1.0 / c_ratio : c_ratio) * vdot(d, recv.e1),
+                   (ORC_MUTATE == 10 && kind == 1 ? 1.0 / c_ratio : c_ratio) * vdot(d, recv.e2), Zq);
         for (int a = 0; a < nb; ++a) {
           double wa = w * Zq[a];
           for (int b = 0; b < nb; ++b) {
@@ -678,7 +691,7 @@ void orc_interior_g(const double* V, const int32_t* T, int64_t t, const double* 
         double dist = vnorm(rs);
         vec3 dd = vscale(rs, 1.0 / dist);
         double cosv = vdot(dd, F.n);
-        double ker = cosv * exp(-mu * dist) / (dist * dist);
+        double ker = (ORC_MUTATE == 8 ? 1.0 : cosv) * exp(-mu * dist) / (dist * dist);
         zern_all(Np, vdot(dd, F.e1), vdot(dd, F.e2), Z);
         for (int k = 0; k < nb; ++k) {
           o[k] += w * ker * Z[k];
@@ -710,7 +723,7 @@ void orc_apply(int64_t nrows, int nb, const double* blocks, const int64_t* dest,
 #else
   (void)nthreads;
 #endif
-  if (!trans) {
+  if (!trans || ORC_MUTATE == 5) {
     /* products of every block with its column's coefficients (parallel), then
      * a serial scatter-add into the receiving rows */
     double* prod = (double*)malloc(sizeof(double) * nrows * 3 * nb);

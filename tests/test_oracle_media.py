@@ -3,8 +3,10 @@ law with Snell's law, Sec. 3.2 Eq. B4DInt):
 
 - the transmission probability: 4 z1 z2 / (z1 + z2)^2 at normal incidence,
   1 between equal media, 0 at grazing incidence and beyond the critical
-  angle, 0 <= lambda_t <= 1, and the same value for the reversed ray (the
-  formula is symmetric under swapping the two media and the two angles);
+  angle, 0 <= lambda_t <= 1, the same value for the reversed ray, and one
+  minus the square of the textbook pressure reflection coefficient
+  (Z2 cos th_i - Z1 cos th_t) / (Z2 cos th_i + Z1 cos th_t), Z1 the medium the
+  ray leaves;
 - equal media everywhere (c, rho_f not 1) give exactly the uniform operator
   and no reflected part;
 - equal speeds with unequal impedances make lambda_t a constant per face:
@@ -37,6 +39,9 @@ def test_transmission_law(oracle_mod):
         lt = T(cr, k, zs, zd)
         assert 0.0 <= lt <= 1.0
         s_t = k * np.sqrt(1 - cr * cr)
+        if s_t < 1:  # textbook: 1 - r_p^2, r_p = (Z2 cos th_i - Z1 cos th_t) / (Z2 cos th_i + Z1 cos th_t)
+            ct = np.sqrt(1 - s_t * s_t)
+            assert lt == pytest.approx(1 - ((zd * cr - zs * ct) / (zd * cr + zs * ct)) ** 2, rel=1e-12)
         if s_t < 1:  # the reversed ray leaves the other medium at theta_t and arrives at theta_r
             assert T(np.sqrt(1 - s_t * s_t), 1.0 / k, zd, zs) == pytest.approx(lt, rel=1e-12)
 

@@ -1,0 +1,88 @@
+"""Mutation test of the oracle's pins: each planted mistake below is compiled
+into a second copy of the oracle's C code (-DORC_MUTATE=k), swapped in for the
+real one, and at least one pin must fail on it.  The mistakes are the kinds a
+reader checks the oracle against the paper for: a sin/cos mix-up in the
+Zernike polynomials, a dropped normalisation factor, the wrong face frame for
+the receiving face, a halved damping exponent, a transposed operator, an
+unnormalised tangent axis, a missing clip of the integration triangle, a dropped
+cosine in the interior density, swapped impedances in the transmission law,
+and an inverted Snell ratio.  Only the C oracle is mutated, on the CPU."""
+import ctypes
+import os
+import subprocess
+
+import pytest
+
+import test_oracle_blocks as blocks
+import test_oracle_media as media
+import test_oracle_solve as solve
+import test_oracle_source as source
+import test_oracle_zernike as zernike
+
+MUTANTS = {
+    1: "Zernike: cos instead of sin for m < 0",
+    2: "inverse norm without eps_m",
+    3: "receiving Zernike vector in the source face frame",
+    4: "damping exponent halved",
+    5: "transposed application applies B",
+    6: "first tangent axis not normalised (e1 = second - first vertex)",
+    7: "integration triangle not clipped to the source face",
+    8: "interior density without the cosine",
+    9: "impedances swapped in the transmission law",
+    10: "inverted Snell ratio for the transmitted direction",
+}
+
+
+def _pins(O):
+    """Cheap pins (no Monte Carlo except for the Snell mutant's own check)."""
+    yield lambda: zernike.test_orthogonality(O)
+    yield lambda: zernike.test_closed_form_matches_paper_recursion(O, 4)
+    yield lambda: blocks.test_regular_tet_view_factor(O)
+    yield lambda: blocks.test_reciprocity_single_tet(O, 0.8)
+    yield lambda: blocks.test_conservation_weighted_column_sums(O)
+    yield lambda: solve.test_interior_kernel_solid_angles(O)
+    yield lambda: solve.test_adjoint_identity_and_fd(O)
+    yield lambda: source.test_textbook_low_orders_on_a_known_frame(O)
+    yield lambda: source.test_rotation_about_the_normal(O)
+    yield lambda: media.test_transmission_law(O)
+
+
+def _build_mutant(O, k, outdir):
+    src = os.path.join(os.path.dirname(O.build()), "..", "dfm_oracle.c")
+    so = os.path.join(outdir, f"liboracle_mut{k}.so")
+    subprocess.check_call(["gcc", "-std=gnu11", "-O2", "-fopenmp", "-fPIC", "-shared", f"-DORC_MUTATE={k}", "-o",
+                           so, os.path.abspath(src), "-lm"])
+    L = ctypes.CDLL(so)
+    L.orc_blocks.restype = ctypes.c_int
+    L.orc_mc_block.restype = ctypes.c_int
+    L.orc_region_cos_measure.restype = ctypes.c_double
+    L.orc_transmission.restype = ctypes.c_double
+    L.orc_transmission.argtypes = [ctypes.c_double] * 4
+    return L
+
+
+@pytest.mark.parametrize("k", sorted(MUTANTS))
+def test_a_pin_fails_on_each_planted_mistake(oracle_mod, k, tmp_path):
+    import oracle.oracle as core
+
+    real = core.lib()
+    core._lib = _build_mutant(oracle_mod, k, str(tmp_path))
+    failed = []
+    try:
+        pins = list(_pins(oracle_mod))
+        if k == 10:
+            pins = [lambda: media.test_monte_carlo_across_an_interface(oracle_mod, 1)]
+        for pin in pins:
+            try:
+                pin()
+            except AssertionError:
+                failed.append(pin)
+                break
+    finally:
+        core._lib = real
+    assert failed, f"no pin caught mutant {k}: {MUTANTS[k]}"
+
+
+def test_the_real_oracle_passes_the_same_pins(oracle_mod):
+    for pin in _pins(oracle_mod):
+        pin()
