@@ -53,6 +53,7 @@ def _build_mutant(O, k, outdir):
     subprocess.check_call(["gcc", "-std=gnu11", "-O2", "-fopenmp", "-fPIC", "-shared", f"-DORC_MUTATE={k}", "-o",
                            so, os.path.abspath(src), "-lm"])
     L = ctypes.CDLL(so)
+    os.remove(so)  # the loaded copy stays mapped
     L.orc_blocks.restype = ctypes.c_int
     L.orc_mc_block.restype = ctypes.c_int
     L.orc_region_cos_measure.restype = ctypes.c_double
@@ -62,11 +63,13 @@ def _build_mutant(O, k, outdir):
 
 
 @pytest.mark.parametrize("k", sorted(MUTANTS))
-def test_a_pin_fails_on_each_planted_mistake(oracle_mod, k, tmp_path):
+def test_a_pin_fails_on_each_planted_mistake(oracle_mod, k):
     import oracle.oracle as core
 
     real = core.lib()
-    core._lib = _build_mutant(oracle_mod, k, str(tmp_path))
+    outdir = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build")
+    os.makedirs(outdir, exist_ok=True)
+    core._lib = _build_mutant(oracle_mod, k, outdir)
     failed = []
     try:
         pins = list(_pins(oracle_mod))
