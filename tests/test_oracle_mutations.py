@@ -6,7 +6,10 @@ Zernike polynomials, a dropped normalisation factor, the wrong face frame for
 the receiving face, a halved damping exponent, a transposed operator, an
 unnormalised tangent axis, a missing clip of the integration triangle, a dropped
 cosine in the interior density, swapped impedances in the transmission law,
-and an inverted Snell ratio.  Only the C oracle is mutated, on the CPU."""
+and an inverted Snell ratio.  A second set plants mistakes in the oracle's
+Python half (a reversed point-source ray, |T| for sqrt|T|, a dropped inverse
+norm, a left-handed frame, a left-out reflection part) by rewriting one line of
+the function's source.  Only the oracle is mutated, on the CPU."""
 import ctypes
 import os
 import subprocess
@@ -89,3 +92,48 @@ def test_a_pin_fails_on_each_planted_mistake(oracle_mod, k):
 def test_the_real_oracle_passes_the_same_pins(oracle_mod):
     for pin in _pins(oracle_mod):
         pin()
+
+
+# Mistakes planted in the oracle's Python half: (function, original text, planted text, pin).
+PY_MUTANTS = {
+    "point source: ray direction reversed": (
+        "point_source", "Z = zernike(Np, (uv @ e1[rec]).reshape(-1), (uv @ e2[rec]).reshape(-1))",
+        "Z = zernike(Np, (-uv @ e1[rec]).reshape(-1), (-uv @ e2[rec]).reshape(-1))",
+        lambda O: __import__("test_oracle_point_source").test_rays_arrive_pointing_away_from_the_source(O)),
+    "isotropic source: |T| instead of sqrt|T|": (
+        "source_vector", "x[int(r), 0] += wt * np.sqrt(area[int(r)])", "x[int(r), 0] += wt * area[int(r)]",
+        lambda O: source.test_tet_density_of_an_isotropic_face_is_its_solid_angle(O)),
+    "directed source: inverse norm dropped": (
+        "source_directed", "out[s, r] = inv * zernike(Np, p[0], p[1])[0] * np.sqrt(area[r])",
+        "out[s, r] = zernike(Np, p[0], p[1])[0] * np.sqrt(area[r])",
+        lambda O: source.test_normal_incidence_closed_form(O)),
+    "face frames: left-handed": (
+        "face_frames", "e1[f::4], nn[f::4], e2[f::4] = u, n, np.cross(n, u)",
+        "e1[f::4], nn[f::4], e2[f::4] = u, n, np.cross(u, n)",
+        lambda O: source.test_textbook_low_orders_on_a_known_frame(O)),
+    "application: interface reflections left out": (
+        "apply", "if op.rblocks is not None:", "if False:",
+        lambda O: media.test_conservation_with_unequal_media(O)),
+}
+
+
+@pytest.mark.parametrize("name", sorted(PY_MUTANTS))
+def test_a_pin_fails_on_each_planted_python_mistake(oracle_mod, name):
+    import inspect
+
+    import oracle.oracle as core
+
+    fname, old, new, pin = PY_MUTANTS[name]
+    real = getattr(core, fname)
+    src = inspect.getsource(real)
+    assert old in src, f"{fname}: the text to mutate is gone"
+    ns = dict(core.__dict__)
+    exec(compile(src.replace(old, new), core.__file__, "exec"), ns)
+    setattr(core, fname, ns[fname])
+    setattr(oracle_mod, fname, ns[fname])
+    try:
+        with pytest.raises(AssertionError):
+            pin(oracle_mod)
+    finally:
+        setattr(core, fname, real)
+        setattr(oracle_mod, fname, real)

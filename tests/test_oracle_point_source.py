@@ -121,3 +121,22 @@ def test_regular_tet_centroid_symmetry(oracle_mod):
     for m in (2, -2):
         np.testing.assert_allclose(a[:, idx(2, m)], 0.0, atol=1e-13)
     assert np.all(np.hypot(a[:, idx(3, 3)], a[:, idx(3, -3)]) > 1e-3)
+
+
+def test_rays_arrive_pointing_away_from_the_source(oracle_mod):
+    """Off-centre source: on a face, the mean tangential direction of the arriving
+    rays (the (1,+-1) moments) points from the source's foot on the face plane
+    towards the face, i.e. along the weighted mean of s - foot (a reversed ray
+    direction would point the other way)."""
+    r0 = REG_V.mean(axis=0) + 0.45 * (REG_V[0] - REG_V.mean(axis=0))  # towards vertex 0
+    a = oracle_mod.point_source(REG_V, ONE_TET, r0, 1, np.zeros(1), 1.0)
+    e1, e2, nn = oracle_mod.face_frames(REG_V, ONE_TET)
+    idx = oracle_mod.zernike_index
+    for l in (1, 2, 3):  # faces that hold vertex 0
+        p = REG_V[[ONE_TET[0, (l + 1 + k) % 4] for k in range(3)]]
+        foot = r0 - ((r0 - p[0]) @ nn[l]) * nn[l]
+        away = p.mean(axis=0) - foot  # the face lies mostly on this side of the foot
+        got = np.array([a[l, idx(1, 1)], a[l, idx(1, -1)]])
+        want = np.array([away @ e1[l], away @ e2[l]])
+        cos = got @ want / (np.linalg.norm(got) * np.linalg.norm(want))
+        assert cos > 0.9, (l, cos)
