@@ -197,6 +197,7 @@ class Operator:
     # boundary, where blocks already hold the reflection)
     rblocks: np.ndarray | None = None
     rdest: np.ndarray | None = None
+    drblocks: np.ndarray | None = None
 
     @property
     def nb(self):
@@ -276,7 +277,7 @@ def transmission(cos_r, c_ratio, z_src, z_dst) -> float:
 
 
 def assemble_media(verts, tets, mu_tet, c_tet, rhof_tet, refl, Np, q=None, rtol=1e-13, topo=None,
-                   nthreads=0) -> Operator:
+                   nthreads=0, with_derivative=False) -> Operator:
     """B for heterogeneous media (Sec. 3.2 Eq. B4DInt with the transmission
     law of Sec. 3.3): per-tet propagation speed c and fluid density rho_f
     (impedance z = rho_f c).  A ray leaving tet j through an interior face
@@ -286,7 +287,8 @@ def assemble_media(verts, tets, mu_tet, c_tet, rhof_tet, refl, Np, q=None, rtol=
     by specular reflection with probability 1 - lambda_t (rblocks, received by
     the exit face's own row).  Boundary faces reflect with weight r as in
     assemble.  With equal media everywhere this is assemble's operator and the
-    rblocks vanish."""
+    rblocks vanish.  with_derivative adds d(blocks)/d(mu_t) (dblocks) and
+    d(rblocks)/d(mu_t) (drblocks): both parts cross tet t, whose damping they carry."""
     G = gl_table()
     topo = topo or topology(tets)
     verts = np.ascontiguousarray(verts, dtype=np.float64)
@@ -310,9 +312,10 @@ def assemble_media(verts, tets, mu_tet, c_tet, rhof_tet, refl, Np, q=None, rtol=
     def run(sel, rows, kind, lam):
         n = int(np.count_nonzero(sel))
         out = np.zeros((n, nb, nb))
+        dout = np.zeros((n, nb, nb)) if with_derivative else None
         qu = np.empty(n, dtype=np.int32)
         if n == 0:
-            return out, qu
+            return out, dout, qu
         a = lambda v, dt=np.float64: np.ascontiguousarray(np.asarray(v)[sel], dtype=dt)  # noqa: E731
         lib().orc_blocks_media(_p(verts), _p(tets, _i32p), ctypes.c_int64(n), _p(a(t, np.int64), _i64p),
                                _p(a(f, np.int32), _i32p), _p(a(fp, np.int32), _i32p), _p(a(rows, np.int64), _i64p),
@@ -320,18 +323,26 @@ def assemble_media(verts, tets, mu_tet, c_tet, rhof_tet, refl, Np, q=None, rtol=
                                _p(a(z_tet[t])), _p(a(z_tet[i])), ctypes.c_int(Np), ctypes.c_int(len(GL_ORDERS)),
                                _p(G.qs, _i32p), _p(G.offs, _i32p), _p(G.x), _p(G.w), ctypes.c_int(lev0),
                                ctypes.c_double(rtol), ctypes.c_int(tri_lev), ctypes.c_int(0x0F),
-                               ctypes.c_int(nthreads), _p(out), None, _p(qu, _i32p))
-        return out, qu
+                               ctypes.c_int(nthreads), _p(out), _p(dout) if dout is not None else None,
+                               _p(qu, _i32p))
+        return out, dout, qu
 
     everything = np.ones(t.size, dtype=bool)
     lam = np.where(bnd, refl_row[recv], 1.0)
     kind = np.where(bnd, 0, 1)
-    b1, q1 = run(everything, recv, kind, lam)
+    b1, d1, q1 = run(everything, recv, kind, lam)
     rb = np.zeros((t.size, nb, nb))
-    b2, _ = run(~bnd, 4 * t + fp, np.full(t.size, 2), np.ones(t.size))
+    b2, d2, _ = run(~bnd, 4 * t + fp, np.full(t.size, 2), np.ones(t.size))
     rb[~bnd] = b2
-    return Operator(Np=Np, blocks=b1.reshape(4 * nt, 3, nb, nb), dest=recv.reshape(4 * nt, 3), q_used=q1,
-                    rblocks=rb.reshape(4 * nt, 3, nb, nb), rdest=(4 * t + fp).reshape(4 * nt, 3))
+    shape = (4 * nt, 3, nb, nb)
+    op = Operator(Np=Np, blocks=b1.reshape(shape), dest=recv.reshape(4 * nt, 3), q_used=q1,
+                  rblocks=rb.reshape(shape), rdest=(4 * t + fp).reshape(4 * nt, 3))
+    if with_derivative:
+        drb = np.zeros((t.size, nb, nb))
+        drb[~bnd] = d2
+        op.dblocks = d1.reshape(shape)
+        op.drblocks = drb.reshape(shape)
+    return op
 
 
 def mc_block_media(verts, tets, t, f, fp, recv_row, mu, kind, c_ratio, z_src, z_dst, Np, nsamp=10 ** 7, seed=1,
@@ -682,6 +693,9 @@ def gradient(op: Operator, rho: np.ndarray, lam: np.ndarray, dg: dict, nt: int) 
     rho_t = rho.reshape(nt, 4, nb)
     lam_r = lam[dest]  # [nt, 4, 3, nb]
     grad += np.einsum("tfka,tfkab,tfb->t", lam_r, db, rho_t)
+    if op.drblocks is not None:  # heterogeneous media: the interface reflections cross tet e too
+        lam_rr = lam[op.rdest.reshape(nt, 4, 3)]
+        grad += np.einsum("tfka,tfkab,tfb->t", lam_rr, op.drblocks.reshape(nt, 4, 3, nb, nb), rho_t)
     for e, d in dg.items():
         grad[e] += float(np.sum(d * rho[4 * e:4 * e + 4]))
     return grad

@@ -132,3 +132,51 @@ def test_monte_carlo_across_an_interface(oracle_mod, kind):
                                          c[i] * rhof[i], Np, nsamp=4 * 10 ** 6, seed=11 + kind)
     z = np.abs(got - mean) / np.maximum(se, 1e-12)
     assert z.max() < 5.0, (z.max(), np.unravel_index(z.argmax(), z.shape))
+
+
+def test_media_derivatives_match_differences(oracle_mod):
+    V, T = _mesh()
+    nt = T.shape[0]
+    rng = np.random.default_rng(13)
+    c = rng.uniform(0.8, 1.25, nt)
+    rhof = rng.uniform(0.5, 2.0, nt)
+    mu = np.full(nt, 0.4)
+    op = oracle_mod.assemble_media(V, T, mu, c, rhof, 0.9, 2, q=16, with_derivative=True)
+    h = 1e-5
+    p = oracle_mod.assemble_media(V, T, mu + h, c, rhof, 0.9, 2, q=16)
+    m = oracle_mod.assemble_media(V, T, mu - h, c, rhof, 0.9, 2, q=16)
+    np.testing.assert_allclose(op.dblocks, (p.blocks - m.blocks) / (2 * h), atol=1e-9)
+    np.testing.assert_allclose(op.drblocks, (p.rblocks - m.rblocks) / (2 * h), atol=1e-9)
+    assert np.abs(op.drblocks).max() > 1e-4
+
+
+def test_media_adjoint_gradient_matches_differences(oracle_mod):
+    """dJ/dmu by the adjoint (transposed solve with both parts of B, and the
+    derivative blocks of both) against central differences of J = g . rho."""
+    V, T = _mesh()
+    nt = T.shape[0]
+    rng = np.random.default_rng(17)
+    c = rng.uniform(0.8, 1.25, nt)
+    rhof = rng.uniform(0.5, 2.0, nt)
+    mu = rng.uniform(0.3, 0.6, nt)
+    Np = 1
+    topo = oracle_mod.topology(T)
+    rows = np.nonzero(topo.boundary)[0][[0, 9]]
+    b = oracle_mod.source_vector(V, T, rows, Np)
+    g, dg = oracle_mod.receiver_functional(V, T, mu, Np, [20, 21])
+    op = oracle_mod.assemble_media(V, T, mu, c, rhof, 0.8, Np, q=16, with_derivative=True)
+    rho = oracle_mod.solve_dense(op, b)
+    lam = np.linalg.solve(np.eye(op.nrows * op.nb) - oracle_mod.dense(op).T, g.reshape(-1)).reshape(g.shape)
+    grad = oracle_mod.gradient(op, rho, lam, dg, nt)
+
+    def J(mv):
+        o = oracle_mod.assemble_media(V, T, mv, c, rhof, 0.8, Np, q=16)
+        gv, _ = oracle_mod.receiver_functional(V, T, mv, Np, [20, 21])
+        return float(np.sum(gv * oracle_mod.solve_dense(o, b)))
+
+    h = 1e-5
+    for e in (0, 20, 33):
+        mp, mm = mu.copy(), mu.copy()
+        mp[e] += h
+        mm[e] -= h
+        assert grad[e] == pytest.approx((J(mp) - J(mm)) / (2 * h), rel=1e-5, abs=1e-10)
