@@ -708,6 +708,128 @@ void orc_interior_g(const double* V, const int32_t* T, int64_t t, const double* 
   free(Z);
 }
 
+/* Adaptive version of the same face integral.  A tet's centroid can sit
+ * close to one of its faces (thin tets of a jittered mesh); the kernel
+ * cos / R^2 then peaks sharply at the foot of r on that face and a fixed
+ * tensor rule loses digits.  Here each face triangle is refined 4-way
+ * wherever an 8 x 8 collapsed Gauss rule on a triangle and the sum of the same
+ * rule on its four children differ by more than tol (absolute, from rtol times
+ * the whole-face estimate); leaves contribute their children's sum. */
+typedef struct {
+  vec3 R;
+  double mu;
+  int Np, nb, nq;
+  const face_t* F;
+  const double *gx, *gw;
+  double* Z;
+} ig_ctx;
+
+static void ig_rule(const ig_ctx* c, vec3 A, vec3 B, vec3 C, double* o, double* od) {
+  vec3 e1 = vsub(B, A), e2 = vsub(C, A);
+  double area = 0.5 * vnorm(vcross(e1, e2));
+  for (int k = 0; k < c->nb; ++k) o[k] = od[k] = 0.0;
+  for (int i = 0; i < c->nq; ++i) {
+    double u = 0.5 * (1.0 + c->gx[i]);
+    for (int j = 0; j < c->nq; ++j) {
+      double v = (1.0 - u) * 0.5 * (1.0 + c->gx[j]);
+      double w = c->gw[i] * c->gw[j] * 0.25 * (1.0 - u) * 2.0 * area;
+      vec3 s = vadd(A, vadd(vscale(e1, u), vscale(e2, v)));
+      vec3 rs = vsub(c->R, s);
+      double dist = vnorm(rs);
+      vec3 dd = vscale(rs, 1.0 / dist);
+      double ker = (ORC_MUTATE == 8 ? 1.0 : vdot(dd, c->F->n)) * exp(-c->mu * dist) / (dist * dist);
+      zern_all(c->Np, vdot(dd, c->F->e1), vdot(dd, c->F->e2), c->Z);
+      for (int k = 0; k < c->nb; ++k) {
+        o[k] += w * ker * c->Z[k];
+        od[k] += w * (-dist) * ker * c->Z[k];
+      }
+    }
+  }
+}
+
+static void ig_adapt(const ig_ctx* c, vec3 A, vec3 B, vec3 C, const double* coarse, double tol, int depth,
+                     double* out, double* dout) {
+  int nb = c->nb;
+  vec3 mab = vscale(vadd(A, B), 0.5), mbc = vscale(vadd(B, C), 0.5), mca = vscale(vadd(C, A), 0.5);
+  vec3 kids[4][3] = {{A, mab, mca}, {mab, B, mbc}, {mca, mbc, C}, {mab, mbc, mca}};
+  double* buf = (double*)malloc(sizeof(double) * 8 * nb);
+  double *fine = buf, *dfine = buf + nb;
+  for (int k = 0; k < nb; ++k) fine[k] = dfine[k] = 0.0;
+  for (int q = 0; q < 4; ++q) {
+    double* o = buf + (2 + q) * nb;
+    double* od = buf + 6 * nb;
+    ig_rule(c, kids[q][0], kids[q][1], kids[q][2], o, od);
+    for (int k = 0; k < nb; ++k) {
+      fine[k] += o[k];
+      dfine[k] += od[k];
+    }
+  }
+  double err = 0.0;
+  for (int k = 0; k < nb; ++k) err = fmax(err, fabs(fine[k] - coarse[k]));
+  if (err <= tol || depth >= 24) {
+    for (int k = 0; k < nb; ++k) {
+      out[k] += fine[k];
+      dout[k] += dfine[k];
+    }
+  } else {
+    /* the children's own estimates serve as their coarse values */
+    double* kid = (double*)malloc(sizeof(double) * 2 * nb);
+    for (int q = 0; q < 4; ++q) {
+      ig_rule(c, kids[q][0], kids[q][1], kids[q][2], kid, kid + nb);
+      ig_adapt(c, kids[q][0], kids[q][1], kids[q][2], kid, tol / 2.0, depth + 1, out, dout);
+    }
+    free(kid);
+  }
+  free(buf);
+}
+
+/* rho_T functional of tet t at point r with adaptive cubature (relative
+ * tolerance rtol per face); layout as orc_interior_g. */
+void orc_interior_g_adaptive(const double* V, const int32_t* T, int64_t t, const double* r, double mu, int Np,
+                             double rtol, int nq, const double* gx, const double* gw, double* out, double* dout) {
+  int nb = nbasis(Np);
+  double* Z = (double*)malloc(sizeof(double) * nb);
+  double* coarse = (double*)malloc(sizeof(double) * 2 * nb);
+  for (int l = 0; l < 4; ++l) {
+    face_t F;
+    face_of(V, T, t, l, &F);
+    ig_ctx c = {v3(r[0], r[1], r[2]), mu, Np, nb, nq, &F, gx, gw, Z};
+    double* o = out + l * nb;
+    double* od = dout + l * nb;
+    for (int k = 0; k < nb; ++k) o[k] = od[k] = 0.0;
+    ig_rule(&c, F.p[0], F.p[1], F.p[2], coarse, coarse + nb);
+    double scale = 0.0;
+    for (int k = 0; k < nb; ++k) scale = fmax(scale, fabs(coarse[k]));
+    ig_adapt(&c, F.p[0], F.p[1], F.p[2], coarse, rtol * scale, 0, o, od);
+    double sc = 1.0 / sqrt(F.area);
+    for (int k = 0; k < nb; ++k) {
+      o[k] *= sc;
+      od[k] *= sc;
+    }
+  }
+  free(coarse);
+  free(Z);
+}
+
+/* Adaptive functional of every tet at its centroid, in parallel over tets:
+ * out, dout [nt][4][nb]. */
+void orc_centroid_g_adaptive(const double* V, const int32_t* T, int64_t nt, const double* mu_tet, int Np, double rtol,
+                             int nq, const double* gx, const double* gw, int nthreads, double* out, double* dout) {
+  int nb = nbasis(Np);
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+  (void)nthreads;
+#endif
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t t = 0; t < nt; ++t) {
+    double r[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < 4; ++k)
+      for (int d = 0; d < 3; ++d) r[d] += 0.25 * V[3 * (int64_t)T[4 * t + k] + d];
+    orc_interior_g_adaptive(V, T, t, r, mu_tet[t], Np, rtol, nq, gx, gw, out + t * 4 * nb, dout + t * 4 * nb);
+  }
+}
+
 /* ------------------------------------------------------------------------ */
 /* FP64 operator application in the oracle's own layout                      */
 /* ------------------------------------------------------------------------ */

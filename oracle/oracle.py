@@ -549,9 +549,23 @@ def point_source(verts, tets, r0, Np, mu_tet, refl, strength=1.0, nq=48, topo=No
     return out
 
 
-def tet_density(verts, tets, mu_tet, Np, rho, nq=48) -> np.ndarray:
+def tet_density(verts, tets, mu_tet, Np, rho, nq=48, rtol=1e-11, nthreads=0) -> np.ndarray:
     """rho_T at every tet centroid (Sec. 4.1, Eq. IntDens) for rho [rows, nb]:
-    the per-tet functional g_t of interior_g applied to the tet's four rows."""
+    the per-tet functional g_t of interior_g applied to the tet's four rows
+    (nq=None: adaptive cubature to rtol, all tets in parallel)."""
+    if nq is None:
+        nt = tets.shape[0]
+        nb = nbasis(Np)
+        x, w = np.polynomial.legendre.leggauss(8)
+        g = np.empty((nt, 4, nb))
+        dg = np.empty((nt, 4, nb))
+        lib().orc_centroid_g_adaptive(_p(np.ascontiguousarray(verts, dtype=np.float64)),
+                                      _p(np.ascontiguousarray(tets, dtype=np.int32), _i32p), ctypes.c_int64(nt),
+                                      _p(np.ascontiguousarray(np.broadcast_to(np.asarray(mu_tet, dtype=np.float64),
+                                                                              (nt,)))),
+                                      ctypes.c_int(Np), ctypes.c_double(rtol), ctypes.c_int(8), _p(x), _p(w),
+                                      ctypes.c_int(nthreads), _p(g), _p(dg))
+        return np.einsum("tlk,tlk->t", g, rho.reshape(nt, 4, nb))
     cen = centroids(verts, tets)
     out = np.empty(tets.shape[0])
     for t in range(tets.shape[0]):
@@ -656,13 +670,22 @@ def centroids(verts, tets):
     return verts[tets].mean(axis=1)
 
 
-def interior_g(verts, tets, t, r, mu, Np, nq=48):
-    """g[4, nb] and dg/dmu with rho_T(r) = sum_{l,nm} rho_(t,l,nm) g[l,nm]."""
+def interior_g(verts, tets, t, r, mu, Np, nq=48, rtol=1e-11):
+    """g[4, nb] and dg/dmu with rho_T(r) = sum_{l,nm} rho_(t,l,nm) g[l,nm]
+    (Sec. 4.1, Eq. IntDens): a fixed collapsed Gauss rule of order nq on each
+    face, or, with nq=None, adaptive 4-way refinement of each face to rtol."""
     nb = nbasis(Np)
-    x, w = np.polynomial.legendre.leggauss(nq)
     g = np.empty((4, nb))
     dg = np.empty((4, nb))
     rr = np.ascontiguousarray(r, dtype=np.float64)
+    if nq is None:
+        x, w = np.polynomial.legendre.leggauss(8)
+        lib().orc_interior_g_adaptive(_p(np.ascontiguousarray(verts, dtype=np.float64)),
+                                      _p(np.ascontiguousarray(tets, dtype=np.int32), _i32p), ctypes.c_int64(int(t)),
+                                      _p(rr), ctypes.c_double(mu), ctypes.c_int(Np), ctypes.c_double(rtol),
+                                      ctypes.c_int(8), _p(x), _p(w), _p(g), _p(dg))
+        return g, dg
+    x, w = np.polynomial.legendre.leggauss(nq)
     lib().orc_interior_g(_p(np.ascontiguousarray(verts, dtype=np.float64)),
                          _p(np.ascontiguousarray(tets, dtype=np.int32), _i32p), ctypes.c_int64(int(t)), _p(rr),
                          ctypes.c_double(mu), ctypes.c_int(Np), ctypes.c_int(nq), _p(x), _p(w), _p(g), _p(dg))

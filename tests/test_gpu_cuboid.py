@@ -112,26 +112,39 @@ def test_tet_density_matches_oracle(D, oracle_mod):
         assert np.all(np.abs(got[r] - ref) <= bound), np.abs(got[r] - ref).max()
 
 
-def _cuboid_density(D, m, Np, mu, tol=1e-10):
+def _cuboid_solution(D, m, Np, mu, tol=1e-10):
     mesh = D.Mesh(m.verts, m.tets, refl=1.0)
     op = D.Operator(mesh, Np, mu=mu, precision=D.F32)
     rho0 = D.source_directed(mesh, Np, cuboid_rows_x0(m), combine=True)
     rho, info = op.solve(rho0, tol=tol)
-    g, _ = D.interior_density(mesh, Np, np.arange(m.n_tets), mu=mu)
+    return mesh, rho
+
+
+def _densities(D, mesh, m, Np, mu, rho, nq):
+    g, _ = D.interior_density(mesh, Np, np.arange(m.n_tets), mu=mu, nq=nq)
     return D.tet_density(mesh, Np, g, rho).cpu().numpy()
 
 
-def test_cuboid_matches_oracle_and_exact_solution(D, oracle_mod):
-    with open(os.path.join(GOLDEN, "cuboid_n2_np4.json")) as f:
+@pytest.mark.parametrize("case", ["cuboid_n2_np4", "cuboid_n4_np4", "cuboid_n4_np8"])
+def test_cuboid_matches_oracle_and_exact_solution(D, oracle_mod, case):
+    """The GPU's interior densities with the default 32-point face rule against
+    the oracle's same rule (FP32 blocks and solve: 2e-4 of the maximum), with
+    the 64-point rule against the oracle's adaptive cubature (within the
+    64-point rule's own deviation, measured by the oracle, plus the same 2e-4),
+    and the relative mean error against the exact ray solution."""
+    with open(os.path.join(GOLDEN, case + ".json")) as f:
         gold = json.load(f)
     m = kuhn_cuboid_mesh(gold["n"], length=gold["length"], jitter=gold["jitter"], seed=gold["seed"])
-    dens = _cuboid_density(D, m, gold["Np"], gold["mu"])
+    mesh, rho = _cuboid_solution(D, m, gold["Np"], gold["mu"])
+    exact = exact_ray_density(oracle_mod.centroids(m.verts, m.tets)[:, 0], gold["mu"], gold["length"])
+    d32 = _densities(D, mesh, m, gold["Np"], gold["mu"], rho, 32)
+    ref32 = np.array(gold["density_nq32"])
+    np.testing.assert_allclose(d32, ref32, rtol=0, atol=2e-4 * np.abs(ref32).max())
+    err32 = np.mean(np.abs(d32 - exact)) / np.mean(exact)
+    assert abs(err32 - gold["rel_mean_err_nq32"]) < 1e-3
+    d64 = _densities(D, mesh, m, gold["Np"], gold["mu"], rho, 64)
     ref = np.array(gold["density"])
-    # FP32 blocks agree with the oracle's to about 1e-5 of each block's maximum
-    # and the solve amplifies that by 1/(1 - rho(B)) at most
-    np.testing.assert_allclose(dens, ref, rtol=0, atol=2e-4 * np.abs(ref).max())
-    x = oracle_mod.centroids(m.verts, m.tets)[:, 0]
-    ex = exact_ray_density(x, gold["mu"], gold["length"])
-    err = np.mean(np.abs(dens - ex)) / np.mean(ex)
+    assert np.abs(d64 - ref).max() <= (gold["nq64_max_dev"] + 2e-4) * np.abs(ref).max()
+    err = np.mean(np.abs(d64 - exact)) / np.mean(exact)
     assert abs(err - gold["rel_mean_err"]) < 1e-3
-    assert err < 0.15
+    assert err < 0.3  # the ray solution is approached as N_p grows (about 5% at N_p = 16-20 in the paper)

@@ -126,3 +126,23 @@ def test_tet_density_of_an_isotropic_face_is_its_solid_angle(oracle_mod):
     # the isotropic unit density has rho(s, p) = 1 for every direction
     assert dens[t] == pytest.approx(_solid_angle(cen, *p), rel=1e-9)
     assert np.count_nonzero(dens) == 1
+
+
+def test_adaptive_interior_rule_on_a_thin_tet(oracle_mod):
+    """A thin tet's centroid sits close to its base, where cos / R^2 peaks:
+    the adaptive cubature still gives each face's solid angle (isotropic unit
+    density, mu = 0), which a fixed 32-point rule misses by far more."""
+    verts = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0], [0.3, 0.3, 0.02]])
+    tets = np.array([[0, 1, 2, 3]], dtype=np.int32)
+    cen = verts.mean(axis=0)
+    for f in range(4):
+        rho = oracle_mod.source_vector(verts, tets, [f], 2)
+        p = verts[[tets[0, (f + 1 + k) % 4] for k in range(3)]]
+        want = _solid_angle(cen, *p)
+        got = oracle_mod.tet_density(verts, tets, np.zeros(1), 2, rho, nq=None)[0]
+        assert got == pytest.approx(want, rel=1e-9)
+        g, _ = oracle_mod.interior_g(verts, tets, 0, cen, 0.0, 2, nq=None)
+        assert np.sum(g * rho) == pytest.approx(want, rel=1e-9)
+    rho = oracle_mod.source_vector(verts, tets, [3], 2)
+    fixed = oracle_mod.tet_density(verts, tets, np.zeros(1), 2, rho, nq=32)[0]
+    assert abs(fixed - _solid_angle(cen, *verts[:3])) > 1e-6
