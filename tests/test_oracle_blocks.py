@@ -6,6 +6,8 @@
   both tangential momenta, so on one tet with lambda = 1,
   B_{(l',n'm'),(l,nm)} / N_{n'm'} = (-1)^(n+n') B_{(l,nm),(l',n'm')} / N_{nm};
 - brute-force Monte Carlo ray tracing of individual blocks (5 sigma);
+- view factors (the (0,0) entries at mu = 0) against the contour-integral
+  (Stokes) form on a jittered tet;
 - conservation (Sec. 2): with mu = 0 and fully reflecting walls the phase-space
   mass pi sum_J sqrt|T_J| rho_(J,00) is preserved, i.e. w^T B = w^T with
   w_I = sqrt|T_I| on the (0,0) slots and 0 elsewhere;
@@ -109,3 +111,40 @@ def test_adaptive_order_reaches_tolerance(oracle_mod):
     out, _, q, _ = oracle_mod.blocks_for_pairs(m.verts, m.tets, topo, np.full(m.n_tets, 0.05), 0.95, 4, t[sel],
                                                f[sel], fp[sel], rtol=1e-12)
     assert np.all(q > 0)
+
+
+def _contour_view_factor_area(P, Q):
+    """A_P F_{P->Q} between two triangles by Stokes' theorem (the contour-integral
+    form of the view factor): (1/2 pi) |sum over edge pairs of
+    Int Int ln|x - y| dx . dy|.  The shared edge uses Int_0^1 Int_0^1 ln(L|s - t|)
+    = ln L - 3/2; the other pairs are integrated numerically (scipy)."""
+    from scipy.integrate import dblquad
+
+    total = 0.0
+    for i in range(3):
+        a0, a1 = P[i], P[(i + 1) % 3]
+        for j in range(3):
+            b0, b1 = Q[j], Q[(j + 1) % 3]
+            da, db = a1 - a0, b1 - b0
+            dot = float(da @ db)
+            if np.allclose(a0, b1) and np.allclose(a1, b0) or np.allclose(a0, b0) and np.allclose(a1, b1):
+                total += dot * (np.log(np.linalg.norm(da)) - 1.5)
+                continue
+            val, _ = dblquad(lambda t, s: np.log(np.linalg.norm(a0 + s * da - b0 - t * db)), 0, 1, 0, 1,
+                             epsabs=1e-13, epsrel=1e-12)
+            total += dot * val
+    return abs(total) / (2 * np.pi)
+
+
+def test_view_factors_by_contour_integrals(oracle_mod):
+    """The (0,0) entries at mu = 0 are view factors: B_00 = F_{l->l'} sqrt(A_l / A_l'),
+    checked on a jittered tet against the contour-integral form."""
+    pytest.importorskip("scipy")
+    V, T = _jittered_tet()
+    op = oracle_mod.assemble(V, T, np.array([0.0]), 1.0, 1, q=32)
+    A = oracle_mod.face_areas(V, T)
+    face = lambda f: V[[T[0, (f + 1 + k) % 4] for k in range(3)]]  # noqa: E731
+    for f in range(4):
+        for k, fp in enumerate([g for g in range(4) if g != f]):
+            F = _contour_view_factor_area(face(f), face(fp)) / A[f]
+            assert op.blocks[f, k, 0, 0] == pytest.approx(F * np.sqrt(A[f] / A[fp]), rel=1e-8), (f, fp)
