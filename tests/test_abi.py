@@ -57,3 +57,23 @@ def test_null_handles_are_rejected_on_the_host():
     for name, call in calls.items():
         assert call() == ARG, name
         assert L.dfm_last_error().decode().startswith(name), (name, L.dfm_last_error())
+
+
+def test_assembly_parameters_are_checked_before_the_mesh_is_touched():
+    """Np out of range, an unknown precision, negative or NaN damping, and out-of-range
+    quadrature settings are refused by dfm_assemble before it reads the mesh or calls
+    CUDA (the mesh handle here is a zeroed host buffer that is never read)."""
+    from paper_1608_04607_gb300 import dfm
+
+    L = dfm.load()
+    fake_mesh = ctypes.create_string_buffer(4096)
+    out = ctypes.c_void_p()
+    good = dict(Np=4, mu=None, mu_uniform=0.1, quad_order=0, max_patch_deg=0.0, precision=dfm.F32, moment=0)
+    cases = [dict(Np=9), dict(Np=-1), dict(precision=7), dict(mu_uniform=-0.1), dict(mu_uniform=float("nan")),
+             dict(quad_order=33), dict(max_patch_deg=5.0), dict(moment=4)]
+    for bad in cases:
+        p = dfm.Params(**{**good, **bad})
+        rc = L.dfm_assemble(ctypes.cast(fake_mesh, ctypes.c_void_p), ctypes.byref(p), None, ctypes.byref(out))
+        assert rc in (dfm.DFM_ERR_ARG, dfm.DFM_ERR_UNSUPPORTED), bad
+        assert L.dfm_last_error().decode().startswith("dfm_assemble"), bad
+        assert not out.value
