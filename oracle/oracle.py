@@ -692,6 +692,53 @@ def interior_g(verts, tets, t, r, mu, Np, nq=48, rtol=1e-11):
     return g, dg
 
 
+def interior_g_split(verts, tets, t, r, mu, Np, n=16):
+    """The functional of interior_g by a rule that stays exact when r is close
+    to a face: each face is split at the foot F of r (height h) into three
+    signed triangles (F, A, B) over its edges and integrated in polar
+    coordinates seen from r: the azimuth psi about the face normal (from the
+    direction of A - F to that of B - F) and the polar angle phi up to the edge,
+    phi in [0, atan(l(psi)/h)], l(psi) the distance from F to the edge along
+    psi.  The area element times cos / R^2 is sin(phi) dphi dpsi, so with
+    exp(-mu h / cos(phi)) and the Zernike vector of the direction the integrand
+    is smooth and n-point Gauss-Legendre in psi and in phi converges fast.
+    Returns g[4, nb] (no dg)."""
+    nb = nbasis(Np)
+    e1, e2, nn = face_frames(verts, tets)
+    area = face_areas(verts, tets)
+    x, w = np.polynomial.legendre.leggauss(n)
+    x01, w01 = 0.5 * (x + 1), 0.5 * w
+    r = np.asarray(r, dtype=np.float64)
+    g = np.zeros((4, nb))
+    for l in range(4):
+        row = 4 * t + l
+        P = verts[[tets[t, (l + 1 + k) % 4] for k in range(3)]]
+        n_in, a1, a2 = nn[row], e1[row], e2[row]
+        h = float((r - P[0]) @ n_in)  # r lies on the inner side
+        F = r - h * n_in
+        orient = np.sign(np.cross(P[1] - P[0], P[2] - P[0]) @ n_in)
+        p2 = [np.array([(X - F) @ a1, (X - F) @ a2]) for X in P]  # vertices in the face plane, F at 0
+        acc = np.zeros(nb)
+        for k in range(3):
+            A, B = p2[k], p2[(k + 1) % 3]
+            dpsi = np.arctan2(A[0] * B[1] - A[1] * B[0], A @ B)  # signed angle from A to B
+            if abs(dpsi) < 1e-15:
+                continue
+            psi = np.arctan2(A[1], A[0]) + x01 * dpsi
+            eh = np.stack([np.cos(psi), np.sin(psi)], axis=1)
+            AB = B - A
+            ell = (A[0] * AB[1] - A[1] * AB[0]) / (eh[:, 0] * AB[1] - eh[:, 1] * AB[0])  # F + ell eh on line AB
+            Phi = np.arctan2(ell, h)
+            phi = Phi[:, None] * x01[None, :]
+            wt = (w01 * dpsi)[:, None] * (Phi[:, None] * w01[None, :]) * np.sin(phi) * np.exp(-mu * h / np.cos(phi))
+            dx = -np.sin(phi) * eh[:, 0:1]  # tangential part of unit(r - s) in the face frame
+            dy = -np.sin(phi) * eh[:, 1:2]
+            Z = zernike(Np, dx.reshape(-1), dy.reshape(-1))
+            acc += orient * (wt.reshape(-1) @ Z)
+        g[l] = acc / np.sqrt(area[row])
+    return g
+
+
 def receiver_functional(verts, tets, mu_tet, Np, receiver, nq=48):
     """J(rho) = mean over receiver tets e of rho_T(centroid_e) = gvec . rho.
     Returns gvec [nrows, nb] and dgvec/dmu_e stacked per receiver tet."""

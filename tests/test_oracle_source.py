@@ -146,3 +146,28 @@ def test_adaptive_interior_rule_on_a_thin_tet(oracle_mod):
     rho = oracle_mod.source_vector(verts, tets, [3], 2)
     fixed = oracle_mod.tet_density(verts, tets, np.zeros(1), 2, rho, nq=32)[0]
     assert abs(fixed - _solid_angle(cen, *verts[:3])) > 1e-6
+
+
+def test_split_polar_interior_rule(oracle_mod):
+    """The rule that splits each face at the foot of r and integrates in polar
+    angles seen from r reproduces the adaptive cubature on the thin tets of the
+    768-tet cuboid, where a 32 x 32 collapsed rule is off by percents, and the
+    solid angles of the thin tet below."""
+    m = inputs.kuhn_cuboid_mesh(4)
+    mu = 0.4 * np.pi
+    for t in (296, 343):
+        r = m.verts[m.tets[t]].mean(axis=0)
+        ga, _ = oracle_mod.interior_g(m.verts, m.tets, t, r, mu, 4, nq=None)
+        gs = oracle_mod.interior_g_split(m.verts, m.tets, t, r, mu, 4, n=24)
+        g32, _ = oracle_mod.interior_g(m.verts, m.tets, t, r, mu, 4, nq=32)
+        s = np.abs(ga).max()
+        assert np.abs(gs - ga).max() <= 1e-6 * s
+        assert np.abs(g32 - ga).max() > 1e-3 * s
+    verts = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0], [0.3, 0.3, 0.02]])
+    tets = np.array([[0, 1, 2, 3]], dtype=np.int32)
+    cen = verts.mean(axis=0)
+    g = oracle_mod.interior_g_split(verts, tets, 0, cen, 0.0, 2, n=24)
+    for f in range(4):
+        rho = oracle_mod.source_vector(verts, tets, [f], 2)
+        p = verts[[tets[0, (f + 1 + k) % 4] for k in range(3)]]
+        assert np.sum(g * rho) == pytest.approx(_solid_angle(cen, *p), rel=1e-9)
