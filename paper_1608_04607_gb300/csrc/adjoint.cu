@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "dfm_internal.cuh"
+#include "interior_rule.cuh"
 #include "node.cuh"
 
 namespace dfm {
@@ -201,6 +202,63 @@ int launch_contract(int Np, const PairConst* pairs, int64_t npairs, const double
   return DFM_OK;
 }
 
+// The same functional with the split polar rule of interior_rule.cuh (3 nq^2
+// nodes per face), which stays accurate when the centroid is close to a face.
+template <int NP>
+__global__ void interior_density_polar_kernel(const double* __restrict__ V, const int32_t* __restrict__ tets,
+                                              const FaceGeom* __restrict__ geom, const double* __restrict__ mu_tet,
+                                              double mu_uniform, const int64_t* __restrict__ list,
+                                              const double* __restrict__ weights, int n,
+                                              const double* __restrict__ gl_x, const double* __restrict__ gl_w,
+                                              int nq, double* __restrict__ gvec, double* __restrict__ dgvec) {
+  constexpr int NB = (NP + 1) * (NP + 2) / 2;
+  const int lane = threadIdx.x & 31;
+  const int64_t wg = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (wg >= 4 * (int64_t)n) return;
+  const int i = (int)(wg >> 2);
+  const int l = (int)(wg & 3);
+  const int64_t e = list[i];
+  const double wt = weights ? weights[i] : 1.0;
+  const int32_t* tv = tets + 4 * e;
+  double r[3] = {0, 0, 0};
+  for (int v = 0; v < 4; ++v)
+    for (int c = 0; c < 3; ++c) r[c] += 0.25 * V[3 * (int64_t)tv[v] + c];
+  const FaceGeom F = geom[4 * e + l];
+  double p[3][3];
+  for (int k = 0; k < 3; ++k)
+    for (int c = 0; c < 3; ++c) p[k][c] = V[3 * (int64_t)tv[(l + 1 + k) & 3] + c];
+  const double mu = mu_tet ? mu_tet[e] : mu_uniform;
+  double g[NB], dg[NB], Z[NB];
+#pragma unroll
+  for (int a = 0; a < NB; ++a) g[a] = dg[a] = 0.0;
+  const int nodes = 3 * nq * nq;
+  for (int k = lane; k < nodes; k += 32) {
+    const rule::PolarNode q = rule::polar_node(p, F.n, F.e1, F.e2, r, nq, k, gl_x, gl_w);
+    if (q.w == 0.0) continue;
+    const double ker = q.w * exp(-mu * q.R);
+    zernike<NP, double>(q.dx, q.dy, Z);
+#pragma unroll
+    for (int a = 0; a < NB; ++a) {
+      g[a] = fma(ker, Z[a], g[a]);
+      dg[a] = fma(-q.R * ker, Z[a], dg[a]);
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < NB; ++a)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      g[a] += __shfl_xor_sync(0xffffffffu, g[a], o);
+      dg[a] += __shfl_xor_sync(0xffffffffu, dg[a], o);
+    }
+  if (lane == 0) {
+    const double s = wt / sqrt(F.area);
+    for (int a = 0; a < NB; ++a) {
+      atomicAdd(&gvec[(4 * e + l) * NB + a], s * g[a]);
+      if (dgvec) atomicAdd(&dgvec[(4 * e + l) * NB + a], s * dg[a]);
+    }
+  }
+}
+
 // out[r][e] = sum over tet e's four rows of gvec . rho_r: one warp per (r, e),
 // the lanes striding over the 4 nb contiguous coefficients of the tet
 __global__ void tet_density_kernel(const double* __restrict__ g, const double* __restrict__ rho, int64_t nt,
@@ -228,8 +286,10 @@ extern "C" int dfm_interior_density(const dfm_mesh* mesh, int Np, const double* 
                                     double* dgvec, void* stream) {
   if (!mesh || !tets_host || !gvec || n < 1 || Np < 0 || Np > 8)
     return set_error(DFM_ERR_ARG, "dfm_interior_density: bad argument");
+  const bool polar = nq < 0;  // the split polar rule with |nq| points per direction
+  if (polar) nq = -nq;
   if (nq == 0) nq = 32;
-  if (nq < 2 || nq > 64) return set_error(DFM_ERR_ARG, "dfm_interior_density: nq must be in 2..64");
+  if (nq < 2 || nq > 64) return set_error(DFM_ERR_ARG, "dfm_interior_density: |nq| must be in 2..64");
   if (!mu && !(mu_uniform >= 0)) return set_error(DFM_ERR_ARG, "dfm_interior_density: mu_uniform must be >= 0");
   for (int i = 0; i < n; ++i)
     if (tets_host[i] < 0 || tets_host[i] >= mesh->nt) return set_error(DFM_ERR_ARG, "dfm_interior_density: bad tet id");
@@ -251,8 +311,13 @@ extern "C" int dfm_interior_density(const dfm_mesh* mesh, int Np, const double* 
   const double* wp = weights_host ? w : nullptr;
 #define CASE(N)                                                                                                  \
   case N:                                                                                                        \
-    interior_density_kernel<N><<<blocks, 128, 0, st>>>(mesh->verts, mesh->tets, mesh->geom, mu, mu_uniform, list, wp, \
-                                                       n, glx, glw, nq, gvec, dgvec);                            \
+    if (polar)                                                                                                   \
+      interior_density_polar_kernel<N><<<blocks, 128, 0, st>>>(mesh->verts, mesh->tets, mesh->geom, mu,         \
+                                                               mu_uniform, list, wp, n, glx, glw, nq, gvec,     \
+                                                               dgvec);                                           \
+    else                                                                                                         \
+      interior_density_kernel<N><<<blocks, 128, 0, st>>>(mesh->verts, mesh->tets, mesh->geom, mu, mu_uniform, list, \
+                                                         wp, n, glx, glw, nq, gvec, dgvec);                      \
     break;
   switch (Np) { CASE(0) CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) }
 #undef CASE

@@ -131,7 +131,8 @@ def test_cuboid_matches_oracle_and_exact_solution(D, oracle_mod, case):
     the oracle's same rule (FP32 blocks and solve: 2e-4 of the maximum), with
     the 64-point rule against the oracle's adaptive cubature (within the
     64-point rule's own deviation, measured by the oracle, plus the same 2e-4),
-    and the relative mean error against the exact ray solution."""
+    the split polar rule against the adaptive cubature (2e-4), and the relative
+    mean error against the exact ray solution."""
     with open(os.path.join(GOLDEN, case + ".json")) as f:
         gold = json.load(f)
     m = kuhn_cuboid_mesh(gold["n"], length=gold["length"], jitter=gold["jitter"], seed=gold["seed"])
@@ -147,4 +148,7 @@ def test_cuboid_matches_oracle_and_exact_solution(D, oracle_mod, case):
     assert np.abs(d64 - ref).max() <= (gold["nq64_max_dev"] + 2e-4) * np.abs(ref).max()
     err = np.mean(np.abs(d64 - exact)) / np.mean(exact)
     assert abs(err - gold["rel_mean_err"]) < 1e-3
+    # the split polar rule (24 points per direction) against the adaptive cubature
+    dpol = _densities(D, mesh, m, gold["Np"], gold["mu"], rho, -24)
+    assert np.abs(dpol - ref).max() <= 2e-4 * np.abs(ref).max()
     assert err < 0.3  # the ray solution is approached as N_p grows (about 5% at N_p = 16-20 in the paper)
