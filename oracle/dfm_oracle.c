@@ -382,7 +382,7 @@ static void block_fixed(const double* V, const int32_t* T, int64_t t, int f, int
         if (S == 0.0 && dS == 0.0) continue;
         if (kind) {
           double lt = transmission(-vdot(d, dstf.n), md->c_ratio, md->z_src, md->z_dst);
-          double wl = kind == 1 ? lt : 1.0 - lt;
+          double wl = kind == 1 ? lt : (ORC_MUTATE == 11 ? lt : 1.0 - lt);
           if (wl == 0.0) continue;
           w *= wl;
         }

@@ -6,7 +6,7 @@ Zernike polynomials, a dropped normalisation factor, the wrong face frame for
 the receiving face, a halved damping exponent, a transposed operator, an
 unnormalised tangent axis, a missing clip of the integration triangle, a dropped
 cosine in the interior density, swapped impedances in the transmission law,
-and an inverted Snell ratio.  A second set plants mistakes in the oracle's
+an inverted Snell ratio and a reflection weighted like a transmission.  A second set plants mistakes in the oracle's
 Python half (a reversed point-source ray, |T| for sqrt|T|, a dropped inverse
 norm, a left-handed frame, a left-out reflection part) by rewriting one line of
 the function's source.  Only the oracle is mutated, on the CPU."""
@@ -33,6 +33,7 @@ MUTANTS = {
     8: "interior density without the cosine",
     9: "impedances swapped in the transmission law",
     10: "inverted Snell ratio for the transmitted direction",
+    11: "interface reflection weighted by lambda_t instead of 1 - lambda_t",
 }
 
 
@@ -78,6 +79,8 @@ def test_a_pin_fails_on_each_planted_mistake(oracle_mod, k):
         pins = list(_pins(oracle_mod))
         if k == 10:
             pins = [lambda: media.test_monte_carlo_across_an_interface(oracle_mod, 1)]
+        if k == 11:
+            pins = [lambda: media.test_conservation_with_unequal_media(oracle_mod)]
         for pin in pins:
             try:
                 pin()
