@@ -288,12 +288,18 @@ int dfm_precond_apply(const dfm_op* op, int precision, int degree, int transpose
  *   g_e[l][nm] = |T_l|^{-1/2} Int_{T_l} Z_nm(p(s->r_e)) cos(vartheta) exp(-mu_e |r_e - s|) / |r_e - s|^2 ds,
  * at r_e = the tet's centroid, p(s->r) the tangential part of unit(r - s) in
  * face l's frame, and dg_e = d g_e / d mu_e.  Each face integral runs in
- * FP64 with, for nq >= 0, a collapsed tensor Gauss-Legendre rule of order nq
- * on the triangle (0 = 32), or, for nq < 0, the split polar rule with |nq|
- * points per direction: the face is cut at the foot of r_e into three signed
- * triangles integrated in the azimuth and polar angle seen from r_e
- * (3 nq^2 nodes), which stays accurate when r_e is close to the face (thin
- * tets), where the flat rule loses digits.  |nq| in 2..64.
+ * FP64 with, for nq < 0, the split polar rule with |nq| points per direction:
+ * the face is cut at the foot of r_e into three signed triangles, one per
+ * edge, integrated in the polar angle seen from r_e and in the azimuth,
+ * sampled through the position along the edge with a tangent substitution
+ * (each edge cut at the foot of the perpendicular from the foot of r_e;
+ * 6 nq^2 nodes), which stays accurate when r_e is close to the face or its
+ * foot close to an edge (thin tets); nq = 0 selects that rule with 24 points
+ * per direction (the default; within 1e-13 of the largest entry of the
+ * adaptive cubature of the integral on the jittered Kuhn meshes tested).
+ * nq > 0 selects a collapsed tensor Gauss-Legendre rule of order nq
+ * on the flat triangle, which loses digits (percents of the largest density
+ * at order 32) when r_e is close to the face.  |nq| in 2..64.
  *   tets_host: HOST int64 [n] tet ids; weights_host: HOST FP64 [n] or NULL (1).
  *   gvec, dgvec: device FP64 [rows][nb]; on return gvec[4e+l] += w_e g_e[l] and
  *   dgvec[4e+l] += w_e dg_e[l] for the listed tets (other rows untouched), so

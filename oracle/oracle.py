@@ -694,15 +694,20 @@ def interior_g(verts, tets, t, r, mu, Np, nq=48, rtol=1e-11):
 
 def interior_g_split(verts, tets, t, r, mu, Np, n=16):
     """The functional of interior_g by a rule that stays exact when r is close
-    to a face: each face is split at the foot F of r (height h) into three
-    signed triangles (F, A, B) over its edges and integrated in polar
-    coordinates seen from r: the azimuth psi about the face normal (from the
-    direction of A - F to that of B - F) and the polar angle phi up to the edge,
-    phi in [0, atan(l(psi)/h)], l(psi) the distance from F to the edge along
-    psi.  The area element times cos / R^2 is sin(phi) dphi dpsi, so with
-    exp(-mu h / cos(phi)) and the Zernike vector of the direction the integrand
-    is smooth and n-point Gauss-Legendre in psi and in phi converges fast.
-    Returns g[4, nb] (no dg)."""
+    to a face or the foot F of r (height h) is close to a face edge: each face
+    is split at F into three signed triangles (F, A, B) over its edges and
+    integrated in polar coordinates seen from r.  The area element times
+    cos / R^2 is sin(phi) dphi dpsi (psi the azimuth about the face normal,
+    phi the polar angle up to the edge, phi in [0, atan(l / h)], l = |X - F|
+    for the edge point X at that azimuth).  The azimuth is sampled through the
+    edge point X = M + u t (M the foot of the perpendicular from F to the
+    line AB, t its unit direction, d = |M - F|): dpsi = d du / (d^2 + u^2),
+    u = c tan(s) with c = sqrt(h^2 + d^2) and Gauss nodes uniform in s, the
+    edge cut at M (or at its middle in s when M lies outside the edge).  The
+    integrand, with exp(-mu h / cos(phi)) and the Zernike vector of the
+    direction, varies in u on the scale c, so n-point Gauss-Legendre in s and
+    in phi converges fast whether r is close to the face (h << d) or F close
+    to an edge's line (d << h).  Returns g[4, nb] (no dg)."""
     nb = nbasis(Np)
     e1, e2, nn = face_frames(verts, tets)
     area = face_areas(verts, tets)
@@ -721,20 +726,29 @@ def interior_g_split(verts, tets, t, r, mu, Np, n=16):
         acc = np.zeros(nb)
         for k in range(3):
             A, B = p2[k], p2[(k + 1) % 3]
-            dpsi = np.arctan2(A[0] * B[1] - A[1] * B[0], A @ B)  # signed angle from A to B
-            if abs(dpsi) < 1e-15:
+            tdir = (B - A) / np.linalg.norm(B - A)
+            d = abs(A[0] * tdir[1] - A[1] * tdir[0])  # distance from F to the line AB
+            if d < 1e-15 * np.linalg.norm(B - A):
                 continue
-            psi = np.arctan2(A[1], A[0]) + x01 * dpsi
-            eh = np.stack([np.cos(psi), np.sin(psi)], axis=1)
-            AB = B - A
-            ell = (A[0] * AB[1] - A[1] * AB[0]) / (eh[:, 0] * AB[1] - eh[:, 1] * AB[0])  # F + ell eh on line AB
-            Phi = np.arctan2(ell, h)
-            phi = Phi[:, None] * x01[None, :]
-            wt = (w01 * dpsi)[:, None] * (Phi[:, None] * w01[None, :]) * np.sin(phi) * np.exp(-mu * h / np.cos(phi))
-            dx = -np.sin(phi) * eh[:, 0:1]  # tangential part of unit(r - s) in the face frame
-            dy = -np.sin(phi) * eh[:, 1:2]
-            Z = zernike(Np, dx.reshape(-1), dy.reshape(-1))
-            acc += orient * (wt.reshape(-1) @ Z)
+            sign = np.sign(A[0] * B[1] - A[1] * B[0])  # orientation of the triangle (F, A, B)
+            uA, uB = A @ tdir, B @ tdir
+            M = A - uA * tdir
+            c = np.hypot(h, d)
+            sA, sB = np.arctan2(uA, c), np.arctan2(uB, c)
+            cut = 0.0 if sA < 0.0 < sB else 0.5 * (sA + sB)
+            for s0, s1 in ((sA, cut), (cut, sB)):
+                sv = s0 + (s1 - s0) * x01
+                u = c * np.tan(sv)
+                ell = np.sqrt(d * d + u * u)
+                eh = (M[None, :] + u[:, None] * tdir[None, :]) / ell[:, None]
+                Phi = np.arctan2(ell, h)
+                phi = Phi[:, None] * x01[None, :]
+                jac = (s1 - s0) * w01 * c / np.cos(sv) ** 2 * d / ell ** 2  # dpsi per unit of s
+                wt = jac[:, None] * (Phi[:, None] * w01[None, :]) * np.sin(phi) * np.exp(-mu * h / np.cos(phi))
+                dx = -np.sin(phi) * eh[:, 0:1]  # tangential part of unit(r - s) in the face frame
+                dy = -np.sin(phi) * eh[:, 1:2]
+                Z = zernike(Np, dx.reshape(-1), dy.reshape(-1))
+                acc += orient * sign * (wt.reshape(-1) @ Z)
         g[l] = acc / np.sqrt(area[row])
     return g
 

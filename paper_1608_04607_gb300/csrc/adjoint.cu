@@ -202,7 +202,7 @@ int launch_contract(int Np, const PairConst* pairs, int64_t npairs, const double
   return DFM_OK;
 }
 
-// The same functional with the split polar rule of interior_rule.cuh (3 nq^2
+// The same functional with the split polar rule of interior_rule.cuh (6 nq^2
 // nodes per face), which stays accurate when the centroid is close to a face.
 template <int NP>
 __global__ void interior_density_polar_kernel(const double* __restrict__ V, const int32_t* __restrict__ tets,
@@ -231,7 +231,7 @@ __global__ void interior_density_polar_kernel(const double* __restrict__ V, cons
   double g[NB], dg[NB], Z[NB];
 #pragma unroll
   for (int a = 0; a < NB; ++a) g[a] = dg[a] = 0.0;
-  const int nodes = 3 * nq * nq;
+  const int nodes = 6 * nq * nq;
   for (int k = lane; k < nodes; k += 32) {
     const rule::PolarNode q = rule::polar_node(p, F.n, F.e1, F.e2, r, nq, k, gl_x, gl_w);
     if (q.w == 0.0) continue;
@@ -286,9 +286,12 @@ extern "C" int dfm_interior_density(const dfm_mesh* mesh, int Np, const double* 
                                     double* dgvec, void* stream) {
   if (!mesh || !tets_host || !gvec || n < 1 || Np < 0 || Np > 8)
     return set_error(DFM_ERR_ARG, "dfm_interior_density: bad argument");
-  const bool polar = nq < 0;  // the split polar rule with |nq| points per direction
+  // nq < 0: the split polar rule with |nq| points per direction; nq = 0: the
+  // same rule with 24 points (accurate for centroids close to a face, as on
+  // thin tets); nq > 0: the flat collapsed Gauss rule of that order
+  if (nq == 0) nq = -24;
+  const bool polar = nq < 0;
   if (polar) nq = -nq;
-  if (nq == 0) nq = 32;
   if (nq < 2 || nq > 64) return set_error(DFM_ERR_ARG, "dfm_interior_density: |nq| must be in 2..64");
   if (!mu && !(mu_uniform >= 0)) return set_error(DFM_ERR_ARG, "dfm_interior_density: mu_uniform must be >= 0");
   for (int i = 0; i < n; ++i)

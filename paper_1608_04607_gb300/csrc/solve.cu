@@ -468,6 +468,7 @@ int gmres(const Ctx& c, const T* b, T* x, double tol, int m, int d, int max_iter
       } else {
         rc = apply_poly_op(vj, w);
       }
+      if (rc) return rc;
       // classical Gram-Schmidt: h = V^T w (plus |w|^2 as the last entry)
       rc = dots<T>(c, V, n, j + 2, w, partial, h_dev, hh.data());
       if (rc) return rc;

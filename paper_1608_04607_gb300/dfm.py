@@ -425,9 +425,10 @@ def moment_coefficients(mu_rhs, mu_c, K):
 def interior_density(mesh: Mesh, Np: int, tets, weights=None, mu=0.0, nq=0, gvec=None, dgvec=None):
     """Interior density coefficients at tet centroids (dfm_interior_density):
     adds w_e g_e into gvec and w_e dg_e/dmu_e into dgvec (FP64 [rows, nb], created
-    zeroed when not given).  J(rho) = (gvec * rho).sum().  nq >= 0: flat
-    collapsed Gauss rule of that order per face (0 = 32); nq < 0: the split
-    polar rule with |nq| points per direction (accurate for thin tets)."""
+    zeroed when not given).  J(rho) = (gvec * rho).sum().  nq = 0 (default):
+    the split polar rule with 24 points per direction; nq < 0: that rule with
+    |nq| points (both accurate for thin tets); nq > 0: the flat collapsed Gauss
+    rule of that order per face."""
     import torch
 
     nb = nbasis(Np)

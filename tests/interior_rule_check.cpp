@@ -24,7 +24,7 @@ int main() {
     for (double* a : {nin, e1, e2, r})
       for (int c = 0; c < 3 && ok; ++c) ok = std::scanf("%lf", &a[c]) == 1;
     if (!ok) break;
-    for (int k = 0; k < 3 * n * n; ++k) {
+    for (int k = 0; k < 6 * n * n; ++k) {
       const dfm::rule::PolarNode q = dfm::rule::polar_node(P, nin, e1, e2, r, n, k, gx.data(), gw.data());
       std::printf("%.17g %.17g %.17g %.17g\n", q.w, q.R, q.dx, q.dy);
     }

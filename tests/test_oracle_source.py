@@ -161,8 +161,18 @@ def test_split_polar_interior_rule(oracle_mod):
         gs = oracle_mod.interior_g_split(m.verts, m.tets, t, r, mu, 4, n=24)
         g32, _ = oracle_mod.interior_g(m.verts, m.tets, t, r, mu, 4, nq=32)
         s = np.abs(ga).max()
-        assert np.abs(gs - ga).max() <= 1e-6 * s
+        assert np.abs(gs - ga).max() <= 1e-11 * s
         assert np.abs(g32 - ga).max() > 1e-3 * s
+    # a jittered-cube tet whose centroid's foot lies within 0.02 h of a face
+    # edge on two faces (an azimuth rule uniform in the angle is off by 4e-4
+    # there with 24 points)
+    m = inputs.kuhn_cube_mesh(8, jitter=0.2, seed=0)
+    mu_t = inputs.lognormal_mu(m)
+    t = 1373
+    r = m.verts[m.tets[t]].mean(axis=0)
+    ga, _ = oracle_mod.interior_g(m.verts, m.tets, t, r, float(mu_t[t]), 4, nq=None, rtol=1e-13)
+    gs = oracle_mod.interior_g_split(m.verts, m.tets, t, r, float(mu_t[t]), 4, n=24)
+    assert np.abs(gs - ga).max() <= 1e-12 * np.abs(ga).max()
     verts = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0], [0.3, 0.3, 0.02]])
     tets = np.array([[0, 1, 2, 3]], dtype=np.int32)
     cen = verts.mean(axis=0)
