@@ -654,7 +654,6 @@ def run_batched(args):
     R = len(mu_rhs)
     tol = args.tol if args.tol else w["tol"]
     mu_c, K = 0.105, 3
-    coef = dfm.moment_coefficients(mu_rhs, mu_c, K)
     mesh = dfm.Mesh(m.verts, m.tets, refl=w["refl"])
     ops = [dfm.Operator(mesh, Np, mu=mu_c, precision=dfm.F32, moment=k) for k in range(K)]
 
@@ -663,8 +662,8 @@ def run_batched(args):
             o.reassemble(mu_c)
         rho0 = dfm.source(mesh, Np, rows)
         # degree 64 with restart 32: 7.6 solves/s against 6.6 with degree 32, restart 128
-        return dfm.solve_combo(ops, coef, rho0, tol=tol, batch=args.batch, poly_degree=args.poly or 64,
-                               restart=args.restart or 32, precond_precision=PRECOND[args.precond])
+        return dfm.solve_damped(ops, mu_rhs, rho0, tol=tol, batch=args.batch, poly_degree=args.poly or 64,
+                                restart=args.restart or 32, precond_precision=PRECOND[args.precond])
 
     rho, info = step()
     torch.cuda.synchronize()

@@ -266,6 +266,25 @@ int dfm_solve(const dfm_op* op, const double* rho0, int R, double* rho, const df
 int dfm_solve_combo(const dfm_op* const* ops, int K, const double* coef_host, const double* rho0, int R, double* rho,
                     const dfm_solve_opts* opts, void* stream, dfm_solve_info* info);
 
+/* Stationary densities for right-hand sides that each have their own uniform
+ * damping mu_r (the absorption factor exp(-mu L) of Sec. 2, in the closed
+ * form of Sec. 3.3), from the damping moments of one assembly:
+ *   rho_r = (I - B(mu_r))^{-1} rho0_r,
+ *   B(mu_r) = sum_{k<K} (mu_r - mu_c)^k / k! B^(k),   B^(k) = d^k B / d mu^k at mu_c,
+ * with the Taylor weights computed here.  moments[k] is the operator
+ * assembled with dfm_params.moment = k; all K (1..4) share the mesh, Np,
+ * FP32 precision and one uniform damping mu_c (dfm_params.mu == NULL,
+ * mu_uniform = mu_c), which is read from them.  The truncation error of an
+ * entry is bounded by (|mu_r - mu_c| L)^K / K! times the entry's size, L the
+ * longest chord of its tet.  mu_rhs_host: HOST FP64 [R], each finite and >= 0;
+ * rho0, rho: device FP64 [R][rows][nb].  Solved as dfm_solve_combo with these
+ * weights (GMRES_IR only, batched; a low-precision preconditioner copy is made
+ * from moments[0] = B(mu_c)).  Errors: DFM_ERR_ARG (a moment of the wrong
+ * order, a per-tet damping field or different mu_c, a bad mu_r) and those of
+ * dfm_solve. */
+int dfm_solve_damped(const dfm_op* const* moments, int K, const double* mu_rhs_host, const double* rho0, int R,
+                     double* rho, const dfm_solve_opts* opts, void* stream, dfm_solve_info* info);
+
 /* The inexact polynomial preconditioner of the flexible inner solve
  * (dfm_solve_opts.precond_precision), on its own.  The paper gives no
  * solver; this is a building block for callers' own Krylov methods:
@@ -334,6 +353,26 @@ int dfm_tet_density(const dfm_mesh* mesh, int Np, const double* gvec, const doub
 int dfm_adjoint(const dfm_op* op, const dfm_params* params, const double* rho, int R, const double* gvec,
                 const double* dgvec, double* lambda_out, double* dJ_dmu, const dfm_solve_opts* opts, void* stream,
                 dfm_solve_info* info);
+
+/* Data-wait time-outs.  The pipelined kernels (operator applications,
+ * preconditioner hops) wait on shared-memory barriers for their bulk copies
+ * with a bounded number of polls (a few seconds); a wait that runs out sets
+ * the operator's device error flag, lets the copies in flight land and ends
+ * the kernel, leaving its output incomplete.  dfm_solve, dfm_solve_combo,
+ * dfm_solve_damped and dfm_adjoint read the flag after their iterations and
+ * return DFM_ERR_TIMEOUT; after dfm_apply, dfm_apply_combo or
+ * dfm_precond_apply the caller reads it with dfm_op_check_error.
+ *   dfm_op_check_error: waits on the stream, returns DFM_ERR_TIMEOUT if a
+ *     kernel of op timed out since the last check (and clears the flag), else
+ *     DFM_OK.
+ *   dfm_selftest_timeout: runs one kernel whose wait is on a barrier that
+ *     nothing completes, with a limit of `polls` polls (1..1000000, each at
+ *     most about a microsecond), so that the time-out path sets op's flag
+ *     exactly as a stalled copy would; asynchronous.  For tests of callers'
+ *     error handling. */
+#define DFM_ERR_TIMEOUT (-8) /* a kernel gave up waiting for its data (see dfm_op_check_error) */
+int dfm_op_check_error(const dfm_op* op, void* stream);
+int dfm_selftest_timeout(const dfm_op* op, int polls, void* stream);
 
 /* Kernel accounting, for benchmarks and profiling.
  *   dfm_launch_count: number of CUDA kernels this library has launched in the

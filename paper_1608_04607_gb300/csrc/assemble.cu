@@ -319,6 +319,8 @@ extern "C" int dfm_assemble_into(const dfm_mesh* mesh, const dfm_params* p, dfm_
   cudaStream_t st = as_stream(stream);
   op->lp_valid = false;  // the low-precision preconditioner copies follow the blocks
   op->lpT_valid = false;
+  op->mu_uniform = p->mu ? -1.0 : p->mu_uniform;
+  op->moment = p->moment;
   const int q = p->quad_order ? p->quad_order : p->Np + 6;
   const double deg = p->max_patch_deg > 0 ? p->max_patch_deg : 60.0;
   const float cos_max = (float)cos(deg * M_PI / 180.0);

@@ -53,6 +53,10 @@ struct dfm_op {
   int64_t nrows = 0, row_stride = 0;
   void* vals = nullptr;  // device
   int64_t bytes = 0;
+  // damping of the last assembly: the uniform mu (or -1 for a per-tet field)
+  // and the moment k of d^k B / d mu^k it holds
+  double mu_uniform = -1.0;
+  int moment = 0;
   int* dev_err = nullptr;  // device flag set by kernels whose bounded waits time out
   // 16-bit copy of the blocks for inexact preconditioner hops (same layout)
   void* lp_vals = nullptr;
@@ -126,6 +130,8 @@ inline LowpView lowp_of(const dfm_op* op, int trans) {
 // two that keeps |v| vscale <= 2^-8).
 int hop_horner(const dfm_op* op, int R, int d, const float* v, float* z, void* vp, void* ha, void* hb, float vscale,
                cudaStream_t st, int trans = 0);
+// reads and clears op's time-out flag (waits on st): DFM_ERR_TIMEOUT if set
+int read_timeout_flag(const dfm_op* op, cudaStream_t st, const char* who);
 // implemented in quad.cu
 int gauss_legendre_device(int q, double* x, double* w, cudaStream_t st);
 }  // namespace dfm

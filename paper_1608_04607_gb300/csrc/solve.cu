@@ -1169,15 +1169,9 @@ int solve_impl(const dfm_op* op, const dfm_op* const* combo, int K, const double
     if (rs != DFM_OK && status == DFM_OK) status = rs;
   }
   if (info) *info = acc_info;
-  if (op->dev_err) {  // a pipelined operator application gave up waiting
-    int e = 0;
-    DFM_CUDA_CHECK(cudaMemcpyAsync(&e, op->dev_err, sizeof(int), cudaMemcpyDeviceToHost, c.st));
-    DFM_CUDA_CHECK(cudaStreamSynchronize(c.st));
-    if (e) {
-      DFM_CUDA_CHECK(cudaMemsetAsync(op->dev_err, 0, sizeof(int), c.st));
-      return set_error(DFM_ERR_CUDA, "dfm_solve: an operator application timed out waiting for its data");
-    }
-  }
+  // a pipelined operator application or hop that gave up waiting for its data
+  const int te = read_timeout_flag(op, c.st, "dfm_solve");
+  if (te) return te;
   return status;
 }
 }  // namespace
@@ -1195,4 +1189,34 @@ extern "C" int dfm_solve_combo(const dfm_op* const* ops, int K, const double* co
     if (!ops[k] || ops[k]->mesh != ops[0]->mesh || ops[k]->Np != ops[0]->Np || ops[k]->precision != DFM_F32)
       return dfm::set_error(DFM_ERR_ARG, "dfm_solve_combo: operators must be FP32 and share mesh and Np");
   return dfm::solve_impl(ops[0], ops, K, coef_host, rho0, R, rho, opts, stream, info);
+}
+
+extern "C" int dfm_solve_damped(const dfm_op* const* moments, int K, const double* mu_rhs_host, const double* rho0,
+                                int R, double* rho, const dfm_solve_opts* opts, void* stream, dfm_solve_info* info) {
+  if (!moments || K < 1 || K > 4 || !mu_rhs_host || R < 1)
+    return dfm::set_error(DFM_ERR_ARG, "dfm_solve_damped: bad argument");
+  for (int k = 0; k < K; ++k) {
+    const dfm_op* o = moments[k];
+    if (!o || o->mesh != moments[0]->mesh || o->Np != moments[0]->Np || o->precision != DFM_F32)
+      return dfm::set_error(DFM_ERR_ARG, "dfm_solve_damped: moments must be FP32 and share mesh and Np");
+    if (o->moment != k)
+      return dfm::set_error(DFM_ERR_ARG, "dfm_solve_damped: moments[k] must be assembled with moment = k");
+    if (!(o->mu_uniform >= 0.0) || o->mu_uniform != moments[0]->mu_uniform)
+      return dfm::set_error(DFM_ERR_ARG, "dfm_solve_damped: moments must share one uniform damping mu_c");
+  }
+  const double mu_c = moments[0]->mu_uniform;
+  // Taylor weights of B(mu_r) = sum_k (mu_r - mu_c)^k / k! B^(k) about the
+  // damping the moments were assembled at (the damping factor exp(-mu L) of
+  // Sec. 2 is analytic in mu)
+  std::vector<double> coef((size_t)R * K);
+  for (int r = 0; r < R; ++r) {
+    const double mr = mu_rhs_host[r];
+    if (!(mr >= 0.0) || isinf(mr)) return dfm::set_error(DFM_ERR_ARG, "dfm_solve_damped: mu_rhs must be finite, >= 0");
+    double c = 1.0;
+    for (int k = 0; k < K; ++k) {
+      coef[(size_t)r * K + k] = c;
+      c *= (mr - mu_c) / (k + 1);
+    }
+  }
+  return dfm::solve_impl(moments[0], moments, K, coef.data(), rho0, R, rho, opts, stream, info);
 }

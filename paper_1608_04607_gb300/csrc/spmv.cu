@@ -605,3 +605,48 @@ extern "C" int dfm_apply(const dfm_op* op, const void* x, const void* x0, void* 
                          int xtype, void* stream) {
   return dfm::apply_impl(op, x, x0, y, R, alpha, trans, xtype, dfm::as_stream(stream));
 }
+
+namespace dfm {
+namespace {
+// One barrier that expects a single arrival nobody makes: the bounded wait of
+// the pipelines runs out after `polls` polls and takes the same exit as a
+// stalled copy (flag the operator, end the kernel).  No copy is in flight.
+__global__ void wait_timeout_selftest_kernel(long long polls, int* __restrict__ err) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    pipe::mbar_init(&bar, 1);
+    pipe::mbar_init_fence();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    bool done = false;
+    for (long long i = 0; i < polls && !done; ++i) done = pipe::mbar_try_wait(&bar, 0);
+    if (!done) atomicExch(err, 1);
+  }
+}
+}  // namespace
+
+int read_timeout_flag(const dfm_op* op, cudaStream_t st, const char* who) {
+  if (!op->dev_err) return DFM_OK;
+  int e = 0;
+  DFM_CUDA_CHECK(cudaMemcpyAsync(&e, op->dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  DFM_CUDA_CHECK(cudaStreamSynchronize(st));
+  if (!e) return DFM_OK;
+  DFM_CUDA_CHECK(cudaMemsetAsync(op->dev_err, 0, sizeof(int), st));
+  return set_error(DFM_ERR_TIMEOUT, std::string(who) + ": a kernel timed out waiting for its data");
+}
+}  // namespace dfm
+
+extern "C" int dfm_op_check_error(const dfm_op* op, void* stream) {
+  if (!op) return dfm::set_error(DFM_ERR_ARG, "dfm_op_check_error: NULL operator");
+  return dfm::read_timeout_flag(op, dfm::as_stream(stream), "dfm_op_check_error");
+}
+
+extern "C" int dfm_selftest_timeout(const dfm_op* op, int polls, void* stream) {
+  if (!op || !op->dev_err || polls < 1 || polls > 1000000)
+    return dfm::set_error(DFM_ERR_ARG, "dfm_selftest_timeout: bad argument (1 <= polls <= 1000000)");
+  dfm::wait_timeout_selftest_kernel<<<1, 32, 0, dfm::as_stream(stream)>>>((long long)polls, op->dev_err);
+  DFM_LAUNCHED();
+  DFM_CUDA_CHECK(cudaGetLastError());
+  return DFM_OK;
+}

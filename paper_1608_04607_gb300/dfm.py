@@ -25,6 +25,7 @@ DFM_ERR_OOM = -4
 DFM_ERR_NOT_CONVERGED = -5
 DFM_ERR_NONFINITE = -6
 DFM_ERR_UNSUPPORTED = -7
+DFM_ERR_TIMEOUT = -8
 
 F64, F32, BF16, F16, FP8E4M3 = 0, 1, 2, 3, 4
 NEUMANN, GMRES, GMRES_IR = 0, 1, 2
@@ -87,6 +88,10 @@ SIGNATURES = {
     "dfm_precond_apply": (_i, [_vp, _i, _i, _i, _vp, _vp, _i, _vp]),
     "dfm_solve_combo": (_i, [_vp, _i, _vp, _vp, _i, _vp, ctypes.POINTER(SolveOpts), _vp, ctypes.POINTER(SolveInfo)]),
     "dfm_solve": (_i, [_vp, _vp, _i, _vp, ctypes.POINTER(SolveOpts), _vp, ctypes.POINTER(SolveInfo)]),
+    "dfm_solve_damped": (_i, [_vp, _i, _vp, _vp, _i, _vp, ctypes.POINTER(SolveOpts), _vp,
+                              ctypes.POINTER(SolveInfo)]),
+    "dfm_op_check_error": (_i, [_vp, _vp]),
+    "dfm_selftest_timeout": (_i, [_vp, _i, _vp]),
     "dfm_interior_density": (_i, [_vp, _i, _vp, _d, _vp, _vp, _i, _i, _vp, _vp, _vp]),
     "dfm_tet_density": (_i, [_vp, _i, _vp, _vp, _i, _vp, _vp]),
     "dfm_adjoint": (_i, [_vp, ctypes.POINTER(Params), _vp, _i, _vp, _vp, _vp, _vp, ctypes.POINTER(SolveOpts), _vp,
@@ -235,8 +240,14 @@ class Operator:
 
         p = Params()
         p.Np = Np
+        if isinstance(mu, torch.Tensor) and mu.dim() == 0:
+            mu = float(mu)
         if isinstance(mu, torch.Tensor):
-            mu_t = mu.to(device="cuda", dtype=torch.float64).contiguous()
+            # the library reads n_tets values through the pointer
+            if mu.numel() != self.mesh.n_tets:
+                raise DFMError(DFM_ERR_ARG, f"mu: expected {self.mesh.n_tets} per-tet values, got shape "
+                                            f"{tuple(mu.shape)}")
+            mu_t = mu.to(device="cuda", dtype=torch.float64).contiguous().reshape(-1)
             self._keep = [mu_t]
             p.mu = mu_t.data_ptr()
             p.mu_uniform = 0.0
@@ -257,6 +268,11 @@ class Operator:
     @property
     def handle(self):
         return self._h
+
+    def check_error(self):
+        """Raise DFMError(DFM_ERR_TIMEOUT) if a kernel of this operator gave up
+        waiting for its data since the last check (dfm_op_check_error)."""
+        _check(_lib.dfm_op_check_error(self._h, _stream()), "dfm_op_check_error")
 
     def blocks(self):
         """Copy of the block storage as a torch CUDA tensor [rows, 3, nb, nb]."""
@@ -410,16 +426,31 @@ def solve_combo(ops, coef, rho0, tol=1e-8, max_iter=0, restart=0, inner_tol=0.0,
     return rho, info
 
 
-def moment_coefficients(mu_rhs, mu_c, K):
-    """Taylor weights (mu_r - mu_c)^k / k! of the damping moments B^(k)."""
-    mu_rhs = np.atleast_1d(np.asarray(mu_rhs, dtype=np.float64))
-    out = np.empty((mu_rhs.size, K))
-    fact = 1.0
-    for k in range(K):
-        if k > 0:
-            fact *= k
-        out[:, k] = (mu_rhs - mu_c) ** k / fact
-    return out
+def solve_damped(moments, mu_rhs, rho0, tol=1e-8, max_iter=0, restart=0, inner_tol=0.0, poly_degree=0, batch=0,
+                 precond_precision=0):
+    """rho_r = (I - B(mu_r))^{-1} rho0_r for per-right-hand-side uniform damping
+    mu_r, from the damping moments moments[k] (Operator(..., moment=k), all at
+    one uniform mu_c); the library forms B(mu_r) = sum_k (mu_r - mu_c)^k / k!
+    B^(k) (dfm_solve_damped).  Returns (rho, SolveInfo)."""
+    import torch
+
+    mu = np.ascontiguousarray(np.atleast_1d(mu_rhs), dtype=np.float64)
+    R = _vec(rho0, moments[0].n_rows, moments[0].nb, (torch.float64,), "solve_damped: rho0")
+    if mu.shape != (R,):
+        raise DFMError(DFM_ERR_ARG, f"solve_damped: mu_rhs must hold {R} values")
+    rho = torch.empty_like(rho0)
+    o = SolveOpts(method=GMRES_IR, tol=tol, max_iter=max_iter, restart=restart, use_x0=0, inner_tol=inner_tol,
+                  transpose=0, poly_degree=poly_degree, batch=batch, precond_precision=precond_precision)
+    info = SolveInfo()
+    _check(load().dfm_solve_damped(_op_array(moments), len(moments), mu.ctypes.data_as(ctypes.c_void_p), _ptr(rho0),
+                                   R, _ptr(rho), ctypes.byref(o), _stream(), ctypes.byref(info)), "dfm_solve_damped")
+    return rho, info
+
+
+def selftest_timeout(op, polls=1000):
+    """Run the library's time-out self-test kernel on op (dfm_selftest_timeout):
+    a bounded wait that nothing completes sets op's time-out flag."""
+    _check(load().dfm_selftest_timeout(op.handle, int(polls), _stream()), "dfm_selftest_timeout")
 
 
 def interior_density(mesh: Mesh, Np: int, tets, weights=None, mu=0.0, nq=0, gvec=None, dgvec=None):
@@ -474,12 +505,20 @@ def tet_density(mesh: Mesh, Np: int, gvec, rho):
 class DFMSolve:
     """rho = (I - B(mu))^{-1} rho0 as a torch.autograd.Function of the per-tet
     damping mu: forward = dfm_assemble + dfm_solve, backward = dfm_adjoint
-    (grad_mu = lambda^T dB/dmu rho, grad_rho0 = lambda).  The functional's own
-    explicit mu-dependence is added by ReceiverFunctional."""
+    (grad_mu = lambda^T dB/dmu rho, grad_rho0 = lambda).  A functional with
+    its own explicit mu-dependence (the dgvec of interior_density) adds
+    dgvec . rho per tet itself.  mu: per-tet [n_tets] tensor, or a 0-dim tensor
+    for uniform damping (its gradient is then the sum over tets)."""
 
     @staticmethod
     def apply(mesh, Np, mu, rho0, tol=1e-8, **solve_kw):
         import torch
+
+        def _grad_mu(per_tet):
+            # a scalar (uniform) damping moves every tet's mu together
+            if mu.dim() == 0:
+                return per_tet.sum().to(mu.dtype)
+            return per_tet.reshape(mu.shape).to(mu.dtype)
 
         class _Fn(torch.autograd.Function):
             @staticmethod
@@ -504,9 +543,9 @@ class DFMSolve:
                         lam, dj, _ = op.adjoint(rho[r:r + 1], gsum[r], tol=tol)
                         grads.append(dj[0])
                         lams.append(lam)
-                    return torch.stack(grads).sum(0), torch.stack(lams)
+                    return _grad_mu(torch.stack(grads).sum(0)), torch.stack(lams)
                 lam, dj, _ = op.adjoint(rho, gsum.reshape(op.n_rows, op.nb), tol=tol)
-                return dj.sum(0), lam.reshape(rho0.shape)
+                return _grad_mu(dj.sum(0)), lam.reshape(rho0.shape)
 
         return _Fn.apply(mu, rho0)
 

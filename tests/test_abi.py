@@ -50,6 +50,9 @@ def test_null_handles_are_rejected_on_the_host():
         "dfm_precond_apply": lambda: L.dfm_precond_apply(None, dfm.F16, 4, 0, None, None, 1, None),
         "dfm_solve": lambda: L.dfm_solve(None, None, 1, None, None, None, None),
         "dfm_solve_combo": lambda: L.dfm_solve_combo(None, 0, None, None, 1, None, None, None, None),
+        "dfm_solve_damped": lambda: L.dfm_solve_damped(None, 0, None, None, 1, None, None, None, None),
+        "dfm_op_check_error": lambda: L.dfm_op_check_error(None, None),
+        "dfm_selftest_timeout": lambda: L.dfm_selftest_timeout(None, 10, None),
         "dfm_adjoint": lambda: L.dfm_adjoint(None, None, None, 1, None, None, None, None, None, None, None),
         "dfm_op_info": lambda: L.dfm_op_info(None, None),
         "dfm_mesh_info": lambda: L.dfm_mesh_info(None, None),

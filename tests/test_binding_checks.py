@@ -69,3 +69,21 @@ def test_operator_methods_check_before_the_abi():
     _bad(dfm.tet_density, mesh, 2, f64, torch.zeros(ROWS, NB))
     _bad(dfm.interior_density, mesh, 2, [0], gvec=torch.zeros(ROWS, NB - 1, dtype=torch.float64),
          dgvec=torch.zeros(ROWS, NB, dtype=torch.float64))
+
+
+def test_damping_field_length_is_checked():
+    """A per-tet damping tensor must hold one value per tet: the library reads
+    n_tets values through the pointer.  A 0-dim tensor means uniform damping."""
+    op = _fake_op()
+    for bad in (torch.zeros(ROWS // 4 - 1, dtype=torch.float64), torch.zeros(ROWS, dtype=torch.float64),
+                torch.zeros(2, ROWS // 4, dtype=torch.float64)):
+        _bad(dfm.Operator._params, op, 2, bad, dfm.F32, 0, 0.0)
+    p = dfm.Operator._params(op, 2, torch.tensor(0.25, dtype=torch.float64), dfm.F32, 0, 0.0)
+    assert p.mu is None and p.mu_uniform == 0.25
+
+
+def test_solve_damped_checks_before_the_abi():
+    op = _fake_op()
+    rho0 = torch.zeros(3, ROWS, NB, dtype=torch.float64)
+    _bad(dfm.solve_damped, [op], [0.1, 0.2], rho0)          # one damping per right-hand side
+    _bad(dfm.solve_damped, [op], [0.1, 0.2, 0.3], rho0.float())

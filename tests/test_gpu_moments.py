@@ -5,8 +5,12 @@ mu_c), against the FP64 oracle:
  - sum_k (mu_r - mu_c)^k / k! B^(k) equals the oracle's B(mu_r) (truncation of
    order (|mu_r - mu_c| L)^K / K!, far below FP32 rounding here);
  - dfm_apply_combo equals the weighted sum of single applications;
- - dfm_solve_combo equals LU solves with the combined operators.
+ - dfm_solve_combo equals LU solves with the combined operators;
+ - dfm_solve_damped (the library forms the Taylor weights from mu_r and the
+   moments' mu_c) equals the oracle's solve with B(mu_r) assembled exactly.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -14,6 +18,12 @@ from gpu_helpers import block_rel_err, need_gpu, to_oracle_layout
 from paper_1608_04607_gb300.inputs import kuhn_cube_mesh
 
 pytestmark = pytest.mark.gpu
+
+
+def taylor_weights(mu_rhs, mu_c, K):
+    """(mu_r - mu_c)^k / k!, restated here to check the combined operators."""
+    mu_rhs = np.atleast_1d(np.asarray(mu_rhs, dtype=np.float64))
+    return np.stack([(mu_rhs - mu_c) ** k / math.factorial(k) for k in range(K)], axis=1)
 
 
 @pytest.fixture(scope="module")
@@ -41,7 +51,7 @@ def test_first_moment_is_oracle_derivative(setup, oracle_mod):
 def test_taylor_sum_matches_oracle(setup, oracle_mod, mu_r):
     dfm, m, mesh, Np, mu_c, K, ops = setup
     recv = mesh.recv()
-    c = dfm.moment_coefficients([mu_r], mu_c, K)[0]
+    c = taylor_weights([mu_r], mu_c, K)[0]
     combo = sum(c[k] * to_oracle_layout(ops[k].blocks().cpu().numpy().astype(np.float64), recv, m.n_tets)
                 for k in range(K))
     ref = oracle_mod.assemble(m.verts, m.tets, np.full(m.n_tets, mu_r), 0.95, Np, rtol=1e-12)
@@ -55,7 +65,7 @@ def test_apply_combo_and_solve_combo(setup, oracle_mod):
     dfm, m, mesh, Np, mu_c, K, ops = setup
     rng = np.random.default_rng(0)
     mu_rhs = rng.uniform(0.01, 0.2, 6)
-    coef = dfm.moment_coefficients(mu_rhs, mu_c, K)
+    coef = taylor_weights(mu_rhs, mu_c, K)
     R = len(mu_rhs)
     x = torch.tensor(rng.standard_normal((R, mesh.n_rows, ops[0].nb)), device="cuda")
     y = dfm.apply_combo(ops, coef, x, x0=x, alpha=-1.0)
@@ -87,7 +97,7 @@ def test_solve_combo_with_low_precision_preconditioner(setup, oracle_mod, precon
     dfm, m, mesh, Np, mu_c, K, ops = setup
     rng = np.random.default_rng(4)
     mu_rhs = rng.uniform(0.01, 0.2, 5)
-    coef = dfm.moment_coefficients(mu_rhs, mu_c, K)
+    coef = taylor_weights(mu_rhs, mu_c, K)
     R = len(mu_rhs)
     recv = mesh.recv()
     t, f, fp = oracle_mod.pair_list(m.n_tets)
@@ -101,3 +111,36 @@ def test_solve_combo_with_low_precision_preconditioner(setup, oracle_mod, precon
         Br = oracle_mod.Operator(Np=Np, blocks=sum(coef[r, k] * blocks[k] for k in range(K)), dest=dest)
         ref = oracle_mod.solve_dense(Br, rho0[r].cpu().numpy())
         assert np.linalg.norm(rho[r].cpu().numpy() - ref) <= 1e-8 * np.linalg.norm(ref)
+
+
+def test_solve_damped_matches_oracle_exact_damping(setup, oracle_mod):
+    """Per-right-hand-side damping through the C ABI: dfm_solve_damped gets
+    mu_r and the moments (assembled at mu_c), and its solutions match the
+    oracle's LU solves with B(mu_r) assembled exactly (adaptive quadrature to
+    1e-12, no Taylor expansion).  Four moments keep the truncation
+    ((|mu_r - mu_c| L)^4 / 4! < 1e-6 per entry here) below the FP32 entry
+    error; the remaining difference is the FP32 assembly's (<= 1e-5 per block)
+    times the conditioning of I - B, within 1e-4."""
+    dfm, m, mesh, Np, mu_c, _, _ = setup
+    ops = [dfm.Operator(mesh, Np, mu=mu_c, precision=dfm.F32, moment=k) for k in range(4)]
+    recv = mesh.recv()
+    rng = np.random.default_rng(8)
+    mu_rhs = np.array([0.01, 0.2, 0.105, 0.06])
+    R = len(mu_rhs)
+    rows = np.nonzero(recv == np.arange(mesh.n_rows))[0][rng.integers(0, 48, R)]
+    rho0 = dfm.source(mesh, Np, rows)
+    rho, info = dfm.solve_damped(ops, mu_rhs, rho0, tol=1e-10, batch=2)
+    assert info.resid <= 1e-10
+    for r in range(R):
+        ref_op = oracle_mod.assemble(m.verts, m.tets, np.full(m.n_tets, mu_rhs[r]), 0.95, Np, rtol=1e-12)
+        ref = oracle_mod.solve_dense(ref_op, oracle_mod.source_vector(m.verts, m.tets, rows[r:r + 1], Np))
+        got = rho[r].cpu().numpy()
+        assert np.linalg.norm(got - ref) <= 1e-4 * np.linalg.norm(ref), np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    # moments given in the wrong order, or a moment at another damping, are refused
+    with pytest.raises(dfm.DFMError):
+        dfm.solve_damped([ops[1], ops[0]], mu_rhs, rho0)
+    other = dfm.Operator(mesh, Np, mu=0.2, precision=dfm.F32, moment=1)
+    with pytest.raises(dfm.DFMError):
+        dfm.solve_damped([ops[0], other], mu_rhs, rho0)
+    with pytest.raises(dfm.DFMError):
+        dfm.solve_damped(ops[:2], np.array([0.1, -0.1, 0.1, 0.1]), rho0)
