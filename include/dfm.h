@@ -374,6 +374,24 @@ int dfm_adjoint(const dfm_op* op, const dfm_params* params, const double* rho, i
 int dfm_op_check_error(const dfm_op* op, void* stream);
 int dfm_selftest_timeout(const dfm_op* op, int polls, void* stream);
 
+/* Autotuning of launch geometries (the paper has no counterpart; a library
+ * service).  The tensor-core preconditioner hops choose their tile rows and
+ * pipeline stages per launch shape (basis, copy precision, right-hand sides
+ * per launch, transposition, operator rows, device): on the first launch of a
+ * shape every candidate geometry is timed on the call's own arguments with
+ * CUDA events (the stream is synchronised; nothing is timed while the stream
+ * is being captured into a graph, where the default geometry is used) and
+ * the fastest is kept for later launches.  Geometry changes no arithmetic:
+ * results are identical with tuning on or off.
+ *   dfm_autotune(mode): 0 = fixed default geometries, 1 = tune on first use
+ *     (the default), 2 = forget the tuned choices and tune again.
+ *   dfm_autotune_report(buf, len): writes a JSON list of the tuned shapes
+ *     with their chosen geometry and every candidate's time ([rows per tile,
+ *     stages, ms]) into buf (len bytes, NUL-terminated, truncated if short);
+ *     returns the bytes needed including the NUL. */
+int dfm_autotune(int mode);
+int64_t dfm_autotune_report(char* buf, int64_t len);
+
 /* Kernel accounting, for benchmarks and profiling.
  *   dfm_launch_count: number of CUDA kernels this library has launched in the
  *     process so far (all kernels, all streams).

@@ -40,17 +40,27 @@
 #include <cmath>
 #include <cstring>
 #include <type_traits>
+#include <vector>
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
 
+#include "hop_frag.cuh"
 #include "hop_kernel.cuh"
+#include "tune.h"
 
 namespace dfm {
 namespace {
 
 using namespace hopk;
+using geom::kFragGroupMin;
+
+// FP16 and e4m3 copies of bases padded to a multiple of 16 are stored
+// fragment-ordered and hopped on tensor cores (hop_frag.cuh)
+bool frag_copy(int nb, int precision) {
+  return geom::frag_basis(nb) && (precision == DFM_F16 || precision == DFM_FP8E4M3);
+}
 
 // FP16/BF16 copy: element i of the copy <- its block entry (0 in pads); the
 // blocks are FP32, or BF16 for a BF16 operator
@@ -122,6 +132,67 @@ __global__ void to_hop8_kernel(const S* __restrict__ src, int64_t row_stride, un
   }
 }
 
+// Fragment-ordered copy (hop_frag.cuh): one warp per row; FP16 values, or
+// e4m3 values with s_R = max |entry| / 448 as in to_hop8_kernel.  Entry (a, b)
+// of block k is B_k[a][b] (forward) or, transposed, the entry (b, a) of the
+// block that face l of t sends to its k-th receiving row (as copy_entry_at).
+template <typename E, typename S>
+__global__ void to_frag_kernel(const S* __restrict__ src, int64_t row_stride, unsigned char* __restrict__ dst,
+                               int64_t nrows, int nb, int nbp, int64_t row_bytes, const int32_t* __restrict__ recvT) {
+  constexpr bool kFp8 = std::is_same<E, __nv_fp8_e4m3>::value;
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t n_vals = 3 * (int64_t)nb * nbp;
+  for (int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; row < nrows; row += warps) {
+    auto entry = [&](int64_t e) -> float {
+      const fragk::FragPos p = fragk::frag_pos(e, nb, nbp);
+      if (p.b >= nb) return 0.f;
+      if (!recvT) return (float)src[row * row_stride + (int64_t)p.k * nb * nb + (int64_t)p.a * nb + p.b];
+      const int l = (int)(row & 3);
+      const int lq = p.k + (p.k >= l ? 1 : 0);
+      const int64_t Rr = recvT[(row & ~int64_t(3)) + lq];
+      const int slot = l - (l > lq ? 1 : 0);
+      return (float)src[Rr * row_stride + (int64_t)slot * nb * nb + (int64_t)p.b * nb + p.a];
+    };
+    unsigned char* dr = dst + row * row_bytes;
+    if constexpr (kFp8) {
+      float mx = 0.f;
+      for (int64_t e = lane; e < n_vals; e += 32) mx = fmaxf(mx, fabsf(entry(e)));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      const float s = mx > 0.f ? mx / 448.f : 1.f;
+      for (int64_t e = lane; e < n_vals; e += 32)
+        dr[e] = (unsigned char)__nv_cvt_float_to_fp8(entry(e) / s, __NV_SATFINITE, __NV_E4M3);
+      if (lane < 4) reinterpret_cast<float*>(dr + n_vals)[lane] = lane == 0 ? s : 0.f;
+    } else {
+      for (int64_t e = lane; e < n_vals; e += 32) reinterpret_cast<__half*>(dr)[e] = __float2half_rn(entry(e));
+    }
+  }
+}
+
+// v (FP32 [R][rows][nb]) times scale into the grouped hop layout
+// [G][rows][NBP][8] (right-hand side q = 8 g + j; zero past R and nb): one
+// thread per (g, row, a), 8 reads coalesced over a, one 16-byte store
+__global__ void frag_pack_kernel(const float* __restrict__ v, __half* __restrict__ vp, int64_t rows, int nb, int nbp,
+                                 int R, int G, float scale) {
+  const int64_t total = (int64_t)G * rows * nbp;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int a = (int)(i % nbp);
+    const int64_t gr = i / nbp;
+    const int64_t row = gr % rows;
+    const int g = (int)(gr / rows);
+    __half h[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int q = 8 * g + j;
+      h[j] = __float2half_rn(q < R && a < nb ? v[((int64_t)q * rows + row) * nb + a] * scale : 0.f);
+    }
+    uint4 u;
+    memcpy(&u, h, 16);
+    reinterpret_cast<uint4*>(vp)[i] = u;
+  }
+}
+
 template <typename V>
 __global__ void hop_pack_kernel(const float* __restrict__ v, V* __restrict__ vp, int64_t rows, int nb, int nbp,
                                 float scale) {
@@ -180,7 +251,15 @@ int prepare_lowp(const dfm_op* cop, int precision, cudaStream_t st, int trans) {
   if (!valid || prec != precision) {
     auto convert = [&](auto src) {
       using S = std::remove_const_t<std::remove_pointer_t<decltype(src)>>;
-      if (precision == DFM_FP8E4M3) {
+      if (frag_copy(nb, precision)) {
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((op->nrows * 32 + 255) / 256, 4096));
+        if (precision == DFM_FP8E4M3)
+          to_frag_kernel<__nv_fp8_e4m3, S><<<grid, 256, 0, st>>>(src, op->row_stride, (unsigned char*)vals, op->nrows,
+                                                                 nb, nbp, row_bytes, recvT);
+        else
+          to_frag_kernel<__half, S><<<grid, 256, 0, st>>>(src, op->row_stride, (unsigned char*)vals, op->nrows, nb,
+                                                          nbp, row_bytes, recvT);
+      } else if (precision == DFM_FP8E4M3) {
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((op->nrows * 32 + 255) / 256, 4096));
         to_hop8_kernel<S><<<grid, 256, 0, st>>>(src, op->row_stride, (unsigned char*)vals, op->nrows, nb, nbp,
                                                 copy_body_bytes<__nv_fp8_e4m3>(nb, nbp), row_bytes, recvT);
@@ -219,8 +298,7 @@ int hop_apply_t(const dfm_op* op, const V* xp, const V* x0p, void* y, int R, boo
   // right-hand sides per launch: at most kHopMaxRhs, and few enough that two
   // stages fit in shared memory (large bases with many right-hand sides)
   const bool fp8 = cp.precision == DFM_FP8E4M3;
-  const int rchunk = geom::hop_rhs_chunk(op->nb, fp8 ? 1 : 2, fp8, (int)sizeof(V),
-                                         std::is_same<V, __half>::value && R > 1);
+  const int rchunk = geom::hop_rhs_chunk(op->nb, fp8 ? 1 : 2, fp8, (int)sizeof(V));
   if (rchunk < 1) return set_error(DFM_ERR_UNSUPPORTED, "preconditioner hop: a tile does not fit shared memory");
   for (int r0 = 0; r0 < R; r0 += rchunk) {
     const int Rp = std::min(rchunk, R - r0);
@@ -237,6 +315,97 @@ int hop_apply_t(const dfm_op* op, const V* xp, const V* x0p, void* y, int R, boo
       rc = hop_launch_bf16(op, x, x0, yy, Rp, out_scale, out_padded, trans, st);
     }
     if (rc) return rc;
+  }
+  return DFM_OK;
+}
+
+// Candidate geometries of the tensor-core hop for the autotuner: tile rows
+// in multiples of the rows that give each warp of a consumer group one item,
+// 2, 4, 6 or 8 stages, every stage at most 100 KB and all within the budget.
+std::vector<tune::Geometry> frag_candidates(int nb, bool fp8, int w, int rgl) {
+  const int64_t row = geom::frag_row_stage_bytes(nb, fp8 ? 1 : 2, fp8, w, rgl);
+  const int unit = rgl >= geom::kFragGroupWarps ? 1 : geom::kFragGroupWarps / rgl;
+  std::vector<tune::Geometry> out;
+  for (int m : {1, 2, 3, 4, 6, 8}) {
+    const int rpt = unit * m;
+    if (rpt > 32 || rpt * row > 100 * 1024) continue;
+    for (int st : {2, 4, 6, 8})  // multiples of the consumer groups (see geom::frag_geometry)
+      if (st * rpt * row <= geom::kStageBudget) out.push_back(tune::Geometry{rpt, st, 0.f});
+  }
+  return out;
+}
+
+tune::Geometry frag_default(int nb, bool fp8, int w, int rgl) {
+  const geom::Frag g = geom::frag_geometry(nb, fp8 ? 1 : 2, fp8, w, rgl);
+  return tune::Geometry{g.rpt, g.stages, 0.f};
+}
+
+// One hop on the fragment-ordered copy over all R right-hand sides: R <= 3
+// in the [R][rows][NBP] layout, one launch per right-hand side; R >= 4 in
+// groups of 8 ([G][rows][NBP][8]), two groups per launch.
+int hop_apply_frag(const dfm_op* op, const __half* xp, const __half* x0p, void* y, int R, bool out_padded,
+                   float out_scale, int trans, cudaStream_t st) {
+  const LowpView cp = lowp_of(op, trans);
+  const int nb = op->nb, nbp = hop_nbp(nb);
+  const int64_t rows = op->nrows;
+  const bool fp8 = cp.precision == DFM_FP8E4M3;
+  int dev = 0;
+  DFM_CUDA_CHECK(cudaGetDevice(&dev));
+  // each launch shape takes the tile rows and stages the autotuner picked for it
+  auto launch = [&](const __half* x, const __half* x0, void* yy, int w, int rgl, int rhs_here) -> int {
+    auto go = [&](int rpt, int stages) -> int {
+      return fp8 ? hop_frag_launch_fp8(op, x, x0, yy, w, rgl, rhs_here, out_padded, out_scale, trans, rpt, stages, st)
+                 : hop_frag_launch_f16(op, x, x0, yy, w, rgl, rhs_here, out_padded, out_scale, trans, rpt, stages, st);
+    };
+    const tune::Key key{0, nb, cp.precision, w, rgl, trans, rows, dev};
+    tune::Geometry g;
+    const int rc = tune::choose(key, st, frag_candidates(nb, fp8, w, rgl), frag_default(nb, fp8, w, rgl), go, &g);
+    if (rc) return rc;
+    return go(g.rpt, g.stages);
+  };
+  if (R < kFragGroupMin) {
+    for (int r = 0; r < R; ++r) {
+      void* yy = out_padded ? static_cast<void*>(static_cast<__half*>(y) + r * rows * nbp)
+                            : static_cast<void*>(static_cast<float*>(y) + r * rows * nb);
+      const int rc = launch(xp + r * rows * nbp, x0p + r * rows * nbp, yy, 1, 1, 1);
+      if (rc) return rc;
+    }
+    return DFM_OK;
+  }
+  const int G = (R + 7) / 8;
+  const int64_t plane = rows * nbp * 8;
+  for (int g0 = 0; g0 < G; g0 += 2) {
+    const int rgl = std::min(2, G - g0);
+    void* yy = out_padded ? static_cast<void*>(static_cast<__half*>(y) + g0 * plane)
+                          : static_cast<void*>(static_cast<float*>(y) + (int64_t)g0 * 8 * rows * nb);
+    const int rc = launch(xp + g0 * plane, x0p + g0 * plane, yy, 8, rgl, std::min(16, R - 8 * g0));
+    if (rc) return rc;
+  }
+  return DFM_OK;
+}
+
+int horner_frag(const dfm_op* op, int R, int d, const float* v, float* z, void* vp_, void* ha_, void* hb_,
+                float vscale, int trans, cudaStream_t st) {
+  __half* vp = static_cast<__half*>(vp_);
+  __half* h[2] = {static_cast<__half*>(ha_), static_cast<__half*>(hb_)};
+  const int nb = op->nb, nbp = hop_nbp(nb);
+  if (R < kFragGroupMin) {
+    const int64_t rows = (int64_t)R * op->nrows;
+    hop_pack_kernel<__half><<<grid_for_elems(rows * nbp), 256, 0, st>>>(v, vp, rows, nb, nbp, vscale);
+  } else {
+    const int G = (R + 7) / 8;
+    frag_pack_kernel<<<grid_for_elems((int64_t)G * op->nrows * nbp), 256, 0, st>>>(v, vp, op->nrows, nb, nbp, R, G,
+                                                                                  vscale);
+  }
+  DFM_LAUNCHED();
+  DFM_CUDA_CHECK(cudaGetLastError());
+  const __half* src = vp;
+  for (int k = 1; k < d; ++k) {
+    const bool last = (k == d - 1);
+    void* dst = last ? static_cast<void*>(z) : static_cast<void*>(h[k & 1]);
+    const int rc = hop_apply_frag(op, src, vp, dst, R, !last, 1.0f / vscale, trans, st);
+    if (rc) return rc;
+    src = h[k & 1];
   }
   return DFM_OK;
 }
@@ -278,6 +447,8 @@ int hop_horner(const dfm_op* op, int R, int d, const float* v, float* z, void* v
   // FP16 and e4m3 copies run the hops on FP16 vectors (v scaled by vscale);
   // the BF16 copy on FP32 vectors
   if (lowp_of(op, trans).precision == DFM_BF16) return horner_t<float>(op, R, d, v, z, vp, ha, hb, 1.0f, trans, st);
+  if (frag_copy(op->nb, lowp_of(op, trans).precision))
+    return horner_frag(op, R, d, v, z, vp, ha, hb, vscale, trans, st);
   return horner_t<__half>(op, R, d, v, z, vp, ha, hb, vscale, trans, st);
 }
 

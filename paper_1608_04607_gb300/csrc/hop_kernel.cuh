@@ -132,9 +132,9 @@ __host__ __device__ constexpr int64_t copy_row_bytes(int nb, int nbp) {
 }
 
 // rows per tile (one or two consumer passes), see geom::hop_tile_rows
-template <typename E, bool MMA>
+template <typename E>
 __host__ __device__ constexpr int hop_tile_rows(int nb) {
-  return geom::hop_tile_rows(nb, Codec<E>::kEB, Codec<E>::kScaled, MMA);
+  return geom::hop_tile_rows(nb, Codec<E>::kEB, Codec<E>::kScaled);
 }
 
 // y = x0 + alpha B~ x for R right-hand sides; x, x0 of type V (float, or
@@ -145,43 +145,7 @@ __host__ __device__ constexpr int hop_tile_rows(int nb) {
 // lane) and the three block sums are added in FP32.  With FP16 vectors the
 // right-hand sides are taken RC at a time, each decoded chunk of B~ serving
 // all RC of them.
-// One 16x8x16 tensor-core multiply-add, FP16 operands, FP32 accumulators
-// (fragment layouts of mma.sync.m16n8k16: a0..a3 hold rows g and g + 8 at
-// columns 2t, 2t + 1 and 2t + 8, 2t + 9; b0, b1 hold rows 2t, 2t + 1 and
-// 2t + 8, 2t + 9 of column g; d0..d3 rows g and g + 8 at columns 2t, 2t + 1;
-// g = lane / 4, t = lane % 4).
-__device__ __forceinline__ void mma_16816(float d[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
-                                          uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
-// The pair of copy values B_k[a][8c + 2t], B_k[a][8c + 2t + 1] as FP16 bits
-// (zero for the pad rows a >= NB).
-template <typename E, int NB>
-__device__ __forceinline__ uint32_t copy_pair(const unsigned char* bk, int c, int a, int t) {
-  if (a >= NB) return 0u;
-  if constexpr (std::is_same<E, __nv_fp8_e4m3>::value) {
-    const __nv_fp8x2_storage_t pair = *reinterpret_cast<const __nv_fp8x2_storage_t*>(bk + (c * NB + a) * 8 + 2 * t);
-    const __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2(pair, __NV_E4M3);
-    uint32_t u;
-    memcpy(&u, &hr, 4);
-    return u;
-  } else {
-    return *reinterpret_cast<const uint32_t*>(bk + ((c * NB + a) * 8 + 2 * t) * 2);
-  }
-}
-
-// MMA: tensor-core consumer (FP16 vectors, NBP a multiple of 16, several
-// right-hand sides): a warp forms a 16-row x 8-right-hand-side tile of one
-// operator row's output, Y = sum_k B~_k X_k with B~_k as the 16 x 16 A tiles
-// and the staged source coefficients as the 16 x 8 B tiles.  The staged
-// coefficients are then laid out per row and right-hand side with a 16-byte
-// gap, which keeps the B-fragment loads of 8 right-hand sides on distinct
-// shared-memory banks.
-template <int NB, typename E, typename V, bool OUTP, int RC, bool MMA, bool TR>
+template <int NB, typename E, typename V, bool OUTP, int RC, bool TR>
 __global__ void __launch_bounds__(32 * (kHopConsumerWarps + 1))
 hop_kernel(const unsigned char* __restrict__ vals, const int32_t* __restrict__ recv, int64_t nrows,
            const V* __restrict__ xp, const V* __restrict__ x0p, void* __restrict__ yv, int R, float alpha,
@@ -189,16 +153,15 @@ hop_kernel(const unsigned char* __restrict__ vals, const int32_t* __restrict__ r
   constexpr int NBP = (NB + 7) / 8 * 8;
   constexpr int NC = NBP / 8;
   constexpr int RSTEP = (32 * kHopConsumerWarps) / NBP;  // rows of one consumer pass
-  constexpr int RPT = hop_tile_rows<E, MMA>(NB);              // rows per tile (one or two passes)
+  constexpr int RPT = hop_tile_rows<E>(NB);                   // rows per tile (one or two passes)
   constexpr int EB = Codec<E>::kEB;
   constexpr unsigned ROW_BYTES = (unsigned)copy_row_bytes<E>(NB, NBP);
   constexpr unsigned BODY_BYTES = (unsigned)copy_body_bytes<E>(NB, NBP);
   constexpr unsigned XBLK_D = 4 * NBP * (unsigned)sizeof(V);  // bytes of a source tet's coefficients
-  constexpr unsigned XBLK = MMA ? XBLK_D + 16 : XBLK_D;         // their stride in shared memory
+  constexpr unsigned XBLK = XBLK_D;                             // their stride in shared memory
   constexpr unsigned X0ROW = NBP * (unsigned)sizeof(V);
   constexpr bool VH = std::is_same<V, __half>::value;
   static_assert(RPT >= 1 && RPT <= 32, "rows per tile");
-  static_assert(!MMA || (NBP % 16 == 0 && std::is_same<V, __half>::value), "tensor-core tiles need NBP % 16 == 0");
   static_assert(ROW_BYTES % 16 == 0 && X0ROW % 16 == 0, "rows must keep 16-byte alignment");
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw);
@@ -275,7 +238,7 @@ hop_kernel(const unsigned char* __restrict__ vals, const int32_t* __restrict__ r
       if (lane < nr)
         for (int rhs = 0; rhs < R; ++rhs) {
           unsigned char* dst =
-              st + (int64_t)RPT * ROW_BYTES + (MMA ? (int64_t)lane * R + rhs : (int64_t)rhs * RPT + lane) * XBLK;
+              st + (int64_t)RPT * ROW_BYTES + ((int64_t)rhs * RPT + lane) * XBLK;
           if constexpr (!TR) {
             const unsigned char* srcp =
                 reinterpret_cast<const unsigned char*>(xp + ((int64_t)rhs * nrows + 4 * (int64_t)(src.x >> 2)) * NBP);
@@ -301,73 +264,6 @@ hop_kernel(const unsigned char* __restrict__ vals, const int32_t* __restrict__ r
     if (lane == 0)
       for (int64_t j = (issued > stages ? issued - stages : 0); j < issued; ++j)
         mbar_wait_bounded(&full[j % stages], (unsigned)((j / stages) & 1));
-    return;
-  }
-  if constexpr (MMA) {
-    // ---------------- tensor-core consumers: work item (row, m-tile, n-tile) per warp ----------------
-    constexpr int MT = NBP / 16;  // 16-row tiles of the output (and 16-column tiles of each block)
-    const int g = lane >> 2, t = lane & 3;
-    const int NT = (R + 7) / 8;
-    for (int64_t i = 0; i < mine; ++i) {
-      const int s = (int)(i % stages);
-      const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&full[s], (unsigned)((i / stages) & 1)));
-      if (!ok) {
-        if (lane == 0) atomicOr(err, 1);
-        break;
-      }
-      const unsigned char* st = stage0 + s * stage_bytes;
-      const int64_t R0 = tile_first_row(i);
-      const int nr = (int)std::min<int64_t>(RPT, nrows - R0);
-      const unsigned char* xbase = st + (int64_t)RPT * ROW_BYTES;
-      const __half* x0base = reinterpret_cast<const __half*>(xbase + (int64_t)R * RPT * XBLK);
-      const int items = nr * MT * NT;
-      for (int it = warp - 1; it < items; it += kHopConsumerWarps) {
-        const int r = it / (MT * NT);
-        const int rem = it - r * (MT * NT);
-        const int mt = rem / NT;
-        const int nt = rem - mt * NT;
-        const int lp = s_recv[s * RPT + r] & 3;
-        const unsigned char* brow = st + r * ROW_BYTES;
-        float scale = 1.f;
-        if constexpr (Codec<E>::kScaled) scale = *reinterpret_cast<const float*>(brow + BODY_BYTES);
-        const int a_lo = mt * 16 + g, a_hi = a_lo + 8;
-        const int qb = nt * 8 + g;  // right-hand side of this lane's B fragment
-        const __half* xq = reinterpret_cast<const __half*>(xbase + ((int64_t)r * R + (qb < R ? qb : 0)) * XBLK);
-        float d[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          const int l = k + (k >= lp ? 1 : 0);
-          const unsigned char* bk = brow + k * NB * NBP * EB;
-#pragma unroll
-          for (int kt = 0; kt < MT; ++kt) {
-            const uint32_t a0 = copy_pair<E, NB>(bk, 2 * kt, a_lo, t);
-            const uint32_t a1 = copy_pair<E, NB>(bk, 2 * kt, a_hi, t);
-            const uint32_t a2 = copy_pair<E, NB>(bk, 2 * kt + 1, a_lo, t);
-            const uint32_t a3 = copy_pair<E, NB>(bk, 2 * kt + 1, a_hi, t);
-            const __half* xk = xq + l * NBP + 16 * kt + 2 * t;
-            const uint32_t b0 = qb < R ? *reinterpret_cast<const uint32_t*>(xk) : 0u;
-            const uint32_t b1 = qb < R ? *reinterpret_cast<const uint32_t*>(xk + 8) : 0u;
-            mma_16816(d, a0, a1, a2, a3, b0, b1);
-          }
-        }
-        // epilogue: (a_lo | a_hi) x (2t, 2t + 1) of this n-tile
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int a = (e < 2) ? a_lo : a_hi;
-          const int q = nt * 8 + 2 * t + (e & 1);
-          if (q < R) {
-            const float out = a < NB ? (float)x0base[((int64_t)q * RPT + r) * NBP + a] + alpha * (scale * d[e]) : 0.f;
-            const int64_t row = (int64_t)q * nrows + R0 + r;
-            if constexpr (OUTP)
-              reinterpret_cast<V*>(yv)[row * NBP + a] = (V)out;  // pads (a >= NB) written as 0
-            else if (a < NB)
-              reinterpret_cast<float*>(yv)[row * NB + a] = out * out_scale;
-          }
-        }
-      }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&empty[s]);
-    }
     return;
   }
   // ---------------- consumers: thread (r, a), a < NBP ----------------
@@ -484,15 +380,15 @@ hop_kernel(const unsigned char* __restrict__ vals, const int32_t* __restrict__ r
   }
 }
 
-template <typename E, typename V, bool OUTP, int RC, bool MMA = false>
+template <typename E, typename V, bool OUTP, int RC>
 int launch_hop(const dfm_op* op, const V* xp, const V* x0p, void* y, int R, float out_scale, int trans,
                cudaStream_t st) {
   const void* copy = lowp_of(op, trans).vals;
   const int nb = op->nb;
   const int nbp = hop_nbp(nb);
-  const int rpt = hop_tile_rows<E, MMA>(nb);
+  const int rpt = hop_tile_rows<E>(nb);
   const int64_t row_bytes = copy_row_bytes<E>(nb, nbp);
-  const int64_t stage_bytes = geom::hop_stage_bytes(nb, Codec<E>::kEB, Codec<E>::kScaled, (int)sizeof(V), R, MMA);
+  const int64_t stage_bytes = geom::hop_stage_bytes(nb, Codec<E>::kEB, Codec<E>::kScaled, (int)sizeof(V), R);
   const int stages = geom::hop_stages(stage_bytes, kHopStages);
   if (stages < 2) return set_error(DFM_ERR_UNSUPPORTED, "preconditioner hop: a tile does not fit shared memory");
   const size_t smem = 128 + ((kHopStages * rpt * 4 + 127) / 128) * 128 + (size_t)stages * stage_bytes;
@@ -519,11 +415,11 @@ int launch_hop(const dfm_op* op, const V* xp, const V* x0p, void* y, int R, floa
   };
   auto go_nb = [&](auto nbc) -> int {
     constexpr int NBC = decltype(nbc)::value;
-    if constexpr (MMA && ((NBC + 7) / 8 * 8) % 16 != 0)
-      return set_error(DFM_ERR_UNSUPPORTED, "preconditioner hop: tensor-core tiles need a basis padded to 16");
+    // FP16 hop vectors on a basis padded to 16 run on the fragment-ordered copy
+    if constexpr (std::is_same<V, __half>::value && geom::frag_basis(NBC))
+      return set_error(DFM_ERR_UNSUPPORTED, "preconditioner hop: this basis uses the tensor-core hop");
     else
-      return trans ? go(hop_kernel<NBC, E, V, OUTP, RC, MMA, true>)
-                   : go(hop_kernel<NBC, E, V, OUTP, RC, MMA, false>);
+      return trans ? go(hop_kernel<NBC, E, V, OUTP, RC, true>) : go(hop_kernel<NBC, E, V, OUTP, RC, false>);
   };
   switch (nb) {
     case 1: return go_nb(std::integral_constant<int, 1>{});
@@ -539,10 +435,6 @@ int launch_hop(const dfm_op* op, const V* xp, const V* x0p, void* y, int R, floa
   }
 }
 
-
-// several right-hand sides with a basis padded to a multiple of 16 go to the
-// tensor-core consumer
-inline bool hop_uses_mma(int nb, int R) { return R > 1 && (((nb + 7) / 8 * 8) % 16) == 0; }
 
 }  // namespace hopk
 

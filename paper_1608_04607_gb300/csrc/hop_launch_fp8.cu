@@ -1,4 +1,7 @@
-// Instantiation of the preconditioner hop kernel for the e4m3 copy.
+// Instantiation of the preconditioner hop kernels for the e4m3 copy: the
+// CUDA-core hop (bases whose padded width is not a multiple of 16) and the
+// tensor-core hop on the fragment-ordered copy (the others).
+#include "hop_frag.cuh"
 #include "hop_kernel.cuh"
 
 namespace dfm {
@@ -9,11 +12,13 @@ int hop_launch_fp8(const dfm_op* op, const __half* xp, const __half* x0p, void* 
   if (R == 1)
     return outp ? launch_hop<__nv_fp8_e4m3, __half, true, 1>(op, xp, x0p, y, R, out_scale, trans, st)
                 : launch_hop<__nv_fp8_e4m3, __half, false, 1>(op, xp, x0p, y, R, out_scale, trans, st);
-  if (hop_uses_mma(op->nb, R))  // several right-hand sides on tensor cores
-    return outp ? launch_hop<__nv_fp8_e4m3, __half, true, 1, true>(op, xp, x0p, y, R, out_scale, trans, st)
-                : launch_hop<__nv_fp8_e4m3, __half, false, 1, true>(op, xp, x0p, y, R, out_scale, trans, st);
   return outp ? launch_hop<__nv_fp8_e4m3, __half, true, kHopRhsInner>(op, xp, x0p, y, R, out_scale, trans, st)
               : launch_hop<__nv_fp8_e4m3, __half, false, kHopRhsInner>(op, xp, x0p, y, R, out_scale, trans, st);
+}
+
+int hop_frag_launch_fp8(const dfm_op* op, const __half* xp, const __half* x0p, void* y, int w, int rgl, int rhs_here,
+                        bool outp, float out_scale, int trans, int rpt, int stages, cudaStream_t st) {
+  return fragk::launch_hop_frag<__nv_fp8_e4m3>(op, xp, x0p, y, w, rgl, rhs_here, outp, out_scale, trans, rpt, stages, st);
 }
 
 }  // namespace dfm

@@ -7,6 +7,12 @@
 
 #include <stdint.h>
 
+#ifdef __CUDACC__
+#define DFM_GEOM_HD __host__ __device__
+#else
+#define DFM_GEOM_HD
+#endif
+
 namespace dfm {
 namespace geom {
 
@@ -73,27 +79,25 @@ constexpr int64_t hop_row_bytes(int nb, int eb, bool scaled) { return hop_body_b
 
 // rows per tile: two consumer passes of (32 x consumer warps) / NBP rows (at
 // most 32, one per producer lane) when the tile's copy rows stay within
-// kHopTileBytes, else one pass; the tensor-core consumer (several right-hand
-// sides, whose staged coefficients already fill the tile) always takes one
-constexpr int hop_tile_rows(int nb, int eb, bool scaled, bool mma) {
+// kHopTileBytes, else one pass
+constexpr int hop_tile_rows(int nb, int eb, bool scaled) {
   const int step = (32 * kHopConsumerWarps) / hop_nbp(nb);
   const int two = step * kHopPasses < 32 ? step * kHopPasses : 32;
-  return (!mma && two * hop_row_bytes(nb, eb, scaled) <= kHopTileBytes) ? two : (step < 32 ? step : 32);
+  return (two * hop_row_bytes(nb, eb, scaled) <= kHopTileBytes) ? two : (step < 32 ? step : 32);
 }
 
 // staged bytes per tile row for R right-hand sides: the copy row, each right-hand
-// side's source-tet coefficients (4 NBP vector entries, plus a 16-byte gap
-// for the tensor-core consumer) and its x0 row (NBP entries)
-constexpr int64_t hop_stage_bytes(int nb, int eb, bool scaled, int vb, int R, bool mma) {
-  return hop_tile_rows(nb, eb, scaled, mma) *
-         (hop_row_bytes(nb, eb, scaled) + (int64_t)R * (4 * hop_nbp(nb) * vb + (mma ? 16 : 0) + hop_nbp(nb) * vb));
+// side's source-tet coefficients (4 NBP vector entries) and its x0 row (NBP entries)
+constexpr int64_t hop_stage_bytes(int nb, int eb, bool scaled, int vb, int R) {
+  return hop_tile_rows(nb, eb, scaled) *
+         (hop_row_bytes(nb, eb, scaled) + (int64_t)R * (4 * hop_nbp(nb) * vb + hop_nbp(nb) * vb));
 }
 
 // right-hand sides per launch: at most kHopMaxRhs, and few enough that two
 // stages fit (0 when even one does not)
-inline int hop_rhs_chunk(int nb, int eb, bool scaled, int vb, bool mma) {
+inline int hop_rhs_chunk(int nb, int eb, bool scaled, int vb) {
   int r = kHopMaxRhs;
-  while (r > 0 && 2 * hop_stage_bytes(nb, eb, scaled, vb, r, mma) > kStageBudget) --r;
+  while (r > 0 && 2 * hop_stage_bytes(nb, eb, scaled, vb, r) > kStageBudget) --r;
   return r;
 }
 
@@ -104,6 +108,88 @@ inline int hop_stages(int64_t stage_bytes, int max_stages) {
   if (s > max_stages) s = max_stages;
   if (s > 2 && s * stage_bytes > kHopTwoBlockBytes) s = kHopTwoBlockBytes / stage_bytes < 2 ? 2 : kHopTwoBlockBytes / stage_bytes;
   return (int)s;
+}
+
+// ---- tensor-core hops on the fragment-ordered copy (hop_frag_kernel) ----
+constexpr int kFragGroups = 2;          // consumer groups taking alternate tiles
+constexpr int kFragGroupWarps = 4;      // warps per consumer group
+constexpr int kFragMaxStages = 8;
+constexpr int kFragGroupMin = 4;        // right-hand sides from which vectors are grouped by 8
+constexpr int64_t kFragStageTarget = 48 * 1024;  // default stage size
+
+// the fragment-ordered copy serves bases whose padded width is a multiple of 16
+constexpr bool frag_basis(int nb) { return hop_nbp(nb) % 16 == 0; }
+// bytes of one face row of one hop-vector group (w = 1 or 8 right-hand sides, FP16)
+constexpr int64_t frag_xrow_bytes(int nb, int w) { return (int64_t)hop_nbp(nb) * w * 2; }
+// staged bytes of one tile row: the copy row, per group the gathered source
+// rows (4 slots) and the x0 row
+constexpr int64_t frag_row_stage_bytes(int nb, int eb, bool scaled, int w, int rgl) {
+  return hop_row_bytes(nb, eb, scaled) + (int64_t)rgl * 5 * frag_xrow_bytes(nb, w);
+}
+
+struct Frag {
+  int rpt;              // operator rows per tile (<= 32)
+  int stages;           // pipeline stages (<= kFragMaxStages)
+  int64_t stage_bytes;  // bytes of one stage
+};
+
+// Tile rows and stages: rpt_req / stages_req if given (clamped to what fits),
+// else tiles of about kFragStageTarget bytes whose (row, group) items split
+// evenly over a consumer group's warps, and as many stages as fit.
+inline Frag frag_geometry(int nb, int eb, bool scaled, int w, int rgl, int rpt_req = 0, int stages_req = 0) {
+  const int64_t row = frag_row_stage_bytes(nb, eb, scaled, w, rgl);
+  int rpt = rpt_req > 0 ? rpt_req : (int)(kFragStageTarget / row);
+  if (rpt > 32) rpt = 32;
+  if (rpt_req <= 0) {
+    const int unit = rgl >= kFragGroupWarps ? 1 : kFragGroupWarps / rgl;  // rows per full round of the group
+    if (rpt >= unit) rpt -= rpt % unit;
+  }
+  if (rpt < 1) rpt = 1;
+  while (rpt > 1 && 2 * rpt * row > kStageBudget) --rpt;  // at least two stages
+  Frag g{};
+  g.rpt = rpt;
+  g.stage_bytes = rpt * row;
+  int64_t st = kStageBudget / g.stage_bytes;
+  if (st > kFragMaxStages) st = kFragMaxStages;
+  if (stages_req > 0 && stages_req < st) st = stages_req;
+  // a multiple of the consumer groups: tile i and tile i - stages, the last
+  // user of its stage, then belong to the same group, which has consumed it
+  // (its barrier phase completed) before it waits for tile i; with another
+  // count a group could meet the stage's barrier a phase behind and read the
+  // parity of an older phase as complete
+  st -= st % kFragGroups;
+  g.stages = (int)st;
+  return g;
+}
+
+// (block k, test a, trial b) of value e of one row of the fragment-ordered
+// copy (hop_frag.cuh): per block, 16 x 16 tiles in (m-tile, k-tile) order,
+// each holding lane (g, t)'s values (row g; columns 2t, 2t+1, 2t+8, 2t+9) for
+// the 32 lanes, then those of row g + 8 for the lanes with g + 8 < vm, the
+// tile's rows (vm = min(16, nb - 16 m-tile)); b >= nb are pads
+struct FragPos {
+  int k, a, b;
+};
+DFM_GEOM_HD inline FragPos frag_pos(int64_t e, int nb, int nbp) {
+  FragPos p;
+  p.k = (int)(e / ((int64_t)nb * nbp));
+  int rem = (int)(e - (int64_t)p.k * nb * nbp);
+  const int mt = rem / (16 * nbp);
+  rem -= mt * 16 * nbp;
+  const int vm = nb - 16 * mt < 16 ? nb - 16 * mt : 16;
+  const int kt = rem / (16 * vm);
+  rem -= kt * 16 * vm;
+  const int half = rem < 128 ? 0 : 8;
+  const int idx = rem < 128 ? rem : rem - 128;
+  const int lane = idx >> 2, j = idx & 3;
+  p.a = 16 * mt + half + (lane >> 2);
+  p.b = 16 * kt + 2 * (lane & 3) + (j & 1) + (j >= 2 ? 8 : 0);
+  return p;
+}
+
+// dynamic shared memory of a launch: barriers, the per-stage row map, stages
+inline int64_t frag_smem_bytes(const Frag& g) {
+  return 128 + ((int64_t)kFragMaxStages * 32 * 4 + 127) / 128 * 128 + (int64_t)g.stages * g.stage_bytes;
 }
 
 }  // namespace geom

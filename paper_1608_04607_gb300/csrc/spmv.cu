@@ -103,6 +103,72 @@ __device__ __forceinline__ TA row_times_x(const TV* blk, const TX* xs, int lp) {
   return (acc[0] + acc[1]) + acc[2];
 }
 
+// The same with FP64 vectors on an FP32 or BF16 operator (the FP64 residual of
+// iterative refinement) without FP64 arithmetic, whose rate on this GPU is a
+// small fraction of the FP32 rate: each x = xh + xl is held as a pair of
+// floats (xh = fl32(x), xl = fl32(x - xh)); the product b xh is split exactly
+// into p + e (e = fma(b, xh, -p)), p is summed by Knuth's two-sum into s with
+// its rounding error, e and b xl are added to a compensation c, and the row
+// sum s + c carries about twice the FP32 precision, ample for a residual
+// that cancels to 1e-10 of the terms.
+template <int NB, typename TV>
+__device__ __forceinline__ double row_times_x_split(const TV* blk, const float2* xs, int lp) {
+  float s = 0.f, c = 0.f;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int l = k + (k >= lp ? 1 : 0);
+    const TV* bk = blk + k * NB * NB;
+    const float2* xl = xs + l * NB;
+#pragma unroll 5
+    for (int b = 0; b < NB; ++b) {
+      const float bv = (float)bk[b];
+      const float2 xv = xl[b];
+      const float p = __fmul_rn(bv, xv.x);
+      const float e = __fmaf_rn(bv, xv.x, -p);
+      const float t = __fadd_rn(s, p);
+      const float z = __fsub_rn(t, s);
+      const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+      c = __fadd_rn(c, __fadd_rn(err, __fmaf_rn(bv, xv.y, e)));
+      s = t;
+    }
+  }
+  return (double)s + (double)c;
+}
+
+// The same for QN <= 4 right-hand sides at once (their staged coefficients
+// xstride float2 apart): the QN independent two-sum chains interleave, which
+// keeps the FP32 pipes busy with few warps, and each block entry is read once.
+template <int NB, typename TV, int QN>
+__device__ __forceinline__ void row_times_x_split_q(const TV* blk, const float2* xs, int64_t xstride, int lp,
+                                                    double out[QN]) {
+  float s[QN], c[QN];
+#pragma unroll
+  for (int q = 0; q < QN; ++q) s[q] = c[q] = 0.f;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int l = k + (k >= lp ? 1 : 0);
+    const TV* bk = blk + k * NB * NB;
+    const float2* xl = xs + l * NB;
+#pragma unroll 3
+    for (int b = 0; b < NB; ++b) {
+      const float bv = (float)bk[b];
+#pragma unroll
+      for (int q = 0; q < QN; ++q) {
+        const float2 xv = xl[q * xstride + b];
+        const float p = __fmul_rn(bv, xv.x);
+        const float e = __fmaf_rn(bv, xv.x, -p);
+        const float t = __fadd_rn(s[q], p);
+        const float z = __fsub_rn(t, s[q]);
+        const float err = __fadd_rn(__fsub_rn(s[q], __fsub_rn(t, z)), __fsub_rn(p, z));
+        c[q] = __fadd_rn(c[q], __fadd_rn(err, __fmaf_rn(bv, xv.y, e)));
+        s[q] = t;
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < QN; ++q) out[q] = (double)s[q] + (double)c[q];
+}
+
 // Warp-specialised pipeline.  Warp 0 is the producer: for each of the block's
 // tiles it waits until the stage is free (`empty` barrier, one arrival per
 // consumer warp), reads the tile's row map (one coalesced load by the lanes),
@@ -211,6 +277,8 @@ spmv_tma_kernel(const Combo cb, int64_t row_stride, const int32_t* __restrict__ 
     return;
   }
   // ---------------- consumers ----------------
+  // FP64 vectors on a 32- or 16-bit operator: compensated FP32 sums
+  constexpr bool kSplit = std::is_same<TX, double>::value && !std::is_same<TV, double>::value;
   const int ctid = threadIdx.x - 32;
   const int nthreads = 32 * kConsumerWarps;
   for (int64_t i = 0; i < mine; ++i) {
@@ -221,6 +289,22 @@ spmv_tma_kernel(const Combo cb, int64_t row_stride, const int32_t* __restrict__ 
       break;
     }
     const unsigned char* st = stage0 + s * stage_bytes;
+    if constexpr (kSplit) {
+      // each staged coefficient (a double) becomes its (hi, lo) float pair in
+      // place, once per tile, before any consumer reads it
+      double* xd = reinterpret_cast<double*>(stage0 + s * stage_bytes + vals_bytes);
+      const int64_t tile = blockIdx.x + i * (int64_t)gridDim.x;
+      const int64_t left = nrows - (reverse ? ntiles - 1 - tile : tile) * rows_per_tile;
+      const int nr = left < rows_per_tile ? (int)left : rows_per_tile;
+      const int per = 4 * NB;
+      for (int e = ctid; e < R * rows_per_tile * per; e += nthreads) {
+        if ((e / per) % rows_per_tile >= nr) continue;  // rows past the mesh end are not staged
+        const double v = xd[e];
+        const float hi = (float)v;
+        reinterpret_cast<float2*>(xd)[e] = make_float2(hi, (float)(v - (double)hi));
+      }
+      asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+    }
     const TV* tv = reinterpret_cast<const TV*>(st);
     const TX* tx = reinterpret_cast<const TX*>(st + vals_bytes);
     const TX* tx0 = reinterpret_cast<const TX*>(st + vals_bytes + (int64_t)R * rows_per_tile * xblk);
@@ -234,10 +318,46 @@ spmv_tma_kernel(const Combo cb, int64_t row_stride, const int32_t* __restrict__ 
       const int a = e - r * NB;
       const int lp = rs[r] & 3;
       const TV* blk0 = tv + (int64_t)r * row_stride + a * NB;
+      if constexpr (kSplit) {
+        if (KC == 1) {  // four right-hand sides per pass of the block row
+          const int64_t xstride = (int64_t)rows_per_tile * 4 * NB;  // float2 pairs between right-hand sides
+          for (int q0 = 0; q0 < R; q0 += 4) {
+            double tot[4];
+            const float2* xs = reinterpret_cast<const float2*>(tx + ((int64_t)q0 * rows_per_tile + r) * 4 * NB);
+            if (R - q0 >= 4)
+              row_times_x_split_q<NB, TV, 4>(blk0, xs, xstride, lp, tot);
+            else if (R - q0 == 3)
+              row_times_x_split_q<NB, TV, 3>(blk0, xs, xstride, lp, tot);
+            else if (R - q0 == 2)
+              row_times_x_split_q<NB, TV, 2>(blk0, xs, xstride, lp, tot);
+            else
+              row_times_x_split_q<NB, TV, 1>(blk0, xs, xstride, lp, tot);
+            for (int q = 0; q < 4 && q0 + q < R; ++q) {
+              const int rhs = q0 + q;
+              const int64_t o = ((int64_t)rhs * nrows + R0 + r) * NB + a;
+              const TA base =
+                  stage_x0 ? (TA)tx0[((int64_t)rhs * rows_per_tile + r) * NB + a] : (x0 ? (TA)x0[o] : TA(0));
+              y[o] = (TX)(base + alpha * (TA)tot[q]);
+            }
+          }
+          continue;
+        }
+      }
       for (int rhs = 0; rhs < R; ++rhs) {
         const TX* xs = tx + ((int64_t)rhs * rows_per_tile + r) * 4 * NB;
         TA total;
-        if (KC == 1) {
+        if constexpr (kSplit) {
+          if (KC == 1) {
+            total = (TA)row_times_x_split<NB, TV>(blk0, reinterpret_cast<const float2*>(xs), lp);
+          } else {
+            total = TA(0);
+            for (int kk = 0; kk < K; ++kk)
+              total = fma((TA)cb.coef[rhs][kk],
+                          (TA)row_times_x_split<NB, TV>(blk0 + kk * (op_tile_bytes / (int64_t)sizeof(TV)),
+                                                        reinterpret_cast<const float2*>(xs), lp),
+                          total);
+          }
+        } else if (KC == 1) {
           total = row_times_x<NB, TV, TX, TA>(blk0, xs, lp);
         } else {
           total = TA(0);

@@ -96,6 +96,8 @@ SIGNATURES = {
     "dfm_tet_density": (_i, [_vp, _i, _vp, _vp, _i, _vp, _vp]),
     "dfm_adjoint": (_i, [_vp, ctypes.POINTER(Params), _vp, _i, _vp, _vp, _vp, _vp, ctypes.POINTER(SolveOpts), _vp,
                          ctypes.POINTER(SolveInfo)]),
+    "dfm_autotune": (_i, [_i]),
+    "dfm_autotune_report": (_i64, [ctypes.c_char_p, _i64]),
     "dfm_launch_count": (ctypes.c_longlong, []),
     "dfm_stats_enable": (_i, [_i]),
     "dfm_stats_reset": (_i, []),
@@ -562,6 +564,23 @@ def gauss_legendre(q: int):
 
 
 KERNEL_ASSEMBLE, KERNEL_SPMV, KERNEL_SPMV_T, KERNEL_DOT, KERNEL_AXPY, KERNEL_SPMV64, KERNEL_CONTRACT, KERNEL_SPMV16 = range(8)
+
+
+def autotune(mode: int = 1):
+    """0: fixed default launch geometries; 1: tune on first use (default);
+    2: forget the tuned choices and tune again (dfm_autotune)."""
+    _check(load().dfm_autotune(int(mode)), "dfm_autotune")
+
+
+def autotune_report() -> list:
+    """The autotuner's choices per launch shape (dfm_autotune_report)."""
+    import json
+
+    L = load()
+    n = int(L.dfm_autotune_report(None, 0))
+    buf = ctypes.create_string_buffer(n)
+    L.dfm_autotune_report(buf, n)
+    return json.loads(buf.value.decode())
 
 
 def launch_count() -> int:

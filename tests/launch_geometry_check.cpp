@@ -61,8 +61,8 @@ int main() {
                   }
                 }
               }
-  // preconditioner hops: copy bytes per value eb (FP16/BF16: 2, e4m3: 1 with a
-  // row scale), vector bytes vb (FP16: 2, FP32: 4), tensor-core layout mma
+  // preconditioner hops (CUDA-core kernel): copy bytes per value eb (FP16/BF16: 2,
+  // e4m3: 1 with a row scale), vector bytes vb (FP16: 2, FP32: 4)
   struct Fmt {
     int eb;
     bool scaled;
@@ -70,28 +70,82 @@ int main() {
   };
   const Fmt fmts[] = {{2, false, 2}, {2, false, 4}, {1, true, 2}};
   for (int nb : nbs)
-    for (const Fmt& f : fmts)
-      for (int mma = 0; mma < 2; ++mma) {
-        if (mma && (f.vb != 2 || hop_nbp(nb) % 16)) continue;
-        const int rpt = hop_tile_rows(nb, f.eb, f.scaled, mma != 0);
-        const int step = (32 * kHopConsumerWarps) / hop_nbp(nb);
-        if (rpt < 1 || rpt > 32 || (rpt != step && rpt != 2 * step)) return fail("hop rows per tile", nb, f.eb, f.vb, mma, rpt);
-        const long long row = hop_row_bytes(nb, f.eb, f.scaled);
-        if (row % 16) return fail("hop copy row", nb, f.eb, f.vb, mma, row);
-        const long long xblk = 4LL * hop_nbp(nb) * f.vb + (mma ? 16 : 0), x0row = (long long)hop_nbp(nb) * f.vb;
-        if (xblk % 16 || x0row % 16) return fail("hop vector rows", nb, f.eb, f.vb, mma, xblk);
-        const int chunk = hop_rhs_chunk(nb, f.eb, f.scaled, f.vb, mma != 0);
-        if (chunk < 1) return fail("hop right-hand-side chunk", nb, f.eb, f.vb, mma, chunk);
-        for (int R = 1; R <= chunk; ++R) {
-          ++checked;
-          const long long stage = hop_stage_bytes(nb, f.eb, f.scaled, f.vb, R, mma != 0);
-          if (stage != rpt * row + (long long)R * rpt * (xblk + x0row)) return fail("hop stage bytes", nb, f.eb, f.vb, R, stage);
-          const int stages = hop_stages(stage, 2);
-          if (stages < 2) return fail("hop stages", nb, f.eb, f.vb, R, stage);
-          const long long smem = 128 + (2LL * rpt * 4 + 127) / 128 * 128 + (long long)stages * stage;
-          if (smem > kSmem) return fail("hop shared memory", nb, f.eb, f.vb, R, smem);
-        }
+    for (const Fmt& f : fmts) {
+      const int rpt = hop_tile_rows(nb, f.eb, f.scaled);
+      const int step = (32 * kHopConsumerWarps) / hop_nbp(nb);
+      if (rpt < 1 || rpt > 32 || (rpt != step && rpt != 2 * step)) return fail("hop rows per tile", nb, f.eb, f.vb, 0, rpt);
+      const long long row = hop_row_bytes(nb, f.eb, f.scaled);
+      if (row % 16) return fail("hop copy row", nb, f.eb, f.vb, 0, row);
+      const long long xblk = 4LL * hop_nbp(nb) * f.vb, x0row = (long long)hop_nbp(nb) * f.vb;
+      if (xblk % 16 || x0row % 16) return fail("hop vector rows", nb, f.eb, f.vb, 0, xblk);
+      const int chunk = hop_rhs_chunk(nb, f.eb, f.scaled, f.vb);
+      if (chunk < 1) return fail("hop right-hand-side chunk", nb, f.eb, f.vb, 0, chunk);
+      for (int R = 1; R <= chunk; ++R) {
+        ++checked;
+        const long long stage = hop_stage_bytes(nb, f.eb, f.scaled, f.vb, R);
+        if (stage != rpt * row + (long long)R * rpt * (xblk + x0row)) return fail("hop stage bytes", nb, f.eb, f.vb, R, stage);
+        const int stages = hop_stages(stage, 2);
+        if (stages < 2) return fail("hop stages", nb, f.eb, f.vb, R, stage);
+        const long long smem = 128 + (2LL * rpt * 4 + 127) / 128 * 128 + (long long)stages * stage;
+        if (smem > kSmem) return fail("hop shared memory", nb, f.eb, f.vb, R, smem);
       }
+    }
+  // tensor-core hops on the fragment-ordered copy: every bulk copy (copy rows,
+  // x0 slices, gathered face rows) 16-byte aligned and sized, shared memory
+  // within a block, stages >= 2, for the default and requested geometries
+  for (int nb : nbs) {
+    if (!frag_basis(nb)) continue;
+    const int nbp = hop_nbp(nb);
+    // the layout: every (block, test < nb, trial < nbp) exactly once, and the
+    // offsets the consumer loads give the mma.sync A-fragment entries
+    static int seen[3 * 48 * 48];
+    for (int i = 0; i < 3 * nb * nbp; ++i) seen[i] = 0;
+    for (long long e = 0; e < 3LL * nb * nbp; ++e) {
+      const FragPos p = frag_pos(e, nb, nbp);
+      if (p.k < 0 || p.k > 2 || p.a < 0 || p.a >= nb || p.b < 0 || p.b >= nbp) return fail("frag position", nb, p.k, p.a, p.b, e);
+      ++seen[(p.k * nb + p.a) * nbp + p.b];
+    }
+    for (int i = 0; i < 3 * nb * nbp; ++i)
+      if (seen[i] != 1) return fail("frag layout not a bijection", nb, i, seen[i], 0, 0);
+    for (int k = 0; k < 3; ++k)
+      for (int mt = 0; mt < nbp / 16; ++mt)
+        for (int kt = 0; kt < nbp / 16; ++kt)
+          for (int lane = 0; lane < 32; ++lane)
+            for (int half = 0; half < 2; ++half)
+              for (int j = 0; j < 4; ++j) {
+                const int vm = nb - 16 * mt < 16 ? nb - 16 * mt : 16;
+                const int g = lane >> 2, t = lane & 3;
+                if (half && g + 8 >= vm) continue;  // rows past nb are not stored (the consumer loads 0)
+                const long long e = (long long)k * nb * nbp + 16LL * mt * nbp + (long long)kt * 16 * vm +
+                                    (half ? 128 : 0) + lane * 4 + j;
+                const FragPos p = frag_pos(e, nb, nbp);
+                const int want_a = 16 * mt + g + 8 * half;
+                const int want_b = 16 * kt + 2 * t + (j & 1) + (j >= 2 ? 8 : 0);
+                ++checked;
+                if (p.k != k || p.a != want_a || p.b != want_b) return fail("frag fragment entry", nb, mt, kt, lane, e);
+              }
+    for (const Fmt& f : fmts) {
+      if (f.vb != 2) continue;  // FP16 hop vectors only
+      for (int w : {1, 8})
+        for (int rgl = 1; rgl <= (w == 8 ? 2 : 1); ++rgl)
+          for (int rpt_req : {0, 1, 2, 3, 4, 6, 8, 12, 16, 24, 32})
+            for (int st_req : {0, 2, 3, 4, 6, 8}) {
+              const Frag g = frag_geometry(nb, f.eb, f.scaled, w, rgl, rpt_req, st_req);
+              ++checked;
+              if (g.rpt < 1 || g.rpt > 32) return fail("frag rows per tile", nb, f.eb, w, rgl, g.rpt);
+              if (g.stages < 2 || g.stages > kFragMaxStages || g.stages % kFragGroups)
+                return fail("frag stages", nb, f.eb, w, rgl, g.stages);
+              if (frag_smem_bytes(g) > kSmem) return fail("frag shared memory", nb, f.eb, w, rgl, frag_smem_bytes(g));
+              const long long row = hop_row_bytes(nb, f.eb, f.scaled), xr = frag_xrow_bytes(nb, w);
+              const long long x_off = g.rpt * row, x0_off = x_off + (long long)g.rpt * rgl * 4 * xr;
+              if (row % 16 || xr % 16 || x_off % 16 || x0_off % 16 || g.stage_bytes % 16 ||
+                  g.stage_bytes != x0_off + (long long)rgl * g.rpt * xr)
+                return fail("frag stage layout", nb, f.eb, w, rgl, g.stage_bytes);
+              if (rpt_req == 0 && g.stage_bytes > kFragStageTarget && g.rpt > 1)
+                return fail("frag default tile", nb, f.eb, w, rgl, g.stage_bytes);
+            }
+    }
+  }
   std::printf("ok %lld\n", checked);
   return 0;
 }

@@ -9,9 +9,11 @@ on the host, so the only difference left is the kernels' arithmetic (see
 TOL).  The mesh drops one tet of the Kuhn cube (161 tets), so the last tile
 of rows is ragged for every basis size; N_p = 2, 4, 5 give 6, 15, 21
 functions, N_p = 3 and 8 give 10 and 45 (padded widths 8, 16, 24, 16, 48).
-With several right-hand sides and a padded width that is a multiple of 16
-(N_p = 3, 4, 8 with the FP16 and e4m3 copies) the hops run on tensor cores;
-R = 9 fills one 8-right-hand-side tile and part of a second."""
+With a padded width that is a multiple of 16 (N_p = 3, 4, 8 with the FP16
+and e4m3 copies) the hops run on tensor cores on the fragment-ordered copy:
+R <= 3 one right-hand side per launch, R >= 4 in groups of 8 (R = 4 and 5
+fill part of one group, 9 one group and part of a second, 16 two full groups
+in one launch, 17 a second launch for the third group)."""
 import numpy as np
 import pytest
 
@@ -80,7 +82,7 @@ def mesh161():
     return m.verts, np.ascontiguousarray(m.tets[:-1])
 
 
-@pytest.mark.parametrize("Np,R", [(2, 3), (3, 3), (4, 3), (4, 9), (5, 3), (8, 5)])
+@pytest.mark.parametrize("Np,R", [(2, 3), (3, 3), (3, 4), (4, 1), (4, 3), (4, 9), (4, 17), (5, 3), (8, 5), (8, 16)])
 @pytest.mark.parametrize("prec", ["f16", "bf16", "e4m3"])
 def test_precond_matches_oracle_on_rounded_blocks(D, oracle_mod, mesh161, Np, R, prec):
     import torch
@@ -164,7 +166,7 @@ def _round_e4m3_columns(blocks32):
     return _e4m3(ratio) * s.astype(np.float64)[:, None, None, None]
 
 
-@pytest.mark.parametrize("Np,R", [(2, 1), (4, 1), (4, 3), (8, 5)])
+@pytest.mark.parametrize("Np,R", [(2, 1), (4, 1), (4, 3), (4, 9), (8, 1), (8, 5)])
 @pytest.mark.parametrize("prec", ["f16", "bf16", "e4m3"])
 def test_transposed_precond_matches_oracle(D, oracle_mod, mesh161, Np, R, prec):
     """z = sum_{k<d} (B~^T)^k x on the transposed copy (the adjoint solve's
@@ -220,3 +222,32 @@ def test_transposed_solve_with_low_precision_preconditioner(D, oracle_mod, mesh1
     for r in range(2):
         want = np.linalg.solve(M.T, b[r].cpu().numpy().ravel())
         assert np.linalg.norm(x[r].cpu().numpy().ravel() - want) <= 1e-8 * np.linalg.norm(want)
+
+
+@pytest.mark.parametrize("Np,R", [(4, 1), (8, 9)])
+def test_autotuned_hops_are_identical_and_reported(D, mesh161, Np, R):
+    """The autotuner times the candidate tile geometries of the tensor-core
+    hop on the first launch of a shape and keeps the fastest; geometry changes
+    no arithmetic, so hops with tuning on and off agree bit for bit, and the
+    report names the shape, its candidates and the fastest as the choice."""
+    import torch
+
+    verts, tets = mesh161
+    mesh = D.Mesh(verts, tets, refl=0.9)
+    op = D.Operator(mesh, Np, mu=0.2, precision=D.F32)
+    x = torch.randn((R, mesh.n_rows, op.nb), device="cuda", dtype=torch.float32)
+    try:
+        D.autotune(0)
+        z0 = op.precond(x, degree=4, precision=D.FP8E4M3)
+        D.autotune(2)
+        z1 = op.precond(x, degree=4, precision=D.FP8E4M3)
+        z2 = op.precond(x, degree=4, precision=D.FP8E4M3)
+    finally:
+        D.autotune(1)
+    assert torch.equal(z0, z1) and torch.equal(z1, z2)
+    rep = [e for e in D.autotune_report() if e["rows"] == mesh.n_rows and e["nb"] == op.nb]
+    assert rep, D.autotune_report()
+    for e in rep:
+        assert e["kernel"] == "hop_frag" and len(e["tried"]) >= 2
+        best = min(e["tried"], key=lambda t: t[2])
+        assert [e["chosen"]["rows_per_tile"], e["chosen"]["stages"]] == best[:2]
