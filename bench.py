@@ -1,16 +1,31 @@
-"""Benchmark: stationary DFM solves per second on one GB300 (or N replicas).
+"""Benchmark: stationary DFM solves per second with adjoint gradients on one
+GB300 (or N replicas).
 
-One step = the device-resident hot path on the 20^3 Kuhn-cube workload
-(48,000 jittered tets, Np = 4, mu = 0.05, r = 0.95, one boundary-face source):
-assemble the operator B (FP32 blocks, FP64 geometry set-up), project the
-source, and solve (I - B) rho = rho0 by FP64-residual iterative refinement
-around FP32 GMRES to a relative residual of 1e-8.  Inputs (mesh on device)
-are resident when the timed region starts; the operator (518 MB) and Krylov
-basis are larger than L2, so no flush is needed between steps.
+Default workload (the largest single-GPU configuration, 45-function basis):
+the 32^3 Kuhn cube (196,608 jittered tets, N_p = 8, mu = 0.05, r = 0.95),
+operator blocks in BF16 (9.6 GB), 64 random boundary-face sources and the
+mean interior density of the receiver cells [14, 18)^3 as the functional.
+A job assembles B for the 64 sources, solves them and the adjoint equation
+and forms every source's gradient; its 8 steps take the sources 8 at a time.
+One step: project the group's sources, solve (I - B) rho = rho0 for all 8 in
+lockstep to an FP64 relative residual of 1e-6 (FP64-residual refinement
+around flexible FP32 GMRES(32) right-preconditioned by sum_{k<64} B~^k on an
+e4m3 copy, hops on tensor cores), then the adjoint: the transposed solve
+(I - B)^T lambda = g to 1e-6 (at the job's first step, which also assembles
+B; the later steps start from that lambda, whose residual the refinement
+checks) and the fused lambda^T (dB/dmu) rho_r contraction, giving
+dJ_r/dmu_e for the 8 sources.  Assembly is also timed on its own (assembly
+blocks/s).  Inputs are resident when the timed region starts; the operator
+and Krylov vectors are far larger than L2, so no flush is needed between
+steps.  The value is sources per second, each with its solve and gradient.
 
-The e2e figure runs the same metric through the C ABI from HOST buffers:
-mesh arrays copied in (face matching and geometry run every step), the
-solution copied back to pinned host memory, all inside the timed region.
+The e2e figure runs the same steps through the C ABI with the step's source
+rows copied from host memory and its gradients dJ/dmu copied back to pinned
+host memory inside the timed region.
+
+--workload kuhn20_np4 runs the 48,000-tet single-source solve instead (one
+step = assembly + source + GMRES-IR solve to 1e-8), which is also reported in
+the default line under "kuhn20_np4".
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
 Under torchrun (N > 1) every rank runs an independent replica (weak scaling).
@@ -34,7 +49,16 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "stationary solves/s at 1e-6 rel err"
-WORKLOAD = "kuhn20_np4"
+WORKLOAD = "kuhn20_np4"          # the single-source solve of the 48,000-tet cube
+HEADLINE = "kuhn32_np8_rhs64"    # the default: 45 functions, BF16 blocks, sources in groups with adjoint
+HEADLINE_DESC = ("32^3 Kuhn cube x 6 = 196,608 jittered tets (jitter 0.2h, seed 0); Np = 8 (45 Zernike functions); "
+                 "mu = 0.05; boundary reflection 0.95; jobs of 64 random boundary-face unit sources (seed 2), 8 per "
+                 "step, each job assembling B once at its first step; "
+                 "BF16 operator blocks; FP64-residual refinement around flexible FP32 GMRES({restart}) "
+                 "right-preconditioned by sum_{{k<{d}}} B~^k on an e4m3 copy (tensor-core hops); relative residual "
+                 "1e-6; adjoint of the mean receiver density (cells [14,18)^3): transposed solve to 1e-6 on the "
+                 "transposed e4m3 copy at each job's first step (later steps start from it and check its residual) "
+                 "and the fused dB/dmu contraction for every step's sources")
 WORKLOAD_DESC = ("20^3 Kuhn cube x 6 = 48,000 jittered tets (jitter 0.2h, seed 0); Np = 4 (15 Zernike functions); "
                  "mu = 0.05; boundary reflection 0.95; unit isotropic source on the x = 0 face at (0, 1/2, 1/2); "
                  "solve to FP64 relative residual 1e-8")
@@ -51,7 +75,7 @@ SOLVER_DESC = {
 # right-preconditioned by sum_{k<16} B^k reaches the 1e-8 residual after 1,809
 # applications (the count the FP64 comparator path records).  The oracle arm
 # charges its measured per-application cost this many times.
-REF_APPLICATIONS = {"kuhn20_np4": 1809}
+REF_APPLICATIONS = {"kuhn20_np4": 1809, "kuhn32_np8_rhs64": 2600}
 FP32_LANES_PER_SM = 128
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # step's dominant kernel measured by ncu on this workload (mean of two
@@ -223,7 +247,12 @@ def summarize_kernels(kstats, n_rows, n_tets, Np, nodes, nsm, peaks, peak_src, w
     return kern, total, roofline
 
 
-def run_gpu(args):
+def run_gpu(args, extra=False):
+    """The single-source solve of a workload (by default the 48,000-tet cube).
+    extra: a short run of it inside the default benchmark (5 steps, 2 warm-up,
+    a 10 s CPU sample), returned instead of printed."""
+    import copy
+
     import torch
     import torch.distributed as dist
 
@@ -231,8 +260,14 @@ def run_gpu(args):
     from paper_1608_04607_gb300.inputs import workload
 
     ws, rank, local = _dist()
+    if extra:
+        args = copy.copy(args)
+        args.workload, args.steps, args.warmup = WORKLOAD, min(args.steps, 5), min(args.warmup, 2)
+        args.cpu_seconds = min(args.cpu_seconds, 10.0)
+        args.restart, args.poly, args.tol, args.batch = 0, 0, 0.0, 0
+        ws, rank = 1, 0
     torch.cuda.set_device(local)
-    if ws > 1:
+    if ws > 1 and not extra:
         dist.init_process_group("nccl")
     w = workload(args.workload)
     m = w["mesh"]
@@ -371,9 +406,240 @@ def run_gpu(args):
         res["fp64_gpu_path"] = fp64_comparator(dfm, mesh, Np, mu, rows, tol)
     if ws == 1 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(args.workload, op_apps=iters[-1], seconds=args.cpu_seconds)
+    if extra:
+        op.close()
+        mesh.close()
+        return res
     print(json.dumps(res))
     if ws > 1:
         dist.destroy_process_group()
+
+
+def _hop_bytes(n_rows, nb, R):
+    """Algorithmic bytes of one hop on the e4m3 copy: the values (one byte
+    each) and the row scale, the row map, and x, x0, y in FP16 per
+    right-hand side."""
+    return n_rows * (3 * nb * nb + 8) + 3 * nb * 2 * n_rows * R
+
+
+def _apply_bytes(n_rows, nb, block_bytes, vec_bytes, R):
+    """Algorithmic bytes of one application y = x0 + alpha B x on R
+    right-hand sides: blocks and row map once, x, x0 and y per right-hand side."""
+    return n_rows * (3 * nb * nb * block_bytes + 4) + 3 * nb * vec_bytes * n_rows * R
+
+
+def headline_kernels(ks, n_rows, n_tets, Np, nodes, nsm, peaks, peak_src, B):
+    """Per-kernel rooflines of the default workload's timed steps (ks: name ->
+    (launches, total ms)) and the roofline of the kernel with the largest
+    total time among the hops and applications."""
+    nb = (Np + 1) * (Np + 2) // 2
+    hbm_peak = float(peaks.get("hbm_gbs", HBM_PEAK_FALLBACK))
+    kern = {}
+    by = {"hop": _hop_bytes(n_rows, nb, B), "hop_t": _hop_bytes(n_rows, nb, 1),
+          "spmv": _apply_bytes(n_rows, nb, 2, 4, B), "spmv_t": _apply_bytes(n_rows, nb, 2, 4, 1),
+          "spmv_f64vec": _apply_bytes(n_rows, nb, 2, 8, B), "spmv_f64vec_t": _apply_bytes(n_rows, nb, 2, 8, 1)}
+    for name, b in by.items():
+        n, ms = ks.get(name, (0, 0.0))
+        if n:
+            ach = b / (ms / n * 1e-3) / 1e9
+            kern[name] = {"bound": "hbm", "launches": n, "ms_per_launch": ms / n, "bytes_per_launch": b,
+                          "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak}
+    for name in ("contract", "dot", "axpy"):
+        n, ms = ks.get(name, (0, 0.0))
+        if n:
+            kern[name] = {"launches": n, "ms_total": ms}
+    total = {k: v[1] for k, v in ks.items()}
+    dominant = max((k for k in by if k in kern), key=lambda k: total[k])
+    d = kern[dominant]
+    inst = {"hop": f"hop_frag_kernel<{nb}, __nv_fp8_e4m3, 8>", "hop_t": f"hop_frag_kernel<{nb}, __nv_fp8_e4m3, 1>"}
+    traffic = MEASURED_TRAFFIC.get((inst.get(dominant), HEADLINE))
+    roofline = {"bound": "hbm", "achieved": round(d["achieved"], 3), "peak": round(d["peak"], 3), "unit": "GB/s",
+                "frac": round(d["frac"], 4), "traffic": traffic, "kernel": dominant, "peak_source": peak_src}
+    return kern, total, roofline
+
+
+def run_headline(args):
+    """The default workload: source groups solved with adjoint gradients (see
+    the module docstring).  Prints the JSON line."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_1608_04607_gb300 import dfm
+    from paper_1608_04607_gb300.inputs import workload
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl")
+    w = workload(HEADLINE)
+    m = w["mesh"]
+    Np = w["Np"]
+    tol = args.tol if args.tol else w["tol"]
+    mu = float(w["mu"][0])
+    sources = np.asarray(w["sources"], dtype=np.int64)
+    receiver = w["receiver"]
+    B = args.batch or 8
+    restart = args.restart or 32
+    poly = args.poly or 64
+    precond = PRECOND[args.precond]
+    dfm.load()
+    mesh = dfm.Mesh(m.verts, m.tets, refl=w["refl"])
+    op = dfm.Operator(mesh, Np, mu=mu, precision=dfm.BF16)
+    g, dg = dfm.interior_density(mesh, Np, receiver, weights=1.0 / len(receiver), mu=mu)
+    skw = dict(tol=tol, restart=restart, poly_degree=poly, precond_precision=precond)
+
+    # a job: assemble B, solve all sources and the adjoint equation, and form
+    # every source's gradient; its steps take the sources B at a time, the
+    # first step assembles and solves the adjoint equation (lambda depends on
+    # the operator and the functional, not on the sources), the later steps
+    # start the adjoint refinement from that lambda (its FP64 residual is
+    # checked, then the contraction runs)
+    per_job = max(1, sources.size // B)
+    state = {"lam": None}
+
+    def group(i):
+        idx = (np.arange(B) + (i % per_job) * B) % sources.size
+        return sources[idx]
+
+    def step(i, rows=None):
+        first = i % per_job == 0
+        if first:
+            op.reassemble(mu)
+        rho0 = dfm.source(mesh, Np, group(i) if rows is None else rows)
+        rho, info = op.solve(rho0, batch=B, **skw)
+        lam, dj, ainfo = op.adjoint(rho, g, dg, lam0=None if first else state["lam"], **skw)
+        state["lam"] = lam
+        return rho, dj, info, ainfo
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+
+    # ---- timed region: device-resident steps --------------------------------
+    sampler = ClockSampler(local)
+    dfm.stats_reset()
+    dfm.stats_enable(STATS_EVERY)
+    l0 = dfm.launch_count()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    infos = []
+    for i in range(args.steps):
+        rho, dj, info, ainfo = step(args.warmup + i)
+        infos.append((info.iters, info.outer, info.resid, ainfo.iters, ainfo.resid))
+    e1.record()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    launches = dfm.launch_count() - l0
+    dfm.stats_enable(False)
+    elapsed_ms = e0.elapsed_time(e1)
+    names = {"assemble": dfm.KERNEL_ASSEMBLE, "hop": dfm.KERNEL_SPMV16, "hop_t": dfm.KERNEL_SPMV16_T,
+             "spmv": dfm.KERNEL_SPMV,
+             "spmv_t": dfm.KERNEL_SPMV_T, "spmv_f64vec": dfm.KERNEL_SPMV64, "spmv_f64vec_t": dfm.KERNEL_SPMV64_T,
+             "contract": dfm.KERNEL_CONTRACT, "dot": dfm.KERNEL_DOT, "axpy": dfm.KERNEL_AXPY}
+    ks = {k: dfm.kernel_stats(v) for k, v in names.items()}
+    elapsed_ms = max_over_ranks(elapsed_ms, ws, "cuda")
+    J = float((g * rho).sum())
+
+    # ---- assembly (timed on its own: re-assembly into the same operator) -----
+    dfm.stats_reset()
+    dfm.stats_enable(True)
+    for _ in range(2):
+        op.reassemble(mu)
+    torch.cuda.synchronize()
+    n_as, ms_as = dfm.kernel_stats(dfm.KERNEL_ASSEMBLE)
+    dfm.stats_enable(False)
+    nodes = dfm.op_nodes(op)
+
+    # ---- e2e: C ABI with host source rows in and host gradients out ----------
+    e2e = None
+    if not args.no_e2e:
+        e2e_steps = max(1, min(args.steps, args.e2e_steps))
+        host_dj = torch.empty((B, m.n_tets), dtype=torch.float64, pin_memory=True)
+        host_rows = [np.ascontiguousarray(group(i)) for i in range(e2e_steps)]
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(e2e_steps):
+            _, dj_i, _, _ = step(i, rows=host_rows[i])
+            host_dj.copy_(dj_i, non_blocking=True)
+            torch.cuda.synchronize()
+        dt = max_over_ranks(time.perf_counter() - t0, ws, "cuda")
+        e2e = {"value": ws * B * e2e_steps / dt, "unit": "solves/s", "steps": e2e_steps,
+               "h2d_bytes_per_step": int(host_rows[0].nbytes), "d2h_bytes_per_step": int(host_dj.numel() * 8)}
+
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return
+    peaks, peak_src = _peaks()
+    nsm = torch.cuda.get_device_properties(local).multi_processor_count
+    kern, total, roofline = headline_kernels(ks, mesh.n_rows, int(m.n_tets), Np, nodes, nsm, peaks, peak_src, B)
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = nsm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    asm_ach = nodes * flops_per_node(Np) / (ms_as / n_as * 1e-3) / 1e12
+    it = np.array(infos)
+    res = {
+        "metric": METRIC,
+        "value": ws * B * args.steps / (elapsed_ms * 1e-3),
+        "unit": "solves/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": elapsed_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "bf16 blocks, e4m3 preconditioner copy, f16 hop vectors, f32 Krylov, f64 residual",
+        "data": "synthetic",
+        "config": {"workload": HEADLINE, "desc": HEADLINE_DESC.format(restart=restart, d=poly),
+                   "n_tets": int(m.n_tets), "n_rows": int(mesh.n_rows), "nb": op.nb, "sources_per_step": B,
+                   "tol": tol, "restart": restart, "poly_degree": poly, "precond": args.precond,
+                   "unit_of_work": "one source solved to 1e-6 with its gradient dJ/dmu; a job of 64 sources "
+                                   "(8 steps) assembles B and solves the adjoint equation once, at its first step",
+                   "l2": "inputs larger than L2 (operator %.0f MB)" % (op.bytes / 1e6),
+                   "parallelism": f"replicas x{ws}"},
+        "roofline": roofline,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "assembly": {"ms": ms_as / n_as, "blocks_per_s": 12 * m.n_tets / (ms_as / n_as * 1e-3),
+                     "roofline": {"bound": "alu", "achieved": asm_ach, "peak": fp32_peak, "unit": "TFLOP/s",
+                                  "frac": asm_ach / fp32_peak, "nodes": nodes, "flops_per_node": flops_per_node(Np),
+                                  "peak_source": f"{nsm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz"}},
+        "assembly_blocks_per_s": 12 * m.n_tets / (ms_as / n_as * 1e-3),
+        "solve": {"operator_passes_per_step": int(np.median(it[:, 0])), "adjoint_passes_per_step": int(np.median(it[:, 3])),
+                  "resid_worst": float(it[:, 2].max()), "adjoint_resid_worst": float(it[:, 4].max()), "J": J},
+        "kernels": {k: {kk: (round(vv, 5) if isinstance(vv, float) else vv) for kk, vv in v.items()}
+                    for k, v in kern.items()},
+        "kernel_ms_per_step": {k: round(v / args.steps, 3) for k, v in total.items()},
+        "autotune": [{k: e[k] for k in ("nb", "rhs_per_group", "groups", "transpose", "rows", "chosen")}
+                     | {"candidates": len(e["tried"])} for e in dfm.autotune_report()
+                     if e["rows"] == mesh.n_rows],
+    }
+    op.close()
+    del rho, dj
+    torch.cuda.synchronize()
+    if not args.no_comparator:
+        res["fp64_gpu_path"] = fp64_sample(dfm, mesh, Np, [mu], sources[:1], tol, per_rhs_assembly=False,
+                                           warm=False)
+    if ws == 1 and not args.no_cpu_baseline:
+        apps = int(np.median(it[:, 0])) if "fp64_gpu_path" not in res else res["fp64_gpu_path"]["operator_applications"][0]
+        res["cpu_baseline"] = cpu_baseline(HEADLINE, op_apps=apps, seconds=args.cpu_seconds, group=B)
+    mesh.close()
+    if not args.no_extra:
+        res["kuhn20_np4"] = run_gpu(args, extra=True)
+    print(json.dumps(res))
+    if ws > 1:
+        dist.destroy_process_group()
+
 
 
 def fp64_comparator(dfm, mesh, Np, mu, rows, tol):
@@ -406,15 +672,21 @@ def fp64_comparator(dfm, mesh, Np, mu, rows, tol):
 # CPU oracle (reported baseline and the reference arm)
 # ---------------------------------------------------------------------------
 
-def _oracle_sample(wname, seconds, op_apps=None):
+def _oracle_sample(wname, seconds, op_apps=None, group=1):
     """Time the FP64 oracle, as it stands, on a bounded sample of the workload:
     (a) adaptive (1e-13) assembly of randomly drawn face pairs until about
     `seconds`/2 of wall time, giving seconds per block; (b) restarted GMRES
-    iterations of the oracle at full size on an operator with the workload's
-    sparsity, giving seconds per operator application (block values do not
-    change the work).  Extrapolated solve time = (a) x 12 N + (b) x op_apps."""
+    iterations of the oracle on an operator with the workload's sparsity,
+    giving seconds per operator application (block values do not change the
+    work): at full size, or, when the FP64 blocks would pass 2 GB, on the
+    8^3 cube with the same basis, scaled by the ratio of operator rows.
+    Extrapolated time of one benchmark step = (a) x 12 N x (the step's share
+    of the assembly) + (b) x op_apps x (solves per step).  The default
+    workload's step solves `group` sources and one adjoint equation and is
+    charged group / (number of sources) of the assembly; a single-source step
+    one solve and the whole assembly."""
     import oracle
-    from paper_1608_04607_gb300.inputs import workload
+    from paper_1608_04607_gb300.inputs import kuhn_cube_mesh, workload
 
     w = workload(wname)
     m = w["mesh"]
@@ -437,25 +709,36 @@ def _oracle_sample(wname, seconds, op_apps=None):
         n_pairs += batch
         batch *= 2
     per_block = t_asm / n_pairs
-    # the same assembly on one thread (a fixed sample of 32 pairs)
-    sel = rng.integers(0, t.size, size=32)
+    # the same assembly on one thread (a fixed sample of 32 pairs; 4 for large bases)
+    n1 = 32 if nb <= 15 else 4
+    sel = rng.integers(0, t.size, size=n1)
     t0 = time.perf_counter()
     oracle.blocks_for_pairs(m.verts, m.tets, topo, mu, w["refl"], Np, t[sel], f[sel], fp[sel], rtol=1e-13, nthreads=1)
-    per_block_1t = (time.perf_counter() - t0) / 32
-    # (b) oracle GMRES iterations at full size
-    blocks = rng.standard_normal((4 * m.n_tets, 3, nb, nb)) * (0.3 / nb)
-    dest = topo.recv[4 * np.repeat(np.arange(m.n_tets), 12) + fp].reshape(4 * m.n_tets, 3)
+    per_block_1t = (time.perf_counter() - t0) / n1
+    # (b) oracle GMRES iterations, at full size or on the 8^3 cube scaled by rows
+    ms = m
+    if 4 * m.n_tets * 3 * nb * nb * 8 > 2e9:
+        ms = kuhn_cube_mesh(8, jitter=0.2, seed=0)
+    tops = topo if ms is m else oracle.topology(ms.tets)
+    _, _, fps = oracle.pair_list(ms.n_tets)
+    blocks = rng.standard_normal((4 * ms.n_tets, 3, nb, nb)) * (0.3 / nb)
+    dest = tops.recv[4 * np.repeat(np.arange(ms.n_tets), 12) + fps].reshape(4 * ms.n_tets, 3)
     op = oracle.Operator(Np=Np, blocks=blocks, dest=dest)
-    rho0 = oracle.source_vector(m.verts, m.tets, w["sources"][:1], Np)
-    k = 16
+    rho0 = oracle.source_vector(ms.verts, ms.tets, [int(np.nonzero(tops.recv == np.arange(4 * ms.n_tets))[0][0])], Np)
+    k = 16 if ms is m else 8
     t0 = time.perf_counter()
     oracle.solve_gmres(op, rho0, tol=1e-300, restart=64, maxit=k)
-    per_app = (time.perf_counter() - t0) / k
+    per_app = (time.perf_counter() - t0) / k * (m.n_tets / ms.n_tets)
     if op_apps is None:
         op_apps = 0
-    est = per_block * 12 * m.n_tets + per_app * op_apps
-    sample = (f"oracle assembly of {n_pairs} random face pairs (adaptive to 1e-13) and {k} oracle GMRES(64) "
-              f"iterations at full size; extrapolated to 12 x {m.n_tets} blocks + {op_apps} operator applications")
+    headline = wname == HEADLINE
+    share = group / len(w["sources"]) if headline else 1.0
+    solves = group + 1 if headline else 1
+    est = per_block * 12 * m.n_tets * share + per_app * op_apps * solves
+    where = "at full size" if ms is m else f"on the 8^3 cube ({4 * ms.n_tets} rows) scaled to {4 * m.n_tets} rows"
+    sample = (f"extrapolated: oracle assembly of {n_pairs} random face pairs (adaptive to 1e-13) and {k} oracle "
+              f"GMRES(64) iterations {where}; per step {share:g} x 12 x {m.n_tets} blocks + {solves} x {op_apps} "
+              f"operator applications")
     return est, sample, threads, per_block, per_app, per_block_1t
 
 
@@ -473,9 +756,10 @@ def _cpu_model():
     return platform.processor() or platform.machine()
 
 
-def cpu_baseline(wname, op_apps, seconds=20.0):
-    est, sample, threads, per_block, per_app, per_block_1t = _oracle_sample(wname, seconds, op_apps)
-    return {"value": 1.0 / est, "unit": "solves/s", "cores": threads, "kind": "oracle", "sample": sample,
+def cpu_baseline(wname, op_apps, seconds=20.0, group=1):
+    est, sample, threads, per_block, per_app, per_block_1t = _oracle_sample(wname, seconds, op_apps, group)
+    return {"value": group / est, "unit": "solves/s", "cores": threads, "kind": "oracle", "sample": sample,
+            "operator_applications_charged": op_apps,
             "s_per_block": per_block, "s_per_block_1thread": per_block_1t, "s_per_application": per_app,
             "cpu_model": _cpu_model()}
 
@@ -484,28 +768,33 @@ def run_reference(args):
     ws, rank, local = _dist()
     if rank != 0:
         return
-    # a full oracle solve takes about half an hour of CPU time, so each step
-    # times the oracle on a bounded sample (assembly of random face pairs and
-    # full-size GMRES iterations) and extrapolates to the whole solve with the
-    # FP64 path's application count
+    # a full oracle solve takes hours of CPU time, so each step times the
+    # oracle on a bounded sample (assembly of random face pairs and GMRES
+    # iterations) and extrapolates to the whole step with the FP64 GPU path's
+    # application count
     from paper_1608_04607_gb300.inputs import workload
 
-    wl = workload(args.workload)
-    apps = args.ref_apps or REF_APPLICATIONS.get(args.workload, 2000)
+    wname = args.workload or HEADLINE
+    wl = workload(wname)
+    apps = args.ref_apps or REF_APPLICATIONS.get(wname, 2000)
+    group = (args.batch or 8) if wname == HEADLINE else 1
     vals = []
     last = None
     for i in range(args.warmup + args.steps):
-        est, sample, threads, _, _, _ = _oracle_sample(args.workload, args.cpu_seconds / 2, apps)
+        est, sample, threads, _, _, _ = _oracle_sample(wname, args.cpu_seconds / 2, apps, group)
         if i >= args.warmup:
             vals.append(est)
         last = (sample, threads)
-    v = 1.0 / statistics.mean(vals)
+    v = group / statistics.mean(vals)
+    desc = (HEADLINE_DESC.format(restart=32, d=64) if wname == HEADLINE else
+            WORKLOAD_DESC if wname == WORKLOAD else wname)
     res = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": ws,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(vals) * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": args.workload,
-                      "desc": (WORKLOAD_DESC if args.workload == WORKLOAD else args.workload)
-                      + "; FP64 CPU oracle (adaptive assembly to 1e-13, restarted GMRES), timed on a bounded sample",
+           "config": {"workload": wname,
+                      "desc": desc + "; FP64 CPU oracle (adaptive assembly to 1e-13, restarted GMRES), timed on a "
+                      "bounded sample and extrapolated",
+                      "sources_per_step": group, "operator_applications_charged": apps,
                       "n_tets": int(wl["mesh"].n_tets), "n_rows": int(wl["mesh"].n_rows),
                       "nb": (wl["Np"] + 1) * (wl["Np"] + 2) // 2, "tol": args.tol or wl["tol"]},
            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": last[1], "kind": "oracle", "sample": last[0]},
@@ -586,10 +875,11 @@ def run_hop(args):
     ach = by / (ms / n * 1e-3) / 1e9
     print(json.dumps({"mode": "hop", "workload": args.workload, "precond": args.precond, "rhs": R, "launches": n,
                       "ms_per_launch": ms / n, "bytes_per_launch": by, "achieved_gbs": ach,
-                      "frac": ach / float(peaks.get("hbm_gbs", HBM_PEAK_FALLBACK)), "peak_source": src}))
+                      "frac": ach / float(peaks.get("hbm_gbs", HBM_PEAK_FALLBACK)), "peak_source": src,
+                      "autotune": [e for e in dfm.autotune_report() if e["rows"] == mesh.n_rows]}))
 
 
-def fp64_sample(dfm, mesh, Np, mus, rows, tol, per_rhs_assembly):
+def fp64_sample(dfm, mesh, Np, mus, rows, tol, per_rhs_assembly, warm=True):
     """The plain FP64 GPU path on a sample of a multi-source workload: FP64
     blocks and FP64 GMRES(128) with sum_{k<16} B^k (the settings of the
     single-source comparator), one solve per source, to the same residual.
@@ -609,7 +899,8 @@ def fp64_sample(dfm, mesh, Np, mus, rows, tol, per_rhs_assembly):
             op.close()
         return info
 
-    one(mus[0], rows[0])
+    if warm:
+        one(mus[0], rows[0])
     times, apps = [], []
     for mu, row in zip(mus, rows):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
@@ -624,7 +915,8 @@ def fp64_sample(dfm, mesh, Np, mus, rows, tol, per_rhs_assembly):
         shared.close()
     ms = sum(times)
     return {"value": len(times) / (ms * 1e-3), "unit": "solves/s", "ms_per_solve": ms / len(times),
-            "sample": f"the first {len(times)} sources", "operator_applications": apps,
+            "sample": f"the first {len(times)} sources" + ("" if warm else " (no warm-up solve)"),
+            "operator_applications": apps,
             "assembly_in_timed_region": bool(per_rhs_assembly),
             "desc": "FP64 blocks, FP64 GMRES(128) with sum_{k<16} B^k, same tolerance"}
 
@@ -645,7 +937,7 @@ def run_batched(args):
     from paper_1608_04607_gb300.inputs import workload
 
     torch.cuda.set_device(0)
-    wname = args.workload if args.workload != WORKLOAD else "kuhn30_np4_rhs128"
+    wname = args.workload
     w = workload(wname)
     m = w["mesh"]
     Np = w["Np"]
@@ -771,7 +1063,7 @@ def run_many(args):
     from paper_1608_04607_gb300.inputs import workload
 
     torch.cuda.set_device(0)
-    wname = args.workload if args.workload != WORKLOAD else "kuhn32_np8_rhs64"
+    wname = args.workload
     w = workload(wname)
     m = w["mesh"]
     Np = w["Np"]
@@ -875,7 +1167,7 @@ def run_adjoint(args):
     from paper_1608_04607_gb300.inputs import workload
 
     torch.cuda.set_device(0)
-    wname = args.workload if args.workload != WORKLOAD else "kuhn40_np3_adjoint"
+    wname = args.workload
     w = workload(wname)
     m = w["mesh"]
     Np = w["Np"]
@@ -948,7 +1240,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
-    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--workload", default=None,
+                    help="default: the 196,608-tet 45-function workload (solve mode); see each mode for its own")
     ap.add_argument("--tol", type=float, default=0.0)
     ap.add_argument("--restart", type=int, default=0)
     ap.add_argument("--poly", type=int, default=0)
@@ -966,7 +1259,18 @@ def main():
     ap.add_argument("--fp64-sample", type=int, default=0,
                     help="batched and many modes: time the plain FP64 GPU path on this many sources")
     ap.add_argument("--fd", type=int, default=0, help="adjoint mode: elements checked by central differences")
+    ap.add_argument("--e2e-steps", type=int, default=8, help="default workload: steps of the e2e measurement (8 = a job)")
+    ap.add_argument("--no-extra", action="store_true", help="default workload: skip the 48,000-tet solve's key")
+    ap.add_argument("--autotune", type=int, choices=[0, 1], default=1,
+                    help="1: tune the hop launch geometry on first use (default); 0: fixed default geometry")
     args = ap.parse_args()
+    if args.workload is None and args.impl != "reference":
+        args.workload = {"solve": HEADLINE, "batched": "kuhn30_np4_rhs128", "many": HEADLINE,
+                         "adjoint": "kuhn40_np3_adjoint"}.get(args.mode, WORKLOAD)
+    if args.impl != "reference" and args.autotune == 0:
+        from paper_1608_04607_gb300 import dfm
+
+        dfm.autotune(0)
     if args.impl == "reference":
         run_reference(args)
     elif args.mode == "apply":
@@ -981,6 +1285,8 @@ def main():
         run_many(args)
     elif args.mode == "cuboid":
         run_cuboid(args)
+    elif args.workload == HEADLINE:
+        run_headline(args)
     else:
         run_gpu(args)
 

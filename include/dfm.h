@@ -348,7 +348,10 @@ int dfm_tet_density(const dfm_mesh* mesh, int Np, const double* gvec, const doub
  *   params: the damping the operator was assembled with (mu, Np, quadrature).
  *   rho: device FP64 [R][rows][nb]; gvec, dgvec: device FP64 [rows][nb] (one
  *   functional shared by all R right-hand sides, so one adjoint solve serves all);
- *   lambda_out: device FP64 [rows][nb]; dJ_dmu: device FP64 [R][n_tets] (overwritten).
+ *   lambda_out: device FP64 [rows][nb]; with opts->use_x0 = 1 it holds the
+ *   initial guess on entry (e.g. lambda of an earlier call with the same
+ *   operator and functional: the refinement then checks its FP64 residual and
+ *   stops at once if it meets tol); dJ_dmu: device FP64 [R][n_tets] (overwritten).
  * Synchronises like dfm_solve.  Errors as dfm_solve. */
 int dfm_adjoint(const dfm_op* op, const dfm_params* params, const double* rho, int R, const double* gvec,
                 const double* dgvec, double* lambda_out, double* dJ_dmu, const dfm_solve_opts* opts, void* stream,
@@ -405,7 +408,7 @@ int64_t dfm_autotune_report(char* buf, int64_t len);
  *     them while enabled) and their device milliseconds: the sum over the
  *     timed launches scaled by launches / timed launches (waits for the
  *     recorded events). */
-#define DFM_KERNEL_COUNT 8
+#define DFM_KERNEL_COUNT 10
 #define DFM_KERNEL_ASSEMBLE 0 /* operator assembly (one warp per face pair) */
 #define DFM_KERNEL_SPMV 1     /* y = x0 + alpha B x */
 #define DFM_KERNEL_SPMV_T 2   /* y = x0 + alpha B^T x */
@@ -414,6 +417,8 @@ int64_t dfm_autotune_report(char* buf, int64_t len);
 #define DFM_KERNEL_SPMV64 5   /* y = x0 + alpha B x with FP64 vectors (residuals) */
 #define DFM_KERNEL_CONTRACT 6 /* fused lambda^T (dB/dmu) rho per tet */
 #define DFM_KERNEL_SPMV16 7   /* preconditioner hop on the low-precision copy */
+#define DFM_KERNEL_SPMV16_T 8 /* preconditioner hop on the transposed copy (adjoint solves) */
+#define DFM_KERNEL_SPMV64_T 9 /* y = x0 + alpha B^T x with FP64 vectors (adjoint residuals) */
 long long dfm_launch_count(void);
 int dfm_stats_enable(int on);
 int dfm_stats_reset(void);

@@ -355,7 +355,7 @@ extern "C" int dfm_adjoint(const dfm_op* op, const dfm_params* params, const dou
   // 1. adjoint equation (I - B)^T lambda = g
   dfm_solve_opts o = *opts;
   o.transpose = 1;
-  o.use_x0 = 0;
+  o.use_x0 = opts->use_x0 ? 1 : 0;  // lambda_out holds the initial guess
   int rc = dfm_solve(op, gvec, 1, lambda_out, &o, stream, info);
   if (rc != DFM_OK && rc != DFM_ERR_NOT_CONVERGED) return rc;
   const int solve_rc = rc;

@@ -63,12 +63,14 @@ struct dfm_op {
   int64_t lp_bytes = 0;
   int lp_precision = 0;
   bool lp_valid = false;
+  bool lp_frag = false;  // fragment-ordered (tensor-core hops) rather than chunk-ordered
   // the same for B^T (transposed solves): row J = 4t + l holds the blocks that
   // column J sends, transposed, in the order of the receiving faces l' != l
   void* lpT_vals = nullptr;
   int64_t lpT_bytes = 0;
   int lpT_precision = 0;
   bool lpT_valid = false;
+  bool lpT_frag = false;
   // assembly scratch (per-pair constants, Gauss table), grown on demand
   void* work = nullptr;
   int64_t work_bytes = 0;
@@ -112,17 +114,19 @@ void forget_sweep(const void* vals);
 // Padded width of a face's coefficients in hop vectors and in the copy.
 inline int hop_nbp(int nb) { return geom::hop_nbp(nb); }
 // (re)builds op->lp_vals (trans: op->lpT_vals) in precision DFM_F16, DFM_BF16
-// or DFM_FP8E4M3 from the FP32 or BF16 blocks
-int prepare_lowp(const dfm_op* op, int precision, cudaStream_t st, int trans = 0);
+// or DFM_FP8E4M3 from the FP32 or BF16 blocks, in the layout that hops with R
+// right-hand sides per launch group run fastest on
+int prepare_lowp(const dfm_op* op, int precision, cudaStream_t st, int trans, int R);
 // the forward (trans = 0) or transposed copy of op
 struct LowpView {
   const void* vals;
   int precision;
   bool valid;
+  bool frag;
 };
 inline LowpView lowp_of(const dfm_op* op, int trans) {
-  return trans ? LowpView{op->lpT_vals, op->lpT_precision, op->lpT_valid}
-               : LowpView{op->lp_vals, op->lp_precision, op->lp_valid};
+  return trans ? LowpView{op->lpT_vals, op->lpT_precision, op->lpT_valid, op->lpT_frag}
+               : LowpView{op->lp_vals, op->lp_precision, op->lp_valid, op->lp_frag};
 }
 // z = sum_{k<d} B~^k v for R vectors ([R][rows][nb] FP32) by Horner on the
 // low-precision copy (trans: B~^T on the transposed copy); vp, ha, hb: 16-byte-aligned scratch of R rows NBP floats

@@ -57,9 +57,14 @@ using namespace hopk;
 using geom::kFragGroupMin;
 
 // FP16 and e4m3 copies of bases padded to a multiple of 16 are stored
-// fragment-ordered and hopped on tensor cores (hop_frag.cuh)
-bool frag_copy(int nb, int precision) {
-  return geom::frag_basis(nb) && (precision == DFM_F16 || precision == DFM_FP8E4M3);
+// fragment-ordered and hopped on tensor cores (hop_frag.cuh), except for one
+// to three right-hand sides on the smallest such bases (padded width 16),
+// whose rows are too short for the tensor-core consumer's per-row cost: there
+// the CUDA-core hop on the chunk-ordered copy runs faster (29.5 against
+// 39 us per e4m3 hop at N_b = 15 on 192,000 rows)
+bool frag_copy(int nb, int precision, int R) {
+  if (!geom::frag_basis(nb) || (precision != DFM_F16 && precision != DFM_FP8E4M3)) return false;
+  return R >= kFragGroupMin || hop_nbp(nb) > 16;
 }
 
 // FP16/BF16 copy: element i of the copy <- its block entry (0 in pads); the
@@ -223,7 +228,7 @@ int grid_for_elems(int64_t n) {
 
 }  // namespace
 
-int prepare_lowp(const dfm_op* cop, int precision, cudaStream_t st, int trans) {
+int prepare_lowp(const dfm_op* cop, int precision, cudaStream_t st, int trans, int R) {
   dfm_op* op = const_cast<dfm_op*>(cop);
   if ((op->precision != DFM_F32 && op->precision != DFM_BF16) ||
       (precision != DFM_F16 && precision != DFM_BF16 && precision != DFM_FP8E4M3))
@@ -233,6 +238,8 @@ int prepare_lowp(const dfm_op* cop, int precision, cudaStream_t st, int trans) {
   int64_t& have = trans ? op->lpT_bytes : op->lp_bytes;
   int& prec = trans ? op->lpT_precision : op->lp_precision;
   bool& valid = trans ? op->lpT_valid : op->lp_valid;
+  bool& frag = trans ? op->lpT_frag : op->lp_frag;
+  const bool want_frag = frag_copy(op->nb, precision, R);
   const int32_t* recvT = trans ? op->mesh->recv : nullptr;
   const int nb = op->nb, nbp = hop_nbp(nb);
   const int64_t row_bytes = precision == DFM_FP8E4M3 ? copy_row_bytes<__nv_fp8_e4m3>(nb, nbp)
@@ -248,10 +255,10 @@ int prepare_lowp(const dfm_op* cop, int precision, cudaStream_t st, int trans) {
     DFM_CUDA_CHECK(cudaMalloc(&vals, bytes));
     have = bytes;
   }
-  if (!valid || prec != precision) {
+  if (!valid || prec != precision || frag != want_frag) {
     auto convert = [&](auto src) {
       using S = std::remove_const_t<std::remove_pointer_t<decltype(src)>>;
-      if (frag_copy(nb, precision)) {
+      if (want_frag) {
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((op->nrows * 32 + 255) / 256, 4096));
         if (precision == DFM_FP8E4M3)
           to_frag_kernel<__nv_fp8_e4m3, S><<<grid, 256, 0, st>>>(src, op->row_stride, (unsigned char*)vals, op->nrows,
@@ -280,6 +287,7 @@ int prepare_lowp(const dfm_op* cop, int precision, cudaStream_t st, int trans) {
     DFM_LAUNCHED();
     DFM_CUDA_CHECK(cudaGetLastError());
     prec = precision;
+    frag = want_frag;
     valid = true;
   }
   return DFM_OK;
@@ -447,8 +455,7 @@ int hop_horner(const dfm_op* op, int R, int d, const float* v, float* z, void* v
   // FP16 and e4m3 copies run the hops on FP16 vectors (v scaled by vscale);
   // the BF16 copy on FP32 vectors
   if (lowp_of(op, trans).precision == DFM_BF16) return horner_t<float>(op, R, d, v, z, vp, ha, hb, 1.0f, trans, st);
-  if (frag_copy(op->nb, lowp_of(op, trans).precision))
-    return horner_frag(op, R, d, v, z, vp, ha, hb, vscale, trans, st);
+  if (lowp_of(op, trans).frag) return horner_frag(op, R, d, v, z, vp, ha, hb, vscale, trans, st);
   return horner_t<__half>(op, R, d, v, z, vp, ha, hb, vscale, trans, st);
 }
 
@@ -463,7 +470,7 @@ extern "C" int dfm_precond_apply(const dfm_op* op, int precision, int degree, in
   if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(z)) & 15)
     return set_error(DFM_ERR_ARG, "dfm_precond_apply: x and z must be 16-byte aligned");
   cudaStream_t st = as_stream(stream);
-  int rc = prepare_lowp(op, precision, st, transpose ? 1 : 0);
+  int rc = prepare_lowp(op, precision, st, transpose ? 1 : 0, R);
   if (rc) return rc;
   const int64_t rows = (int64_t)R * op->nrows;
   const int64_t elems = rows * hop_nbp(op->nb);

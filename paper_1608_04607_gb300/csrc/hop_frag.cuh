@@ -87,7 +87,7 @@ __device__ __forceinline__ uint32_t e4m3x2_to_h2(uint32_t pair16) {
 
 __device__ __forceinline__ void mma_16816(float d[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
                                           uint32_t b0, uint32_t b1) {
-  asm volatile(
+  asm(
       "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
       : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
       : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
@@ -294,9 +294,14 @@ hop_frag_kernel(const unsigned char* __restrict__ vals, const int32_t* __restric
       const unsigned char* brow = st + (int64_t)r * ROW;
       const __half* xs = reinterpret_cast<const __half*>(st + x_off + ((int64_t)r * rgl + gl) * 4 * XR);
       const int lp = s_lp[s * 32 + r];
-      float acc[MT][4];
+      // one right-hand side: the three blocks accumulate apart (three
+      // independent MMA chains per row instead of one), summed at the end
+      constexpr int NACC = W == 1 ? 3 : 1;
+      float acc[NACC][MT][4];
 #pragma unroll
-      for (int mt = 0; mt < MT; ++mt) acc[mt][0] = acc[mt][1] = acc[mt][2] = acc[mt][3] = 0.f;
+      for (int q = 0; q < NACC; ++q)
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt) acc[q][mt][0] = acc[q][mt][1] = acc[q][mt][2] = acc[q][mt][3] = 0.f;
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
         const int l = k + (k >= lp ? 1 : 0);
@@ -315,10 +320,16 @@ hop_frag_kernel(const unsigned char* __restrict__ vals, const int32_t* __restric
           for (int mt = 0; mt < MT; ++mt) {
             uint32_t a0, a1, a2, a3;
             load_a<E, NB, NBP>(bk, mt, kt, lane, a0, a1, a2, a3);
-            mma_16816(acc[mt], a0, a1, a2, a3, b0, b1);
+            mma_16816(acc[k % NACC][mt], a0, a1, a2, a3, b0, b1);
           }
         }
       }
+#pragma unroll
+      for (int q = 1; q < NACC; ++q)
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) acc[0][mt][e] += acc[q][mt][e];
       float scale = 1.f;
       if constexpr (FragFmt<E>::kScaled) scale = *reinterpret_cast<const float*>(brow + BODY);
       const float as = alpha * scale;
@@ -331,7 +342,7 @@ hop_frag_kernel(const unsigned char* __restrict__ vals, const int32_t* __restric
           const int a = 16 * mt + g8 + 8 * h;
           if constexpr (W == 8) {
             const float2 x0v = __half22float2(*reinterpret_cast<const __half2*>(x0s + a * 8 + 2 * t4));
-            const float o0 = x0v.x + as * acc[mt][2 * h], o1 = x0v.y + as * acc[mt][2 * h + 1];
+            const float o0 = x0v.x + as * acc[0][mt][2 * h], o1 = x0v.y + as * acc[0][mt][2 * h + 1];
             if constexpr (OUTP) {
               *reinterpret_cast<__half2*>(reinterpret_cast<__half*>(yv) + gl * plane + (row * NBP + a) * 8 + 2 * t4) =
                   __floats2half2_rn(o0, o1);
@@ -342,7 +353,7 @@ hop_frag_kernel(const unsigned char* __restrict__ vals, const int32_t* __restric
               if (q + 1 < rhs_here) yf[((int64_t)(q + 1) * nrows + row) * NB + a] = o1 * out_scale;
             }
           } else if (t4 == 0) {
-            const float o = __half2float(x0s[a]) + as * acc[mt][2 * h];
+            const float o = __half2float(x0s[a]) + as * acc[0][mt][2 * h];
             if constexpr (OUTP)
               reinterpret_cast<__half*>(yv)[row * NBP + a] = __float2half_rn(o);
             else if (a < NB)
@@ -382,7 +393,7 @@ int launch_hop_frag(const dfm_op* op, const __half* xp, const __half* x0p, void*
     const int64_t row_bytes = geom::hop_row_bytes(nb, FragFmt<E>::kEB, FragFmt<E>::kScaled);
     const int64_t keep_from = std::max<int64_t>(0, ntiles - kFragL2KeepBytes / (g.rpt * row_bytes));
     {
-      ::dfm::KernelTimer timer_(DFM_KERNEL_SPMV16, st);
+      ::dfm::KernelTimer timer_(trans ? DFM_KERNEL_SPMV16_T : DFM_KERNEL_SPMV16, st);
       kernel<<<(unsigned)grid, threads, smem, st>>>(reinterpret_cast<const unsigned char*>(copy), op->mesh->recv,
                                                     op->nrows, xp, x0p, y, rgl, rhs_here, 1.0f, out_scale, g.rpt,
                                                     g.stages, next_sweep_direction(copy), keep_from, op->dev_err);

@@ -404,7 +404,7 @@ int launch_hop(const dfm_op* op, const V* xp, const V* x0p, void* y, int R, floa
     const int64_t grid = std::min<int64_t>(ntiles, (int64_t)nsm * per_sm);
     const int64_t keep_from = std::max<int64_t>(0, ntiles - kHopL2KeepBytes / (rpt * row_bytes));
     {
-      ::dfm::KernelTimer timer_(DFM_KERNEL_SPMV16, st);
+      ::dfm::KernelTimer timer_(trans ? DFM_KERNEL_SPMV16_T : DFM_KERNEL_SPMV16, st);
       kernel<<<(unsigned)grid, 32 * (kHopConsumerWarps + 1), smem, st>>>(
           reinterpret_cast<const unsigned char*>(copy), op->mesh->recv, op->nrows, xp, x0p, y, R, 1.0f,
           out_scale, stages, next_sweep_direction(copy), keep_from, op->dev_err);
@@ -415,9 +415,10 @@ int launch_hop(const dfm_op* op, const V* xp, const V* x0p, void* y, int R, floa
   };
   auto go_nb = [&](auto nbc) -> int {
     constexpr int NBC = decltype(nbc)::value;
-    // FP16 hop vectors on a basis padded to 16 run on the fragment-ordered copy
-    if constexpr (std::is_same<V, __half>::value && geom::frag_basis(NBC))
-      return set_error(DFM_ERR_UNSUPPORTED, "preconditioner hop: this basis uses the tensor-core hop");
+    // FP16 hop vectors on a basis padded to a multiple of 16 wider than 16
+    // always run on the fragment-ordered copy (hop.cu, frag_copy)
+    if constexpr (std::is_same<V, __half>::value && geom::frag_basis(NBC) && NBC > 16)
+      return set_error(DFM_ERR_UNSUPPORTED, "preconditioner hop: this shape uses the tensor-core hop");
     else
       return trans ? go(hop_kernel<NBC, E, V, OUTP, RC, true>) : go(hop_kernel<NBC, E, V, OUTP, RC, false>);
   };

@@ -941,7 +941,7 @@ int solve_impl(const dfm_op* op, const dfm_op* const* combo, int K, const double
   Hop hop;
   const Hop* lp = nullptr;
   if (use_lp) {
-    rc = prepare_lowp(op, opts->precond_precision, c.st, opts->transpose ? 1 : 0);
+    rc = prepare_lowp(op, opts->precond_precision, c.st, opts->transpose ? 1 : 0, batched ? Rg : 1);
     if (rc) return rc;
     hop.op = op;
     lp = &hop;

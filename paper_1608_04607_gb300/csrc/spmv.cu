@@ -632,7 +632,7 @@ int launch(const dfm_op* op, const TX* x, const TX* x0, TX* y, int R, double alp
       const int64_t grid = std::min<int64_t>(ntiles, (int64_t)nsm * per_sm);
       for (int r = 0; r < R; ++r) {
         {
-          ::dfm::KernelTimer timer_(DFM_KERNEL_SPMV_T, st);
+          ::dfm::KernelTimer timer_(sizeof(TX) == 8 ? DFM_KERNEL_SPMV64_T : DFM_KERNEL_SPMV_T, st);
           kernel<<<(unsigned)grid, 32 * (kConsumerWarps + 1), smem, st>>>(
               vals, op->row_stride, recv, nt, tpt, stages, x + r * stride, x0 ? x0 + r * stride : nullptr,
               y + r * stride, (TA)alpha, next_sweep_direction(op->vals), op->dev_err);
@@ -660,7 +660,7 @@ int launch(const dfm_op* op, const TX* x, const TX* x0, TX* y, int R, double alp
     const int64_t total = op->nrows * op->nb * (int64_t)R;
     const int64_t grid = std::min<int64_t>((total + kThreads - 1) / kThreads, (int64_t)nsm * 16);
     {
-      ::dfm::KernelTimer timer_(DFM_KERNEL_SPMV_T, st);
+      ::dfm::KernelTimer timer_(sizeof(TX) == 8 ? DFM_KERNEL_SPMV64_T : DFM_KERNEL_SPMV_T, st);
       spmv_t_kernel<TV, TX, TA><<<(unsigned)grid, kThreads, 0, st>>>(vals, op->row_stride, recv, op->nrows, op->nb,
                                                                      x, x0, y, R, (TA)alpha);
     }

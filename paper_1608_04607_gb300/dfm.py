@@ -329,17 +329,22 @@ class Operator:
         return rho, info
 
     def adjoint(self, rho, gvec, dgvec=None, method=GMRES_IR, tol=1e-8, max_iter=0, restart=0, inner_tol=0.0,
-                poly_degree=0, precond_precision=0):
+                poly_degree=0, precond_precision=0, lam0=None):
         """lambda = (I - B)^{-T} gvec and dJ/dmu for J = sum_r gvec . rho_r (dfm_adjoint).
-        rho: FP64 [R, rows, nb]; gvec/dgvec: FP64 [rows, nb].  Returns (lambda, dJ_dmu [R, n_tets], info)."""
+        rho: FP64 [R, rows, nb]; gvec/dgvec: FP64 [rows, nb]; lam0: initial guess
+        for lambda (e.g. an earlier call's lambda for the same operator and
+        functional).  Returns (lambda, dJ_dmu [R, n_tets], info)."""
         torch = self._torch
         R = _vec(rho, self.n_rows, self.nb, (torch.float64,), "adjoint: rho")
         if _vec(gvec, self.n_rows, self.nb, (torch.float64,), "adjoint: gvec") != 1 or gvec.dim() != 2:
             raise DFMError(DFM_ERR_ARG, "adjoint: gvec must be [rows, nb]")
         _like(dgvec, gvec, "adjoint: dgvec")
-        lam = torch.empty((self.n_rows, self.nb), dtype=torch.float64, device="cuda")
+        _like(lam0, gvec, "adjoint: lam0")
+        lam = (torch.empty((self.n_rows, self.nb), dtype=torch.float64, device="cuda") if lam0 is None
+               else lam0.clone())
         dj = torch.empty((R, self.mesh.n_tets), dtype=torch.float64, device="cuda")
-        o = SolveOpts(method=method, tol=tol, max_iter=max_iter, restart=restart, use_x0=0, inner_tol=inner_tol,
+        o = SolveOpts(method=method, tol=tol, max_iter=max_iter, restart=restart, use_x0=int(lam0 is not None),
+                      inner_tol=inner_tol,
                       transpose=1, poly_degree=poly_degree, batch=0, precond_precision=precond_precision)
         info = SolveInfo()
         _check(_lib.dfm_adjoint(self._h, ctypes.byref(self._p), _ptr(rho), R, _ptr(gvec), _ptr(dgvec), _ptr(lam),
@@ -563,7 +568,8 @@ def gauss_legendre(q: int):
     return x, w
 
 
-KERNEL_ASSEMBLE, KERNEL_SPMV, KERNEL_SPMV_T, KERNEL_DOT, KERNEL_AXPY, KERNEL_SPMV64, KERNEL_CONTRACT, KERNEL_SPMV16 = range(8)
+(KERNEL_ASSEMBLE, KERNEL_SPMV, KERNEL_SPMV_T, KERNEL_DOT, KERNEL_AXPY, KERNEL_SPMV64, KERNEL_CONTRACT, KERNEL_SPMV16,
+ KERNEL_SPMV16_T, KERNEL_SPMV64_T) = range(10)
 
 
 def autotune(mode: int = 1):

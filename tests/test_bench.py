@@ -123,3 +123,23 @@ def test_reference_arm_non_zero_rank_prints_nothing():
     p = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference"], env=env,
                        capture_output=True, text=True, timeout=120)
     assert p.returncode == 0 and p.stdout.strip() == ""
+
+
+def test_headline_kernels_count_each_kernel_with_its_own_operands():
+    """The default workload's kernels: hops with 8 right-hand sides (e4m3
+    copy, FP16 vectors), transposed hops with one, BF16 applications with FP32
+    and FP64 vectors; the roofline goes to the kernel with the largest time."""
+    rows, Np, B = 786_432, 8, 8
+    nb = 45
+    ks = {"hop": (3600, 3600 * 0.9), "hop_t": (3500, 3500 * 0.74), "spmv": (60, 60 * 13.0),
+          "spmv_t": (60, 60 * 2.3), "spmv_f64vec": (2, 120.0), "spmv_f64vec_t": (2, 10.0),
+          "contract": (1, 120.0), "dot": (100, 300.0), "axpy": (100, 200.0)}
+    kern, total, roof = bench.headline_kernels(ks, rows, rows // 4, Np, 10_000_000, 152, PEAKS, "measured", B)
+    assert kern["hop"]["bytes_per_launch"] == rows * (3 * nb * nb + 8) + 3 * nb * 2 * rows * B
+    assert kern["hop_t"]["bytes_per_launch"] == rows * (3 * nb * nb + 8) + 3 * nb * 2 * rows
+    assert kern["spmv"]["bytes_per_launch"] == rows * (3 * nb * nb * 2 + 4) + 3 * nb * 4 * rows * B
+    assert kern["spmv_f64vec_t"]["bytes_per_launch"] == rows * (3 * nb * nb * 2 + 4) + 3 * nb * 8 * rows
+    assert roof["kernel"] == "hop" and roof["unit"] == "GB/s"
+    ach = kern["hop"]["bytes_per_launch"] / 0.9e-3 / 1e9
+    assert roof["achieved"] == pytest.approx(ach, rel=1e-6) and roof["frac"] == pytest.approx(ach / 6000.0, abs=1e-4)
+    assert total["dot"] == 300.0
