@@ -134,6 +134,10 @@ inline LowpView lowp_of(const dfm_op* op, int trans) {
 // two that keeps |v| vscale <= 2^-8).
 int hop_horner(const dfm_op* op, int R, int d, const float* v, float* z, void* vp, void* ha, void* hb, float vscale,
                cudaStream_t st, int trans = 0);
+// tensor-core forward application of a BF16 operator to R >= 4 FP32
+// right-hand sides (spmv_mma.cu)
+bool apply_mma_supported(const dfm_op* op, int R);
+int apply_mma(const dfm_op* op, const float* x, const float* x0, float* y, int R, double alpha, cudaStream_t st);
 // reads and clears op's time-out flag (waits on st): DFM_ERR_TIMEOUT if set
 int read_timeout_flag(const dfm_op* op, cudaStream_t st, const char* who);
 // implemented in quad.cu

@@ -548,6 +548,10 @@ int launch(const dfm_op* op, const TX* x, const TX* x0, TX* y, int R, double alp
   if (!trans) {
     if ((reinterpret_cast<uintptr_t>(x) & 15) || (reinterpret_cast<uintptr_t>(op->vals) & 15))
       return set_error(DFM_ERR_ARG, "dfm_apply: x must be 16-byte aligned");
+    // BF16 blocks with several FP32 right-hand sides: a dense contraction per
+    // row, on tensor cores (spmv_mma.cu)
+    if constexpr (std::is_same<TV, __nv_bfloat16>::value && std::is_same<TX, float>::value)
+      if (K == 1 && !combo_ops && apply_mma_supported(op, R)) return apply_mma(op, x, x0, y, R, alpha, st);
     if (R > kMaxStagedRhs) {  // several passes, each staging up to kMaxStagedRhs right-hand sides
       const int64_t stride = op->nrows * (int64_t)op->nb;
       for (int r0 = 0; r0 < R; r0 += kMaxStagedRhs) {

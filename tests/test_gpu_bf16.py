@@ -120,3 +120,26 @@ def test_bf16_adjoint_matches_oracle_on_the_same_blocks(D, oracle_mod, small):
         gref = oracle_mod.gradient(same, rref, lref.reshape(same.nrows, same.nb), dgref, m.n_tets)
         got = dj[r].cpu().numpy()
         assert np.abs(got - gref).max() <= 2e-5 * np.abs(gref).max()
+
+
+@pytest.mark.parametrize("Np,R", [(8, 4), (8, 9), (8, 17), (4, 8), (3, 16)])
+def test_bf16_apply_many_rhs_on_tensor_cores(D, oracle_mod, small, Np, R):
+    """Four or more FP32 right-hand sides on a BF16 operator run on tensor
+    cores (each coefficient split exactly into three BF16 parts, FP32
+    accumulation): the same 2e-6 of max |y| as the CUDA-core application,
+    with x0 given, aliasing x, or absent; R = 17 spans two launches (16 + 1)."""
+    import torch
+
+    m, mesh = small
+    op = D.Operator(mesh, Np, mu=0.3, precision=D.BF16)
+    ref = _as_oracle(oracle_mod, op, mesh, m.n_tets, Np)
+    rng = np.random.default_rng(R)
+    x = torch.tensor(rng.standard_normal((R, mesh.n_rows, op.nb)), dtype=torch.float32, device="cuda")
+    x0 = torch.tensor(rng.standard_normal((R, mesh.n_rows, op.nb)), dtype=torch.float32, device="cuda")
+    for kind in ("x0", "alias", "none"):
+        xx0 = {"x0": x0, "alias": x, "none": None}[kind]
+        y = op.apply(x, x0=xx0, alpha=-0.7).cpu().numpy()
+        for r in range(R):
+            base = None if xx0 is None else xx0[r].double().cpu().numpy()
+            yr = oracle_mod.apply(ref, x[r].double().cpu().numpy(), x0=base, alpha=-0.7)
+            assert np.abs(y[r] - yr).max() <= 2e-6 * np.abs(yr).max(), (kind, r)
