@@ -804,8 +804,9 @@ def run_reference(args):
 
 def run_apply(args):
     """Operator-application micro-benchmark: K timed y = x0 - B x launches
-    (FP32 vectors) on the workload's assembled operator, for the SpMV roofline
-    and for profiling the kernel in isolation."""
+    (FP32 vectors, --rhs right-hand sides, default 1) on the workload's
+    assembled operator (BF16 blocks for N_p = 8, else FP32), for the
+    application's roofline and for profiling the kernel in isolation."""
     import torch
 
     from paper_1608_04607_gb300 import dfm
@@ -815,9 +816,11 @@ def run_apply(args):
     w = workload(args.workload)
     m = w["mesh"]
     mesh = dfm.Mesh(m.verts, m.tets, refl=w["refl"])
-    op = dfm.Operator(mesh, w["Np"], mu=float(w["mu"][0]), precision=dfm.F32)
+    bf16 = w["Np"] >= 8
+    op = dfm.Operator(mesh, w["Np"], mu=float(w["mu"][0]), precision=dfm.BF16 if bf16 else dfm.F32)
+    R = args.rhs or 1
     g = torch.Generator(device="cuda").manual_seed(0)
-    x = torch.randn((1, mesh.n_rows, op.nb), device="cuda", dtype=torch.float32, generator=g)
+    x = torch.randn((R, mesh.n_rows, op.nb), device="cuda", dtype=torch.float32, generator=g)
     y = torch.empty_like(x)
     for _ in range(args.warmup):
         op.apply(x, x0=x, alpha=-1.0, out=y)
@@ -830,9 +833,9 @@ def run_apply(args):
     n, ms = dfm.kernel_stats(dfm.KERNEL_SPMV)
     dfm.stats_enable(False)
     peaks, src = _peaks()
-    by = spmv_bytes(mesh.n_rows, op.nb, 4, with_x0=True)
+    by = _apply_bytes(mesh.n_rows, op.nb, 2 if bf16 else 4, 4, R)
     ach = by / (ms / n * 1e-3) / 1e9
-    print(json.dumps({"mode": "apply", "workload": args.workload, "launches": n, "ms_per_launch": ms / n,
+    print(json.dumps({"mode": "apply", "workload": args.workload, "rhs": R, "launches": n, "ms_per_launch": ms / n,
                       "bytes_per_launch": by, "achieved_gbs": ach, "peak_gbs": peaks.get("hbm_gbs"),
                       "frac": ach / float(peaks.get("hbm_gbs", HBM_PEAK_FALLBACK)), "peak_source": src}))
 

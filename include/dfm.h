@@ -144,6 +144,18 @@ typedef struct {
                            2|OBC| phi2(mu L_O) replaced by 2|OBC| L_O^k phi2^(k)(mu L_O).  Then
                            B(mu_c + e) = sum_k e^k/k! B^(k): Taylor moments that let right-hand
                            sides with different uniform damping share one set of operators. */
+  const double* c;      /* device FP64 [n_tets] propagation speed per tet, or NULL (all 1) */
+  const double* rho_f;  /* device FP64 [n_tets] fluid density per tet, or NULL (all 1).  With
+                           either given, an interior face between tets of different impedance
+                           z = rho_f c or speed is an interface (Sec. 3.3): a ray crossing it is
+                           transmitted with probability
+                             lambda_t = 4 z_i z_j cos(th_r) cos(th_t) / (z_i cos(th_r) + z_j cos(th_t))^2
+                           (Snell: sin(th_t) = (c_i/c_j) sin(th_r); zero beyond the critical angle),
+                           its receiving momentum scaled by c_i/c_j, and reflected specularly back
+                           into its tet with 1 - lambda_t.  The reflected blocks form a second
+                           part of the operator (up to six blocks per row in all), applied with
+                           the first by dfm_apply and the solvers; preconditioner copies hold
+                           the first part only.  Not with moment > 0 or combined operators. */
 } dfm_params;
 
 typedef struct {
@@ -172,6 +184,12 @@ int dfm_op_info(const dfm_op* op, dfm_op_info_t* info);
 /* Copy the block storage (dfm_op_info_t.bytes bytes, layout above) to dst, a
  * device or host pointer; asynchronous on the stream. */
 int dfm_op_copy_vals(const dfm_op* op, void* dst, int64_t bytes, void* stream);
+/* The reflected part of an operator assembled with heterogeneous media
+ * (dfm_params.c / rho_f): the same layout and size as dfm_op_copy_vals, row
+ * R = 4t + l' holding the blocks reflected at face l' of tet t from the tet's
+ * other faces (slot k = the k-th face of t other than l'); zero blocks where
+ * l' is not an interface.  DFM_ERR_ARG if the operator has no reflected part. */
+int dfm_op_copy_reflected(const dfm_op* op, void* dst, int64_t bytes, void* stream);
 
 /* y = x0 + alpha * B x (trans = 0) or y = x0 + alpha * B^T x (trans = 1) for
  * R right-hand sides; x, y, x0 device [R][rows][nb] of type xtype

@@ -43,6 +43,7 @@ contract_kernel(const PairConst* __restrict__ pairs, int64_t npairs, const doubl
   const int64_t p = (int64_t)blockIdx.x * kCWarps + wid;
   if (p >= npairs) return;  // no block-wide barrier follows
   const PairConst pc = pairs[p];
+  if (pc.kind < 0) return;  // no block for this pair in this part
   const int64_t t = p / 12;
   const int f = (int)((p % 12) / 3);
   const int64_t J = 4 * t + f;
@@ -72,11 +73,12 @@ contract_kernel(const PairConst* __restrict__ pairs, int64_t npairs, const doubl
       const int j = rem - i * q;
       const NodeGeom<float> g = node_geom<float>(S.patch[pi], s_x[i], s_x[j], pc);
       if (!g.valid) continue;
-      const float wd = s_w[i] * s_w[j] * g.jac * 2.f * g.Anab * g.LO * phi2_prime<float>(mu * g.LO);
+      const float wd = s_w[i] * s_w[j] * g.jac * 2.f * g.Anab * g.LO * phi2_prime<float>(mu * g.LO) *
+                       media_weight<float>(pc, g.d0, g.d1, g.d2);
       float Zp[NB], Zq[NB];
       zernike<NP, float>(g.d0, g.d1, Zp);
-      const float qx = g.d0 * pc.R1[0] + g.d1 * pc.R1[1] + g.d2 * pc.R1[2];
-      const float qy = g.d0 * pc.R2[0] + g.d1 * pc.R2[1] + g.d2 * pc.R2[2];
+      const float qx = pc.qscale * (g.d0 * pc.R1[0] + g.d1 * pc.R1[1] + g.d2 * pc.R1[2]);
+      const float qy = pc.qscale * (g.d0 * pc.R2[0] + g.d1 * pc.R2[1] + g.d2 * pc.R2[2]);
       zernike<NP, float>(qx, qy, Zq);
       float sq = 0.f;
 #pragma unroll
@@ -373,15 +375,23 @@ extern "C" int dfm_adjoint(const dfm_op* op, const dfm_params* params, const dou
   double* glw = glx + 64;
   rc = gauss_legendre_device(q, glx, glw, st);
   if (rc) return rc;
-  pair_setup_kernel<<<(unsigned)((npairs + 127) / 128), 128, 0, st>>>(mesh->verts, mesh->tets, mesh->recv, mesh->refl,
-                                                                     mesh->geom, params->mu, params->mu_uniform,
-                                                                     npairs, pairs);
-  DFM_LAUNCHED();
-  DFM_CUDA_CHECK(cudaGetLastError());
   DFM_CUDA_CHECK(cudaMemsetAsync(dJ_dmu, 0, sizeof(double) * R * mesh->nt, st));
-  rc = launch_contract(op->Np, pairs, npairs, glx, glw, q, cos_max, lambda_out, rho, R, op->nrows, mesh->nt, dJ_dmu,
-                       st);
-  if (rc) return rc;
+  // part 0: the blocks received across each exit face; part 1 (heterogeneous
+  // media): the blocks reflected at interfaces; both cross tet t
+  const bool media = params->c || params->rho_f;
+  if (media != (op->rop != nullptr))
+    return set_error(DFM_ERR_ARG, "dfm_adjoint: params->c / rho_f differ from the operator's assembly");
+  for (int part = 0; part < (media ? 2 : 1); ++part) {
+    pair_setup_kernel<<<(unsigned)((npairs + 127) / 128), 128, 0, st>>>(mesh->verts, mesh->tets, mesh->recv,
+                                                                       mesh->refl, mesh->geom, params->mu,
+                                                                       params->mu_uniform, npairs, pairs, params->c,
+                                                                       params->rho_f, part);
+    DFM_LAUNCHED();
+    DFM_CUDA_CHECK(cudaGetLastError());
+    rc = launch_contract(op->Np, pairs, npairs, glx, glw, q, cos_max, lambda_out, rho, R, op->nrows, mesh->nt,
+                         dJ_dmu, st);
+    if (rc) return rc;
+  }
   if (dgvec) {
     explicit_term_kernel<<<(unsigned)((mesh->nt + 127) / 128), 128, 0, st>>>(dgvec, rho, R, op->nb, op->nrows,
                                                                               mesh->nt, dJ_dmu);

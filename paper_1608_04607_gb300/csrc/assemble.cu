@@ -39,6 +39,7 @@
 #include "dfm_internal.cuh"
 #include "node.cuh"
 
+#include <algorithm>
 #include <cstddef>
 #include <type_traits>
 
@@ -131,6 +132,7 @@ assemble_kernel(const PairConst* __restrict__ pairs, int64_t npairs, const doubl
     const int64_t p = (int64_t)blockIdx.x * kWarps + wid;
     if (p >= npairs) return;  // no block-wide barrier follows
     const PairConst pc = pairs[p];
+    if (pc.kind < 0) return;  // no block for this pair in this part
     T acc[TR][TC];
 #pragma unroll
     for (int r = 0; r < TR; ++r)
@@ -169,12 +171,13 @@ assemble_kernel(const PairConst* __restrict__ pairs, int64_t npairs, const doubl
               sk = phi2_deriv<T>(moment, mu * g.LO);
               for (int e = 0; e < moment; ++e) sk *= g.LO;
             }
-            wnode = s_w[i] * s_w[j] * g.jac * T(2) * g.Anab * sk;
+            wnode = s_w[i] * s_w[j] * g.jac * T(2) * g.Anab * sk * media_weight<T>(pc, g.d0, g.d1, g.d2);
           }
           const T d0 = g.d0, d1 = g.d1, d2 = g.d2;
           zernike<NP, T>(d0, d1, Zp);
-          const T qx = d0 * (T)pc.R1[0] + d1 * (T)pc.R1[1] + d2 * (T)pc.R1[2];
-          const T qy = d0 * (T)pc.R2[0] + d1 * (T)pc.R2[1] + d2 * (T)pc.R2[2];
+          // receiving momentum (scaled by c_i / c_j after a refraction)
+          const T qx = (T)pc.qscale * (d0 * (T)pc.R1[0] + d1 * (T)pc.R1[1] + d2 * (T)pc.R1[2]);
+          const T qy = (T)pc.qscale * (d0 * (T)pc.R2[0] + d1 * (T)pc.R2[1] + d2 * (T)pc.R2[2]);
           zernike<NP, T>(qx, qy, Zq);
         } else {
 #pragma unroll
@@ -303,6 +306,43 @@ int check_params(const dfm_mesh* mesh, const dfm_params* p) {
   const double deg = p->max_patch_deg > 0 ? p->max_patch_deg : 60.0;
   if (!(deg >= 10.0 && deg <= 180.0)) return set_error(DFM_ERR_ARG, "dfm_assemble: max_patch_deg must be in [10, 180]");
   if (p->moment < 0 || p->moment > 3) return set_error(DFM_ERR_ARG, "dfm_assemble: moment must be in 0..3");
+  if ((p->c || p->rho_f) && p->moment != 0)
+    return set_error(DFM_ERR_UNSUPPORTED, "dfm_assemble: damping moments are built for uniform media only");
+  return DFM_OK;
+}
+
+// identity row map of a reflection operator: row R receives from R's own tet
+__global__ void iota_kernel(int32_t* __restrict__ r, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    r[i] = (int32_t)i;
+}
+
+// the reflected part of op (heterogeneous media), created on first use; its
+// time-out flag is op's
+int ensure_reflection(dfm_op* op, cudaStream_t st) {
+  if (op->rop) return DFM_OK;
+  dfm_op* r = new dfm_op();
+  r->mesh = op->mesh;
+  r->Np = op->Np;
+  r->nb = op->nb;
+  r->precision = op->precision;
+  r->nrows = op->nrows;
+  r->row_stride = op->row_stride;
+  r->bytes = op->bytes;
+  r->dev_err = op->dev_err;
+  cudaError_t e = cudaMalloc(&r->vals, r->bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&r->own_recv, sizeof(int32_t) * r->nrows);
+  if (e != cudaSuccess) {
+    cudaFree(r->vals);
+    cudaFree(r->own_recv);
+    delete r;
+    return cuda_error(e, "dfm_assemble: reflected part");
+  }
+  iota_kernel<<<(unsigned)std::min<int64_t>((r->nrows + 255) / 256, 4096), 256, 0, st>>>(r->own_recv, r->nrows);
+  DFM_LAUNCHED();
+  DFM_CUDA_CHECK(cudaGetLastError());
+  r->recv = r->own_recv;
+  op->rop = r;
   return DFM_OK;
 }
 
@@ -341,20 +381,41 @@ extern "C" int dfm_assemble_into(const dfm_mesh* mesh, const dfm_params* p, dfm_
   DFM_CUDA_CHECK(cudaMemsetAsync(nodes, 0, sizeof(unsigned long long), st));
   rc = gauss_legendre_device(q, glx, glw, st);
   if (rc) return rc;
+  const bool media = p->c || p->rho_f;
+  if (media) {
+    rc = ensure_reflection(op, st);
+    if (rc) return rc;
+    op->rop->mu_uniform = op->mu_uniform;
+    op->rop->moment = 0;
+  } else if (op->rop) {  // uniform media now: no reflected part
+    op->rop->dev_err = nullptr;
+    dfm_op_destroy(op->rop);
+    op->rop = nullptr;
+  }
   const int bs = 128;
-  pair_setup_kernel<<<(unsigned)((npairs + bs - 1) / bs), bs, 0, st>>>(mesh->verts, mesh->tets, mesh->recv,
-                                                                       mesh->refl, mesh->geom, p->mu,
-                                                                       p->mu_uniform, npairs, pairs);
-  DFM_LAUNCHED();
-  DFM_CUDA_CHECK(cudaGetLastError());
-  if (op->precision == DFM_F32)
-    return dispatch_np<float>(p->Np, pairs, npairs, glx, glw, q, cos_max, (float*)op->vals, op->row_stride, nodes,
+  // part 0: the blocks received across each exit face; part 1 (media): the
+  // blocks reflected at interfaces, into the reflection operator
+  for (int part = 0; part < (media ? 2 : 1); ++part) {
+    dfm_op* dst = part == 0 ? op : op->rop;
+    if (part == 1) DFM_CUDA_CHECK(cudaMemsetAsync(dst->vals, 0, dst->bytes, st));  // non-interface blocks stay 0
+    pair_setup_kernel<<<(unsigned)((npairs + bs - 1) / bs), bs, 0, st>>>(mesh->verts, mesh->tets, mesh->recv,
+                                                                         mesh->refl, mesh->geom, p->mu,
+                                                                         p->mu_uniform, npairs, pairs, p->c,
+                                                                         p->rho_f, part);
+    DFM_LAUNCHED();
+    DFM_CUDA_CHECK(cudaGetLastError());
+    if (op->precision == DFM_F32)
+      rc = dispatch_np<float>(p->Np, pairs, npairs, glx, glw, q, cos_max, (float*)dst->vals, op->row_stride, nodes,
                               p->moment, st);
-  if (op->precision == DFM_BF16)
-    return dispatch_np<float, __nv_bfloat16>(p->Np, pairs, npairs, glx, glw, q, cos_max, (__nv_bfloat16*)op->vals,
-                                             op->row_stride, nodes, p->moment, st);
-  return dispatch_np<double>(p->Np, pairs, npairs, glx, glw, q, cos_max, (double*)op->vals, op->row_stride, nodes,
-                             p->moment, st);
+    else if (op->precision == DFM_BF16)
+      rc = dispatch_np<float, __nv_bfloat16>(p->Np, pairs, npairs, glx, glw, q, cos_max,
+                                             (__nv_bfloat16*)dst->vals, op->row_stride, nodes, p->moment, st);
+    else
+      rc = dispatch_np<double>(p->Np, pairs, npairs, glx, glw, q, cos_max, (double*)dst->vals, op->row_stride,
+                               nodes, p->moment, st);
+    if (rc) return rc;
+  }
+  return DFM_OK;
 }
 
 extern "C" int dfm_assemble(const dfm_mesh* mesh, const dfm_params* p, void* stream, dfm_op** out) {
@@ -398,6 +459,11 @@ extern "C" int dfm_assemble(const dfm_mesh* mesh, const dfm_params* p, void* str
 
 extern "C" void dfm_op_destroy(dfm_op* op) {
   if (!op) return;
+  if (op->rop) {
+    op->rop->dev_err = nullptr;  // shared with op
+    dfm_op_destroy(op->rop);
+  }
+  cudaFree(op->own_recv);
   forget_sweep(op->vals);
   forget_sweep(op->lp_vals);
   forget_sweep(op->lpT_vals);
@@ -426,6 +492,15 @@ extern "C" int dfm_op_copy_vals(const dfm_op* op, void* dst, int64_t bytes, void
   if (!op || !dst) return set_error(DFM_ERR_ARG, "dfm_op_copy_vals: NULL argument");
   if (bytes != op->bytes) return set_error(DFM_ERR_ARG, "dfm_op_copy_vals: bytes must equal the operator size");
   DFM_CUDA_CHECK(cudaMemcpyAsync(dst, op->vals, bytes, cudaMemcpyDefault, as_stream(stream)));
+  return DFM_OK;
+}
+
+extern "C" int dfm_op_copy_reflected(const dfm_op* op, void* dst, int64_t bytes, void* stream) {
+  if (!op || !dst) return set_error(DFM_ERR_ARG, "dfm_op_copy_reflected: NULL argument");
+  if (!op->rop) return set_error(DFM_ERR_ARG, "dfm_op_copy_reflected: the operator has no reflected part");
+  if (bytes != op->rop->bytes)
+    return set_error(DFM_ERR_ARG, "dfm_op_copy_reflected: bytes must equal the operator size");
+  DFM_CUDA_CHECK(cudaMemcpyAsync(dst, op->rop->vals, bytes, cudaMemcpyDefault, as_stream(stream)));
   return DFM_OK;
 }
 

@@ -58,6 +58,13 @@ struct dfm_op {
   double mu_uniform = -1.0;
   int moment = 0;
   int* dev_err = nullptr;  // device flag set by kernels whose bounded waits time out
+  // heterogeneous media (Sec. 3.3): the blocks reflected at interfaces between
+  // different media, an operator of its own whose row R receives from R's own
+  // tet (recv = the identity map); applied after this one.  recv: the row map
+  // of the applications (NULL: mesh->recv)
+  dfm_op* rop = nullptr;
+  const int32_t* recv = nullptr;
+  int32_t* own_recv = nullptr;  // owned identity map of a reflection operator
   // 16-bit copy of the blocks for inexact preconditioner hops (same layout)
   void* lp_vals = nullptr;
   int64_t lp_bytes = 0;

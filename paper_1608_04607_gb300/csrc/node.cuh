@@ -22,19 +22,55 @@ struct PairConst {
   float mu;                   // damping of the tet
   float scale;                // lambda / sqrt(|T_l| |T_l'|)
   int out_row, slot;          // destination of the block
-  float pad[4];
+  // heterogeneous media (Sec. 3.3 transmission law) at the exit face l':
+  // kind 0 = no interface (lambda in scale), 1 = the part transmitted into the
+  // neighbour (weight lambda_t(d), receiving momentum scaled by qscale =
+  // c_i / c_j), 2 = the part reflected back into the tet (weight
+  // 1 - lambda_t(d), received by face l' itself), -1 = no block
+  float ndst[3];              // inward normal of face l' in the source frame
+  float c_ratio;              // c_i / c_j (Snell: sin theta_t = c_ratio sin theta_r)
+  float z_src, z_dst;         // impedances rho_f c of the tet and of the neighbour
+  float qscale;               // factor on the receiving tangential momentum
+  int kind;
 };
-static_assert(sizeof(PairConst) == 144, "PairConst layout");
+static_assert(sizeof(PairConst) == 160, "PairConst layout");
+
+// Acoustic transmission probability across an interface (Sec. 3.3):
+//   lambda_t = 4 z_dst z_src cos_r cos_t / (z_dst cos_r + z_src cos_t)^2,
+// cos_t from Snell's law, zero beyond the critical angle.
+template <typename T>
+__host__ __device__ inline T transmission_prob(T cos_r, T c_ratio, T z_src, T z_dst) {
+  const T s2 = c_ratio * c_ratio * (T(1) - cos_r * cos_r);
+  if (s2 >= T(1)) return T(0);
+  const T cos_t = sqrt(T(1) - s2);
+  const T den = z_dst * cos_r + z_src * cos_t;
+  return T(4) * z_dst * z_src * cos_r * cos_t / (den * den);
+}
+
+// Weight of a ray d (source frame) in the pair's part of the operator.
+template <typename T>
+__device__ __forceinline__ T media_weight(const PairConst& pc, T d0, T d1, T d2) {
+  if (pc.kind <= 0) return T(1);
+  const T cos_r = -(d0 * (T)pc.ndst[0] + d1 * (T)pc.ndst[1] + d2 * (T)pc.ndst[2]);
+  const T lt = transmission_prob<T>(cos_r, (T)pc.c_ratio, (T)pc.z_src, (T)pc.z_dst);
+  return pc.kind == 1 ? lt : T(1) - lt;
+}
 
 __device__ __forceinline__ double dot3(const double* a, const double* b) {
   return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
 }
 
 // One thread per face pair p = 12 t + 3 f + k (k-th destination face l' != f).
+// c_tet, rhof_tet: per-tet speed and fluid density (NULL: 1).  part 0: the
+// blocks received across l' (transmitted, or reflected at the boundary);
+// part 1: the blocks reflected at an interface between different media, kind
+// -1 where there is none.
 __global__ void pair_setup_kernel(const double* __restrict__ V, const int32_t* __restrict__ tets,
                                   const int32_t* __restrict__ recv, const double* __restrict__ refl,
                                   const FaceGeom* __restrict__ geom, const double* __restrict__ mu_tet,
-                                  double mu_uniform, int64_t npairs, PairConst* __restrict__ out) {
+                                  double mu_uniform, int64_t npairs, PairConst* __restrict__ out,
+                                  const double* __restrict__ c_tet = nullptr,
+                                  const double* __restrict__ rhof_tet = nullptr, int part = 0) {
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= npairs) return;
   const int64_t t = p / 12;
@@ -77,7 +113,15 @@ __global__ void pair_setup_kernel(const double* __restrict__ V, const int32_t* _
   mvec(A, B, C, pc.mA);
   mvec(B, C, A, pc.mB);
   mvec(C, A, B, pc.mC);
-  const int32_t R = recv[4 * t + fp];
+  const int32_t R0 = recv[4 * t + fp];
+  const bool boundary = (R0 == 4 * t + fp);
+  // media of the tet and of the neighbour across l'
+  const int64_t ti = R0 / 4;
+  const double cj = c_tet ? c_tet[t] : 1.0, ci = c_tet ? c_tet[ti] : 1.0;
+  const double zj = cj * (rhof_tet ? rhof_tet[t] : 1.0), zi = ci * (rhof_tet ? rhof_tet[ti] : 1.0);
+  const bool interface = !boundary && (ci != cj || zi != zj);
+  // part 1 blocks are received by face l' of the tet itself
+  const int32_t R = part == 1 ? (int32_t)(4 * t + fp) : R0;
   const FaceGeom gr = geom[R];
   pc.R1[0] = (float)dot3(gr.e1, g.e1);
   pc.R1[1] = (float)dot3(gr.e1, g.e2);
@@ -93,11 +137,19 @@ __global__ void pair_setup_kernel(const double* __restrict__ V, const int32_t* _
   }
   pc.area_src = (float)g.area;
   pc.mu = (float)(mu_tet ? mu_tet[t] : mu_uniform);
-  const double lam = (R == 4 * t + fp) ? refl[R] : 1.0;
+  const double lam = boundary ? refl[R] : 1.0;
   pc.scale = (float)(lam / sqrt(g.area * geom[4 * t + fp].area));
   pc.out_row = R;
   pc.slot = f - (f > fp ? 1 : 0);
-  pc.pad[0] = pc.pad[1] = pc.pad[2] = pc.pad[3] = 0.f;
+  const FaceGeom gd = geom[4 * t + fp];
+  pc.ndst[0] = (float)dot3(gd.n, g.e1);
+  pc.ndst[1] = (float)dot3(gd.n, g.e2);
+  pc.ndst[2] = (float)dot3(gd.n, g.n);
+  pc.c_ratio = (float)(ci / cj);
+  pc.z_src = (float)zj;
+  pc.z_dst = (float)zi;
+  pc.qscale = (part == 0 && interface) ? (float)(ci / cj) : 1.f;
+  pc.kind = part == 0 ? (interface ? 1 : 0) : (interface ? 2 : -1);
   out[p] = pc;
 }
 

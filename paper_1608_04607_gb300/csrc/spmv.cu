@@ -541,7 +541,7 @@ template <typename TV, typename TX, typename TA>
 int launch(const dfm_op* op, const TX* x, const TX* x0, TX* y, int R, double alpha, int trans, cudaStream_t st,
            const dfm_op* const* combo_ops = nullptr, int K = 1, const double* coef = nullptr) {
   const TV* vals = reinterpret_cast<const TV*>(op->vals);
-  const int32_t* recv = op->mesh->recv;
+  const int32_t* recv = op->recv ? op->recv : op->mesh->recv;
   int dev = 0, nsm = 0;
   DFM_CUDA_CHECK(cudaGetDevice(&dev));
   DFM_CUDA_CHECK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -676,8 +676,20 @@ int launch(const dfm_op* op, const TX* x, const TX* x0, TX* y, int R, double alp
 
 }  // namespace
 
+int apply_one(const dfm_op* op, const void* x, const void* x0, void* y, int R, double alpha, int trans, int xtype,
+              cudaStream_t st);
+
+// y = x0 + alpha (B x), B with its reflected part (heterogeneous media) if any:
+// the first part with x0, then the reflected part accumulated onto y
 int apply_impl(const dfm_op* op, const void* x, const void* x0, void* y, int R, double alpha, int trans, int xtype,
                cudaStream_t st) {
+  int rc = apply_one(op, x, x0, y, R, alpha, trans, xtype, st);
+  if (rc || !op->rop) return rc;
+  return apply_one(op->rop, x, y, y, R, alpha, trans, xtype, st);
+}
+
+int apply_one(const dfm_op* op, const void* x, const void* x0, void* y, int R, double alpha, int trans, int xtype,
+              cudaStream_t st) {
   if (!op || !x || !y || R < 1) return set_error(DFM_ERR_ARG, "dfm_apply: NULL operator/vector or R < 1");
   if (x == y) return set_error(DFM_ERR_ARG, "dfm_apply: y must not alias x");
   if (xtype == DFM_F64) {
@@ -708,6 +720,8 @@ int apply_combo_impl(const dfm_op* const* ops, int K, const double* coef, const 
   for (int k = 0; k < K; ++k) {
     if (!ops[k] || ops[k]->mesh != ops[0]->mesh || ops[k]->Np != ops[0]->Np || ops[k]->precision != DFM_F32)
       return set_error(DFM_ERR_ARG, "dfm_apply_combo: operators must be FP32 and share mesh and Np");
+    if (ops[k]->rop)
+      return set_error(DFM_ERR_UNSUPPORTED, "dfm_apply_combo: operators with a reflected part are not combined");
   }
   if (xtype == DFM_F64)
     return launch<float, double, double>(ops[0], (const double*)x, (const double*)x0, (double*)y, R, alpha, 0, st, ops,

@@ -273,7 +273,8 @@ int launch_nb(const dfm_op* op, const float* x, const float* x0, float* y, int R
   {
     ::dfm::KernelTimer timer_(DFM_KERNEL_SPMV, st);
     kernel<<<(unsigned)grid, threads, smem, st>>>(reinterpret_cast<const __nv_bfloat16*>(op->vals), op->row_stride,
-                                                  op->mesh->recv, op->nrows, x, x0, y, R, alpha, g.rpt, g.stages,
+                                                  op->recv ? op->recv : op->mesh->recv, op->nrows, x, x0, y, R,
+                                                  alpha, g.rpt, g.stages,
                                                   next_sweep_direction(op->vals), keep_from, op->dev_err);
   }
   DFM_LAUNCHED();

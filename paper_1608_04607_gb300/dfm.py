@@ -46,7 +46,7 @@ class MeshInfo(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("Np", ctypes.c_int), ("mu", ctypes.c_void_p), ("mu_uniform", ctypes.c_double),
                 ("quad_order", ctypes.c_int), ("max_patch_deg", ctypes.c_double), ("precision", ctypes.c_int),
-                ("moment", ctypes.c_int)]
+                ("moment", ctypes.c_int), ("c", ctypes.c_void_p), ("rho_f", ctypes.c_void_p)]
 
 
 class OpInfo(ctypes.Structure):
@@ -81,6 +81,7 @@ SIGNATURES = {
     "dfm_op_destroy": (None, [_vp]),
     "dfm_op_info": (_i, [_vp, ctypes.POINTER(OpInfo)]),
     "dfm_op_copy_vals": (_i, [_vp, _vp, _i64, _vp]),
+    "dfm_op_copy_reflected": (_i, [_vp, _vp, _i64, _vp]),
     "dfm_apply": (_i, [_vp, _vp, _vp, _vp, _i, _d, _i, _i, _vp]),
     "dfm_source": (_i, [_vp, _i, _vp, _i, _vp, _vp]),
     "dfm_source_directed": (_i, [_vp, _i, _vp, _vp, _i, _i, _vp, _vp]),
@@ -220,12 +221,24 @@ class Mesh:
 class Operator:
     """The assembled operator B (dfm_assemble)."""
 
-    def __init__(self, mesh: Mesh, Np: int, mu=0.0, precision=F32, quad_order=0, max_patch_deg=0.0, moment=0):
+    def __init__(self, mesh: Mesh, Np: int, mu=0.0, precision=F32, quad_order=0, max_patch_deg=0.0, moment=0,
+                 c=None, rho_f=None):
+        """c, rho_f: per-tet propagation speed and fluid density (heterogeneous
+        media, Sec. 3.3), tensors or arrays of n_tets values, or None (1)."""
         import torch
 
         self.mesh = mesh
         self._keep = []
         self.moment = moment
+        self._media = []
+        for v, what in ((c, "c"), (rho_f, "rho_f")):
+            if v is None:
+                self._media.append(None)
+                continue
+            t = torch.as_tensor(v, dtype=torch.float64, device="cuda").contiguous().reshape(-1)
+            if t.numel() != mesh.n_tets:
+                raise DFMError(DFM_ERR_ARG, f"{what}: expected {mesh.n_tets} per-tet values")
+            self._media.append(t)
         p = self._params(Np, mu, precision, quad_order, max_patch_deg)
         self._p = p
         h = ctypes.c_void_p()
@@ -260,6 +273,9 @@ class Operator:
         p.max_patch_deg = max_patch_deg
         p.precision = precision
         p.moment = getattr(self, "moment", 0)
+        media = getattr(self, "_media", [None, None])
+        p.c = media[0].data_ptr() if media[0] is not None else None
+        p.rho_f = media[1].data_ptr() if media[1] is not None else None
         return p
 
     def reassemble(self, mu, quad_order=0, max_patch_deg=0.0):
@@ -282,6 +298,16 @@ class Operator:
         dt = {F64: torch.float64, F32: torch.float32, BF16: torch.bfloat16}[self.precision]
         buf = torch.empty(self.n_rows * self.row_stride, dtype=dt, device="cuda")
         _check(_lib.dfm_op_copy_vals(self._h, _ptr(buf), self.bytes, _stream()), "dfm_op_copy_vals")
+        nb = self.nb
+        return buf.view(self.n_rows, self.row_stride)[:, :3 * nb * nb].reshape(self.n_rows, 3, nb, nb)
+
+    def blocks_reflected(self):
+        """The reflected part (heterogeneous media) as [rows, 3, nb, nb]: row
+        R = 4t + l' holds the blocks reflected at face l' from tet t's other faces."""
+        torch = self._torch
+        dt = {F64: torch.float64, F32: torch.float32, BF16: torch.bfloat16}[self.precision]
+        buf = torch.empty(self.n_rows * self.row_stride, dtype=dt, device="cuda")
+        _check(_lib.dfm_op_copy_reflected(self._h, _ptr(buf), self.bytes, _stream()), "dfm_op_copy_reflected")
         nb = self.nb
         return buf.view(self.n_rows, self.row_stride)[:, :3 * nb * nb].reshape(self.n_rows, 3, nb, nb)
 
