@@ -37,14 +37,32 @@ static_assert(sizeof(PairConst) == 160, "PairConst layout");
 
 // Acoustic transmission probability across an interface (Sec. 3.3):
 //   lambda_t = 4 z_dst z_src cos_r cos_t / (z_dst cos_r + z_src cos_t)^2,
-// cos_t from Snell's law, zero beyond the critical angle.
+// cos_t from Snell's law, zero beyond the critical angle.  cos_t^2 =
+// 1 - c^2 (1 - cos_r^2) is formed as (1 - c^2) + c^2 cos_r^2: the direct form
+// cancels for grazing rays in FP32 (cos_r = 1e-3 lost 3% of cos_t, and every
+// cos_r below 2.4e-4 gave total reflection at equal speeds).
 template <typename T>
 __host__ __device__ inline T transmission_prob(T cos_r, T c_ratio, T z_src, T z_dst) {
-  const T s2 = c_ratio * c_ratio * (T(1) - cos_r * cos_r);
-  if (s2 >= T(1)) return T(0);
-  const T cos_t = sqrt(T(1) - s2);
+  const T c2 = c_ratio * c_ratio;
+  const T ct2 = (T(1) - c2) + c2 * cos_r * cos_r;
+  if (ct2 <= T(0)) return T(0);
+  const T cos_t = sqrt(ct2);
   const T den = z_dst * cos_r + z_src * cos_t;
   return T(4) * z_dst * z_src * cos_r * cos_t / (den * den);
+}
+
+// The reflected share 1 - lambda_t, formed as ((a - b) / (a + b))^2 with
+// a = z_dst cos_r, b = z_src cos_t (the same quantity: (a + b)^2 - (a - b)^2
+// = 4ab) so that nearly matched impedances do not cancel in FP32; 1 beyond
+// the critical angle.
+template <typename T>
+__host__ __device__ inline T reflection_prob(T cos_r, T c_ratio, T z_src, T z_dst) {
+  const T c2 = c_ratio * c_ratio;
+  const T ct2 = (T(1) - c2) + c2 * cos_r * cos_r;
+  if (ct2 <= T(0)) return T(1);
+  const T a = z_dst * cos_r, b = z_src * sqrt(ct2);
+  const T r = (a - b) / (a + b);
+  return r * r;
 }
 
 // Weight of a ray d (source frame) in the pair's part of the operator.
@@ -52,8 +70,8 @@ template <typename T>
 __device__ __forceinline__ T media_weight(const PairConst& pc, T d0, T d1, T d2) {
   if (pc.kind <= 0) return T(1);
   const T cos_r = -(d0 * (T)pc.ndst[0] + d1 * (T)pc.ndst[1] + d2 * (T)pc.ndst[2]);
-  const T lt = transmission_prob<T>(cos_r, (T)pc.c_ratio, (T)pc.z_src, (T)pc.z_dst);
-  return pc.kind == 1 ? lt : T(1) - lt;
+  return pc.kind == 1 ? transmission_prob<T>(cos_r, (T)pc.c_ratio, (T)pc.z_src, (T)pc.z_dst)
+                      : reflection_prob<T>(cos_r, (T)pc.c_ratio, (T)pc.z_src, (T)pc.z_dst);
 }
 
 __device__ __forceinline__ double dot3(const double* a, const double* b) {
