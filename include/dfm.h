@@ -235,6 +235,32 @@ int dfm_source(const dfm_mesh* mesh, int Np, const int64_t* rows_host, int n_src
 int dfm_source_directed(const dfm_mesh* mesh, int Np, const int64_t* rows_host, const double* dirs_host, int n_src,
                         int combine, double* rho0, void* stream);
 
+/* Galerkin coefficients of point sources in uniform media (Sec. 4.2,
+ * Eq. SourceRho): rays leave r0 in every direction and enter the next tet
+ * through each face F of the tet holding r0 that does not contain r0; the row
+ * across F (on the boundary: F's own row, weighted by its reflection
+ * coefficient, the reflected direction keeping the tangential components)
+ * receives
+ *   rho0[rec][(n,m)] = N_nm / sqrt|F| Int_F strength cos(theta) exp(-mu R) / R^2 Z_n^m(p(u)) ds,
+ * u = unit(s - r0), R = |s - r0|, theta the angle between u and F's normal,
+ * p(u) the tangential part of u in the receiving face's frame, mu the damping
+ * of the tet holding r0 and N_nm as in dfm_source_directed (strength =
+ * rho_f omega^2 / (16 pi^2 c) for the paper's acoustic source).  A source on
+ * a face, an edge or a vertex (barycentric coordinates within 1e-12 of 0)
+ * sends from every tet whose closure holds it, through the faces that do not
+ * contain it.  Each face integral runs in FP64: nq = 0 (default) the split
+ * polar rule of dfm_interior_density with 24 points per direction, nq < 0 that
+ * rule with |nq| points (accurate for sources close to a face), nq > 0 the
+ * collapsed tensor Gauss-Legendre rule of order nq on the flat triangle.
+ *   r0_host: HOST FP64 [n_src][3] positions.  mu: device FP64 [n_tets] or NULL
+ *   for mu_uniform.  rho0: device FP64 [n_src][rows][nb], fully overwritten.
+ * Waits on the stream (the tets holding each source are found on the device
+ * and counted on the host).  Errors: DFM_ERR_ARG (NULL, Np outside 0..8, |nq|
+ * outside 2..64, negative mu_uniform, non-finite position or strength; a
+ * source outside the mesh, whose rows then stay zero). */
+int dfm_point_source(const dfm_mesh* mesh, int Np, const double* r0_host, int n_src, const double* mu,
+                     double mu_uniform, double strength, int nq, double* rho0, void* stream);
+
 typedef struct {
   int method;        /* DFM_SOLVE_* */
   double tol;        /* stop when ||rho0 - (I - B) x|| <= tol ||rho0|| (FP64 residual; Neumann: relative increment) */

@@ -85,6 +85,7 @@ SIGNATURES = {
     "dfm_apply": (_i, [_vp, _vp, _vp, _vp, _i, _d, _i, _i, _vp]),
     "dfm_source": (_i, [_vp, _i, _vp, _i, _vp, _vp]),
     "dfm_source_directed": (_i, [_vp, _i, _vp, _vp, _i, _i, _vp, _vp]),
+    "dfm_point_source": (_i, [_vp, _i, _vp, _i, _vp, _d, _d, _i, _vp, _vp]),
     "dfm_apply_combo": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _i, _d, _i, _vp]),
     "dfm_precond_apply": (_i, [_vp, _i, _i, _i, _vp, _vp, _i, _vp]),
     "dfm_solve_combo": (_i, [_vp, _i, _vp, _vp, _i, _vp, ctypes.POINTER(SolveOpts), _vp, ctypes.POINTER(SolveInfo)]),
@@ -416,6 +417,29 @@ def source_directed(mesh: Mesh, Np: int, rows, dirs=None, combine=False):
     out = torch.empty(shape, dtype=torch.float64, device="cuda")
     _check(load().dfm_source_directed(mesh.handle, Np, rows.ctypes.data_as(ctypes.c_void_p), dp, rows.size,
                                       int(bool(combine)), _ptr(out), _stream()), "dfm_source_directed")
+    return out
+
+
+def point_source(mesh: Mesh, Np: int, r0, mu=0.0, strength=1.0, nq=0):
+    """Point sources at r0 [n_src, 3] (or one [3]) in uniform media
+    (dfm_point_source, Eq. SourceRho): FP64 [n_src, rows, nb].  mu: a float or
+    a per-tet tensor; nq = 0: the split polar rule with 24 points per
+    direction, nq < 0: that rule with |nq| points, nq > 0: the collapsed Gauss
+    rule of that order."""
+    import torch
+
+    r0 = np.ascontiguousarray(np.asarray(r0, dtype=np.float64).reshape(-1, 3))
+    out = torch.empty((r0.shape[0], mesh.n_rows, nbasis(Np)), dtype=torch.float64, device="cuda")
+    keep = None
+    if isinstance(mu, torch.Tensor):
+        keep = mu.to(device="cuda", dtype=torch.float64).contiguous()
+        if keep.numel() != mesh.n_tets:
+            raise DFMError(DFM_ERR_ARG, "point_source: mu must hold one value per tet")
+        mup, muu = _ptr(keep), 0.0
+    else:
+        mup, muu = None, float(mu)
+    _check(load().dfm_point_source(mesh.handle, Np, r0.ctypes.data_as(ctypes.c_void_p), r0.shape[0], mup, muu,
+                                   float(strength), int(nq), _ptr(out), _stream()), "dfm_point_source")
     return out
 
 

@@ -43,6 +43,7 @@ def test_null_handles_are_rejected_on_the_host():
     calls = {
         "dfm_source": lambda: L.dfm_source(None, 2, one, 1, None, None),
         "dfm_source_directed": lambda: L.dfm_source_directed(None, 2, one, None, 1, 0, None, None),
+        "dfm_point_source": lambda: L.dfm_point_source(None, 2, one, 1, None, 0.0, 1.0, 0, None, None),
         "dfm_tet_density": lambda: L.dfm_tet_density(None, 2, None, None, 1, None, None),
         "dfm_interior_density": lambda: L.dfm_interior_density(None, 2, None, 0.0, one, None, 1, 0, None, None,
                                                                None),
