@@ -345,6 +345,23 @@ int dfm_solve_damped(const dfm_op* const* moments, int K, const double* mu_rhs_h
 int dfm_precond_apply(const dfm_op* op, int precision, int degree, int transpose, const float* x, float* z, int R,
                       void* stream);
 
+/* CUDA graphs of the preconditioner's Horner chains (process-wide switch,
+ * default on).  A chain of degree d >= 4 runs the pack of x, d - 1 hops on
+ * the low-precision copy, the last into z; the d - 3 hops in between touch
+ * only the chain's scratch, so per operator, copy, right-hand-side count,
+ * degree and scratch buffers they are the same launches every time.  The
+ * first chain of such a shape runs eagerly (the autotuner's timing happens
+ * then), the second is captured into a graph (stream capture, relaxed mode)
+ * and later ones replay it as one launch; a capture that fails leaves that
+ * shape to eager launches.  Results are bit-identical with graphs on or off.
+ * Graphs are kept per operator (at most 16 shapes) and freed with it.
+ * mode 1: on, 0: off, -1: query.  Returns the state after the call (0 or 1),
+ * or DFM_ERR_ARG for another mode. */
+int dfm_hop_graphs(int mode);
+/* Hop-chain graph replays so far in this process (each counts its d - 3 hops
+ * in dfm_launch_count). */
+long long dfm_hop_graph_replays(void);
+
 /* Interior density functional (Sec. 4.1, Eq. IntDens, c = 1): for each listed
  * tet e, the coefficients g_e of
  *   rho_T(r_e) = sum_{l, nm} rho_(e,l,nm) g_e[l][nm],

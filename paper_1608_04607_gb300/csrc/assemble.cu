@@ -464,6 +464,7 @@ extern "C" void dfm_op_destroy(dfm_op* op) {
     dfm_op_destroy(op->rop);
   }
   cudaFree(op->own_recv);
+  destroy_hop_graphs(op);
   forget_sweep(op->vals);
   forget_sweep(op->lp_vals);
   forget_sweep(op->lpT_vals);

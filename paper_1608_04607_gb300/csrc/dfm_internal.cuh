@@ -78,6 +78,9 @@ struct dfm_op {
   int lpT_precision = 0;
   bool lpT_valid = false;
   bool lpT_frag = false;
+  // CUDA graphs of the preconditioner's hop chains, keyed by their shape and
+  // buffers (hop.cu); destroyed with the operator
+  void* hop_graphs = nullptr;
   // assembly scratch (per-pair constants, Gauss table), grown on demand
   void* work = nullptr;
   int64_t work_bytes = 0;
@@ -89,15 +92,21 @@ struct dfm_op {
 namespace dfm {
 // launch accounting (stats.cu): every kernel launch site calls count_launch();
 // timed sites wrap the launch in a KernelTimer (event pair when enabled).
+// Under stream capture (set_capturing) neither counts nor times: a replayed
+// graph is counted with count_launches and timed as one span of `weight`
+// launches.
 void count_launch();
+void count_launches(long long n);
+void set_capturing(bool on);
 class KernelTimer {
  public:
-  KernelTimer(int kernel, cudaStream_t st);
+  KernelTimer(int kernel, cudaStream_t st, int weight = 1);
   ~KernelTimer();
  private:
   int kernel_;
   cudaStream_t st_;
   int e0_;
+  int weight_;
 };
 #define DFM_LAUNCHED() ::dfm::count_launch()
 
@@ -141,6 +150,8 @@ inline LowpView lowp_of(const dfm_op* op, int trans) {
 // two that keeps |v| vscale <= 2^-8).
 int hop_horner(const dfm_op* op, int R, int d, const float* v, float* z, void* vp, void* ha, void* hb, float vscale,
                cudaStream_t st, int trans = 0);
+// frees the operator's cached hop-chain graphs (hop.cu)
+void destroy_hop_graphs(dfm_op* op);
 // tensor-core forward application of a BF16 operator to R >= 4 FP32
 // right-hand sides (spmv_mma.cu)
 bool apply_mma_supported(const dfm_op* op, int R);

@@ -37,6 +37,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <type_traits>
@@ -392,53 +393,134 @@ int hop_apply_frag(const dfm_op* op, const __half* xp, const __half* x0p, void* 
   return DFM_OK;
 }
 
-int horner_frag(const dfm_op* op, int R, int d, const float* v, float* z, void* vp_, void* ha_, void* hb_,
-                float vscale, int trans, cudaStream_t st) {
-  __half* vp = static_cast<__half*>(vp_);
-  __half* h[2] = {static_cast<__half*>(ha_), static_cast<__half*>(hb_)};
+// CUDA graphs of the hop chains.  A Horner chain is a pack of v, d - 1 hops
+// and nothing else; the hops between the first and the last read and write
+// only the chain's fixed scratch (vp, ha, hb), so for a given operator copy,
+// right-hand-side count, degree and scratch they are the same launches every
+// time.  The first chain of a shape runs eagerly (the autotuner picks its
+// geometries then), the second is captured into a graph, later ones replay
+// it: one launch instead of d - 3.  The pack (reading v) and the last hop
+// (writing z) stay outside the graph.
+struct HopGraph {
+  const void* copy;
+  int prec;
+  bool frag;
+  int trans, R, d;
+  const void *vp, *ha, *hb;
+  float vscale;
+  int state;  // 0: seen once, 1: captured, 2: capture failed (eager)
+  cudaGraphExec_t exec;
+  long long nodes;
+};
+struct HopGraphs {
+  std::vector<HopGraph> g;
+  cudaStream_t cap = nullptr;  // private stream the chains are captured on
+};
+constexpr size_t kMaxHopGraphs = 16;
+std::atomic<int> g_hop_graphs{1};
+std::atomic<long long> g_hop_graph_replays{0};
+
+int chain(const dfm_op* op, int R, int d, const float* v, float* z, void* vp, void* ha, void* hb, float vscale,
+          int trans, cudaStream_t st) {
+  const LowpView cp = lowp_of(op, trans);
+  const bool bf16 = cp.precision == DFM_BF16;  // FP32 hop vectors, unscaled
+  const float vs = bf16 ? 1.0f : vscale;
   const int nb = op->nb, nbp = hop_nbp(nb);
-  if (R < kFragGroupMin) {
-    const int64_t rows = (int64_t)R * op->nrows;
-    hop_pack_kernel<__half><<<grid_for_elems(rows * nbp), 256, 0, st>>>(v, vp, rows, nb, nbp, vscale);
-  } else {
-    const int G = (R + 7) / 8;
-    frag_pack_kernel<<<grid_for_elems((int64_t)G * op->nrows * nbp), 256, 0, st>>>(v, vp, op->nrows, nb, nbp, R, G,
-                                                                                  vscale);
-  }
-  DFM_LAUNCHED();
-  DFM_CUDA_CHECK(cudaGetLastError());
-  const __half* src = vp;
-  for (int k = 1; k < d; ++k) {
-    const bool last = (k == d - 1);
-    void* dst = last ? static_cast<void*>(z) : static_cast<void*>(h[k & 1]);
-    const int rc = hop_apply_frag(op, src, vp, dst, R, !last, 1.0f / vscale, trans, st);
-    if (rc) return rc;
-    src = h[k & 1];
-  }
-  return DFM_OK;
-}
-
-template <typename V>
-int horner_t(const dfm_op* op, int R, int d, const float* v, float* z, void* vp_, void* ha_, void* hb_, float vscale,
-             int trans, cudaStream_t st) {
-  V* vp = static_cast<V*>(vp_);
-  V* h[2] = {static_cast<V*>(ha_), static_cast<V*>(hb_)};
   const int64_t rows = (int64_t)R * op->nrows;
-  hop_pack_kernel<V><<<grid_for_elems(rows * hop_nbp(op->nb)), 256, 0, st>>>(v, vp, rows, op->nb, hop_nbp(op->nb),
-                                                                           vscale);
+  if (bf16) {
+    hop_pack_kernel<float><<<grid_for_elems(rows * nbp), 256, 0, st>>>(v, static_cast<float*>(vp), rows, nb, nbp, 1.0f);
+  } else if (cp.frag && R >= kFragGroupMin) {
+    const int G = (R + 7) / 8;
+    frag_pack_kernel<<<grid_for_elems((int64_t)G * op->nrows * nbp), 256, 0, st>>>(v, static_cast<__half*>(vp),
+                                                                                  op->nrows, nb, nbp, R, G, vs);
+  } else {
+    hop_pack_kernel<__half><<<grid_for_elems(rows * nbp), 256, 0, st>>>(v, static_cast<__half*>(vp), rows, nb, nbp,
+                                                                       vs);
+  }
   DFM_LAUNCHED();
   DFM_CUDA_CHECK(cudaGetLastError());
-  const V* src = vp;
-  for (int k = 1; k < d; ++k) {
-    const bool last = (k == d - 1);
-    void* dst = last ? static_cast<void*>(z) : static_cast<void*>(h[k & 1]);
-    const int rc = hop_apply_t<V>(op, src, vp, dst, R, !last, 1.0f / vscale, trans, st);
-    if (rc) return rc;
-    src = h[k & 1];
+  // one hop: dst = vp + B~ src (the last one unpadded FP32 into z)
+  auto hop = [&](const void* src, void* dst, bool last, cudaStream_t s) -> int {
+    if (bf16)
+      return hop_apply_t<float>(op, static_cast<const float*>(src), static_cast<const float*>(vp), dst, R, !last,
+                                1.0f, trans, s);
+    if (cp.frag)
+      return hop_apply_frag(op, static_cast<const __half*>(src), static_cast<const __half*>(vp), dst, R, !last,
+                            1.0f / vs, trans, s);
+    return hop_apply_t<__half>(op, static_cast<const __half*>(src), static_cast<const __half*>(vp), dst, R, !last,
+                               1.0f / vs, trans, s);
+  };
+  void* h[2] = {ha, hb};
+  // hops 1 .. d - 2 into the scratch
+  auto middle = [&](cudaStream_t s) -> int {
+    const void* src = vp;
+    for (int k = 1; k <= d - 2; ++k) {
+      const int rc = hop(src, h[k & 1], false, s);
+      if (rc) return rc;
+      src = h[k & 1];
+    }
+    return DFM_OK;
+  };
+  int rc = DFM_OK;
+  bool issued = false;  // the middle hops are on the stream
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  DFM_CUDA_CHECK(cudaStreamIsCapturing(st, &cap));
+  if (d - 2 >= 2 && g_hop_graphs.load() && cap == cudaStreamCaptureStatusNone) {
+    dfm_op* mop = const_cast<dfm_op*>(op);
+    if (!mop->hop_graphs) mop->hop_graphs = new HopGraphs();
+    std::vector<HopGraph>& list = static_cast<HopGraphs*>(mop->hop_graphs)->g;
+    HopGraph* ent = nullptr;
+    for (HopGraph& e : list)
+      if (e.copy == cp.vals && e.prec == cp.precision && e.frag == cp.frag && e.trans == trans && e.R == R &&
+          e.d == d && e.vp == vp && e.ha == ha && e.hb == hb && e.vscale == vs) {
+        ent = &e;
+        break;
+      }
+    if (!ent) {  // first use: eager (the autotuner decides here)
+      if (list.size() >= kMaxHopGraphs) {
+        if (list.front().exec) cudaGraphExecDestroy(list.front().exec);
+        list.erase(list.begin());
+      }
+      list.push_back(HopGraph{cp.vals, cp.precision, cp.frag, trans, R, d, vp, ha, hb, vs, 0, nullptr, 0});
+      rc = middle(st);
+      issued = true;
+    } else if (ent->state == 0) {
+      // second use: capture on the operator's private stream (nothing runs
+      // there; the legacy default stream cannot be captured), replay below
+      // on the caller's stream
+      ent->state = 2;
+      HopGraphs* gs = static_cast<HopGraphs*>(mop->hop_graphs);
+      if (!gs->cap && cudaStreamCreateWithFlags(&gs->cap, cudaStreamNonBlocking) != cudaSuccess) gs->cap = nullptr;
+      if (gs->cap && cudaStreamBeginCapture(gs->cap, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
+        set_capturing(true);
+        const int crc = middle(gs->cap);
+        set_capturing(false);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ee = cudaStreamEndCapture(gs->cap, &graph);
+        size_t n = 0;
+        if (crc == DFM_OK && ee == cudaSuccess && graph && cudaGraphGetNodes(graph, nullptr, &n) == cudaSuccess &&
+            n > 0 && cudaGraphInstantiate(&ent->exec, graph, 0) == cudaSuccess) {
+          ent->state = 1;
+          ent->nodes = (long long)n;
+        }
+        if (graph) cudaGraphDestroy(graph);
+      }
+      (void)cudaGetLastError();  // a failed capture leaves this chain to eager launches
+    }
+    if (!issued && ent && ent->state == 1) {
+      {
+        ::dfm::KernelTimer timer_(trans ? DFM_KERNEL_SPMV16_T : DFM_KERNEL_SPMV16, st, (int)ent->nodes);
+        DFM_CUDA_CHECK(cudaGraphLaunch(ent->exec, st));
+      }
+      count_launches(ent->nodes);
+      g_hop_graph_replays.fetch_add(1);
+      issued = true;
+    }
   }
-  return DFM_OK;
+  if (!issued) rc = middle(st);
+  if (rc) return rc;
+  return hop(d >= 3 ? h[(d - 2) & 1] : vp, z, true, st);
 }
-
 }  // namespace
 
 int hop_horner(const dfm_op* op, int R, int d, const float* v, float* z, void* vp, void* ha, void* hb, float vscale,
@@ -454,12 +536,29 @@ int hop_horner(const dfm_op* op, int R, int d, const float* v, float* z, void* v
   }
   // FP16 and e4m3 copies run the hops on FP16 vectors (v scaled by vscale);
   // the BF16 copy on FP32 vectors
-  if (lowp_of(op, trans).precision == DFM_BF16) return horner_t<float>(op, R, d, v, z, vp, ha, hb, 1.0f, trans, st);
-  if (lowp_of(op, trans).frag) return horner_frag(op, R, d, v, z, vp, ha, hb, vscale, trans, st);
-  return horner_t<__half>(op, R, d, v, z, vp, ha, hb, vscale, trans, st);
+  return chain(op, R, d, v, z, vp, ha, hb, vscale, trans, st);
+}
+
+void destroy_hop_graphs(dfm_op* op) {
+  if (!op || !op->hop_graphs) return;
+  auto* gs = static_cast<HopGraphs*>(op->hop_graphs);
+  for (HopGraph& e : gs->g)
+    if (e.exec) cudaGraphExecDestroy(e.exec);
+  if (gs->cap) cudaStreamDestroy(gs->cap);
+  delete gs;
+  op->hop_graphs = nullptr;
 }
 
 }  // namespace dfm
+
+extern "C" int dfm_hop_graphs(int mode) {
+  using namespace dfm;
+  if (mode < -1 || mode > 1) return set_error(DFM_ERR_ARG, "dfm_hop_graphs: mode must be -1, 0 or 1");
+  if (mode >= 0) g_hop_graphs.store(mode);
+  return g_hop_graphs.load();
+}
+
+extern "C" long long dfm_hop_graph_replays(void) { return dfm::g_hop_graph_replays.load(); }
 
 extern "C" int dfm_precond_apply(const dfm_op* op, int precision, int degree, int transpose, const float* x, float* z,
                                  int R, void* stream) {

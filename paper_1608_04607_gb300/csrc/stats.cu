@@ -20,6 +20,7 @@ long long g_count[DFM_KERNEL_COUNT] = {};  // launches per kernel while timing w
 struct Rec {
   int kernel;
   int e0, e1;
+  int weight;  // launches the event pair spans (a replayed graph: all its nodes)
 };
 std::vector<cudaEvent_t> g_pool;
 std::vector<Rec> g_recs;
@@ -35,13 +36,26 @@ int take_event() {
 }
 }  // namespace
 
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+// launches recorded into a graph under capture are counted when it is replayed
+thread_local bool t_capturing = false;
 
-KernelTimer::KernelTimer(int kernel, cudaStream_t st) : kernel_(kernel), st_(st), e0_(-1) {
+void set_capturing(bool on) { t_capturing = on; }
+
+void count_launch() {
+  if (!t_capturing) g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+void count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+KernelTimer::KernelTimer(int kernel, cudaStream_t st, int weight)
+    : kernel_(kernel), st_(st), e0_(-1), weight_(weight) {
   const int every = g_timing.load(std::memory_order_relaxed);
-  if (!every || kernel < 0 || kernel >= DFM_KERNEL_COUNT) return;
+  if (!every || t_capturing || kernel < 0 || kernel >= DFM_KERNEL_COUNT) return;
   std::lock_guard<std::mutex> lk(g_mu);
-  if (g_count[kernel]++ % every != 0) return;
+  const long long before = g_count[kernel];
+  g_count[kernel] += weight;
+  // a single launch is timed every n-th time; a replayed graph every time
+  if (weight == 1 && before % every != 0) return;
   e0_ = take_event();
   if (e0_ >= 0) cudaEventRecord(g_pool[e0_], st_);
 }
@@ -52,7 +66,7 @@ KernelTimer::~KernelTimer() {
   const int e1 = take_event();
   if (e1 < 0) return;
   cudaEventRecord(g_pool[e1], st_);
-  g_recs.push_back(Rec{kernel_, e0_, e1});
+  g_recs.push_back(Rec{kernel_, e0_, e1, weight_});
 }
 
 }  // namespace dfm
@@ -88,7 +102,7 @@ extern "C" int dfm_kernel_stats(int kernel, int64_t* launches, double* total_ms)
     e = cudaEventElapsedTime(&t, g_pool[r.e0], g_pool[r.e1]);
     if (e != cudaSuccess) return cuda_error(e, "dfm_kernel_stats: cudaEventElapsedTime");
     ms += t;
-    ++n;
+    n += r.weight;
   }
   const int64_t all = (kernel >= 0 && kernel < DFM_KERNEL_COUNT) ? g_count[kernel] : n;
   *launches = all;

@@ -99,6 +99,8 @@ SIGNATURES = {
     "dfm_adjoint": (_i, [_vp, ctypes.POINTER(Params), _vp, _i, _vp, _vp, _vp, _vp, ctypes.POINTER(SolveOpts), _vp,
                          ctypes.POINTER(SolveInfo)]),
     "dfm_autotune": (_i, [_i]),
+    "dfm_hop_graphs": (_i, [_i]),
+    "dfm_hop_graph_replays": (ctypes.c_longlong, []),
     "dfm_autotune_report": (_i64, [ctypes.c_char_p, _i64]),
     "dfm_launch_count": (ctypes.c_longlong, []),
     "dfm_stats_enable": (_i, [_i]),
@@ -626,6 +628,20 @@ def autotune(mode: int = 1):
     """0: fixed default launch geometries; 1: tune on first use (default);
     2: forget the tuned choices and tune again (dfm_autotune)."""
     _check(load().dfm_autotune(int(mode)), "dfm_autotune")
+
+
+def hop_graphs(mode: int = -1) -> bool:
+    """CUDA graphs of the preconditioner's Horner chains (dfm_hop_graphs):
+    1 on (default), 0 off, -1 query; returns the state after the call."""
+    rc = load().dfm_hop_graphs(int(mode))
+    if rc < 0:
+        _check(rc, "dfm_hop_graphs")
+    return bool(rc)
+
+
+def hop_graph_replays() -> int:
+    """Hop-chain graph replays so far (dfm_hop_graph_replays)."""
+    return int(load().dfm_hop_graph_replays())
 
 
 def autotune_report() -> list:

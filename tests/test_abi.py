@@ -81,3 +81,17 @@ def test_assembly_parameters_are_checked_before_the_mesh_is_touched():
         assert rc in (dfm.DFM_ERR_ARG, dfm.DFM_ERR_UNSUPPORTED), bad
         assert L.dfm_last_error().decode().startswith("dfm_assemble"), bad
         assert not out.value
+
+
+def test_hop_graph_switch_on_the_host():
+    """dfm_hop_graphs only flips a process-wide switch: no CUDA call."""
+    from paper_1608_04607_gb300 import dfm
+
+    L = dfm.load()
+    assert L.dfm_hop_graphs(-1) == 1
+    assert L.dfm_hop_graphs(2) == dfm.DFM_ERR_ARG
+    try:
+        assert L.dfm_hop_graphs(0) == 0 and L.dfm_hop_graphs(-1) == 0
+    finally:
+        assert L.dfm_hop_graphs(1) == 1
+    assert L.dfm_hop_graph_replays() == 0
