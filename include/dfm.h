@@ -283,6 +283,13 @@ typedef struct {
   int batch;         /* GMRES_IR with R > 1: right-hand sides iterated in lockstep, sharing
                         every operator pass (0 = up to 16, capped so the group's FP32 Krylov
                         basis stays within 24 GiB) */
+  int block;         /* GMRES_IR with R > 1 and a low-precision precond_precision: 1 = block
+                        flexible GMRES, one Krylov space spanned by the whole group (block
+                        Gram-Schmidt with Cholesky QR, each pass repeated once; restart counts
+                        block steps, capped at 512 / group size - 1); 0 = each right-hand side
+                        in its own Krylov space, in lockstep.  The operator passes are shared
+                        either way; the block space needs fewer of them.  Ignored by
+                        dfm_solve_combo / dfm_solve_damped (one operator per right-hand side). */
 } dfm_solve_opts;
 
 typedef struct {

@@ -1,0 +1,463 @@
+// Block flexible GMRES for a group of right-hand sides sharing one Krylov
+// space (included by solve.cu inside its anonymous namespace, after Ctx, Hop,
+// ctx_apply and precond_hops).
+//
+// The paper gives no solver.  The lockstep solver iterates each right-hand
+// side in its own Krylov space and shares only the operator passes; the slow
+// directional modes of I - B are common to all sources of one operator, so
+// one block space spanned by all of them converges in fewer passes.  Per
+// block step j (R columns):
+//   Z_j = p~(B) V_j (the same low-precision hops as the lockstep solver),
+//   W = (I - B) Z_j,
+//   [V_0 .. V_j]^T W and W^T W in one pass (gdot_kernel: a tall-skinny
+//   product, every basis vector read once), then W <- (W - V C) S^-1 with S
+//   the Cholesky factor of W^T W - C^T C (gtrans_kernel, in place), twice
+//   (block classical Gram-Schmidt with Cholesky QR, each pass repeated once),
+//   so H_(:,j) = C1 + C2 S1 and H_(j+1,j) = S2 S1;
+//   the block Hessenberg least-squares problem min |E1 S0 - H Y| is kept in
+//   upper-triangular form by Givens rotations on the host (FP64), its
+//   residual rows giving every right-hand side's residual estimate;
+// at the end of a cycle x += [Z_0 .. Z_k] Y (gtrans_kernel).
+// A Gram matrix pivot below 1e-14 of the largest diagonal marks a column with
+// no new direction (a zero right-hand side, or a block that has become
+// invariant): its basis vector is set to zero and stays zero.
+
+constexpr int kGQ = 4;            // basis vectors per CTA of gdot_kernel
+constexpr int kGMaxSplits = 256;  // element ranges of gdot_kernel
+constexpr int kBlockMaxR = 16;    // largest block
+
+// partial[(s * K + q) * R + r] = sum over element range s of V_q . W_r,
+// q < K, r < R; V_q = V + q n, W_r = W + r n (n a multiple of 4, 16-byte
+// aligned vectors).  Grid (ceil(K / kGQ), S): the CTAs of one element range
+// run side by side, so W's range is read from DRAM about once.
+template <int RM>
+__global__ void __launch_bounds__(256)
+gdot_kernel(const float* __restrict__ V, int K, const float* __restrict__ W, int R, int64_t n,
+            float* __restrict__ partial) {
+  __shared__ float sh[8][kGQ * RM];
+  const int q0 = blockIdx.x * kGQ;
+  const int64_t n4 = n >> 2;
+  const int64_t per = (n4 + gridDim.y - 1) / gridDim.y;
+  const int64_t e0 = blockIdx.y * per, e1 = min(n4, e0 + per);
+  float acc[kGQ][RM];
+#pragma unroll
+  for (int c = 0; c < kGQ; ++c)
+#pragma unroll
+    for (int r = 0; r < RM; ++r) acc[c][r] = 0.f;
+  const float4* W4 = reinterpret_cast<const float4*>(W);
+  const float4* V4 = reinterpret_cast<const float4*>(V);
+  for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    float4 w[RM];
+#pragma unroll
+    for (int r = 0; r < RM; ++r) w[r] = r < R ? W4[r * n4 + e] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int c = 0; c < kGQ; ++c) {
+      if (q0 + c >= K) break;
+      const float4 v = V4[(int64_t)(q0 + c) * n4 + e];
+#pragma unroll
+      for (int r = 0; r < RM; ++r)
+        acc[c][r] = fmaf(v.x, w[r].x, fmaf(v.y, w[r].y, fmaf(v.z, w[r].z, fmaf(v.w, w[r].w, acc[c][r]))));
+    }
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < kGQ; ++c)
+#pragma unroll
+    for (int r = 0; r < RM; ++r) {
+      float v = acc[c][r];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) sh[wid][c * RM + r] = v;
+    }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kGQ * RM; i += blockDim.x) {
+    const int c = i / RM, r = i - c * RM;
+    if (q0 + c >= K || r >= R) continue;
+    float s = 0.f;
+    for (int w8 = 0; w8 < (int)(blockDim.x >> 5); ++w8) s += sh[w8][i];
+    partial[((int64_t)blockIdx.y * K + q0 + c) * R + r] = s;
+  }
+}
+
+// out[q * R + r] = sum_s partial[(s * K + q) * R + r] (fixed order)
+__global__ void gdot_reduce_kernel(const float* __restrict__ partial, int S, int KR, float* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= KR) return;
+  float s = 0.f;
+  for (int k = 0; k < S; ++k) s += partial[(int64_t)k * KR + i];
+  out[i] = s;
+}
+
+// In place, per element: W_r <- sum_i W_i T[i][r] + sum_q V_q H[q][r]
+// (T = the identity when Tm is NULL); coef = [H (K x R) | T (R x R)] in FP32;
+// partial[b * R + r] = block b's share of |W_r|^2 when partial is given.
+template <int RM>
+__global__ void __launch_bounds__(256)
+gtrans_kernel(const float* __restrict__ V, int K, const float* __restrict__ coef, int has_t, float* W, int R,
+              int64_t n, float* __restrict__ partial) {
+  extern __shared__ float cs[];  // K R + R R
+  for (int i = threadIdx.x; i < K * R + (has_t ? R * R : 0); i += blockDim.x) cs[i] = coef[i];
+  __syncthreads();
+  const float* Hs = cs;
+  const float* Ts = cs + K * R;
+  const int64_t n4 = n >> 2;
+  float4* W4 = reinterpret_cast<float4*>(W);
+  const float4* V4 = reinterpret_cast<const float4*>(V);
+  float sq[RM];
+#pragma unroll
+  for (int r = 0; r < RM; ++r) sq[r] = 0.f;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n4; e += (int64_t)gridDim.x * blockDim.x) {
+    float4 acc[RM];
+    if (has_t) {
+      float4 w[RM];
+#pragma unroll
+      for (int i = 0; i < RM; ++i) w[i] = i < R ? W4[i * n4 + e] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int r = 0; r < RM; ++r) {
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (r < R) {
+#pragma unroll
+          for (int i = 0; i < RM; ++i) {
+            if (i >= R) break;
+            const float t = Ts[i * R + r];
+            a.x = fmaf(w[i].x, t, a.x);
+            a.y = fmaf(w[i].y, t, a.y);
+            a.z = fmaf(w[i].z, t, a.z);
+            a.w = fmaf(w[i].w, t, a.w);
+          }
+        }
+        acc[r] = a;
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < RM; ++r) acc[r] = r < R ? W4[r * n4 + e] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    for (int q = 0; q < K; ++q) {
+      const float4 v = V4[(int64_t)q * n4 + e];
+#pragma unroll
+      for (int r = 0; r < RM; ++r) {
+        if (r >= R) break;
+        const float h = Hs[q * R + r];
+        acc[r].x = fmaf(v.x, h, acc[r].x);
+        acc[r].y = fmaf(v.y, h, acc[r].y);
+        acc[r].z = fmaf(v.z, h, acc[r].z);
+        acc[r].w = fmaf(v.w, h, acc[r].w);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < RM; ++r) {
+      if (r >= R) break;
+      W4[r * n4 + e] = acc[r];
+      sq[r] = fmaf(acc[r].x, acc[r].x, fmaf(acc[r].y, acc[r].y, fmaf(acc[r].z, acc[r].z, fmaf(acc[r].w, acc[r].w, sq[r]))));
+    }
+  }
+  if (!partial) return;
+  __shared__ float sh[8][RM];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int r = 0; r < RM; ++r) {
+    float v = sq[r];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[wid][r] = v;
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < R) {
+    float s = 0.f;
+    for (int w8 = 0; w8 < (int)(blockDim.x >> 5); ++w8) s += sh[w8][threadIdx.x];
+    partial[(int64_t)blockIdx.x * R + threadIdx.x] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+
+struct BlockScratch {
+  float* part = nullptr;  // gdot partials: kGMaxSplits * kmax * R floats
+  int64_t part_elems = 0;
+  float* small = nullptr;  // device coefficients / reduced products (>= (kmax + R) * R + R * R floats)
+  float* sq = nullptr;     // gtrans norm partials (grid * R floats)
+};
+
+inline int gdot_splits(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(kGMaxSplits, (n >> 2) / 4096)); }
+
+// G[q][r] = V_q . W_r for q < K (host, FP64 copies of the FP32 products)
+inline int block_dot(const Ctx& c, const float* V, int K, const float* W, int R, const BlockScratch& bs,
+                     std::vector<double>* G) {
+  const int S = gdot_splits(c.n);
+  if ((int64_t)S * K * R > bs.part_elems) return set_error(DFM_ERR_ARG, "block solve: Gram partials overflow");
+  const dim3 grid((unsigned)((K + kGQ - 1) / kGQ), (unsigned)S);
+  {
+    ::dfm::KernelTimer timer_(DFM_KERNEL_DOT, c.st);
+    if (R <= 2) gdot_kernel<2><<<grid, 256, 0, c.st>>>(V, K, W, R, c.n, bs.part);
+    else if (R <= 4) gdot_kernel<4><<<grid, 256, 0, c.st>>>(V, K, W, R, c.n, bs.part);
+    else if (R <= 8) gdot_kernel<8><<<grid, 256, 0, c.st>>>(V, K, W, R, c.n, bs.part);
+    else gdot_kernel<16><<<grid, 256, 0, c.st>>>(V, K, W, R, c.n, bs.part);
+  }
+  DFM_LAUNCHED();
+  DFM_CUDA_CHECK(cudaGetLastError());
+  gdot_reduce_kernel<<<(K * R + 127) / 128, 128, 0, c.st>>>(bs.part, S, K * R, bs.small);
+  DFM_LAUNCHED();
+  DFM_CUDA_CHECK(cudaGetLastError());
+  std::vector<float> h((size_t)K * R);
+  DFM_CUDA_CHECK(cudaMemcpyAsync(h.data(), bs.small, sizeof(float) * K * R, cudaMemcpyDeviceToHost, c.st));
+  DFM_CUDA_CHECK(cudaStreamSynchronize(c.st));
+  G->assign(h.begin(), h.end());
+  return DFM_OK;
+}
+
+// W <- W T + sign V H (T: R x R or empty for the identity; H: K x R)
+inline int block_update(const Ctx& c, const float* V, int K, const std::vector<double>& H, double sign,
+                        const std::vector<double>& T, float* W, int R, const BlockScratch& bs) {
+  const bool has_t = !T.empty();
+  std::vector<float> coef((size_t)K * R + (has_t ? R * R : 0));
+  for (int64_t i = 0; i < (int64_t)K * R; ++i) coef[i] = (float)(sign * H[i]);
+  if (has_t)
+    for (int i = 0; i < R * R; ++i) coef[(size_t)K * R + i] = (float)T[i];
+  DFM_CUDA_CHECK(cudaMemcpyAsync(bs.small, coef.data(), sizeof(float) * coef.size(), cudaMemcpyHostToDevice, c.st));
+  const size_t smem = sizeof(float) * coef.size();
+  if (smem > 48 * 1024) return set_error(DFM_ERR_ARG, "block solve: too many basis vectors for one update");
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(((c.n >> 2) + 255) / 256, 4 * c.nsm));
+  {
+    ::dfm::KernelTimer timer_(DFM_KERNEL_AXPY, c.st);
+    if (R <= 2) gtrans_kernel<2><<<grid, 256, smem, c.st>>>(V, K, bs.small, has_t, W, R, c.n, nullptr);
+    else if (R <= 4) gtrans_kernel<4><<<grid, 256, smem, c.st>>>(V, K, bs.small, has_t, W, R, c.n, nullptr);
+    else if (R <= 8) gtrans_kernel<8><<<grid, 256, smem, c.st>>>(V, K, bs.small, has_t, W, R, c.n, nullptr);
+    else gtrans_kernel<16><<<grid, 256, smem, c.st>>>(V, K, bs.small, has_t, W, R, c.n, nullptr);
+  }
+  DFM_LAUNCHED();
+  DFM_CUDA_CHECK(cudaGetLastError());
+  return DFM_OK;
+}
+
+// Cholesky M = S^T S (M: R x R symmetric, row-major) with pivots below
+// 1e-14 of the largest diagonal entry marked dead; Sinv maps W' to W1 = W' Sinv
+// (dead columns of W1 zero) and S (rows of dead columns zero) gives
+// W' ~ W1 S.  Returns false on a non-finite entry.
+inline bool chol_block(const std::vector<double>& M, int R, std::vector<double>* S, std::vector<double>* Sinv) {
+  double mx = 0.0;
+  for (int i = 0; i < R; ++i) {
+    if (!std::isfinite(M[i * R + i])) return false;
+    mx = std::max(mx, M[i * R + i]);
+  }
+  S->assign((size_t)R * R, 0.0);
+  Sinv->assign((size_t)R * R, 0.0);
+  std::vector<char> dead(R, 0);
+  const double floor_ = 1e-14 * mx;
+  for (int j = 0; j < R; ++j) {
+    // S[k][j] = (M[k][j] - sum_{l<k} S[l][k] S[l][j]) / S[k][k] for live k < j
+    for (int k = 0; k < j; ++k) {
+      if (dead[k]) continue;
+      double a = M[k * R + j];
+      for (int l = 0; l < k; ++l) a -= (*S)[l * R + k] * (*S)[l * R + j];
+      (*S)[k * R + j] = a / (*S)[k * R + k];
+    }
+    double d = M[j * R + j];
+    for (int l = 0; l < j; ++l) d -= (*S)[l * R + j] * (*S)[l * R + j];
+    if (!std::isfinite(d)) return false;
+    if (!(d > floor_) || mx == 0.0) {
+      dead[j] = 1;
+      continue;
+    }
+    (*S)[j * R + j] = sqrt(d);
+  }
+  // Sinv column j = (e_j - sum_{live k < j} Sinv[:, k] S[k][j]) / S[j][j] for live j
+  for (int j = 0; j < R; ++j) {
+    if (dead[j]) continue;
+    for (int i = 0; i < R; ++i) {
+      double a = (i == j) ? 1.0 : 0.0;
+      for (int k = 0; k < j; ++k)
+        if (!dead[k]) a -= (*Sinv)[i * R + k] * (*S)[k * R + j];
+      (*Sinv)[i * R + j] = a / (*S)[j * R + j];
+    }
+  }
+  return true;
+}
+
+// Orthonormalise the R vectors W (stored right after the K orthonormal basis
+// vectors V, so that [V, W] is contiguous) against V and among themselves:
+// W_in = V Hc + W_out Rs, Hc K x R, Rs R x R upper triangular.
+inline int block_orth(const Ctx& c, float* V, int K, int R, const BlockScratch& bs, std::vector<double>* Hc,
+                      std::vector<double>* Rs) {
+  float* W = V + (int64_t)K * c.n;
+  Hc->assign((size_t)K * R, 0.0);
+  std::vector<double> Sacc((size_t)R * R, 0.0);
+  for (int i = 0; i < R; ++i) Sacc[i * R + i] = 1.0;
+  for (int pass = 0; pass < 2; ++pass) {
+    std::vector<double> G;
+    int rc = block_dot(c, V, K + R, W, R, bs, &G);
+    if (rc) return rc;
+    // M = W^T W - C^T C, C = G[0..K)
+    std::vector<double> M((size_t)R * R);
+    for (int a = 0; a < R; ++a)
+      for (int b = 0; b < R; ++b) {
+        double s = 0.5 * (G[(size_t)(K + a) * R + b] + G[(size_t)(K + b) * R + a]);
+        for (int q = 0; q < K; ++q) s -= G[(size_t)q * R + a] * G[(size_t)q * R + b];
+        M[a * R + b] = s;
+      }
+    std::vector<double> S, Sinv;
+    if (!chol_block(M, R, &S, &Sinv)) return set_error(DFM_ERR_NONFINITE, "dfm_solve: non-finite Krylov block");
+    // W <- (W - V C) Sinv = W Sinv - V (C Sinv)
+    std::vector<double> CS((size_t)K * R, 0.0);
+    for (int q = 0; q < K; ++q)
+      for (int r = 0; r < R; ++r) {
+        double s = 0.0;
+        for (int i = 0; i < R; ++i) s += G[(size_t)q * R + i] * Sinv[i * R + r];
+        CS[(size_t)q * R + r] = s;
+      }
+    rc = block_update(c, V, K, CS, -1.0, Sinv, W, R, bs);
+    if (rc) return rc;
+    // W_in = V (Hc + C Sacc) + W_new (S Sacc)
+    for (int q = 0; q < K; ++q)
+      for (int r = 0; r < R; ++r) {
+        double s = 0.0;
+        for (int i = 0; i < R; ++i) s += G[(size_t)q * R + i] * Sacc[i * R + r];
+        (*Hc)[(size_t)q * R + r] += s;
+      }
+    std::vector<double> SS((size_t)R * R, 0.0);
+    for (int a = 0; a < R; ++a)
+      for (int b = 0; b < R; ++b) {
+        double s = 0.0;
+        for (int i = 0; i < R; ++i) s += S[a * R + i] * Sacc[i * R + b];
+        SS[a * R + b] = s;
+      }
+    Sacc.swap(SS);
+  }
+  *Rs = Sacc;
+  return DFM_OK;
+}
+
+// Block flexible GMRES(m) for the R (<= kBlockMaxR) right-hand sides b
+// ([R][n]) of one group, x ([R][n]) holding the initial guess; tol is relative
+// to each |b_r|.  V: (m + 1) R vectors, Z: m R vectors, tmp: R vectors.
+// Operator applications are added to *iters (one per pass over the group).
+inline int gmres_block(const Ctx& c, int R, const float* b, float* x, double tol, int m, int d, int max_iter,
+                       int* iters, std::vector<double>* est, float* V, float* Z, float* tmp, const Hop& lp,
+                       const BlockScratch& bs) {
+  const int64_t n = c.n;
+  const int64_t Rn = (int64_t)R * n;
+  est->assign(R, 0.0);
+  std::vector<double> G;
+  int rc = block_dot(c, b, R, b, R, bs, &G);
+  if (rc) return rc;
+  std::vector<double> bnorm(R);
+  for (int r = 0; r < R; ++r) {
+    bnorm[r] = sqrt(std::max(0.0, G[(size_t)r * R + r]));
+    if (!std::isfinite(bnorm[r])) return set_error(DFM_ERR_NONFINITE, "dfm_solve: non-finite right-hand side");
+  }
+  const int rows = (m + 1) * R, cols = m * R;
+  double prev_worst = -1.0;
+  while (true) {
+    // block residual V_0 = b - (I - B) x
+    axpby_kernel<float><<<grid_for(Rn, c.nsm), 256, 0, c.st>>>(tmp, 1.f, b, -1.f, x, Rn);
+    DFM_LAUNCHED();
+    DFM_CUDA_CHECK(cudaGetLastError());
+    rc = ctx_apply(c, x, tmp, V, R, 1.0, DFM_F32);
+    if (rc) return rc;
+    ++*iters;
+    std::vector<double> Hc, S0;
+    rc = block_orth(c, V, 0, R, bs, &Hc, &S0);
+    if (rc) return rc;
+    // least-squares state: Hm (rows x cols), Gm = E1 S0 (rows x R), rotations
+    std::vector<double> Hm((size_t)rows * cols, 0.0), Gm((size_t)rows * R, 0.0);
+    for (int a = 0; a < R; ++a)
+      for (int r = 0; r < R; ++r) Gm[(size_t)a * R + r] = S0[a * R + r];
+    struct Rot {
+      int i, k;
+      double c, s;
+    };
+    std::vector<Rot> rots;
+    double worst = 0.0;
+    for (int r = 0; r < R; ++r) {
+      double rn = 0.0;
+      for (int a = 0; a < R; ++a) rn += Gm[(size_t)a * R + r] * Gm[(size_t)a * R + r];
+      (*est)[r] = bnorm[r] > 0 ? sqrt(rn) / bnorm[r] : 0.0;
+      worst = std::max(worst, (*est)[r]);
+    }
+    if (worst <= tol) return DFM_OK;
+    if (*iters >= max_iter) return DFM_ERR_NOT_CONVERGED;
+    if (prev_worst > 0 && worst > 0.9 * prev_worst) return DFM_ERR_NOT_CONVERGED;  // precision exhausted
+    prev_worst = worst;
+    int kdone = 0;
+    for (int j = 0; j < m; ++j) {
+      float* vj = V + (int64_t)j * Rn;
+      float* zj = Z + (int64_t)j * Rn;
+      float* w = V + (int64_t)(j + 1) * Rn;
+      rc = precond_hops(c, lp, R, d, vj, zj);
+      if (rc) return rc;
+      *iters += d;
+      rc = ctx_apply(c, zj, zj, w, R, -1.0, DFM_F32);
+      if (rc) return rc;
+      std::vector<double> Rs;
+      rc = block_orth(c, V, (j + 1) * R, R, bs, &Hc, &Rs);
+      if (rc) return rc;
+      // new block column: rows [0, (j+1)R) = Hc, rows [(j+1)R, (j+2)R) = Rs
+      const int c0 = j * R;
+      for (int q = 0; q < (j + 1) * R; ++q)
+        for (int r = 0; r < R; ++r) Hm[(size_t)q * cols + c0 + r] = Hc[(size_t)q * R + r];
+      for (int a = 0; a < R; ++a)
+        for (int r = 0; r < R; ++r) Hm[(size_t)((j + 1) * R + a) * cols + c0 + r] = Rs[a * R + r];
+      for (const Rot& g : rots)
+        for (int r = 0; r < R; ++r) {
+          double& hi = Hm[(size_t)g.i * cols + c0 + r];
+          double& hk = Hm[(size_t)g.k * cols + c0 + r];
+          const double a = hi, bb = hk;
+          hi = g.c * a + g.s * bb;
+          hk = -g.s * a + g.c * bb;
+        }
+      for (int r = 0; r < R; ++r) {
+        const int col = c0 + r;
+        const int last = (j + 1) * R + r;  // lowest non-zero row of this column
+        for (int k = col + 1; k <= last; ++k) {
+          const double a = Hm[(size_t)col * cols + col], bb = Hm[(size_t)k * cols + col];
+          if (bb == 0.0) continue;
+          const double den = hypot(a, bb);
+          const Rot g{col, k, a / den, bb / den};
+          for (int cc = col; cc < c0 + R; ++cc) {
+            double& hi = Hm[(size_t)g.i * cols + cc];
+            double& hk = Hm[(size_t)g.k * cols + cc];
+            const double x1 = hi, x2 = hk;
+            hi = g.c * x1 + g.s * x2;
+            hk = -g.s * x1 + g.c * x2;
+          }
+          for (int rr = 0; rr < R; ++rr) {
+            double& gi = Gm[(size_t)g.i * R + rr];
+            double& gk = Gm[(size_t)g.k * R + rr];
+            const double x1 = gi, x2 = gk;
+            gi = g.c * x1 + g.s * x2;
+            gk = -g.s * x1 + g.c * x2;
+          }
+          rots.push_back(g);
+        }
+      }
+      kdone = j + 1;
+      worst = 0.0;
+      for (int r = 0; r < R; ++r) {
+        double rn = 0.0;
+        for (int a = 0; a < R; ++a) {
+          const double v = Gm[(size_t)((j + 1) * R + a) * R + r];
+          rn += v * v;
+        }
+        if (!std::isfinite(rn)) return set_error(DFM_ERR_NONFINITE, "dfm_solve: non-finite Krylov block");
+        (*est)[r] = bnorm[r] > 0 ? sqrt(rn) / bnorm[r] : 0.0;
+        worst = std::max(worst, (*est)[r]);
+      }
+      if (worst <= 0.5 * tol || *iters + d >= max_iter) break;
+    }
+    // Y = U^-1 Gm (upper triangular kdone R), x += [Z_0 .. Z_kdone) Y
+    const int kc = kdone * R;
+    std::vector<double> Y((size_t)kc * R, 0.0);
+    for (int r = 0; r < R; ++r)
+      for (int i = kc - 1; i >= 0; --i) {
+        double a = Gm[(size_t)i * R + r];
+        for (int k = i + 1; k < kc; ++k) a -= Hm[(size_t)i * cols + k] * Y[(size_t)k * R + r];
+        const double dg = Hm[(size_t)i * cols + i];
+        Y[(size_t)i * R + r] = dg != 0.0 ? a / dg : 0.0;
+      }
+    if (kc > 0) {
+      rc = block_update(c, Z, kc, Y, 1.0, std::vector<double>(), x, R, bs);
+      if (rc) return rc;
+    }
+  }
+}

@@ -396,6 +396,8 @@ inline int precond_hops(const Ctx& c, const Hop& hp, int R, int d, const float* 
   return ::dfm::hop_horner(hp.op, R, d, v, z, hp.vp, hp.ha, hp.hb, 1.0f / 256.0f, c.st, c.trans);
 }
 
+#include "block_gmres.cuh"
+
 template <typename T>
 int gmres(const Ctx& c, const T* b, T* x, double tol, int m, int d, int max_iter, int* iters, double* est, T* V,
           T* tmp, T* t1, T* t2, T* h_dev, T* partial, T* red_dev, const Hop* lp = nullptr, T* Z = nullptr) {
@@ -926,6 +928,13 @@ int solve_impl(const dfm_op* op, const dfm_op* const* combo, int K, const double
   bytes += inner_bytes + 4096;
   const int64_t part_elems = std::max<int64_t>((int64_t)kRedBlocks * (kMaxKrylov + 8), (int64_t)kBRedBlocks * hcap);
   bytes += (part_elems + 2 * hcap + 2 * Rg + 256) * 8 + 4096;  // partials, h, red
+  // block flexible GMRES: restart in block steps, (mb + 1) Rg basis vectors at most 512
+  // (one operator for the whole group: not with per-right-hand-side combinations)
+  const bool block = batched && use_lp && opts->block && Rg > 1 && !combo;
+  const int mb = block ? std::max(1, std::min(m, 512 / Rg - 1)) : 0;
+  const int64_t bpart = block ? (int64_t)kGMaxSplits * (mb + 1) * Rg * Rg : 0;
+  const int64_t bsmall = block ? (int64_t)(mb + 3) * Rg * Rg : 0;
+  if (block) bytes += (bpart + bsmall) * 4 + 1024;
   int rc = ensure_work(op, bytes + 8 * 256);
   if (rc) return rc;
   Work W{reinterpret_cast<char*>(op->swork)};
@@ -938,6 +947,12 @@ int solve_impl(const dfm_op* op, const dfm_op* const* combo, int K, const double
   double* h64 = W.take<double>(2 * hcap);
   double* red64 = W.take<double>(std::max(8, 2 * Rg));
   char* inner_base = W.take<char>(inner_bytes);
+  BlockScratch bscr;
+  if (block) {
+    bscr.part = W.take<float>(bpart);
+    bscr.part_elems = bpart;
+    bscr.small = W.take<float>(bsmall);
+  }
   Hop hop;
   const Hop* lp = nullptr;
   if (use_lp) {
@@ -1030,8 +1045,10 @@ int solve_impl(const dfm_op* op, const dfm_op* const* combo, int K, const double
         DFM_CUDA_CHECK(cudaGetLastError());
         DFM_CUDA_CHECK(cudaMemsetAsync(xf, 0, sizeof(float) * Rc * n, c.st));
         const double itol = std::max(inner_tol, 0.3 * opts->tol / std::max(worst, 1e-300));
-        int gi = gmres_batched<float>(c, Rc, bf, xf, itol, m, poly, max_iter, &iters, &est, V, tmp, t1, t2, h32,
-                                      part32, red32, lp, Zb);
+        int gi = (block && Rc > 1)
+                     ? gmres_block(c, Rc, bf, xf, itol, mb, poly, max_iter, &iters, &est, V, Zb, tmp, *lp, bscr)
+                     : gmres_batched<float>(c, Rc, bf, xf, itol, m, poly, max_iter, &iters, &est, V, tmp, t1, t2,
+                                            h32, part32, red32, lp, Zb);
         if (gi != DFM_OK && gi != DFM_ERR_NOT_CONVERGED) return gi;
         DFM_CUDA_CHECK(cudaMemcpyAsync(red64, sup.data(), sizeof(double) * Rc, cudaMemcpyHostToDevice, c.st));
         badd_f32_kernel<<<dim3(grid_for(n, c.nsm), Rc), 256, 0, c.st>>>(x, xf, red64, n);
