@@ -54,8 +54,9 @@ HEADLINE = "kuhn32_np8_rhs64"    # the default: 45 functions, BF16 blocks, sourc
 HEADLINE_DESC = ("32^3 Kuhn cube x 6 = 196,608 jittered tets (jitter 0.2h, seed 0); Np = 8 (45 Zernike functions); "
                  "mu = 0.05; boundary reflection 0.95; jobs of 64 random boundary-face unit sources (seed 2), 8 per "
                  "step, each job assembling B once at its first step; "
-                 "BF16 operator blocks; FP64-residual refinement around flexible FP32 GMRES({restart}) "
-                 "right-preconditioned by sum_{{k<{d}}} B~^k on an e4m3 copy (tensor-core hops); relative residual "
+                 "BF16 operator blocks; FP64-residual refinement around flexible FP32 {krylov} GMRES({restart}) "
+                 "right-preconditioned by sum_{{k<{d}}} B~^k on an e4m3 copy (tensor-core hops, CUDA graphs of the "
+                 "Horner chains); relative residual "
                  "1e-6; adjoint of the mean receiver density (cells [14,18)^3): transposed solve to 1e-6 on the "
                  "transposed e4m3 copy at each job's first step (later steps start from it and check its residual) "
                  "and the fused dB/dmu contraction for every step's sources")
@@ -506,7 +507,7 @@ def run_headline(args):
         if first:
             op.reassemble(mu)
         rho0 = dfm.source(mesh, Np, group(i) if rows is None else rows)
-        rho, info = op.solve(rho0, batch=B, **skw)
+        rho, info = op.solve(rho0, batch=B, block=0 if args.lockstep else 1, **skw)
         lam, dj, ainfo = op.adjoint(rho, g, dg, lam0=None if first else state["lam"], **skw)
         state["lam"] = lam
         return rho, dj, info, ainfo
@@ -520,6 +521,7 @@ def run_headline(args):
     dfm.stats_reset()
     dfm.stats_enable(STATS_EVERY)
     l0 = dfm.launch_count()
+    g0 = dfm.hop_graph_replays()
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -537,6 +539,7 @@ def run_headline(args):
         dist.barrier()
     clocks = sampler.stop()
     launches = dfm.launch_count() - l0
+    graph_replays = dfm.hop_graph_replays() - g0
     dfm.stats_enable(False)
     elapsed_ms = e0.elapsed_time(e1)
     names = {"assemble": dfm.KERNEL_ASSEMBLE, "hop": dfm.KERNEL_SPMV16, "hop_t": dfm.KERNEL_SPMV16_T,
@@ -599,7 +602,10 @@ def run_headline(args):
         "vs_baseline": None,
         "dtype": "bf16 blocks, e4m3 preconditioner copy, f16 hop vectors, f32 Krylov, f64 residual",
         "data": "synthetic",
-        "config": {"workload": HEADLINE, "desc": HEADLINE_DESC.format(restart=restart, d=poly),
+        "config": {"workload": HEADLINE, "desc": HEADLINE_DESC.format(restart=restart, d=poly,
+                                                                      krylov="lockstep" if args.lockstep else "block"),
+                   "krylov": "lockstep" if args.lockstep else "block (one Krylov space per group of 8 sources)",
+                   "hop_graph_replays": int(graph_replays),
                    "n_tets": int(m.n_tets), "n_rows": int(mesh.n_rows), "nb": op.nb, "sources_per_step": B,
                    "tol": tol, "restart": restart, "poly_degree": poly, "precond": args.precond,
                    "unit_of_work": "one source solved to 1e-6 with its gradient dJ/dmu; a job of 64 sources "
@@ -786,7 +792,7 @@ def run_reference(args):
             vals.append(est)
         last = (sample, threads)
     v = group / statistics.mean(vals)
-    desc = (HEADLINE_DESC.format(restart=32, d=64) if wname == HEADLINE else
+    desc = (HEADLINE_DESC.format(restart=32, d=64, krylov="block") if wname == HEADLINE else
             WORKLOAD_DESC if wname == WORKLOAD else wname)
     res = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": ws,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(vals) * 1e3,
@@ -1264,6 +1270,8 @@ def main():
     ap.add_argument("--fd", type=int, default=0, help="adjoint mode: elements checked by central differences")
     ap.add_argument("--e2e-steps", type=int, default=8, help="default workload: steps of the e2e measurement (8 = a job)")
     ap.add_argument("--no-extra", action="store_true", help="default workload: skip the 48,000-tet solve's key")
+    ap.add_argument("--lockstep", action="store_true",
+                    help="default workload: each source in its own Krylov space (lockstep) instead of block GMRES")
     ap.add_argument("--autotune", type=int, choices=[0, 1], default=1,
                     help="1: tune the hop launch geometry on first use (default); 0: fixed default geometry")
     args = ap.parse_args()

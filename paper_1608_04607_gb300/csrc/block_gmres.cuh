@@ -10,7 +10,7 @@
 //   Z_j = p~(B) V_j (the same low-precision hops as the lockstep solver),
 //   W = (I - B) Z_j,
 //   [V_0 .. V_j]^T W and W^T W in one pass (gdot_kernel: a tall-skinny
-//   product, every basis vector read once), then W <- (W - V C) S^-1 with S
+//   product, every basis vector and W read once), then W <- (W - V C) S^-1 with S
 //   the Cholesky factor of W^T W - C^T C (gtrans_kernel, in place), twice
 //   (block classical Gram-Schmidt with Cholesky QR, each pass repeated once),
 //   so H_(:,j) = C1 + C2 S1 and H_(j+1,j) = S2 S1;
@@ -22,60 +22,71 @@
 // no new direction (a zero right-hand side, or a block that has become
 // invariant): its basis vector is set to zero and stays zero.
 
-constexpr int kGQ = 4;            // basis vectors per CTA of gdot_kernel
-constexpr int kGMaxSplits = 256;  // element ranges of gdot_kernel
+constexpr int kGQ = 8;            // basis vectors per warp of gdot_kernel
+constexpr int kGMaxSplits = 512;  // element ranges of gdot_kernel
 constexpr int kBlockMaxR = 16;    // largest block
 
 // partial[(s * K + q) * R + r] = sum over element range s of V_q . W_r,
 // q < K, r < R; V_q = V + q n, W_r = W + r n (n a multiple of 4, 16-byte
-// aligned vectors).  Grid (ceil(K / kGQ), S): the CTAs of one element range
-// run side by side, so W's range is read from DRAM about once.
+// aligned vectors).  One CTA per element range s: the range's W is staged in
+// shared memory chunk by chunk; each warp takes kGQ basis vectors at a time
+// and its lanes stream consecutive 16-byte pieces of them (coalesced), each
+// piece multiplied with the R staged W pieces; the warp's kGQ x R sums are
+// reduced by shuffles once per group of basis vectors.  W is staged once per
+// group of (warps x kGQ) basis vectors.
 template <int RM>
 __global__ void __launch_bounds__(256)
 gdot_kernel(const float* __restrict__ V, int K, const float* __restrict__ W, int R, int64_t n,
             float* __restrict__ partial) {
-  __shared__ float sh[8][kGQ * RM];
-  const int q0 = blockIdx.x * kGQ;
+  constexpr int CH = 2048 / RM;  // float4 elements of W per staged chunk (32 KB)
+  __shared__ float4 ws[RM * CH];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int64_t n4 = n >> 2;
-  const int64_t per = (n4 + gridDim.y - 1) / gridDim.y;
-  const int64_t e0 = blockIdx.y * per, e1 = min(n4, e0 + per);
-  float acc[kGQ][RM];
-#pragma unroll
-  for (int c = 0; c < kGQ; ++c)
-#pragma unroll
-    for (int r = 0; r < RM; ++r) acc[c][r] = 0.f;
+  const int64_t per = (n4 + gridDim.x - 1) / gridDim.x;
+  const int64_t e0 = blockIdx.x * per, e1 = min(n4, e0 + per);
   const float4* W4 = reinterpret_cast<const float4*>(W);
   const float4* V4 = reinterpret_cast<const float4*>(V);
-  for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-    float4 w[RM];
+  for (int qg = 0; qg < K; qg += nw * kGQ) {
+    const int q0 = qg + wid * kGQ;
+    float acc[kGQ][RM];
 #pragma unroll
-    for (int r = 0; r < RM; ++r) w[r] = r < R ? W4[r * n4 + e] : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int u = 0; u < kGQ; ++u)
 #pragma unroll
-    for (int c = 0; c < kGQ; ++c) {
-      if (q0 + c >= K) break;
-      const float4 v = V4[(int64_t)(q0 + c) * n4 + e];
+      for (int r = 0; r < RM; ++r) acc[u][r] = 0.f;
+    for (int64_t c0 = e0; c0 < e1; c0 += CH) {
+      const int len = (int)(e1 - c0 < (int64_t)CH ? e1 - c0 : (int64_t)CH);
+      __syncthreads();
+      for (int i = threadIdx.x; i < R * CH; i += blockDim.x) {
+        const int r = i / CH, j = i - r * CH;
+        ws[r * CH + j] = j < len ? W4[r * n4 + c0 + j] : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      __syncthreads();
+      if (q0 >= K) continue;
+      for (int j = lane; j < len; j += 32) {
+        float4 v[kGQ];
 #pragma unroll
-      for (int r = 0; r < RM; ++r)
-        acc[c][r] = fmaf(v.x, w[r].x, fmaf(v.y, w[r].y, fmaf(v.z, w[r].z, fmaf(v.w, w[r].w, acc[c][r]))));
+        for (int u = 0; u < kGQ; ++u)
+          v[u] = q0 + u < K ? V4[(int64_t)(q0 + u) * n4 + c0 + j] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int r = 0; r < RM; ++r) {
+          if (r >= R) break;
+          const float4 w = ws[r * CH + j];
+#pragma unroll
+          for (int u = 0; u < kGQ; ++u)
+            acc[u][r] = fmaf(v[u].x, w.x, fmaf(v[u].y, w.y, fmaf(v[u].z, w.z, fmaf(v[u].w, w.w, acc[u][r]))));
+        }
+      }
     }
-  }
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (q0 >= K) continue;
 #pragma unroll
-  for (int c = 0; c < kGQ; ++c)
+    for (int u = 0; u < kGQ; ++u)
 #pragma unroll
-    for (int r = 0; r < RM; ++r) {
-      float v = acc[c][r];
+      for (int r = 0; r < RM; ++r) {
+        float v = acc[u][r];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) sh[wid][c * RM + r] = v;
-    }
-  __syncthreads();
-  for (int i = threadIdx.x; i < kGQ * RM; i += blockDim.x) {
-    const int c = i / RM, r = i - c * RM;
-    if (q0 + c >= K || r >= R) continue;
-    float s = 0.f;
-    for (int w8 = 0; w8 < (int)(blockDim.x >> 5); ++w8) s += sh[w8][i];
-    partial[((int64_t)blockIdx.y * K + q0 + c) * R + r] = s;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0 && q0 + u < K && r < R) partial[((int64_t)blockIdx.x * K + q0 + u) * R + r] = v;
+      }
   }
 }
 
@@ -132,7 +143,26 @@ gtrans_kernel(const float* __restrict__ V, int K, const float* __restrict__ coef
 #pragma unroll
       for (int r = 0; r < RM; ++r) acc[r] = r < R ? W4[r * n4 + e] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    for (int q = 0; q < K; ++q) {
+    // four basis vectors per round: four independent 16-byte loads in flight
+    // per thread keep enough bytes moving to stream at the HBM rate
+    int q = 0;
+    for (; q + 4 <= K; q += 4) {
+      float4 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = V4[(int64_t)(q + u) * n4 + e];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int r = 0; r < RM; ++r) {
+          if (r >= R) break;
+          const float h = Hs[(q + u) * R + r];
+          acc[r].x = fmaf(v[u].x, h, acc[r].x);
+          acc[r].y = fmaf(v[u].y, h, acc[r].y);
+          acc[r].z = fmaf(v[u].z, h, acc[r].z);
+          acc[r].w = fmaf(v[u].w, h, acc[r].w);
+        }
+    }
+    for (; q < K; ++q) {
       const float4 v = V4[(int64_t)q * n4 + e];
 #pragma unroll
       for (int r = 0; r < RM; ++r) {
@@ -180,20 +210,21 @@ struct BlockScratch {
   float* sq = nullptr;     // gtrans norm partials (grid * R floats)
 };
 
-inline int gdot_splits(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(kGMaxSplits, (n >> 2) / 4096)); }
+inline int gdot_splits(int64_t n, int nsm) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>(std::min(2 * nsm, kGMaxSplits), (n >> 2) / 2048));
+}
 
 // G[q][r] = V_q . W_r for q < K (host, FP64 copies of the FP32 products)
 inline int block_dot(const Ctx& c, const float* V, int K, const float* W, int R, const BlockScratch& bs,
                      std::vector<double>* G) {
-  const int S = gdot_splits(c.n);
+  const int S = gdot_splits(c.n, c.nsm);
   if ((int64_t)S * K * R > bs.part_elems) return set_error(DFM_ERR_ARG, "block solve: Gram partials overflow");
-  const dim3 grid((unsigned)((K + kGQ - 1) / kGQ), (unsigned)S);
   {
     ::dfm::KernelTimer timer_(DFM_KERNEL_DOT, c.st);
-    if (R <= 2) gdot_kernel<2><<<grid, 256, 0, c.st>>>(V, K, W, R, c.n, bs.part);
-    else if (R <= 4) gdot_kernel<4><<<grid, 256, 0, c.st>>>(V, K, W, R, c.n, bs.part);
-    else if (R <= 8) gdot_kernel<8><<<grid, 256, 0, c.st>>>(V, K, W, R, c.n, bs.part);
-    else gdot_kernel<16><<<grid, 256, 0, c.st>>>(V, K, W, R, c.n, bs.part);
+    if (R <= 2) gdot_kernel<2><<<S, 256, 0, c.st>>>(V, K, W, R, c.n, bs.part);
+    else if (R <= 4) gdot_kernel<4><<<S, 256, 0, c.st>>>(V, K, W, R, c.n, bs.part);
+    else if (R <= 8) gdot_kernel<8><<<S, 256, 0, c.st>>>(V, K, W, R, c.n, bs.part);
+    else gdot_kernel<16><<<S, 256, 0, c.st>>>(V, K, W, R, c.n, bs.part);
   }
   DFM_LAUNCHED();
   DFM_CUDA_CHECK(cudaGetLastError());
@@ -218,14 +249,22 @@ inline int block_update(const Ctx& c, const float* V, int K, const std::vector<d
   DFM_CUDA_CHECK(cudaMemcpyAsync(bs.small, coef.data(), sizeof(float) * coef.size(), cudaMemcpyHostToDevice, c.st));
   const size_t smem = sizeof(float) * coef.size();
   if (smem > 48 * 1024) return set_error(DFM_ERR_ARG, "block solve: too many basis vectors for one update");
-  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(((c.n >> 2) + 255) / 256, 4 * c.nsm));
-  {
+  int rc = DFM_OK;
+  // one resident wave of CTAs, each striding over the elements
+  auto go = [&](auto kernel) -> int {
+    int per_sm = 0;
+    DFM_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, smem));
+    const unsigned grid = (unsigned)std::max<int64_t>(
+        1, std::min<int64_t>(((c.n >> 2) + 255) / 256, (int64_t)std::max(per_sm, 1) * c.nsm));
     ::dfm::KernelTimer timer_(DFM_KERNEL_AXPY, c.st);
-    if (R <= 2) gtrans_kernel<2><<<grid, 256, smem, c.st>>>(V, K, bs.small, has_t, W, R, c.n, nullptr);
-    else if (R <= 4) gtrans_kernel<4><<<grid, 256, smem, c.st>>>(V, K, bs.small, has_t, W, R, c.n, nullptr);
-    else if (R <= 8) gtrans_kernel<8><<<grid, 256, smem, c.st>>>(V, K, bs.small, has_t, W, R, c.n, nullptr);
-    else gtrans_kernel<16><<<grid, 256, smem, c.st>>>(V, K, bs.small, has_t, W, R, c.n, nullptr);
-  }
+    kernel<<<grid, 256, smem, c.st>>>(V, K, bs.small, has_t, W, R, c.n, nullptr);
+    return DFM_OK;
+  };
+  if (R <= 2) rc = go(gtrans_kernel<2>);
+  else if (R <= 4) rc = go(gtrans_kernel<4>);
+  else if (R <= 8) rc = go(gtrans_kernel<8>);
+  else rc = go(gtrans_kernel<16>);
+  if (rc) return rc;
   DFM_LAUNCHED();
   DFM_CUDA_CHECK(cudaGetLastError());
   return DFM_OK;
