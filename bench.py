@@ -6,16 +6,19 @@ the 32^3 Kuhn cube (196,608 jittered tets, N_p = 8, mu = 0.05, r = 0.95),
 operator blocks in BF16 (9.6 GB), 64 random boundary-face sources and the
 mean interior density of the receiver cells [14, 18)^3 as the functional.
 A job assembles B for the 64 sources, solves them and the adjoint equation
-and forms every source's gradient; its 8 steps take the sources 8 at a time.
-One step: project the group's sources, solve (I - B) rho = rho0 for all 8 in
-lockstep to an FP64 relative residual of 1e-6 (FP64-residual refinement
-around flexible FP32 GMRES(32) right-preconditioned by sum_{k<64} B~^k on an
-e4m3 copy, hops on tensor cores), then the adjoint: the transposed solve
+and forms every source's gradient; its 4 steps take the sources 16 at a time.
+One step: project the group's sources, solve (I - B) rho = rho0 for all 16 in
+one block Krylov space to an FP64 relative residual of 1e-6 (FP64-residual
+refinement around block flexible FP32 GMRES(24) right-preconditioned by
+sum_{k<64} B~^k on an e4m3 copy, hops on tensor cores, the Horner chains
+replayed as CUDA graphs), then the adjoint: the transposed solve
 (I - B)^T lambda = g to 1e-6 (at the job's first step, which also assembles
 B; the later steps start from that lambda, whose residual the refinement
 checks) and the fused lambda^T (dB/dmu) rho_r contraction, giving
-dJ_r/dmu_e for the 8 sources.  Assembly is also timed on its own (assembly
-blocks/s).  Inputs are resident when the timed region starts; the operator
+dJ_r/dmu_e for the 16 sources.  Assembly is also timed on its own (assembly
+blocks/s).  The timed steps start a job (4 steps by default: one whole job
+with its assembly and adjoint solve).  Inputs are resident when the timed
+region starts; the operator
 and Krylov vectors are far larger than L2, so no flush is needed between
 steps.  The value is sources per second, each with its solve and gradient.
 
@@ -51,8 +54,10 @@ if ROOT not in sys.path:
 METRIC = "stationary solves/s at 1e-6 rel err"
 WORKLOAD = "kuhn20_np4"          # the single-source solve of the 48,000-tet cube
 HEADLINE = "kuhn32_np8_rhs64"    # the default: 45 functions, BF16 blocks, sources in groups with adjoint
+HEADLINE_GROUP = 16              # sources per step (one block Krylov space)
+HEADLINE_RESTART = 24            # block steps per restart cycle
 HEADLINE_DESC = ("32^3 Kuhn cube x 6 = 196,608 jittered tets (jitter 0.2h, seed 0); Np = 8 (45 Zernike functions); "
-                 "mu = 0.05; boundary reflection 0.95; jobs of 64 random boundary-face unit sources (seed 2), 8 per "
+                 "mu = 0.05; boundary reflection 0.95; jobs of 64 random boundary-face unit sources (seed 2), {group} per "
                  "step, each job assembling B once at its first step; "
                  "BF16 operator blocks; FP64-residual refinement around flexible FP32 {krylov} GMRES({restart}) "
                  "right-preconditioned by sum_{{k<{d}}} B~^k on an e4m3 copy (tensor-core hops, CUDA graphs of the "
@@ -479,8 +484,8 @@ def run_headline(args):
     mu = float(w["mu"][0])
     sources = np.asarray(w["sources"], dtype=np.int64)
     receiver = w["receiver"]
-    B = args.batch or 8
-    restart = args.restart or 32
+    B = args.batch or HEADLINE_GROUP
+    restart = args.restart or (HEADLINE_RESTART if B == HEADLINE_GROUP else 32)
     poly = args.poly or 64
     precond = PRECOND[args.precond]
     dfm.load()
@@ -531,7 +536,7 @@ def run_headline(args):
     e0.record()
     infos = []
     for i in range(args.steps):
-        rho, dj, info, ainfo = step(args.warmup + i)
+        rho, dj, info, ainfo = step(i)  # the timed steps start a job: its assembly and adjoint solve included
         infos.append((info.iters, info.outer, info.resid, ainfo.iters, ainfo.resid))
     e1.record()
     torch.cuda.synchronize()
@@ -563,7 +568,7 @@ def run_headline(args):
     # ---- e2e: C ABI with host source rows in and host gradients out ----------
     e2e = None
     if not args.no_e2e:
-        e2e_steps = max(1, min(args.steps, args.e2e_steps))
+        e2e_steps = max(1, min(args.steps, args.e2e_steps or per_job))
         host_dj = torch.empty((B, m.n_tets), dtype=torch.float64, pin_memory=True)
         host_rows = [np.ascontiguousarray(group(i)) for i in range(e2e_steps)]
         if ws > 1:
@@ -602,14 +607,14 @@ def run_headline(args):
         "vs_baseline": None,
         "dtype": "bf16 blocks, e4m3 preconditioner copy, f16 hop vectors, f32 Krylov, f64 residual",
         "data": "synthetic",
-        "config": {"workload": HEADLINE, "desc": HEADLINE_DESC.format(restart=restart, d=poly,
+        "config": {"workload": HEADLINE, "desc": HEADLINE_DESC.format(restart=restart, d=poly, group=B,
                                                                       krylov="lockstep" if args.lockstep else "block"),
-                   "krylov": "lockstep" if args.lockstep else "block (one Krylov space per group of 8 sources)",
+                   "krylov": "lockstep" if args.lockstep else f"block (one Krylov space per group of {B} sources)",
                    "hop_graph_replays": int(graph_replays),
                    "n_tets": int(m.n_tets), "n_rows": int(mesh.n_rows), "nb": op.nb, "sources_per_step": B,
                    "tol": tol, "restart": restart, "poly_degree": poly, "precond": args.precond,
                    "unit_of_work": "one source solved to 1e-6 with its gradient dJ/dmu; a job of 64 sources "
-                                   "(8 steps) assembles B and solves the adjoint equation once, at its first step",
+                                   f"({per_job} steps) assembles B and solves the adjoint equation once, at its first step",
                    "l2": "inputs larger than L2 (operator %.0f MB)" % (op.bytes / 1e6),
                    "parallelism": f"replicas x{ws}"},
         "roofline": roofline,
@@ -783,7 +788,7 @@ def run_reference(args):
     wname = args.workload or HEADLINE
     wl = workload(wname)
     apps = args.ref_apps or REF_APPLICATIONS.get(wname, 2000)
-    group = (args.batch or 8) if wname == HEADLINE else 1
+    group = (args.batch or HEADLINE_GROUP) if wname == HEADLINE else 1
     vals = []
     last = None
     for i in range(args.warmup + args.steps):
@@ -792,7 +797,8 @@ def run_reference(args):
             vals.append(est)
         last = (sample, threads)
     v = group / statistics.mean(vals)
-    desc = (HEADLINE_DESC.format(restart=32, d=64, krylov="block") if wname == HEADLINE else
+    desc = (HEADLINE_DESC.format(restart=HEADLINE_RESTART, d=64, krylov="block", group=HEADLINE_GROUP)
+            if wname == HEADLINE else
             WORKLOAD_DESC if wname == WORKLOAD else wname)
     res = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": ws,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(vals) * 1e3,
@@ -1246,7 +1252,8 @@ def run_adjoint(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 8 = one whole job of the default workload, else 5)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--workload", default=None,
@@ -1268,13 +1275,18 @@ def main():
     ap.add_argument("--fp64-sample", type=int, default=0,
                     help="batched and many modes: time the plain FP64 GPU path on this many sources")
     ap.add_argument("--fd", type=int, default=0, help="adjoint mode: elements checked by central differences")
-    ap.add_argument("--e2e-steps", type=int, default=8, help="default workload: steps of the e2e measurement (8 = a job)")
+    ap.add_argument("--e2e-steps", type=int, default=0,
+                    help="default workload: steps of the e2e measurement (0 = one job)")
     ap.add_argument("--no-extra", action="store_true", help="default workload: skip the 48,000-tet solve's key")
     ap.add_argument("--lockstep", action="store_true",
                     help="default workload: each source in its own Krylov space (lockstep) instead of block GMRES")
     ap.add_argument("--autotune", type=int, choices=[0, 1], default=1,
                     help="1: tune the hop launch geometry on first use (default); 0: fixed default geometry")
     args = ap.parse_args()
+    if args.steps is None:
+        # the default workload: one whole job (its assembly and adjoint solve included)
+        args.steps = 64 // (args.batch or HEADLINE_GROUP) if args.mode == "solve" and args.workload in (None, HEADLINE) \
+            else 5
     if args.workload is None and args.impl != "reference":
         args.workload = {"solve": HEADLINE, "batched": "kuhn30_np4_rhs128", "many": HEADLINE,
                          "adjoint": "kuhn40_np3_adjoint"}.get(args.mode, WORKLOAD)

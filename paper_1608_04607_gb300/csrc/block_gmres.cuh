@@ -11,9 +11,11 @@
 //   W = (I - B) Z_j,
 //   [V_0 .. V_j]^T W and W^T W in one pass (gdot_kernel: a tall-skinny
 //   product, every basis vector and W read once), then W <- (W - V C) S^-1 with S
-//   the Cholesky factor of W^T W - C^T C (gtrans_kernel, in place), twice
-//   (block classical Gram-Schmidt with Cholesky QR, each pass repeated once),
-//   so H_(:,j) = C1 + C2 S1 and H_(j+1,j) = S2 S1;
+//   the Cholesky factor of W^T W - C^T C (gtrans_kernel, in place), then a
+//   second pass: against the basis again where the first lost more than half
+//   of a column's norm, else Cholesky QR of the block alone (block classical
+//   Gram-Schmidt with Cholesky QR and selective re-orthogonalisation), so
+//   H_(:,j) = C1 + C2 S1 and H_(j+1,j) = S2 S1;
 //   the block Hessenberg least-squares problem min |E1 S0 - H Y| is kept in
 //   upper-triangular form by Givens rotations on the host (FP64), its
 //   residual rows giving every right-hand side's residual estimate;
@@ -22,7 +24,11 @@
 // no new direction (a zero right-hand side, or a block that has become
 // invariant): its basis vector is set to zero and stays zero.
 
-constexpr int kGQ = 8;            // basis vectors per warp of gdot_kernel
+// basis vectors per warp of gdot_kernel (its registers hold kGQ x RM sums)
+template <int RM>
+struct GdotQ {
+  static constexpr int value = RM >= 16 ? 4 : 8;
+};
 constexpr int kGMaxSplits = 512;  // element ranges of gdot_kernel
 constexpr int kBlockMaxR = 16;    // largest block
 
@@ -39,6 +45,7 @@ __global__ void __launch_bounds__(256)
 gdot_kernel(const float* __restrict__ V, int K, const float* __restrict__ W, int R, int64_t n,
             float* __restrict__ partial) {
   constexpr int CH = 2048 / RM;  // float4 elements of W per staged chunk (32 KB)
+  constexpr int kGQ = GdotQ<RM>::value;
   __shared__ float4 ws[RM * CH];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int64_t n4 = n >> 2;
@@ -103,7 +110,7 @@ __global__ void gdot_reduce_kernel(const float* __restrict__ partial, int S, int
 // (T = the identity when Tm is NULL); coef = [H (K x R) | T (R x R)] in FP32;
 // partial[b * R + r] = block b's share of |W_r|^2 when partial is given.
 template <int RM>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, RM >= 16 ? 2 : 3)
 gtrans_kernel(const float* __restrict__ V, int K, const float* __restrict__ coef, int has_t, float* W, int R,
               int64_t n, float* __restrict__ partial) {
   extern __shared__ float cs[];  // K R + R R
@@ -120,24 +127,22 @@ gtrans_kernel(const float* __restrict__ V, int K, const float* __restrict__ coef
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n4; e += (int64_t)gridDim.x * blockDim.x) {
     float4 acc[RM];
     if (has_t) {
-      float4 w[RM];
+      // acc = W T, one W column at a time (all R loads precede the stores below)
 #pragma unroll
-      for (int i = 0; i < RM; ++i) w[i] = i < R ? W4[i * n4 + e] : make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int r = 0; r < RM; ++r) acc[r] = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-      for (int r = 0; r < RM; ++r) {
-        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (r < R) {
+      for (int i = 0; i < RM; ++i) {
+        if (i >= R) break;
+        const float4 wi = W4[i * n4 + e];
 #pragma unroll
-          for (int i = 0; i < RM; ++i) {
-            if (i >= R) break;
-            const float t = Ts[i * R + r];
-            a.x = fmaf(w[i].x, t, a.x);
-            a.y = fmaf(w[i].y, t, a.y);
-            a.z = fmaf(w[i].z, t, a.z);
-            a.w = fmaf(w[i].w, t, a.w);
-          }
+        for (int r = 0; r < RM; ++r) {
+          if (r >= R) break;
+          const float t = Ts[i * R + r];
+          acc[r].x = fmaf(wi.x, t, acc[r].x);
+          acc[r].y = fmaf(wi.y, t, acc[r].y);
+          acc[r].z = fmaf(wi.z, t, acc[r].z);
+          acc[r].w = fmaf(wi.w, t, acc[r].w);
         }
-        acc[r] = a;
       }
     } else {
 #pragma unroll
@@ -323,32 +328,44 @@ inline int block_orth(const Ctx& c, float* V, int K, int R, const BlockScratch& 
   Hc->assign((size_t)K * R, 0.0);
   std::vector<double> Sacc((size_t)R * R, 0.0);
   for (int i = 0; i < R; ++i) Sacc[i * R + i] = 1.0;
+  // The second pass projects against the basis again only when the first
+  // lost more than half of some column's norm to it (the cancellation that
+  // leaves rounding-size components along the basis); otherwise it
+  // re-orthonormalises the block within itself (Cholesky QR on W alone,
+  // reading R vectors instead of K + R).
+  bool full = true;
   for (int pass = 0; pass < 2; ++pass) {
+    const int Kp = full ? K : 0;
+    float* Vp = W - (int64_t)Kp * c.n;  // [Vp, W] contiguous
     std::vector<double> G;
-    int rc = block_dot(c, V, K + R, W, R, bs, &G);
+    int rc = block_dot(c, Vp, Kp + R, W, R, bs, &G);
     if (rc) return rc;
-    // M = W^T W - C^T C, C = G[0..K)
+    // M = W^T W - C^T C, C = G[0..Kp)
     std::vector<double> M((size_t)R * R);
     for (int a = 0; a < R; ++a)
       for (int b = 0; b < R; ++b) {
-        double s = 0.5 * (G[(size_t)(K + a) * R + b] + G[(size_t)(K + b) * R + a]);
-        for (int q = 0; q < K; ++q) s -= G[(size_t)q * R + a] * G[(size_t)q * R + b];
+        double s = 0.5 * (G[(size_t)(Kp + a) * R + b] + G[(size_t)(Kp + b) * R + a]);
+        for (int q = 0; q < Kp; ++q) s -= G[(size_t)q * R + a] * G[(size_t)q * R + b];
         M[a * R + b] = s;
       }
+    if (pass == 0) {
+      full = false;
+      for (int a = 0; a < R; ++a) full |= M[a * R + a] < 0.25 * G[(size_t)(Kp + a) * R + a];
+    }
     std::vector<double> S, Sinv;
     if (!chol_block(M, R, &S, &Sinv)) return set_error(DFM_ERR_NONFINITE, "dfm_solve: non-finite Krylov block");
-    // W <- (W - V C) Sinv = W Sinv - V (C Sinv)
-    std::vector<double> CS((size_t)K * R, 0.0);
-    for (int q = 0; q < K; ++q)
+    // W <- (W - Vp C) Sinv = W Sinv - Vp (C Sinv)
+    std::vector<double> CS((size_t)Kp * R, 0.0);
+    for (int q = 0; q < Kp; ++q)
       for (int r = 0; r < R; ++r) {
         double s = 0.0;
         for (int i = 0; i < R; ++i) s += G[(size_t)q * R + i] * Sinv[i * R + r];
         CS[(size_t)q * R + r] = s;
       }
-    rc = block_update(c, V, K, CS, -1.0, Sinv, W, R, bs);
+    rc = block_update(c, Vp, Kp, CS, -1.0, Sinv, W, R, bs);
     if (rc) return rc;
     // W_in = V (Hc + C Sacc) + W_new (S Sacc)
-    for (int q = 0; q < K; ++q)
+    for (int q = 0; q < Kp; ++q)
       for (int r = 0; r < R; ++r) {
         double s = 0.0;
         for (int i = 0; i < R; ++i) s += G[(size_t)q * R + i] * Sacc[i * R + r];
