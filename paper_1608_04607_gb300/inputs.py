@@ -315,7 +315,7 @@ def workload(name: str) -> dict:
     if name == "kuhn16_np8":  # a smaller case of the 45-function workload (98,304 rows), for profiling
         m = kuhn_cube_mesh(16, jitter=0.2, seed=0)
         return dict(name=name, mesh=m, Np=8, mu=uniform_mu(m, 0.05), refl=0.95,
-                    sources=random_boundary_rows(m, 8, seed=2), receiver=cell_tets(m, 6, 10), solver="ir", tol=1e-6)
+                    sources=random_boundary_rows(m, 16, seed=2), receiver=cell_tets(m, 6, 10), solver="ir", tol=1e-6)
     if name == "kuhn32_np8_rhs64":
         m = kuhn_cube_mesh(32, jitter=0.2, seed=0)
         return dict(name=name, mesh=m, Np=8, mu=uniform_mu(m, 0.05), refl=0.95,
