@@ -133,7 +133,9 @@ int dfm_face_match_static(const int32_t* tets, int64_t n_verts, int64_t n_tets, 
 int dfm_gauss_legendre(int q, double* x, double* w, void* stream);
 
 typedef struct {
-  int Np;               /* momentum order 0..8 (N_b = (Np+1)(Np+2)/2) */
+  int Np;               /* momentum order 0..20 (N_b = (Np+1)(Np+2)/2); above 8 (the orders of the
+                           cuboid verification, Sec. 4.1) DFM_F32 blocks only, built by the kernels
+                           for wide bases, and applied without preconditioner copies */
   const double* mu;     /* device FP64 [n_tets] damping per tet, or NULL */
   double mu_uniform;    /* damping when mu == NULL (>= 0) */
   int quad_order;       /* Gauss-Legendre order per direction patch; 0 = Np + 6 */
@@ -230,7 +232,7 @@ int dfm_source(const dfm_mesh* mesh, int Np, const int64_t* rows_host, int n_src
  * Asynchronous when dirs_host is NULL; with directions it waits on the stream
  * and returns DFM_ERR_ARG if some d does not point strictly into its tet
  * (d.n <= 0 after normalisation), leaving rho0 with that source's row zero.
- * Errors: DFM_ERR_ARG (NULL, Np outside 0..8, row out of range, zero
+ * Errors: DFM_ERR_ARG (NULL, Np outside 0..20, row out of range, zero
  * direction, repeated row with combine = 1). */
 int dfm_source_directed(const dfm_mesh* mesh, int Np, const int64_t* rows_host, const double* dirs_host, int n_src,
                         int combine, double* rho0, void* stream);
@@ -346,7 +348,8 @@ int dfm_solve_damped(const dfm_op* const* moments, int K, const double* mu_rhs_h
  * in FP32 (made on first use and again after each assembly),
  * evaluated by Horner's rule z <- x + B~ z with FP32 vectors and FP32
  * accumulation.  op: FP32 operator; x, z: device FP32 [R][rows][nb], 16-byte
- * aligned, z must not alias x; 1 <= degree <= 64.  Uses a scratch of
+ * aligned, z must not alias x; 1 <= degree <= 64; DFM_ERR_UNSUPPORTED for
+ * bases above Np = 8.  Uses a scratch of
  * 3 R rows NBP floats (NBP = nb rounded up to 8) taken with cudaMallocAsync
  * on the stream and released in stream order.  Asynchronous. */
 int dfm_precond_apply(const dfm_op* op, int precision, int degree, int transpose, const float* x, float* z, int R,
@@ -391,7 +394,7 @@ long long dfm_hop_graph_replays(void);
  *   gvec, dgvec: device FP64 [rows][nb]; on return gvec[4e+l] += w_e g_e[l] and
  *   dgvec[4e+l] += w_e dg_e[l] for the listed tets (other rows untouched), so
  *   J(rho) = gvec . rho and dJ/dmu_e (explicit part) = dgvec[4e..4e+3] . rho[4e..4e+3].
- *   mu: device FP64 [n_tets] or NULL for mu_uniform.  Asynchronous. */
+ *   mu: device FP64 [n_tets] or NULL for mu_uniform.  Np in 0..20.  Asynchronous. */
 int dfm_interior_density(const dfm_mesh* mesh, int Np, const double* mu, double mu_uniform, const int64_t* tets_host,
                          const double* weights_host, int n, int nq, double* gvec, double* dgvec, void* stream);
 
@@ -402,7 +405,7 @@ int dfm_interior_density(const dfm_mesh* mesh, int Np, const double* mu, double 
  * (Sec. 4.1, Eq. IntDens).
  *   gvec: device FP64 [rows][nb]; rho: device FP64 [R][rows][nb];
  *   out: device FP64 [R][n_tets] (overwritten).  Asynchronous.
- * Errors: DFM_ERR_ARG (NULL, R < 1, Np outside 0..8). */
+ * Errors: DFM_ERR_ARG (NULL, R < 1, Np outside 0..20). */
 int dfm_tet_density(const dfm_mesh* mesh, int Np, const double* gvec, const double* rho, int R, double* out,
                     void* stream);
 
@@ -420,7 +423,8 @@ int dfm_tet_density(const dfm_mesh* mesh, int Np, const double* gvec, const doub
  *   initial guess on entry (e.g. lambda of an earlier call with the same
  *   operator and functional: the refinement then checks its FP64 residual and
  *   stops at once if it meets tol); dJ_dmu: device FP64 [R][n_tets] (overwritten).
- * Synchronises like dfm_solve.  Errors as dfm_solve. */
+ * Synchronises like dfm_solve.  Errors as dfm_solve; DFM_ERR_UNSUPPORTED for
+ * operators above Np = 8 (the contraction is built for bases up to 45). */
 int dfm_adjoint(const dfm_op* op, const dfm_params* params, const double* rho, int R, const double* gvec,
                 const double* dgvec, double* lambda_out, double* dJ_dmu, const dfm_solve_opts* opts, void* stream,
                 dfm_solve_info* info);

@@ -286,7 +286,7 @@ using namespace dfm;
 extern "C" int dfm_interior_density(const dfm_mesh* mesh, int Np, const double* mu, double mu_uniform,
                                     const int64_t* tets_host, const double* weights_host, int n, int nq, double* gvec,
                                     double* dgvec, void* stream) {
-  if (!mesh || !tets_host || !gvec || n < 1 || Np < 0 || Np > 8)
+  if (!mesh || !tets_host || !gvec || n < 1 || Np < 0 || Np > geom::kWideMaxNp)
     return set_error(DFM_ERR_ARG, "dfm_interior_density: bad argument");
   // nq < 0: the split polar rule with |nq| points per direction; nq = 0: the
   // same rule with 24 points (accurate for centroids close to a face, as on
@@ -324,9 +324,17 @@ extern "C" int dfm_interior_density(const dfm_mesh* mesh, int Np, const double* 
       interior_density_kernel<N><<<blocks, 128, 0, st>>>(mesh->verts, mesh->tets, mesh->geom, mu, mu_uniform, list, \
                                                          wp, n, glx, glw, nq, gvec, dgvec);                      \
     break;
-  switch (Np) { CASE(0) CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) }
+  switch (Np) {
+    CASE(0) CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
+    default:  // Np = 9..20 (wide.cu)
+      rc = launch_interior_density_wide(Np, polar, mesh, mu, mu_uniform, list, wp, n, glx, glw, nq, gvec, dgvec, st);
+      if (rc) {
+        cudaFreeAsync(buf, st);
+        return rc;
+      }
+  }
 #undef CASE
-  DFM_LAUNCHED();
+  if (Np <= 8) DFM_LAUNCHED();
   DFM_CUDA_CHECK(cudaGetLastError());
   DFM_CUDA_CHECK(cudaFreeAsync(buf, st));
   return DFM_OK;
@@ -334,7 +342,7 @@ extern "C" int dfm_interior_density(const dfm_mesh* mesh, int Np, const double* 
 
 extern "C" int dfm_tet_density(const dfm_mesh* mesh, int Np, const double* gvec, const double* rho, int R,
                                double* out, void* stream) {
-  if (!mesh || !gvec || !rho || !out || R < 1 || Np < 0 || Np > 8)
+  if (!mesh || !gvec || !rho || !out || R < 1 || Np < 0 || Np > geom::kWideMaxNp)
     return set_error(DFM_ERR_ARG, "dfm_tet_density: bad argument");
   const int64_t units = (int64_t)R * mesh->nt;
   const int64_t blocks = (units + 7) / 8;  // 8 warps per block
@@ -352,6 +360,7 @@ extern "C" int dfm_adjoint(const dfm_op* op, const dfm_params* params, const dou
   if (!op || !params || !rho || !gvec || !lambda_out || !dJ_dmu || !opts || R < 1)
     return set_error(DFM_ERR_ARG, "dfm_adjoint: bad argument");
   if (params->Np != op->Np) return set_error(DFM_ERR_ARG, "dfm_adjoint: params->Np differs from the operator's");
+  if (op->Np > 8) return set_error(DFM_ERR_UNSUPPORTED, "dfm_adjoint: the dB/dmu contraction is built for Np <= 8");
   const dfm_mesh* mesh = op->mesh;
   cudaStream_t st = as_stream(stream);
   // 1. adjoint equation (I - B)^T lambda = g

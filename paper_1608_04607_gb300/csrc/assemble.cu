@@ -291,15 +291,21 @@ int dispatch_np(int Np, const PairConst* pairs, int64_t npairs, const double* gl
     case 6: return launch_assemble<6, T, TO>(pairs, npairs, glx, glw, q, cos_max, vals, row_stride, nodes, moment, st);
     case 7: return launch_assemble<7, T, TO>(pairs, npairs, glx, glw, q, cos_max, vals, row_stride, nodes, moment, st);
     case 8: return launch_assemble<8, T, TO>(pairs, npairs, glx, glw, q, cos_max, vals, row_stride, nodes, moment, st);
-    default: return set_error(DFM_ERR_ARG, "dfm_assemble: Np must be in 0..8");
+    default:
+      // N_p = 9..20: one block per (face pair, tile of test rows), FP32 blocks
+      if constexpr (std::is_same<T, float>::value && std::is_same<TO, float>::value)
+        return launch_assemble_wide(Np, pairs, npairs, glx, glw, q, cos_max, vals, row_stride, nodes, moment, st);
+      return set_error(DFM_ERR_UNSUPPORTED, "dfm_assemble: Np above 8 is built for FP32 blocks only");
   }
 }
 
 int check_params(const dfm_mesh* mesh, const dfm_params* p) {
   if (!mesh || !p) return set_error(DFM_ERR_ARG, "dfm_assemble: NULL mesh or params");
-  if (p->Np < 0 || p->Np > 8) return set_error(DFM_ERR_ARG, "dfm_assemble: Np must be in 0..8");
+  if (p->Np < 0 || p->Np > geom::kWideMaxNp) return set_error(DFM_ERR_ARG, "dfm_assemble: Np must be in 0..20");
   if (p->precision != DFM_F32 && p->precision != DFM_F64 && p->precision != DFM_BF16)
     return set_error(DFM_ERR_UNSUPPORTED, "dfm_assemble: precision must be DFM_F32, DFM_F64 or DFM_BF16");
+  if (p->Np > 8 && p->precision != DFM_F32)
+    return set_error(DFM_ERR_UNSUPPORTED, "dfm_assemble: Np above 8 is built for DFM_F32 only");
   if (!p->mu && !(p->mu_uniform >= 0.0)) return set_error(DFM_ERR_ARG, "dfm_assemble: mu_uniform must be >= 0");
   const int q = p->quad_order ? p->quad_order : p->Np + 6;
   if (q < 1 || q > kMaxQ) return set_error(DFM_ERR_ARG, "dfm_assemble: quad_order must be in 1..32");

@@ -158,6 +158,18 @@ bool apply_mma_supported(const dfm_op* op, int R);
 int apply_mma(const dfm_op* op, const float* x, const float* x0, float* y, int R, double alpha, cudaStream_t st);
 // reads and clears op's time-out flag (waits on st): DFM_ERR_TIMEOUT if set
 int read_timeout_flag(const dfm_op* op, cudaStream_t st, const char* who);
+// bases above N_p = 8 (wide.cu).  pairs: the assembly's per-pair constants
+// (PairConst of node.cuh); vals FP32.
+int launch_assemble_wide(int Np, const void* pairs, int64_t npairs, const double* glx, const double* glw, int q,
+                         float cos_max, float* vals, int64_t row_stride, unsigned long long* nodes, int moment,
+                         cudaStream_t st);
+int apply_wide(const dfm_op* op, const float* x, const float* x0, float* y, int R, double alpha, cudaStream_t st);
+int apply_wide(const dfm_op* op, const double* x, const double* x0, double* y, int R, double alpha, cudaStream_t st);
+int launch_directed_source_wide(int Np, const FaceGeom* geom, const int64_t* rows, const double* dirs, int n_src,
+                                int64_t nrows, int combine, double* rho0, int* bad, cudaStream_t st);
+int launch_interior_density_wide(int Np, bool polar, const dfm_mesh* mesh, const double* mu, double mu_uniform,
+                                 const int64_t* list, const double* weights, int n, const double* glx,
+                                 const double* glw, int nq, double* gvec, double* dgvec, cudaStream_t st);
 // implemented in quad.cu
 int gauss_legendre_device(int q, double* x, double* w, cudaStream_t st);
 }  // namespace dfm

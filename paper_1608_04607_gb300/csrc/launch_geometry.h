@@ -63,6 +63,46 @@ inline Fwd fwd_geometry(int nb, int tv, int tx, int K, int R, int64_t nrows, boo
   return g;
 }
 
+// ---- bases above N_p = 8 (wide.cu): N_b = 55 .. 231 ----
+constexpr int kNarrowMaxNb = 45;  // largest basis of the per-warp kernels (N_p = 8)
+constexpr int kWideMaxNp = 20;    // largest order of the wide kernels (N_b = 231)
+
+// Assembly of one face pair by one block per tile of test rows: the block's
+// CG x RG threads each own 8 test rows x 8 trial columns of the tile (CG =
+// NBP / 8 column groups, RG row groups, TRW = 8 RG rows per tile), NC nodes
+// are staged per pass (Z(p) of all NBP trial columns, w Z(p') of the tile's
+// rows), evaluated by threads [0, NC) and [NC, 2 NC).
+struct WideAsm {
+  int nb, nbp;   // basis size and its padding to 8
+  int cg, rg;    // column and row groups of a tile
+  int trw;       // test rows per tile (8 rg)
+  int ntile;     // tiles per face pair
+  int threads;   // block size (a multiple of 32, >= cg rg and >= 2 nc)
+  int nc;        // nodes staged per pass
+  int ldq, ldp;  // staging row strides (floats): trw + 4, nbp + 4
+  int64_t smem;  // dynamic shared memory bytes beyond the patch state
+};
+
+inline WideAsm wide_asm_geometry(int nb) {
+  WideAsm g{};
+  g.nb = nb;
+  g.nbp = (nb + 7) / 8 * 8;
+  g.cg = g.nbp / 8;
+  const int nrg = g.cg;  // row groups of the whole block
+  int max_rg = 256 / g.cg;
+  if (max_rg < 1) max_rg = 1;
+  g.ntile = (nrg + max_rg - 1) / max_rg;
+  g.rg = (nrg + g.ntile - 1) / g.ntile;
+  g.trw = 8 * g.rg;
+  g.threads = (g.cg * g.rg + 31) / 32 * 32;
+  if (g.threads < 64) g.threads = 64;
+  g.nc = g.threads / 2 < 64 ? g.threads / 2 : 64;
+  g.ldq = g.trw + 4;
+  g.ldp = g.nbp + 4;
+  g.smem = (int64_t)g.nc * (g.ldq + g.ldp) * 4 + ((int64_t)g.trw + 2 * 32) * 4;
+  return g;
+}
+
 // ---- preconditioner hops on the low-precision copy (hop_kernel) ----
 constexpr int kHopConsumerWarps = 8;
 constexpr int kHopPasses = 2;  // consumer passes per tile when the copy rows are small

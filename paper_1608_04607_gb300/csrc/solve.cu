@@ -842,7 +842,7 @@ using namespace dfm;
 
 extern "C" int dfm_source(const dfm_mesh* mesh, int Np, const int64_t* rows_host, int n_src, double* rho0,
                           void* stream) {
-  if (!mesh || !rows_host || !rho0 || n_src < 1 || Np < 0 || Np > 8)
+  if (!mesh || !rows_host || !rho0 || n_src < 1 || Np < 0 || Np > geom::kWideMaxNp)
     return set_error(DFM_ERR_ARG, "dfm_source: bad argument");
   for (int s = 0; s < n_src; ++s)
     if (rows_host[s] < 0 || rows_host[s] >= mesh->nrows) return set_error(DFM_ERR_ARG, "dfm_source: row out of range");

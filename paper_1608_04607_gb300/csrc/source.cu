@@ -212,7 +212,7 @@ using namespace dfm;
 
 extern "C" int dfm_source_directed(const dfm_mesh* mesh, int Np, const int64_t* rows_host, const double* dirs_host,
                                    int n_src, int combine, double* rho0, void* stream) {
-  if (!mesh || !rows_host || !rho0 || n_src < 1 || Np < 0 || Np > 8 || (combine != 0 && combine != 1))
+  if (!mesh || !rows_host || !rho0 || n_src < 1 || Np < 0 || Np > geom::kWideMaxNp || (combine != 0 && combine != 1))
     return set_error(DFM_ERR_ARG, "dfm_source_directed: bad argument");
   for (int s = 0; s < n_src; ++s)
     if (rows_host[s] < 0 || rows_host[s] >= mesh->nrows)
@@ -251,9 +251,19 @@ extern "C" int dfm_source_directed(const dfm_mesh* mesh, int Np, const int64_t* 
     directed_source_kernel<N><<<blocks, 128, 0, st>>>(mesh->geom, rows_d, dp, n_src, mesh->nrows, combine, rho0, \
                                                       bad_d);                                                    \
     break;
-  switch (Np) { CASE(0) CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) }
+  switch (Np) {
+    CASE(0) CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
+    default: {  // Np = 9..20 (wide.cu)
+      const int rc = launch_directed_source_wide(Np, mesh->geom, rows_d, dp, n_src, mesh->nrows, combine, rho0, bad_d,
+                                                 st);
+      if (rc) {
+        cudaFreeAsync(buf, st);
+        return rc;
+      }
+    }
+  }
 #undef CASE
-  DFM_LAUNCHED();
+  if (Np <= 8) DFM_LAUNCHED();
   DFM_CUDA_CHECK(cudaGetLastError());
   int bad = 0;
   if (dirs_host) DFM_CUDA_CHECK(cudaMemcpyAsync(&bad, bad_d, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -548,6 +548,15 @@ int launch(const dfm_op* op, const TX* x, const TX* x0, TX* y, int R, double alp
   if (!trans) {
     if ((reinterpret_cast<uintptr_t>(x) & 15) || (reinterpret_cast<uintptr_t>(op->vals) & 15))
       return set_error(DFM_ERR_ARG, "dfm_apply: x must be 16-byte aligned");
+    // bases above N_p = 8: a block row per warp, no staged row tiles (wide.cu)
+    if (op->nb > geom::kNarrowMaxNb) {
+      if constexpr (std::is_same<TV, float>::value && std::is_same<TX, TA>::value) {
+        if (K != 1 || combo_ops)
+          return set_error(DFM_ERR_UNSUPPORTED, "dfm_apply_combo: combined operators need Np <= 8");
+        return apply_wide(op, x, x0, y, R, alpha, st);
+      }
+      return set_error(DFM_ERR_UNSUPPORTED, "dfm_apply: bases above Np = 8 need FP32 blocks");
+    }
     // BF16 blocks with several FP32 right-hand sides: a dense contraction per
     // row, on tensor cores (spmv_mma.cu)
     if constexpr (std::is_same<TV, __nv_bfloat16>::value && std::is_same<TX, float>::value)
@@ -615,7 +624,8 @@ int launch(const dfm_op* op, const TX* x, const TX* x0, TX* y, int R, double alp
     else
       return set_error(DFM_ERR_UNSUPPORTED, "dfm_apply_combo: operators must be FP32");
     if (rc) return rc;
-  } else if (combo_ops == nullptr && !(reinterpret_cast<uintptr_t>(op->vals) & 15)) {
+  } else if (combo_ops == nullptr && !(reinterpret_cast<uintptr_t>(op->vals) & 15) &&
+             op->nb <= geom::kNarrowMaxNb) {
     // pipelined transposed application, one right-hand side per launch
     const int64_t nt = op->nrows / 4;
     const int64_t row_bytes = op->row_stride * (int64_t)sizeof(TV);

@@ -64,7 +64,7 @@ def test_null_handles_are_rejected_on_the_host():
 
 
 def test_assembly_parameters_are_checked_before_the_mesh_is_touched():
-    """Np out of range, an unknown precision, negative or NaN damping, and out-of-range
+    """Np out of range (0..20; above 8 FP32 blocks only), an unknown precision, negative or NaN damping, and out-of-range
     quadrature settings are refused by dfm_assemble before it reads the mesh or calls
     CUDA (the mesh handle here is a zeroed host buffer that is never read)."""
     from paper_1608_04607_gb300 import dfm
@@ -73,7 +73,8 @@ def test_assembly_parameters_are_checked_before_the_mesh_is_touched():
     fake_mesh = ctypes.create_string_buffer(4096)
     out = ctypes.c_void_p()
     good = dict(Np=4, mu=None, mu_uniform=0.1, quad_order=0, max_patch_deg=0.0, precision=dfm.F32, moment=0)
-    cases = [dict(Np=9), dict(Np=-1), dict(precision=7), dict(mu_uniform=-0.1), dict(mu_uniform=float("nan")),
+    cases = [dict(Np=21), dict(Np=-1), dict(Np=9, precision=dfm.BF16), dict(Np=20, precision=dfm.F64),
+             dict(precision=7), dict(mu_uniform=-0.1), dict(mu_uniform=float("nan")),
              dict(quad_order=33), dict(max_patch_deg=5.0), dict(moment=4)]
     for bad in cases:
         p = dfm.Params(**{**good, **bad})

@@ -148,3 +148,28 @@ def test_view_factors_by_contour_integrals(oracle_mod):
         for k, fp in enumerate([g for g in range(4) if g != f]):
             F = _contour_view_factor_area(face(f), face(fp)) / A[f]
             assert op.blocks[f, k, 0, 0] == pytest.approx(F * np.sqrt(A[f] / A[fp]), rel=1e-8), (f, fp)
+
+
+def test_reciprocity_and_conservation_at_order_20(oracle_mod):
+    """The largest basis of the cuboid verification (Sec. 4.1, N_p = 20,
+    231 functions) on one jittered tet with fully reflecting faces at mu = 0:
+    the reciprocity relation ties every test function to every trial function,
+    and w^T B = w^T (mass conservation, Sec. 2) constrains all 231 trial
+    columns of the (0,0) test row."""
+    V, T = _jittered_tet()
+    Np = 20
+    op = oracle_mod.assemble(V, T, np.array([0.0]), 1.0, Np, q=32)
+    N = oracle_mod.zernike_invnorm(Np)
+    sign = np.array([(-1) ** n for n, m in oracle_mod.zernike_nm(Np)])
+    fps = {f: [k for k in range(4) if k != f] for f in range(4)}
+    blk = lambda f, fp: op.blocks[f, fps[f].index(fp)]
+    for f in range(4):
+        for fp in range(4):
+            if fp != f:
+                lhs = blk(f, fp) / N[:, None]
+                rhs = (blk(fp, f) / N[:, None]).T * np.outer(sign, sign)
+                np.testing.assert_allclose(lhs, rhs, atol=1e-10)
+    A = oracle_mod.face_areas(V, T)
+    w = np.zeros((op.nrows, op.nb))
+    w[:, 0] = np.sqrt(A)
+    np.testing.assert_allclose(oracle_mod.apply(op, w, trans=True), w, atol=1e-9)

@@ -83,3 +83,30 @@ def test_parity(oracle_mod):
     Zm = oracle_mod.zernike(Np, -p[:, 0], -p[:, 1])
     sign = np.array([(-1) ** n for n, m in oracle_mod.zernike_nm(Np)])
     np.testing.assert_allclose(Zm, Zp * sign, atol=1e-13)
+
+
+def test_closed_form_and_orthogonality_at_order_20(oracle_mod):
+    """The orders of the cuboid verification (Sec. 4.1, up to N_p = 20): the
+    closed form against the paper's recursion (its alternating sums lose about
+    1e-10 near rho = 1 at n = 20) and the orthogonality relation, with Gauss in
+    u = rho^2 exact to degree 47 and a 64-point trapezoid rule in phi exact for
+    the angular products up to degree 40."""
+    Np = 20
+    rng = np.random.default_rng(20)
+    rho = np.sqrt(rng.uniform(0, 1, 100))
+    phi = rng.uniform(0, 2 * np.pi, 100)
+    Z = oracle_mod.zernike(Np, rho * np.cos(phi), rho * np.sin(phi))
+    for n, m in oracle_mod.zernike_nm(Np):
+        R = radial_by_recursion(n, m, rho)
+        ang = np.cos(m * phi) if m >= 0 else np.sin(-m * phi)
+        np.testing.assert_allclose(Z[:, oracle_mod.zernike_index(n, m)], R * ang, atol=2e-9)
+    x, w = np.polynomial.legendre.leggauss(24)
+    u = 0.5 * (x + 1)
+    wu = 0.5 * w * 0.5
+    K = 64
+    ph = 2 * np.pi * np.arange(K) / K
+    RR, PP = np.meshgrid(np.sqrt(u), ph, indexing="ij")
+    W = np.outer(wu, np.full(K, 2 * np.pi / K))
+    Z = oracle_mod.zernike(Np, (RR * np.cos(PP)).ravel(), (RR * np.sin(PP)).ravel())
+    G = Z.T @ (Z * W.ravel()[:, None])
+    np.testing.assert_allclose(G, np.diag(1.0 / oracle_mod.zernike_invnorm(Np)), atol=1e-9)
