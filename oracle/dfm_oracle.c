@@ -231,6 +231,144 @@ static double spatial_clip(const face_t* src, const vec3* dst, vec3 dst_n, vec3 
 }
 
 /* ------------------------------------------------------------------------ */
+/* Linear spatial basis on each face (the higher-order spatial               */
+/* approximation the paper suggests in Sec. 3.1 and at the end of Sec. 4.1)  */
+/* ------------------------------------------------------------------------ */
+
+/* (1/|T|) Int_T (sum_k u_k l_k)(sum_k v_k l_k) over a triangle in barycentric
+ * coordinates l_k: the mass matrix of barycentrics is |T| (1 + delta_ij) / 12. */
+static double p1_ip(const double* u, const double* v) {
+  return (u[0] * v[0] + u[1] * v[1] + u[2] * v[2] + (u[0] + u[1] + u[2]) * (v[0] + v[1] + v[2])) / 12.0;
+}
+
+/* L2-orthonormal basis of the affine functions on a face, by Gram-Schmidt of
+ * (1, l_1, l_2) in this order (l_k the barycentric coordinate of the face's
+ * k-th vertex in frame order): sqrt|T| phi_a = sum_k C[a][k] l_k. */
+static void p1_coeffs(double C[3][3]) {
+  const double F[3][3] = {{1.0, 1.0, 1.0}, {0.0, 1.0, 0.0}, {0.0, 0.0, 1.0}};
+  for (int a = 0; a < 3; ++a) {
+    double v[3] = {F[a][0], F[a][1], F[a][2]};
+    for (int c = 0; c < a; ++c) {
+      double pr = p1_ip(v, C[c]);
+      for (int k = 0; k < 3; ++k) v[k] -= pr * C[c][k];
+    }
+    double nrm = sqrt(p1_ip(v, v));
+    for (int k = 0; k < 3; ++k) C[a][k] = v[k] / nrm;
+  }
+}
+
+/* the coefficients C[a][k] of p1_coeffs, row-major (for checks) */
+void orc_p1_coeffs(double* out) {
+  double C[3][3];
+  p1_coeffs(C);
+  for (int a = 0; a < 3; ++a)
+    for (int k = 0; k < 3; ++k) out[3 * a + k] = C[a][k];
+}
+
+typedef struct { double x, y, L, b[3]; } pt2b;
+
+static int clip_half_b(const pt2b* in, int nin, pt2b* out, double a, double b, double c) {
+  int nout = 0;
+  for (int i = 0; i < nin; ++i) {
+    pt2b P = in[i], Q = in[(i + 1) % nin];
+    double fp = a * P.x + b * P.y + c, fq = a * Q.x + b * Q.y + c;
+    if (fp >= 0) out[nout++] = P;
+    if ((fp >= 0) != (fq >= 0)) {
+      double s = fp / (fp - fq);
+      pt2b R;
+      R.x = P.x + s * (Q.x - P.x);
+      R.y = P.y + s * (Q.y - P.y);
+      R.L = P.L + s * (Q.L - P.L);
+      for (int k = 0; k < 3; ++k) R.b[k] = P.b[k] + s * (Q.b[k] - P.b[k]);
+      out[nout++] = R;
+    }
+  }
+  return nout;
+}
+
+/* Linear-basis spatial matrix of direction d:
+ *   S[b][a] = Int_{s in src, ray s + t d exits through dst} (sqrt|T_l| phi_a)(s) (sqrt|T_l'| psi_b)(y(s)) exp(-mu L(s)) ds,
+ * y(s) = s + L(s) d the exit point on dst, phi the basis of the source face,
+ * psi that of the receiving row's face, whose vertex perm[k] is dst->p[k].
+ * The projection of dst onto the source plane along d carries the
+ * barycentric coordinates of y on dst, clipped together with the polygon
+ * (the projection is affine).  dS: d/dmu.  Returns S[0][0]. */
+static double spatial_clip_p1(const face_t* src, const face_t* dst, const int* perm, vec3 d, double mu, int nq,
+                              const double* gx, const double* gw, const double C[3][3], double* S, double* dS) {
+  double dn = vdot(d, src->n);
+  pt2b poly[16], tmp[16];
+  int np = 3;
+  for (int k = 0; k < 3; ++k) {
+    double t = vdot(vsub(dst->p[k], src->p[0]), src->n) / dn;
+    vec3 r = vsub(vsub(dst->p[k], vscale(d, t)), src->p[0]);
+    poly[k].x = vdot(r, src->e1);
+    poly[k].y = vdot(r, src->e2);
+    poly[k].L = t;
+    for (int c = 0; c < 3; ++c) poly[k].b[c] = c == k ? 1.0 : 0.0;
+  }
+  double sx[3], sy[3];
+  for (int k = 0; k < 3; ++k) {
+    vec3 r = vsub(src->p[k], src->p[0]);
+    sx[k] = vdot(r, src->e1);
+    sy[k] = vdot(r, src->e2);
+  }
+  double orient = (sx[1] - sx[0]) * (sy[2] - sy[0]) - (sx[2] - sx[0]) * (sy[1] - sy[0]);
+  double sgn = orient > 0 ? 1.0 : -1.0;
+  for (int k = 0; k < 3 && np > 0; ++k) {
+    int k1 = (k + 1) % 3;
+    double ex = sx[k1] - sx[k], ey = sy[k1] - sy[k];
+    double a = -sgn * ey, b = sgn * ex, c = -(a * sx[k] + b * sy[k]);
+    np = clip_half_b(poly, np, tmp, a, b, c);
+    memcpy(poly, tmp, sizeof(pt2b) * np);
+  }
+  /* source barycentrics l_1, l_2 of a plane point from the inverse edge matrix */
+  double m00 = sx[1] - sx[0], m01 = sx[2] - sx[0], m10 = sy[1] - sy[0], m11 = sy[2] - sy[0];
+  double det = m00 * m11 - m01 * m10;
+  for (int k = 0; k < 9; ++k) S[k] = dS[k] = 0.0;
+  for (int k = 1; k + 1 < np; ++k) {
+    const pt2b *A = &poly[0], *B = &poly[k], *Cc = &poly[k + 1];
+    double area = 0.5 * fabs((B->x - A->x) * (Cc->y - A->y) - (Cc->x - A->x) * (B->y - A->y));
+    for (int i = 0; i < nq; ++i) {
+      double u = 0.5 * (1.0 + gx[i]);
+      for (int j = 0; j < nq; ++j) {
+        double v = (1.0 - u) * 0.5 * (1.0 + gx[j]);
+        double w = 2.0 * area * gw[i] * gw[j] * 0.25 * (1.0 - u);
+        double x = A->x + u * (B->x - A->x) + v * (Cc->x - A->x);
+        double y = A->y + u * (B->y - A->y) + v * (Cc->y - A->y);
+        double L = A->L + u * (B->L - A->L) + v * (Cc->L - A->L);
+        double ls[3], lr[3];
+        ls[1] = (m11 * x - m01 * y) / det;
+        ls[2] = (-m10 * x + m00 * y) / det;
+        ls[0] = 1.0 - ls[1] - ls[2];
+        for (int c = 0; c < 3; ++c)
+          lr[perm[c]] = A->b[c] + u * (B->b[c] - A->b[c]) + v * (Cc->b[c] - A->b[c]);
+        double ph[3], ps[3];
+        for (int a = 0; a < 3; ++a) {
+          ph[a] = C[a][0] * ls[0] + C[a][1] * ls[1] + C[a][2] * ls[2];
+          ps[a] = C[a][0] * lr[0] + C[a][1] * lr[1] + C[a][2] * lr[2];
+        }
+        double e = exp(-mu * L);
+        for (int bb = 0; bb < 3; ++bb)
+          for (int a = 0; a < 3; ++a) {
+            S[bb * 3 + a] += w * e * ps[bb] * ph[a];
+            dS[bb * 3 + a] += w * (-L * e) * ps[bb] * ph[a];
+          }
+      }
+    }
+  }
+  return S[0];
+}
+
+/* position k' in face g's frame order of the vertex of face f at position k */
+static void face_perm(const face_t* f, const face_t* g, int* perm) {
+  for (int k = 0; k < 3; ++k) {
+    perm[k] = 0;
+    for (int k2 = 0; k2 < 3; ++k2)
+      if (f->p[k].x == g->p[k2].x && f->p[k].y == g->p[k2].y && f->p[k].z == g->p[k2].z) perm[k] = k2;
+  }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Direction sub-regions (Sec. 3.3-3.4)                                      */
 /* ------------------------------------------------------------------------ */
 
@@ -348,13 +486,20 @@ double orc_transmission(double cos_r, double c_ratio, double z_src, double z_dst
 
 static void block_fixed(const double* V, const int32_t* T, int64_t t, int f, int fp, int64_t recv_row,
                         double mu, double lam, int Np, int q, const double* gx, const double* gw, int nq_tri,
-                        const double* tx, const double* tw, int regions_mask, const media_t* md, double* out,
-                        double* dout) {
+                        const double* tx, const double* tw, int regions_mask, const media_t* md, int ns,
+                        double* out, double* dout) {
   int nb = nbasis(Np);
+  int nbe = ns * nb; /* ns spatial functions per face (1: constant, 3: linear), index s nb + idx */
   face_t src, dstf, recv;
   face_of(V, T, t, f, &src);
   face_of(V, T, t, fp, &dstf);
   face_of(V, T, recv_row / 4, (int)(recv_row % 4), &recv);
+  double Cp1[3][3];
+  int perm[3] = {0, 1, 2};
+  if (ns == 3) {
+    p1_coeffs(Cp1);
+    face_perm(&dstf, &recv, perm);
+  }
   const int kind = md ? md->kind : 0;
   const double c_ratio = kind == 1 ? md->c_ratio : 1.0;
   const int32_t* tv = T + 4 * t;
@@ -366,8 +511,8 @@ static void block_fixed(const double* V, const int32_t* T, int64_t t, int f, int
   vec3 dst_n_out = vscale(dstf.n, -1.0);
   double* Zp = (double*)malloc(sizeof(double) * nb);
   double* Zq = (double*)malloc(sizeof(double) * nb);
-  memset(out, 0, sizeof(double) * nb * nb);
-  if (dout) memset(dout, 0, sizeof(double) * nb * nb);
+  memset(out, 0, sizeof(double) * nbe * nbe);
+  if (dout) memset(dout, 0, sizeof(double) * nbe * nbe);
   for (int region = 0; region < 7; ++region) {
     if (!(regions_mask & (1 << region))) continue;
     vec3 v[4];
@@ -378,7 +523,14 @@ static void block_fixed(const double* V, const int32_t* T, int64_t t, int f, int
         vec3 d = bilinear_dir(v, gx[i], gx[j], src.n, &jac);
         double w = gw[i] * gw[j] * jac;
         double dS;
-        double S = spatial_clip(&src, dstf.p, dst_n_out, d, mu, nq_tri, tx, tw, &dS, NULL);
+        double Sm[9], dSm[9];
+        double S;
+        if (ns == 1) {
+          S = spatial_clip(&src, dstf.p, dst_n_out, d, mu, nq_tri, tx, tw, &dS, NULL);
+        } else {
+          S = spatial_clip_p1(&src, &dstf, perm, d, mu, nq_tri, tx, tw, (const double(*)[3])Cp1, Sm, dSm);
+          dS = dSm[0];
+        }
         if (S == 0.0 && dS == 0.0) continue;
         if (kind) {
           double lt = transmission(-vdot(d, dstf.n), md->c_ratio, md->z_src, md->z_dst);
@@ -392,25 +544,43 @@ static void block_fixed(const double* V, const int32_t* T, int64_t t, int f, int
         else
           zern_all(Np, (ORC_MUTATE == 10 && kind == 1 ? 1.0 / c_ratio : c_ratio) * vdot(d, recv.e1),
                    (ORC_MUTATE == 10 && kind == 1 ? 1.0 / c_ratio : c_ratio) * vdot(d, recv.e2), Zq);
-        for (int a = 0; a < nb; ++a) {
-          double wa = w * Zq[a];
-          for (int b = 0; b < nb; ++b) {
-            out[a * nb + b] += wa * S * Zp[b];
-            if (dout) dout[a * nb + b] += wa * dS * Zp[b];
+        if (ns == 1) {
+          for (int a = 0; a < nb; ++a) {
+            double wa = w * Zq[a];
+            for (int b = 0; b < nb; ++b) {
+              out[a * nb + b] += wa * S * Zp[b];
+              if (dout) dout[a * nb + b] += wa * dS * Zp[b];
+            }
           }
+        } else {
+          /* row (sb, a): test spatial function sb, Zernike a; column (sa, b) */
+          for (int sb = 0; sb < 3; ++sb)
+            for (int a = 0; a < nb; ++a) {
+              double wa = w * Zq[a];
+              double* orow = out + (int64_t)(sb * nb + a) * nbe;
+              double* drow = dout ? dout + (int64_t)(sb * nb + a) * nbe : NULL;
+              for (int sa = 0; sa < 3; ++sa) {
+                double v = wa * Sm[sb * 3 + sa], dv = wa * dSm[sb * 3 + sa];
+                for (int b = 0; b < nb; ++b) {
+                  orow[sa * nb + b] += v * Zp[b];
+                  if (drow) drow[sa * nb + b] += dv * Zp[b];
+                }
+              }
+            }
         }
       }
   }
   double sc = lam / sqrt(src.area * dstf.area);
-  for (int n = 0; n <= Np; ++n)
-    for (int m = -n; m <= n; m += 2) {
-      int a = (n * (n + 2) + m) / 2;
-      double s = sc * zern_invnorm(n, m);
-      for (int b = 0; b < nb; ++b) {
-        out[a * nb + b] *= s;
-        if (dout) dout[a * nb + b] *= s;
+  for (int sb = 0; sb < ns; ++sb)
+    for (int n = 0; n <= Np; ++n)
+      for (int m = -n; m <= n; m += 2) {
+        int a = sb * nb + (n * (n + 2) + m) / 2;
+        double s = sc * zern_invnorm(n, m);
+        for (int b = 0; b < nbe; ++b) {
+          out[a * nbe + b] *= s;
+          if (dout) dout[a * nbe + b] *= s;
+        }
       }
-    }
   free(Zp);
   free(Zq);
 }
@@ -434,8 +604,8 @@ static int blocks_adaptive(const double* V, const int32_t* T, int64_t npairs, co
                            const double* lam, const int32_t* kind, const double* c_ratio, const double* z_src,
                            const double* z_dst, int Np, int nlev, const int* qs, const int* offs,
                            const double* gx, const double* gw, int lev0, double rtol, int tri_lev,
-                           int regions_mask, int nthreads, double* out, double* dout, int32_t* q_used) {
-  int nb = nbasis(Np);
+                           int regions_mask, int ns, int nthreads, double* out, double* dout, int32_t* q_used) {
+  int nb = ns * nbasis(Np); /* block side with ns spatial functions per face */
   gl_table G = {nlev, qs, offs, gx, gw};
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);
@@ -464,14 +634,14 @@ static int blocks_adaptive(const double* V, const int32_t* T, int64_t npairs, co
         md = &mdi;
       }
       block_fixed(V, T, tet[i], f[i], fp[i], recv_row[i], mu[i], lam[i], Np, G.qs[lev], G.gx + G.offs[lev],
-                  G.gw + G.offs[lev], nt, tx, tw, regions_mask, md, o, od);
+                  G.gw + G.offs[lev], nt, tx, tw, regions_mask, md, ns, o, od);
       int accepted = rtol > 0 ? -G.qs[lev] : G.qs[lev];
       while (rtol > 0 && lev + 1 < G.nlev) {
         memcpy(prev, o, sizeof(double) * nb * nb);
         if (od) memcpy(prevd, od, sizeof(double) * nb * nb);
         ++lev;
         block_fixed(V, T, tet[i], f[i], fp[i], recv_row[i], mu[i], lam[i], Np, G.qs[lev], G.gx + G.offs[lev],
-                    G.gw + G.offs[lev], nt, tx, tw, regions_mask, md, o, od);
+                    G.gw + G.offs[lev], nt, tx, tw, regions_mask, md, ns, o, od);
         double dmax = 0.0, bmax = 0.0, ddmax = 0.0, dbmax = 0.0;
         for (int k = 0; k < nb * nb; ++k) {
           dmax = fmax(dmax, fabs(o[k] - prev[k]));
@@ -501,7 +671,17 @@ int orc_blocks(const double* V, const int32_t* T, int64_t npairs, const int64_t*
                double rtol, int tri_lev, int regions_mask, int nthreads, double* out, double* dout,
                int32_t* q_used) {
   return blocks_adaptive(V, T, npairs, tet, f, fp, recv_row, mu, lam, NULL, NULL, NULL, NULL, Np, nlev, qs, offs,
-                         gx, gw, lev0, rtol, tri_lev, regions_mask, nthreads, out, dout, q_used);
+                         gx, gw, lev0, rtol, tri_lev, regions_mask, 1, nthreads, out, dout, q_used);
+}
+
+/* As orc_blocks with the linear spatial basis (3 functions per face): blocks
+ * of side 3 nb, index s nb + idx for spatial function s and Zernike idx. */
+int orc_blocks_p1(const double* V, const int32_t* T, int64_t npairs, const int64_t* tet, const int32_t* f,
+                  const int32_t* fp, const int64_t* recv_row, const double* mu, const double* lam, int Np, int nlev,
+                  const int* qs, const int* offs, const double* gx, const double* gw, int lev0, double rtol,
+                  int tri_lev, int regions_mask, int nthreads, double* out, double* dout, int32_t* q_used) {
+  return blocks_adaptive(V, T, npairs, tet, f, fp, recv_row, mu, lam, NULL, NULL, NULL, NULL, Np, nlev, qs, offs,
+                         gx, gw, lev0, rtol, tri_lev, regions_mask, 3, nthreads, out, dout, q_used);
 }
 
 /* As orc_blocks, with per-pair media (kind, c_ratio, z_src, z_dst; see media_t). */
@@ -512,7 +692,7 @@ int orc_blocks_media(const double* V, const int32_t* T, int64_t npairs, const in
                      double rtol, int tri_lev, int regions_mask, int nthreads, double* out, double* dout,
                      int32_t* q_used) {
   return blocks_adaptive(V, T, npairs, tet, f, fp, recv_row, mu, lam, kind, c_ratio, z_src, z_dst, Np, nlev, qs,
-                         offs, gx, gw, lev0, rtol, tri_lev, regions_mask, nthreads, out, dout, q_used);
+                         offs, gx, gw, lev0, rtol, tri_lev, regions_mask, 1, nthreads, out, dout, q_used);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -532,15 +712,26 @@ static double urand(uint64_t* s) { return (splitmix64(s) >> 11) * (1.0 / 9007199
  * (a cosine-weighted inward direction), the ray traced to the face it leaves
  * through; B = lam N_{n'm'} pi sqrt(A_l/A_l') E[Z(p') Z(p) exp(-mu L) 1{exit=l'}]. */
 static int mc_block(const double* V, const int32_t* T, int64_t t, int f, int fp, int64_t recv_row, double mu,
-                    double lam, const media_t* md, int Np, int64_t nsamp, uint64_t seed, int nthreads, double* mean,
-                    double* stderr_) {
-  int nb = nbasis(Np);
+                    double lam, const media_t* md, int Np, int ns, int64_t nsamp, uint64_t seed, int nthreads,
+                    double* mean, double* stderr_) {
+  int nz = nbasis(Np);
+  int nb = ns * nz; /* block side; with ns = 3 the score carries phi_a(s) psi_b(exit point) */
   const int kind = md ? md->kind : 0;
   const double c_ratio = kind == 1 ? md->c_ratio : 1.0;
   face_t src, recv, faces[4];
   face_of(V, T, t, f, &src);
   face_of(V, T, recv_row / 4, (int)(recv_row % 4), &recv);
   for (int k = 0; k < 4; ++k) face_of(V, T, t, k, &faces[k]);
+  double Cp1[3][3];
+  p1_coeffs(Cp1);
+  /* receiving face: plane coordinates of its vertices for barycentrics */
+  double rx[3], ry[3];
+  for (int k = 0; k < 3; ++k) {
+    vec3 r = vsub(recv.p[k], recv.p[0]);
+    rx[k] = vdot(r, recv.e1);
+    ry[k] = vdot(r, recv.e2);
+  }
+  const double rdet = (rx[1] - rx[0]) * (ry[2] - ry[0]) - (rx[2] - rx[0]) * (ry[1] - ry[0]);
   double* S1 = (double*)calloc(nb * nb, sizeof(double));
   double* S2 = (double*)calloc(nb * nb, sizeof(double));
 #ifdef _OPENMP
@@ -554,6 +745,7 @@ static int mc_block(const double* V, const int32_t* T, int64_t t, int f, int fp,
     double* s2 = (double*)calloc(nb * nb, sizeof(double));
     double* Zp = (double*)malloc(sizeof(double) * nb);
     double* Zq = (double*)malloc(sizeof(double) * nb);
+    double ph[3] = {1.0, 0.0, 0.0}, ps[3] = {1.0, 0.0, 0.0};
 #pragma omp for schedule(static)
     for (int64_t chunk = 0; chunk < 1024; ++chunk) {
       /* independent stream per chunk: start at a hashed point of the 2^64 cycle */
@@ -592,12 +784,28 @@ static int mc_block(const double* V, const int32_t* T, int64_t t, int f, int fp,
         }
         zern_all(Np, px, py, Zp);
         zern_all(Np, c_ratio * vdot(d, recv.e1), c_ratio * vdot(d, recv.e2), Zq);
-        for (int a = 0; a < nb; ++a)
-          for (int b = 0; b < nb; ++b) {
-            double x = Zq[a] * Zp[b] * e;
-            s1[a * nb + b] += x;
-            s2[a * nb + b] += x * x;
+        if (ns == 3) {
+          /* source point barycentrics (1 - r1 - r2, r1, r2); exit point on the receiving face */
+          double ls[3] = {1.0 - r1 - r2, r1, r2}, lr[3];
+          vec3 y = vsub(vadd(s, vscale(d, L)), recv.p[0]);
+          double yx = vdot(y, recv.e1), yy = vdot(y, recv.e2);
+          lr[1] = (yx * (ry[2] - ry[0]) - (rx[2] - rx[0]) * yy) / rdet;
+          lr[2] = ((rx[1] - rx[0]) * yy - yx * (ry[1] - ry[0])) / rdet;
+          lr[0] = 1.0 - lr[1] - lr[2];
+          for (int a = 0; a < 3; ++a) {
+            ph[a] = Cp1[a][0] * ls[0] + Cp1[a][1] * ls[1] + Cp1[a][2] * ls[2];
+            ps[a] = Cp1[a][0] * lr[0] + Cp1[a][1] * lr[1] + Cp1[a][2] * lr[2];
           }
+        }
+        for (int sb = 0; sb < ns; ++sb)
+          for (int a = 0; a < nz; ++a)
+            for (int sa = 0; sa < ns; ++sa)
+              for (int b = 0; b < nz; ++b) {
+                double x = Zq[a] * Zp[b] * e * ps[sb] * ph[sa];
+                int k = (sb * nz + a) * nb + sa * nz + b;
+                s1[k] += x;
+                s2[k] += x * x;
+              }
       }
     }
 #pragma omp critical
@@ -608,9 +816,10 @@ static int mc_block(const double* V, const int32_t* T, int64_t t, int f, int fp,
     free(s1); free(s2); free(Zp); free(Zq);
   }
   double Adst = faces[fp].area;
+  for (int sb = 0; sb < ns; ++sb)
   for (int n = 0; n <= Np; ++n)
     for (int m = -n; m <= n; m += 2) {
-      int a = (n * (n + 2) + m) / 2;
+      int a = sb * nz + (n * (n + 2) + m) / 2;
       double sc = lam * zern_invnorm(n, m) * M_PI * sqrt(src.area / Adst);
       for (int b = 0; b < nb; ++b) {
         double m1 = S1[a * nb + b] / (double)nsamp;
@@ -626,7 +835,12 @@ static int mc_block(const double* V, const int32_t* T, int64_t t, int f, int fp,
 
 int orc_mc_block(const double* V, const int32_t* T, int64_t t, int f, int fp, int64_t recv_row, double mu,
                  double lam, int Np, int64_t nsamp, uint64_t seed, int nthreads, double* mean, double* stderr_) {
-  return mc_block(V, T, t, f, fp, recv_row, mu, lam, NULL, Np, nsamp, seed, nthreads, mean, stderr_);
+  return mc_block(V, T, t, f, fp, recv_row, mu, lam, NULL, Np, 1, nsamp, seed, nthreads, mean, stderr_);
+}
+/* As orc_mc_block with the linear spatial basis: mean, stderr_ [3 nb][3 nb]. */
+int orc_mc_block_p1(const double* V, const int32_t* T, int64_t t, int f, int fp, int64_t recv_row, double mu,
+                    double lam, int Np, int64_t nsamp, uint64_t seed, int nthreads, double* mean, double* stderr_) {
+  return mc_block(V, T, t, f, fp, recv_row, mu, lam, NULL, Np, 3, nsamp, seed, nthreads, mean, stderr_);
 }
 
 /* As orc_mc_block, with the media of the exit face (see media_t): the traced
@@ -635,7 +849,7 @@ int orc_mc_block_media(const double* V, const int32_t* T, int64_t t, int f, int 
                        int kind, double c_ratio, double z_src, double z_dst, int Np, int64_t nsamp, uint64_t seed,
                        int nthreads, double* mean, double* stderr_) {
   media_t md = {kind, c_ratio, z_src, z_dst};
-  return mc_block(V, T, t, f, fp, recv_row, mu, 1.0, &md, Np, nsamp, seed, nthreads, mean, stderr_);
+  return mc_block(V, T, t, f, fp, recv_row, mu, 1.0, &md, Np, 1, nsamp, seed, nthreads, mean, stderr_);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -669,9 +883,27 @@ void orc_spatial(const double* V, const int32_t* T, int64_t t, int f, const doub
  *   g_(l,nm) = (1/sqrt|T_l|) Int_{T_l} Z_nm(p(s->r)) cos(vartheta) exp(-mu|r-s|)/|r-s|^2 ds
  * (c = 1), with p(s->r) the tangential part of unit(r - s) in face l's frame.
  * out: [4][nb]; dout: d/dmu of the same.  Collapsed Gauss of order nq per face. */
+static void interior_g_ns(const double* V, const int32_t* T, int64_t t, const double* r, double mu, int Np,
+                          int ns, int nq, const double* gx, const double* gw, double* out, double* dout);
+
 void orc_interior_g(const double* V, const int32_t* T, int64_t t, const double* r, double mu, int Np, int nq,
                     const double* gx, const double* gw, double* out, double* dout) {
-  int nb = nbasis(Np);
+  interior_g_ns(V, T, t, r, mu, Np, 1, nq, gx, gw, out, dout);
+}
+
+/* The same with the linear spatial basis: out, dout [4][3][nb], the face
+ * integrand weighted by sqrt|T_l| phi_s(point) for s = 0, 1, 2. */
+void orc_interior_g_p1(const double* V, const int32_t* T, int64_t t, const double* r, double mu, int Np, int nq,
+                       const double* gx, const double* gw, double* out, double* dout) {
+  interior_g_ns(V, T, t, r, mu, Np, 3, nq, gx, gw, out, dout);
+}
+
+static void interior_g_ns(const double* V, const int32_t* T, int64_t t, const double* r, double mu, int Np,
+                          int ns, int nq, const double* gx, const double* gw, double* out, double* dout) {
+  int nz = nbasis(Np);
+  int nb = ns * nz;
+  double Cp1[3][3];
+  p1_coeffs(Cp1);
   double* Z = (double*)malloc(sizeof(double) * nb);
   vec3 R = v3(r[0], r[1], r[2]);
   for (int l = 0; l < 4; ++l) {
@@ -693,9 +925,13 @@ void orc_interior_g(const double* V, const int32_t* T, int64_t t, const double* 
         double cosv = vdot(dd, F.n);
         double ker = (ORC_MUTATE == 8 ? 1.0 : cosv) * exp(-mu * dist) / (dist * dist);
         zern_all(Np, vdot(dd, F.e1), vdot(dd, F.e2), Z);
-        for (int k = 0; k < nb; ++k) {
-          o[k] += w * ker * Z[k];
-          od[k] += w * (-dist) * ker * Z[k];
+        double lb[3] = {1.0 - u - v, u, v};
+        for (int sp = 0; sp < ns; ++sp) {
+          double ph = ns == 1 ? 1.0 : Cp1[sp][0] * lb[0] + Cp1[sp][1] * lb[1] + Cp1[sp][2] * lb[2];
+          for (int k = 0; k < nz; ++k) {
+            o[sp * nz + k] += w * ker * ph * Z[k];
+            od[sp * nz + k] += w * (-dist) * ker * ph * Z[k];
+          }
         }
       }
     }
@@ -722,7 +958,21 @@ typedef struct {
   const face_t* F;
   const double *gx, *gw;
   double* Z;
+  int ns, nz;         /* spatial functions per face (1 or 3), Zernike functions: nb = ns nz */
+  double C[3][3];     /* linear basis coefficients (p1_coeffs) */
+  double fx[3], fy[3]; /* face vertices in the face's plane coordinates */
 } ig_ctx;
+
+/* face barycentrics of a point of face c->F */
+static void ig_bary(const ig_ctx* c, vec3 s, double* lb) {
+  vec3 r = vsub(s, c->F->p[0]);
+  double x = vdot(r, c->F->e1), y = vdot(r, c->F->e2);
+  double a = c->fx[1] - c->fx[0], b = c->fx[2] - c->fx[0], cc = c->fy[1] - c->fy[0], d = c->fy[2] - c->fy[0];
+  double det = a * d - b * cc;
+  lb[1] = (d * x - b * y) / det;
+  lb[2] = (-cc * x + a * y) / det;
+  lb[0] = 1.0 - lb[1] - lb[2];
+}
 
 static void ig_rule(const ig_ctx* c, vec3 A, vec3 B, vec3 C, double* o, double* od) {
   vec3 e1 = vsub(B, A), e2 = vsub(C, A);
@@ -739,9 +989,14 @@ static void ig_rule(const ig_ctx* c, vec3 A, vec3 B, vec3 C, double* o, double* 
       vec3 dd = vscale(rs, 1.0 / dist);
       double ker = (ORC_MUTATE == 8 ? 1.0 : vdot(dd, c->F->n)) * exp(-c->mu * dist) / (dist * dist);
       zern_all(c->Np, vdot(dd, c->F->e1), vdot(dd, c->F->e2), c->Z);
-      for (int k = 0; k < c->nb; ++k) {
-        o[k] += w * ker * c->Z[k];
-        od[k] += w * (-dist) * ker * c->Z[k];
+      double lb[3] = {1.0, 0.0, 0.0};
+      if (c->ns == 3) ig_bary(c, s, lb);
+      for (int sp = 0; sp < c->ns; ++sp) {
+        double ph = c->ns == 1 ? 1.0 : c->C[sp][0] * lb[0] + c->C[sp][1] * lb[1] + c->C[sp][2] * lb[2];
+        for (int k = 0; k < c->nz; ++k) {
+          o[sp * c->nz + k] += w * ker * ph * c->Z[k];
+          od[sp * c->nz + k] += w * (-dist) * ker * ph * c->Z[k];
+        }
       }
     }
   }
@@ -785,15 +1040,40 @@ static void ig_adapt(const ig_ctx* c, vec3 A, vec3 B, vec3 C, const double* coar
 
 /* rho_T functional of tet t at point r with adaptive cubature (relative
  * tolerance rtol per face); layout as orc_interior_g. */
+static void interior_g_adaptive_ns(const double* V, const int32_t* T, int64_t t, const double* r, double mu,
+                                   int Np, int ns, double rtol, int nq, const double* gx, const double* gw,
+                                   double* out, double* dout);
+
 void orc_interior_g_adaptive(const double* V, const int32_t* T, int64_t t, const double* r, double mu, int Np,
                              double rtol, int nq, const double* gx, const double* gw, double* out, double* dout) {
-  int nb = nbasis(Np);
+  interior_g_adaptive_ns(V, T, t, r, mu, Np, 1, rtol, nq, gx, gw, out, dout);
+}
+
+/* The same with the linear spatial basis: out, dout [4][3][nb]. */
+void orc_interior_g_adaptive_p1(const double* V, const int32_t* T, int64_t t, const double* r, double mu, int Np,
+                                double rtol, int nq, const double* gx, const double* gw, double* out,
+                                double* dout) {
+  interior_g_adaptive_ns(V, T, t, r, mu, Np, 3, rtol, nq, gx, gw, out, dout);
+}
+
+static void interior_g_adaptive_ns(const double* V, const int32_t* T, int64_t t, const double* r, double mu,
+                                   int Np, int ns, double rtol, int nq, const double* gx, const double* gw,
+                                   double* out, double* dout) {
+  int nb = ns * nbasis(Np);
   double* Z = (double*)malloc(sizeof(double) * nb);
   double* coarse = (double*)malloc(sizeof(double) * 2 * nb);
   for (int l = 0; l < 4; ++l) {
     face_t F;
     face_of(V, T, t, l, &F);
     ig_ctx c = {v3(r[0], r[1], r[2]), mu, Np, nb, nq, &F, gx, gw, Z};
+    c.ns = ns;
+    c.nz = nbasis(Np);
+    p1_coeffs(c.C);
+    for (int k = 0; k < 3; ++k) {
+      vec3 q = vsub(F.p[k], F.p[0]);
+      c.fx[k] = vdot(q, F.e1);
+      c.fy[k] = vdot(q, F.e2);
+    }
     double* o = out + l * nb;
     double* od = dout + l * nb;
     for (int k = 0; k < nb; ++k) o[k] = od[k] = 0.0;

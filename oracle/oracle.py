@@ -48,6 +48,8 @@ def lib():
         L = ctypes.CDLL(build())
         L.orc_blocks.restype = ctypes.c_int
         L.orc_mc_block.restype = ctypes.c_int
+        L.orc_blocks_p1.restype = ctypes.c_int
+        L.orc_mc_block_p1.restype = ctypes.c_int
         L.orc_region_cos_measure.restype = ctypes.c_double
         L.orc_transmission.restype = ctypes.c_double
         L.orc_transmission.argtypes = [ctypes.c_double] * 4
@@ -198,10 +200,13 @@ class Operator:
     rblocks: np.ndarray | None = None
     rdest: np.ndarray | None = None
     drblocks: np.ndarray | None = None
+    # spatial functions per face: 1 (piecewise constant, Sec. 3.1) or 3 (the
+    # linear basis); unknowns of a row are ordered s * nbasis(Np) + Zernike idx
+    ns: int = 1
 
     @property
     def nb(self):
-        return nbasis(self.Np)
+        return self.ns * nbasis(self.Np)
 
     @property
     def nrows(self):
@@ -218,13 +223,16 @@ def pair_list(nt: int):
 
 
 def blocks_for_pairs(verts, tets, topo: Topology, mu_tet, refl_row, Np, t, f, fp, q=None, rtol=1e-13,
-                     lev0=1, with_derivative=False, regions_mask=0x0F, nthreads=0):
+                     lev0=1, with_derivative=False, regions_mask=0x0F, nthreads=0, spatial=0):
     """Blocks for the listed face pairs (t, f) -> fp.
 
     Fixed order when q is given (one of GL_ORDERS); otherwise the order doubles
     from GL_ORDERS[lev0] until the block max-norm changes by <= rtol relative.
     lambda = refl_row[recv] on boundary rows, 1 on interior faces (uniform media,
     transmission probability 1, Sec. 3.3).  The damping is mu of tet t.
+    spatial=1: the linear spatial basis (3 orthonormal functions per face:
+    Gram-Schmidt of 1, l_1, l_2 in the face's barycentric coordinates), blocks
+    of side 3 nb.
     """
     G = gl_table()
     verts = np.ascontiguousarray(verts, dtype=np.float64)
@@ -238,7 +246,7 @@ def blocks_for_pairs(verts, tets, topo: Topology, mu_tet, refl_row, Np, t, f, fp
     refl_row = np.broadcast_to(np.asarray(refl_row, dtype=np.float64), (4 * tets.shape[0],))
     lam = np.where(topo.boundary[recv], refl_row[recv], 1.0).astype(np.float64)
     lam = np.ascontiguousarray(lam)
-    nb = nbasis(Np)
+    nb = (3 if spatial else 1) * nbasis(Np)
     out = np.empty((n, nb, nb))
     dout = np.empty((n, nb, nb)) if with_derivative else None
     qu = np.empty(n, dtype=np.int32)
@@ -247,7 +255,7 @@ def blocks_for_pairs(verts, tets, topo: Topology, mu_tet, refl_row, Np, t, f, fp
         rtol = 0.0
     tri_lev = list(G.qs).index(TRI_ORDER)
     nlev = len(GL_ORDERS)
-    lib().orc_blocks(_p(verts), _p(tets, _i32p), ctypes.c_int64(n), _p(t, _i64p), _p(f, _i32p), _p(fp, _i32p),
+    (lib().orc_blocks_p1 if spatial else lib().orc_blocks)(_p(verts), _p(tets, _i32p), ctypes.c_int64(n), _p(t, _i64p), _p(f, _i32p), _p(fp, _i32p),
                      _p(recv, _i64p), _p(mu), _p(lam), ctypes.c_int(Np), ctypes.c_int(nlev), _p(G.qs, _i32p),
                      _p(G.offs, _i32p), _p(G.x), _p(G.w), ctypes.c_int(lev0), ctypes.c_double(rtol),
                      ctypes.c_int(tri_lev), ctypes.c_int(regions_mask), ctypes.c_int(nthreads), _p(out),
@@ -256,16 +264,18 @@ def blocks_for_pairs(verts, tets, topo: Topology, mu_tet, refl_row, Np, t, f, fp
 
 
 def assemble(verts, tets, mu_tet, refl, Np, q=None, rtol=1e-13, with_derivative=False, topo=None,
-             nthreads=0) -> Operator:
-    """The whole operator B (all 12 face pairs of every tet), Sec. 3.2."""
+             nthreads=0, spatial=0) -> Operator:
+    """The whole operator B (all 12 face pairs of every tet), Sec. 3.2
+    (spatial=1: the linear spatial basis, see blocks_for_pairs)."""
     topo = topo or topology(tets)
     nt = tets.shape[0]
     t, f, fp = pair_list(nt)
     out, dout, qu, recv = blocks_for_pairs(verts, tets, topo, mu_tet, refl, Np, t, f, fp, q=q, rtol=rtol,
-                                           with_derivative=with_derivative, nthreads=nthreads)
-    nb = nbasis(Np)
+                                           with_derivative=with_derivative, nthreads=nthreads, spatial=spatial)
+    ns = 3 if spatial else 1
+    nb = ns * nbasis(Np)
     return Operator(Np=Np, blocks=out.reshape(4 * nt, 3, nb, nb), dest=recv.reshape(4 * nt, 3),
-                    dblocks=None if dout is None else dout.reshape(4 * nt, 3, nb, nb), q_used=qu)
+                    dblocks=None if dout is None else dout.reshape(4 * nt, 3, nb, nb), q_used=qu, ns=ns)
 
 
 def transmission(cos_r, c_ratio, z_src, z_dst) -> float:
@@ -384,12 +394,14 @@ def spatial(verts, tets, t, f, direction, mu, nq=TRI_ORDER):
     return S, dS, A
 
 
-def mc_block(verts, tets, t, f, fp, recv_row, mu, lam, Np, nsamp=10 ** 7, seed=1, nthreads=0):
-    """Brute-force Monte Carlo ray tracing of one block: (mean, standard error)."""
-    nb = nbasis(Np)
+def mc_block(verts, tets, t, f, fp, recv_row, mu, lam, Np, nsamp=10 ** 7, seed=1, nthreads=0, spatial=0):
+    """Brute-force Monte Carlo ray tracing of one block: (mean, standard error)
+    (spatial=1: the linear spatial basis, the score weighted by the source
+    function at the ray's start and the receiving function at its exit)."""
+    nb = (3 if spatial else 1) * nbasis(Np)
     mean = np.empty((nb, nb))
     se = np.empty((nb, nb))
-    lib().orc_mc_block(_p(np.ascontiguousarray(verts, dtype=np.float64)),
+    (lib().orc_mc_block_p1 if spatial else lib().orc_mc_block)(_p(np.ascontiguousarray(verts, dtype=np.float64)),
                        _p(np.ascontiguousarray(tets, dtype=np.int32), _i32p), ctypes.c_int64(t), ctypes.c_int(f),
                        ctypes.c_int(fp), ctypes.c_int64(recv_row), ctypes.c_double(mu), ctypes.c_double(lam),
                        ctypes.c_int(Np), ctypes.c_int64(nsamp), ctypes.c_uint64(seed), ctypes.c_int(nthreads),
@@ -436,12 +448,22 @@ def dense(op: Operator) -> np.ndarray:
     return M
 
 
-def source_vector(verts, tets, rows, Np, weights=None) -> np.ndarray:
+def p1_coeffs() -> np.ndarray:
+    """C[a][k] of the linear spatial basis: sqrt|T| phi_a = sum_k C[a][k] l_k
+    with l_k the barycentric coordinate of the face's k-th vertex (frame order)."""
+    out = np.empty(9)
+    lib().orc_p1_coeffs(_p(out))
+    return out.reshape(3, 3)
+
+
+def source_vector(verts, tets, rows, Np, weights=None, spatial=0) -> np.ndarray:
     """Galerkin coefficients of a unit isotropic density on boundary face rows:
     rho0 = 1 on Q_row projects onto b_l Z_0^0 with coefficient sqrt(|T_l|) * 1
     (b_l = 1/sqrt|T_l|, the Zernike (0,0) inverse norm 1/pi times the disc area pi),
-    and to zero on every other basis function (Sec. 3.1-3.2).  [nrows, nb]."""
-    nb = nbasis(Np)
+    and to zero on every other basis function (Sec. 3.1-3.2).  [nrows, nb]
+    (spatial=1: nb = 3 nbasis(Np); the linear functions have zero mean, so the
+    coefficient sits on the constant one, index 0, as well)."""
+    nb = (3 if spatial else 1) * nbasis(Np)
     area = face_areas(verts, tets)
     x = np.zeros((4 * tets.shape[0], nb))
     w = np.ones(len(rows)) if weights is None else weights
@@ -470,14 +492,17 @@ def face_frames(verts, tets):
     return e1, e2, nn
 
 
-def source_directed(verts, tets, rows, Np, dirs=None, combine=False) -> np.ndarray:
+def source_directed(verts, tets, rows, Np, dirs=None, combine=False, spatial=0) -> np.ndarray:
     """Galerkin coefficients of a unit density travelling in one direction d on
     each listed face (Sec. 4.1, Eq. RhoNeumann for d = the inward normal).  The
     density delta(p - p_d), p_d = (d.e1, d.e2), projected onto the basis of
     Eq. FBApprox: coefficient (n, m) = (inverse norm N_nm) * <delta, Z_n^m> *
     <1_T, 1/sqrt|T|> = N_nm Z_n^m(p_d) sqrt|T|.  dirs None = inward normals.
-    Returns [n_src, rows, nb], or [rows, nb] summed when combine is set."""
-    nb = nbasis(Np)
+    Returns [n_src, rows, nb], or [rows, nb] summed when combine is set
+    (spatial=1: nb = 3 nbasis(Np), a constant density projects onto the
+    constant spatial function only, the first nbasis(Np) entries)."""
+    nz = nbasis(Np)
+    nb = (3 if spatial else 1) * nz
     rows = np.atleast_1d(np.asarray(rows, dtype=np.int64))
     area = face_areas(verts, tets)
     e1, e2, nn = face_frames(verts, tets)
@@ -492,7 +517,7 @@ def source_directed(verts, tets, rows, Np, dirs=None, combine=False) -> np.ndarr
             if not d @ nn[r] > 0:
                 raise ValueError("direction does not enter the tet")
             p = (d @ e1[r], d @ e2[r])
-        out[s, r] = inv * zernike(Np, p[0], p[1])[0] * np.sqrt(area[r])
+        out[s, r, :nz] = inv * zernike(Np, p[0], p[1])[0] * np.sqrt(area[r])
     return out.sum(axis=0) if combine else out
 
 
@@ -549,10 +574,19 @@ def point_source(verts, tets, r0, Np, mu_tet, refl, strength=1.0, nq=48, topo=No
     return out
 
 
-def tet_density(verts, tets, mu_tet, Np, rho, nq=48, rtol=1e-11, nthreads=0) -> np.ndarray:
+def tet_density(verts, tets, mu_tet, Np, rho, nq=48, rtol=1e-11, nthreads=0, spatial=0) -> np.ndarray:
     """rho_T at every tet centroid (Sec. 4.1, Eq. IntDens) for rho [rows, nb]:
     the per-tet functional g_t of interior_g applied to the tet's four rows
-    (nq=None: adaptive cubature to rtol, all tets in parallel)."""
+    (nq=None: adaptive cubature to rtol, all tets in parallel; spatial=1: the
+    linear spatial basis, one tet after the other)."""
+    if spatial:
+        cen = centroids(verts, tets)
+        mu_b = np.broadcast_to(np.asarray(mu_tet, dtype=np.float64), (tets.shape[0],))
+        out = np.empty(tets.shape[0])
+        for t in range(tets.shape[0]):
+            g, _ = interior_g(verts, tets, t, cen[t], float(mu_b[t]), Np, nq=nq, rtol=rtol, spatial=1)
+            out[t] = np.sum(g * rho[4 * t:4 * t + 4])
+        return out
     if nq is None:
         nt = tets.shape[0]
         nb = nbasis(Np)
@@ -670,23 +704,26 @@ def centroids(verts, tets):
     return verts[tets].mean(axis=1)
 
 
-def interior_g(verts, tets, t, r, mu, Np, nq=48, rtol=1e-11):
+def interior_g(verts, tets, t, r, mu, Np, nq=48, rtol=1e-11, spatial=0):
     """g[4, nb] and dg/dmu with rho_T(r) = sum_{l,nm} rho_(t,l,nm) g[l,nm]
     (Sec. 4.1, Eq. IntDens): a fixed collapsed Gauss rule of order nq on each
-    face, or, with nq=None, adaptive 4-way refinement of each face to rtol."""
-    nb = nbasis(Np)
+    face, or, with nq=None, adaptive 4-way refinement of each face to rtol.
+    spatial=1: the linear spatial basis, g[4, 3 nb] with the integrand weighted
+    by each face function sqrt|T_l| phi_s at the face point."""
+    nb = (3 if spatial else 1) * nbasis(Np)
     g = np.empty((4, nb))
     dg = np.empty((4, nb))
     rr = np.ascontiguousarray(r, dtype=np.float64)
     if nq is None:
         x, w = np.polynomial.legendre.leggauss(8)
-        lib().orc_interior_g_adaptive(_p(np.ascontiguousarray(verts, dtype=np.float64)),
+        (lib().orc_interior_g_adaptive_p1 if spatial else lib().orc_interior_g_adaptive)(
+                                      _p(np.ascontiguousarray(verts, dtype=np.float64)),
                                       _p(np.ascontiguousarray(tets, dtype=np.int32), _i32p), ctypes.c_int64(int(t)),
                                       _p(rr), ctypes.c_double(mu), ctypes.c_int(Np), ctypes.c_double(rtol),
                                       ctypes.c_int(8), _p(x), _p(w), _p(g), _p(dg))
         return g, dg
     x, w = np.polynomial.legendre.leggauss(nq)
-    lib().orc_interior_g(_p(np.ascontiguousarray(verts, dtype=np.float64)),
+    (lib().orc_interior_g_p1 if spatial else lib().orc_interior_g)(_p(np.ascontiguousarray(verts, dtype=np.float64)),
                          _p(np.ascontiguousarray(tets, dtype=np.int32), _i32p), ctypes.c_int64(int(t)), _p(rr),
                          ctypes.c_double(mu), ctypes.c_int(Np), ctypes.c_int(nq), _p(x), _p(w), _p(g), _p(dg))
     return g, dg
