@@ -107,8 +107,8 @@ PY_MUTANTS = {
         "source_vector", "x[int(r), 0] += wt * np.sqrt(area[int(r)])", "x[int(r), 0] += wt * area[int(r)]",
         lambda O: source.test_tet_density_of_an_isotropic_face_is_its_solid_angle(O)),
     "directed source: inverse norm dropped": (
-        "source_directed", "out[s, r] = inv * zernike(Np, p[0], p[1])[0] * np.sqrt(area[r])",
-        "out[s, r] = zernike(Np, p[0], p[1])[0] * np.sqrt(area[r])",
+        "source_directed", "out[s, r, :nz] = inv * zernike(Np, p[0], p[1])[0] * np.sqrt(area[r])",
+        "out[s, r, :nz] = zernike(Np, p[0], p[1])[0] * np.sqrt(area[r])",
         lambda O: source.test_normal_incidence_closed_form(O)),
     "face frames: left-handed": (
         "face_frames", "e1[f::4], nn[f::4], e2[f::4] = u, n, np.cross(n, u)",
