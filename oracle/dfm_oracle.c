@@ -238,7 +238,8 @@ static double spatial_clip(const face_t* src, const vec3* dst, vec3 dst_n, vec3 
 /* (1/|T|) Int_T (sum_k u_k l_k)(sum_k v_k l_k) over a triangle in barycentric
  * coordinates l_k: the mass matrix of barycentrics is |T| (1 + delta_ij) / 12. */
 static double p1_ip(const double* u, const double* v) {
-  return (u[0] * v[0] + u[1] * v[1] + u[2] * v[2] + (u[0] + u[1] + u[2]) * (v[0] + v[1] + v[2])) / 12.0;
+  return (u[0] * v[0] + u[1] * v[1] + u[2] * v[2] +
+          (ORC_MUTATE == 13 ? 0.0 : 1.0) * (u[0] + u[1] + u[2]) * (v[0] + v[1] + v[2])) / 12.0;
 }
 
 /* L2-orthonormal basis of the affine functions on a face, by Gram-Schmidt of
@@ -342,6 +343,8 @@ static double spatial_clip_p1(const face_t* src, const face_t* dst, const int* p
         ls[0] = 1.0 - ls[1] - ls[2];
         for (int c = 0; c < 3; ++c)
           lr[perm[c]] = A->b[c] + u * (B->b[c] - A->b[c]) + v * (Cc->b[c] - A->b[c]);
+        if (ORC_MUTATE == 12) /* the receiving function read at the source point */
+          for (int c = 0; c < 3; ++c) lr[c] = ls[c];
         double ph[3], ps[3];
         for (int a = 0; a < 3; ++a) {
           ph[a] = C[a][0] * ls[0] + C[a][1] * ls[1] + C[a][2] * ls[2];

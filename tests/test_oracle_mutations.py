@@ -6,7 +6,8 @@ Zernike polynomials, a dropped normalisation factor, the wrong face frame for
 the receiving face, a halved damping exponent, a transposed operator, an
 unnormalised tangent axis, a missing clip of the integration triangle, a dropped
 cosine in the interior density, swapped impedances in the transmission law,
-an inverted Snell ratio and a reflection weighted like a transmission.  A second set plants mistakes in the oracle's
+an inverted Snell ratio, a reflection weighted like a transmission, and two in the
+linear spatial basis (the receiving function read at the ray's start, a wrong mass matrix).  A second set plants mistakes in the oracle's
 Python half (a reversed point-source ray, |T| for sqrt|T|, a dropped inverse
 norm, a left-handed frame, a left-out reflection part) by rewriting one line of
 the function's source.  Only the oracle is mutated, on the CPU."""
@@ -18,6 +19,7 @@ import pytest
 
 import test_oracle_blocks as blocks
 import test_oracle_media as media
+import test_oracle_p1 as p1
 import test_oracle_solve as solve
 import test_oracle_source as source
 import test_oracle_zernike as zernike
@@ -34,6 +36,8 @@ MUTANTS = {
     9: "impedances swapped in the transmission law",
     10: "inverted Snell ratio for the transmitted direction",
     11: "interface reflection weighted by lambda_t instead of 1 - lambda_t",
+    12: "linear spatial basis: receiving function read at the source point",
+    13: "linear spatial basis: Gram-Schmidt with a wrong mass matrix",
 }
 
 
@@ -60,6 +64,8 @@ def _build_mutant(O, k, outdir):
     os.remove(so)  # the loaded copy stays mapped
     L.orc_blocks.restype = ctypes.c_int
     L.orc_mc_block.restype = ctypes.c_int
+    L.orc_blocks_p1.restype = ctypes.c_int
+    L.orc_mc_block_p1.restype = ctypes.c_int
     L.orc_region_cos_measure.restype = ctypes.c_double
     L.orc_transmission.restype = ctypes.c_double
     L.orc_transmission.argtypes = [ctypes.c_double] * 4
@@ -81,6 +87,10 @@ def test_a_pin_fails_on_each_planted_mistake(oracle_mod, k):
             pins = [lambda: media.test_monte_carlo_across_an_interface(oracle_mod, 1)]
         if k == 11:
             pins = [lambda: media.test_conservation_with_unequal_media(oracle_mod)]
+        if k == 12:
+            pins = [lambda: p1.test_reciprocity_linear_basis(oracle_mod, 0.8)]
+        if k == 13:
+            pins = [lambda: p1.test_linear_basis_is_orthonormal(oracle_mod)]
         for pin in pins:
             try:
                 pin()
