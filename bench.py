@@ -1019,7 +1019,9 @@ def run_cuboid(args):
     solves to an FP64 relative residual of 1e-10 and reads rho_T at every
     centroid (Eq. IntDens); the line gives each case's median step time and
     the relative mean error (mean |rho_T - rho*| / mean rho*) against the
-    exact ray solution rho* of Eq. ExactSol."""
+    exact ray solution rho* of Eq. ExactSol.  Each order runs with the
+    piecewise-constant spatial function per face and, up to N_p = 8, with the
+    linear spatial basis (three functions per face)."""
     import torch
 
     from paper_1608_04607_gb300 import dfm
@@ -1029,6 +1031,7 @@ def run_cuboid(args):
     mu, length = 0.4 * np.pi, 2.0
     cases = []
     plan = []
+    spatials = [int(v) for v in args.cuboid_spatial.split(",")]
     for part in args.cuboid_cases.split(";"):
         n_s, nps = part.split(":")
         plan.append((int(n_s), [int(v) for v in nps.split(",")]))
@@ -1039,15 +1042,16 @@ def run_cuboid(args):
         x = m.verts[m.tets].mean(axis=1)[:, 0]
         exact = (np.exp(-mu * x) + np.exp(-mu * (2 * length - x))) / (1 - np.exp(-2 * mu * length))
         tets = np.arange(m.n_tets)
-        for Np in nps:
-            op = dfm.Operator(mesh, Np, mu=mu, precision=dfm.F32)
+        for Np, spatial in [(a, b) for b in spatials for a in nps if b == 0 or a <= 8]:
+            code = dfm.basis(Np, spatial)
+            op = dfm.Operator(mesh, code, mu=mu, precision=dfm.F32)
 
             def step():
                 op.reassemble(mu)
-                rho0 = dfm.source_directed(mesh, Np, rows, combine=True)
+                rho0 = dfm.source_directed(mesh, code, rows, combine=True)
                 rho, info = op.solve(rho0, tol=1e-10)
-                g, _ = dfm.interior_density(mesh, Np, tets, mu=mu)
-                return dfm.tet_density(mesh, Np, g, rho), info
+                g, _ = dfm.interior_density(mesh, code, tets, mu=mu)
+                return dfm.tet_density(mesh, code, g, rho), info
 
             for _ in range(max(args.warmup, 1)):
                 step()
@@ -1062,14 +1066,15 @@ def run_cuboid(args):
                 times.append(ev[0].elapsed_time(ev[1]))
             d = dens.cpu().numpy()
             err = float(np.mean(np.abs(d - exact)) / np.mean(exact))
-            cases.append({"n_tets": m.n_tets, "Np": Np, "ms_per_step": statistics.median(times),
+            cases.append({"n_tets": m.n_tets, "Np": Np, "spatial": "linear" if spatial else "constant",
+                          "unknowns_per_face": op.nb, "ms_per_step": statistics.median(times),
                           "rel_mean_err": err, "operator_applications": info.iters, "resid": info.resid})
             op.close()
         mesh.close()
     best = min(cases, key=lambda c: c["rel_mean_err"])
     print(json.dumps({"metric": "cuboid relative mean error against the exact ray solution", "mode": "cuboid",
                       "value": best["rel_mean_err"], "unit": "fraction", "higher_is_better": False,
-                      "best_case": {"n_tets": best["n_tets"], "Np": best["Np"]},
+                      "best_case": {"n_tets": best["n_tets"], "Np": best["Np"], "spatial": best["spatial"]},
                       "steps": args.steps, "warmup": args.warmup, "data": "synthetic",
                       "config": {"workload": "kuhn cuboid 2 x 1 x 1, " + args.cuboid_cases + " (cells per unit length: "
                                              "basis orders)",
@@ -1291,6 +1296,8 @@ def main():
     ap.add_argument("--fd", type=int, default=0, help="adjoint mode: elements checked by central differences")
     ap.add_argument("--cuboid-cases", default="4:4,6,8,10,12,16,20;8:4,6,8,12,16",
                     help="cuboid mode: 'n:Np,Np,...;n:...' (n cells per unit length, basis orders)")
+    ap.add_argument("--cuboid-spatial", default="0,1",
+                    help="cuboid mode: spatial bases per face, 0 = constant, 1 = linear (orders <= 8 only)")
     ap.add_argument("--e2e-steps", type=int, default=0,
                     help="default workload: steps of the e2e measurement (0 = one job)")
     ap.add_argument("--no-extra", action="store_true", help="default workload: skip the 48,000-tet solve's key")

@@ -70,6 +70,19 @@ extern "C" {
 #define DFM_F16 3
 #define DFM_FP8E4M3 4 /* preconditioner copy only: e4m3 values with one FP32 scale per operator row */
 
+/* Basis codes.  Every argument named Np takes the momentum order N_p in its
+ * low 8 bits and the spatial basis on each face in the bits above:
+ * DFM_BASIS(Np, 0) = Np is the paper's piecewise-constant function per face
+ * (Sec. 3.1), N_b = (Np+1)(Np+2)/2 unknowns per face (row); DFM_BASIS(Np, 1)
+ * is the linear basis, the finer spatial approximation Sec. 3.1 and the end
+ * of Sec. 4.1 point to: three orthonormal affine functions per face, from
+ * Gram-Schmidt of (1, l_1, l_2) with l_k the barycentric coordinate of the
+ * face's k-th vertex in frame order (the vertex order of the face frame),
+ * 3 N_b unknowns per row ordered s N_b + (Zernike index), s = 0 the constant.
+ * The linear basis is built for Np <= 8, FP32 blocks, uniform media, moment 0,
+ * without the adjoint contraction and point sources. */
+#define DFM_BASIS(Np, s) ((Np) | ((s) << 8))
+
 /* stationary solvers */
 #define DFM_SOLVE_NEUMANN 0   /* x <- rho0 + B x (Eq. NSum), FP64 */
 #define DFM_SOLVE_GMRES 1     /* restarted GMRES on (I - B) x = rho0 in the operator's precision */

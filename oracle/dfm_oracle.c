@@ -877,6 +877,24 @@ void orc_spatial(const double* V, const int32_t* T, int64_t t, int f, const doub
   }
 }
 
+/* The linear-basis spatial matrix S[b][a] of spatial_clip_p1 for the pair
+ * (t, f) -> (t, fp) received by recv_row, direction dir (unit after
+ * normalisation), for checks. */
+void orc_spatial_p1(const double* V, const int32_t* T, int64_t t, int f, int fp, int64_t recv_row,
+                    const double* dir, double mu, int nq, const double* gx, const double* gw, double* out,
+                    double* dout) {
+  face_t src, dstf, recv;
+  face_of(V, T, t, f, &src);
+  face_of(V, T, t, fp, &dstf);
+  face_of(V, T, recv_row / 4, (int)(recv_row % 4), &recv);
+  double C[3][3];
+  int perm[3];
+  p1_coeffs(C);
+  face_perm(&dstf, &recv, perm);
+  spatial_clip_p1(&src, &dstf, perm, vunit(v3(dir[0], dir[1], dir[2])), mu, nq, gx, gw, (const double(*)[3])C, out,
+                  dout);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Interior density functional (Sec. 4.1, Eq. IntDens)                      */
 /* ------------------------------------------------------------------------ */

@@ -394,6 +394,22 @@ def spatial(verts, tets, t, f, direction, mu, nq=TRI_ORDER):
     return S, dS, A
 
 
+def spatial_p1(verts, tets, t, f, fp, recv_row, direction, mu, nq=TRI_ORDER):
+    """The linear-basis spatial matrix S[b][a] = Int (sqrt|T_l| phi_a)(s)
+    (sqrt|T_l'| psi_b)(exit point) exp(-mu L(s)) ds over the source points of
+    face (t, f) whose ray in `direction` leaves through face fp (received by
+    recv_row), by clipping; and its mu-derivative.  [3, 3] each."""
+    x, w = np.polynomial.legendre.leggauss(nq)
+    S = np.empty(9)
+    dS = np.empty(9)
+    lib().orc_spatial_p1(_p(np.ascontiguousarray(verts, dtype=np.float64)),
+                         _p(np.ascontiguousarray(tets, dtype=np.int32), _i32p), ctypes.c_int64(t), ctypes.c_int(f),
+                         ctypes.c_int(fp), ctypes.c_int64(recv_row),
+                         _p(np.ascontiguousarray(direction, dtype=np.float64)), ctypes.c_double(mu), ctypes.c_int(nq),
+                         _p(x), _p(w), _p(S), _p(dS))
+    return S.reshape(3, 3), dS.reshape(3, 3)
+
+
 def mc_block(verts, tets, t, f, fp, recv_row, mu, lam, Np, nsamp=10 ** 7, seed=1, nthreads=0, spatial=0):
     """Brute-force Monte Carlo ray tracing of one block: (mean, standard error)
     (spatial=1: the linear spatial basis, the score weighted by the source

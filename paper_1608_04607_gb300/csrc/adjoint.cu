@@ -286,8 +286,10 @@ using namespace dfm;
 extern "C" int dfm_interior_density(const dfm_mesh* mesh, int Np, const double* mu, double mu_uniform,
                                     const int64_t* tets_host, const double* weights_host, int n, int nq, double* gvec,
                                     double* dgvec, void* stream) {
-  if (!mesh || !tets_host || !gvec || n < 1 || Np < 0 || Np > geom::kWideMaxNp)
+  if (!mesh || !tets_host || !gvec || n < 1 || !basis_ok(Np, geom::kWideMaxNp))
     return set_error(DFM_ERR_ARG, "dfm_interior_density: bad argument");
+  const int ns = basis_ns(Np);
+  Np = basis_np(Np);
   // nq < 0: the split polar rule with |nq| points per direction; nq = 0: the
   // same rule with 24 points (accurate for centroids close to a face, as on
   // thin tets); nq > 0: the flat collapsed Gauss rule of that order
@@ -324,17 +326,18 @@ extern "C" int dfm_interior_density(const dfm_mesh* mesh, int Np, const double* 
       interior_density_kernel<N><<<blocks, 128, 0, st>>>(mesh->verts, mesh->tets, mesh->geom, mu, mu_uniform, list, \
                                                          wp, n, glx, glw, nq, gvec, dgvec);                      \
     break;
-  switch (Np) {
+  switch (ns == 1 ? Np : -1) {
     CASE(0) CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
-    default:  // Np = 9..20 (wide.cu)
-      rc = launch_interior_density_wide(Np, polar, mesh, mu, mu_uniform, list, wp, n, glx, glw, nq, gvec, dgvec, st);
+    default:  // Np = 9..20, and the linear spatial basis (wide.cu)
+      rc = launch_interior_density_wide(Np, ns, polar, mesh, mu, mu_uniform, list, wp, n, glx, glw, nq, gvec, dgvec,
+                                        st);
       if (rc) {
         cudaFreeAsync(buf, st);
         return rc;
       }
   }
 #undef CASE
-  if (Np <= 8) DFM_LAUNCHED();
+  if (Np <= 8 && ns == 1) DFM_LAUNCHED();
   DFM_CUDA_CHECK(cudaGetLastError());
   DFM_CUDA_CHECK(cudaFreeAsync(buf, st));
   return DFM_OK;
@@ -342,13 +345,13 @@ extern "C" int dfm_interior_density(const dfm_mesh* mesh, int Np, const double* 
 
 extern "C" int dfm_tet_density(const dfm_mesh* mesh, int Np, const double* gvec, const double* rho, int R,
                                double* out, void* stream) {
-  if (!mesh || !gvec || !rho || !out || R < 1 || Np < 0 || Np > geom::kWideMaxNp)
+  if (!mesh || !gvec || !rho || !out || R < 1 || !basis_ok(Np, geom::kWideMaxNp))
     return set_error(DFM_ERR_ARG, "dfm_tet_density: bad argument");
   const int64_t units = (int64_t)R * mesh->nt;
   const int64_t blocks = (units + 7) / 8;  // 8 warps per block
   if (blocks > 0x7fffffff) return set_error(DFM_ERR_ARG, "dfm_tet_density: too many right-hand sides");
   cudaStream_t st = as_stream(stream);
-  tet_density_kernel<<<(unsigned)blocks, 256, 0, st>>>(gvec, rho, mesh->nt, nbasis(Np), units, out);
+  tet_density_kernel<<<(unsigned)blocks, 256, 0, st>>>(gvec, rho, mesh->nt, basis_size(Np), units, out);
   DFM_LAUNCHED();
   DFM_CUDA_CHECK(cudaGetLastError());
   return DFM_OK;
@@ -359,8 +362,11 @@ extern "C" int dfm_adjoint(const dfm_op* op, const dfm_params* params, const dou
                            void* stream, dfm_solve_info* info) {
   if (!op || !params || !rho || !gvec || !lambda_out || !dJ_dmu || !opts || R < 1)
     return set_error(DFM_ERR_ARG, "dfm_adjoint: bad argument");
-  if (params->Np != op->Np) return set_error(DFM_ERR_ARG, "dfm_adjoint: params->Np differs from the operator's");
-  if (op->Np > 8) return set_error(DFM_ERR_UNSUPPORTED, "dfm_adjoint: the dB/dmu contraction is built for Np <= 8");
+  if (basis_np(params->Np) != op->Np || basis_ns(params->Np) != op->ns)
+    return set_error(DFM_ERR_ARG, "dfm_adjoint: params->Np differs from the operator's");
+  if (op->Np > 8 || op->ns > 1)
+    return set_error(DFM_ERR_UNSUPPORTED,
+                     "dfm_adjoint: the dB/dmu contraction is built for Np <= 8 and the piecewise-constant basis");
   const dfm_mesh* mesh = op->mesh;
   cudaStream_t st = as_stream(stream);
   // 1. adjoint equation (I - B)^T lambda = g

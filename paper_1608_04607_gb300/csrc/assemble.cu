@@ -301,13 +301,18 @@ int dispatch_np(int Np, const PairConst* pairs, int64_t npairs, const double* gl
 
 int check_params(const dfm_mesh* mesh, const dfm_params* p) {
   if (!mesh || !p) return set_error(DFM_ERR_ARG, "dfm_assemble: NULL mesh or params");
-  if (p->Np < 0 || p->Np > geom::kWideMaxNp) return set_error(DFM_ERR_ARG, "dfm_assemble: Np must be in 0..20");
+  if (!basis_ok(p->Np, geom::kWideMaxNp))
+    return set_error(DFM_ERR_ARG, "dfm_assemble: Np must be in 0..20 (0..8 with the linear spatial basis)");
+  const int np = basis_np(p->Np);
   if (p->precision != DFM_F32 && p->precision != DFM_F64 && p->precision != DFM_BF16)
     return set_error(DFM_ERR_UNSUPPORTED, "dfm_assemble: precision must be DFM_F32, DFM_F64 or DFM_BF16");
-  if (p->Np > 8 && p->precision != DFM_F32)
+  if (np > 8 && p->precision != DFM_F32)
     return set_error(DFM_ERR_UNSUPPORTED, "dfm_assemble: Np above 8 is built for DFM_F32 only");
+  if (basis_ns(p->Np) > 1 && (p->precision != DFM_F32 || p->moment != 0 || p->c || p->rho_f))
+    return set_error(DFM_ERR_UNSUPPORTED,
+                     "dfm_assemble: the linear spatial basis is built for DFM_F32, moment 0 and uniform media");
   if (!p->mu && !(p->mu_uniform >= 0.0)) return set_error(DFM_ERR_ARG, "dfm_assemble: mu_uniform must be >= 0");
-  const int q = p->quad_order ? p->quad_order : p->Np + 6;
+  const int q = p->quad_order ? p->quad_order : np + 6;
   if (q < 1 || q > kMaxQ) return set_error(DFM_ERR_ARG, "dfm_assemble: quad_order must be in 1..32");
   const double deg = p->max_patch_deg > 0 ? p->max_patch_deg : 60.0;
   if (!(deg >= 10.0 && deg <= 180.0)) return set_error(DFM_ERR_ARG, "dfm_assemble: max_patch_deg must be in [10, 180]");
@@ -330,6 +335,7 @@ int ensure_reflection(dfm_op* op, cudaStream_t st) {
   dfm_op* r = new dfm_op();
   r->mesh = op->mesh;
   r->Np = op->Np;
+  r->ns = op->ns;
   r->nb = op->nb;
   r->precision = op->precision;
   r->nrows = op->nrows;
@@ -360,19 +366,23 @@ using namespace dfm;
 extern "C" int dfm_assemble_into(const dfm_mesh* mesh, const dfm_params* p, dfm_op* op, void* stream) {
   int rc = check_params(mesh, p);
   if (rc) return rc;
-  if (!op || op->mesh != mesh || op->Np != p->Np || op->precision != p->precision)
+  if (!op || op->mesh != mesh || op->Np != basis_np(p->Np) || op->ns != basis_ns(p->Np) ||
+      op->precision != p->precision)
     return set_error(DFM_ERR_ARG, "dfm_assemble_into: operator does not match mesh/Np/precision");
+  const int np = op->Np;
   cudaStream_t st = as_stream(stream);
   op->lp_valid = false;  // the low-precision preconditioner copies follow the blocks
   op->lpT_valid = false;
   op->mu_uniform = p->mu ? -1.0 : p->mu_uniform;
   op->moment = p->moment;
-  const int q = p->quad_order ? p->quad_order : p->Np + 6;
+  const int q = p->quad_order ? p->quad_order : np + 6;
   const double deg = p->max_patch_deg > 0 ? p->max_patch_deg : 60.0;
   const float cos_max = (float)cos(deg * M_PI / 180.0);
   const int64_t npairs = 12 * mesh->nt;
   // scratch: per-pair constants and the Gauss table, kept with the operator
-  const int64_t need = npairs * (int64_t)sizeof(PairConst) + 2 * 64 * (int64_t)sizeof(double) + 256;
+  // (the linear spatial basis adds two words of vertex positions per pair)
+  const int64_t base_need = npairs * (int64_t)sizeof(PairConst) + 2 * 64 * (int64_t)sizeof(double) + 256;
+  const int64_t need = base_need + (op->ns > 1 ? 8 * npairs : 0);
   if (op->work_bytes < need) {
     cudaFree(op->work);
     op->work = nullptr;
@@ -410,14 +420,17 @@ extern "C" int dfm_assemble_into(const dfm_mesh* mesh, const dfm_params* p, dfm_
                                                                          p->rho_f, part);
     DFM_LAUNCHED();
     DFM_CUDA_CHECK(cudaGetLastError());
-    if (op->precision == DFM_F32)
-      rc = dispatch_np<float>(p->Np, pairs, npairs, glx, glw, q, cos_max, (float*)dst->vals, op->row_stride, nodes,
+    if (op->ns > 1)
+      rc = launch_assemble_p1(mesh, np, pairs, reinterpret_cast<char*>(op->work) + base_need, npairs, glx, glw, q,
+                              cos_max, (float*)dst->vals, op->row_stride, nodes, st);
+    else if (op->precision == DFM_F32)
+      rc = dispatch_np<float>(np, pairs, npairs, glx, glw, q, cos_max, (float*)dst->vals, op->row_stride, nodes,
                               p->moment, st);
     else if (op->precision == DFM_BF16)
-      rc = dispatch_np<float, __nv_bfloat16>(p->Np, pairs, npairs, glx, glw, q, cos_max,
+      rc = dispatch_np<float, __nv_bfloat16>(np, pairs, npairs, glx, glw, q, cos_max,
                                              (__nv_bfloat16*)dst->vals, op->row_stride, nodes, p->moment, st);
     else
-      rc = dispatch_np<double>(p->Np, pairs, npairs, glx, glw, q, cos_max, (double*)dst->vals, op->row_stride,
+      rc = dispatch_np<double>(np, pairs, npairs, glx, glw, q, cos_max, (double*)dst->vals, op->row_stride,
                                nodes, p->moment, st);
     if (rc) return rc;
   }
@@ -431,8 +444,9 @@ extern "C" int dfm_assemble(const dfm_mesh* mesh, const dfm_params* p, void* str
   if (rc) return rc;
   dfm_op* op = new dfm_op();
   op->mesh = mesh;
-  op->Np = p->Np;
-  op->nb = nbasis(p->Np);
+  op->Np = basis_np(p->Np);
+  op->ns = basis_ns(p->Np);
+  op->nb = basis_size(p->Np);
   op->precision = p->precision;
   op->nrows = mesh->nrows;
   op->row_stride = op_row_stride(op->nb);
@@ -485,7 +499,7 @@ extern "C" void dfm_op_destroy(dfm_op* op) {
 
 extern "C" int dfm_op_info(const dfm_op* op, dfm_op_info_t* info) {
   if (!op || !info) return set_error(DFM_ERR_ARG, "dfm_op_info: NULL argument");
-  info->Np = op->Np;
+  info->Np = op->ns > 1 ? DFM_BASIS(op->Np, 1) : op->Np;
   info->nb = op->nb;
   info->precision = op->precision;
   info->n_rows = op->nrows;

@@ -25,6 +25,21 @@ inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s
 
 inline int nbasis(int Np) { return (Np + 1) * (Np + 2) / 2; }
 
+// basis codes of the C ABI (DFM_BASIS): momentum order, spatial functions
+// per face, unknowns per row
+inline int basis_np(int code) { return code & 0xff; }
+inline int basis_ns(int code) { return (code >> 8) == 1 ? 3 : 1; }
+inline int basis_size(int code) { return basis_ns(code) * nbasis(basis_np(code)); }
+// a valid code: order 0..max_np, spatial basis 0 or 1 (the linear one up to order 8)
+inline bool basis_ok(int code, int max_np) {
+  const int s = code >> 8, np = code & 0xff;
+  return code >= 0 && (s == 0 || s == 1) && np <= max_np && (s == 0 || np <= 8);
+}
+// the basis sizes the per-warp kernels and preconditioner copies are built for
+inline bool narrow_nb(int nb) {
+  return nb == 1 || nb == 3 || nb == 6 || nb == 10 || nb == 15 || nb == 21 || nb == 28 || nb == 36 || nb == 45;
+}
+
 // Per-row face geometry (FP64), row = 4 t + f.
 struct FaceGeom {
   double o[3];   // frame origin (first face vertex)
@@ -50,6 +65,7 @@ struct dfm_mesh {
 struct dfm_op {
   const dfm_mesh* mesh = nullptr;
   int Np = 0, nb = 0, precision = DFM_F32;
+  int ns = 1;  // spatial functions per face (1 constant, 3 linear); nb = ns (Np+1)(Np+2)/2
   int64_t nrows = 0, row_stride = 0;
   void* vals = nullptr;  // device
   int64_t bytes = 0;
@@ -163,13 +179,21 @@ int read_timeout_flag(const dfm_op* op, cudaStream_t st, const char* who);
 int launch_assemble_wide(int Np, const void* pairs, int64_t npairs, const double* glx, const double* glw, int q,
                          float cos_max, float* vals, int64_t row_stride, unsigned long long* nodes, int moment,
                          cudaStream_t st);
+// the linear spatial basis (3 functions per face, N_p <= 8): pos_scratch holds
+// 8 bytes per pair (vertex positions), 8-byte aligned
+int launch_assemble_p1(const dfm_mesh* mesh, int Np, const void* pairs, void* pos_scratch, int64_t npairs,
+                       const double* glx, const double* glw, int q, float cos_max, float* vals, int64_t row_stride,
+                       unsigned long long* nodes, cudaStream_t st);
 int apply_wide(const dfm_op* op, const float* x, const float* x0, float* y, int R, double alpha, cudaStream_t st);
 int apply_wide(const dfm_op* op, const double* x, const double* x0, double* y, int R, double alpha, cudaStream_t st);
+// stride: unknowns per row of rho0 (3 (Np+1)(Np+2)/2 with the linear spatial basis)
 int launch_directed_source_wide(int Np, const FaceGeom* geom, const int64_t* rows, const double* dirs, int n_src,
-                                int64_t nrows, int combine, double* rho0, int* bad, cudaStream_t st);
-int launch_interior_density_wide(int Np, bool polar, const dfm_mesh* mesh, const double* mu, double mu_uniform,
-                                 const int64_t* list, const double* weights, int n, const double* glx,
-                                 const double* glw, int nq, double* gvec, double* dgvec, cudaStream_t st);
+                                int64_t nrows, int combine, double* rho0, int* bad, int stride, cudaStream_t st);
+// ns spatial functions per face (1, or 3 for the linear spatial basis)
+int launch_interior_density_wide(int Np, int ns, bool polar, const dfm_mesh* mesh, const double* mu,
+                                 double mu_uniform, const int64_t* list, const double* weights, int n,
+                                 const double* glx, const double* glw, int nq, double* gvec, double* dgvec,
+                                 cudaStream_t st);
 // implemented in quad.cu
 int gauss_legendre_device(int q, double* x, double* w, cudaStream_t st);
 }  // namespace dfm

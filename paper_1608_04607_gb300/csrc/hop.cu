@@ -235,8 +235,9 @@ int prepare_lowp(const dfm_op* cop, int precision, cudaStream_t st, int trans, i
       (precision != DFM_F16 && precision != DFM_BF16 && precision != DFM_FP8E4M3))
     return set_error(DFM_ERR_UNSUPPORTED,
                      "preconditioner copy: needs an FP32 or BF16 operator and DFM_F16, DFM_BF16 or DFM_FP8E4M3");
-  if (op->nb > geom::kNarrowMaxNb)
-    return set_error(DFM_ERR_UNSUPPORTED, "preconditioner copy: built for bases up to Np = 8");
+  if (!narrow_nb(op->nb))
+    return set_error(DFM_ERR_UNSUPPORTED, "preconditioner copy: built for the bases of the per-warp kernels "
+                                          "(Np <= 8; with the linear spatial basis Np = 0 or 4)");
   void*& vals = trans ? op->lpT_vals : op->lp_vals;
   int64_t& have = trans ? op->lpT_bytes : op->lp_bytes;
   int& prec = trans ? op->lpT_precision : op->lp_precision;

@@ -69,11 +69,15 @@ constexpr int kWideMaxNp = 20;    // largest order of the wide kernels (N_b = 23
 
 // Assembly of one face pair by one block per tile of test rows: the block's
 // CG x RG threads each own 8 test rows x 8 trial columns of the tile (CG =
-// NBP / 8 column groups, RG row groups, TRW = 8 RG rows per tile), NC nodes
-// are staged per pass (Z(p) of all NBP trial columns, w Z(p') of the tile's
-// rows), evaluated by threads [0, NC) and [NC, 2 NC).
+// NS NBP / 8 column groups, RG row groups, TRW = 8 RG rows per tile), NC nodes
+// are staged per pass (Z(p) of the NBP padded Zernike columns, and for each
+// of the NS source spatial functions the weighted w Z(p') of the tile's
+// rows), evaluated by threads [0, NC) and [NC, 2 NC).  NS = 1: the
+// piecewise-constant spatial basis (block side NB); NS = 3: the linear one
+// (block side 3 NB, columns padded to NBP per spatial function).
 struct WideAsm {
-  int nb, nbp;   // basis size and its padding to 8
+  int nb, nbp;   // Zernike functions per face and their padding to 8
+  int ns, nrow;  // spatial functions per face, block side ns nb
   int cg, rg;    // column and row groups of a tile
   int trw;       // test rows per tile (8 rg)
   int ntile;     // tiles per face pair
@@ -83,12 +87,14 @@ struct WideAsm {
   int64_t smem;  // dynamic shared memory bytes beyond the patch state
 };
 
-inline WideAsm wide_asm_geometry(int nb) {
+inline WideAsm wide_asm_geometry(int nb, int ns = 1) {
   WideAsm g{};
   g.nb = nb;
   g.nbp = (nb + 7) / 8 * 8;
-  g.cg = g.nbp / 8;
-  const int nrg = g.cg;  // row groups of the whole block
+  g.ns = ns;
+  g.nrow = ns * nb;
+  g.cg = ns * g.nbp / 8;
+  const int nrg = (g.nrow + 7) / 8;  // row groups of the whole block
   int max_rg = 256 / g.cg;
   if (max_rg < 1) max_rg = 1;
   g.ntile = (nrg + max_rg - 1) / max_rg;
@@ -99,7 +105,7 @@ inline WideAsm wide_asm_geometry(int nb) {
   g.nc = g.threads / 2 < 64 ? g.threads / 2 : 64;
   g.ldq = g.trw + 4;
   g.ldp = g.nbp + 4;
-  g.smem = (int64_t)g.nc * (g.ldq + g.ldp) * 4 + ((int64_t)g.trw + 2 * 32) * 4;
+  g.smem = (int64_t)g.nc * (ns * g.ldq + g.ldp) * 4 + ((int64_t)g.trw + 2 * 32) * 4;
   return g;
 }
 

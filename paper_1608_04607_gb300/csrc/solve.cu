@@ -842,12 +842,14 @@ using namespace dfm;
 
 extern "C" int dfm_source(const dfm_mesh* mesh, int Np, const int64_t* rows_host, int n_src, double* rho0,
                           void* stream) {
-  if (!mesh || !rows_host || !rho0 || n_src < 1 || Np < 0 || Np > geom::kWideMaxNp)
+  if (!mesh || !rows_host || !rho0 || n_src < 1 || !basis_ok(Np, geom::kWideMaxNp))
     return set_error(DFM_ERR_ARG, "dfm_source: bad argument");
   for (int s = 0; s < n_src; ++s)
     if (rows_host[s] < 0 || rows_host[s] >= mesh->nrows) return set_error(DFM_ERR_ARG, "dfm_source: row out of range");
   cudaStream_t st = as_stream(stream);
-  const int nb = nbasis(Np);
+  // the linear functions of the linear spatial basis have zero mean: the
+  // coefficient sits on index 0 (constant function, Zernike (0, 0)) either way
+  const int nb = basis_size(Np);
   int64_t* rows_d = nullptr;
   DFM_CUDA_CHECK(cudaMallocAsync(&rows_d, sizeof(int64_t) * n_src, st));
   DFM_CUDA_CHECK(cudaMemcpyAsync(rows_d, rows_host, sizeof(int64_t) * n_src, cudaMemcpyHostToDevice, st));
@@ -1203,7 +1205,8 @@ extern "C" int dfm_solve_combo(const dfm_op* const* ops, int K, const double* co
                                double* rho, const dfm_solve_opts* opts, void* stream, dfm_solve_info* info) {
   if (!ops || K < 1 || K > 4 || !coef_host) return dfm::set_error(DFM_ERR_ARG, "dfm_solve_combo: bad argument");
   for (int k = 0; k < K; ++k)
-    if (!ops[k] || ops[k]->mesh != ops[0]->mesh || ops[k]->Np != ops[0]->Np || ops[k]->precision != DFM_F32)
+    if (!ops[k] || ops[k]->mesh != ops[0]->mesh || ops[k]->Np != ops[0]->Np || ops[k]->ns != ops[0]->ns ||
+        ops[k]->precision != DFM_F32)
       return dfm::set_error(DFM_ERR_ARG, "dfm_solve_combo: operators must be FP32 and share mesh and Np");
   return dfm::solve_impl(ops[0], ops, K, coef_host, rho0, R, rho, opts, stream, info);
 }
@@ -1214,7 +1217,8 @@ extern "C" int dfm_solve_damped(const dfm_op* const* moments, int K, const doubl
     return dfm::set_error(DFM_ERR_ARG, "dfm_solve_damped: bad argument");
   for (int k = 0; k < K; ++k) {
     const dfm_op* o = moments[k];
-    if (!o || o->mesh != moments[0]->mesh || o->Np != moments[0]->Np || o->precision != DFM_F32)
+    if (!o || o->mesh != moments[0]->mesh || o->Np != moments[0]->Np || o->ns != moments[0]->ns ||
+        o->precision != DFM_F32)
       return dfm::set_error(DFM_ERR_ARG, "dfm_solve_damped: moments must be FP32 and share mesh and Np");
     if (o->moment != k)
       return dfm::set_error(DFM_ERR_ARG, "dfm_solve_damped: moments[k] must be assembled with moment = k");

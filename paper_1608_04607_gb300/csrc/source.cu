@@ -25,7 +25,7 @@ namespace {
 template <int NP>
 __global__ void directed_source_kernel(const FaceGeom* __restrict__ geom, const int64_t* __restrict__ rows,
                                        const double* __restrict__ dirs, int n_src, int64_t nrows, int combine,
-                                       double* __restrict__ rho0, int* __restrict__ bad) {
+                                       double* __restrict__ rho0, int* __restrict__ bad, int stride) {
   constexpr int NB = (NP + 1) * (NP + 2) / 2;
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n_src) return;
@@ -46,7 +46,7 @@ __global__ void directed_source_kernel(const FaceGeom* __restrict__ geom, const 
   double Z[NB];
   zernike<NP, double>(px, py, Z);
   const double sa = sqrt(F.area);
-  double* out = rho0 + ((combine ? 0 : (int64_t)s * nrows) + r) * NB;
+  double* out = rho0 + ((combine ? 0 : (int64_t)s * nrows) + r) * stride;
   int i = 0;
 #pragma unroll
   for (int n = 0; n <= NP; ++n)
@@ -212,8 +212,12 @@ using namespace dfm;
 
 extern "C" int dfm_source_directed(const dfm_mesh* mesh, int Np, const int64_t* rows_host, const double* dirs_host,
                                    int n_src, int combine, double* rho0, void* stream) {
-  if (!mesh || !rows_host || !rho0 || n_src < 1 || Np < 0 || Np > geom::kWideMaxNp || (combine != 0 && combine != 1))
+  if (!mesh || !rows_host || !rho0 || n_src < 1 || !basis_ok(Np, geom::kWideMaxNp) || (combine != 0 && combine != 1))
     return set_error(DFM_ERR_ARG, "dfm_source_directed: bad argument");
+  // a constant density on the face projects onto the constant spatial
+  // function only: the first (Np+1)(Np+2)/2 entries of each row
+  const int stride = basis_size(Np);
+  Np = basis_np(Np);
   for (int s = 0; s < n_src; ++s)
     if (rows_host[s] < 0 || rows_host[s] >= mesh->nrows)
       return set_error(DFM_ERR_ARG, "dfm_source_directed: row out of range");
@@ -231,7 +235,6 @@ extern "C" int dfm_source_directed(const dfm_mesh* mesh, int Np, const int64_t* 
       return set_error(DFM_ERR_ARG, "dfm_source_directed: repeated row in a combined source");
   }
   cudaStream_t st = as_stream(stream);
-  const int nb = nbasis(Np);
   // stream-ordered scratch: rows, directions, the direction check flag
   char* buf = nullptr;
   const size_t bytes = sizeof(int64_t) * n_src + 3 * sizeof(double) * n_src + 16;
@@ -243,19 +246,19 @@ extern "C" int dfm_source_directed(const dfm_mesh* mesh, int Np, const int64_t* 
   if (dirs_host)
     DFM_CUDA_CHECK(cudaMemcpyAsync(dirs_d, dirs_host, 3 * sizeof(double) * n_src, cudaMemcpyHostToDevice, st));
   DFM_CUDA_CHECK(cudaMemsetAsync(bad_d, 0, sizeof(int), st));
-  DFM_CUDA_CHECK(cudaMemsetAsync(rho0, 0, sizeof(double) * (combine ? 1 : n_src) * mesh->nrows * nb, st));
+  DFM_CUDA_CHECK(cudaMemsetAsync(rho0, 0, sizeof(double) * (combine ? 1 : n_src) * mesh->nrows * stride, st));
   const unsigned blocks = (unsigned)((n_src + 127) / 128);
   const double* dp = dirs_host ? dirs_d : nullptr;
 #define CASE(N)                                                                                                  \
   case N:                                                                                                        \
     directed_source_kernel<N><<<blocks, 128, 0, st>>>(mesh->geom, rows_d, dp, n_src, mesh->nrows, combine, rho0, \
-                                                      bad_d);                                                    \
+                                                      bad_d, stride);                                            \
     break;
   switch (Np) {
     CASE(0) CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
     default: {  // Np = 9..20 (wide.cu)
       const int rc = launch_directed_source_wide(Np, mesh->geom, rows_d, dp, n_src, mesh->nrows, combine, rho0, bad_d,
-                                                 st);
+                                                 stride, st);
       if (rc) {
         cudaFreeAsync(buf, st);
         return rc;

@@ -548,11 +548,12 @@ int launch(const dfm_op* op, const TX* x, const TX* x0, TX* y, int R, double alp
   if (!trans) {
     if ((reinterpret_cast<uintptr_t>(x) & 15) || (reinterpret_cast<uintptr_t>(op->vals) & 15))
       return set_error(DFM_ERR_ARG, "dfm_apply: x must be 16-byte aligned");
-    // bases above N_p = 8: a block row per warp, no staged row tiles (wide.cu)
-    if (op->nb > geom::kNarrowMaxNb) {
+    // bases above N_p = 8 and linear-spatial-basis sizes: a block row per warp,
+    // no staged row tiles (wide.cu)
+    if (!narrow_nb(op->nb)) {
       if constexpr (std::is_same<TV, float>::value && std::is_same<TX, TA>::value) {
         if (K != 1 || combo_ops)
-          return set_error(DFM_ERR_UNSUPPORTED, "dfm_apply_combo: combined operators need Np <= 8");
+          return set_error(DFM_ERR_UNSUPPORTED, "dfm_apply_combo: combined operators need a basis of the per-warp kernels");
         return apply_wide(op, x, x0, y, R, alpha, st);
       }
       return set_error(DFM_ERR_UNSUPPORTED, "dfm_apply: bases above Np = 8 need FP32 blocks");
@@ -624,8 +625,10 @@ int launch(const dfm_op* op, const TX* x, const TX* x0, TX* y, int R, double alp
     else
       return set_error(DFM_ERR_UNSUPPORTED, "dfm_apply_combo: operators must be FP32");
     if (rc) return rc;
-  } else if (combo_ops == nullptr && !(reinterpret_cast<uintptr_t>(op->vals) & 15) &&
-             op->nb <= geom::kNarrowMaxNb) {
+  } else if (combo_ops == nullptr && !(reinterpret_cast<uintptr_t>(op->vals) & 15) && narrow_nb(op->nb) &&
+             (200 * 1024 - 512) / (8 * op->row_stride * (int64_t)sizeof(TV) +
+                                   ((int64_t)8 * op->nb * (int64_t)sizeof(TA) + 15) / 16 * 16) >= 2) {
+    // (two stages of two tets' rows fit; larger rows take the gather below)
     // pipelined transposed application, one right-hand side per launch
     const int64_t nt = op->nrows / 4;
     const int64_t row_bytes = op->row_stride * (int64_t)sizeof(TV);

@@ -172,8 +172,18 @@ def _like(t, ref, what):
         raise DFMError(DFM_ERR_ARG, f"{what}: expected {tuple(ref.shape)} {ref.dtype}")
 
 
+def basis(Np: int, spatial: int = 0) -> int:
+    """Basis code of the C ABI (DFM_BASIS): momentum order Np with the
+    piecewise-constant spatial function per face (spatial=0, Sec. 3.1) or the
+    linear spatial basis, three orthonormal affine functions per face
+    (spatial=1).  Every argument named Np accepts a code."""
+    return int(Np) | (int(spatial) << 8)
+
+
 def nbasis(Np: int) -> int:
-    return (Np + 1) * (Np + 2) // 2
+    """Unknowns per row of basis code Np: (Np+1)(Np+2)/2 per spatial function."""
+    n = Np & 0xFF
+    return (3 if Np >> 8 else 1) * ((n + 1) * (n + 2) // 2)
 
 
 class Mesh:

@@ -146,29 +146,43 @@ int main() {
             }
     }
   }
-  // wide assembly (N_p = 9..20): tiles cover the block once, thread roles fit
-  // the block, staged rows hold every read of the accumulation (rows
-  // 8 rg .. 8 rg + 7 of a tile, columns 4 cg .. 4 cg + 3 and NBP/2 + 4 cg ..)
-  // as aligned 16-byte vectors, and two blocks fit an SM's shared memory
-  for (int np = 9; np <= kWideMaxNp; ++np) {
-    const int nb = (np + 1) * (np + 2) / 2;
-    const WideAsm g = wide_asm_geometry(nb);
-    ++checked;
-    if (g.threads % 32 || g.threads > 256 || g.threads < 64) return fail("wide threads", nb, g.threads, 0, 0, 0);
-    if (g.cg * g.rg > g.threads || 2 * g.nc > g.threads || g.nc < 1 || g.nc > 64)
-      return fail("wide roles", nb, g.cg, g.rg, g.nc, g.threads);
-    if (g.nbp < nb || g.nbp % 8 || g.cg * 8 != g.nbp) return fail("wide columns", nb, g.nbp, g.cg, 0, 0);
-    if ((long long)g.trw * g.ntile < nb || (long long)g.trw * (g.ntile - 1) >= nb)
-      return fail("wide tiles", nb, g.trw, g.ntile, 0, 0);
-    if (g.trw != 8 * g.rg || g.ldq != g.trw + 4 || g.ldp != g.nbp + 4 || g.ldq % 4 || g.ldp % 4 || (g.nbp / 2) % 4)
-      return fail("wide strides", nb, g.ldq, g.ldp, g.trw, 0);
-    if (8 * (g.rg - 1) + 7 >= g.ldq || 4 * (g.cg - 1) + 3 + g.nbp / 2 >= g.ldp)
-      return fail("wide staged reads", nb, g.rg, g.cg, 0, 0);
-    if ((g.nc * (long long)g.ldq * 4) % 16) return fail("wide zp offset", nb, g.nc, g.ldq, 0, 0);
-    const long long static_smem = 4096;  // patch state and pair constants
-    if (2 * (g.smem + static_smem) > 228LL * 1024 || g.smem > 200 * 1024)
-      return fail("wide shared memory", nb, 0, 0, 0, g.smem);
-  }
+  // wide assembly (N_p = 9..20 with one spatial function, 0..8 with the three
+  // of the linear basis): tiles cover the block once, thread roles fit the
+  // block, staged rows hold every read of the accumulation (rows 8 rg ..
+  // 8 rg + 7 of a tile; columns 4 cg .. 4 cg + 3 and NS NBP/2 + 4 cg .., each
+  // group inside one spatial function's NBP columns) as aligned 16-byte
+  // vectors, and two blocks fit an SM's shared memory
+  for (int ns : {1, 3})
+    for (int np = (ns == 1 ? 9 : 0); np <= (ns == 1 ? kWideMaxNp : 8); ++np) {
+      const int nb = (np + 1) * (np + 2) / 2;
+      const WideAsm g = wide_asm_geometry(nb, ns);
+      ++checked;
+      if (g.threads % 32 || g.threads > 256 || g.threads < 64) return fail("wide threads", nb, g.threads, ns, 0, 0);
+      if (g.cg * g.rg > g.threads || 2 * g.nc > g.threads || g.nc < 1 || g.nc > 64)
+        return fail("wide roles", nb, g.cg, g.rg, g.nc, g.threads);
+      if (g.nbp < nb || g.nbp % 8 || g.cg * 8 != ns * g.nbp || g.nrow != ns * nb)
+        return fail("wide columns", nb, g.nbp, g.cg, ns, 0);
+      if ((long long)g.trw * g.ntile < g.nrow || (long long)g.trw * (g.ntile - 1) >= g.nrow)
+        return fail("wide tiles", nb, g.trw, g.ntile, ns, 0);
+      if (g.trw != 8 * g.rg || g.ldq != g.trw + 4 || g.ldp != g.nbp + 4 || g.ldq % 4 || g.ldp % 4 ||
+          (ns * g.nbp / 2) % 4)
+        return fail("wide strides", nb, g.ldq, g.ldp, g.trw, ns);
+      if (8 * (g.rg - 1) + 7 >= g.ldq) return fail("wide staged rows", nb, g.rg, g.cg, ns, 0);
+      for (int cg = 0; cg < g.cg; ++cg)
+        for (int c : {4 * cg, ns * g.nbp / 2 + 4 * cg}) {
+          const int a = c / g.nbp, j = c - a * g.nbp;
+          if (a < 0 || a >= ns || j % 4 || j + 3 >= g.nbp) return fail("wide column group", nb, cg, c, ns, 0);
+        }
+      if ((g.nc * (long long)g.ldq * 4) % 16) return fail("wide zq plane", nb, g.nc, g.ldq, ns, 0);
+      const long long static_smem = 4096;  // patch state and pair constants
+      if (2 * (g.smem + static_smem) > 228LL * 1024 || g.smem > 200 * 1024)
+        return fail("wide shared memory", nb, ns, 0, 0, g.smem);
+      if (ns == 1) {  // the same geometry as before the spatial functions were added
+        const WideAsm h = wide_asm_geometry(nb);
+        if (h.cg != g.cg || h.trw != g.trw || h.threads != g.threads || h.smem != g.smem)
+          return fail("wide default", nb, 0, 0, 0, 0);
+      }
+    }
   std::printf("ok %lld\n", checked);
   return 0;
 }

@@ -74,6 +74,8 @@ def test_assembly_parameters_are_checked_before_the_mesh_is_touched():
     out = ctypes.c_void_p()
     good = dict(Np=4, mu=None, mu_uniform=0.1, quad_order=0, max_patch_deg=0.0, precision=dfm.F32, moment=0)
     cases = [dict(Np=21), dict(Np=-1), dict(Np=9, precision=dfm.BF16), dict(Np=20, precision=dfm.F64),
+             dict(Np=dfm.basis(9, 1)), dict(Np=dfm.basis(4, 2)), dict(Np=dfm.basis(4, 1), precision=dfm.BF16),
+             dict(Np=dfm.basis(4, 1), moment=1),
              dict(precision=7), dict(mu_uniform=-0.1), dict(mu_uniform=float("nan")),
              dict(quad_order=33), dict(max_patch_deg=5.0), dict(moment=4)]
     for bad in cases:
