@@ -305,6 +305,15 @@ typedef struct {
                         in its own Krylov space, in lockstep.  The operator passes are shared
                         either way; the block space needs fewer of them.  Ignored by
                         dfm_solve_combo / dfm_solve_damped (one operator per right-hand side). */
+  int coarse;        /* GMRES_IR, right-hand sides solved one at a time, with a low-precision
+                        precond_precision: 0 = off; g in 1..4 = two-level preconditioner
+                        z = Q v + p~(B)(v - (I - B) Q v), Q = V (V^T (I - B) V)^{-1} V^T, V the
+                        isotropic (0,0) density sqrt|T| on each of g^3 spatial aggregates of tets
+                        (boxes of the mesh's bounding box, by tet centroid; empty ones dropped),
+                        for the slow near-isotropic mode (not in the paper).  (I - B) V is formed
+                        once per call (its g^3 applications are counted in iters), so each
+                        preconditioner call adds g^3-long dot and update passes, no application.
+                        Ignored by batched and block solves and by dfm_solve_combo. */
 } dfm_solve_opts;
 
 typedef struct {

@@ -398,9 +398,153 @@ inline int precond_hops(const Ctx& c, const Hop& hp, int R, int d, const float* 
 
 #include "block_gmres.cuh"
 
+// Two-level correction of the flexible preconditioner (dfm_solve_opts.coarse;
+// not in the paper, the solver acceleration its slow modes call for): the
+// slowest mode of I - B at small loss is the isotropic density, so a coarse
+// space V of the (0,0) slot weighted by sqrt|T| on g^3 spatial aggregates of
+// tets (by centroid, boxes of the bounding box) is solved exactly and the
+// polynomial handles the rest:
+//   z = Q v + p~(B) (v - A Q v),  Q = V E^{-1} V^T,  E = V^T A V,  A = I - B.
+// A V is formed once per solve (nc operator applications), so each
+// preconditioner call costs nc-long dot and update passes, not an extra
+// application: A Q v = (A V) E^{-1} V^T v.
+struct Coarse {
+  int nc = 0;
+  float* V = nullptr;   // [nc][n]
+  float* AV = nullptr;  // [nc][n]
+  float* r = nullptr;   // [n] v - A Q v
+  float* y = nullptr;   // [nc] E^{-1} V^T v (device)
+  int32_t* agg = nullptr;  // [n_tets] aggregate of each tet
+  std::vector<double> Einv;  // nc x nc
+};
+
+// V[agg(t)][R nb] = sqrt|T_R| for row R = 4t + f (the (0,0) slot)
+__global__ void coarse_basis_kernel(const FaceGeom* __restrict__ geom, const int32_t* __restrict__ agg, int64_t nrows,
+                                    int nb, int64_t n, float* __restrict__ V) {
+  for (int64_t R = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; R < nrows; R += (int64_t)gridDim.x * blockDim.x)
+    V[(int64_t)agg[R >> 2] * n + R * nb] = (float)sqrt(geom[R].area);
+}
+
+// Builds V, A V and E^{-1} for g aggregates per axis; counts the nc
+// applications in *iters.  Empty aggregates are dropped; a singular E (or
+// g = 0) leaves nc = 0 (no correction).
+inline int coarse_setup(const Ctx& c, const dfm_mesh* mesh, int g, Coarse& cs, float* partial, float* h_dev,
+                        int* iters) {
+  cs.nc = 0;
+  if (g < 1) return DFM_OK;
+  std::vector<double> verts((size_t)mesh->nv * 3);
+  std::vector<int32_t> tets((size_t)mesh->nt * 4);
+  DFM_CUDA_CHECK(cudaMemcpyAsync(verts.data(), mesh->verts, sizeof(double) * verts.size(), cudaMemcpyDeviceToHost, c.st));
+  DFM_CUDA_CHECK(cudaMemcpyAsync(tets.data(), mesh->tets, sizeof(int32_t) * tets.size(), cudaMemcpyDeviceToHost, c.st));
+  DFM_CUDA_CHECK(cudaStreamSynchronize(c.st));
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int64_t v = 0; v < mesh->nv; ++v)
+    for (int k = 0; k < 3; ++k) {
+      lo[k] = std::min(lo[k], verts[3 * v + k]);
+      hi[k] = std::max(hi[k], verts[3 * v + k]);
+    }
+  std::vector<int32_t> box((size_t)mesh->nt);
+  std::vector<int> count((size_t)g * g * g, 0);
+  for (int64_t t = 0; t < mesh->nt; ++t) {
+    int idx[3];
+    for (int k = 0; k < 3; ++k) {
+      double cen = 0;
+      for (int j = 0; j < 4; ++j) cen += 0.25 * verts[3 * (int64_t)tets[4 * t + j] + k];
+      const double ext = hi[k] - lo[k];
+      int i = ext > 0 ? (int)std::floor(g * (cen - lo[k]) / ext) : 0;
+      idx[k] = std::max(0, std::min(g - 1, i));
+    }
+    box[t] = idx[0] + g * (idx[1] + g * idx[2]);
+    ++count[box[t]];
+  }
+  std::vector<int> remap(count.size(), -1);
+  int nc = 0;
+  for (size_t b = 0; b < count.size(); ++b)
+    if (count[b] > 0) remap[b] = nc++;
+  for (auto& b : box) b = remap[b];
+  DFM_CUDA_CHECK(cudaMemcpyAsync(cs.agg, box.data(), sizeof(int32_t) * box.size(), cudaMemcpyHostToDevice, c.st));
+  const int64_t n = c.n;
+  DFM_CUDA_CHECK(cudaMemsetAsync(cs.V, 0, sizeof(float) * nc * n, c.st));
+  coarse_basis_kernel<<<grid_for(mesh->nrows, c.nsm), 256, 0, c.st>>>(mesh->geom, cs.agg, mesh->nrows, c.op->nb, n,
+                                                                        cs.V);
+  DFM_LAUNCHED();
+  DFM_CUDA_CHECK(cudaGetLastError());
+  for (int k = 0; k < nc; ++k) {
+    const int rc = ctx_apply(c, cs.V + (int64_t)k * n, cs.V + (int64_t)k * n, cs.AV + (int64_t)k * n, 1, -1.0,
+                             DFM_F32);
+    if (rc) return rc;
+    ++*iters;
+  }
+  // E[i][k] = V_i . (A V)_k, inverted by Gauss-Jordan with partial pivoting
+  std::vector<double> E((size_t)nc * nc), col(nc);
+  std::vector<float> colf(nc);
+  for (int k = 0; k < nc; ++k) {
+    const int rc = dots<float>(c, cs.V, n, nc, cs.AV + (int64_t)k * n, partial, h_dev, colf.data());
+    if (rc) return rc;
+    for (int i = 0; i < nc; ++i) E[(size_t)i * nc + k] = colf[i];
+  }
+  std::vector<double> inv((size_t)nc * nc, 0.0);
+  for (int i = 0; i < nc; ++i) inv[(size_t)i * nc + i] = 1.0;
+  double emax = 0;
+  for (double e : E) emax = std::max(emax, std::fabs(e));
+  for (int k = 0; k < nc; ++k) {
+    int p = k;
+    for (int i = k + 1; i < nc; ++i)
+      if (std::fabs(E[(size_t)i * nc + k]) > std::fabs(E[(size_t)p * nc + k])) p = i;
+    if (!(std::fabs(E[(size_t)p * nc + k]) > 1e-12 * emax)) return DFM_OK;  // singular: no correction
+    for (int j = 0; j < nc; ++j) {
+      std::swap(E[(size_t)k * nc + j], E[(size_t)p * nc + j]);
+      std::swap(inv[(size_t)k * nc + j], inv[(size_t)p * nc + j]);
+    }
+    const double piv = E[(size_t)k * nc + k];
+    for (int j = 0; j < nc; ++j) {
+      E[(size_t)k * nc + j] /= piv;
+      inv[(size_t)k * nc + j] /= piv;
+    }
+    for (int i = 0; i < nc; ++i) {
+      if (i == k) continue;
+      const double f = E[(size_t)i * nc + k];
+      if (f == 0.0) continue;
+      for (int j = 0; j < nc; ++j) {
+        E[(size_t)i * nc + j] -= f * E[(size_t)k * nc + j];
+        inv[(size_t)i * nc + j] -= f * inv[(size_t)k * nc + j];
+      }
+    }
+  }
+  cs.Einv = inv;
+  cs.nc = nc;
+  return DFM_OK;
+}
+
+// z = Q v + p~(B) (v - A Q v) (see Coarse)
+inline int coarse_hops(const Ctx& c, const Coarse& cs, const Hop& hp, int d, const float* v, float* z, float* partial,
+                       float* h_dev) {
+  const int nc = cs.nc;
+  std::vector<float> cv(nc), y(nc);
+  int rc = dots<float>(c, cs.V, c.n, nc, v, partial, h_dev, cv.data());
+  if (rc) return rc;
+  for (int i = 0; i < nc; ++i) {
+    double s = 0;
+    for (int j = 0; j < nc; ++j) s += cs.Einv[(size_t)i * nc + j] * cv[j];
+    y[i] = (float)s;
+  }
+  DFM_CUDA_CHECK(cudaMemcpyAsync(cs.y, y.data(), sizeof(float) * nc, cudaMemcpyHostToDevice, c.st));
+  DFM_CUDA_CHECK(cudaMemcpyAsync(cs.r, v, sizeof(float) * c.n, cudaMemcpyDeviceToDevice, c.st));
+  multi_axpy_kernel<float><<<kRedBlocks, kRedThreads, 0, c.st>>>(cs.AV, c.n, nc, cs.y, -1.f, cs.r, c.n, nullptr);
+  DFM_LAUNCHED();
+  DFM_CUDA_CHECK(cudaGetLastError());
+  rc = precond_hops(c, hp, 1, d, cs.r, z);
+  if (rc) return rc;
+  multi_axpy_kernel<float><<<kRedBlocks, kRedThreads, 0, c.st>>>(cs.V, c.n, nc, cs.y, 1.f, z, c.n, nullptr);
+  DFM_LAUNCHED();
+  DFM_CUDA_CHECK(cudaGetLastError());
+  return DFM_OK;
+}
+
 template <typename T>
 int gmres(const Ctx& c, const T* b, T* x, double tol, int m, int d, int max_iter, int* iters, double* est, T* V,
-          T* tmp, T* t1, T* t2, T* h_dev, T* partial, T* red_dev, const Hop* lp = nullptr, T* Z = nullptr) {
+          T* tmp, T* t1, T* t2, T* h_dev, T* partial, T* red_dev, const Hop* lp = nullptr, T* Z = nullptr,
+          const Coarse* coarse = nullptr) {
   const int64_t n = c.n;
   const int xtype = sizeof(T) == 8 ? DFM_F64 : DFM_F32;
   if (d < 1) d = 1;
@@ -460,7 +604,8 @@ int gmres(const Ctx& c, const T* b, T* x, double tol, int m, int d, int max_iter
         // flexible step: z_j = p~(B) v_j by Horner on the 16-bit copy, w = z_j - B z_j
         T* zj = Z + (int64_t)j * n;
         if constexpr (std::is_same<T, float>::value) {
-          rc = precond_hops(c, *lp, 1, d, vj, zj);
+          rc = (coarse && coarse->nc > 0) ? coarse_hops(c, *coarse, *lp, d, vj, zj, partial, h_dev)
+                                          : precond_hops(c, *lp, 1, d, vj, zj);
         } else {
           rc = set_error(DFM_ERR_UNSUPPORTED, "dfm_solve: 16-bit preconditioner hops need FP32 Krylov vectors");
         }
@@ -937,6 +1082,12 @@ int solve_impl(const dfm_op* op, const dfm_op* const* combo, int K, const double
   const int64_t bpart = block ? (int64_t)kGMaxSplits * (mb + 1) * Rg * Rg : 0;
   const int64_t bsmall = block ? (int64_t)(mb + 3) * Rg * Rg : 0;
   if (block) bytes += (bpart + bsmall) * 4 + 1024;
+  // two-level correction (single right-hand-side flexible solves): V, A V, r, y, aggregates
+  if (opts->coarse < 0 || opts->coarse > 4) return set_error(DFM_ERR_ARG, "dfm_solve: coarse must be in 0..4");
+  const bool use_coarse = opts->coarse > 0 && !batched && use_lp && method == DFM_SOLVE_GMRES_IR && !combo;
+  const int g_coarse = use_coarse ? opts->coarse : 0;
+  const int nc_max = g_coarse * g_coarse * g_coarse;
+  if (use_coarse) bytes += ((2 * (int64_t)nc_max + 1) * n + 64) * 4 + op->mesh->nt * 4 + 5 * 256;
   int rc = ensure_work(op, bytes + 8 * 256);
   if (rc) return rc;
   Work W{reinterpret_cast<char*>(op->swork)};
@@ -954,6 +1105,14 @@ int solve_impl(const dfm_op* op, const dfm_op* const* combo, int K, const double
     bscr.part = W.take<float>(bpart);
     bscr.part_elems = bpart;
     bscr.small = W.take<float>(bsmall);
+  }
+  Coarse coarse;
+  if (use_coarse) {
+    coarse.V = W.take<float>((int64_t)nc_max * n);
+    coarse.AV = W.take<float>((int64_t)nc_max * n);
+    coarse.r = W.take<float>(n);
+    coarse.y = W.take<float>(64);
+    coarse.agg = W.take<int32_t>(op->mesh->nt);
   }
   Hop hop;
   const Hop* lp = nullptr;
@@ -1146,6 +1305,10 @@ int solve_impl(const dfm_op* op, const dfm_op* const* combo, int K, const double
       float* part32 = reinterpret_cast<float*>(part64);
       float* h32 = reinterpret_cast<float*>(h64);
       float* red32 = reinterpret_cast<float*>(red64);
+      if (use_coarse && s == 0) {  // one coarse space for every right-hand side of the call
+        rs = coarse_setup(c, op->mesh, g_coarse, coarse, part32, h32, &iters);
+        if (rs) return rs;
+      }
       while (true) {
         int r2 = residual64(c, b, x, r64, part64, red64, &resid, &rabs);
         if (r2) return r2;
@@ -1170,7 +1333,7 @@ int solve_impl(const dfm_op* op, const dfm_op* const* combo, int K, const double
         const double itol = method == DFM_SOLVE_GMRES_IR ? std::max(inner_tol, 0.3 * need)
                                                          : std::max(opts->tol, 1e-6);
         int gi = gmres<float>(c, bf, xf, itol, m, poly, max_iter, &iters, &est, V, tmp, t1, t2, h32, part32, red32,
-                              method == DFM_SOLVE_GMRES_IR ? lp : nullptr, Zs);
+                              method == DFM_SOLVE_GMRES_IR ? lp : nullptr, Zs, use_coarse ? &coarse : nullptr);
         if (gi != DFM_OK && gi != DFM_ERR_NOT_CONVERGED) return gi;
         add_f32_kernel<<<grid_for(n, c.nsm), 256, 0, c.st>>>(x, xf, rabs, n);
         DFM_LAUNCHED();

@@ -58,7 +58,7 @@ class SolveOpts(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("restart", ctypes.c_int), ("use_x0", ctypes.c_int), ("inner_tol", ctypes.c_double),
                 ("transpose", ctypes.c_int), ("poly_degree", ctypes.c_int), ("precond_precision", ctypes.c_int),
-                ("batch", ctypes.c_int), ("block", ctypes.c_int)]
+                ("batch", ctypes.c_int), ("block", ctypes.c_int), ("coarse", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -351,16 +351,18 @@ class Operator:
         return z
 
     def solve(self, rho0, method=GMRES_IR, tol=1e-8, max_iter=0, restart=0, x0=None, inner_tol=0.0,
-              raise_on_nonconvergence=True, transpose=False, poly_degree=0, batch=0, precond_precision=0, block=0):
+              raise_on_nonconvergence=True, transpose=False, poly_degree=0, batch=0, precond_precision=0, block=0,
+              coarse=0):
         """rho = (I - B)^{-1} rho0 (FP64, [R, rows, nb] or [rows, nb]); returns (rho, SolveInfo).
-        block=1: groups of right-hand sides share one Krylov space (dfm_solve_opts.block)."""
+        block=1: groups of right-hand sides share one Krylov space (dfm_solve_opts.block);
+        coarse=g: two-level preconditioner on g^3 aggregates (dfm_solve_opts.coarse)."""
         torch = self._torch
         R = _vec(rho0, self.n_rows, self.nb, (torch.float64,), "solve: rho0")
         _like(x0, rho0, "solve: x0")
         rho = torch.empty_like(rho0) if x0 is None else x0.clone()
         o = SolveOpts(method=method, tol=tol, max_iter=max_iter, restart=restart, use_x0=int(x0 is not None),
                       inner_tol=inner_tol, transpose=int(bool(transpose)), poly_degree=poly_degree,
-                      precond_precision=precond_precision, batch=batch, block=int(bool(block)))
+                      precond_precision=precond_precision, batch=batch, block=int(bool(block)), coarse=int(coarse))
         info = SolveInfo()
         rc = _lib.dfm_solve(self._h, _ptr(rho0), R, _ptr(rho), ctypes.byref(o), _stream(), ctypes.byref(info))
         if rc == DFM_ERR_NOT_CONVERGED and not raise_on_nonconvergence:
