@@ -11,7 +11,8 @@
 //   W = (I - B) Z_j,
 //   [V_0 .. V_j]^T W and W^T W in one pass (gdot_kernel: a tall-skinny
 //   product, every basis vector and W read once), then W <- (W - V C) S^-1 with S
-//   the Cholesky factor of W^T W - C^T C (gtrans_kernel, in place), then a
+//   the Cholesky factor of W^T W - C^T C (gtrans_kernel in place; 9..16 columns
+//   on tensor cores, gtrans_mma_kernel), then a
 //   second pass: against the basis again where the first lost more than half
 //   of a column's norm, else Cholesky QR of the block alone (block classical
 //   Gram-Schmidt with Cholesky QR and selective re-orthogonalisation), so
@@ -205,6 +206,135 @@ gtrans_kernel(const float* __restrict__ V, int K, const float* __restrict__ coef
 }
 
 // ---------------------------------------------------------------------------
+// Tensor-core block update for blocks of 9..16 columns.  The update is a dense
+// contraction (K basis vectors into 16 columns over n elements, 8 FLOP per
+// byte of basis, close to the FP32 ridge), so it runs as mma.sync m16n8k8
+// TF32 products with every FP32 operand split into two TF32 parts,
+// x = hi + lo, and the three products lo hi + hi lo + hi hi accumulated in
+// FP32 (the lo lo term lies below FP32 rounding): about 22 significant bits
+// per product.  The contraction index of a product may be assigned to the
+// MMA's k slots in any order used alike for both operands; here a lane's k
+// slots hold consecutive elements of one float4 of its operand rows, so every
+// operand moves as coalesced 16-byte vectors.  Fragment layout of m16n8k8
+// (g = lane / 4, t = lane % 4): A a0..a3 = (g, t), (g + 8, t), (g, t + 4),
+// (g + 8, t + 4); B b0, b1 = (k t, n g), (k t + 4, n g); C c0..c3 = (g, 2t),
+// (g, 2t + 1), (g + 8, 2t), (g + 8, 2t + 1).
+// The tall-skinny product [V_0 .. V_j]^T W stays on CUDA cores (gdot_kernel):
+// in the same form on tensor cores its three-product chains per accumulator
+// tile serialised and it ran 60% slower at 16 columns (892 against 557 ms per
+// step of the 45-function benchmark), while this update ran 13% faster.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t tf32_round(float x) {
+  uint32_t h;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+  return h;
+}
+__device__ __forceinline__ void tf32_split(float x, uint32_t& hi, uint32_t& lo) {
+  hi = tf32_round(x);
+  lo = tf32_round(x - __uint_as_float(hi));
+}
+__device__ __forceinline__ void mma_tf32(float* c, const uint32_t* a, uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+// c += A B from the hi / lo parts of both (three products, smallest first)
+__device__ __forceinline__ void mma3_tf32(float* c, const uint32_t* ah, const uint32_t* al, uint32_t bh0, uint32_t bh1,
+                                          uint32_t bl0, uint32_t bl1) {
+  mma_tf32(c, al, bh0, bh1);
+  mma_tf32(c, ah, bl0, bl1);
+  mma_tf32(c, ah, bh0, bh1);
+}
+__device__ __forceinline__ void split4(float x0, float x1, float x2, float x3, uint32_t* hi, uint32_t* lo) {
+  tf32_split(x0, hi[0], lo[0]);
+  tf32_split(x1, hi[1], lo[1]);
+  tf32_split(x2, hi[2], lo[2]);
+  tf32_split(x3, hi[3], lo[3]);
+}
+
+// In place, per element: W_r <- sum_i W_i T[i][r] + sum_q V_q H[q][r] as
+// gtrans_kernel (no norm partials), R <= 16, on tensor cores: the rows of
+// X = [V; W] (W only with T) contract with B = [H; T] (coefficients split once
+// into shared memory, zero-padded to 16 columns and to a multiple of 8 rows).
+// A warp owns tiles of 32 elements: lane (g, t) loads float4 g of the tile
+// from X rows k0 + t and k0 + t + 4, so MMA rows g, g + 8 are the float4's
+// elements 0, 1 (first M tile) or 2, 3 (second), and its C fragment holds, for
+// columns 2t and 2t + 1, the four elements of that float4.
+__global__ void __launch_bounds__(256, 2)
+gtrans_mma_kernel(const float* __restrict__ V, int K, const float* __restrict__ coef, int has_t, float* W, int R,
+                  int64_t n) {
+  extern __shared__ uint32_t cfs[];  // [K8][16] hi, then [K8][16] lo
+  const int KX = K + (has_t ? R : 0);
+  const int K8 = (KX + 7) / 8 * 8;
+  uint32_t* chi = cfs;
+  uint32_t* clo = cfs + K8 * 16;
+  for (int i = threadIdx.x; i < K8 * 16; i += blockDim.x) {
+    const int k = i >> 4, r = i & 15;
+    float v = 0.f;
+    if (r < R) {
+      if (k < K) v = coef[k * R + r];
+      else if (k < KX) v = coef[K * R + (k - K) * R + r];
+    }
+    tf32_split(v, chi[i], clo[i]);
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int g = lane >> 2, t = lane & 3;
+  const int64_t n4 = n >> 2;
+  float4* W4 = reinterpret_cast<float4*>(W);
+  const float4* V4 = reinterpret_cast<const float4*>(V);
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  const int64_t ntile = (n4 + 7) / 8;
+  const int64_t nwarp = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t tile = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); tile < ntile; tile += nwarp) {
+    const int64_t e4 = tile * 8 + g;
+    const bool valid = e4 < n4;
+    float acc[2][2][4];  // [M tile][N tile][c]
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) {
+      const int r0 = nt * 8 + 2 * t, r1 = r0 + 1;
+      float4 w0 = zero, w1 = zero;
+      if (!has_t && valid) {
+        if (r0 < R) w0 = W4[(int64_t)r0 * n4 + e4];
+        if (r1 < R) w1 = W4[(int64_t)r1 * n4 + e4];
+      }
+      acc[0][nt][0] = w0.x; acc[0][nt][1] = w1.x; acc[0][nt][2] = w0.y; acc[0][nt][3] = w1.y;
+      acc[1][nt][0] = w0.z; acc[1][nt][1] = w1.z; acc[1][nt][2] = w0.w; acc[1][nt][3] = w1.w;
+    }
+    for (int k0 = 0; k0 < K8; k0 += 8) {
+      const int ka = k0 + t, kb = ka + 4;
+      float4 xa = zero, xb = zero;
+      if (valid) {
+        if (ka < K) xa = V4[(int64_t)ka * n4 + e4];
+        else if (ka < KX) xa = W4[(int64_t)(ka - K) * n4 + e4];
+        if (kb < K) xb = V4[(int64_t)kb * n4 + e4];
+        else if (kb < KX) xb = W4[(int64_t)(kb - K) * n4 + e4];
+      }
+      uint32_t ah[2][4], al[2][4];
+      split4(xa.x, xa.y, xb.x, xb.y, ah[0], al[0]);
+      split4(xa.z, xa.w, xb.z, xb.w, ah[1], al[1]);
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt) {
+        const int col = nt * 8 + g;
+        const uint32_t bh0 = chi[ka * 16 + col], bh1 = chi[kb * 16 + col];
+        const uint32_t bl0 = clo[ka * 16 + col], bl1 = clo[kb * 16 + col];
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) mma3_tf32(acc[mt][nt], ah[mt], al[mt], bh0, bh1, bl0, bl1);
+      }
+    }
+    if (valid) {
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt) {
+        const int r0 = nt * 8 + 2 * t, r1 = r0 + 1;
+        if (r0 < R) W4[(int64_t)r0 * n4 + e4] = make_float4(acc[0][nt][0], acc[0][nt][2], acc[1][nt][0], acc[1][nt][2]);
+        if (r1 < R) W4[(int64_t)r1 * n4 + e4] = make_float4(acc[0][nt][1], acc[0][nt][3], acc[1][nt][1], acc[1][nt][3]);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
 
@@ -268,7 +398,19 @@ inline int block_update(const Ctx& c, const float* V, int K, const std::vector<d
   if (R <= 2) rc = go(gtrans_kernel<2>);
   else if (R <= 4) rc = go(gtrans_kernel<4>);
   else if (R <= 8) rc = go(gtrans_kernel<8>);
-  else rc = go(gtrans_kernel<16>);
+  else {  // 9..16 columns: tensor cores, coefficients split into TF32 parts in shared memory
+    const int K8 = (K + (has_t ? R : 0) + 7) / 8 * 8;
+    const size_t msmem = (size_t)K8 * 16 * 2 * sizeof(uint32_t);
+    if (msmem > 200 * 1024) return set_error(DFM_ERR_ARG, "block solve: too many basis vectors for one update");
+    DFM_CUDA_CHECK(cudaFuncSetAttribute(gtrans_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msmem));
+    int per_sm = 0;
+    DFM_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gtrans_mma_kernel, 256, msmem));
+    const int64_t tiles = ((c.n >> 2) + 7) / 8;
+    const unsigned grid =
+        (unsigned)std::max<int64_t>(1, std::min<int64_t>((tiles + 7) / 8, (int64_t)std::max(per_sm, 1) * c.nsm));
+    ::dfm::KernelTimer timer_(DFM_KERNEL_AXPY, c.st);
+    gtrans_mma_kernel<<<grid, 256, msmem, c.st>>>(V, K, bs.small, has_t ? 1 : 0, W, R, c.n);
+  }
   if (rc) return rc;
   DFM_LAUNCHED();
   DFM_CUDA_CHECK(cudaGetLastError());
