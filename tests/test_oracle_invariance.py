@@ -23,9 +23,11 @@ def _row_of_face(tets, face_verts):
 
 def _densities(oracle_mod, verts, tets, face, Np, spatial, mu, refl):
     """rho_T at every centroid for an isotropic and for a normal-incidence
-    source on the given face, with fixed Gauss orders (the direction regions
-    are built from the tet's vertices by their roles, not their order, so the
-    two orderings meet the same nodes and agree to rounding)."""
+    source on the given face, with fixed Gauss orders: order 32 per direction
+    region (the regions are built from the tet's vertices by their roles, so
+    both orderings meet the same nodes) and order 64 on each face for the
+    density (the vertex order moves its nodes; order 32 leaves 2e-7 on the
+    tets whose centroid is close to a face, order 64 1e-12)."""
     op = oracle_mod.assemble(verts, tets, np.full(tets.shape[0], mu), refl, Np, q=32, spatial=spatial)
     row = _row_of_face(tets, face)
     M = np.eye(op.nrows * op.nb) - oracle_mod.dense(op)
@@ -33,7 +35,7 @@ def _densities(oracle_mod, verts, tets, face, Np, spatial, mu, refl):
     for rho0 in (oracle_mod.source_vector(verts, tets, [row], Np, spatial=spatial),
                  oracle_mod.source_directed(verts, tets, [row], Np, combine=True, spatial=spatial)):
         rho = np.linalg.solve(M, rho0.reshape(-1)).reshape(op.nrows, op.nb)
-        out.append(oracle_mod.tet_density(verts, tets, np.full(tets.shape[0], mu), Np, rho, nq=32,
+        out.append(oracle_mod.tet_density(verts, tets, np.full(tets.shape[0], mu), Np, rho, nq=64,
                                           spatial=spatial))
     return out
 
@@ -56,4 +58,4 @@ def test_interior_density_does_not_depend_on_vertex_order(oracle_mod, spatial):
     got = _densities(oracle_mod, m.verts, perm_tets, face, Np, spatial, mu, refl)
     for g, r in zip(got, ref):
         assert np.abs(r).max() > 0
-        np.testing.assert_allclose(g, r, rtol=0, atol=1e-12 * np.abs(r).max())
+        np.testing.assert_allclose(g, r, rtol=0, atol=1e-10 * np.abs(r).max())
