@@ -125,7 +125,7 @@ def _densities(D, mesh, m, Np, mu, rho, nq):
     return D.tet_density(mesh, Np, g, rho).cpu().numpy()
 
 
-@pytest.mark.parametrize("case", ["cuboid_n2_np4", "cuboid_n4_np4", "cuboid_n4_np8"])
+@pytest.mark.parametrize("case", ["cuboid_n2_np4", "cuboid_n4_np4", "cuboid_n4_np8", "cuboid_n2_np12"])
 def test_cuboid_matches_oracle_and_exact_solution(D, oracle_mod, case):
     """The GPU's interior densities with the default face rule (nq = 0, the
     split polar rule) against the oracle's adaptive cubature of Eq. IntDens
