@@ -12,7 +12,8 @@ three orthonormal affine functions per face in place of the constant one.
   weighted by the source function at the ray's start and the receiving
   function at its exit;
 - the interior-density functional of the linear functions against a numpy
-  collapsed Gauss rule of its definition (Eq. IntDens).
+  collapsed Gauss rule of its definition (Eq. IntDens);
+- sources of constant densities have no linear component (zero mean).
 """
 import numpy as np
 import pytest
@@ -125,3 +126,23 @@ def test_interior_density_linear_basis(oracle_mod):
         phi = C @ np.stack([1 - l1 - l2, l1, l2])
         ref = np.concatenate([(ker * phi[a]) @ Z for a in range(3)]) / np.sqrt(A[l])
         np.testing.assert_allclose(g[l], ref, atol=1e-10 * np.abs(ref).max())
+
+
+def test_constant_densities_project_on_the_constant_function(oracle_mod):
+    """A density constant over a face has no component along the linear
+    functions (they have zero mean), so both sources of the linear basis are
+    the constant basis' coefficients followed by zeros."""
+    m = kuhn_cube_mesh(2, jitter=0.2, seed=11)
+    topo = oracle_mod.topology(m.tets)
+    rows = np.nonzero(topo.boundary)[0][:5]
+    Np = 3
+    nz = oracle_mod.nbasis(Np)
+    e1, e2, nn = oracle_mod.face_frames(m.verts, m.tets)
+    dirs = nn[rows] + 0.3 * e1[rows] - 0.2 * e2[rows]
+    for p0, p1 in ((oracle_mod.source_vector(m.verts, m.tets, rows, Np),
+                    oracle_mod.source_vector(m.verts, m.tets, rows, Np, spatial=1)),
+                   (oracle_mod.source_directed(m.verts, m.tets, rows, Np, dirs=dirs),
+                    oracle_mod.source_directed(m.verts, m.tets, rows, Np, dirs=dirs, spatial=1))):
+        assert p1.shape[-1] == 3 * nz
+        np.testing.assert_array_equal(p1[..., :nz], p0)
+        assert not np.any(p1[..., nz:])
